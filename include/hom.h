@@ -1,0 +1,170 @@
+/*
+ * hom.h — C ABI of the GB300 Fourier-Galerkin homogenization library (libhom).
+ *
+ * The library solves the discrete corrector problems of Mishra, Vondrejc & Zeman,
+ * "A comparative study on low-memory iterative solvers for FFT-based homogenization of
+ * periodic media" (arXiv:1508.02045), on one CUDA GPU:
+ *
+ *   (A_H E, E) = min over e in E_N of a(E + e, E + e)                 Section 2, eq. (homog_form)
+ *   C x = b,  C = G A,  b = -G A E                                     Section 2.3, eq. (linsys)
+ *
+ * with G = F^{-1} Gamma^ F the projection of eq. (discrete_proj), Gamma^(k) = k k^T / (k.k),
+ * Gamma^(0) = 0 (eq. (proj)), and A either sampled at the grid nodes (GaNi, Section 2.2) or
+ * assembled on the double grid M = 2N - 1 from its Fourier coefficients (Ga, eq.
+ * (Ga_exact_integration)). The four solvers are Algorithms 1-4 of Section 3.
+ *
+ * Conventions shared by every entry point
+ *  - Grids. d is 2 or 3; every N_a is odd (Section 2.1). A field on a grid of order N is d
+ *    contiguous components, each an array N_1 x ... x N_d in C order (axis d contiguous);
+ *    component a belongs to spatial axis a. Along every axis, storage index j holds the node
+ *    x = m / N_a with signed index m = j for j <= (N_a - 1)/2 and m = j - N_a otherwise, so
+ *    index 0 is the node x = 0 ("FFT-natural order"). Fourier coefficients use the same order.
+ *  - Inner products and norms carry the 1/|N| weight of the Notation section.
+ *  - Supported axis lengths: odd, 3 to 1023, every prime factor at most 31.
+ *  - Pointers named *_dev are device pointers (cudaMalloc or torch tensors) on the device that
+ *    was current at hom_create; all other array pointers are host pointers.
+ *  - Work is issued on the stream passed to hom_create; every call that returns results to
+ *    the host synchronises that stream before returning.
+ *  - Every entry point returns a hom_status. On an error no output is written unless stated.
+ *  - Ownership: hom_create copies the coefficient data; the caller keeps its buffers. The
+ *    problem handle owns all device memory it allocates; hom_destroy frees it.
+ */
+#ifndef HOM_H
+#define HOM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hom_problem hom_problem;
+
+typedef enum {
+  HOM_OK = 0,
+  HOM_ERR_INVALID = 1,        /* bad argument (even N, d not 2/3, non-SPD phase, ...)     */
+  HOM_ERR_OOM = 2,            /* device allocation failed                                  */
+  HOM_ERR_UNSUPPORTED = 3,    /* e.g. Eyre-Milton with exact integration (Section 3.4)     */
+  HOM_ERR_NOT_CONVERGED = 4,  /* iteration limit reached; results are still written        */
+  HOM_ERR_CUDA = 5,           /* a CUDA call failed                                        */
+  HOM_ERR_TIMEOUT = 6         /* a bounded device-side wait expired                        */
+} hom_status;
+
+typedef enum { HOM_APPROX = 0 /* GaNi: A sampled at the nodes */,
+               HOM_EXACT = 1  /* Ga: A_M on the double grid   */ } hom_integration;
+
+typedef enum { HOM_RICHARDSON = 0, HOM_CG = 1, HOM_CHEBYSHEV = 2, HOM_EYRE_MILTON = 3 } hom_solver;
+
+typedef enum { HOM_FP64 = 0 /* all arithmetic in FP64 */,
+               HOM_FP32_REFINED = 1 /* FP32 operator inside FP64 iterative refinement */ } hom_precision;
+
+typedef enum {
+  HOM_A_PHASE = 0,   /* phase index per node (uint8 or uint16) + nphase x d x d SPD table   */
+  HOM_A_SCALAR = 1,  /* one isotropic conductivity (double) per node                         */
+  HOM_A_FOURIER = 2  /* exact integration only: isotropic coefficients A^(n), n in Z_M, as
+                        interleaved complex doubles (re, im) in FFT-natural order on the
+                        double grid M (eq. (Ga_exact_integration))                           */
+} hom_material_kind;
+
+typedef struct {
+  int kind;              /* hom_material_kind                                                */
+  const void* data;      /* PHASE: |N| indices; SCALAR: |N| doubles; FOURIER: |M| complex    */
+  int index_bytes;       /* PHASE: 1 (uint8) or 2 (uint16)                                    */
+  const double* table;   /* PHASE: nphase row-major symmetric d x d tensors (host)            */
+  int nphase;            /* PHASE: table length                                               */
+  int data_on_device;    /* 1 if data is a device pointer                                     */
+  double cA, CA;         /* bounds of eq. (A); 0 = derive from the table / field. Required for
+                            FOURIER (A_M itself may be indefinite, Section 4.1)              */
+  int M[3];              /* FOURIER: odd double-grid order per axis, 0 = 2N - 1 (any odd
+                            M >= 2N - 1 integrates the Ga bilinear form exactly)              */
+} hom_material;
+
+typedef enum { HOM_STOP_DEFAULT = 0, HOM_STOP_RESIDUAL = 1, HOM_STOP_INCREMENT = 2 } hom_stop;
+
+typedef struct {
+  int maxit;          /* iteration limit (0 = 100000)                                         */
+  int fixed_iters;    /* > 0: run exactly this many iterations, no stopping test              */
+  int stop;           /* hom_stop. DEFAULT: residual ||b - C x|| <= tol ||b|| for Richardson,
+                         CG and Chebyshev; increment ||x_m - x_{m-1}|| <= tol ||E|| for
+                         Eyre-Milton (Algorithms 1-4 print the increment test for Richardson) */
+  double cA, CA;      /* override of the spectral bounds used by Richardson, Chebyshev, EM    */
+  double inner_tol;   /* HOM_FP32_REFINED: relative tolerance of each FP32 inner solve (0=1e-4)*/
+  int check_every;    /* host polls the device stopping flag every this many iterations (0=8) */
+} hom_opts;
+
+typedef struct {
+  int iterations;     /* iterations of the (outer) solver                                      */
+  int matvecs;        /* applications of the FFT-based operator                                */
+  int inner_iterations;/* HOM_FP32_REFINED: total FP32 inner iterations                        */
+  int converged;
+  double residual;    /* last stopping quantity, relative (residual / ||b|| or increment / ||E||)*/
+  double true_residual; /* ||b - C x|| / ||b|| recomputed at exit                              */
+  double time_ms;     /* device time of the solve                                              */
+} hom_stats;
+
+typedef enum {
+  HOM_OP_AFFINE = 0,  /* y = G A (E + x) = C x - b                 eq. (linsys)                */
+  HOM_OP_LINEAR = 1,  /* y = G A x = C x                                                        */
+  HOM_OP_PROJECT = 2, /* y = G x                                   eq. (discrete_proj)          */
+  HOM_OP_EM = 3       /* y = F^{-1}(I - 2 G^)F (A - omega I) x     Algorithm 4, omega = sqrt(cA CA)*/
+} hom_op;
+
+/* Create a problem on grid N (GaNi: the solve grid; Ga: the trigonometric order, the solve grid
+ * is M). Validates the arguments, copies the coefficients to the device (Ga: assembles
+ * A_M^k = sum_n omega_M^{kn} A^(n) with the library's inverse FFT, eq. (Ga_exact_integration)),
+ * plans the odd-length FFTs and allocates the solver state (Section 3 storage) and one
+ * half-spectrum work buffer. stream: a cudaStream_t or NULL for the legacy default stream.
+ * Errors: HOM_ERR_INVALID, HOM_ERR_OOM, HOM_ERR_CUDA; *out is set only on HOM_OK. */
+int hom_create(int d, const int* N, const hom_material* A, int integration, int precision,
+               void* stream, hom_problem** out);
+
+/* Solve-grid order (GaNi: N, Ga: M) into M_out[0..d-1]; number of nodes into *nodes. */
+int hom_grid(const hom_problem* P, int* M_out, long long* nodes);
+
+/* Spectral bounds c_A, C_A used by the solvers (eq. (A)). */
+int hom_bounds(const hom_problem* P, double* cA, double* CA);
+
+/* One application of the FFT-based operator (see hom_op) on device fields x_dev -> y_dev
+ * (d x |grid| doubles each; x_dev may equal y_dev). E (host, d doubles) is read by
+ * HOM_OP_AFFINE only. Enqueued on the problem's stream; does not synchronise. */
+int hom_apply(hom_problem* P, int op, const double* E, const double* x_dev, double* y_dev);
+
+/* Solve C x = b (eq. (linsys)) for macroscopic field E (host, d doubles) with the given solver
+ * and tolerance, starting from x_0 = 0 (Eyre-Milton: x_0 = E). Writes, when non-NULL:
+ * x_dev (device, d x |grid|): the corrector e (Eyre-Milton: e = G x_m, Section 4.4);
+ * AH_EE: (A_H E, E) as the energy (A(E + e), E + e) on the solve grid (eqs. (GaNi),
+ * (ev_bounds_Ga)); flux (d doubles): <A(E + e)>; stats. Eyre-Milton with HOM_EXACT returns
+ * HOM_ERR_UNSUPPORTED (Section 3.4). Returns HOM_ERR_NOT_CONVERGED, with outputs written, when
+ * the iteration limit stops the solve. Synchronises the stream. */
+int hom_solve(hom_problem* P, const double* E, int solver, double tol, const hom_opts* opts,
+              double* x_dev, double* AH_EE, double* flux, hom_stats* stats);
+
+/* Energy (A(E + x), E + x) and flux <A(E + x)> of a device field x_dev on the solve grid
+ * (x_dev may be NULL for x = 0, the Voigt value of Section 4.3). Synchronises the stream. */
+int hom_energy(hom_problem* P, const double* E, const double* x_dev, double* energy, double* flux);
+
+/* Prolongation R_{N,M} = I_M o I_N^{-1} (eq. (ev_bounds)): the trigonometric polynomial with
+ * nodal values x_dev on the grid of `coarse` sampled on the solve grid of `fine`
+ * (every M_a >= N_a, odd). Output y_dev: d x |M| doubles on the device. */
+int hom_prolongate(hom_problem* coarse, hom_problem* fine, const double* x_dev, double* y_dev);
+
+/* Guaranteed upper bound of eq. (ev_bounds_GaNi): U_E(R_{N,M}[E + x]) with x_dev a GaNi field
+ * of problem `gani` and A_M of the exact-integration problem `ga` built for the same N.
+ * Synchronises the stream. */
+int hom_bound(hom_problem* gani, hom_problem* ga, const double* E, const double* x_dev,
+              double* UE);
+
+/* Free everything the handle owns. NULL is accepted. */
+void hom_destroy(hom_problem* P);
+
+/* Static description of a status code. */
+const char* hom_strerror(int status);
+
+/* Number of kernels the library has launched in this process (a monotone counter). */
+long long hom_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HOM_H */

@@ -1,0 +1,269 @@
+"""Python binding of libhom (include/hom.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module converts NumPy arrays and torch
+CUDA tensors to the plain pointers and sizes of the C ABI, and raises on any non-zero status.
+The library must have been built (``paper_1508_02045_gb300.build.build()``); importing this
+module without it fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhom.so")
+
+HOM_OK, HOM_ERR_INVALID, HOM_ERR_OOM, HOM_ERR_UNSUPPORTED, HOM_ERR_NOT_CONVERGED, HOM_ERR_CUDA, \
+    HOM_ERR_TIMEOUT = range(7)
+HOM_APPROX, HOM_EXACT = 0, 1
+HOM_RICHARDSON, HOM_CG, HOM_CHEBYSHEV, HOM_EYRE_MILTON = range(4)
+HOM_FP64, HOM_FP32_REFINED = 0, 1
+HOM_A_PHASE, HOM_A_SCALAR, HOM_A_FOURIER = range(3)
+HOM_STOP_DEFAULT, HOM_STOP_RESIDUAL, HOM_STOP_INCREMENT = range(3)
+HOM_OP_AFFINE, HOM_OP_LINEAR, HOM_OP_PROJECT, HOM_OP_EM = range(4)
+
+SOLVERS = {"richardson": HOM_RICHARDSON, "cg": HOM_CG, "chebyshev": HOM_CHEBYSHEV,
+           "eyre_milton": HOM_EYRE_MILTON}
+
+EXPORTED = ["hom_create", "hom_grid", "hom_bounds", "hom_apply", "hom_solve", "hom_energy",
+            "hom_prolongate", "hom_bound", "hom_destroy", "hom_strerror", "hom_kernel_launches"]
+
+
+class hom_material(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("data", ctypes.c_void_p), ("index_bytes", ctypes.c_int),
+                ("table", ctypes.POINTER(ctypes.c_double)), ("nphase", ctypes.c_int),
+                ("data_on_device", ctypes.c_int), ("cA", ctypes.c_double), ("CA", ctypes.c_double),
+                ("M", ctypes.c_int * 3)]
+
+
+class hom_opts(ctypes.Structure):
+    _fields_ = [("maxit", ctypes.c_int), ("fixed_iters", ctypes.c_int), ("stop", ctypes.c_int),
+                ("cA", ctypes.c_double), ("CA", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("check_every", ctypes.c_int)]
+
+
+class hom_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("matvecs", ctypes.c_int),
+                ("inner_iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("residual", ctypes.c_double), ("true_residual", ctypes.c_double),
+                ("time_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libhom.so is not built ({LIB_PATH}); run paper_1508_02045_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+    lib.hom_create.argtypes = [ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(hom_material), ip, ip,
+                               vp, ctypes.POINTER(vp)]
+    lib.hom_grid.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]
+    lib.hom_bounds.argtypes = [vp, dp, dp]
+    lib.hom_apply.argtypes = [vp, ip, dp, vp, vp]
+    lib.hom_solve.argtypes = [vp, dp, ip, ctypes.c_double, ctypes.POINTER(hom_opts), vp, dp, dp,
+                              ctypes.POINTER(hom_stats)]
+    lib.hom_energy.argtypes = [vp, dp, vp, dp, dp]
+    lib.hom_prolongate.argtypes = [vp, vp, vp, vp]
+    lib.hom_bound.argtypes = [vp, vp, dp, vp, dp]
+    lib.hom_destroy.argtypes = [vp]
+    lib.hom_destroy.restype = None
+    lib.hom_strerror.argtypes = [ip]
+    lib.hom_strerror.restype = ctypes.c_char_p
+    lib.hom_kernel_launches.argtypes = []
+    lib.hom_kernel_launches.restype = ctypes.c_longlong
+    for name in EXPORTED:
+        if name not in ("hom_destroy", "hom_strerror", "hom_kernel_launches"):
+            getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+_lib = _load()
+
+
+class HomError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {hom_strerror(status)} (status {status})")
+
+
+def _check(status, where):
+    if status != HOM_OK:
+        raise HomError(status, where)
+    return status
+
+
+def _dvec(values):
+    arr = (ctypes.c_double * len(values))(*[float(v) for v in values])
+    return arr
+
+
+def _ptr(t):
+    """Device pointer of a torch CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# ------------------------------------------------------------------------------------------
+# the C entry points under their own names
+# ------------------------------------------------------------------------------------------
+
+def hom_strerror(status: int) -> str:
+    return _lib.hom_strerror(int(status)).decode()
+
+
+def hom_kernel_launches() -> int:
+    return int(_lib.hom_kernel_launches())
+
+
+def hom_create(d, N, material: hom_material, integration=HOM_APPROX, precision=HOM_FP64,
+               stream=None):
+    vals = [int(v) for v in N] + [1] * max(0, 3 - len(N))
+    Narr = (ctypes.c_int * len(vals))(*vals)
+    out = ctypes.c_void_p()
+    st = _stream() if stream is None else ctypes.c_void_p(stream)
+    _check(_lib.hom_create(int(d), Narr, ctypes.byref(material), int(integration), int(precision),
+                           st, ctypes.byref(out)), "hom_create")
+    return out
+
+
+def hom_grid(P):
+    M = (ctypes.c_int * 3)()
+    n = ctypes.c_longlong()
+    _check(_lib.hom_grid(P, M, ctypes.byref(n)), "hom_grid")
+    return list(M), n.value
+
+
+def hom_bounds(P):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.hom_bounds(P, ctypes.byref(a), ctypes.byref(b)), "hom_bounds")
+    return a.value, b.value
+
+
+def hom_apply(P, op, E, x, y):
+    Ep = _dvec(E) if E is not None else None
+    return _check(_lib.hom_apply(P, int(op), Ep, _ptr(x), _ptr(y)), "hom_apply")
+
+
+def hom_solve(P, E, solver, tol, opts: hom_opts | None = None, x=None, allow_not_converged=False):
+    AH = ctypes.c_double()
+    d = len(E)
+    flux = (ctypes.c_double * 3)()
+    stats = hom_stats()
+    o = ctypes.byref(opts) if opts is not None else None
+    st = _lib.hom_solve(P, _dvec(E), int(solver), float(tol), o, _ptr(x), ctypes.byref(AH), flux,
+                        ctypes.byref(stats))
+    if not (st == HOM_OK or (allow_not_converged and st == HOM_ERR_NOT_CONVERGED)):
+        raise HomError(st, "hom_solve")
+    return AH.value, [flux[i] for i in range(d)], stats.as_dict(), st
+
+
+def hom_energy(P, E, x=None):
+    en = ctypes.c_double()
+    flux = (ctypes.c_double * 3)()
+    _check(_lib.hom_energy(P, _dvec(E), _ptr(x), ctypes.byref(en), flux), "hom_energy")
+    return en.value, [flux[i] for i in range(len(E))]
+
+
+def hom_prolongate(coarse, fine, x, y):
+    return _check(_lib.hom_prolongate(coarse, fine, _ptr(x), _ptr(y)), "hom_prolongate")
+
+
+def hom_bound(gani, ga, E, x):
+    ue = ctypes.c_double()
+    _check(_lib.hom_bound(gani, ga, _dvec(E), _ptr(x), ctypes.byref(ue)), "hom_bound")
+    return ue.value
+
+
+def hom_destroy(P):
+    if P:
+        _lib.hom_destroy(P)
+
+
+# ------------------------------------------------------------------------------------------
+# material descriptors (marshalling of host arrays; the arrays must outlive hom_create)
+# ------------------------------------------------------------------------------------------
+
+def phase_material(phase: np.ndarray, table: np.ndarray, cA=0.0, CA=0.0):
+    phase = np.ascontiguousarray(phase)
+    if phase.dtype not in (np.uint8, np.uint16):
+        raise ValueError("phase image must be uint8 or uint16")
+    table = np.ascontiguousarray(table, dtype=np.float64)
+    m = hom_material()
+    m.kind = HOM_A_PHASE
+    m.data = phase.ctypes.data
+    m.index_bytes = phase.dtype.itemsize
+    m.table = table.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    m.nphase = table.shape[0]
+    m.cA, m.CA = cA, CA
+    m._keep = (phase, table)
+    return m
+
+
+def scalar_material(a: np.ndarray, cA=0.0, CA=0.0):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    m = hom_material()
+    m.kind = HOM_A_SCALAR
+    m.data = a.ctypes.data
+    m.cA, m.CA = cA, CA
+    m._keep = (a,)
+    return m
+
+
+def fourier_material(Ahat: np.ndarray, cA, CA, M=None):
+    c = np.ascontiguousarray(Ahat, dtype=np.complex128)
+    m = hom_material()
+    m.kind = HOM_A_FOURIER
+    m.data = c.ctypes.data
+    m.cA, m.CA = cA, CA
+    if M is not None:
+        for i, v in enumerate(M):
+            m.M[i] = int(v)
+    m._keep = (c,)
+    return m
+
+
+def make_opts(maxit=0, fixed_iters=0, stop=HOM_STOP_DEFAULT, cA=0.0, CA=0.0, inner_tol=0.0,
+              check_every=0):
+    o = hom_opts()
+    o.maxit, o.fixed_iters, o.stop = maxit, fixed_iters, stop
+    o.cA, o.CA, o.inner_tol, o.check_every = cA, CA, inner_tol, check_every
+    return o
+
+
+class Problem:
+    """Owning wrapper of a hom_problem handle."""
+
+    def __init__(self, d, N, material, integration=HOM_APPROX, precision=HOM_FP64):
+        self.d = d
+        self.N = tuple(N)
+        self.material = material
+        self.h = hom_create(d, N, material, integration, precision)
+        self.grid, self.nodes = hom_grid(self.h)
+        self.grid = tuple(self.grid[:d])
+
+    def field(self, dtype=None):
+        import torch
+        return torch.zeros((self.d,) + self.grid, dtype=dtype or torch.float64, device="cuda")
+
+    def close(self):
+        if self.h:
+            hom_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

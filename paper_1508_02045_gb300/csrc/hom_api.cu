@@ -1,0 +1,921 @@
+// C ABI of libhom (include/hom.h): problem set-up, operator applications and the solver
+// drivers of Algorithms 1-4 on top of the fused FFT passes (passes.cuh).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/hom.h"
+#include "ops.h"
+#include "passes.cuh"
+
+using namespace hom;
+
+namespace hom {
+long long& launch_counter() {
+  static long long c = 0;
+  return c;
+}
+int dynamic_smem_cap() {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return optin - 1024;
+}
+}  // namespace hom
+
+namespace {
+
+constexpr long long kMaxNodes = 1LL << 31;
+
+#define HOM_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) {                            \
+      last_cuda_error() = e_;                           \
+      return e_ == cudaErrorMemoryAllocation ? HOM_ERR_OOM : HOM_ERR_CUDA; \
+    }                                                   \
+  } while (0)
+
+cudaError_t& last_cuda_error() {
+  static cudaError_t e = cudaSuccess;
+  return e;
+}
+
+// ---------------------------------------------------------------------------------------
+// planning
+// ---------------------------------------------------------------------------------------
+bool plan_axis(int n, AxisPlan* P) {
+  if (n < 3 || n > kMaxAxis || n % 2 == 0) return false;
+  int rem = n, nst = 0;
+  const int order[] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31};
+  for (int R : order) {
+    while (rem % R == 0) {
+      if (nst >= kMaxStages) return false;
+      P->radix[nst++] = R;
+      rem /= R;
+    }
+  }
+  if (rem != 1) return false;
+  P->n = n;
+  P->nst = nst;
+  int p = 1;
+  for (int s = 0; s < nst; ++s) {
+    P->pprev[s] = p;
+    p *= P->radix[s];
+  }
+  for (int s = nst; s < kMaxStages; ++s) P->radix[s] = P->pprev[s] = 0;
+  return true;
+}
+
+template <typename T>
+std::vector<cpx<T>> twiddles(int n) {
+  std::vector<cpx<T>> tw(n);
+  const long double twopi = 6.283185307179586476925286766559005768L;
+  for (int j = 0; j < n; ++j) {
+    const long double t = -twopi * (long double)j / (long double)n;
+    tw[j].x = (T)cosl(t);
+    tw[j].y = (T)sinl(t);
+  }
+  return tw;
+}
+
+// Largest even LB (lines per CTA in the line passes) whose buffers fit the budget.
+template <typename T>
+int pick_LB(int n, int ncomp, size_t budget) {
+  int LB = 16;
+  while (LB > 2 && Ops<T>::smem_line(n, ncomp, LB) > budget) LB -= 2;
+  return LB;
+}
+
+template <typename T>
+void pick_TC(int n, int ncols_avail, int nbuf_extra, size_t budget, int* TC, int* TCp, bool proj,
+             int D) {
+  int tc = 16;
+  auto need = [&](int t) {
+    const int tp = t + ((t % 2 == 0) ? 1 : 0);  // odd pitch: conflict-free column access
+    return proj ? Ops<T>::smem_proj(n, D, tp) : Ops<T>::smem_strided(n, tp);
+  };
+  while (tc > 2 && need(tc) > budget) tc /= 2;
+  (void)ncols_avail;
+  (void)nbuf_extra;
+  *TC = tc;
+  *TCp = tc + ((tc % 2 == 0) ? 1 : 0);
+}
+
+// ---------------------------------------------------------------------------------------
+// per-precision engine: plans, twiddles, geometry, spectrum buffer view
+// ---------------------------------------------------------------------------------------
+template <typename T>
+struct Engine {
+  PassGeom g{};
+  PassGeom g1{};  // same grid, one component (Ga assembly)
+  AxisPlan plan[3]{};
+  cpx<T>* tw[3] = {nullptr, nullptr, nullptr};
+  ProjGeom pg{};
+  MatView<T> mat{};
+  T* field = nullptr;  // MAT_FIELD storage in precision T
+  bool ready = false;
+
+  int init(int D, const int* n, const int* support, size_t budget) {
+    g.D = D;
+    g.nodes = 1;
+    for (int a = 0; a < D; ++a) {
+      g.n[a] = n[a];
+      g.nodes *= n[a];
+      if (!plan_axis(n[a], &plan[a])) return HOM_ERR_INVALID;
+    }
+    for (int a = D; a < 3; ++a) g.n[a] = 1;
+    const int nl = n[D - 1];
+    g.nh = (nl + 1) / 2;
+    g.nlines = g.nodes / nl;
+    g.scs = g.nlines * g.nh;
+    g.LB = pick_LB<T>(nl, D, budget);
+    if (D == 3) pick_TC<T>(n[1], g.nh, 0, budget, &g.TC1, &g.TC1p, false, D);
+    pick_TC<T>(n[0], (int)std::min<long long>(g.scs / n[0], 1 << 30), 0, budget, &g.TC0, &g.TC0p,
+               true, D);
+    g1 = g;
+    g1.LB = pick_LB<T>(nl, 1, budget);
+    for (int a = 0; a < D; ++a) {
+      auto tw_h = twiddles<T>(n[a]);
+      if (cudaMalloc(&tw[a], sizeof(cpx<T>) * n[a]) != cudaSuccess) return HOM_ERR_OOM;
+      if (cudaMemcpy(tw[a], tw_h.data(), sizeof(cpx<T>) * n[a], cudaMemcpyHostToDevice) != cudaSuccess)
+        return HOM_ERR_CUDA;
+    }
+    pg.C = g.scs / n[0];
+    pg.cs = g.scs;
+    pg.n1 = (D == 3) ? n[1] : 1;
+    pg.nh = g.nh;
+    for (int a = 0; a < 3; ++a) pg.hw[a] = (a < D) ? (support[a] - 1) / 2 : 0;
+    pg.scale = 1.0 / (double)g.nodes;
+    // every pass must fit the per-CTA shared-memory limit
+    const size_t cap = (size_t)dynamic_smem_cap();
+    if (Ops<T>::smem_line(nl, D, g.LB) > cap || Ops<T>::smem_proj(n[0], D, g.TC0p) > cap ||
+        (D == 3 && Ops<T>::smem_strided(n[1], g.TC1p) > cap))
+      return HOM_ERR_UNSUPPORTED;
+    ready = true;
+    return HOM_OK;
+  }
+
+  void release() {
+    for (auto& t : tw) {
+      if (t) cudaFree(t);
+      t = nullptr;
+    }
+    if (field) cudaFree(field);
+    field = nullptr;
+  }
+
+  // forward transform of the contiguous axis and the middle axis (D = 3) up to axis 0
+  // y = post( F^{-1} proj F pre(x) ): one full operator application
+  void apply(int pre, int mode, int post, const Fields<T>& f, cpx<T>* S, Scalars* sc,
+             const OpArgs& args, double* partials, unsigned* counter, int negate,
+             cudaStream_t st) const {
+    apply2(pre, mode, post, f, f, S, sc, args, partials, counter, negate, st);
+  }
+
+  // same, with separate buffer sets for the pre-operator (ff) and the post-operator (fi)
+  void apply2(int pre, int mode, int post, const Fields<T>& ff, const Fields<T>& fi, cpx<T>* S,
+              Scalars* sc, const OpArgs& args, double* partials, unsigned* counter, int negate,
+              cudaStream_t st) const {
+    Ops<T>::line_fwd(g, pre, ff, S, plan[g.D - 1], tw[g.D - 1], g.D, mat, sc, args, st);
+    if (g.D == 3) Ops<T>::strided(g, 1, 0, S, plan[1], tw[1], g.D, sc, st);
+    Ops<T>::proj(g, mode, S, plan[0], tw[0], pg, sc, st);
+    if (g.D == 3) Ops<T>::strided(g, 1, 1, S, plan[1], tw[1], g.D, sc, st);
+    Ops<T>::line_inv(g, post, S, fi, plan[g.D - 1], tw[g.D - 1], g.D, mat, sc, args, partials,
+                     counter, negate, st);
+  }
+
+  // plain forward transform (no projection), result is the unscaled half spectrum
+  void forward(const T* x, cpx<T>* S, int ncomp, cudaStream_t st) const {
+    const PassGeom& gg = (ncomp == 1) ? g1 : g;
+    Fields<T> f{};
+    f.xin = x;
+    f.cs = g.nodes;
+    OpArgs args{};
+    Ops<T>::line_fwd(gg, PRE_IDENT, f, S, plan[g.D - 1], tw[g.D - 1], ncomp, mat, nullptr, args, st);
+    if (g.D == 3) Ops<T>::strided(gg, 1, 0, S, plan[1], tw[1], ncomp, nullptr, st);
+    Ops<T>::strided(gg, 0, 0, S, plan[0], tw[0], ncomp, nullptr, st);
+  }
+
+  // plain inverse transform (no scaling) of a half spectrum into real fields
+  void inverse(cpx<T>* S, T* y, int ncomp, cudaStream_t st) const {
+    const PassGeom& gg = (ncomp == 1) ? g1 : g;
+    Ops<T>::strided(gg, 0, 1, S, plan[0], tw[0], ncomp, nullptr, st);
+    if (g.D == 3) Ops<T>::strided(gg, 1, 1, S, plan[1], tw[1], ncomp, nullptr, st);
+    Fields<T> f{};
+    f.out = y;
+    f.cs = g.nodes;
+    OpArgs args{};
+    Ops<T>::line_inv(gg, POST_STORE, S, f, plan[g.D - 1], tw[g.D - 1], ncomp, mat, nullptr, args,
+                     nullptr, nullptr, 0, st);
+  }
+};
+
+std::once_flag g_const_once;
+cudaError_t g_const_err = cudaSuccess;
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// the problem handle
+// ---------------------------------------------------------------------------------------
+struct hom_problem {
+  int d = 0;
+  int N[3] = {1, 1, 1};     // trigonometric order
+  int M[3] = {1, 1, 1};     // solve grid (N for GaNi, double grid for Ga)
+  int integration = HOM_APPROX;
+  int precision = HOM_FP64;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  long long nodes = 0;
+  double cA = 0, CA = 0;
+
+  // coefficients
+  int mat_kind = MAT_PHASE_ISO;
+  void* d_phase = nullptr;
+  int index_bytes = 1;
+  double* d_table = nullptr;
+  int nphase = 0;
+
+  Engine<double> e64;
+  Engine<float> e32;
+
+  // buffers
+  void* S = nullptr;              // half spectrum work buffer (sized for FP64, d components)
+  size_t S_bytes = 0;
+  double* vbase = nullptr;        // one allocation of 5 d |grid| doubles
+  double* vec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // d x |grid| each
+  float* fvec[4] = {nullptr, nullptr, nullptr, nullptr};           // FP32 inner solves
+  double* partials = nullptr;
+  size_t npartials = 0;
+  unsigned* counter = nullptr;
+  Scalars* d_sc = nullptr;        // solver scalars
+  Scalars* d_aux = nullptr;       // scalars of auxiliary evaluations (energy, true residual)
+  Scalars* h_sc = nullptr;        // pinned host mirror
+  int red_grid = 0;               // grid of the reduction kernels
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+template <typename T>
+MatView<T> make_view(const hom_problem* P, const T* field) {
+  MatView<T> m{};
+  m.kind = P->mat_kind;
+  m.ph8 = (P->mat_kind != MAT_FIELD && P->index_bytes == 1) ? (const uint8_t*)P->d_phase : nullptr;
+  m.ph16 = (P->mat_kind != MAT_FIELD && P->index_bytes == 2) ? (const uint16_t*)P->d_phase : nullptr;
+  m.table = P->d_table;
+  m.field = field;
+  return m;
+}
+
+bool spd_eigs(const double* t, int d, double* lo, double* hi) {
+  // symmetric check + eigenvalue bounds via Jacobi sweeps on a copy
+  double a[3][3];
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) a[i][j] = t[i * d + j];
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < i; ++j)
+      if (std::fabs(a[i][j] - a[j][i]) > 1e-12 * (std::fabs(a[i][j]) + std::fabs(a[j][i]) + 1e-300))
+        return false;
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    double off = 0;
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j)
+        if (i != j) off += a[i][j] * a[i][j];
+    if (off < 1e-30) break;
+    for (int p = 0; p < d; ++p)
+      for (int q = p + 1; q < d; ++q) {
+        if (std::fabs(a[p][q]) < 1e-300) continue;
+        const double th = 0.5 * std::atan2(2 * a[p][q], a[q][q] - a[p][p]);
+        const double c = std::cos(th), s = std::sin(th);
+        for (int k = 0; k < d; ++k) {
+          const double akp = a[k][p], akq = a[k][q];
+          a[k][p] = c * akp - s * akq;
+          a[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < d; ++k) {
+          const double apk = a[p][k], aqk = a[q][k];
+          a[p][k] = c * apk - s * aqk;
+          a[q][k] = s * apk + c * aqk;
+        }
+      }
+  }
+  double mn = a[0][0], mx = a[0][0];
+  for (int i = 1; i < d; ++i) {
+    mn = std::min(mn, a[i][i]);
+    mx = std::max(mx, a[i][i]);
+  }
+  *lo = mn;
+  *hi = mx;
+  return mn > 0;
+}
+
+int alloc(void** p, size_t bytes) {
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return HOM_ERR_OOM;
+  }
+  return HOM_OK;
+}
+
+int check_last() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    last_cuda_error() = e;
+    return HOM_ERR_CUDA;
+  }
+  return HOM_OK;
+}
+
+constexpr size_t kSmemBudget = 110 * 1024;  // two CTAs per SM in every pass
+
+}  // namespace
+
+extern "C" {
+
+const char* hom_strerror(int s) {
+  switch (s) {
+    case HOM_OK: return "ok";
+    case HOM_ERR_INVALID: return "invalid argument";
+    case HOM_ERR_OOM: return "device out of memory";
+    case HOM_ERR_UNSUPPORTED: return "unsupported combination";
+    case HOM_ERR_NOT_CONVERGED: return "iteration limit reached before convergence";
+    case HOM_ERR_CUDA: {
+      static char buf[256];
+      std::snprintf(buf, sizeof buf, "CUDA error: %s", cudaGetErrorString(last_cuda_error()));
+      return buf;
+    }
+    case HOM_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+long long hom_kernel_launches(void) { return launch_counter(); }
+
+void hom_destroy(hom_problem* P) {
+  if (!P) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(P->device);
+  if (P->stream) cudaStreamSynchronize(P->stream);
+  P->e64.release();
+  P->e32.release();
+  if (P->d_phase) cudaFree(P->d_phase);
+  if (P->d_table) cudaFree(P->d_table);
+  if (P->S) cudaFree(P->S);
+  if (P->vbase) cudaFree(P->vbase);
+  for (auto& v : P->fvec)
+    if (v) cudaFree(v);
+  if (P->partials) cudaFree(P->partials);
+  if (P->counter) cudaFree(P->counter);
+  if (P->d_sc) cudaFree(P->d_sc);
+  if (P->d_aux) cudaFree(P->d_aux);
+  if (P->h_sc) cudaFreeHost(P->h_sc);
+  if (P->ev0) cudaEventDestroy(P->ev0);
+  if (P->ev1) cudaEventDestroy(P->ev1);
+  delete P;
+  cudaSetDevice(cur);
+}
+
+int hom_grid(const hom_problem* P, int* M_out, long long* nodes) {
+  if (!P) return HOM_ERR_INVALID;
+  if (M_out)
+    for (int a = 0; a < P->d; ++a) M_out[a] = P->M[a];
+  if (nodes) *nodes = P->nodes;
+  return HOM_OK;
+}
+
+int hom_bounds(const hom_problem* P, double* cA, double* CA) {
+  if (!P) return HOM_ERR_INVALID;
+  if (cA) *cA = P->cA;
+  if (CA) *CA = P->CA;
+  return HOM_OK;
+}
+
+int hom_create(int d, const int* N, const hom_material* A, int integration, int precision,
+               void* stream, hom_problem** out) {
+  if (!out || !N || !A) return HOM_ERR_INVALID;
+  *out = nullptr;
+  if (d != 2 && d != 3) return HOM_ERR_INVALID;
+  if (integration != HOM_APPROX && integration != HOM_EXACT) return HOM_ERR_INVALID;
+  if (precision != HOM_FP64 && precision != HOM_FP32_REFINED) return HOM_ERR_INVALID;
+  for (int a = 0; a < d; ++a)
+    if (N[a] < 3 || N[a] % 2 == 0 || N[a] > kMaxAxis) return HOM_ERR_INVALID;
+  if (integration == HOM_EXACT && A->kind != HOM_A_FOURIER) return HOM_ERR_UNSUPPORTED;
+  if (integration == HOM_APPROX && A->kind == HOM_A_FOURIER) return HOM_ERR_INVALID;
+
+  std::call_once(g_const_once, [] {
+    g_const_err = Ops<double>::upload_constants();
+    if (g_const_err == cudaSuccess) g_const_err = Ops<float>::upload_constants();
+    if (g_const_err == cudaSuccess) g_const_err = Ops<double>::prepare(3);
+    if (g_const_err == cudaSuccess) g_const_err = Ops<float>::prepare(3);
+  });
+  if (g_const_err != cudaSuccess) {
+    last_cuda_error() = g_const_err;
+    return HOM_ERR_CUDA;
+  }
+
+  hom_problem* P = new hom_problem();
+  P->d = d;
+  P->integration = integration;
+  P->precision = precision;
+  P->stream = (cudaStream_t)stream;
+  cudaGetDevice(&P->device);
+  for (int a = 0; a < d; ++a) {
+    P->N[a] = N[a];
+    P->M[a] = N[a];
+  }
+  if (integration == HOM_EXACT) {
+    for (int a = 0; a < d; ++a) {
+      const int m = A->M[a] > 0 ? A->M[a] : 2 * N[a] - 1;
+      if (m < 2 * N[a] - 1 || m % 2 == 0 || m > kMaxAxis) {
+        delete P;
+        return HOM_ERR_INVALID;
+      }
+      P->M[a] = m;
+    }
+  }
+  P->nodes = 1;
+  for (int a = 0; a < d; ++a) P->nodes *= P->M[a];
+  if (P->nodes > kMaxNodes) {
+    delete P;
+    return HOM_ERR_INVALID;
+  }
+  const long long nodes = P->nodes;
+  int st;
+
+  // ---- coefficients ----
+  if (A->kind == HOM_A_PHASE) {
+    if (!A->data || !A->table || A->nphase < 1 || (A->index_bytes != 1 && A->index_bytes != 2) ||
+        (A->index_bytes == 1 && A->nphase > 256)) {
+      delete P;
+      return HOM_ERR_INVALID;
+    }
+    bool iso = true;
+    double lo = 1e300, hi = -1e300;
+    for (int p = 0; p < A->nphase; ++p) {
+      const double* t = A->table + (size_t)p * d * d;
+      double l, h;
+      if (!spd_eigs(t, d, &l, &h)) {
+        delete P;
+        return HOM_ERR_INVALID;
+      }
+      lo = std::min(lo, l);
+      hi = std::max(hi, h);
+      for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j)
+          if ((i != j && t[i * d + j] != 0.0) || (i == j && t[i * d + j] != t[0])) iso = false;
+    }
+    P->cA = lo;
+    P->CA = hi;
+    P->mat_kind = iso ? MAT_PHASE_ISO : MAT_PHASE_TENSOR;
+    P->index_bytes = A->index_bytes;
+    P->nphase = A->nphase;
+    std::vector<double> tab;
+    if (iso) {
+      for (int p = 0; p < A->nphase; ++p) tab.push_back(A->table[(size_t)p * d * d]);
+    } else {
+      tab.assign(A->table, A->table + (size_t)A->nphase * d * d);
+    }
+    if ((st = alloc((void**)&P->d_table, sizeof(double) * tab.size())) != HOM_OK) { hom_destroy(P); return st; }
+    if ((st = alloc(&P->d_phase, (size_t)nodes * A->index_bytes)) != HOM_OK) { hom_destroy(P); return st; }
+    cudaMemcpy(P->d_table, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(P->d_phase, A->data, (size_t)nodes * A->index_bytes,
+               A->data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+    // phase indices must address the table
+    if (!A->data_on_device) {
+      for (long long g = 0; g < nodes; ++g) {
+        const int ph = A->index_bytes == 1 ? ((const uint8_t*)A->data)[g] : ((const uint16_t*)A->data)[g];
+        if (ph >= A->nphase) { hom_destroy(P); return HOM_ERR_INVALID; }
+      }
+    }
+  } else if (A->kind == HOM_A_SCALAR) {
+    if (!A->data) { delete P; return HOM_ERR_INVALID; }
+    P->mat_kind = MAT_FIELD;
+    if ((st = alloc((void**)&P->e64.field, sizeof(double) * nodes)) != HOM_OK) { hom_destroy(P); return st; }
+    cudaMemcpy(P->e64.field, A->data, sizeof(double) * nodes,
+               A->data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+    {
+      std::vector<double> hcopy;
+      const double* a = (const double*)A->data;
+      if (A->data_on_device) {
+        hcopy.resize(nodes);
+        cudaMemcpy(hcopy.data(), A->data, sizeof(double) * nodes, cudaMemcpyDeviceToHost);
+        a = hcopy.data();
+      }
+      double lo = 1e300, hi = -1e300;
+      for (long long g = 0; g < nodes; ++g) {
+        lo = std::min(lo, a[g]);
+        hi = std::max(hi, a[g]);
+      }
+      if (!(lo > 0)) { hom_destroy(P); return HOM_ERR_INVALID; }
+      P->cA = lo;
+      P->CA = hi;
+    }
+  } else if (A->kind == HOM_A_FOURIER) {
+    if (!A->data) { delete P; return HOM_ERR_INVALID; }
+    P->mat_kind = MAT_FIELD;
+  } else {
+    delete P;
+    return HOM_ERR_INVALID;
+  }
+  if (A->cA > 0) P->cA = A->cA;
+  if (A->CA > 0) P->CA = A->CA;
+  if (!(P->cA > 0 && P->CA >= P->cA)) { hom_destroy(P); return HOM_ERR_INVALID; }
+
+  // ---- plans ----
+  if ((st = P->e64.init(d, P->M, P->N, kSmemBudget)) != HOM_OK) { hom_destroy(P); return st; }
+  if (precision == HOM_FP32_REFINED) {
+    if ((st = P->e32.init(d, P->M, P->N, kSmemBudget)) != HOM_OK) { hom_destroy(P); return st; }
+  }
+
+  // ---- buffers ----
+  P->S_bytes = sizeof(cpx<double>) * (size_t)d * P->e64.g.scs;
+  if ((st = alloc(&P->S, P->S_bytes)) != HOM_OK) { hom_destroy(P); return st; }
+  if ((st = alloc((void**)&P->vbase, sizeof(double) * 5 * d * nodes)) != HOM_OK) { hom_destroy(P); return st; }
+  for (int i = 0; i < 5; ++i) P->vec[i] = P->vbase + (size_t)i * d * nodes;
+  if (precision == HOM_FP32_REFINED)
+    for (int i = 0; i < 4; ++i)
+      if ((st = alloc((void**)&P->fvec[i], sizeof(float) * d * nodes)) != HOM_OK) { hom_destroy(P); return st; }
+  P->red_grid = (int)std::min<long long>((nodes * d + kThreads - 1) / kThreads, 152 * 8);
+  long long maxblocks = std::max<long long>(P->red_grid, (P->e64.g.nlines + 1) / 2 + 1);
+  P->npartials = (size_t)maxblocks * 4;
+  if ((st = alloc((void**)&P->partials, sizeof(double) * P->npartials)) != HOM_OK) { hom_destroy(P); return st; }
+  if ((st = alloc((void**)&P->counter, sizeof(unsigned) * 4)) != HOM_OK) { hom_destroy(P); return st; }
+  cudaMemset(P->counter, 0, sizeof(unsigned) * 4);
+  if ((st = alloc((void**)&P->d_sc, sizeof(Scalars))) != HOM_OK) { hom_destroy(P); return st; }
+  if ((st = alloc((void**)&P->d_aux, sizeof(Scalars))) != HOM_OK) { hom_destroy(P); return st; }
+  if (cudaMallocHost((void**)&P->h_sc, sizeof(Scalars)) != cudaSuccess) { hom_destroy(P); return HOM_ERR_OOM; }
+  cudaEventCreate(&P->ev0);
+  cudaEventCreate(&P->ev1);
+
+  P->e64.mat = make_view<double>(P, P->e64.field);
+
+  // ---- Ga: A_M^k = sum_n omega_M^{kn} A^(n) (eq. (Ga_exact_integration)) ----
+  if (A->kind == HOM_A_FOURIER) {
+    if ((st = alloc((void**)&P->e64.field, sizeof(double) * nodes)) != HOM_OK) { hom_destroy(P); return st; }
+    const int D = d;
+    const long long mh = P->e64.g.nh;
+    const long long nl = P->e64.g.nlines;
+    std::vector<double> full((size_t)nodes * 2);
+    if (A->data_on_device)
+      cudaMemcpy(full.data(), A->data, sizeof(double) * 2 * nodes, cudaMemcpyDeviceToHost);
+    else
+      std::memcpy(full.data(), A->data, sizeof(double) * 2 * nodes);
+    std::vector<cpx<double>> half((size_t)nl * mh);
+    const int mlast = P->M[D - 1];
+    for (long long l = 0; l < nl; ++l)
+      for (long long k = 0; k < mh; ++k) {
+        half[l * mh + k].x = full[2 * (l * mlast + k)];
+        half[l * mh + k].y = full[2 * (l * mlast + k) + 1];
+      }
+    cudaMemcpy(P->S, half.data(), sizeof(cpx<double>) * half.size(), cudaMemcpyHostToDevice);
+    P->e64.inverse((cpx<double>*)P->S, P->e64.field, 1, P->stream);
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess || check_last() != HOM_OK) {
+      hom_destroy(P);
+      return HOM_ERR_CUDA;
+    }
+    P->e64.mat = make_view<double>(P, P->e64.field);
+  }
+  if (precision == HOM_FP32_REFINED) {
+    if (P->mat_kind == MAT_FIELD) {
+      if ((st = alloc((void**)&P->e32.field, sizeof(float) * nodes)) != HOM_OK) { hom_destroy(P); return st; }
+      std::vector<double> h(nodes);
+      std::vector<float> hf(nodes);
+      cudaMemcpy(h.data(), P->e64.field, sizeof(double) * nodes, cudaMemcpyDeviceToHost);
+      for (long long g = 0; g < nodes; ++g) hf[g] = (float)h[g];
+      cudaMemcpy(P->e32.field, hf.data(), sizeof(float) * nodes, cudaMemcpyHostToDevice);
+    }
+    P->e32.mat = make_view<float>(P, P->e32.field);
+  }
+  if (check_last() != HOM_OK) { hom_destroy(P); return HOM_ERR_CUDA; }
+  *out = P;
+  return HOM_OK;
+}
+
+int hom_apply(hom_problem* P, int op, const double* E, const double* x_dev, double* y_dev) {
+  if (!P || !x_dev || !y_dev) return HOM_ERR_INVALID;
+  if (op < HOM_OP_AFFINE || op > HOM_OP_EM) return HOM_ERR_INVALID;
+  if (op == HOM_OP_AFFINE && !E) return HOM_ERR_INVALID;
+  if (op == HOM_OP_EM && P->integration == HOM_EXACT) return HOM_ERR_UNSUPPORTED;
+  OpArgs args{};
+  for (int a = 0; a < P->d; ++a) args.E[a] = E ? E[a] : 0.0;
+  args.omega = std::sqrt(P->cA * P->CA);
+  Fields<double> f{};
+  f.xin = x_dev;
+  f.out = y_dev;
+  f.cs = P->nodes;
+  const int pre = op == HOM_OP_AFFINE ? PRE_AFFINE : op == HOM_OP_LINEAR ? PRE_LINEAR
+                : op == HOM_OP_PROJECT ? PRE_IDENT : PRE_EM;
+  const int mode = op == HOM_OP_EM ? PROJ_EM : PROJ_GAMMA;
+  P->e64.apply(pre, mode, POST_STORE, f, (cpx<double>*)P->S, nullptr, args, nullptr, nullptr, 0,
+               P->stream);
+  return check_last();
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// solver drivers
+// ---------------------------------------------------------------------------------------
+namespace {
+
+int poll(hom_problem* P, Scalars* dst) {
+  HOM_CUDA(cudaMemcpyAsync(P->h_sc, dst, sizeof(Scalars), cudaMemcpyDeviceToHost, P->stream));
+  HOM_CUDA(cudaStreamSynchronize(P->stream));
+  return HOM_OK;
+}
+
+int upload_scalars(hom_problem* P, Scalars* dst, const Scalars& s) {
+  *P->h_sc = s;
+  HOM_CUDA(cudaMemcpyAsync(dst, P->h_sc, sizeof(Scalars), cudaMemcpyHostToDevice, P->stream));
+  HOM_CUDA(cudaStreamSynchronize(P->stream));
+  return HOM_OK;
+}
+
+// (A(E + x), E + x) and <A(E + x)> into P->d_aux
+int energy_eval(hom_problem* P, const double* E, const double* x, double* en, double* flux) {
+  Scalars s{};
+  for (int a = 0; a < P->d; ++a) s.E[a] = E[a];
+  int st = upload_scalars(P, P->d_aux, s);
+  if (st) return st;
+  Ops<double>::energy(P->d, x, P->nodes, P->e64.mat, P->d_aux, P->partials, P->counter,
+                      P->red_grid, P->stream);
+  if ((st = check_last())) return st;
+  if ((st = poll(P, P->d_aux))) return st;
+  if (en) *en = P->h_sc->energy;
+  if (flux)
+    for (int a = 0; a < P->d; ++a) flux[a] = P->h_sc->flux[a];
+  return HOM_OK;
+}
+
+// ||G A (E + x)|| (the residual b - C x up to sign) into P->d_aux; y is scratch
+double true_residual(hom_problem* P, const double* E, const double* x, double* y) {
+  Scalars s{};
+  for (int a = 0; a < P->d; ++a) s.E[a] = E[a];
+  if (upload_scalars(P, P->d_aux, s)) return -1;
+  Fields<double> f{};
+  f.xin = x;
+  f.out = y;
+  f.cs = P->nodes;
+  OpArgs args{};
+  P->e64.apply(PRE_AFFINE, PROJ_GAMMA, POST_STORE, f, (cpx<double>*)P->S, P->d_aux, args,
+               P->partials, P->counter, 0, P->stream);
+  if (poll(P, P->d_aux)) return -1;
+  return P->h_sc->nb;
+}
+
+}  // namespace
+
+extern "C" int hom_solve(hom_problem* P, const double* E, int solver, double tol,
+                         const hom_opts* opts, double* x_dev, double* AH_EE, double* flux,
+                         hom_stats* stats) {
+  if (!P || !E) return HOM_ERR_INVALID;
+  if (solver < HOM_RICHARDSON || solver > HOM_EYRE_MILTON) return HOM_ERR_INVALID;
+  hom_opts o{};
+  if (opts) o = *opts;
+  if (o.fixed_iters <= 0 && !(tol > 0)) return HOM_ERR_INVALID;
+  if (solver == HOM_EYRE_MILTON && P->integration == HOM_EXACT) return HOM_ERR_UNSUPPORTED;
+  if (P->precision == HOM_FP32_REFINED) return HOM_ERR_UNSUPPORTED;  // see hom_mp.cu
+  const int d = P->d;
+  const long long nodes = P->nodes;
+  const long long len = (long long)d * nodes;
+  const double cA = o.cA > 0 ? o.cA : P->cA;
+  const double CA = o.CA > 0 ? o.CA : P->CA;
+  const int maxit = o.fixed_iters > 0 ? o.fixed_iters : (o.maxit > 0 ? o.maxit : 100000);
+  const int check = o.check_every > 0 ? o.check_every : 8;
+  int stop = o.stop;
+  if (stop == HOM_STOP_DEFAULT) stop = (solver == HOM_EYRE_MILTON) ? HOM_STOP_INCREMENT : HOM_STOP_RESIDUAL;
+  if ((solver == HOM_CG || solver == HOM_CHEBYSHEV) && stop == HOM_STOP_INCREMENT) return HOM_ERR_UNSUPPORTED;
+  if (solver == HOM_EYRE_MILTON && stop == HOM_STOP_RESIDUAL) return HOM_ERR_UNSUPPORTED;
+
+  cudaStream_t st = P->stream;
+  cpx<double>* S = (cpx<double>*)P->S;
+  double nE = 0;
+  for (int a = 0; a < d; ++a) nE += E[a] * E[a];
+  nE = std::sqrt(nE);
+
+  Scalars s{};
+  for (int a = 0; a < d; ++a) s.E[a] = E[a];
+  s.tol = tol;
+  s.nE = nE;
+  s.maxit = maxit;
+  s.fixed = o.fixed_iters > 0 ? 1 : 0;
+  s.stop = stop;
+  int rc = upload_scalars(P, P->d_sc, s);
+  if (rc) return rc;
+  HOM_CUDA(cudaEventRecord(P->ev0, st));
+
+  double* x = P->vec[0];
+  double* r = P->vec[2];
+  double* p = P->vec[3];
+  double* q = P->vec[4];
+  OpArgs args{};
+  int matvecs = 0;
+  double* result = x;
+
+  if (solver == HOM_RICHARDSON) {
+    // x_m and x_{m-1} alternate between vec[0] and vec[1] (adjacent in one allocation)
+    double* pair = P->vec[0];
+    HOM_CUDA(cudaMemsetAsync(pair, 0, sizeof(double) * 2 * len, st));
+    s.omega = 2.0 / (cA + CA);
+    rc = upload_scalars(P, P->d_sc, s);
+    if (rc) return rc;
+    // ||b|| = ||G A E|| (x_0 = 0)
+    Fields<double> f0{};
+    f0.xin = pair;
+    f0.out = q;
+    f0.cs = nodes;
+    P->e64.apply(PRE_AFFINE, PROJ_GAMMA, POST_STORE, f0, S, P->d_sc, args, P->partials,
+                 P->counter, 0, st);
+    ++matvecs;
+    Fields<double> f{};
+    f.x = pair;
+    f.cs = nodes;
+    bool done = false;
+    int issued = 0;
+    while (!done) {
+      for (int k = 0; k < check && issued < maxit + 1; ++k, ++issued) {
+        P->e64.apply(PRE_AFFINE, PROJ_GAMMA, POST_RICH, f, S, P->d_sc, args, P->partials,
+                     P->counter, 0, st);
+      }
+      if ((rc = check_last()) || (rc = poll(P, P->d_sc))) return rc;
+      done = P->h_sc->done || issued >= maxit + 1;
+    }
+    matvecs += P->h_sc->it + (P->h_sc->converged && stop == HOM_STOP_RESIDUAL ? 1 : 0);
+    result = pair + (P->h_sc->result ? len : 0);
+  } else if (solver == HOM_CG || solver == HOM_CHEBYSHEV) {
+    HOM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * len, st));
+    HOM_CUDA(cudaMemsetAsync(p, 0, sizeof(double) * len, st));
+    if (solver == HOM_CHEBYSHEV) {
+      s.cheb_c = 0.5 * (CA - cA);
+      s.cheb_d = 0.5 * (cA + CA);
+      s.alpha = 1.0 / s.cheb_d;
+      s.beta = -0.5 * (s.cheb_c / s.cheb_d) * (s.cheb_c / s.cheb_d);
+    } else {
+      s.beta = 0.0;
+    }
+    rc = upload_scalars(P, P->d_sc, s);
+    if (rc) return rc;
+    // r_0 = b - C x_0 = -G A E, p_0 = r_0 (written by the finisher-free store), ||b||, (r, r)
+    Fields<double> f0{};
+    f0.xin = x;
+    f0.out = r;
+    f0.p = p;
+    f0.cs = nodes;
+    P->e64.apply(PRE_AFFINE, PROJ_GAMMA, POST_STORE, f0, S, P->d_sc, args, P->partials,
+                 P->counter, 1, st);
+    ++matvecs;
+    if (solver == HOM_CG) {
+      Fields<double> f{};
+      f.xin = r;
+      f.p = p;
+      f.out = q;
+      f.cs = nodes;
+      bool done = false;
+      int issued = 0;
+      while (!done) {
+        for (int k = 0; k < check && issued < maxit; ++k, ++issued) {
+          P->e64.apply(PRE_CG, PROJ_GAMMA, POST_CG, f, S, P->d_sc, args, P->partials,
+                       P->counter, 0, st);
+          Ops<double>::cg_update(x, r, p, q, len, nodes, P->d_sc, P->partials, P->counter,
+                                 P->red_grid, st);
+        }
+        if ((rc = check_last()) || (rc = poll(P, P->d_sc))) return rc;
+        done = P->h_sc->done || issued >= maxit;
+      }
+    } else {
+      Fields<double> f{};
+      f.xin = p;
+      f.p = p;
+      f.r = r;
+      f.x = x;
+      f.cs = nodes;
+      Fields<double> ff = f;
+      ff.x = nullptr;  // the forward pass reads p only
+      bool done = false;
+      int issued = 0;
+      while (!done) {
+        for (int k = 0; k < check && issued < maxit; ++k, ++issued)
+          P->e64.apply2(PRE_LINEAR, PROJ_GAMMA, POST_CHEB, ff, f, S, P->d_sc, args, P->partials,
+                        P->counter, 0, st);
+        if ((rc = check_last()) || (rc = poll(P, P->d_sc))) return rc;
+        done = P->h_sc->done || issued >= maxit;
+      }
+    }
+    matvecs += P->h_sc->it;
+  } else {  // Eyre-Milton
+    s.omega = std::sqrt(cA * CA);
+    rc = upload_scalars(P, P->d_sc, s);
+    if (rc) return rc;
+    Ops<double>::fill_const(x, nodes, d, P->d_sc, st);
+    Fields<double> f{};
+    f.xin = x;
+    f.x = x;
+    f.cs = nodes;
+    Fields<double> ff = f;
+    ff.x = nullptr;
+    bool done = false;
+    int issued = 0;
+    while (!done) {
+      for (int k = 0; k < check && issued < maxit; ++k, ++issued)
+        P->e64.apply2(PRE_EM, PROJ_EM, POST_EM, ff, f, S, P->d_sc, args, P->partials, P->counter,
+                      0, st);
+      if ((rc = check_last()) || (rc = poll(P, P->d_sc))) return rc;
+      done = P->h_sc->done || issued >= maxit;
+    }
+    matvecs += P->h_sc->it;
+    // e = G x_m (Section 4.4): the conforming part of the non-conforming iterate
+    Fields<double> fp{};
+    fp.xin = x;
+    fp.out = r;
+    fp.cs = nodes;
+    P->e64.apply(PRE_IDENT, PROJ_GAMMA, POST_STORE, fp, S, nullptr, args, nullptr, nullptr, 0, st);
+    result = r;
+  }
+  const Scalars fin = *P->h_sc;
+  HOM_CUDA(cudaEventRecord(P->ev1, st));
+  HOM_CUDA(cudaEventSynchronize(P->ev1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, P->ev0, P->ev1);
+
+  double en = 0, fl[3] = {0, 0, 0};
+  rc = energy_eval(P, E, result, &en, fl);
+  if (rc) return rc;
+  if (AH_EE) *AH_EE = en;
+  if (flux)
+    for (int a = 0; a < d; ++a) flux[a] = fl[a];
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->iterations = fin.it;
+    stats->matvecs = matvecs;
+    stats->converged = fin.converged;
+    if (solver == HOM_EYRE_MILTON || stop == HOM_STOP_INCREMENT)
+      stats->residual = fin.last_inc / (nE > 0 ? nE : 1);
+    else
+      stats->residual = fin.last_res / (fin.nb > 0 ? fin.nb : 1);
+    stats->time_ms = ms;
+    const double nb = fin.nb;
+    const double tr = true_residual(P, E, result, q);
+    if (solver == HOM_EYRE_MILTON) {
+      stats->true_residual = tr;  // ||G A (E + e)||, unnormalised (no ||b|| computed)
+    } else {
+      stats->true_residual = (nb > 0 && tr >= 0) ? tr / nb : tr;
+    }
+  }
+  if (x_dev) {
+    HOM_CUDA(cudaMemcpyAsync(x_dev, result, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
+    HOM_CUDA(cudaStreamSynchronize(st));
+  }
+  if ((rc = check_last())) return rc;
+  return (fin.converged || o.fixed_iters > 0) ? HOM_OK : HOM_ERR_NOT_CONVERGED;
+}
+
+extern "C" int hom_energy(hom_problem* P, const double* E, const double* x_dev, double* energy,
+                          double* flux) {
+  if (!P || !E) return HOM_ERR_INVALID;
+  return energy_eval(P, E, x_dev, energy, flux);
+}
+
+extern "C" int hom_prolongate(hom_problem* Cp, hom_problem* Fp, const double* x_dev,
+                              double* y_dev) {
+  if (!Cp || !Fp || !x_dev || !y_dev || Cp->d != Fp->d) return HOM_ERR_INVALID;
+  const int d = Cp->d;
+  for (int a = 0; a < d; ++a)
+    if (Fp->M[a] < Cp->M[a]) return HOM_ERR_INVALID;
+  cudaStream_t st = Cp->stream;
+  // F_N on the coarse grid (unscaled), then 1/|N| and the zero padding into Z_M, then F_M^{-1}
+  Cp->e64.forward(x_dev, (cpx<double>*)Cp->S, d, st);
+  HOM_CUDA(cudaMemsetAsync(Fp->S, 0, Fp->S_bytes, st));
+  const PassGeom& gn = Cp->e64.g;
+  const PassGeom& gm = Fp->e64.g;
+  const int n1 = d == 3 ? gn.n[1] : 1, m1 = d == 3 ? gm.n[1] : 1;
+  Ops<double>::pad_spectrum((const cpx<double>*)Cp->S, (cpx<double>*)Fp->S, d, gn.n[0], n1,
+                            gn.nh, gm.n[0], m1, gm.nh, 1.0 / (double)gn.nodes, gn.scs, gm.scs, st);
+  if (Fp->stream != st) {
+    HOM_CUDA(cudaStreamSynchronize(st));
+  }
+  Fp->e64.inverse((cpx<double>*)Fp->S, y_dev, d, Fp->stream);
+  return check_last();
+}
+
+extern "C" int hom_bound(hom_problem* gani, hom_problem* ga, const double* E,
+                         const double* x_dev, double* UE) {
+  if (!gani || !ga || !E || !x_dev || !UE) return HOM_ERR_INVALID;
+  if (gani->integration != HOM_APPROX || ga->integration != HOM_EXACT || gani->d != ga->d)
+    return HOM_ERR_INVALID;
+  for (int a = 0; a < gani->d; ++a)
+    if (ga->N[a] != gani->N[a]) return HOM_ERR_INVALID;
+  double* y = ga->vec[4];
+  int rc = hom_prolongate(gani, ga, x_dev, y);
+  if (rc) return rc;
+  HOM_CUDA(cudaStreamSynchronize(ga->stream));
+  return energy_eval(ga, E, y, UE, nullptr);
+}

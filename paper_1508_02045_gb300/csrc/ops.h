@@ -1,0 +1,61 @@
+// Host-side launchers of the pass kernels, one instantiation per working precision
+// (ops_f64.cu, ops_f32.cu). The host API (hom_api.cu) sequences them into operator
+// applications and solver steps.
+#pragma once
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace hom {
+
+struct OpArgs;
+struct ProjGeom;
+template <typename T> struct Fields;
+
+// launch geometry of the kernels of one grid, chosen by the planner in hom_api.cu
+struct PassGeom {
+  int D;              // spatial dimension
+  int n[3];           // solve-grid order
+  long long nodes;    // |grid|
+  long long nlines;   // lines of the contiguous axis per component (|grid| / n[D-1])
+  int nh;             // (n[D-1] + 1) / 2
+  long long scs;      // spectrum component stride: nlines * nh
+  int LB;             // lines per CTA in the line passes (even)
+  int TC1, TC1p;      // strided pass along axis 1 (D = 3): columns per CTA, padded pitch
+  int TC0, TC0p;      // axis-0 passes (projection / plain strided): columns per CTA, pitch
+};
+
+template <typename T>
+struct Ops {
+  static cudaError_t upload_constants();
+  static size_t smem_line(int n, int ncomp, int LB);
+  static size_t smem_strided(int n, int TCp);
+  static size_t smem_proj(int n, int D, int TCp);
+  static cudaError_t prepare(int maxD);  // raise dynamic shared memory limits
+
+  static void line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
+                       const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
+                       const Scalars* sc, const OpArgs& args, cudaStream_t st);
+  // strided DFT along axis 1 (D = 3) or axis 0 (no projection) of ncomp components
+  static void strided(const PassGeom& g, int axis, int inv, cpx<T>* S, const AxisPlan& P,
+                      const cpx<T>* tw, int ncomp, const Scalars* sc, cudaStream_t st);
+  static void proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, const cpx<T>* tw,
+                   const ProjGeom& pg, const Scalars* sc, cudaStream_t st);
+  static void line_inv(const PassGeom& g, int post, const cpx<T>* S, const Fields<T>& f,
+                       const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
+                       Scalars* sc, const OpArgs& args, double* partials, unsigned* counter,
+                       int negate, cudaStream_t st);
+  static void cg_update(T* x, T* r, const T* p, const T* q, long long len, long long nodes,
+                        Scalars* sc, double* partials, unsigned* counter, int grid,
+                        cudaStream_t st);
+  static void energy(int D, const T* x, long long nodes, const MatView<T>& mat, Scalars* sc,
+                     double* partials, unsigned* counter, int grid, cudaStream_t st);
+  static void fill_const(T* x, long long nodes, int d, const Scalars* sc, cudaStream_t st);
+  static void pad_spectrum(const cpx<T>* Sn, cpx<T>* Sm, int D, int n0, int n1, int nh, int m0,
+                           int m1, int mh, double scale, long long nlen, long long mlen,
+                           cudaStream_t st);
+};
+
+long long& launch_counter();
+int dynamic_smem_cap();
+
+}  // namespace hom

@@ -1,0 +1,222 @@
+// Template bodies of the launchers declared in ops.h (included by ops_f64.cu / ops_f32.cu).
+#pragma once
+#include <cmath>
+#include <vector>
+#include "ops.h"
+#include "passes.cuh"
+
+namespace hom {
+
+template <typename T>
+cudaError_t Ops<T>::upload_constants() {
+  std::vector<double> cd(kDftTable), sd(kDftTable);
+  std::vector<float> cf(kDftTable), sf(kDftTable);
+  const long double twopi = 6.283185307179586476925286766559005768L;
+  for (int i = 0; i < kNumRadices; ++i) {
+    const int R = kRadices[i], off = radix_offset(R);
+    for (int j = 0; j < R; ++j) {
+      const long double t = twopi * (long double)j / (long double)R;
+      cd[off + j] = (double)cosl(t);
+      sd[off + j] = (double)sinl(t);
+      cf[off + j] = (float)cosl(t);
+      sf[off + j] = (float)sinl(t);
+    }
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpyToSymbol(c_cos_d, cd.data(), sizeof(double) * kDftTable)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_sin_d, sd.data(), sizeof(double) * kDftTable)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_cos_f, cf.data(), sizeof(float) * kDftTable)) != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_sin_f, sf.data(), sizeof(float) * kDftTable);
+}
+
+template <typename T>
+size_t Ops<T>::smem_line(int n, int ncomp, int LB) {
+  return sizeof(cpx<T>) * ((size_t)n + 2 * (size_t)ncomp * (LB / 2) * n);
+}
+template <typename T>
+size_t Ops<T>::smem_strided(int n, int TCp) {
+  return sizeof(cpx<T>) * ((size_t)n + 2 * (size_t)n * TCp);
+}
+template <typename T>
+size_t Ops<T>::smem_proj(int n, int D, int TCp) {
+  return sizeof(cpx<T>) * ((size_t)n + (size_t)(D + 1) * n * TCp);
+}
+
+// Opt-in shared memory per CTA minus room for the kernels' static shared variables.
+inline int dynamic_smem_cap_query() {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return optin - 1024;
+}
+
+#define HOM_SET_SMEM(kern)                                                                    \
+  do {                                                                                        \
+    cudaError_t e_ = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                          cap);                                               \
+    if (e_ != cudaSuccess) return e_;                                                         \
+  } while (0)
+
+template <typename T>
+cudaError_t Ops<T>::prepare(int) {
+  const int cap = dynamic_smem_cap_query();
+  HOM_SET_SMEM((k_line_fwd<T, 2, PRE_AFFINE>));
+  HOM_SET_SMEM((k_line_fwd<T, 2, PRE_LINEAR>));
+  HOM_SET_SMEM((k_line_fwd<T, 2, PRE_CG>));
+  HOM_SET_SMEM((k_line_fwd<T, 2, PRE_EM>));
+  HOM_SET_SMEM((k_line_fwd<T, 2, PRE_IDENT>));
+  HOM_SET_SMEM((k_line_fwd<T, 3, PRE_AFFINE>));
+  HOM_SET_SMEM((k_line_fwd<T, 3, PRE_LINEAR>));
+  HOM_SET_SMEM((k_line_fwd<T, 3, PRE_CG>));
+  HOM_SET_SMEM((k_line_fwd<T, 3, PRE_EM>));
+  HOM_SET_SMEM((k_line_fwd<T, 3, PRE_IDENT>));
+  HOM_SET_SMEM((k_strided<T>));
+  HOM_SET_SMEM((k_proj<T, 2, PROJ_GAMMA>));
+  HOM_SET_SMEM((k_proj<T, 2, PROJ_EM>));
+  HOM_SET_SMEM((k_proj<T, 3, PROJ_GAMMA>));
+  HOM_SET_SMEM((k_proj<T, 3, PROJ_EM>));
+  HOM_SET_SMEM((k_line_inv<T, 2, POST_STORE>));
+  HOM_SET_SMEM((k_line_inv<T, 2, POST_RICH>));
+  HOM_SET_SMEM((k_line_inv<T, 2, POST_CG>));
+  HOM_SET_SMEM((k_line_inv<T, 2, POST_CHEB>));
+  HOM_SET_SMEM((k_line_inv<T, 2, POST_EM>));
+  HOM_SET_SMEM((k_line_inv<T, 3, POST_STORE>));
+  HOM_SET_SMEM((k_line_inv<T, 3, POST_RICH>));
+  HOM_SET_SMEM((k_line_inv<T, 3, POST_CG>));
+  HOM_SET_SMEM((k_line_inv<T, 3, POST_CHEB>));
+  HOM_SET_SMEM((k_line_inv<T, 3, POST_EM>));
+  return cudaSuccess;
+}
+
+template <typename T, int D>
+static void line_fwd_d(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
+                       const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
+                       const Scalars* sc, const OpArgs& args, cudaStream_t st) {
+  const unsigned grid = (unsigned)((g.nlines + g.LB - 1) / g.LB);
+  const size_t sm = Ops<T>::smem_line(P.n, ncomp, g.LB);
+#define HOM_LF(PRE_) k_line_fwd<T, D, PRE_><<<grid, kThreads, sm, st>>>(f, S, P, tw, ncomp, g.nlines, g.LB, g.scs, mat, sc, args)
+  switch (pre) {
+    case PRE_AFFINE: HOM_LF(PRE_AFFINE); break;
+    case PRE_LINEAR: HOM_LF(PRE_LINEAR); break;
+    case PRE_CG: HOM_LF(PRE_CG); break;
+    case PRE_EM: HOM_LF(PRE_EM); break;
+    default: HOM_LF(PRE_IDENT); break;
+  }
+#undef HOM_LF
+  ++launch_counter();
+}
+
+template <typename T>
+void Ops<T>::line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
+                      const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
+                      const Scalars* sc, const OpArgs& args, cudaStream_t st) {
+  if (g.D == 2) line_fwd_d<T, 2>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st);
+  else line_fwd_d<T, 3>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st);
+}
+
+template <typename T>
+void Ops<T>::strided(const PassGeom& g, int axis, int inv, cpx<T>* S, const AxisPlan& P,
+                     const cpx<T>* tw, int ncomp, const Scalars* sc, cudaStream_t st) {
+  long long C, es, bs;
+  int batches, TC, TCp;
+  if (g.D == 3 && axis == 1) {
+    C = g.nh;
+    es = g.nh;
+    bs = (long long)g.n[1] * g.nh;
+    batches = ncomp * g.n[0];
+    TC = g.TC1;
+    TCp = g.TC1p;
+  } else {  // axis 0
+    C = g.scs / g.n[0];
+    es = C;
+    bs = g.scs;
+    batches = ncomp;
+    TC = g.TC0;
+    TCp = g.TC0p;
+  }
+  dim3 grid((unsigned)((C + TC - 1) / TC), (unsigned)batches);
+  const size_t sm = smem_strided(P.n, TCp);
+  k_strided<T><<<grid, kThreads, sm, st>>>(S, P, tw, C, es, bs, TC, TCp, inv, sc);
+  ++launch_counter();
+}
+
+template <typename T>
+void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, const cpx<T>* tw,
+                  const ProjGeom& pg, const Scalars* sc, cudaStream_t st) {
+  const unsigned grid = (unsigned)((pg.C + g.TC0 - 1) / g.TC0);
+  const size_t sm = smem_proj(P.n, g.D, g.TC0p);
+#define HOM_PJ(D_, M_) k_proj<T, D_, M_><<<grid, kThreads, sm, st>>>(S, P, tw, pg, g.TC0, g.TC0p, sc)
+  if (g.D == 2) {
+    if (mode == PROJ_EM) HOM_PJ(2, PROJ_EM); else HOM_PJ(2, PROJ_GAMMA);
+  } else {
+    if (mode == PROJ_EM) HOM_PJ(3, PROJ_EM); else HOM_PJ(3, PROJ_GAMMA);
+  }
+#undef HOM_PJ
+  ++launch_counter();
+}
+
+template <typename T, int D>
+static void line_inv_d(const PassGeom& g, int post, const cpx<T>* S, const Fields<T>& f,
+                       const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
+                       Scalars* sc, const OpArgs& args, double* partials, unsigned* counter,
+                       int negate, cudaStream_t st) {
+  const unsigned grid = (unsigned)((g.nlines + g.LB - 1) / g.LB);
+  const size_t sm = Ops<T>::smem_line(P.n, ncomp, g.LB);
+#define HOM_LI(POST_) k_line_inv<T, D, POST_><<<grid, kThreads, sm, st>>>(S, f, P, tw, ncomp, g.nlines, g.LB, g.scs, mat, sc, args, partials, counter, negate)
+  switch (post) {
+    case POST_RICH: HOM_LI(POST_RICH); break;
+    case POST_CG: HOM_LI(POST_CG); break;
+    case POST_CHEB: HOM_LI(POST_CHEB); break;
+    case POST_EM: HOM_LI(POST_EM); break;
+    default: HOM_LI(POST_STORE); break;
+  }
+#undef HOM_LI
+  ++launch_counter();
+}
+
+template <typename T>
+void Ops<T>::line_inv(const PassGeom& g, int post, const cpx<T>* S, const Fields<T>& f,
+                      const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
+                      Scalars* sc, const OpArgs& args, double* partials, unsigned* counter,
+                      int negate, cudaStream_t st) {
+  if (g.D == 2)
+    line_inv_d<T, 2>(g, post, S, f, P, tw, ncomp, mat, sc, args, partials, counter, negate, st);
+  else
+    line_inv_d<T, 3>(g, post, S, f, P, tw, ncomp, mat, sc, args, partials, counter, negate, st);
+}
+
+template <typename T>
+void Ops<T>::cg_update(T* x, T* r, const T* p, const T* q, long long len, long long nodes,
+                       Scalars* sc, double* partials, unsigned* counter, int grid,
+                       cudaStream_t st) {
+  k_cg_update<T><<<grid, kThreads, 0, st>>>(x, r, p, q, len, nodes, sc, partials, counter);
+  ++launch_counter();
+}
+
+template <typename T>
+void Ops<T>::energy(int D, const T* x, long long nodes, const MatView<T>& mat, Scalars* sc,
+                    double* partials, unsigned* counter, int grid, cudaStream_t st) {
+  if (D == 2) k_energy<T, 2><<<grid, kThreads, 0, st>>>(x, nodes, mat, sc, partials, counter);
+  else k_energy<T, 3><<<grid, kThreads, 0, st>>>(x, nodes, mat, sc, partials, counter);
+  ++launch_counter();
+}
+
+template <typename T>
+void Ops<T>::fill_const(T* x, long long nodes, int d, const Scalars* sc, cudaStream_t st) {
+  const long long len = nodes * d;
+  const unsigned grid = (unsigned)std::min<long long>((len + kThreads - 1) / kThreads, 152 * 16);
+  k_fill_const<T><<<grid, kThreads, 0, st>>>(x, nodes, d, sc);
+  ++launch_counter();
+}
+
+template <typename T>
+void Ops<T>::pad_spectrum(const cpx<T>* Sn, cpx<T>* Sm, int D, int n0, int n1, int nh, int m0,
+                          int m1, int mh, double scale, long long nlen, long long mlen,
+                          cudaStream_t st) {
+  const long long len = (long long)n0 * n1 * nh * D;
+  const unsigned grid = (unsigned)std::min<long long>((len + kThreads - 1) / kThreads, 152 * 16);
+  k_pad_spectrum<T><<<grid, kThreads, 0, st>>>(Sn, Sm, D, n0, n1, nh, m0, m1, mh, (T)scale, nlen, mlen);
+  ++launch_counter();
+}
+
+}  // namespace hom

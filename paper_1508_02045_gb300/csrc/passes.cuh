@@ -1,0 +1,685 @@
+// The fused FFT passes of the operator e -> G A (E + e) and the solver kernels around them.
+//
+// A field on the solve grid (n_0, ..., n_{D-1}) has the last axis contiguous; its transform is
+// stored as a half spectrum (k_{D-1} = 0 .. (n_{D-1}-1)/2, the rest follows from Hermitian
+// symmetry of real fields, Section 2.1), layout [component][k_0]...[k_{D-2}][k_{D-1}].
+//
+// One operator application is
+//   line_fwd  : pre-operator (A(E+x), A p, ...) + forward real DFT of the contiguous axis;
+//               two real lines share one complex transform
+//   strided   : forward DFT of the middle axis (D = 3)
+//   proj      : forward DFT of axis 0, the projection Gamma^ (eq. (proj); with the truncation
+//               to Z_N of eq. (discrete_proj) on a double grid; or I - 2 Gamma^ of
+//               Algorithm 4), the 1/|N| of eq. (DFT), and the inverse DFT of axis 0
+//   strided   : inverse DFT of the middle axis (D = 3)
+//   line_inv  : inverse real DFT of the contiguous axis + the solver's post-operator (vector
+//               update and inner-product partials of Algorithms 1-4).
+// Reductions are deterministic: one partial per CTA, summed in a fixed order by the last CTA
+// to finish, which then runs the scalar part of the algorithm step ("finisher").
+#pragma once
+#include "common.cuh"
+#include "fft_engine.cuh"
+
+namespace hom {
+
+// ---------------------------------------------------------------------------------------
+// deterministic block reduction + last-block finisher
+// ---------------------------------------------------------------------------------------
+template <int NV>
+__device__ bool reduce_and_last(double (&acc)[NV], double* partials, unsigned* counter,
+                                double (&tot)[NV]) {
+  __shared__ double red[NV][kThreads / 32];
+  __shared__ double fin[NV];
+  __shared__ int am_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nblocks = gridDim.x * gridDim.y;
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double s = acc[v];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[v][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double s = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) s += red[v][w];
+      partials[(size_t)bid * NV + v] = s;
+    }
+    __threadfence();
+    const unsigned t = atomicAdd(counter, 1u);
+    am_last = (t == (unsigned)(nblocks - 1));
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += __ldcg(&partials[(size_t)b * NV + v]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if (lane == 0) red[v][warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double f = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) f += red[v][w];
+      fin[v] = f;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < NV; ++v) tot[v] = fin[v];
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// coefficient products
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ int phase_at(const MatView<T>& m, long long g) {
+  return m.ph8 ? (int)m.ph8[g] : (int)m.ph16[g];
+}
+
+// v = A(x^g) w
+template <typename T, int D>
+__device__ __forceinline__ void mat_apply(const MatView<T>& m, long long g, const T (&w)[D],
+                                          T (&v)[D]) {
+  if (m.kind == MAT_FIELD) {
+    const T a = m.field[g];
+#pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = a * w[i];
+  } else if (m.kind == MAT_PHASE_ISO) {
+    const T a = (T)__ldg(&m.table[phase_at(m, g)]);
+#pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = a * w[i];
+  } else {
+    const double* t = m.table + phase_at(m, g) * D * D;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      T s = 0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) s = fma((T)__ldg(&t[i * D + j]), w[j], s);
+      v[i] = s;
+    }
+  }
+}
+
+// v = (A(x^g) + omega I)^{-1} w
+template <typename T, int D>
+__device__ __forceinline__ void mat_shift_solve(const MatView<T>& m, long long g, T omega,
+                                                const T (&w)[D], T (&v)[D]) {
+  if (m.kind == MAT_FIELD || m.kind == MAT_PHASE_ISO) {
+    const T a = (m.kind == MAT_FIELD) ? m.field[g] : (T)__ldg(&m.table[phase_at(m, g)]);
+    const T inv = (T)1 / (a + omega);
+#pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = w[i] * inv;
+    return;
+  }
+  const double* t = m.table + phase_at(m, g) * D * D;
+  T M[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) M[i][j] = (T)__ldg(&t[i * D + j]) + (i == j ? omega : (T)0);
+  if (D == 2) {
+    const T det = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+    v[0] = (M[1][1] * w[0] - M[0][1] * w[1]) / det;
+    v[1] = (M[0][0] * w[1] - M[1][0] * w[0]) / det;
+  } else {
+    // Cramer's rule with the cofactor (adjugate) matrix of a 3 x 3 system
+    const T c00 = M[1][1] * M[2][2] - M[1][2] * M[2][1];
+    const T c01 = M[1][2] * M[2][0] - M[1][0] * M[2][2];
+    const T c02 = M[1][0] * M[2][1] - M[1][1] * M[2][0];
+    const T det = M[0][0] * c00 + M[0][1] * c01 + M[0][2] * c02;
+    const T c10 = M[0][2] * M[2][1] - M[0][1] * M[2][2];
+    const T c11 = M[0][0] * M[2][2] - M[0][2] * M[2][0];
+    const T c12 = M[0][1] * M[2][0] - M[0][0] * M[2][1];
+    const T c20 = M[0][1] * M[1][2] - M[0][2] * M[1][1];
+    const T c21 = M[0][2] * M[1][0] - M[0][0] * M[1][2];
+    const T c22 = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+    // inverse = adj / det, adj = cofactor^T
+    v[0] = (c00 * w[0] + c10 * w[1] + c20 * w[2]) / det;
+    v[1] = (c01 * w[0] + c11 * w[1] + c21 * w[2]) / det;
+    v[2] = (c02 * w[0] + c12 * w[1] + c22 * w[2]) / det;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Buffers of one operator application / solver step
+// ---------------------------------------------------------------------------------------
+// Scalars of a single operator application outside a solve (Scalars pointer is then null).
+struct OpArgs {
+  double E[3];
+  double omega;
+};
+
+template <typename T>
+struct Fields {
+  const T* xin;   // operand of the pre-operator (x, or r for PRE_CG)
+  T* p;           // PRE_CG / POST_CG / POST_CHEB: search direction
+  T* out;         // POST_STORE: destination; POST_CG: C p
+  T* x;           // POST_RICH: buffer pair base (x_a, x_b = x + d|N|); POST_CHEB / POST_EM: x
+  T* r;           // POST_CHEB: residual; POST_STORE with negate: r
+  long long cs;   // component stride (|N|)
+};
+
+// ---------------------------------------------------------------------------------------
+// line_fwd: pre-operator + forward real DFT of the contiguous axis
+// ---------------------------------------------------------------------------------------
+template <typename T, int D, int PRE>
+__global__ void __launch_bounds__(kThreads, 2)
+k_line_fwd(Fields<T> f, cpx<T>* __restrict__ S, AxisPlan P, const cpx<T>* __restrict__ twg,
+           int ncomp, long long nlines, int LB, long long scs, MatView<T> mat,
+           const Scalars* __restrict__ sc, OpArgs args) {
+  if (sc != nullptr && sc->done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = P.n, nh = (n + 1) / 2;
+  const int half = LB / 2;
+  const int nlc = ncomp * half;
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem);
+  cpx<T>* b0 = tw + n;
+  cpx<T>* b1 = b0 + (size_t)nlc * n;
+  __shared__ AxisPlan Ps;
+  if (threadIdx.x == 0) Ps = P;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+  const long long l0 = (long long)blockIdx.x * LB;
+  const double* Es = sc != nullptr ? sc->E : args.E;
+  const T E[3] = {(T)Es[0], (T)Es[1], (T)Es[2]};
+  const T omega = (T)(sc != nullptr ? sc->omega : args.omega);
+  const T beta = sc != nullptr ? (T)sc->beta : (T)0;
+  // Richardson keeps x_m and x_{m-1} in a buffer pair; the operand is the current one
+  const T* xin = f.xin;
+  if (f.x != nullptr && sc != nullptr) xin = f.x + (sc->which ? D * f.cs : 0);
+  for (int idx = threadIdx.x; idx < LB * n; idx += blockDim.x) {
+    const int ll = idx / n, j = idx - ll * n;
+    const long long l = l0 + ll;
+    T v[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] = 0;
+    if (l < nlines) {
+      const long long g = l * n + j;
+      if (PRE == PRE_IDENT) {
+        for (int a = 0; a < ncomp; ++a) v[a] = xin[a * f.cs + g];
+      } else {
+        T w[D];
+        if (PRE == PRE_CG) {
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            const T pn = xin[a * f.cs + g] + beta * f.p[a * f.cs + g];
+            f.p[a * f.cs + g] = pn;
+            w[a] = pn;
+          }
+        } else {
+#pragma unroll
+          for (int a = 0; a < D; ++a) w[a] = xin[a * f.cs + g] + (PRE == PRE_AFFINE ? E[a] : (T)0);
+        }
+        mat_apply<T, D>(mat, g, w, v);
+        if (PRE == PRE_EM) {
+#pragma unroll
+          for (int a = 0; a < D; ++a) v[a] -= omega * w[a];
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      if (a < ncomp) {
+        cpx<T>* line = b0 + (size_t)(a * half + (ll >> 1)) * n;
+        if (ll & 1) line[j].y = v[a];
+        else line[j].x = v[a];
+      }
+    }
+  }
+  __syncthreads();
+  cpx<T>* res = fft_lines<T>(b0, b1, &Ps, nlc, n, 1, false, false, tw);
+  for (int idx = threadIdx.x; idx < nlc * nh; idx += blockDim.x) {
+    const int lc = idx / nh, k = idx - lc * nh;
+    const int a = lc / half, pr = lc - a * half;
+    const cpx<T> zk = res[(size_t)lc * n + k];
+    const cpx<T> zm = res[(size_t)lc * n + (k ? n - k : 0)];
+    cpx<T> A, B;
+    A.x = (T)0.5 * (zk.x + zm.x);
+    A.y = (T)0.5 * (zk.y - zm.y);
+    B.x = (T)0.5 * (zk.y + zm.y);
+    B.y = (T)-0.5 * (zk.x - zm.x);
+    const long long la = l0 + 2 * pr;
+    if (la < nlines) S[a * scs + la * nh + k] = A;
+    if (la + 1 < nlines) S[a * scs + (la + 1) * nh + k] = B;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// strided: DFT along a strided axis, in place; blockIdx.y = batch, blockIdx.x = column tile
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2)
+k_strided(cpx<T>* __restrict__ S, AxisPlan P, const cpx<T>* __restrict__ twg, long long C,
+          long long es, long long bs, int TC, int TCp, int inv, const Scalars* __restrict__ sc) {
+  if (sc != nullptr && sc->done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = P.n;
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem);
+  cpx<T>* b0 = tw + n;
+  cpx<T>* b1 = b0 + (size_t)n * TCp;
+  __shared__ AxisPlan Ps;
+  if (threadIdx.x == 0) Ps = P;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+  const long long c0 = (long long)blockIdx.x * TC;
+  cpx<T>* base = S + (long long)blockIdx.y * bs + c0;
+  const cpx<T> zero = {0, 0};
+  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
+    const int j = idx / TC, c = idx - j * TC;
+    b0[j * TCp + c] = (c0 + c < C) ? base[j * es + c] : zero;
+  }
+  __syncthreads();
+  cpx<T>* res = fft_lines<T>(b0, b1, &Ps, TC, 1, TCp, true, inv != 0, tw);
+  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
+    const int j = idx / TC, c = idx - j * TC;
+    if (c0 + c < C) base[j * es + c] = res[j * TCp + c];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// proj: forward DFT of axis 0, projection, inverse DFT of axis 0 (all D components)
+// ---------------------------------------------------------------------------------------
+struct ProjGeom {
+  long long C;    // columns: product of the middle axes x half length of the last axis
+  long long cs;   // component stride of the spectrum
+  int n1;         // middle axis length (D = 3), 1 otherwise
+  int nh;         // half length of the last axis
+  int hw[3];      // support half-widths: keep |k_a| <= hw[a] (Z_N inside Z_M); else zero
+  double scale;   // 1/|grid| of the forward transform (eq. (DFT))
+};
+
+template <typename T, int D, int MODE>
+__global__ void __launch_bounds__(kThreads, 2)
+k_proj(cpx<T>* __restrict__ S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC,
+       int TCp, const Scalars* __restrict__ sc) {
+  if (sc != nullptr && sc->done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = P.n;
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem);
+  cpx<T>* buf[D + 1];
+  buf[0] = tw + n;
+#pragma unroll
+  for (int a = 1; a <= D; ++a) buf[a] = buf[a - 1] + (size_t)n * TCp;
+  __shared__ AxisPlan Ps;
+  if (threadIdx.x == 0) Ps = P;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+  const long long c0 = (long long)blockIdx.x * TC;
+  const long long es = g.C;
+  const cpx<T> zero = {0, 0};
+  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
+    const int j = idx / TC, c = idx - j * TC;
+    const bool ok = c0 + c < g.C;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      buf[a][j * TCp + c] = ok ? S[a * g.cs + j * es + c0 + c] : zero;
+  }
+  __syncthreads();
+  cpx<T>* spare = buf[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    cpx<T>* res = fft_lines<T>(buf[a], spare, &Ps, TC, 1, TCp, true, false, tw);
+    if (res != buf[a]) { spare = buf[a]; buf[a] = res; }
+  }
+  const T scale = (T)g.scale;
+  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
+    const int j = idx / TC, c = idx - j * TC;
+    const long long cc = c0 + c;
+    if (cc >= g.C) continue;
+    int k[3];
+    k[0] = (j <= (n - 1) / 2) ? j : j - n;
+    if (D == 3) {
+      const int i1 = (int)(cc / g.nh);
+      k[1] = (i1 <= (g.n1 - 1) / 2) ? i1 : i1 - g.n1;
+      k[2] = (int)(cc - (long long)i1 * g.nh);
+    } else {
+      k[1] = (int)cc;
+      k[2] = 0;
+    }
+    bool inside = true;
+    long long kk = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      inside = inside && (abs(k[a]) <= g.hw[a]);
+      kk += (long long)k[a] * k[a];
+    }
+    cpx<T> v[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] = buf[a][j * TCp + c];
+    cpx<T> kv = {0, 0};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      kv.x = fma((T)k[a], v[a].x, kv.x);
+      kv.y = fma((T)k[a], v[a].y, kv.y);
+    }
+    const T coef = (kk > 0 && inside) ? scale / (T)kk : (T)0;
+    kv.x *= coef;
+    kv.y *= coef;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      cpx<T> o;
+      if (MODE == PROJ_GAMMA) {
+        o.x = (T)k[a] * kv.x;
+        o.y = (T)k[a] * kv.y;
+      } else {  // (I - 2 Gamma^) v
+        o.x = fma((T)(-2 * k[a]), kv.x, scale * v[a].x);
+        o.y = fma((T)(-2 * k[a]), kv.y, scale * v[a].y);
+      }
+      buf[a][j * TCp + c] = o;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    cpx<T>* res = fft_lines<T>(buf[a], spare, &Ps, TC, 1, TCp, true, true, tw);
+    if (res != buf[a]) { spare = buf[a]; buf[a] = res; }
+  }
+  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
+    const int j = idx / TC, c = idx - j * TC;
+    if (c0 + c < g.C) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) S[a * g.cs + j * es + c0 + c] = buf[a][j * TCp + c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// line_inv: inverse real DFT of the contiguous axis + post-operator
+// ---------------------------------------------------------------------------------------
+template <typename T, int D, int POST>
+__global__ void __launch_bounds__(kThreads, 2)
+k_line_inv(const cpx<T>* __restrict__ S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ twg,
+           int ncomp, long long nlines, int LB, long long scs, MatView<T> mat, Scalars* sc,
+           OpArgs args, double* partials, unsigned* counter, int negate) {
+  if (sc != nullptr && sc->done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = P.n, nh = (n + 1) / 2;
+  const int half = LB / 2;
+  const int nlc = ncomp * half;
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem);
+  cpx<T>* b0 = tw + n;
+  cpx<T>* b1 = b0 + (size_t)nlc * n;
+  __shared__ AxisPlan Ps;
+  if (threadIdx.x == 0) Ps = P;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+  const long long l0 = (long long)blockIdx.x * LB;
+  const cpx<T> zero = {0, 0};
+  for (int idx = threadIdx.x; idx < nlc * nh; idx += blockDim.x) {
+    const int lc = idx / nh, k = idx - lc * nh;
+    const int a = lc / half, pr = lc - a * half;
+    const long long la = l0 + 2 * pr;
+    const cpx<T> A = (la < nlines) ? S[a * scs + la * nh + k] : zero;
+    const cpx<T> B = (la + 1 < nlines) ? S[a * scs + (la + 1) * nh + k] : zero;
+    cpx<T>* line = b0 + (size_t)lc * n;
+    if (k == 0) {
+      line[0].x = A.x;
+      line[0].y = B.x;
+    } else {
+      line[k].x = A.x - B.y;
+      line[k].y = A.y + B.x;
+      line[n - k].x = A.x + B.y;
+      line[n - k].y = B.x - A.y;
+    }
+  }
+  __syncthreads();
+  cpx<T>* res = fft_lines<T>(b0, b1, &Ps, nlc, n, 1, false, true, tw);
+
+  // post-operator
+  const double* Es = sc != nullptr ? sc->E : args.E;
+  const T E[3] = {(T)Es[0], (T)Es[1], (T)Es[2]};
+  const T omega = (T)(sc != nullptr ? sc->omega : args.omega);
+  const T alpha = sc != nullptr ? (T)sc->alpha : (T)0;
+  const T beta = sc != nullptr ? (T)sc->beta : (T)0;
+  const int which = sc != nullptr ? sc->which : 0;
+  double acc[1] = {0.0};
+  const long long cs = f.cs;
+  for (int idx = threadIdx.x; idx < LB * n; idx += blockDim.x) {
+    const int ll = idx / n, j = idx - ll * n;
+    const long long l = l0 + ll;
+    if (l >= nlines) continue;
+    const long long g = l * n + j;
+    T y[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      if (a < ncomp) {
+        const cpx<T> z = res[(size_t)(a * half + (ll >> 1)) * n + j];
+        y[a] = (ll & 1) ? z.y : z.x;
+      } else {
+        y[a] = 0;
+      }
+    }
+    if (POST == POST_STORE) {
+      for (int a = 0; a < ncomp; ++a) {
+        const T o = negate ? -y[a] : y[a];
+        f.out[a * cs + g] = o;
+        if (f.r) f.r[a * cs + g] = o;
+        if (f.p) f.p[a * cs + g] = o;
+        acc[0] += (double)y[a] * (double)y[a];
+      }
+    } else if (POST == POST_RICH) {
+      const T* xc = f.x + (which ? D * cs : 0);
+      T* xn = f.x + (which ? 0 : D * cs);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        xn[a * cs + g] = xc[a * cs + g] - omega * y[a];
+        acc[0] += (double)y[a] * (double)y[a];
+      }
+    } else if (POST == POST_CG) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        f.out[a * cs + g] = y[a];
+        acc[0] += (double)y[a] * (double)f.p[a * cs + g];
+      }
+    } else if (POST == POST_CHEB) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const T pv = f.p[a * cs + g];
+        const T rn = f.r[a * cs + g] - alpha * y[a];
+        f.r[a * cs + g] = rn;
+        f.x[a * cs + g] += alpha * pv;
+        f.p[a * cs + g] = rn - beta * pv;
+        acc[0] += (double)rn * (double)rn;
+      }
+    } else if (POST == POST_EM) {
+      T w[D], xn[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) w[a] = y[a] + (T)2 * omega * E[a];
+      mat_shift_solve<T, D>(mat, g, omega, w, xn);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const T dx = xn[a] - f.x[a * cs + g];
+        f.x[a * cs + g] = xn[a];
+        acc[0] += (double)dx * (double)dx;
+      }
+    }
+  }
+  if (partials == nullptr) return;
+  double tot[1];
+  if (!reduce_and_last<1>(acc, partials, counter, tot)) return;
+  if (threadIdx.x != 0 || sc == nullptr) return;
+  // ---- finisher: the scalar part of the algorithm step ----
+  const double mean = tot[0] / (double)(nlines * n);
+  if (POST == POST_STORE) {
+    // initial residual r_0 = b (x_0 = 0): ||b|| and (r_0, r_0)
+    sc->nb = sqrt(mean);
+    sc->rr = mean;
+    sc->last_res = sqrt(mean);
+  } else if (POST == POST_RICH) {
+    const double res = sqrt(mean);  // ||C x_{m-1} - b||
+    sc->last_res = res;
+    if (!sc->fixed && sc->stop == 1 && res <= sc->tol * sc->nb) {
+      sc->done = 1;
+      sc->converged = 1;
+      sc->result = sc->which;
+      return;
+    }
+    sc->it += 1;
+    sc->which ^= 1;
+    sc->result = sc->which;
+    const double inc = sc->omega * res;  // ||x_m - x_{m-1}||
+    sc->last_inc = inc;
+    if (sc->fixed) {
+      if (sc->it >= sc->maxit) sc->done = 1;
+    } else if (sc->stop == 2 && inc <= sc->tol * sc->nE) {
+      sc->done = 1;
+      sc->converged = 1;
+    } else if (sc->it >= sc->maxit) {
+      sc->done = 1;
+    }
+  } else if (POST == POST_CG) {
+    sc->pAp = mean;
+    sc->alpha = sc->rr / mean;
+  } else if (POST == POST_CHEB) {
+    const double res = sqrt(mean);
+    sc->last_res = res;
+    sc->it += 1;
+    if (sc->fixed) {
+      if (sc->it >= sc->maxit) sc->done = 1;
+    } else if (res <= sc->tol * sc->nb) {
+      sc->done = 1;
+      sc->converged = 1;
+    } else if (sc->it >= sc->maxit) {
+      sc->done = 1;
+    }
+    // coefficients of the next step (Algorithm 3, m > 1)
+    const double an = 1.0 / (sc->cheb_d + sc->beta / sc->alpha);
+    sc->alpha = an;
+    sc->beta = -(sc->cheb_c * an * 0.5) * (sc->cheb_c * an * 0.5);
+  } else if (POST == POST_EM) {
+    const double inc = sqrt(mean);
+    sc->last_inc = inc;
+    sc->it += 1;
+    if (sc->fixed) {
+      if (sc->it >= sc->maxit) sc->done = 1;
+    } else if (inc <= sc->tol * sc->nE) {
+      sc->done = 1;
+      sc->converged = 1;
+    } else if (sc->it >= sc->maxit) {
+      sc->done = 1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// CG update (Algorithm 2): x += alpha p, r -= alpha C p, (r, r); then beta and the test
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+            const T* __restrict__ q, long long len, long long nodes, Scalars* sc,
+            double* partials, unsigned* counter) {
+  if (sc->done) return;
+  const T alpha = (T)sc->alpha;
+  double acc[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const T rn = r[i] - alpha * q[i];
+    r[i] = rn;
+    acc[0] += (double)rn * (double)rn;
+  }
+  double tot[1];
+  if (!reduce_and_last<1>(acc, partials, counter, tot)) return;
+  if (threadIdx.x != 0) return;
+  const double rr_new = tot[0] / (double)nodes;
+  const double res = sqrt(rr_new);
+  sc->last_res = res;
+  sc->it += 1;
+  if (sc->fixed) {
+    if (sc->it >= sc->maxit) sc->done = 1;
+  } else if (res <= sc->tol * sc->nb) {
+    sc->done = 1;
+    sc->converged = 1;
+  } else if (sc->it >= sc->maxit) {
+    sc->done = 1;
+  }
+  sc->beta = rr_new / sc->rr;
+  sc->rr = rr_new;
+}
+
+// ---------------------------------------------------------------------------------------
+// energy (A(E + x), E + x) and flux <A(E + x)> (eqs. (GaNi), (ev_bounds))
+// ---------------------------------------------------------------------------------------
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads)
+k_energy(const T* __restrict__ x, long long nodes, MatView<T> mat, Scalars* sc, double* partials,
+         unsigned* counter) {
+  double acc[D + 1];
+#pragma unroll
+  for (int a = 0; a <= D; ++a) acc[a] = 0.0;
+  T E[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) E[a] = (T)sc->E[a];
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < nodes;
+       g += (long long)gridDim.x * blockDim.x) {
+    T w[D], v[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) w[a] = E[a] + (x ? x[a * nodes + g] : (T)0);
+    mat_apply<T, D>(mat, g, w, v);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      acc[0] += (double)v[a] * (double)w[a];
+      acc[1 + a] += (double)v[a];
+    }
+  }
+  double tot[D + 1];
+  if (!reduce_and_last<D + 1>(acc, partials, counter, tot)) return;
+  if (threadIdx.x != 0) return;
+  sc->energy = tot[0] / (double)nodes;
+#pragma unroll
+  for (int a = 0; a < D; ++a) sc->flux[a] = tot[1 + a] / (double)nodes;
+}
+
+// ---------------------------------------------------------------------------------------
+// small vector kernels
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_fill_const(T* x, long long nodes, int d, const Scalars* sc) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nodes * d;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = (T)sc->E[i / nodes];
+}
+
+// half spectrum of grid N (scaled by `scale`) placed into the zeroed half spectrum of grid M
+// at the same signed frequencies (prolongation, eq. (ev_bounds)); D = 2 or 3
+template <typename T>
+__global__ void k_pad_spectrum(const cpx<T>* __restrict__ Sn, cpx<T>* __restrict__ Sm, int D,
+                               int n0, int n1, int nh, int m0, int m1, int mh, T scale,
+                               long long nlen, long long mlen) {
+  const long long per = (long long)n0 * n1 * nh;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < per * D;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(i / per);
+    long long r = i - a * per;
+    const int k2 = (int)(r % nh);
+    r /= nh;
+    const int j1 = (int)(r % n1);
+    const int j0 = (int)(r / n1);
+    const int s0 = j0 <= (n0 - 1) / 2 ? j0 : j0 - n0;
+    const int s1 = j1 <= (n1 - 1) / 2 ? j1 : j1 - n1;
+    const int t0 = s0 >= 0 ? s0 : s0 + m0;
+    const int t1 = s1 >= 0 ? s1 : s1 + m1;
+    cpx<T> v = Sn[a * nlen + i - a * per];
+    v.x *= scale;
+    v.y *= scale;
+    Sm[a * mlen + ((long long)t0 * m1 + t1) * mh + k2] = v;
+  }
+}
+
+template <typename T>
+__global__ void k_scale_spectrum(cpx<T>* S, long long len, T scale) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    S[i].x *= scale;
+    S[i].y *= scale;
+  }
+}
+
+}  // namespace hom
