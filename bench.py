@@ -1,0 +1,390 @@
+"""Benchmark of the Fourier-Galerkin hot path on one GB300 (or N replicas under torchrun).
+
+Workload: 3-D scalar conductivity on the 243^3 grid (3^5), FP64, GaNi (trapezoidal
+integration), centred cubic inclusion of volume fraction 0.2 (143^3 nodes, 0.2038 realised),
+contrast 1e3, E = (1, 0, 0). One step is one conjugate-gradient iteration (Algorithm 2):
+the fused pre-pass p = r + beta p with A p, the forward 3-D DFT, the projection Gamma^, the
+inverse DFT with the (C p, p) partials, and the x/r update with (r, r). `value` counts
+G A matvecs per second (one per step). The 243^3 fields (344 MB each) exceed the 129 MB L2,
+so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Profiling helpers (not bench lines): --quick skips the end-to-end, CG-to-tolerance and CPU
+legs; --grid n runs the same step on an n^3 grid (used for ncu captures on a smaller case).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import microstructure as ms  # noqa: E402
+
+N_GRID = (243, 243, 243)  # may be overridden by --grid for profiling captures
+VF = 0.2
+CONTRAST = 1000.0
+E_MACRO = np.array([1.0, 0.0, 0.0])
+METRIC = "G·A matvecs/s at 243^3 (FP64 CG step)"
+UNIT = "matvec/s"
+D = 3
+
+
+def workload():
+    h = ms.inclusion_side_for_fraction(VF, D)
+    ph = ms.box_phase(N_GRID, h)
+    table = ms.isotropic_table([1.0, CONTRAST], D)
+    return ph, table
+
+
+def config(extra=None):
+    c = {"workload": "GaNi 243^3 FP64 CG step, centred cube vf 0.2, contrast 1e3, E=(1,0,0)",
+         "grid": list(N_GRID), "d": D, "integration": "approx (GaNi)", "solver": "cg",
+         "l2": "inputs larger than L2 (344 MB per field)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------------------------------------
+# distributed helpers (replicas: each rank solves its own copy, no data-path collective)
+# ------------------------------------------------------------------------------------------
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.strip().split(",") for r in self.file.read().splitlines() if r.strip()]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for i, nm in enumerate(names):
+                if len(r) > 5 + i and "Active" in r[5 + i] and "Not" not in r[5 + i]:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle leg (test infrastructure, timed as it stands)
+# ------------------------------------------------------------------------------------------
+
+def cpu_oracle_cg_steps(nsteps=1):
+    """Time CG iterations of the FP64 NumPy oracle on this host at the bench workload."""
+    import oracle as O
+    ph, table = workload()
+    a = O.expand_phase(ph, table)[0, 0]
+    sysn = O.GaNi(a, D)
+    t0 = time.perf_counter()
+    res = O.cg(sysn, E_MACRO, fixed_iters=nsteps)
+    dt = time.perf_counter() - t0
+    # fixed_iters=k costs k matvecs plus the two of the set-up (b and r_0)
+    matvecs = nsteps + 2
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    del res
+    return {"value": matvecs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{nsteps} oracle CG iteration(s) + set-up at 243^3 ({matvecs} matvecs, "
+                      f"{dt:.1f} s, NumPy FP64 dense-matrix DFT, BLAS threads = host cores)"}
+
+
+# ------------------------------------------------------------------------------------------
+# roofline bookkeeping of the dominant kernel
+# ------------------------------------------------------------------------------------------
+
+def fft_flops_per_point(n):
+    """FP64 flops per complex point per transform of length n with this library's radix plan
+    (FMA = 2 flops): per radix-R butterfly 8H^2 + 20H flops with twiddles, 8H^2 + 8H without
+    (H = (R-1)/2); the first stage has no twiddles."""
+    rad = []
+    m = n
+    for R in (3, 5, 7, 11, 13, 17, 19, 23, 29, 31):
+        while m % R == 0:
+            rad.append(R)
+            m //= R
+    total = 0.0
+    for s, R in enumerate(rad):
+        H = (R - 1) // 2
+        fl = 8 * H * H + (20 * H if s > 0 else 8 * H)
+        total += fl / R
+    return total
+
+
+def pass_flops():
+    """Algorithmic FP64 flops of one launch of each pass kind at 243^3, d = 3."""
+    n = N_GRID[0]
+    nh = (n + 1) // 2
+    lines_c = n * n * D / 2.0                 # complex lines of the packed real transforms
+    f1 = fft_flops_per_point(n)
+    spec = n * n * nh * D                     # half-spectrum points per transform pass
+    return {
+        "line_fwd": lines_c * n * f1 + n * n * n * D * 2 + n * n * nh * D * 6,
+        "strided": spec * f1,
+        "proj": 2 * spec * f1 + n * n * nh * (4 * D + 2 + 2 * D),
+        "line_inv": lines_c * n * f1 + n * n * n * D * 2,
+    }
+
+
+def pass_bytes():
+    """Compulsory DRAM bytes of one launch of each pass kind at 243^3 (FP64)."""
+    n = N_GRID[0]
+    nh = (n + 1) // 2
+    spec = n * n * nh * D * 16
+    field = n * n * n * D * 8
+    return {"line_fwd": 2 * field + field + n ** 3 + spec,  # r, p read; p written; phase; spectrum
+            "strided": 2 * spec, "proj": 2 * spec,
+            "line_inv": spec + 2 * field}                    # spectrum; p read; C p written
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_1508_02045_gb300 as H
+
+    global N_GRID
+    if args.grid:
+        N_GRID = (args.grid,) * 3
+
+    torch.cuda.set_device(local)
+    ph, table = workload()
+    prob = H.Problem(D, N_GRID, H.phase_material(ph, table))
+    stream = torch.cuda.current_stream()
+    total = args.warmup + args.steps
+    opts = H.make_opts(fixed_iters=total + 1)
+    H.hom_solve_begin(prob.h, E_MACRO, H.HOM_CG, 0.0, opts)
+    H.hom_solve_iterate(prob.h, args.warmup)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K CG steps, inputs resident in HBM ----
+    clocks = ClockSampler(local)
+    clocks.start()
+    H.hom_profile_enable(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = H.hom_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    H.hom_solve_iterate(prob.h, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = H.hom_kernel_launches() - launches0
+    H.hom_profile_enable(False)
+    clk = clocks.stop()
+    passes = H.hom_profile_read()
+    ms_total = max_over_ranks(e0.elapsed_time(e1), world)
+    ms_step = ms_total / args.steps
+    H.hom_solve_end(prob.h, D, allow_not_converged=True)
+    if args.quick:
+        prob.close()
+        if rank == 0:
+            print(json.dumps({"quick": True, "grid": list(N_GRID), "ms_per_step": ms_step,
+                              "passes": passes, "gpu_launches": int(launches)}), flush=True)
+        return None
+
+    # ---- end to end: host field -> device, one G A application, result -> host ----
+    nfield = D * int(np.prod(N_GRID))
+    xh = torch.empty(nfield, dtype=torch.float64).pin_memory()
+    yh = torch.empty(nfield, dtype=torch.float64).pin_memory()
+    xh.copy_(torch.from_numpy(ms.random_field((nfield,), 11)))
+    xd = prob.field()
+    yd = prob.field()
+    for _ in range(2):
+        xd.view(-1).copy_(xh, non_blocking=True)
+        H.hom_apply(prob.h, H.HOM_OP_LINEAR, None, xd, yd)
+        yh.copy_(yd.view(-1), non_blocking=True)
+    torch.cuda.synchronize()
+    e_steps = max(3, min(args.steps, 10))
+    barrier(world)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e_steps):
+        xd.view(-1).copy_(xh, non_blocking=True)
+        H.hom_apply(prob.h, H.HOM_OP_LINEAR, None, xd, yd)
+        yh.copy_(yd.view(-1), non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1), world) / e_steps
+
+    # ---- CG time to 1e-6 (outside the timed region) ----
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    AH, flux, stats, st = H.hom_solve(prob.h, E_MACRO, H.HOM_CG, 1e-6,
+                                      H.make_opts(maxit=2000, check_every=16), None,
+                                      allow_not_converged=True)
+    cg_wall = time.perf_counter() - t0
+    prob.close()
+
+    if rank != 0:
+        return None
+    flops = pass_flops()
+    byts = pass_bytes()
+    per_kind = {}
+    for k, (ms_k, cnt) in passes.items():
+        if cnt:
+            per_kind[k] = {"ms_avg": ms_k / cnt, "launches": cnt, "share": None}
+    tot_ms = sum(v["ms_avg"] * v["launches"] for v in per_kind.values())
+    for v in per_kind.values():
+        v["share"] = round(v["ms_avg"] * v["launches"] / tot_ms, 4) if tot_ms else None
+    dom = max((k for k in per_kind if k in flops), key=lambda k: per_kind[k]["ms_avg"] * per_kind[k]["launches"])
+    dom_ms = per_kind[dom]["ms_avg"]
+    achieved = flops[dom] / (dom_ms * 1e-3) / 1e12
+    peak = 1.25  # FP64 TFLOP/s: 152 SMs x 2 DFMA/clk x 2 flops x ~2.07 GHz (nominal)
+    value = world * 1000.0 / ms_step
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded centred-cube phase image)",
+        "config": config({"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+        "e2e": {"value": round(world * 1000.0 / e2e_ms, 3), "unit": UNIT,
+                "h2d_bytes_per_step": nfield * 8, "d2h_bytes_per_step": nfield * 8,
+                "path": "pinned host field -> hom_apply(HOM_OP_LINEAR) -> pinned host field"},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "kernel": f"k_{dom}", "achieved": round(achieved, 4),
+                     "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                     "traffic": None, "peak_source": "recipe nominal FP64 (1.25 TFLOP/s)",
+                     "hbm_gbs_of_dominant": round(byts[dom] / (dom_ms * 1e-3) / 1e9, 1)},
+        "passes": per_kind,
+        "clocks": clk,
+        "cg_to_1e-6": {"iterations": stats["iterations"], "seconds": round(cg_wall, 3),
+                       "device_ms": round(stats["time_ms"], 2), "A_H": AH,
+                       "converged": bool(stats["converged"])},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_cg_steps(1)
+    return line
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    # the oracle as it stands, on this host's cores, same workload and unit
+    samples = []
+    for _ in range(max(1, args.warmup)):
+        pass
+    for _ in range(max(1, min(args.steps, 3))):
+        samples.append(cpu_oracle_cg_steps(1))
+    v = statistics.median(s["value"] for s in samples)
+    base = samples[0]
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": UNIT, "n_gpus": world,
+        "steps": len(samples), "warmup": 0, "ms_per_step": round(1000.0 / v, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded centred-cube phase image)", "config": config(),
+        "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                         "sample": base["sample"]},
+        "e2e": {"value": round(v, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true")
+    ap.add_argument("--grid", type=int, default=0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+        line = run_reference(args, rank, world)
+    else:
+        rank, world, local = dist_init()
+        line = run_ours(args, rank, world, local)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -140,6 +140,16 @@ int hom_apply(hom_problem* P, int op, const double* E, const double* x_dev, doub
 int hom_solve(hom_problem* P, const double* E, int solver, double tol, const hom_opts* opts,
               double* x_dev, double* AH_EE, double* flux, hom_stats* stats);
 
+/* hom_solve in three steps, for callers that interleave work (benchmarks, schedulers):
+ * begin validates like hom_solve, sets x_0 and enqueues the initial residual; iterate enqueues
+ * up to `iterations` further steps (fewer once the limit is reached) without synchronising,
+ * unless `done` is non-NULL, in which case it waits for the stream and reports whether the
+ * solver has stopped; end waits, then writes the same outputs and status as hom_solve. A
+ * problem holds one session at a time; begin discards an unfinished one. */
+int hom_solve_begin(hom_problem* P, const double* E, int solver, double tol, const hom_opts* opts);
+int hom_solve_iterate(hom_problem* P, int iterations, int* done);
+int hom_solve_end(hom_problem* P, double* x_dev, double* AH_EE, double* flux, hom_stats* stats);
+
 /* Energy (A(E + x), E + x) and flux <A(E + x)> of a device field x_dev on the solve grid
  * (x_dev may be NULL for x = 0, the Voigt value of Section 4.3). Synchronises the stream. */
 int hom_energy(hom_problem* P, const double* E, const double* x_dev, double* energy, double* flux);
@@ -163,6 +173,17 @@ const char* hom_strerror(int status);
 
 /* Number of kernels the library has launched in this process (a monotone counter). */
 long long hom_kernel_launches(void);
+
+/* Per-pass device timing for measurement: while enabled, every pass launch is bracketed by two
+ * CUDA events on its stream. Enabling clears earlier records. Not thread-safe; intended for
+ * benchmarks. Pass kinds: 0 pre-operator + forward DFT of the contiguous axis, 1 strided-axis
+ * DFT, 2 axis-0 DFT with the projection, 3 inverse DFT of the contiguous axis + solver update,
+ * 4 vector update / reduction kernels. */
+int hom_profile_enable(int on);
+
+/* Total milliseconds and launch counts per pass kind recorded since the last enable
+ * (ms[k], launches[k] for k < nkinds <= 5). Waits for the recorded events. */
+int hom_profile_read(double* ms, long long* launches, int nkinds);
 
 #ifdef __cplusplus
 }

@@ -28,7 +28,10 @@ SOLVERS = {"richardson": HOM_RICHARDSON, "cg": HOM_CG, "chebyshev": HOM_CHEBYSHE
            "eyre_milton": HOM_EYRE_MILTON}
 
 EXPORTED = ["hom_create", "hom_grid", "hom_bounds", "hom_apply", "hom_solve", "hom_energy",
-            "hom_prolongate", "hom_bound", "hom_destroy", "hom_strerror", "hom_kernel_launches"]
+            "hom_prolongate", "hom_bound", "hom_destroy", "hom_strerror", "hom_kernel_launches",
+            "hom_profile_enable", "hom_profile_read", "hom_solve_begin", "hom_solve_iterate",
+            "hom_solve_end"]
+PASS_KINDS = ["line_fwd", "strided", "proj", "line_inv", "vector"]
 
 
 class hom_material(ctypes.Structure):
@@ -67,6 +70,9 @@ def _load():
     lib.hom_solve.argtypes = [vp, dp, ip, ctypes.c_double, ctypes.POINTER(hom_opts), vp, dp, dp,
                               ctypes.POINTER(hom_stats)]
     lib.hom_energy.argtypes = [vp, dp, vp, dp, dp]
+    lib.hom_solve_begin.argtypes = [vp, dp, ip, ctypes.c_double, ctypes.POINTER(hom_opts)]
+    lib.hom_solve_iterate.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]
+    lib.hom_solve_end.argtypes = [vp, vp, dp, dp, ctypes.POINTER(hom_stats)]
     lib.hom_prolongate.argtypes = [vp, vp, vp, vp]
     lib.hom_bound.argtypes = [vp, vp, dp, vp, dp]
     lib.hom_destroy.argtypes = [vp]
@@ -75,6 +81,8 @@ def _load():
     lib.hom_strerror.restype = ctypes.c_char_p
     lib.hom_kernel_launches.argtypes = []
     lib.hom_kernel_launches.restype = ctypes.c_longlong
+    lib.hom_profile_enable.argtypes = [ip]
+    lib.hom_profile_read.argtypes = [dp, ctypes.POINTER(ctypes.c_longlong), ip]
     for name in EXPORTED:
         if name not in ("hom_destroy", "hom_strerror", "hom_kernel_launches"):
             getattr(lib, name).restype = ctypes.c_int
@@ -127,6 +135,18 @@ def hom_kernel_launches() -> int:
     return int(_lib.hom_kernel_launches())
 
 
+def hom_profile_enable(on: bool):
+    return _check(_lib.hom_profile_enable(1 if on else 0), "hom_profile_enable")
+
+
+def hom_profile_read():
+    n = len(PASS_KINDS)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_longlong * n)()
+    _check(_lib.hom_profile_read(ms, cnt, n), "hom_profile_read")
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(PASS_KINDS)}
+
+
 def hom_create(d, N, material: hom_material, integration=HOM_APPROX, precision=HOM_FP64,
                stream=None):
     vals = [int(v) for v in N] + [1] * max(0, 3 - len(N))
@@ -166,6 +186,28 @@ def hom_solve(P, E, solver, tol, opts: hom_opts | None = None, x=None, allow_not
                         ctypes.byref(stats))
     if not (st == HOM_OK or (allow_not_converged and st == HOM_ERR_NOT_CONVERGED)):
         raise HomError(st, "hom_solve")
+    return AH.value, [flux[i] for i in range(d)], stats.as_dict(), st
+
+
+def hom_solve_begin(P, E, solver, tol, opts: hom_opts | None = None):
+    o = ctypes.byref(opts) if opts is not None else None
+    return _check(_lib.hom_solve_begin(P, _dvec(E), int(solver), float(tol), o), "hom_solve_begin")
+
+
+def hom_solve_iterate(P, iterations, poll=False):
+    done = ctypes.c_int(0)
+    _check(_lib.hom_solve_iterate(P, int(iterations), ctypes.byref(done) if poll else None),
+           "hom_solve_iterate")
+    return bool(done.value) if poll else None
+
+
+def hom_solve_end(P, d, x=None, allow_not_converged=False):
+    AH = ctypes.c_double()
+    flux = (ctypes.c_double * 3)()
+    stats = hom_stats()
+    st = _lib.hom_solve_end(P, _ptr(x), ctypes.byref(AH), flux, ctypes.byref(stats))
+    if not (st == HOM_OK or (allow_not_converged and st == HOM_ERR_NOT_CONVERGED)):
+        raise HomError(st, "hom_solve_end")
     return AH.value, [flux[i] for i in range(d)], stats.as_dict(), st
 
 

@@ -20,6 +20,39 @@ long long& launch_counter() {
   static long long c = 0;
   return c;
 }
+// per-pass event timing: pairs of events recorded around each launch while enabled
+namespace {
+struct ProfState {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+  cudaEvent_t open[KIND_COUNT] = {};
+  size_t used = 0;
+  cudaEvent_t take() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+};
+ProfState& prof_state() {
+  static ProfState s;
+  return s;
+}
+}  // namespace
+bool profiling() { return prof_state().on; }
+void prof_mark(int kind, cudaStream_t st, bool start) {
+  ProfState& ps = prof_state();
+  cudaEvent_t e = ps.take();
+  cudaEventRecord(e, st);
+  if (start) {
+    ps.open[kind] = e;
+  } else {
+    ps.marks.push_back({kind, {ps.open[kind], e}});
+  }
+}
 int dynamic_smem_cap() {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
@@ -224,6 +257,19 @@ cudaError_t g_const_err = cudaSuccess;
 // ---------------------------------------------------------------------------------------
 // the problem handle
 // ---------------------------------------------------------------------------------------
+struct SolveState {
+  bool active = false;
+  int solver = 0;
+  int stop = 0;
+  bool fixed = false;
+  int maxit = 0;
+  int check = 8;
+  int issued = 0;
+  int matvecs = 0;
+  double E[3] = {0, 0, 0};
+  double nE = 0;
+};
+
 struct hom_problem {
   int d = 0;
   int N[3] = {1, 1, 1};     // trigonometric order
@@ -259,6 +305,7 @@ struct hom_problem {
   Scalars* h_sc = nullptr;        // pinned host mirror
   int red_grid = 0;               // grid of the reduction kernels
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  SolveState sv;
 };
 
 namespace {
@@ -358,6 +405,34 @@ const char* hom_strerror(int s) {
 }
 
 long long hom_kernel_launches(void) { return launch_counter(); }
+
+int hom_profile_enable(int on) {
+  ProfState& ps = prof_state();
+  if (on) {
+    ps.marks.clear();
+    ps.used = 0;
+  }
+  ps.on = on != 0;
+  return HOM_OK;
+}
+
+int hom_profile_read(double* ms, long long* launches, int nkinds) {
+  if (!ms || !launches || nkinds < 1) return HOM_ERR_INVALID;
+  ProfState& ps = prof_state();
+  for (int k = 0; k < nkinds; ++k) {
+    ms[k] = 0;
+    launches[k] = 0;
+  }
+  for (auto& m : ps.marks) {
+    if (m.first >= nkinds) continue;
+    if (cudaEventSynchronize(m.second.second) != cudaSuccess) return HOM_ERR_CUDA;
+    float t = 0;
+    cudaEventElapsedTime(&t, m.second.first, m.second.second);
+    ms[m.first] += t;
+    launches[m.first] += 1;
+  }
+  return HOM_OK;
+}
 
 void hom_destroy(hom_problem* P) {
   if (!P) return;
@@ -674,180 +749,198 @@ double true_residual(hom_problem* P, const double* E, const double* x, double* y
 
 }  // namespace
 
-extern "C" int hom_solve(hom_problem* P, const double* E, int solver, double tol,
-                         const hom_opts* opts, double* x_dev, double* AH_EE, double* flux,
-                         hom_stats* stats) {
+// ---------------------------------------------------------------------------------------
+// solve sessions: begin (validation, x_0, r_0 = b), iterate (enqueue steps), end (outputs)
+// ---------------------------------------------------------------------------------------
+namespace {
+
+int solve_stop_mode(int solver, int stop) {
+  if (stop == HOM_STOP_DEFAULT) return solver == HOM_EYRE_MILTON ? HOM_STOP_INCREMENT : HOM_STOP_RESIDUAL;
+  return stop;
+}
+
+// enqueue one iteration of the active solver (Algorithms 1-4); kernels exit early once the
+// device stopping flag is set
+void enqueue_step(hom_problem* P) {
+  SolveState& S_ = P->sv;
+  const int d = P->d;
+  const long long nodes = P->nodes;
+  cpx<double>* S = (cpx<double>*)P->S;
+  cudaStream_t st = P->stream;
+  OpArgs args{};
+  double* x = P->vec[0];
+  double* r = P->vec[2];
+  double* p = P->vec[3];
+  double* q = P->vec[4];
+  Fields<double> f{};
+  f.cs = nodes;
+  switch (S_.solver) {
+    case HOM_RICHARDSON:
+      f.x = P->vec[0];  // x_m / x_{m-1} alternate between vec[0] and vec[1]
+      P->e64.apply(PRE_AFFINE, PROJ_GAMMA, POST_RICH, f, S, P->d_sc, args, P->partials,
+                   P->counter, 0, st);
+      break;
+    case HOM_CG:
+      f.xin = r;
+      f.p = p;
+      f.out = q;
+      P->e64.apply(PRE_CG, PROJ_GAMMA, POST_CG, f, S, P->d_sc, args, P->partials, P->counter, 0, st);
+      Ops<double>::cg_update(x, r, p, q, (long long)d * nodes, nodes, P->d_sc, P->partials,
+                             P->counter, P->red_grid, st);
+      break;
+    case HOM_CHEBYSHEV: {
+      f.xin = p;
+      Fields<double> fi = f;
+      fi.p = p;
+      fi.r = r;
+      fi.x = x;
+      P->e64.apply2(PRE_LINEAR, PROJ_GAMMA, POST_CHEB, f, fi, S, P->d_sc, args, P->partials,
+                    P->counter, 0, st);
+      break;
+    }
+    default: {  // Eyre-Milton
+      f.xin = x;
+      Fields<double> fi = f;
+      fi.x = x;
+      P->e64.apply2(PRE_EM, PROJ_EM, POST_EM, f, fi, S, P->d_sc, args, P->partials, P->counter,
+                    0, st);
+      break;
+    }
+  }
+  S_.issued += 1;
+}
+
+}  // namespace
+
+extern "C" int hom_solve_begin(hom_problem* P, const double* E, int solver, double tol,
+                               const hom_opts* opts) {
   if (!P || !E) return HOM_ERR_INVALID;
   if (solver < HOM_RICHARDSON || solver > HOM_EYRE_MILTON) return HOM_ERR_INVALID;
   hom_opts o{};
   if (opts) o = *opts;
   if (o.fixed_iters <= 0 && !(tol > 0)) return HOM_ERR_INVALID;
   if (solver == HOM_EYRE_MILTON && P->integration == HOM_EXACT) return HOM_ERR_UNSUPPORTED;
-  if (P->precision == HOM_FP32_REFINED) return HOM_ERR_UNSUPPORTED;  // see hom_mp.cu
+  if (P->precision == HOM_FP32_REFINED) return HOM_ERR_UNSUPPORTED;
+  const int stop = solve_stop_mode(solver, o.stop);
+  if ((solver == HOM_CG || solver == HOM_CHEBYSHEV) && stop == HOM_STOP_INCREMENT) return HOM_ERR_UNSUPPORTED;
+  if (solver == HOM_EYRE_MILTON && stop == HOM_STOP_RESIDUAL) return HOM_ERR_UNSUPPORTED;
   const int d = P->d;
   const long long nodes = P->nodes;
   const long long len = (long long)d * nodes;
   const double cA = o.cA > 0 ? o.cA : P->cA;
   const double CA = o.CA > 0 ? o.CA : P->CA;
-  const int maxit = o.fixed_iters > 0 ? o.fixed_iters : (o.maxit > 0 ? o.maxit : 100000);
-  const int check = o.check_every > 0 ? o.check_every : 8;
-  int stop = o.stop;
-  if (stop == HOM_STOP_DEFAULT) stop = (solver == HOM_EYRE_MILTON) ? HOM_STOP_INCREMENT : HOM_STOP_RESIDUAL;
-  if ((solver == HOM_CG || solver == HOM_CHEBYSHEV) && stop == HOM_STOP_INCREMENT) return HOM_ERR_UNSUPPORTED;
-  if (solver == HOM_EYRE_MILTON && stop == HOM_STOP_RESIDUAL) return HOM_ERR_UNSUPPORTED;
-
-  cudaStream_t st = P->stream;
-  cpx<double>* S = (cpx<double>*)P->S;
+  SolveState& S_ = P->sv;
+  S_ = SolveState{};
+  S_.active = true;
+  S_.solver = solver;
+  S_.stop = stop;
+  S_.fixed = o.fixed_iters > 0;
+  S_.maxit = o.fixed_iters > 0 ? o.fixed_iters : (o.maxit > 0 ? o.maxit : 100000);
+  S_.check = o.check_every > 0 ? o.check_every : 8;
+  for (int a = 0; a < d; ++a) S_.E[a] = E[a];
   double nE = 0;
   for (int a = 0; a < d; ++a) nE += E[a] * E[a];
   nE = std::sqrt(nE);
+  S_.nE = nE;
 
+  cudaStream_t st = P->stream;
+  cpx<double>* S = (cpx<double>*)P->S;
   Scalars s{};
   for (int a = 0; a < d; ++a) s.E[a] = E[a];
   s.tol = tol;
   s.nE = nE;
-  s.maxit = maxit;
-  s.fixed = o.fixed_iters > 0 ? 1 : 0;
+  s.maxit = S_.maxit;
+  s.fixed = S_.fixed ? 1 : 0;
   s.stop = stop;
-  int rc = upload_scalars(P, P->d_sc, s);
-  if (rc) return rc;
-  HOM_CUDA(cudaEventRecord(P->ev0, st));
-
   double* x = P->vec[0];
   double* r = P->vec[2];
   double* p = P->vec[3];
   double* q = P->vec[4];
   OpArgs args{};
-  int matvecs = 0;
-  double* result = x;
-
-  if (solver == HOM_RICHARDSON) {
-    // x_m and x_{m-1} alternate between vec[0] and vec[1] (adjacent in one allocation)
-    double* pair = P->vec[0];
-    HOM_CUDA(cudaMemsetAsync(pair, 0, sizeof(double) * 2 * len, st));
-    s.omega = 2.0 / (cA + CA);
-    rc = upload_scalars(P, P->d_sc, s);
-    if (rc) return rc;
-    // ||b|| = ||G A E|| (x_0 = 0)
-    Fields<double> f0{};
-    f0.xin = pair;
-    f0.out = q;
-    f0.cs = nodes;
-    P->e64.apply(PRE_AFFINE, PROJ_GAMMA, POST_STORE, f0, S, P->d_sc, args, P->partials,
-                 P->counter, 0, st);
-    ++matvecs;
-    Fields<double> f{};
-    f.x = pair;
-    f.cs = nodes;
-    bool done = false;
-    int issued = 0;
-    while (!done) {
-      for (int k = 0; k < check && issued < maxit + 1; ++k, ++issued) {
-        P->e64.apply(PRE_AFFINE, PROJ_GAMMA, POST_RICH, f, S, P->d_sc, args, P->partials,
-                     P->counter, 0, st);
-      }
-      if ((rc = check_last()) || (rc = poll(P, P->d_sc))) return rc;
-      done = P->h_sc->done || issued >= maxit + 1;
-    }
-    matvecs += P->h_sc->it + (P->h_sc->converged && stop == HOM_STOP_RESIDUAL ? 1 : 0);
-    result = pair + (P->h_sc->result ? len : 0);
-  } else if (solver == HOM_CG || solver == HOM_CHEBYSHEV) {
-    HOM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * len, st));
+  if (solver == HOM_RICHARDSON) s.omega = 2.0 / (cA + CA);
+  if (solver == HOM_EYRE_MILTON) s.omega = std::sqrt(cA * CA);
+  if (solver == HOM_CHEBYSHEV) {
+    s.cheb_c = 0.5 * (CA - cA);
+    s.cheb_d = 0.5 * (cA + CA);
+    s.alpha = 1.0 / s.cheb_d;
+    s.beta = -0.5 * (s.cheb_c / s.cheb_d) * (s.cheb_c / s.cheb_d);
+  }
+  int rc = upload_scalars(P, P->d_sc, s);
+  if (rc) return rc;
+  HOM_CUDA(cudaEventRecord(P->ev0, st));
+  if (solver == HOM_EYRE_MILTON) {
+    Ops<double>::fill_const(x, nodes, d, P->d_sc, st);  // x_0 = E
+  } else {
+    // x_0 = 0; one affine application gives b = -G A E: ||b|| (and r_0 = p_0 = b for CG and
+    // Chebyshev, Algorithms 2-3)
+    HOM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * len * (solver == HOM_RICHARDSON ? 2 : 1), st));
     HOM_CUDA(cudaMemsetAsync(p, 0, sizeof(double) * len, st));
-    if (solver == HOM_CHEBYSHEV) {
-      s.cheb_c = 0.5 * (CA - cA);
-      s.cheb_d = 0.5 * (cA + CA);
-      s.alpha = 1.0 / s.cheb_d;
-      s.beta = -0.5 * (s.cheb_c / s.cheb_d) * (s.cheb_c / s.cheb_d);
-    } else {
-      s.beta = 0.0;
-    }
-    rc = upload_scalars(P, P->d_sc, s);
-    if (rc) return rc;
-    // r_0 = b - C x_0 = -G A E, p_0 = r_0 (written by the finisher-free store), ||b||, (r, r)
     Fields<double> f0{};
     f0.xin = x;
-    f0.out = r;
-    f0.p = p;
     f0.cs = nodes;
-    P->e64.apply(PRE_AFFINE, PROJ_GAMMA, POST_STORE, f0, S, P->d_sc, args, P->partials,
-                 P->counter, 1, st);
-    ++matvecs;
-    if (solver == HOM_CG) {
-      Fields<double> f{};
-      f.xin = r;
-      f.p = p;
-      f.out = q;
-      f.cs = nodes;
-      bool done = false;
-      int issued = 0;
-      while (!done) {
-        for (int k = 0; k < check && issued < maxit; ++k, ++issued) {
-          P->e64.apply(PRE_CG, PROJ_GAMMA, POST_CG, f, S, P->d_sc, args, P->partials,
-                       P->counter, 0, st);
-          Ops<double>::cg_update(x, r, p, q, len, nodes, P->d_sc, P->partials, P->counter,
-                                 P->red_grid, st);
-        }
-        if ((rc = check_last()) || (rc = poll(P, P->d_sc))) return rc;
-        done = P->h_sc->done || issued >= maxit;
-      }
+    if (solver == HOM_RICHARDSON) {
+      f0.out = q;
+      P->e64.apply(PRE_AFFINE, PROJ_GAMMA, POST_STORE, f0, S, P->d_sc, args, P->partials,
+                   P->counter, 0, st);
     } else {
-      Fields<double> f{};
-      f.xin = p;
-      f.p = p;
-      f.r = r;
-      f.x = x;
-      f.cs = nodes;
-      Fields<double> ff = f;
-      ff.x = nullptr;  // the forward pass reads p only
-      bool done = false;
-      int issued = 0;
-      while (!done) {
-        for (int k = 0; k < check && issued < maxit; ++k, ++issued)
-          P->e64.apply2(PRE_LINEAR, PROJ_GAMMA, POST_CHEB, ff, f, S, P->d_sc, args, P->partials,
-                        P->counter, 0, st);
-        if ((rc = check_last()) || (rc = poll(P, P->d_sc))) return rc;
-        done = P->h_sc->done || issued >= maxit;
-      }
+      f0.out = r;
+      f0.p = p;
+      P->e64.apply(PRE_AFFINE, PROJ_GAMMA, POST_STORE, f0, S, P->d_sc, args, P->partials,
+                   P->counter, 1, st);
     }
-    matvecs += P->h_sc->it;
-  } else {  // Eyre-Milton
-    s.omega = std::sqrt(cA * CA);
-    rc = upload_scalars(P, P->d_sc, s);
-    if (rc) return rc;
-    Ops<double>::fill_const(x, nodes, d, P->d_sc, st);
-    Fields<double> f{};
-    f.xin = x;
-    f.x = x;
-    f.cs = nodes;
-    Fields<double> ff = f;
-    ff.x = nullptr;
-    bool done = false;
-    int issued = 0;
-    while (!done) {
-      for (int k = 0; k < check && issued < maxit; ++k, ++issued)
-        P->e64.apply2(PRE_EM, PROJ_EM, POST_EM, ff, f, S, P->d_sc, args, P->partials, P->counter,
-                      0, st);
-      if ((rc = check_last()) || (rc = poll(P, P->d_sc))) return rc;
-      done = P->h_sc->done || issued >= maxit;
-    }
-    matvecs += P->h_sc->it;
+    S_.matvecs = 1;
+  }
+  return check_last();
+}
+
+extern "C" int hom_solve_iterate(hom_problem* P, int iterations, int* done) {
+  if (!P || !P->sv.active || iterations < 0) return HOM_ERR_INVALID;
+  SolveState& S_ = P->sv;
+  const int cap = S_.maxit + (S_.solver == HOM_RICHARDSON ? 1 : 0);
+  for (int k = 0; k < iterations && S_.issued < cap; ++k) enqueue_step(P);
+  int rc = check_last();
+  if (rc) return rc;
+  if (done) {
+    if ((rc = poll(P, P->d_sc))) return rc;
+    *done = (P->h_sc->done || S_.issued >= cap) ? 1 : 0;
+  }
+  return HOM_OK;
+}
+
+extern "C" int hom_solve_end(hom_problem* P, double* x_dev, double* AH_EE, double* flux,
+                             hom_stats* stats) {
+  if (!P || !P->sv.active) return HOM_ERR_INVALID;
+  SolveState& S_ = P->sv;
+  S_.active = false;
+  const int d = P->d;
+  const long long nodes = P->nodes;
+  const long long len = (long long)d * nodes;
+  cudaStream_t st = P->stream;
+  int rc = poll(P, P->d_sc);
+  if (rc) return rc;
+  const Scalars fin = *P->h_sc;
+  double* result = P->vec[0];
+  int matvecs = S_.matvecs + fin.it;
+  if (S_.solver == HOM_RICHARDSON) {
+    result = P->vec[0] + (fin.result ? len : 0);
+    if (fin.converged && S_.stop == HOM_STOP_RESIDUAL) matvecs += 1;
+  } else if (S_.solver == HOM_EYRE_MILTON) {
     // e = G x_m (Section 4.4): the conforming part of the non-conforming iterate
     Fields<double> fp{};
-    fp.xin = x;
-    fp.out = r;
+    fp.xin = P->vec[0];
+    fp.out = P->vec[2];
     fp.cs = nodes;
-    P->e64.apply(PRE_IDENT, PROJ_GAMMA, POST_STORE, fp, S, nullptr, args, nullptr, nullptr, 0, st);
-    result = r;
+    OpArgs args{};
+    P->e64.apply(PRE_IDENT, PROJ_GAMMA, POST_STORE, fp, (cpx<double>*)P->S, nullptr, args,
+                 nullptr, nullptr, 0, st);
+    result = P->vec[2];
   }
-  const Scalars fin = *P->h_sc;
   HOM_CUDA(cudaEventRecord(P->ev1, st));
   HOM_CUDA(cudaEventSynchronize(P->ev1));
   float ms = 0;
   cudaEventElapsedTime(&ms, P->ev0, P->ev1);
-
   double en = 0, fl[3] = {0, 0, 0};
-  rc = energy_eval(P, E, result, &en, fl);
+  rc = energy_eval(P, S_.E, result, &en, fl);
   if (rc) return rc;
   if (AH_EE) *AH_EE = en;
   if (flux)
@@ -857,25 +950,36 @@ extern "C" int hom_solve(hom_problem* P, const double* E, int solver, double tol
     stats->iterations = fin.it;
     stats->matvecs = matvecs;
     stats->converged = fin.converged;
-    if (solver == HOM_EYRE_MILTON || stop == HOM_STOP_INCREMENT)
-      stats->residual = fin.last_inc / (nE > 0 ? nE : 1);
+    if (S_.stop == HOM_STOP_INCREMENT)
+      stats->residual = fin.last_inc / (S_.nE > 0 ? S_.nE : 1);
     else
       stats->residual = fin.last_res / (fin.nb > 0 ? fin.nb : 1);
     stats->time_ms = ms;
-    const double nb = fin.nb;
-    const double tr = true_residual(P, E, result, q);
-    if (solver == HOM_EYRE_MILTON) {
-      stats->true_residual = tr;  // ||G A (E + e)||, unnormalised (no ||b|| computed)
-    } else {
-      stats->true_residual = (nb > 0 && tr >= 0) ? tr / nb : tr;
-    }
+    const double tr = true_residual(P, S_.E, result, P->vec[4]);
+    if (S_.solver == HOM_EYRE_MILTON)
+      stats->true_residual = tr;  // ||G A (E + e)||, no ||b|| formed by this solver
+    else
+      stats->true_residual = (fin.nb > 0 && tr >= 0) ? tr / fin.nb : tr;
   }
   if (x_dev) {
     HOM_CUDA(cudaMemcpyAsync(x_dev, result, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
     HOM_CUDA(cudaStreamSynchronize(st));
   }
   if ((rc = check_last())) return rc;
-  return (fin.converged || o.fixed_iters > 0) ? HOM_OK : HOM_ERR_NOT_CONVERGED;
+  return (fin.converged || S_.fixed) ? HOM_OK : HOM_ERR_NOT_CONVERGED;
+}
+
+extern "C" int hom_solve(hom_problem* P, const double* E, int solver, double tol,
+                         const hom_opts* opts, double* x_dev, double* AH_EE, double* flux,
+                         hom_stats* stats) {
+  int rc = hom_solve_begin(P, E, solver, tol, opts);
+  if (rc) return rc;
+  int done = 0;
+  while (!done) {
+    rc = hom_solve_iterate(P, P->sv.check, &done);
+    if (rc) return rc;
+  }
+  return hom_solve_end(P, x_dev, AH_EE, flux, stats);
 }
 
 extern "C" int hom_energy(hom_problem* P, const double* E, const double* x_dev, double* energy,

@@ -58,4 +58,10 @@ struct Ops {
 long long& launch_counter();
 int dynamic_smem_cap();
 
+// Optional per-pass event timing (hom_profile_enable): kinds of launches
+enum PassKind { KIND_LINE_FWD = 0, KIND_STRIDED = 1, KIND_PROJ = 2, KIND_LINE_INV = 3,
+                KIND_VECTOR = 4, KIND_COUNT = 5 };
+bool profiling();
+void prof_mark(int kind, cudaStream_t st, bool start);
+
 }  // namespace hom

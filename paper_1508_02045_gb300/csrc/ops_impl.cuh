@@ -94,6 +94,8 @@ static void line_fwd_d(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S
                        const Scalars* sc, const OpArgs& args, cudaStream_t st) {
   const unsigned grid = (unsigned)((g.nlines + g.LB - 1) / g.LB);
   const size_t sm = Ops<T>::smem_line(P.n, ncomp, g.LB);
+  const bool prof = profiling();
+  if (prof) prof_mark(KIND_LINE_FWD, st, true);
 #define HOM_LF(PRE_) k_line_fwd<T, D, PRE_><<<grid, kThreads, sm, st>>>(f, S, P, tw, ncomp, g.nlines, g.LB, g.scs, mat, sc, args)
   switch (pre) {
     case PRE_AFFINE: HOM_LF(PRE_AFFINE); break;
@@ -103,6 +105,7 @@ static void line_fwd_d(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S
     default: HOM_LF(PRE_IDENT); break;
   }
 #undef HOM_LF
+  if (prof) prof_mark(KIND_LINE_FWD, st, false);
   ++launch_counter();
 }
 
@@ -136,7 +139,10 @@ void Ops<T>::strided(const PassGeom& g, int axis, int inv, cpx<T>* S, const Axis
   }
   dim3 grid((unsigned)((C + TC - 1) / TC), (unsigned)batches);
   const size_t sm = smem_strided(P.n, TCp);
+  const bool prof = profiling();
+  if (prof) prof_mark(KIND_STRIDED, st, true);
   k_strided<T><<<grid, kThreads, sm, st>>>(S, P, tw, C, es, bs, TC, TCp, inv, sc);
+  if (prof) prof_mark(KIND_STRIDED, st, false);
   ++launch_counter();
 }
 
@@ -145,6 +151,8 @@ void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, con
                   const ProjGeom& pg, const Scalars* sc, cudaStream_t st) {
   const unsigned grid = (unsigned)((pg.C + g.TC0 - 1) / g.TC0);
   const size_t sm = smem_proj(P.n, g.D, g.TC0p);
+  const bool prof = profiling();
+  if (prof) prof_mark(KIND_PROJ, st, true);
 #define HOM_PJ(D_, M_) k_proj<T, D_, M_><<<grid, kThreads, sm, st>>>(S, P, tw, pg, g.TC0, g.TC0p, sc)
   if (g.D == 2) {
     if (mode == PROJ_EM) HOM_PJ(2, PROJ_EM); else HOM_PJ(2, PROJ_GAMMA);
@@ -152,6 +160,7 @@ void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, con
     if (mode == PROJ_EM) HOM_PJ(3, PROJ_EM); else HOM_PJ(3, PROJ_GAMMA);
   }
 #undef HOM_PJ
+  if (prof) prof_mark(KIND_PROJ, st, false);
   ++launch_counter();
 }
 
@@ -162,6 +171,8 @@ static void line_inv_d(const PassGeom& g, int post, const cpx<T>* S, const Field
                        int negate, cudaStream_t st) {
   const unsigned grid = (unsigned)((g.nlines + g.LB - 1) / g.LB);
   const size_t sm = Ops<T>::smem_line(P.n, ncomp, g.LB);
+  const bool prof = profiling();
+  if (prof) prof_mark(KIND_LINE_INV, st, true);
 #define HOM_LI(POST_) k_line_inv<T, D, POST_><<<grid, kThreads, sm, st>>>(S, f, P, tw, ncomp, g.nlines, g.LB, g.scs, mat, sc, args, partials, counter, negate)
   switch (post) {
     case POST_RICH: HOM_LI(POST_RICH); break;
@@ -171,6 +182,7 @@ static void line_inv_d(const PassGeom& g, int post, const cpx<T>* S, const Field
     default: HOM_LI(POST_STORE); break;
   }
 #undef HOM_LI
+  if (prof) prof_mark(KIND_LINE_INV, st, false);
   ++launch_counter();
 }
 
@@ -189,7 +201,10 @@ template <typename T>
 void Ops<T>::cg_update(T* x, T* r, const T* p, const T* q, long long len, long long nodes,
                        Scalars* sc, double* partials, unsigned* counter, int grid,
                        cudaStream_t st) {
+  const bool prof = profiling();
+  if (prof) prof_mark(KIND_VECTOR, st, true);
   k_cg_update<T><<<grid, kThreads, 0, st>>>(x, r, p, q, len, nodes, sc, partials, counter);
+  if (prof) prof_mark(KIND_VECTOR, st, false);
   ++launch_counter();
 }
 
