@@ -48,8 +48,13 @@ typedef enum {
   HOM_ERR_UNSUPPORTED = 3,    /* e.g. Eyre-Milton with exact integration (Section 3.4)     */
   HOM_ERR_NOT_CONVERGED = 4,  /* iteration limit reached; results are still written        */
   HOM_ERR_CUDA = 5,           /* a CUDA call failed                                        */
-  HOM_ERR_TIMEOUT = 6         /* a bounded device-side wait expired                        */
+  HOM_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired                        */
+  HOM_ERR_SCRATCH = 7         /* problem larger than the static scratch of hom_apply_static */
 } hom_status;
+
+/* Bytes of device memory reserved at load time, on every GPU that loads the library, for
+ * hom_apply_static (held until the process exits). */
+#define HOM_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
 
 typedef enum { HOM_APPROX = 0 /* GaNi: A sampled at the nodes */,
                HOM_EXACT = 1  /* Ga: A_M on the double grid   */ } hom_integration;
@@ -164,6 +169,39 @@ int hom_prolongate(hom_problem* coarse, hom_problem* fine, const double* x_dev, 
  * Synchronises the stream. */
 int hom_bound(hom_problem* gani, hom_problem* ga, const double* E, const double* x_dev,
               double* UE);
+
+/* hom_apply_static: the GaNi operator of hom_apply for callers that cannot allocate device
+ * memory. The paper has no counterpart; this entry point exists for integration only.
+ *
+ * Who needs it: a host application that owns every byte of device memory through its own
+ * allocator or a fixed budget (and plugins running inside one), and latency-critical loops
+ * that cannot pay for cudaMalloc/cudaFree, which may synchronise the device. hom_create
+ * allocates; this call does not: it calls no cudaMalloc, cudaFree or allocating library
+ * routine. Its work memory (half spectrum, twiddles, coefficient table) lives in one static
+ * device array of HOM_STATIC_SCRATCH_BYTES that the library reserves when it is loaded.
+ *
+ * Arguments: d = 2 or 3, N (d odd orders, as hom_create), phase_dev a DEVICE array of |N|
+ * phase indices (index_bytes 1 = uint8, 2 = uint16), table a HOST array of nphase row-major
+ * SPD d x d tensors (validated like hom_create), op one of hom_op (HOM_OP_EM uses
+ * omega = sqrt(c_A C_A) of the table), E (host, d doubles; read by HOM_OP_AFFINE only),
+ * x_dev / y_dev device fields of d x |N| doubles in the layout of hom_apply (distinct
+ * buffers), stream a cudaStream_t or NULL. The result equals hom_apply's for the same
+ * problem (same kernels).
+ *
+ * Limits and errors: the half spectrum (16 d |N| (N_d + 1) / (2 N_d) bytes) must fit in
+ * HOM_STATIC_SCRATCH_BYTES minus 576 KiB (e.g. 135^3 with d = 3 fits, 243^3 does not); larger
+ * problems return HOM_ERR_SCRATCH before any device work. Bad arguments: HOM_ERR_INVALID.
+ *
+ * Sharing: every call on a device uses the same scratch and leaves its contents behind;
+ * nothing in it needs to start at zero (each call writes the twiddles, the table and every
+ * spectrum entry before reading them). Calls whose work overlaps on the GPU (different
+ * streams or threads without ordering) race on the scratch and give wrong results; issue them
+ * on one stream or order them. Set-up: the first call on each device resolves the scratch
+ * address (cudaGetSymbolAddress) and uploads constants, so make that first call before any
+ * stream capture. Enqueued on `stream`; does not synchronise. */
+int hom_apply_static(int d, const int* N, const void* phase_dev, int index_bytes,
+                     const double* table, int nphase, int op, const double* E,
+                     const double* x_dev, double* y_dev, void* stream);
 
 /* Free everything the handle owns. NULL is accepted. */
 void hom_destroy(hom_problem* P);

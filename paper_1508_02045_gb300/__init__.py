@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhom.so")
 
 HOM_OK, HOM_ERR_INVALID, HOM_ERR_OOM, HOM_ERR_UNSUPPORTED, HOM_ERR_NOT_CONVERGED, HOM_ERR_CUDA, \
-    HOM_ERR_TIMEOUT = range(7)
+    HOM_ERR_TIMEOUT, HOM_ERR_SCRATCH = range(8)
+HOM_STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
 HOM_APPROX, HOM_EXACT = 0, 1
 HOM_RICHARDSON, HOM_CG, HOM_CHEBYSHEV, HOM_EYRE_MILTON = range(4)
 HOM_FP64, HOM_FP32_REFINED = 0, 1
@@ -30,7 +31,7 @@ SOLVERS = {"richardson": HOM_RICHARDSON, "cg": HOM_CG, "chebyshev": HOM_CHEBYSHE
 EXPORTED = ["hom_create", "hom_grid", "hom_bounds", "hom_apply", "hom_solve", "hom_energy",
             "hom_prolongate", "hom_bound", "hom_destroy", "hom_strerror", "hom_kernel_launches",
             "hom_profile_enable", "hom_profile_read", "hom_solve_begin", "hom_solve_iterate",
-            "hom_solve_end"]
+            "hom_solve_end", "hom_apply_static"]
 PASS_KINDS = ["line_fwd", "strided", "proj", "line_inv", "vector"]
 
 
@@ -70,6 +71,8 @@ def _load():
     lib.hom_solve.argtypes = [vp, dp, ip, ctypes.c_double, ctypes.POINTER(hom_opts), vp, dp, dp,
                               ctypes.POINTER(hom_stats)]
     lib.hom_energy.argtypes = [vp, dp, vp, dp, dp]
+    lib.hom_apply_static.argtypes = [ip, ctypes.POINTER(ctypes.c_int), vp, ip, dp, ip, ip, dp, vp,
+                                     vp, vp]
     lib.hom_solve_begin.argtypes = [vp, dp, ip, ctypes.c_double, ctypes.POINTER(hom_opts)]
     lib.hom_solve_iterate.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]
     lib.hom_solve_end.argtypes = [vp, vp, dp, dp, ctypes.POINTER(hom_stats)]
@@ -187,6 +190,20 @@ def hom_solve(P, E, solver, tol, opts: hom_opts | None = None, x=None, allow_not
     if not (st == HOM_OK or (allow_not_converged and st == HOM_ERR_NOT_CONVERGED)):
         raise HomError(st, "hom_solve")
     return AH.value, [flux[i] for i in range(d)], stats.as_dict(), st
+
+
+def hom_apply_static(d, N, phase_dev, table, op, E, x, y, stream=None):
+    """Allocation-free operator application (see include/hom.h): phase_dev is a CUDA uint8 /
+    uint16 tensor, table a host (nphase, d, d) array; x, y CUDA float64 fields."""
+    vals = [int(v) for v in N] + [1] * max(0, 3 - len(N))
+    Narr = (ctypes.c_int * len(vals))(*vals)
+    table = np.ascontiguousarray(table, dtype=np.float64)
+    Ep = _dvec(E) if E is not None else None
+    st = _stream() if stream is None else ctypes.c_void_p(stream)
+    return _check(_lib.hom_apply_static(int(d), Narr, _ptr(phase_dev), phase_dev.element_size(),
+                                        table.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        int(table.shape[0]), int(op), Ep, _ptr(x), _ptr(y), st),
+                  "hom_apply_static")
 
 
 def hom_solve_begin(P, E, solver, tol, opts: hom_opts | None = None):

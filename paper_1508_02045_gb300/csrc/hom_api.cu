@@ -400,6 +400,7 @@ const char* hom_strerror(int s) {
       return buf;
     }
     case HOM_ERR_TIMEOUT: return "device wait timed out";
+    case HOM_ERR_SCRATCH: return "problem too large for the static scratch of hom_apply_static";
     default: return "unknown status";
   }
 }
