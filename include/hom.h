@@ -95,6 +95,8 @@ typedef struct {
                          Eyre-Milton (Algorithms 1-4 print the increment test for Richardson) */
   double cA, CA;      /* override of the spectral bounds used by Richardson, Chebyshev, EM    */
   double inner_tol;   /* HOM_FP32_REFINED: relative tolerance of each FP32 inner solve (0=1e-4)*/
+                      /* HOM_FP32_REFINED uses maxit as the outer limit (0 = 50); only CG
+                         and Chebyshev run as inner solvers                                 */
   int check_every;    /* host polls the device stopping flag every this many iterations (0=8) */
 } hom_opts;
 
@@ -112,7 +114,9 @@ typedef enum {
   HOM_OP_AFFINE = 0,  /* y = G A (E + x) = C x - b                 eq. (linsys)                */
   HOM_OP_LINEAR = 1,  /* y = G A x = C x                                                        */
   HOM_OP_PROJECT = 2, /* y = G x                                   eq. (discrete_proj)          */
-  HOM_OP_EM = 3       /* y = F^{-1}(I - 2 G^)F (A - omega I) x     Algorithm 4, omega = sqrt(cA CA)*/
+  HOM_OP_EM = 3,      /* y = F^{-1}(I - 2 G^)F (A - omega I) x     Algorithm 4, omega = sqrt(cA CA)*/
+  HOM_OP_FP32 = 16    /* flag, or-ed into the above: apply the FP32 operator of a
+                         HOM_FP32_REFINED problem (x rounded to FP32, y widened to FP64)     */
 } hom_op;
 
 /* Create a problem on grid N (GaNi: the solve grid; Ga: the trigonometric order, the solve grid

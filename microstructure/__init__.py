@@ -75,13 +75,14 @@ def rsa_spheres(N, seed: int, rmin: float = 0.02, rmax: float = 0.06, vf: float 
     Radii are uniform in [rmin, rmax] (fractions of the cell), centres uniform in the cell.
     Spheres are added until the node-sampled volume fraction reaches vf. Returns
     (phase, centres, radii): phase is uint16, 0 for the matrix and s+1 inside sphere s.
+    Each sphere is rasterised only over its periodic bounding box of nodes.
     """
     N = tuple(int(n) for n in N)
     d = len(N)
     rng = np.random.default_rng(seed)
-    xs = node_coords(N)
     phase = np.zeros(N, dtype=np.uint16)
-    centres, radii = [], []
+    centres = np.zeros((0, d))
+    radii = np.zeros(0)
     covered = 0
     total = int(np.prod(N))
     tries = 0
@@ -89,26 +90,33 @@ def rsa_spheres(N, seed: int, rmin: float = 0.02, rmax: float = 0.06, vf: float 
         tries += 1
         r = rng.uniform(rmin, rmax)
         c = rng.uniform(-0.5, 0.5, size=d)
-        ok = True
-        for c2, r2 in zip(centres, radii):
-            dv = c - c2
+        if len(radii):
+            dv = centres - c[None, :]
             dv -= np.round(dv)
-            if float(np.dot(dv, dv)) < (r + r2) ** 2:
-                ok = False
-                break
-        if not ok:
-            continue
-        dist2 = np.zeros(N)
+            if np.any(np.sum(dv * dv, axis=1) < (radii + r) ** 2):
+                continue
+        # nodes m/N_a within the periodic bounding box of the sphere
+        idx, offs = [], []
+        for a, n in enumerate(N):
+            lo = int(np.floor((c[a] - r) * n)) - 1
+            hi = int(np.ceil((c[a] + r) * n)) + 1
+            m = np.arange(lo, hi + 1)
+            idx.append(np.mod(m, n))
+            offs.append(m / n - c[a])
+        dist2 = np.zeros([len(o) for o in offs])
         for a in range(d):
-            t = xs[a] - c[a]
-            t = t - np.round(t)
-            dist2 = dist2 + t * t
-        mask = (dist2 < r * r) & (phase == 0)
-        phase[mask] = len(radii) + 1
-        covered += int(mask.sum())
-        centres.append(c)
-        radii.append(r)
-    return phase, np.array(centres), np.array(radii)
+            shape = [1] * d
+            shape[a] = len(offs[a])
+            dist2 = dist2 + (offs[a] ** 2).reshape(shape)
+        inside = dist2 < r * r
+        sub = phase[np.ix_(*idx)]
+        newly = inside & (sub == 0)
+        sub[newly] = len(radii) + 1
+        phase[np.ix_(*idx)] = sub
+        covered += int(newly.sum())
+        centres = np.vstack([centres, c[None, :]])
+        radii = np.append(radii, r)
+    return phase, centres, radii
 
 
 def box_fourier_coefficients(M, h, a_matrix: float, a_incl: float) -> np.ndarray:

@@ -24,6 +24,7 @@ HOM_FP64, HOM_FP32_REFINED = 0, 1
 HOM_A_PHASE, HOM_A_SCALAR, HOM_A_FOURIER = range(3)
 HOM_STOP_DEFAULT, HOM_STOP_RESIDUAL, HOM_STOP_INCREMENT = range(3)
 HOM_OP_AFFINE, HOM_OP_LINEAR, HOM_OP_PROJECT, HOM_OP_EM = range(4)
+HOM_OP_FP32 = 16
 
 SOLVERS = {"richardson": HOM_RICHARDSON, "cg": HOM_CG, "chebyshev": HOM_CHEBYSHEV,
            "eyre_milton": HOM_EYRE_MILTON}

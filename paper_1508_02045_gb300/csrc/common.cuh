@@ -55,7 +55,7 @@ struct Scalars {
 };
 
 enum PreOp { PRE_AFFINE = 0, PRE_LINEAR = 1, PRE_CG = 2, PRE_EM = 3, PRE_IDENT = 4 };
-enum PostOp { POST_STORE = 0, POST_RICH = 1, POST_CG = 2, POST_CHEB = 3, POST_EM = 4 };
+enum PostOp { POST_STORE = 0, POST_RICH = 1, POST_CG = 2, POST_CHEB = 3, POST_EM = 4, POST_ADD = 5 };
 enum ProjMode { PROJ_GAMMA = 0, PROJ_EM = 1 };
 enum MatKind { MAT_PHASE_ISO = 0, MAT_PHASE_TENSOR = 1, MAT_FIELD = 2 };
 

@@ -268,6 +268,18 @@ struct SolveState {
   int matvecs = 0;
   double E[3] = {0, 0, 0};
   double nE = 0;
+  // iterative refinement (HOM_FP32_REFINED): FP32 inner solves of C d = r, FP64 outer residual
+  bool refined = false;
+  double tol = 0;
+  double inner_tol = 1e-4;
+  int inner_maxit = 10000;
+  int outer_it = 0;
+  int inner_total = 0;
+  double nb = 0;         // ||b|| (FP64)
+  double res = 0;        // ||b - C x|| (FP64) after the last outer update
+  bool finished = false;
+  bool converged = false;
+  float inner_ms = 0;
 };
 
 struct hom_problem {
@@ -302,6 +314,7 @@ struct hom_problem {
   unsigned* counter = nullptr;
   Scalars* d_sc = nullptr;        // solver scalars
   Scalars* d_aux = nullptr;       // scalars of auxiliary evaluations (energy, true residual)
+  Scalars* d_sc2 = nullptr;       // scalars of the FP32 inner solves (refinement)
   Scalars* h_sc = nullptr;        // pinned host mirror
   int red_grid = 0;               // grid of the reduction kernels
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -453,6 +466,7 @@ void hom_destroy(hom_problem* P) {
   if (P->counter) cudaFree(P->counter);
   if (P->d_sc) cudaFree(P->d_sc);
   if (P->d_aux) cudaFree(P->d_aux);
+  if (P->d_sc2) cudaFree(P->d_sc2);
   if (P->h_sc) cudaFreeHost(P->h_sc);
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
@@ -628,6 +642,7 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
   cudaMemset(P->counter, 0, sizeof(unsigned) * 4);
   if ((st = alloc((void**)&P->d_sc, sizeof(Scalars))) != HOM_OK) { hom_destroy(P); return st; }
   if ((st = alloc((void**)&P->d_aux, sizeof(Scalars))) != HOM_OK) { hom_destroy(P); return st; }
+  if ((st = alloc((void**)&P->d_sc2, sizeof(Scalars))) != HOM_OK) { hom_destroy(P); return st; }
   if (cudaMallocHost((void**)&P->h_sc, sizeof(Scalars)) != cudaSuccess) { hom_destroy(P); return HOM_ERR_OOM; }
   cudaEventCreate(&P->ev0);
   cudaEventCreate(&P->ev1);
@@ -678,19 +693,34 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
 
 int hom_apply(hom_problem* P, int op, const double* E, const double* x_dev, double* y_dev) {
   if (!P || !x_dev || !y_dev) return HOM_ERR_INVALID;
+  const bool fp32 = (op & HOM_OP_FP32) != 0;
+  op &= ~HOM_OP_FP32;
   if (op < HOM_OP_AFFINE || op > HOM_OP_EM) return HOM_ERR_INVALID;
   if (op == HOM_OP_AFFINE && !E) return HOM_ERR_INVALID;
   if (op == HOM_OP_EM && P->integration == HOM_EXACT) return HOM_ERR_UNSUPPORTED;
+  if (fp32 && P->precision != HOM_FP32_REFINED) return HOM_ERR_UNSUPPORTED;
   OpArgs args{};
   for (int a = 0; a < P->d; ++a) args.E[a] = E ? E[a] : 0.0;
   args.omega = std::sqrt(P->cA * P->CA);
+  const int pre = op == HOM_OP_AFFINE ? PRE_AFFINE : op == HOM_OP_LINEAR ? PRE_LINEAR
+                : op == HOM_OP_PROJECT ? PRE_IDENT : PRE_EM;
+  const int mode = op == HOM_OP_EM ? PROJ_EM : PROJ_GAMMA;
+  if (fp32) {
+    const long long len = (long long)P->d * P->nodes;
+    Ops<float>::convert_in(x_dev, P->fvec[0], len, P->stream);
+    Fields<float> f{};
+    f.xin = P->fvec[0];
+    f.out = P->fvec[1];
+    f.cs = P->nodes;
+    P->e32.apply(pre, mode, POST_STORE, f, (cpx<float>*)P->S, nullptr, args, nullptr, nullptr, 0,
+                 P->stream);
+    Ops<float>::convert_out(P->fvec[1], y_dev, len, P->stream);
+    return check_last();
+  }
   Fields<double> f{};
   f.xin = x_dev;
   f.out = y_dev;
   f.cs = P->nodes;
-  const int pre = op == HOM_OP_AFFINE ? PRE_AFFINE : op == HOM_OP_LINEAR ? PRE_LINEAR
-                : op == HOM_OP_PROJECT ? PRE_IDENT : PRE_EM;
-  const int mode = op == HOM_OP_EM ? PROJ_EM : PROJ_GAMMA;
   P->e64.apply(pre, mode, POST_STORE, f, (cpx<double>*)P->S, nullptr, args, nullptr, nullptr, 0,
                P->stream);
   return check_last();
@@ -813,6 +843,140 @@ void enqueue_step(hom_problem* P) {
 
 }  // namespace
 
+namespace {
+
+// r = b - C x = -G A (E + x) in FP64 into vec[2]; returns ||r|| (host synchronises)
+int refine_residual(hom_problem* P, double* res) {
+  SolveState& S_ = P->sv;
+  Scalars s{};
+  for (int a = 0; a < P->d; ++a) s.E[a] = S_.E[a];
+  int rc = upload_scalars(P, P->d_aux, s);
+  if (rc) return rc;
+  Fields<double> f{};
+  f.xin = P->vec[0];
+  f.out = P->vec[2];
+  f.cs = P->nodes;
+  OpArgs args{};
+  P->e64.apply(PRE_AFFINE, PROJ_GAMMA, POST_STORE, f, (cpx<double>*)P->S, P->d_aux, args,
+               P->partials, P->counter, 1, P->stream);
+  if ((rc = check_last()) || (rc = poll(P, P->d_aux))) return rc;
+  *res = P->h_sc->nb;
+  return HOM_OK;
+}
+
+// start an FP32 inner solve of C d = r (Algorithm 2 or 3 on the FP32 operator)
+int refine_start_inner(hom_problem* P) {
+  SolveState& S_ = P->sv;
+  Scalars s{};
+  s.tol = S_.inner_tol;
+  s.maxit = S_.inner_maxit;
+  s.stop = HOM_STOP_RESIDUAL;
+  if (S_.solver == HOM_CHEBYSHEV) {
+    s.cheb_c = 0.5 * (P->CA - P->cA);
+    s.cheb_d = 0.5 * (P->cA + P->CA);
+    s.alpha = 1.0 / s.cheb_d;
+    s.beta = -0.5 * (s.cheb_c / s.cheb_d) * (s.cheb_c / s.cheb_d);
+  }
+  int rc = upload_scalars(P, P->d_sc2, s);
+  if (rc) return rc;
+  const long long len = (long long)P->d * P->nodes;
+  Ops<float>::demote(P->vec[2], P->fvec[1], P->fvec[2], P->fvec[0], len, P->nodes, P->d_sc2,
+                     P->partials, P->counter, P->red_grid, P->stream);
+  if (S_.solver == HOM_CHEBYSHEV) {
+    // demote zeroes beta; restore Algorithm 3's initial coefficients
+    Scalars* h = P->h_sc;
+    if ((rc = poll(P, P->d_sc2))) return rc;
+    h->alpha = s.alpha;
+    h->beta = s.beta;
+    h->cheb_c = s.cheb_c;
+    h->cheb_d = s.cheb_d;
+    Scalars copy = *h;
+    if ((rc = upload_scalars(P, P->d_sc2, copy))) return rc;
+  }
+  return check_last();
+}
+
+void refine_enqueue_inner(hom_problem* P) {
+  const long long nodes = P->nodes;
+  cpx<float>* S = (cpx<float>*)P->S;
+  float* x = P->fvec[0];
+  float* r = P->fvec[1];
+  float* p = P->fvec[2];
+  float* q = P->fvec[3];
+  OpArgs args{};
+  Fields<float> f{};
+  f.cs = nodes;
+  if (P->sv.solver == HOM_CG) {
+    f.xin = r;
+    f.p = p;
+    f.out = q;
+    P->e32.apply(PRE_CG, PROJ_GAMMA, POST_CG, f, S, P->d_sc2, args, P->partials, P->counter, 0,
+                 P->stream);
+    Ops<float>::cg_update(x, r, p, q, (long long)P->d * nodes, nodes, P->d_sc2, P->partials,
+                          P->counter, P->red_grid, P->stream);
+  } else {
+    f.xin = p;
+    Fields<float> fi = f;
+    fi.p = p;
+    fi.r = r;
+    fi.x = x;
+    P->e32.apply2(PRE_LINEAR, PROJ_GAMMA, POST_CHEB, f, fi, S, P->d_sc2, args, P->partials,
+                  P->counter, 0, P->stream);
+  }
+}
+
+// after an inner solve stopped: x += d (FP64), new FP64 residual, stopping test
+int refine_outer_update(hom_problem* P) {
+  SolveState& S_ = P->sv;
+  const long long len = (long long)P->d * P->nodes;
+  int rc = poll(P, P->d_sc2);
+  if (rc) return rc;
+  S_.inner_total += P->h_sc->it;
+  // x += G d: the FP32 correction carries round-off outside the conforming space E (Section
+  // 4.4); C does not see that part but the energy does, so it is projected out in FP64
+  Ops<float>::convert_out(P->fvec[0], P->vec[4], len, P->stream);
+  Fields<double> f{};
+  f.xin = P->vec[4];
+  f.x = P->vec[0];
+  f.cs = P->nodes;
+  Fields<double> ff = f;
+  ff.x = nullptr;
+  OpArgs args{};
+  P->e64.apply2(PRE_IDENT, PROJ_GAMMA, POST_ADD, ff, f, (cpx<double>*)P->S, nullptr, args,
+                nullptr, nullptr, 0, P->stream);
+  S_.matvecs += 1;
+  if ((rc = refine_residual(P, &S_.res))) return rc;
+  S_.outer_it += 1;
+  if (S_.res <= S_.tol * S_.nb) {
+    S_.finished = true;
+    S_.converged = true;
+  } else if (S_.outer_it >= S_.maxit) {
+    S_.finished = true;
+  } else {
+    rc = refine_start_inner(P);
+  }
+  return rc;
+}
+
+int refine_begin(hom_problem* P) {
+  SolveState& S_ = P->sv;
+  const long long len = (long long)P->d * P->nodes;
+  HOM_CUDA(cudaEventRecord(P->ev0, P->stream));
+  HOM_CUDA(cudaMemsetAsync(P->vec[0], 0, sizeof(double) * len, P->stream));
+  int rc = refine_residual(P, &S_.nb);
+  if (rc) return rc;
+  S_.res = S_.nb;
+  S_.matvecs = 1;
+  if (S_.nb == 0.0) {
+    S_.finished = true;
+    S_.converged = true;
+    return HOM_OK;
+  }
+  return refine_start_inner(P);
+}
+
+}  // namespace
+
 extern "C" int hom_solve_begin(hom_problem* P, const double* E, int solver, double tol,
                                const hom_opts* opts) {
   if (!P || !E) return HOM_ERR_INVALID;
@@ -821,7 +985,6 @@ extern "C" int hom_solve_begin(hom_problem* P, const double* E, int solver, doub
   if (opts) o = *opts;
   if (o.fixed_iters <= 0 && !(tol > 0)) return HOM_ERR_INVALID;
   if (solver == HOM_EYRE_MILTON && P->integration == HOM_EXACT) return HOM_ERR_UNSUPPORTED;
-  if (P->precision == HOM_FP32_REFINED) return HOM_ERR_UNSUPPORTED;
   const int stop = solve_stop_mode(solver, o.stop);
   if ((solver == HOM_CG || solver == HOM_CHEBYSHEV) && stop == HOM_STOP_INCREMENT) return HOM_ERR_UNSUPPORTED;
   if (solver == HOM_EYRE_MILTON && stop == HOM_STOP_RESIDUAL) return HOM_ERR_UNSUPPORTED;
@@ -843,6 +1006,15 @@ extern "C" int hom_solve_begin(hom_problem* P, const double* E, int solver, doub
   for (int a = 0; a < d; ++a) nE += E[a] * E[a];
   nE = std::sqrt(nE);
   S_.nE = nE;
+  if (P->precision == HOM_FP32_REFINED) {
+    if (solver != HOM_CG && solver != HOM_CHEBYSHEV) return HOM_ERR_UNSUPPORTED;
+    if (!(tol > 0)) return HOM_ERR_INVALID;
+    S_.refined = true;
+    S_.tol = tol;
+    S_.inner_tol = o.inner_tol > 0 ? o.inner_tol : 1e-4;
+    S_.maxit = o.maxit > 0 ? o.maxit : 50;
+    return refine_begin(P);
+  }
 
   cudaStream_t st = P->stream;
   cpx<double>* S = (cpx<double>*)P->S;
@@ -897,6 +1069,20 @@ extern "C" int hom_solve_begin(hom_problem* P, const double* E, int solver, doub
 extern "C" int hom_solve_iterate(hom_problem* P, int iterations, int* done) {
   if (!P || !P->sv.active || iterations < 0) return HOM_ERR_INVALID;
   SolveState& S_ = P->sv;
+  if (S_.refined) {
+    if (!S_.finished)
+      for (int k = 0; k < iterations; ++k) refine_enqueue_inner(P);
+    int rc = check_last();
+    if (rc) return rc;
+    if (done) {
+      if (!S_.finished) {
+        if ((rc = poll(P, P->d_sc2))) return rc;
+        if (P->h_sc->done && (rc = refine_outer_update(P))) return rc;
+      }
+      *done = S_.finished ? 1 : 0;
+    }
+    return HOM_OK;
+  }
   const int cap = S_.maxit + (S_.solver == HOM_RICHARDSON ? 1 : 0);
   for (int k = 0; k < iterations && S_.issued < cap; ++k) enqueue_step(P);
   int rc = check_last();
@@ -917,7 +1103,35 @@ extern "C" int hom_solve_end(hom_problem* P, double* x_dev, double* AH_EE, doubl
   const long long nodes = P->nodes;
   const long long len = (long long)d * nodes;
   cudaStream_t st = P->stream;
-  int rc = poll(P, P->d_sc);
+  int rc;
+  if (S_.refined) {
+    HOM_CUDA(cudaEventRecord(P->ev1, st));
+    HOM_CUDA(cudaEventSynchronize(P->ev1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, P->ev0, P->ev1);
+    double en = 0, fl[3] = {0, 0, 0};
+    if ((rc = energy_eval(P, S_.E, P->vec[0], &en, fl))) return rc;
+    if (AH_EE) *AH_EE = en;
+    if (flux)
+      for (int a = 0; a < d; ++a) flux[a] = fl[a];
+    if (stats) {
+      std::memset(stats, 0, sizeof(*stats));
+      stats->iterations = S_.outer_it;
+      stats->inner_iterations = S_.inner_total;
+      stats->matvecs = S_.inner_total + S_.matvecs + S_.outer_it;
+      stats->converged = S_.converged ? 1 : 0;
+      stats->residual = S_.nb > 0 ? S_.res / S_.nb : 0.0;
+      stats->true_residual = stats->residual;  // the outer residual is formed in FP64
+      stats->time_ms = ms;
+    }
+    if (x_dev) {
+      HOM_CUDA(cudaMemcpyAsync(x_dev, P->vec[0], sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
+      HOM_CUDA(cudaStreamSynchronize(st));
+    }
+    if ((rc = check_last())) return rc;
+    return S_.converged ? HOM_OK : HOM_ERR_NOT_CONVERGED;
+  }
+  rc = poll(P, P->d_sc);
   if (rc) return rc;
   const Scalars fin = *P->h_sc;
   double* result = P->vec[0];

@@ -50,6 +50,11 @@ struct Ops {
   static void energy(int D, const T* x, long long nodes, const MatView<T>& mat, Scalars* sc,
                      double* partials, unsigned* counter, int grid, cudaStream_t st);
   static void fill_const(T* x, long long nodes, int d, const Scalars* sc, cudaStream_t st);
+  static void demote(const double* r64, T* r, T* p, T* x, long long len, long long nodes,
+                     Scalars* sc, double* partials, unsigned* counter, int grid, cudaStream_t st);
+  static void promote(double* x64, const T* dx, long long len, cudaStream_t st);
+  static void convert_in(const double* src, T* dst, long long len, cudaStream_t st);
+  static void convert_out(const T* src, double* dst, long long len, cudaStream_t st);
   static void pad_spectrum(const cpx<T>* Sn, cpx<T>* Sm, int D, int n0, int n1, int nh, int m0,
                            int m1, int mh, double scale, long long nlen, long long mlen,
                            cudaStream_t st);

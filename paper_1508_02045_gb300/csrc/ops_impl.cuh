@@ -80,6 +80,8 @@ cudaError_t Ops<T>::prepare(int) {
   HOM_SET_SMEM((k_line_inv<T, 2, POST_CG>));
   HOM_SET_SMEM((k_line_inv<T, 2, POST_CHEB>));
   HOM_SET_SMEM((k_line_inv<T, 2, POST_EM>));
+  HOM_SET_SMEM((k_line_inv<T, 2, POST_ADD>));
+  HOM_SET_SMEM((k_line_inv<T, 3, POST_ADD>));
   HOM_SET_SMEM((k_line_inv<T, 3, POST_STORE>));
   HOM_SET_SMEM((k_line_inv<T, 3, POST_RICH>));
   HOM_SET_SMEM((k_line_inv<T, 3, POST_CG>));
@@ -179,6 +181,7 @@ static void line_inv_d(const PassGeom& g, int post, const cpx<T>* S, const Field
     case POST_CG: HOM_LI(POST_CG); break;
     case POST_CHEB: HOM_LI(POST_CHEB); break;
     case POST_EM: HOM_LI(POST_EM); break;
+    case POST_ADD: HOM_LI(POST_ADD); break;
     default: HOM_LI(POST_STORE); break;
   }
 #undef HOM_LI
@@ -221,6 +224,40 @@ void Ops<T>::fill_const(T* x, long long nodes, int d, const Scalars* sc, cudaStr
   const long long len = nodes * d;
   const unsigned grid = (unsigned)std::min<long long>((len + kThreads - 1) / kThreads, 152 * 16);
   k_fill_const<T><<<grid, kThreads, 0, st>>>(x, nodes, d, sc);
+  ++launch_counter();
+}
+
+template <typename T>
+void Ops<T>::demote(const double* r64, T* r, T* p, T* x, long long len, long long nodes,
+                    Scalars* sc, double* partials, unsigned* counter, int grid, cudaStream_t st) {
+  const bool prof = profiling();
+  if (prof) prof_mark(KIND_VECTOR, st, true);
+  k_demote<T><<<grid, kThreads, 0, st>>>(r64, r, p, x, len, nodes, sc, partials, counter);
+  if (prof) prof_mark(KIND_VECTOR, st, false);
+  ++launch_counter();
+}
+
+template <typename T>
+void Ops<T>::promote(double* x64, const T* dx, long long len, cudaStream_t st) {
+  const unsigned grid = (unsigned)std::min<long long>((len + kThreads - 1) / kThreads, 152 * 16);
+  const bool prof = profiling();
+  if (prof) prof_mark(KIND_VECTOR, st, true);
+  k_promote<T><<<grid, kThreads, 0, st>>>(x64, dx, len);
+  if (prof) prof_mark(KIND_VECTOR, st, false);
+  ++launch_counter();
+}
+
+template <typename T>
+void Ops<T>::convert_in(const double* src, T* dst, long long len, cudaStream_t st) {
+  const unsigned grid = (unsigned)std::min<long long>((len + kThreads - 1) / kThreads, 152 * 16);
+  k_to_working<T><<<grid, kThreads, 0, st>>>(src, dst, len);
+  ++launch_counter();
+}
+
+template <typename T>
+void Ops<T>::convert_out(const T* src, double* dst, long long len, cudaStream_t st) {
+  const unsigned grid = (unsigned)std::min<long long>((len + kThreads - 1) / kThreads, 152 * 16);
+  k_to_double<T><<<grid, kThreads, 0, st>>>(src, dst, len);
   ++launch_counter();
 }
 

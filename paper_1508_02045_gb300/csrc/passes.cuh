@@ -487,6 +487,9 @@ k_line_inv(const cpx<T>* __restrict__ S, Fields<T> f, AxisPlan P, const cpx<T>* 
         f.p[a * cs + g] = rn - beta * pv;
         acc[0] += (double)rn * (double)rn;
       }
+    } else if (POST == POST_ADD) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) f.x[a * cs + g] += y[a];
     } else if (POST == POST_EM) {
       T w[D], xn[D];
 #pragma unroll
@@ -645,6 +648,53 @@ __global__ void k_fill_const(T* x, long long nodes, int d, const Scalars* sc) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nodes * d;
        i += (long long)gridDim.x * blockDim.x)
     x[i] = (T)sc->E[i / nodes];
+}
+
+// Iterative refinement, start of an inner solve of C d = r in precision T: r_T = (T) r,
+// p_T = r_T, d_T = 0, and (r_T, r_T) in FP64 (the inner ||b|| and (r, r)).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_demote(const double* __restrict__ r64, T* __restrict__ r, T* __restrict__ p, T* __restrict__ x,
+         long long len, long long nodes, Scalars* sc, double* partials, unsigned* counter) {
+  double acc[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T v = (T)r64[i];
+    r[i] = v;
+    p[i] = v;
+    x[i] = (T)0;
+    acc[0] += (double)v * (double)v;
+  }
+  double tot[1];
+  if (!reduce_and_last<1>(acc, partials, counter, tot)) return;
+  if (threadIdx.x != 0) return;
+  const double rr = tot[0] / (double)nodes;
+  sc->rr = rr;
+  sc->nb = sqrt(rr);
+  sc->last_res = sqrt(rr);
+  sc->beta = 0.0;
+}
+
+// precision conversions of whole fields (FP32 operator applications on FP64 arguments)
+template <typename T>
+__global__ void k_to_working(const double* __restrict__ src, T* __restrict__ dst, long long len) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (T)src[i];
+}
+template <typename T>
+__global__ void k_to_double(const T* __restrict__ src, double* __restrict__ dst, long long len) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
+}
+
+// Iterative refinement, end of an inner solve: x_64 += (double) d_T
+template <typename T>
+__global__ void k_promote(double* __restrict__ x64, const T* __restrict__ dx, long long len) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    x64[i] += (double)dx[i];
 }
 
 // half spectrum of grid N (scaled by `scale`) placed into the zeroed half spectrum of grid M

@@ -1,0 +1,90 @@
+"""FP32 operator inside FP64 iterative refinement (HOM_FP32_REFINED) vs the FP64 oracle.
+
+The FP32 operator is compared at FP32 accuracy; the refined solves must reach A_H within the
+mixed-precision bar (1e-8 relative) because the outer residual is formed in FP64.
+"""
+import numpy as np
+import pytest
+
+import microstructure as ms
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1508_02045_gb300 as H  # noqa: E402
+
+AH_TOL_MIXED = 1e-8
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def spheres(N, seed, contrast=(10.0, 1000.0)):
+    d = len(N)
+    ph, c, r = ms.rsa_spheres(N, seed, vf=0.3)
+    rng = np.random.default_rng(seed + 100)
+    vals = np.concatenate([[1.0], np.exp(rng.uniform(np.log(contrast[0]), np.log(contrast[1]), len(r)))])
+    return ph, ms.isotropic_table(vals, d)
+
+
+@pytest.mark.parametrize("N", [(63, 63), (27, 25, 21), (45, 45, 45)])
+def test_fp32_operator_parity(N):
+    d = len(N)
+    ph = ms.box_phase(N, 0.6)
+    table = ms.isotropic_table([1.0, 10.0], d)
+    P = H.Problem(d, N, H.phase_material(ph, table), precision=H.HOM_FP32_REFINED)
+    x = ms.random_field((d,) + N, 4)
+    y = P.field()
+    H.hom_apply(P.h, H.HOM_OP_LINEAR | H.HOM_OP_FP32, None, torch.from_numpy(x).cuda(), y)
+    ref = O.GaNi(O.expand_phase(ph, table)[0, 0], d).matvec(x)
+    err = rel(y.cpu().numpy(), ref)
+    assert err < 2e-6, err  # FP32 arithmetic, ~log2(N) stages of rounding
+    P.close()
+
+
+@pytest.mark.parametrize("solver", ["cg", "chebyshev"])
+@pytest.mark.parametrize("N", [(85, 85), (33, 35, 31)])
+def test_refined_solve_matches_fp64_oracle(N, solver):
+    d = len(N)
+    ph = ms.box_phase(N, 0.6)
+    table = ms.isotropic_table([1.0, 100.0], d)
+    P = H.Problem(d, N, H.phase_material(ph, table), precision=H.HOM_FP32_REFINED)
+    E = np.eye(d)[0]
+    x = P.field()
+    AH, flux, stats, _ = H.hom_solve(P.h, E, H.SOLVERS[solver], 1e-10, None, x)
+    sysn = O.GaNi(O.expand_phase(ph, table)[0, 0], d)
+    xr = O.cg(sysn, E, tol=1e-12).x
+    ref = sysn.energy(E, xr)
+    assert stats["converged"] and stats["true_residual"] <= 1e-10
+    assert abs(AH - ref) < AH_TOL_MIXED * ref
+    assert rel(x.cpu().numpy(), xr) < 1e-8
+    assert stats["iterations"] <= 6  # outer FP64 residuals: FP32 inner solves to 1e-4 each
+    P.close()
+
+
+def test_refined_spheres_anisotropic_contrast():
+    # the 405^3 workload's microstructure at 45^3: RSA spheres, log-uniform conductivities
+    N = (45, 45, 45)
+    ph, table = spheres(N, 7)
+    P = H.Problem(3, N, H.phase_material(ph, table), precision=H.HOM_FP32_REFINED)
+    E = np.array([1.0, 0.0, 0.0])
+    AH, _, stats, _ = H.hom_solve(P.h, E, H.HOM_CG, 1e-8, None, None)
+    sysn = O.GaNi(O.expand_phase(ph, table)[0, 0], 3)
+    ref = sysn.energy(E, O.cg(sysn, E, tol=1e-11).x)
+    assert abs(AH - ref) < AH_TOL_MIXED * ref
+    P.close()
+
+
+def test_refined_rejects_other_solvers():
+    N = (9, 9)
+    P = H.Problem(2, N, H.phase_material(ms.box_phase(N, 0.6), ms.isotropic_table([1.0, 10.0], 2)),
+                  precision=H.HOM_FP32_REFINED)
+    with pytest.raises(H.HomError) as ei:
+        H.hom_solve(P.h, np.array([1.0, 0.0]), H.HOM_RICHARDSON, 1e-6)
+    assert ei.value.status == H.HOM_ERR_UNSUPPORTED
+    P.close()
