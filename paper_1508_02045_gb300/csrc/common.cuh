@@ -5,8 +5,9 @@
 
 namespace hom {
 
+// complex value; aligned to its size so that loads and stores are single vector accesses
 template <typename T>
-struct cpx {
+struct __align__(2 * sizeof(T)) cpx {
   T x, y;
 };
 
@@ -20,13 +21,40 @@ constexpr int kMaxStages = 16;    // radix stages per axis
 constexpr int kMaxRadix = 31;     // largest supported prime factor of an axis length
 constexpr int kMaxAxis = 1023;    // longest supported axis (shared-memory tiles)
 
-// Radix plan of one axis of odd length n = prod radix[s]; pprev[s] = prod_{t<s} radix[t].
+// Division of 32-bit unsigned numerators by a fixed divisor d >= 1 with a multiply-high and two
+// shifts (Granlund-Montgomery round-up method): l = ceil(log2 d), m = floor(2^32 (2^l - d)/d) + 1,
+// q = (t + ((x - t) >> min(l, 1))) >> max(l - 1, 0) with t = mulhi(m, x); exact for all x.
+struct FastDiv {
+  unsigned mul;
+  unsigned sh1, sh2;
+};
+inline __host__ __device__ FastDiv make_fastdiv(int d) {
+  unsigned l = 0;
+  while ((1u << l) < (unsigned)d) ++l;
+  FastDiv f;
+  f.mul = (unsigned)(((1ull << 32) * ((1ull << l) - (unsigned long long)d)) / (unsigned long long)d + 1);
+  f.sh1 = l > 0 ? 1u : 0u;
+  f.sh2 = l > 0 ? l - 1 : 0u;
+  return f;
+}
+
+// Radix plan of one axis of odd length n = prod radix[s]; pprev[s] = prod_{t<s} radix[t];
+// fdm[s], fdp[s] divide by n / radix[s] and by pprev[s] (computed on the host).
 struct AxisPlan {
   int n;
   int nst;
   int radix[kMaxStages];
   int pprev[kMaxStages];
+  FastDiv fdm[kMaxStages];
+  FastDiv fdp[kMaxStages];
 };
+
+inline __host__ void plan_fastdivs(AxisPlan* P) {
+  for (int s = 0; s < P->nst; ++s) {
+    P->fdm[s] = make_fastdiv(P->n / P->radix[s]);
+    P->fdp[s] = make_fastdiv(P->pprev[s]);
+  }
+}
 
 // Scalars of one solve, resident on the device so that a captured iteration replays without
 // host round trips. Written by the reduction finishers, read by every kernel of a step.
@@ -59,15 +87,41 @@ enum PostOp { POST_STORE = 0, POST_RICH = 1, POST_CG = 2, POST_CHEB = 3, POST_EM
 enum ProjMode { PROJ_GAMMA = 0, PROJ_EM = 1 };
 enum MatKind { MAT_PHASE_ISO = 0, MAT_PHASE_TENSOR = 1, MAT_FIELD = 2 };
 
-// Coefficient view used by the pre/post operators. Phase tables live in double on the device
-// and are converted per use; scalar fields are stored in the working precision T.
+// Coefficient view used by the pre/post operators, in the working precision T.
 template <typename T>
 struct MatView {
   int kind;
   const uint8_t* ph8;
   const uint16_t* ph16;
-  const double* table;   // nphase * d * d (tensor) or nphase (isotropic)
+  const T* table;        // nphase * d * d (tensor) or nphase (isotropic)
   const T* field;        // one scalar per node
+};
+
+// Accumulator of a dot product in FP64 accuracy. FP64 kernels accumulate in double; FP32
+// kernels keep an unevaluated sum hi + lo of two floats and add each product with the
+// error-free transformations TwoProduct (p + e = a b via one FMA) and TwoSum (Ogita, Rump &
+// Oishi's compensated dot product), so the FP64 pipe is not used per element.
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += err + e;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
 }  // namespace hom

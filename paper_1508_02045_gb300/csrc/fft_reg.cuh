@@ -1,0 +1,300 @@
+// Register-resident odd DFTs and the Stockham stage that drives them.
+//
+// A transform of eq. (DFT) along one axis of odd length n = R_0 R_1 ... R_{S-1} runs as S
+// self-sorting (Stockham, decimation-in-time) stages. Stage s with radix R and p = R_0 ... R_{s-1}
+// takes, for butterfly i < n/R and k = i mod p,
+//   u_r = in[i + r n/R] * w^{r k},  w = exp(-2 pi i / (p R)),   r < R,
+//   U = DFT_R(u),   out[(i - k) R + k + r p] = U_r,
+// so the output is in natural order after the last stage. Each R_s is an odd number <= 31 and
+// DFT_R is computed entirely in registers: a prime R by pairing the terms r and R - r (a cosine
+// and a sine part per output pair), a composite R = A B by the same Cooley-Tukey split in
+// registers with compile-time indices and constant twiddles. The planner groups the prime
+// factors of n into as few such radices as fit in registers, so most axes need two stages.
+// The inverse transform (eq. (DFT), no scaling) is conj(F(conj(.))): imaginary parts are
+// negated on every load and store of a stage.
+#pragma once
+#include "common.cuh"
+
+namespace hom {
+
+// ---------------------------------------------------------------------------------------
+// constants cos/sin(2 pi j / R) for every odd R <= 31
+// ---------------------------------------------------------------------------------------
+__host__ __device__ constexpr int reg_offset(int R) {
+  // sum of the odd sizes below R, starting at 3
+  return R <= 3 ? 0 : reg_offset(R - 2) + (R - 2);
+}
+constexpr int kRegMax = 31;
+constexpr int kRegTable = reg_offset(kRegMax) + kRegMax;  // 255
+
+static __constant__ double c_rcos_d[kRegTable];
+static __constant__ double c_rsin_d[kRegTable];
+static __constant__ float c_rcos_f[kRegTable];
+static __constant__ float c_rsin_f[kRegTable];
+
+template <typename T> __device__ __forceinline__ T rcos(int j);
+template <typename T> __device__ __forceinline__ T rsin(int j);
+template <> __device__ __forceinline__ double rcos<double>(int j) { return c_rcos_d[j]; }
+template <> __device__ __forceinline__ double rsin<double>(int j) { return c_rsin_d[j]; }
+template <> __device__ __forceinline__ float rcos<float>(int j) { return c_rcos_f[j]; }
+template <> __device__ __forceinline__ float rsin<float>(int j) { return c_rsin_f[j]; }
+
+__host__ __device__ constexpr int smallest_factor(int R) {
+  return R % 3 == 0 ? 3 : R % 5 == 0 ? 5 : R % 7 == 0 ? 7 : R % 11 == 0 ? 11 : R % 13 == 0 ? 13
+       : R % 17 == 0 ? 17 : R % 19 == 0 ? 19 : R % 23 == 0 ? 23 : R % 29 == 0 ? 29 : R;
+}
+
+// ---------------------------------------------------------------------------------------
+// forward DFT of R points held in registers, natural order in and out
+// ---------------------------------------------------------------------------------------
+template <typename T, int R, int A = smallest_factor(R)>
+struct RegDft;
+
+// prime R
+template <typename T, int R>
+struct RegDft<T, R, R> {
+  static __device__ __forceinline__ void run(cpx<T> (&u)[R]) {
+    constexpr int H = (R - 1) / 2;
+    constexpr int off = reg_offset(R);
+    cpx<T> y0 = u[0];
+#pragma unroll
+    for (int r = 1; r <= H; ++r) {
+      const cpx<T> t = u[r];
+      u[r].x = t.x + u[R - r].x;
+      u[r].y = t.y + u[R - r].y;
+      u[R - r].x = t.x - u[R - r].x;
+      u[R - r].y = t.y - u[R - r].y;
+      y0.x += u[r].x;
+      y0.y += u[r].y;
+    }
+    cpx<T> o[R];
+    o[0] = y0;
+#pragma unroll
+    for (int s = 1; s <= H; ++s) {
+      cpx<T> C, S;
+      C.x = fma(rcos<T>(off + s), u[1].x, u[0].x);
+      C.y = fma(rcos<T>(off + s), u[1].y, u[0].y);
+      S.x = rsin<T>(off + s) * u[R - 1].x;
+      S.y = rsin<T>(off + s) * u[R - 1].y;
+#pragma unroll
+      for (int r = 2; r <= H; ++r) {
+        const int j = (r * s) % R;
+        C.x = fma(rcos<T>(off + j), u[r].x, C.x);
+        C.y = fma(rcos<T>(off + j), u[r].y, C.y);
+        S.x = fma(rsin<T>(off + j), u[R - r].x, S.x);
+        S.y = fma(rsin<T>(off + j), u[R - r].y, S.y);
+      }
+      // y_s = C - i S, y_{R-s} = C + i S
+      o[s].x = C.x + S.y;
+      o[s].y = C.y - S.x;
+      o[R - s].x = C.x - S.y;
+      o[R - s].y = C.y + S.x;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) u[r] = o[r];
+  }
+};
+
+// composite R = A * B: A-point DFTs over the stride-B subsequences, twiddles
+// exp(-2 pi i j2 k1 / R), B-point DFTs over j2: X[k1 + A k2]
+template <typename T, int R, int A>
+struct RegDft {
+  static __device__ __forceinline__ void run(cpx<T> (&u)[R]) {
+    constexpr int B = R / A;
+    constexpr int off = reg_offset(R);
+    cpx<T> y[R];  // y[k1 * B + j2]
+#pragma unroll
+    for (int j2 = 0; j2 < B; ++j2) {
+      cpx<T> v[A];
+#pragma unroll
+      for (int j1 = 0; j1 < A; ++j1) v[j1] = u[j2 + B * j1];
+      RegDft<T, A>::run(v);
+#pragma unroll
+      for (int k1 = 0; k1 < A; ++k1) {
+        const int m = (j2 * k1) % R;
+        if (m == 0) {
+          y[k1 * B + j2] = v[k1];
+        } else {
+          const T c = rcos<T>(off + m), s = -rsin<T>(off + m);
+          y[k1 * B + j2].x = v[k1].x * c - v[k1].y * s;
+          y[k1 * B + j2].y = v[k1].x * s + v[k1].y * c;
+        }
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) {
+      cpx<T> v[B];
+#pragma unroll
+      for (int j2 = 0; j2 < B; ++j2) v[j2] = y[k1 * B + j2];
+      RegDft<T, B>::run(v);
+#pragma unroll
+      for (int k2 = 0; k2 < B; ++k2) u[k1 + A * k2] = v[k2];
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------------------
+// dynamic shared memory of every pass kernel, addressed with 32-bit element offsets
+// ---------------------------------------------------------------------------------------
+extern __shared__ __align__(16) unsigned char hom_dyn_smem[];
+
+template <typename T>
+__device__ __forceinline__ cpx<T>* smem_c() {
+  return reinterpret_cast<cpx<T>*>(hom_dyn_smem);
+}
+
+__device__ __forceinline__ int fdiv(int x, const FastDiv& f) {
+  const unsigned t = __umulhi(f.mul, (unsigned)x);
+  return (int)((t + (((unsigned)x - t) >> f.sh1)) >> f.sh2);
+}
+
+// One side of a stage: shared memory (g == nullptr; offsets into hom_dyn_smem as cpx<T>) or a
+// global tile (element (l, j) at g + l*ls + j*es, offsets below 2^31).
+template <typename T>
+struct Loc {
+  cpx<T>* g;
+  int base;
+  int ls;
+  int es;
+};
+
+// One Stockham stage with radix R over nl lines of length n (p = product of earlier radices).
+// Work items: (line, butterfly); colmajor puts the line index fastest.
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void reg_stage(Loc<T> in, Loc<T> out, int n, int p, int nl,
+                                         bool colmajor, int tw_base, FastDiv fd_m, FastDiv fd_p) {
+  const int m = n / R;
+  const int total = nl * m;
+  const int ts = n / (p * R);
+  // column counts are powers of two except in a ragged last tile
+  const bool nl_pow2 = (nl & (nl - 1)) == 0;
+  const int nl_log = __ffs(nl) - 1;
+  cpx<T>* sm = smem_c<T>();
+  const int istride = m * in.es;
+  const int ostride = p * out.es;
+  for (int w = threadIdx.x; w < total; w += blockDim.x) {
+    int l, i;
+    if (colmajor) {
+      i = nl_pow2 ? (w >> nl_log) : w / nl;
+      l = w - i * nl;
+    } else {
+      l = fdiv(w, fd_m);
+      i = w - l * m;
+    }
+    const int k = i - fdiv(i, fd_p) * p;
+    cpx<T> u[R];
+    const int io = in.base + l * in.ls + i * in.es;
+    if (in.g != nullptr) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) u[r] = in.g[io + r * istride];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) u[r] = sm[io + r * istride];
+    }
+    if (INV) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) u[r].y = -u[r].y;
+    }
+    if (p > 1) {
+      const int step = k * ts;
+#pragma unroll
+      for (int r = 1; r < R; ++r) u[r] = cmul(u[r], sm[tw_base + r * step]);
+    }
+    RegDft<T, R>::run(u);
+    if (INV) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) u[r].y = -u[r].y;
+    }
+    const int oo = out.base + l * out.ls + ((i - k) * R + k) * out.es;
+    if (out.g != nullptr) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) out.g[oo + r * ostride] = u[r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm[oo + r * ostride] = u[r];
+    }
+  }
+}
+
+// Dispatch of one stage on the runtime radix (not inlined: one copy per precision/direction).
+template <typename T, bool INV>
+__device__ __noinline__ void reg_stage_any(int R, Loc<T> in, Loc<T> out, int n, int p, int nl,
+                                           bool colmajor, int tw_base, FastDiv fm, FastDiv fp) {
+  switch (R) {
+    case 3: reg_stage<T, 3, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
+    case 5: reg_stage<T, 5, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
+    case 7: reg_stage<T, 7, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
+    case 9: reg_stage<T, 9, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
+    case 11: reg_stage<T, 11, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
+    case 13: reg_stage<T, 13, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
+    case 15: reg_stage<T, 15, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
+    case 17: reg_stage<T, 17, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
+    case 19: reg_stage<T, 19, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
+    case 21: reg_stage<T, 21, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
+    case 23: reg_stage<T, 23, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
+    case 25: reg_stage<T, 25, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
+    case 27: reg_stage<T, 27, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
+    case 29: reg_stage<T, 29, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
+    case 31: reg_stage<T, 31, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
+    default: break;
+  }
+}
+
+// stage st of plan P
+template <typename T>
+__device__ __forceinline__ void stage_any(bool inv, const AxisPlan* P, int st, Loc<T> in,
+                                          Loc<T> out, int nl, bool colmajor, int tw_base) {
+  if (inv)
+    reg_stage_any<T, true>(P->radix[st], in, out, P->n, P->pprev[st], nl, colmajor, tw_base,
+                           P->fdm[st], P->fdp[st]);
+  else
+    reg_stage_any<T, false>(P->radix[st], in, out, P->n, P->pprev[st], nl, colmajor, tw_base,
+                            P->fdm[st], P->fdp[st]);
+}
+
+// shared-memory location helper
+template <typename T>
+__device__ __forceinline__ Loc<T> sloc(int base, int ls, int es) {
+  return Loc<T>{nullptr, base, ls, es};
+}
+
+// All stages of one axis on nl lines in shared memory (element j of line l at a + l*ls + j*es,
+// a and b element offsets of the two ping-pong buffers); returns the offset of the buffer that
+// holds the natural-order result. Ends with a __syncthreads().
+template <typename T>
+__device__ __forceinline__ int reg_lines(int a, int b, const AxisPlan* P, int nl, int ls, int es,
+                                         bool colmajor, bool inv, int tw_base) {
+  const int nst = P->nst, n = P->n;
+#pragma unroll 1
+  for (int st = 0; st < nst; ++st) {
+    stage_any<T>(inv, P, st, sloc<T>(a, ls, es), sloc<T>(b, ls, es), nl, colmajor, tw_base);
+    __syncthreads();
+    const int t = a;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+// Column transform of a TC-column tile held in shared memory (natural order, at src, pitch
+// TCp); the last stage writes the global tile g (element (c, j) at g + c + j*ges); spare is the
+// ping-pong partner. Ends with a __syncthreads().
+template <typename T>
+__device__ __forceinline__ void reg_columns_out(int src, int spare, cpx<T>* g, int ges, int ncols,
+                                                int TCp, const AxisPlan* P, bool inv,
+                                                int tw_base) {
+  const int nst = P->nst, n = P->n;
+  int a = src, b = spare;
+#pragma unroll 1
+  for (int st = 0; st < nst - 1; ++st) {
+    stage_any<T>(inv, P, st, sloc<T>(a, 1, TCp), sloc<T>(b, 1, TCp), ncols, true, tw_base);
+    __syncthreads();
+    const int t = a;
+    a = b;
+    b = t;
+  }
+  stage_any<T>(inv, P, nst - 1, sloc<T>(a, 1, TCp), Loc<T>{g, 0, 1, ges}, ncols, true, tw_base);
+  __syncthreads();
+}
+
+}  // namespace hom

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -82,28 +83,46 @@ cudaError_t& last_cuda_error() {
 // ---------------------------------------------------------------------------------------
 // planning
 // ---------------------------------------------------------------------------------------
-bool plan_axis(int n, AxisPlan* P) {
+// Radix plan of one axis: the prime factors of n (all <= 31) grouped into register radices of
+// at most rmax (first fit, largest factors first), as few stages as possible.
+bool plan_axis(int n, int rmax, AxisPlan* P) {
   if (n < 3 || n > kMaxAxis || n % 2 == 0) return false;
-  int rem = n, nst = 0;
-  const int order[] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31};
-  for (int R : order) {
+  std::vector<int> primes;
+  int rem = n;
+  for (int R : {31, 29, 23, 19, 17, 13, 11, 7, 5, 3})
     while (rem % R == 0) {
-      if (nst >= kMaxStages) return false;
-      P->radix[nst++] = R;
+      primes.push_back(R);
       rem /= R;
     }
-  }
   if (rem != 1) return false;
-  P->n = n;
-  P->nst = nst;
-  int p = 1;
-  for (int s = 0; s < nst; ++s) {
-    P->pprev[s] = p;
-    p *= P->radix[s];
+  std::vector<int> groups;
+  for (int f : primes) {
+    int best = -1;
+    for (size_t gi = 0; gi < groups.size(); ++gi)
+      if (groups[gi] * f <= rmax && (best < 0 || groups[gi] > groups[best])) best = (int)gi;
+    if (best >= 0) groups[best] *= f;
+    else groups.push_back(f);
   }
-  for (int s = nst; s < kMaxStages; ++s) P->radix[s] = P->pprev[s] = 0;
+  if ((int)groups.size() > kMaxStages) return false;
+  std::sort(groups.begin(), groups.end(), [](int a, int b) { return a > b; });
+  P->n = n;
+  P->nst = (int)groups.size();
+  int p = 1;
+  for (int s = 0; s < kMaxStages; ++s) {
+    if (s < P->nst) {
+      P->radix[s] = groups[s];
+      P->pprev[s] = p;
+      p *= groups[s];
+    } else {
+      P->radix[s] = P->pprev[s] = 0;
+    }
+  }
+  plan_fastdivs(P);
   return true;
 }
+
+// largest register radix per precision (FP64 values take twice the registers)
+template <typename T> constexpr int reg_rmax() { return sizeof(T) == 8 ? 15 : 27; }
 
 template <typename T>
 std::vector<cpx<T>> twiddles(int n) {
@@ -125,17 +144,16 @@ int pick_LB(int n, int ncomp, size_t budget) {
   return LB;
 }
 
+// columns per CTA of a column pass: the widest tile (<= 32 columns, 128-byte rows for FP32 at
+// 16) whose shared-memory buffers fit the budget; odd pitch for conflict-free column access
 template <typename T>
-void pick_TC(int n, int ncols_avail, int nbuf_extra, size_t budget, int* TC, int* TCp, bool proj,
-             int D) {
-  int tc = 16;
+void pick_TC(int n, int nst, size_t budget, int* TC, int* TCp, bool proj, int D) {
+  int tc = 32;
   auto need = [&](int t) {
-    const int tp = t + ((t % 2 == 0) ? 1 : 0);  // odd pitch: conflict-free column access
-    return proj ? Ops<T>::smem_proj(n, D, tp) : Ops<T>::smem_strided(n, tp);
+    const int tp = t + ((t % 2 == 0) ? 1 : 0);
+    return proj ? Ops<T>::smem_proj(n, D, tp) : Ops<T>::smem_strided(n, tp, nst);
   };
   while (tc > 2 && need(tc) > budget) tc /= 2;
-  (void)ncols_avail;
-  (void)nbuf_extra;
   *TC = tc;
   *TCp = tc + ((tc % 2 == 0) ? 1 : 0);
 }
@@ -152,6 +170,7 @@ struct Engine {
   ProjGeom pg{};
   MatView<T> mat{};
   T* field = nullptr;  // MAT_FIELD storage in precision T
+  T* table = nullptr;  // phase table in precision T
   bool ready = false;
 
   int init(int D, const int* n, const int* support, size_t budget) {
@@ -160,7 +179,9 @@ struct Engine {
     for (int a = 0; a < D; ++a) {
       g.n[a] = n[a];
       g.nodes *= n[a];
-      if (!plan_axis(n[a], &plan[a])) return HOM_ERR_INVALID;
+      int rmax = reg_rmax<T>();
+      if (const char* e = getenv(sizeof(T) == 4 ? "HOM_RMAX32" : "HOM_RMAX64")) rmax = atoi(e);
+      if (!plan_axis(n[a], rmax, &plan[a])) return HOM_ERR_INVALID;
     }
     for (int a = D; a < 3; ++a) g.n[a] = 1;
     const int nl = n[D - 1];
@@ -168,9 +189,9 @@ struct Engine {
     g.nlines = g.nodes / nl;
     g.scs = g.nlines * g.nh;
     g.LB = pick_LB<T>(nl, D, budget);
-    if (D == 3) pick_TC<T>(n[1], g.nh, 0, budget, &g.TC1, &g.TC1p, false, D);
-    pick_TC<T>(n[0], (int)std::min<long long>(g.scs / n[0], 1 << 30), 0, budget, &g.TC0, &g.TC0p,
-               true, D);
+    if (D == 3) pick_TC<T>(n[1], plan[1].nst, budget, &g.TC1, &g.TC1p, false, D);
+    pick_TC<T>(n[0], plan[0].nst, budget, &g.TC0, &g.TC0p, true, D);
+    pick_TC<T>(n[0], plan[0].nst, budget, &g.TCs0, &g.TCs0p, false, D);
     g1 = g;
     g1.LB = pick_LB<T>(nl, 1, budget);
     for (int a = 0; a < D; ++a) {
@@ -188,7 +209,8 @@ struct Engine {
     // every pass must fit the per-CTA shared-memory limit
     const size_t cap = (size_t)dynamic_smem_cap();
     if (Ops<T>::smem_line(nl, D, g.LB) > cap || Ops<T>::smem_proj(n[0], D, g.TC0p) > cap ||
-        (D == 3 && Ops<T>::smem_strided(n[1], g.TC1p) > cap))
+        (D == 3 && Ops<T>::smem_strided(n[1], g.TC1p, plan[1].nst) > cap) ||
+        Ops<T>::smem_strided(n[0], g.TCs0p, plan[0].nst) > cap)
       return HOM_ERR_UNSUPPORTED;
     ready = true;
     return HOM_OK;
@@ -201,6 +223,8 @@ struct Engine {
     }
     if (field) cudaFree(field);
     field = nullptr;
+    if (table) cudaFree(table);
+    table = nullptr;
   }
 
   // forward transform of the contiguous axis and the middle axis (D = 3) up to axis 0
@@ -324,12 +348,12 @@ struct hom_problem {
 namespace {
 
 template <typename T>
-MatView<T> make_view(const hom_problem* P, const T* field) {
+MatView<T> make_view(const hom_problem* P, const T* field, const T* table) {
   MatView<T> m{};
   m.kind = P->mat_kind;
   m.ph8 = (P->mat_kind != MAT_FIELD && P->index_bytes == 1) ? (const uint8_t*)P->d_phase : nullptr;
   m.ph16 = (P->mat_kind != MAT_FIELD && P->index_bytes == 2) ? (const uint16_t*)P->d_phase : nullptr;
-  m.table = P->d_table;
+  m.table = table;
   m.field = field;
   return m;
 }
@@ -394,7 +418,10 @@ int check_last() {
   return HOM_OK;
 }
 
-constexpr size_t kSmemBudget = 110 * 1024;  // two CTAs per SM in every pass
+size_t smem_budget() {
+  if (const char* e = getenv("HOM_SMEM_BUDGET_KB")) return (size_t)atoi(e) * 1024;
+  return 110 * 1024;  // two CTAs per SM in every pass
+}
 
 }  // namespace
 
@@ -621,9 +648,9 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
   if (!(P->cA > 0 && P->CA >= P->cA)) { hom_destroy(P); return HOM_ERR_INVALID; }
 
   // ---- plans ----
-  if ((st = P->e64.init(d, P->M, P->N, kSmemBudget)) != HOM_OK) { hom_destroy(P); return st; }
+  if ((st = P->e64.init(d, P->M, P->N, smem_budget())) != HOM_OK) { hom_destroy(P); return st; }
   if (precision == HOM_FP32_REFINED) {
-    if ((st = P->e32.init(d, P->M, P->N, kSmemBudget)) != HOM_OK) { hom_destroy(P); return st; }
+    if ((st = P->e32.init(d, P->M, P->N, smem_budget())) != HOM_OK) { hom_destroy(P); return st; }
   }
 
   // ---- buffers ----
@@ -647,7 +674,7 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
   cudaEventCreate(&P->ev0);
   cudaEventCreate(&P->ev1);
 
-  P->e64.mat = make_view<double>(P, P->e64.field);
+  P->e64.mat = make_view<double>(P, P->e64.field, P->d_table);
 
   // ---- Ga: A_M^k = sum_n omega_M^{kn} A^(n) (eq. (Ga_exact_integration)) ----
   if (A->kind == HOM_A_FOURIER) {
@@ -673,9 +700,18 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
       hom_destroy(P);
       return HOM_ERR_CUDA;
     }
-    P->e64.mat = make_view<double>(P, P->e64.field);
+    P->e64.mat = make_view<double>(P, P->e64.field, P->d_table);
   }
   if (precision == HOM_FP32_REFINED) {
+    if (P->d_table) {
+      const size_t ntab = (P->mat_kind == MAT_PHASE_ISO) ? (size_t)P->nphase : (size_t)P->nphase * d * d;
+      std::vector<double> h(ntab);
+      std::vector<float> hf(ntab);
+      cudaMemcpy(h.data(), P->d_table, sizeof(double) * ntab, cudaMemcpyDeviceToHost);
+      for (size_t i = 0; i < ntab; ++i) hf[i] = (float)h[i];
+      if ((st = alloc((void**)&P->e32.table, sizeof(float) * ntab)) != HOM_OK) { hom_destroy(P); return st; }
+      cudaMemcpy(P->e32.table, hf.data(), sizeof(float) * ntab, cudaMemcpyHostToDevice);
+    }
     if (P->mat_kind == MAT_FIELD) {
       if ((st = alloc((void**)&P->e32.field, sizeof(float) * nodes)) != HOM_OK) { hom_destroy(P); return st; }
       std::vector<double> h(nodes);
@@ -684,7 +720,7 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
       for (long long g = 0; g < nodes; ++g) hf[g] = (float)h[g];
       cudaMemcpy(P->e32.field, hf.data(), sizeof(float) * nodes, cudaMemcpyHostToDevice);
     }
-    P->e32.mat = make_view<float>(P, P->e32.field);
+    P->e32.mat = make_view<float>(P, P->e32.field, P->e32.table);
   }
   if (check_last() != HOM_OK) { hom_destroy(P); return HOM_ERR_CUDA; }
   *out = P;

@@ -9,6 +9,7 @@
 // library holds until the process exits. The caller passes inputs and outputs only.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -61,25 +62,35 @@ int static_setup(int dev, unsigned char** base) {
   return HOM_OK;
 }
 
+// radix plan of one axis: prime factors (<= 31) grouped first-fit into register radices <= 15
 bool plan_static_axis(int n, AxisPlan* P) {
   if (n < 3 || n > kMaxAxis || n % 2 == 0) return false;
-  int rem = n, nst = 0;
-  for (int R : {3, 5, 7, 11, 13, 17, 19, 23, 29, 31}) {
+  int groups[kMaxStages];
+  int ng = 0, rem = n;
+  for (int R : {31, 29, 23, 19, 17, 13, 11, 7, 5, 3})
     while (rem % R == 0) {
-      if (nst >= kMaxStages) return false;
-      P->radix[nst++] = R;
       rem /= R;
+      int best = -1;
+      for (int gi = 0; gi < ng; ++gi)
+        if (groups[gi] * R <= 15 && (best < 0 || groups[gi] > groups[best])) best = gi;
+      if (best >= 0) {
+        groups[best] *= R;
+      } else {
+        if (ng >= kMaxStages) return false;
+        groups[ng++] = R;
+      }
     }
-  }
   if (rem != 1) return false;
+  std::sort(groups, groups + ng, [](int a, int b) { return a > b; });
   P->n = n;
-  P->nst = nst;
+  P->nst = ng;
   int p = 1;
   for (int s = 0; s < kMaxStages; ++s) {
-    P->pprev[s] = s < nst ? p : 0;
-    if (s < nst) p *= P->radix[s];
-    else P->radix[s] = 0;
+    P->pprev[s] = s < ng ? p : 0;
+    P->radix[s] = s < ng ? groups[s] : 0;
+    if (s < ng) p *= groups[s];
   }
+  plan_fastdivs(P);
   return true;
 }
 
@@ -178,21 +189,22 @@ extern "C" int hom_apply_static(int d, const int* N, const void* phase_dev, int 
   const size_t budget = 110 * 1024;
   g.LB = 16;
   while (g.LB > 2 && Ops<double>::smem_line(nl, d, g.LB) > budget) g.LB -= 2;
-  auto tc_for = [&](int n, bool proj, int* TC, int* TCp) {
-    int tc = 16;
+  auto tc_for = [&](int n, int nst, bool proj, int* TC, int* TCp) {
+    int tc = 32;
     auto need = [&](int t) {
       const int tp = t + (t % 2 == 0 ? 1 : 0);
-      return proj ? Ops<double>::smem_proj(n, d, tp) : Ops<double>::smem_strided(n, tp);
+      return proj ? Ops<double>::smem_proj(n, d, tp) : Ops<double>::smem_strided(n, tp, nst);
     };
     while (tc > 2 && need(tc) > budget) tc /= 2;
     *TC = tc;
     *TCp = tc + (tc % 2 == 0 ? 1 : 0);
   };
-  if (d == 3) tc_for(N[1], false, &g.TC1, &g.TC1p);
-  tc_for(N[0], true, &g.TC0, &g.TC0p);
+  if (d == 3) tc_for(N[1], plan[1].nst, false, &g.TC1, &g.TC1p);
+  tc_for(N[0], plan[0].nst, true, &g.TC0, &g.TC0p);
+  tc_for(N[0], plan[0].nst, false, &g.TCs0, &g.TCs0p);
   const size_t cap = (size_t)dynamic_smem_cap();
   if (Ops<double>::smem_line(nl, d, g.LB) > cap || Ops<double>::smem_proj(N[0], d, g.TC0p) > cap ||
-      (d == 3 && Ops<double>::smem_strided(N[1], g.TC1p) > cap))
+      (d == 3 && Ops<double>::smem_strided(N[1], g.TC1p, plan[1].nst) > cap))
     return HOM_ERR_UNSUPPORTED;
 
   // ---- twiddles and table into the scratch (ordered on the caller's stream) ----

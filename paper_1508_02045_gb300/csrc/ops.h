@@ -21,6 +21,7 @@ struct PassGeom {
   long long scs;      // spectrum component stride: nlines * nh
   int LB;             // lines per CTA in the line passes (even)
   int TC1, TC1p;      // strided pass along axis 1 (D = 3): columns per CTA, padded pitch
+  int TCs0, TCs0p;    // plain strided pass along axis 0 (prolongation, Ga assembly)
   int TC0, TC0p;      // axis-0 passes (projection / plain strided): columns per CTA, pitch
 };
 
@@ -28,7 +29,7 @@ template <typename T>
 struct Ops {
   static cudaError_t upload_constants();
   static size_t smem_line(int n, int ncomp, int LB);
-  static size_t smem_strided(int n, int TCp);
+  static size_t smem_strided(int n, int TCp, int nst);
   static size_t smem_proj(int n, int D, int TCp);
   static cudaError_t prepare(int maxD);  // raise dynamic shared memory limits
 

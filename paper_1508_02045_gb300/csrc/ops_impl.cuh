@@ -9,11 +9,12 @@ namespace hom {
 
 template <typename T>
 cudaError_t Ops<T>::upload_constants() {
-  std::vector<double> cd(kDftTable), sd(kDftTable);
-  std::vector<float> cf(kDftTable), sf(kDftTable);
+  // cos / sin (2 pi j / R) for every odd register radix R <= 31, from long double
+  std::vector<double> cd(kRegTable), sd(kRegTable);
+  std::vector<float> cf(kRegTable), sf(kRegTable);
   const long double twopi = 6.283185307179586476925286766559005768L;
-  for (int i = 0; i < kNumRadices; ++i) {
-    const int R = kRadices[i], off = radix_offset(R);
+  for (int R = 3; R <= kRegMax; R += 2) {
+    const int off = reg_offset(R);
     for (int j = 0; j < R; ++j) {
       const long double t = twopi * (long double)j / (long double)R;
       cd[off + j] = (double)cosl(t);
@@ -23,19 +24,21 @@ cudaError_t Ops<T>::upload_constants() {
     }
   }
   cudaError_t e;
-  if ((e = cudaMemcpyToSymbol(c_cos_d, cd.data(), sizeof(double) * kDftTable)) != cudaSuccess) return e;
-  if ((e = cudaMemcpyToSymbol(c_sin_d, sd.data(), sizeof(double) * kDftTable)) != cudaSuccess) return e;
-  if ((e = cudaMemcpyToSymbol(c_cos_f, cf.data(), sizeof(float) * kDftTable)) != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(c_sin_f, sf.data(), sizeof(float) * kDftTable);
+  if ((e = cudaMemcpyToSymbol(c_rcos_d, cd.data(), sizeof(double) * kRegTable)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_rsin_d, sd.data(), sizeof(double) * kRegTable)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_rcos_f, cf.data(), sizeof(float) * kRegTable)) != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_rsin_f, sf.data(), sizeof(float) * kRegTable);
 }
 
 template <typename T>
 size_t Ops<T>::smem_line(int n, int ncomp, int LB) {
-  return sizeof(cpx<T>) * ((size_t)n + 2 * (size_t)ncomp * (LB / 2) * n);
+  const size_t nlc = (size_t)ncomp * (LB / 2);
+  return sizeof(cpx<T>) * ((size_t)n + nlc * n + nlc * (n + 1));
 }
 template <typename T>
-size_t Ops<T>::smem_strided(int n, int TCp) {
-  return sizeof(cpx<T>) * ((size_t)n + 2 * (size_t)n * TCp);
+size_t Ops<T>::smem_strided(int n, int TCp, int nst) {
+  const size_t nbuf = nst >= 2 ? 2 : 1;
+  return sizeof(cpx<T>) * ((size_t)n + nbuf * (size_t)n * TCp);
 }
 template <typename T>
 size_t Ops<T>::smem_proj(int n, int D, int TCp) {
@@ -136,11 +139,11 @@ void Ops<T>::strided(const PassGeom& g, int axis, int inv, cpx<T>* S, const Axis
     es = C;
     bs = g.scs;
     batches = ncomp;
-    TC = g.TC0;
-    TCp = g.TC0p;
+    TC = g.TCs0;
+    TCp = g.TCs0p;
   }
   dim3 grid((unsigned)((C + TC - 1) / TC), (unsigned)batches);
-  const size_t sm = smem_strided(P.n, TCp);
+  const size_t sm = smem_strided(P.n, TCp, P.nst);
   const bool prof = profiling();
   if (prof) prof_mark(KIND_STRIDED, st, true);
   k_strided<T><<<grid, kThreads, sm, st>>>(S, P, tw, C, es, bs, TC, TCp, inv, sc);

@@ -18,7 +18,7 @@
 // to finish, which then runs the scalar part of the algorithm step ("finisher").
 #pragma once
 #include "common.cuh"
-#include "fft_engine.cuh"
+#include "fft_reg.cuh"
 
 namespace hom {
 
@@ -95,44 +95,84 @@ __device__ __forceinline__ void mat_apply(const MatView<T>& m, long long g, cons
 #pragma unroll
     for (int i = 0; i < D; ++i) v[i] = a * w[i];
   } else if (m.kind == MAT_PHASE_ISO) {
-    const T a = (T)__ldg(&m.table[phase_at(m, g)]);
+    const T a = __ldg(&m.table[phase_at(m, g)]);
 #pragma unroll
     for (int i = 0; i < D; ++i) v[i] = a * w[i];
   } else {
-    const double* t = m.table + phase_at(m, g) * D * D;
+    const T* t = m.table + phase_at(m, g) * D * D;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       T s = 0;
 #pragma unroll
-      for (int j = 0; j < D; ++j) s = fma((T)__ldg(&t[i * D + j]), w[j], s);
+      for (int j = 0; j < D; ++j) s = fma(__ldg(&t[i * D + j]), w[j], s);
       v[i] = s;
     }
   }
 }
 
-// v = (A(x^g) + omega I)^{-1} w
+// the coefficient of node g in two steps, so that the loads of a batch of nodes can be issued
+// before any of them is used: fetch (phase index or field value), then evaluate v = A w
+template <typename T>
+__device__ __forceinline__ T mat_fetch(const MatView<T>& m, long long g) {
+  if (m.kind == MAT_FIELD) return m.field[g];
+  return (T)phase_at(m, g);
+}
+
 template <typename T, int D>
-__device__ __forceinline__ void mat_shift_solve(const MatView<T>& m, long long g, T omega,
-                                                const T (&w)[D], T (&v)[D]) {
+__device__ __forceinline__ void mat_eval(const MatView<T>& m, T sample, const T (&w)[D],
+                                         T (&v)[D]) {
   if (m.kind == MAT_FIELD || m.kind == MAT_PHASE_ISO) {
-    const T a = (m.kind == MAT_FIELD) ? m.field[g] : (T)__ldg(&m.table[phase_at(m, g)]);
+    const T a = (m.kind == MAT_FIELD) ? sample : __ldg(&m.table[(int)sample]);
+#pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = a * w[i];
+  } else {
+    const T* t = m.table + (int)sample * D * D;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      T s = 0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) s = fma(__ldg(&t[i * D + j]), w[j], s);
+      v[i] = s;
+    }
+  }
+}
+
+// asynchronous global -> shared copies of one complex element (LDGSTS), and the wait
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(cpx<T>* dst, const cpx<T>* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if (sizeof(cpx<T>) == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// (A + omega I)^{-1} w with the coefficient given by a fetched sample (see mat_fetch)
+template <typename T, int D>
+__device__ __forceinline__ void mat_shift_solve_s(const MatView<T>& m, T sample, T omega,
+                                                  const T (&w)[D], T (&v)[D]) {
+  if (m.kind == MAT_FIELD || m.kind == MAT_PHASE_ISO) {
+    const T a = (m.kind == MAT_FIELD) ? sample : __ldg(&m.table[(int)sample]);
     const T inv = (T)1 / (a + omega);
 #pragma unroll
     for (int i = 0; i < D; ++i) v[i] = w[i] * inv;
     return;
   }
-  const double* t = m.table + phase_at(m, g) * D * D;
+  const int ph = (int)sample;
+  const T* t = m.table + ph * D * D;
   T M[D][D];
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
-    for (int j = 0; j < D; ++j) M[i][j] = (T)__ldg(&t[i * D + j]) + (i == j ? omega : (T)0);
+    for (int j = 0; j < D; ++j) M[i][j] = __ldg(&t[i * D + j]) + (i == j ? omega : (T)0);
   if (D == 2) {
     const T det = M[0][0] * M[1][1] - M[0][1] * M[1][0];
     v[0] = (M[1][1] * w[0] - M[0][1] * w[1]) / det;
     v[1] = (M[0][0] * w[1] - M[1][0] * w[0]) / det;
   } else {
-    // Cramer's rule with the cofactor (adjugate) matrix of a 3 x 3 system
     const T c00 = M[1][1] * M[2][2] - M[1][2] * M[2][1];
     const T c01 = M[1][2] * M[2][0] - M[1][0] * M[2][2];
     const T c02 = M[1][0] * M[2][1] - M[1][1] * M[2][0];
@@ -143,7 +183,6 @@ __device__ __forceinline__ void mat_shift_solve(const MatView<T>& m, long long g
     const T c20 = M[0][1] * M[1][2] - M[0][2] * M[1][1];
     const T c21 = M[0][2] * M[1][0] - M[0][0] * M[1][2];
     const T c22 = M[0][0] * M[1][1] - M[0][1] * M[1][0];
-    // inverse = adj / det, adj = cofactor^T
     v[0] = (c00 * w[0] + c10 * w[1] + c20 * w[2]) / det;
     v[1] = (c01 * w[0] + c11 * w[1] + c21 * w[2]) / det;
     v[2] = (c02 * w[0] + c12 * w[1] + c22 * w[2]) / det;
@@ -178,16 +217,14 @@ k_line_fwd(Fields<T> f, cpx<T>* __restrict__ S, AxisPlan P, const cpx<T>* __rest
            int ncomp, long long nlines, int LB, long long scs, MatView<T> mat,
            const Scalars* __restrict__ sc, OpArgs args) {
   if (sc != nullptr && sc->done) return;
-  extern __shared__ __align__(16) unsigned char smem[];
   const int n = P.n, nh = (n + 1) / 2;
   const int half = LB / 2;
   const int nlc = ncomp * half;
-  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem);
-  cpx<T>* b0 = tw + n;
-  cpx<T>* b1 = b0 + (size_t)nlc * n;
+  cpx<T>* sm = smem_c<T>();
+  const int b0 = n, b1 = n + nlc * n;  // element offsets; twiddles at 0
   __shared__ AxisPlan Ps;
   if (threadIdx.x == 0) Ps = P;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = twg[i];
   const long long l0 = (long long)blockIdx.x * LB;
   const double* Es = sc != nullptr ? sc->E : args.E;
   const T E[3] = {(T)Es[0], (T)Es[1], (T)Es[2]};
@@ -196,52 +233,75 @@ k_line_fwd(Fields<T> f, cpx<T>* __restrict__ S, AxisPlan P, const cpx<T>* __rest
   // Richardson keeps x_m and x_{m-1} in a buffer pair; the operand is the current one
   const T* xin = f.xin;
   if (f.x != nullptr && sc != nullptr) xin = f.x + (sc->which ? D * f.cs : 0);
-  for (int idx = threadIdx.x; idx < LB * n; idx += blockDim.x) {
-    const int ll = idx / n, j = idx - ll * n;
-    const long long l = l0 + ll;
-    T v[D];
+  // batches of K nodes per thread: every global load of a batch is issued before any use
+  constexpr int K = sizeof(T) == 4 ? 8 : 4;
+  const T* __restrict__ pin = f.p;
+  for (int base = 0; base < LB * n; base += K * blockDim.x) {
+    T xv[K][D], pv[K][D], ms[K];
 #pragma unroll
-    for (int a = 0; a < D; ++a) v[a] = 0;
-    if (l < nlines) {
+    for (int k = 0; k < K; ++k) {
+      const int idx = base + k * blockDim.x + threadIdx.x;
+      const int ll = idx / n, j = idx - ll * n;
+      const long long l = l0 + ll;
+      const bool ok = idx < LB * n && l < nlines;
       const long long g = l * n + j;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        xv[k][a] = (ok && a < ncomp) ? xin[a * f.cs + g] : (T)0;
+        pv[k][a] = (PRE == PRE_CG && ok) ? pin[a * f.cs + g] : (T)0;
+      }
+      ms[k] = (PRE != PRE_IDENT && ok) ? mat_fetch<T>(mat, g) : (T)0;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int idx = base + k * blockDim.x + threadIdx.x;
+      if (idx >= LB * n) continue;
+      const int ll = idx / n, j = idx - ll * n;
+      const long long l = l0 + ll;
+      const bool ok = l < nlines;
+      const long long g = l * n + j;
+      T v[D];
       if (PRE == PRE_IDENT) {
-        for (int a = 0; a < ncomp; ++a) v[a] = xin[a * f.cs + g];
+#pragma unroll
+        for (int a = 0; a < D; ++a) v[a] = xv[k][a];
       } else {
         T w[D];
-        if (PRE == PRE_CG) {
 #pragma unroll
-          for (int a = 0; a < D; ++a) {
-            const T pn = xin[a * f.cs + g] + beta * f.p[a * f.cs + g];
-            f.p[a * f.cs + g] = pn;
-            w[a] = pn;
+        for (int a = 0; a < D; ++a) {
+          if (PRE == PRE_CG) {
+            w[a] = xv[k][a] + beta * pv[k][a];
+            if (ok) f.p[a * f.cs + g] = w[a];
+          } else {
+            w[a] = xv[k][a] + (PRE == PRE_AFFINE && ok ? E[a] : (T)0);
           }
-        } else {
-#pragma unroll
-          for (int a = 0; a < D; ++a) w[a] = xin[a * f.cs + g] + (PRE == PRE_AFFINE ? E[a] : (T)0);
         }
-        mat_apply<T, D>(mat, g, w, v);
+        mat_eval<T, D>(mat, ms[k], w, v);
         if (PRE == PRE_EM) {
 #pragma unroll
           for (int a = 0; a < D; ++a) v[a] -= omega * w[a];
         }
-      }
-    }
+        if (!ok) {
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      if (a < ncomp) {
-        cpx<T>* line = b0 + (size_t)(a * half + (ll >> 1)) * n;
-        if (ll & 1) line[j].y = v[a];
-        else line[j].x = v[a];
+          for (int a = 0; a < D; ++a) v[a] = 0;
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        if (a < ncomp) {
+          cpx<T>& e = sm[b0 + (a * half + (ll >> 1)) * n + j];
+          if (ll & 1) e.y = v[a];
+          else e.x = v[a];
+        }
       }
     }
   }
   __syncthreads();
-  cpx<T>* res = fft_lines<T>(b0, b1, &Ps, nlc, n, 1, false, false, tw);
+  const int res = reg_lines<T>(b0, b1, &Ps, nlc, n, 1, false, false, 0);
   for (int idx = threadIdx.x; idx < nlc * nh; idx += blockDim.x) {
     const int lc = idx / nh, k = idx - lc * nh;
     const int a = lc / half, pr = lc - a * half;
-    const cpx<T> zk = res[(size_t)lc * n + k];
-    const cpx<T> zm = res[(size_t)lc * n + (k ? n - k : 0)];
+    const cpx<T> zk = sm[res + lc * n + k];
+    const cpx<T> zm = sm[res + lc * n + (k ? n - k : 0)];
     cpx<T> A, B;
     A.x = (T)0.5 * (zk.x + zm.x);
     A.y = (T)0.5 * (zk.y - zm.y);
@@ -261,27 +321,24 @@ __global__ void __launch_bounds__(kThreads, 2)
 k_strided(cpx<T>* __restrict__ S, AxisPlan P, const cpx<T>* __restrict__ twg, long long C,
           long long es, long long bs, int TC, int TCp, int inv, const Scalars* __restrict__ sc) {
   if (sc != nullptr && sc->done) return;
-  extern __shared__ __align__(16) unsigned char smem[];
   const int n = P.n;
-  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem);
-  cpx<T>* b0 = tw + n;
-  cpx<T>* b1 = b0 + (size_t)n * TCp;
+  cpx<T>* sm = smem_c<T>();
+  const int b0 = n, b1 = n + n * TCp;
   __shared__ AxisPlan Ps;
   if (threadIdx.x == 0) Ps = P;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = twg[i];
   const long long c0 = (long long)blockIdx.x * TC;
+  const int ncols = (int)min((long long)TC, C - c0);
   cpx<T>* base = S + (long long)blockIdx.y * bs + c0;
-  const cpx<T> zero = {0, 0};
-  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
-    const int j = idx / TC, c = idx - j * TC;
-    b0[j * TCp + c] = (c0 + c < C) ? base[j * es + c] : zero;
+  const int ges = (int)es;
+  // stage the whole tile with asynchronous copies (all rows in flight at once)
+  for (int idx = threadIdx.x; idx < n * ncols; idx += blockDim.x) {
+    const int j = idx / ncols, c = idx - j * ncols;
+    cp_async_elem<T>(sm + b0 + j * TCp + c, base + j * ges + c);
   }
+  cp_async_wait_all();
   __syncthreads();
-  cpx<T>* res = fft_lines<T>(b0, b1, &Ps, TC, 1, TCp, true, inv != 0, tw);
-  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
-    const int j = idx / TC, c = idx - j * TC;
-    if (c0 + c < C) base[j * es + c] = res[j * TCp + c];
-  }
+  reg_columns_out<T>(b0, b1, base, ges, ncols, TCp, &Ps, inv != 0, 0);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -301,38 +358,39 @@ __global__ void __launch_bounds__(kThreads, 2)
 k_proj(cpx<T>* __restrict__ S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC,
        int TCp, const Scalars* __restrict__ sc) {
   if (sc != nullptr && sc->done) return;
-  extern __shared__ __align__(16) unsigned char smem[];
   const int n = P.n;
-  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem);
-  cpx<T>* buf[D + 1];
-  buf[0] = tw + n;
+  cpx<T>* sm = smem_c<T>();
+  int buf[D + 1];
 #pragma unroll
-  for (int a = 1; a <= D; ++a) buf[a] = buf[a - 1] + (size_t)n * TCp;
+  for (int a = 0; a <= D; ++a) buf[a] = n + a * n * TCp;
   __shared__ AxisPlan Ps;
   if (threadIdx.x == 0) Ps = P;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = twg[i];
   const long long c0 = (long long)blockIdx.x * TC;
-  const long long es = g.C;
-  const cpx<T> zero = {0, 0};
-  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
-    const int j = idx / TC, c = idx - j * TC;
-    const bool ok = c0 + c < g.C;
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-      buf[a][j * TCp + c] = ok ? S[a * g.cs + j * es + c0 + c] : zero;
+  const int es = (int)g.C;
+  const int ncols = (int)min((long long)TC, g.C - c0);
+  // stage the tiles of all components with asynchronous copies
+  for (int idx = threadIdx.x; idx < D * n * ncols; idx += blockDim.x) {
+    const int a = idx / (n * ncols);
+    const int rem = idx - a * n * ncols;
+    const int j = rem / ncols, c = rem - j * ncols;
+    cp_async_elem<T>(sm + n + a * n * TCp + j * TCp + c, S + a * g.cs + c0 + j * es + c);
   }
+  cp_async_wait_all();
   __syncthreads();
-  cpx<T>* spare = buf[D];
+  int spare = buf[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    cpx<T>* res = fft_lines<T>(buf[a], spare, &Ps, TC, 1, TCp, true, false, tw);
-    if (res != buf[a]) { spare = buf[a]; buf[a] = res; }
+    const int res = reg_lines<T>(buf[a], spare, &Ps, ncols, 1, TCp, true, false, 0);
+    if (res != buf[a]) {
+      spare = buf[a];
+      buf[a] = res;
+    }
   }
   const T scale = (T)g.scale;
-  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
-    const int j = idx / TC, c = idx - j * TC;
+  for (int idx = threadIdx.x; idx < n * ncols; idx += blockDim.x) {
+    const int j = idx / ncols, c = idx - j * ncols;
     const long long cc = c0 + c;
-    if (cc >= g.C) continue;
     int k[3];
     k[0] = (j <= (n - 1) / 2) ? j : j - n;
     if (D == 3) {
@@ -344,15 +402,15 @@ k_proj(cpx<T>* __restrict__ S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjG
       k[2] = 0;
     }
     bool inside = true;
-    long long kk = 0;
+    int kk = 0;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       inside = inside && (abs(k[a]) <= g.hw[a]);
-      kk += (long long)k[a] * k[a];
+      kk += k[a] * k[a];
     }
     cpx<T> v[D];
 #pragma unroll
-    for (int a = 0; a < D; ++a) v[a] = buf[a][j * TCp + c];
+    for (int a = 0; a < D; ++a) v[a] = sm[buf[a] + j * TCp + c];
     cpx<T> kv = {0, 0};
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -372,22 +430,13 @@ k_proj(cpx<T>* __restrict__ S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjG
         o.x = fma((T)(-2 * k[a]), kv.x, scale * v[a].x);
         o.y = fma((T)(-2 * k[a]), kv.y, scale * v[a].y);
       }
-      buf[a][j * TCp + c] = o;
+      sm[buf[a] + j * TCp + c] = o;
     }
   }
   __syncthreads();
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    cpx<T>* res = fft_lines<T>(buf[a], spare, &Ps, TC, 1, TCp, true, true, tw);
-    if (res != buf[a]) { spare = buf[a]; buf[a] = res; }
-  }
-  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
-    const int j = idx / TC, c = idx - j * TC;
-    if (c0 + c < g.C) {
-#pragma unroll
-      for (int a = 0; a < D; ++a) S[a * g.cs + j * es + c0 + c] = buf[a][j * TCp + c];
-    }
-  }
+  for (int a = 0; a < D; ++a)
+    reg_columns_out<T>(buf[a], spare, S + a * g.cs + c0, es, ncols, TCp, &Ps, true, 0);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -399,111 +448,139 @@ k_line_inv(const cpx<T>* __restrict__ S, Fields<T> f, AxisPlan P, const cpx<T>* 
            int ncomp, long long nlines, int LB, long long scs, MatView<T> mat, Scalars* sc,
            OpArgs args, double* partials, unsigned* counter, int negate) {
   if (sc != nullptr && sc->done) return;
-  extern __shared__ __align__(16) unsigned char smem[];
   const int n = P.n, nh = (n + 1) / 2;
   const int half = LB / 2;
   const int nlc = ncomp * half;
-  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem);
-  cpx<T>* b0 = tw + n;
-  cpx<T>* b1 = b0 + (size_t)nlc * n;
+  cpx<T>* sm = smem_c<T>();
+  const int b0 = n, b1 = n + nlc * n;  // b1 holds nlc (n + 1): staged half spectra, ping-pong
   __shared__ AxisPlan Ps;
   if (threadIdx.x == 0) Ps = P;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = twg[i];
   const long long l0 = (long long)blockIdx.x * LB;
   const cpx<T> zero = {0, 0};
+  // stage the half spectra of the CTA's lines (contiguous per line) asynchronously
+  for (int idx = threadIdx.x; idx < ncomp * LB * nh; idx += blockDim.x) {
+    const int al = idx / nh, k = idx - al * nh;
+    const int a = al / LB, ll = al - a * LB;
+    if (l0 + ll < nlines) cp_async_elem<T>(sm + b1 + idx, S + a * scs + (l0 + ll) * nh + k);
+    else sm[b1 + idx] = zero;
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // pack two Hermitian half spectra (lines 2 pr, 2 pr + 1) into one complex line
   for (int idx = threadIdx.x; idx < nlc * nh; idx += blockDim.x) {
     const int lc = idx / nh, k = idx - lc * nh;
     const int a = lc / half, pr = lc - a * half;
-    const long long la = l0 + 2 * pr;
-    const cpx<T> A = (la < nlines) ? S[a * scs + la * nh + k] : zero;
-    const cpx<T> B = (la + 1 < nlines) ? S[a * scs + (la + 1) * nh + k] : zero;
-    cpx<T>* line = b0 + (size_t)lc * n;
+    const cpx<T> A = sm[b1 + (a * LB + 2 * pr) * nh + k];
+    const cpx<T> B = sm[b1 + (a * LB + 2 * pr + 1) * nh + k];
+    const int line = b0 + lc * n;
     if (k == 0) {
-      line[0].x = A.x;
-      line[0].y = B.x;
+      sm[line].x = A.x;
+      sm[line].y = B.x;
     } else {
-      line[k].x = A.x - B.y;
-      line[k].y = A.y + B.x;
-      line[n - k].x = A.x + B.y;
-      line[n - k].y = B.x - A.y;
+      sm[line + k].x = A.x - B.y;
+      sm[line + k].y = A.y + B.x;
+      sm[line + n - k].x = A.x + B.y;
+      sm[line + n - k].y = B.x - A.y;
     }
   }
   __syncthreads();
-  cpx<T>* res = fft_lines<T>(b0, b1, &Ps, nlc, n, 1, false, true, tw);
+  const int res = reg_lines<T>(b0, b1, &Ps, nlc, n, 1, false, true, 0);
 
-  // post-operator
+  // post-operator, in batches of K nodes whose operands are loaded before any use
   const double* Es = sc != nullptr ? sc->E : args.E;
   const T E[3] = {(T)Es[0], (T)Es[1], (T)Es[2]};
   const T omega = (T)(sc != nullptr ? sc->omega : args.omega);
   const T alpha = sc != nullptr ? (T)sc->alpha : (T)0;
   const T beta = sc != nullptr ? (T)sc->beta : (T)0;
   const int which = sc != nullptr ? sc->which : 0;
-  double acc[1] = {0.0};
+  DotAcc<T> dacc;
   const long long cs = f.cs;
-  for (int idx = threadIdx.x; idx < LB * n; idx += blockDim.x) {
-    const int ll = idx / n, j = idx - ll * n;
-    const long long l = l0 + ll;
-    if (l >= nlines) continue;
-    const long long g = l * n + j;
-    T y[D];
+  const T* xc = (POST == POST_RICH) ? f.x + (which ? D * cs : 0) : f.x;
+  T* xn = (POST == POST_RICH) ? f.x + (which ? 0 : D * cs) : f.x;
+  constexpr int K = sizeof(T) == 4 ? 4 : 2;
+  for (int base = 0; base < LB * n; base += K * blockDim.x) {
+    T o1[K][D], o2[K][D], o3[K][D], ms[K];
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      if (a < ncomp) {
-        const cpx<T> z = res[(size_t)(a * half + (ll >> 1)) * n + j];
-        y[a] = (ll & 1) ? z.y : z.x;
-      } else {
-        y[a] = 0;
+    for (int k = 0; k < K; ++k) {
+      const int idx = base + k * blockDim.x + threadIdx.x;
+      const int ll = idx / n, j = idx - ll * n;
+      const bool ok = idx < LB * n && l0 + ll < nlines;
+      const long long g = (l0 + ll) * n + j;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        o1[k][a] = (ok && (POST == POST_RICH || POST == POST_CHEB || POST == POST_EM || POST == POST_ADD))
+                       ? xc[a * cs + g] : (T)0;
+        o2[k][a] = (ok && (POST == POST_CG || POST == POST_CHEB)) ? f.p[a * cs + g] : (T)0;
+        o3[k][a] = (ok && POST == POST_CHEB) ? f.r[a * cs + g] : (T)0;
       }
+      ms[k] = (ok && POST == POST_EM) ? mat_fetch<T>(mat, g) : (T)0;
     }
-    if (POST == POST_STORE) {
-      for (int a = 0; a < ncomp; ++a) {
-        const T o = negate ? -y[a] : y[a];
-        f.out[a * cs + g] = o;
-        if (f.r) f.r[a * cs + g] = o;
-        if (f.p) f.p[a * cs + g] = o;
-        acc[0] += (double)y[a] * (double)y[a];
-      }
-    } else if (POST == POST_RICH) {
-      const T* xc = f.x + (which ? D * cs : 0);
-      T* xn = f.x + (which ? 0 : D * cs);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int idx = base + k * blockDim.x + threadIdx.x;
+      const int ll = idx / n, j = idx - ll * n;
+      if (idx >= LB * n || l0 + ll >= nlines) continue;
+      const long long g = (l0 + ll) * n + j;
+      T y[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        xn[a * cs + g] = xc[a * cs + g] - omega * y[a];
-        acc[0] += (double)y[a] * (double)y[a];
+        if (a < ncomp) {
+          const cpx<T> z = sm[res + (a * half + (ll >> 1)) * n + j];
+          y[a] = (ll & 1) ? z.y : z.x;
+        } else {
+          y[a] = 0;
+        }
       }
-    } else if (POST == POST_CG) {
+      if (POST == POST_STORE) {
+        for (int a = 0; a < ncomp; ++a) {
+          const T o = negate ? -y[a] : y[a];
+          f.out[a * cs + g] = o;
+          if (f.r) f.r[a * cs + g] = o;
+          if (f.p) f.p[a * cs + g] = o;
+          dacc.add(y[a], y[a]);
+        }
+      } else if (POST == POST_RICH) {
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        f.out[a * cs + g] = y[a];
-        acc[0] += (double)y[a] * (double)f.p[a * cs + g];
-      }
-    } else if (POST == POST_CHEB) {
+        for (int a = 0; a < D; ++a) {
+          xn[a * cs + g] = o1[k][a] - omega * y[a];
+          dacc.add(y[a], y[a]);
+        }
+      } else if (POST == POST_CG) {
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const T pv = f.p[a * cs + g];
-        const T rn = f.r[a * cs + g] - alpha * y[a];
-        f.r[a * cs + g] = rn;
-        f.x[a * cs + g] += alpha * pv;
-        f.p[a * cs + g] = rn - beta * pv;
-        acc[0] += (double)rn * (double)rn;
-      }
-    } else if (POST == POST_ADD) {
+        for (int a = 0; a < D; ++a) {
+          f.out[a * cs + g] = y[a];
+          dacc.add(y[a], o2[k][a]);
+        }
+      } else if (POST == POST_CHEB) {
 #pragma unroll
-      for (int a = 0; a < D; ++a) f.x[a * cs + g] += y[a];
-    } else if (POST == POST_EM) {
-      T w[D], xn[D];
+        for (int a = 0; a < D; ++a) {
+          const T pv = o2[k][a];
+          const T rn = o3[k][a] - alpha * y[a];
+          f.r[a * cs + g] = rn;
+          f.x[a * cs + g] = o1[k][a] + alpha * pv;
+          f.p[a * cs + g] = rn - beta * pv;
+          dacc.add(rn, rn);
+        }
+      } else if (POST == POST_ADD) {
 #pragma unroll
-      for (int a = 0; a < D; ++a) w[a] = y[a] + (T)2 * omega * E[a];
-      mat_shift_solve<T, D>(mat, g, omega, w, xn);
+        for (int a = 0; a < D; ++a) f.x[a * cs + g] = o1[k][a] + y[a];
+      } else if (POST == POST_EM) {
+        T w[D], xv[D];
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const T dx = xn[a] - f.x[a * cs + g];
-        f.x[a * cs + g] = xn[a];
-        acc[0] += (double)dx * (double)dx;
+        for (int a = 0; a < D; ++a) w[a] = y[a] + (T)2 * omega * E[a];
+        mat_shift_solve_s<T, D>(mat, ms[k], omega, w, xv);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const T dx = xv[a] - o1[k][a];
+          f.x[a * cs + g] = xv[a];
+          dacc.add(dx, dx);
+        }
       }
     }
   }
   if (partials == nullptr) return;
+  double acc[1] = {dacc.value()};
   double tot[1];
   if (!reduce_and_last<1>(acc, partials, counter, tot)) return;
   if (threadIdx.x != 0 || sc == nullptr) return;
@@ -580,14 +657,15 @@ k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
             double* partials, unsigned* counter) {
   if (sc->done) return;
   const T alpha = (T)sc->alpha;
-  double acc[1] = {0.0};
+  DotAcc<T> dacc;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
        i += (long long)gridDim.x * blockDim.x) {
     x[i] += alpha * p[i];
     const T rn = r[i] - alpha * q[i];
     r[i] = rn;
-    acc[0] += (double)rn * (double)rn;
+    dacc.add(rn, rn);
   }
+  double acc[1] = {dacc.value()};
   double tot[1];
   if (!reduce_and_last<1>(acc, partials, counter, tot)) return;
   if (threadIdx.x != 0) return;
