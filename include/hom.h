@@ -207,6 +207,70 @@ int hom_apply_static(int d, const int* N, const void* phase_dev, int index_bytes
                      const double* table, int nphase, int op, const double* E,
                      const double* x_dev, double* y_dev, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched iterations and continuous batching (build extensions; the paper has one solve at
+ * a time). Every request runs exactly the steps of a solo hom_solve with its own buffers,
+ * device scalars and reduction partials, in a fixed reduction order, so its result is
+ * bit-identical whether it runs alone or batched with others.
+ * --------------------------------------------------------------------------------------- */
+
+typedef struct hom_batch hom_batch;
+
+/* Group `count` problems with an active session (hom_solve_begin) of the same solver,
+ * precision, integration, grid and stream. The handles stay owned by the caller and must
+ * outlive the batch. Errors: HOM_ERR_INVALID if they differ. */
+int hom_batch_create(hom_problem* const* problems, int count, hom_batch** out);
+
+/* Advance every member by `iterations` steps with one launch per pass for all members
+ * (use_graph != 0: replay a captured CUDA graph of the batched step; ignored on the legacy
+ * default stream, which cannot be captured). Members whose solver has
+ * stopped skip their work on the device. all_done (nullable): synchronise and report whether
+ * every member has stopped (for HOM_FP32_REFINED also runs the FP64 outer updates). Finish
+ * each member with hom_solve_end. */
+int hom_batch_iterate(hom_batch* B, int iterations, int use_graph, int* all_done);
+void hom_batch_destroy(hom_batch* B);
+
+typedef struct hom_server hom_server;
+
+typedef struct {
+  int d;
+  int N[3];
+  hom_material material;   /* host data only; copied at submit                              */
+  int integration;
+  int precision;
+  double E[3];
+  int solver;
+  double tol;
+  hom_opts opts;
+} hom_request;
+
+typedef struct {
+  long long id;
+  int status;              /* hom_solve status of the request                              */
+  double AH_EE;            /* (A_H E, E)                                                    */
+  double flux[3];
+  hom_stats stats;
+  double latency_ms;       /* submit -> finished, host wall clock                           */
+  double queue_ms;         /* submit -> admitted                                            */
+} hom_result;
+
+/* A continuous-batching solve server on one stream (NULL: the server creates its own
+ * non-blocking stream, since CUDA graphs cannot be captured on the legacy default stream). Requests are admitted in arrival order
+ * while their estimated device memory fits hbm_budget_bytes (at least one is always admitted),
+ * grouped into buckets of equal grid, integration, precision and solver with up to max_batch
+ * slots each, and advanced together: one launch per pass and bucket (captured CUDA graphs of
+ * the batched step), whatever the mix of arrival times. Finished requests free their slot and
+ * memory at the step that detects them, and queued ones take their place. */
+int hom_server_create(size_t hbm_budget_bytes, int max_batch, void* stream, hom_server** out);
+/* Queue a request (the coefficient data is copied); *id identifies its result. */
+int hom_server_submit(hom_server* S, const hom_request* req, long long* id);
+/* Admit, advance every active request by `iterations` steps, retire finished ones, admit. */
+int hom_server_step(hom_server* S, int iterations);
+/* Move up to max finished results into out; *count = how many. */
+int hom_server_poll(hom_server* S, hom_result* out, int max, int* count);
+int hom_server_status(hom_server* S, int* active, int* queued, size_t* bytes_in_use);
+void hom_server_destroy(hom_server* S);
+
 /* Free everything the handle owns. NULL is accepted. */
 void hom_destroy(hom_problem* P);
 

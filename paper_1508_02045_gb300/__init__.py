@@ -32,7 +32,9 @@ SOLVERS = {"richardson": HOM_RICHARDSON, "cg": HOM_CG, "chebyshev": HOM_CHEBYSHE
 EXPORTED = ["hom_create", "hom_grid", "hom_bounds", "hom_apply", "hom_solve", "hom_energy",
             "hom_prolongate", "hom_bound", "hom_destroy", "hom_strerror", "hom_kernel_launches",
             "hom_profile_enable", "hom_profile_read", "hom_solve_begin", "hom_solve_iterate",
-            "hom_solve_end", "hom_apply_static"]
+            "hom_solve_end", "hom_apply_static", "hom_batch_create", "hom_batch_iterate",
+            "hom_batch_destroy", "hom_server_create", "hom_server_submit", "hom_server_step",
+            "hom_server_poll", "hom_server_status", "hom_server_destroy"]
 PASS_KINDS = ["line_fwd", "strided", "proj", "line_inv", "vector"]
 
 
@@ -59,6 +61,19 @@ class hom_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class hom_request(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("N", ctypes.c_int * 3), ("material", hom_material),
+                ("integration", ctypes.c_int), ("precision", ctypes.c_int),
+                ("E", ctypes.c_double * 3), ("solver", ctypes.c_int), ("tol", ctypes.c_double),
+                ("opts", hom_opts)]
+
+
+class hom_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("status", ctypes.c_int), ("AH_EE", ctypes.c_double),
+                ("flux", ctypes.c_double * 3), ("stats", hom_stats),
+                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libhom.so is not built ({LIB_PATH}); run paper_1508_02045_gb300.build.build()")
@@ -74,6 +89,18 @@ def _load():
     lib.hom_energy.argtypes = [vp, dp, vp, dp, dp]
     lib.hom_apply_static.argtypes = [ip, ctypes.POINTER(ctypes.c_int), vp, ip, dp, ip, ip, dp, vp,
                                      vp, vp]
+    lib.hom_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp)]
+    lib.hom_batch_iterate.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_int)]
+    lib.hom_batch_destroy.argtypes = [vp]
+    lib.hom_batch_destroy.restype = None
+    lib.hom_server_create.argtypes = [ctypes.c_size_t, ip, vp, ctypes.POINTER(vp)]
+    lib.hom_server_submit.argtypes = [vp, ctypes.POINTER(hom_request), ctypes.POINTER(ctypes.c_longlong)]
+    lib.hom_server_step.argtypes = [vp, ip]
+    lib.hom_server_poll.argtypes = [vp, ctypes.POINTER(hom_result), ip, ctypes.POINTER(ctypes.c_int)]
+    lib.hom_server_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_size_t)]
+    lib.hom_server_destroy.argtypes = [vp]
+    lib.hom_server_destroy.restype = None
     lib.hom_solve_begin.argtypes = [vp, dp, ip, ctypes.c_double, ctypes.POINTER(hom_opts)]
     lib.hom_solve_iterate.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]
     lib.hom_solve_end.argtypes = [vp, vp, dp, dp, ctypes.POINTER(hom_stats)]
@@ -88,7 +115,8 @@ def _load():
     lib.hom_profile_enable.argtypes = [ip]
     lib.hom_profile_read.argtypes = [dp, ctypes.POINTER(ctypes.c_longlong), ip]
     for name in EXPORTED:
-        if name not in ("hom_destroy", "hom_strerror", "hom_kernel_launches"):
+        if name not in ("hom_destroy", "hom_strerror", "hom_kernel_launches", "hom_batch_destroy",
+                        "hom_server_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -227,6 +255,82 @@ def hom_solve_end(P, d, x=None, allow_not_converged=False):
     if not (st == HOM_OK or (allow_not_converged and st == HOM_ERR_NOT_CONVERGED)):
         raise HomError(st, "hom_solve_end")
     return AH.value, [flux[i] for i in range(d)], stats.as_dict(), st
+
+
+def hom_batch_create(problems):
+    arr = (ctypes.c_void_p * len(problems))(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in problems])
+    out = ctypes.c_void_p()
+    _check(_lib.hom_batch_create(arr, len(problems), ctypes.byref(out)), "hom_batch_create")
+    return out
+
+
+def hom_batch_iterate(B, iterations, use_graph=True, poll=False):
+    done = ctypes.c_int(0)
+    _check(_lib.hom_batch_iterate(B, int(iterations), 1 if use_graph else 0,
+                                  ctypes.byref(done) if poll else None), "hom_batch_iterate")
+    return bool(done.value) if poll else None
+
+
+def hom_batch_destroy(B):
+    if B:
+        _lib.hom_batch_destroy(B)
+
+
+def hom_server_create(hbm_budget_bytes, max_batch=16, stream=0):
+    out = ctypes.c_void_p()
+    _check(_lib.hom_server_create(int(hbm_budget_bytes), int(max_batch), ctypes.c_void_p(stream),
+                                  ctypes.byref(out)), "hom_server_create")
+    return out
+
+
+def make_request(d, N, material, E, solver, tol, integration=HOM_APPROX, precision=HOM_FP64,
+                 opts=None):
+    r = hom_request()
+    r.d = d
+    for i, v in enumerate(N):
+        r.N[i] = int(v)
+    r.material = material
+    r.integration, r.precision = integration, precision
+    for i, v in enumerate(E):
+        r.E[i] = float(v)
+    r.solver, r.tol = int(solver), float(tol)
+    if opts is not None:
+        r.opts = opts
+    r._keep = material
+    return r
+
+
+def hom_server_submit(S, request):
+    rid = ctypes.c_longlong()
+    _check(_lib.hom_server_submit(S, ctypes.byref(request), ctypes.byref(rid)), "hom_server_submit")
+    return rid.value
+
+
+def hom_server_step(S, iterations):
+    return _check(_lib.hom_server_step(S, int(iterations)), "hom_server_step")
+
+
+def hom_server_poll(S, max_results=256):
+    buf = (hom_result * max_results)()
+    n = ctypes.c_int()
+    _check(_lib.hom_server_poll(S, buf, max_results, ctypes.byref(n)), "hom_server_poll")
+    out = []
+    for i in range(n.value):
+        r = buf[i]
+        out.append({"id": r.id, "status": r.status, "AH_EE": r.AH_EE, "flux": list(r.flux),
+                    "stats": r.stats.as_dict(), "latency_ms": r.latency_ms, "queue_ms": r.queue_ms})
+    return out
+
+
+def hom_server_status(S):
+    a, q, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+    _check(_lib.hom_server_status(S, ctypes.byref(a), ctypes.byref(q), ctypes.byref(b)), "hom_server_status")
+    return a.value, q.value, b.value
+
+
+def hom_server_destroy(S):
+    if S:
+        _lib.hom_server_destroy(S)
 
 
 def hom_energy(P, E, x=None):

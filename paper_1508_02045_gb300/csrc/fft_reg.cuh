@@ -264,7 +264,7 @@ __device__ __forceinline__ Loc<T> sloc(int base, int ls, int es) {
 template <typename T>
 __device__ __forceinline__ int reg_lines(int a, int b, const AxisPlan* P, int nl, int ls, int es,
                                          bool colmajor, bool inv, int tw_base) {
-  const int nst = P->nst, n = P->n;
+  const int nst = P->nst;
 #pragma unroll 1
   for (int st = 0; st < nst; ++st) {
     stage_any<T>(inv, P, st, sloc<T>(a, ls, es), sloc<T>(b, ls, es), nl, colmajor, tw_base);
@@ -283,7 +283,7 @@ template <typename T>
 __device__ __forceinline__ void reg_columns_out(int src, int spare, cpx<T>* g, int ges, int ncols,
                                                 int TCp, const AxisPlan* P, bool inv,
                                                 int tw_base) {
-  const int nst = P->nst, n = P->n;
+  const int nst = P->nst;
   int a = src, b = spare;
 #pragma unroll 1
   for (int st = 0; st < nst - 1; ++st) {

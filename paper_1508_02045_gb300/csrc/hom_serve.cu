@@ -1,0 +1,671 @@
+// Batched iterations of same-shape solves (hom_batch) and the continuous-batching request
+// server built on them (hom_server). Both are build extensions around Algorithms 1-4: every
+// request runs exactly the solver steps of a solo hom_solve, with its own buffers, device
+// scalars and reduction partials, so its result does not depend on what it is batched with.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <tuple>
+#include <vector>
+
+#include "problem.h"
+
+using namespace hom;
+using namespace hom::detail;
+
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// per-request descriptors of the batched launches
+// ---------------------------------------------------------------------------------------
+ReqDesc<double> desc64(hom_problem* P) {
+  ReqDesc<double> r{};
+  r.S = (cpx<double>*)P->S;
+  r.mat = P->e64.mat;
+  r.sc = P->d_sc;
+  r.partials = P->partials;
+  r.counter = P->counter;
+  r.ff.cs = r.fi.cs = P->nodes;
+  double* x = P->vec[0];
+  double* rr = P->vec[2];
+  double* p = P->vec[3];
+  double* q = P->vec[4];
+  switch (P->sv.solver) {
+    case HOM_RICHARDSON:  // x_m / x_{m-1} alternate between vec[0] and vec[1]
+      r.ff.x = x;
+      r.fi.x = x;
+      break;
+    case HOM_CG:
+      r.ff.xin = rr;
+      r.ff.p = p;
+      r.fi.out = q;
+      r.fi.p = p;
+      r.fi.x = x;
+      r.fi.r = rr;
+      break;
+    case HOM_CHEBYSHEV:
+      r.ff.xin = p;
+      r.fi.p = p;
+      r.fi.r = rr;
+      r.fi.x = x;
+      break;
+    default:  // Eyre-Milton
+      r.ff.xin = x;
+      r.fi.x = x;
+      break;
+  }
+  return r;
+}
+
+// inner FP32 solve of the iterative refinement (CG or Chebyshev on the FP32 operator)
+ReqDesc<float> desc32(hom_problem* P) {
+  ReqDesc<float> r{};
+  r.S = (cpx<float>*)P->S;
+  r.mat = P->e32.mat;
+  r.sc = P->d_sc2;
+  r.partials = P->partials;
+  r.counter = P->counter;
+  r.ff.cs = r.fi.cs = P->nodes;
+  float* x = P->fvec[0];
+  float* rr = P->fvec[1];
+  float* p = P->fvec[2];
+  float* q = P->fvec[3];
+  if (P->sv.solver == HOM_CG) {
+    r.ff.xin = rr;
+    r.ff.p = p;
+    r.fi.out = q;
+    r.fi.p = p;
+    r.fi.x = x;
+    r.fi.r = rr;
+  } else {
+    r.ff.xin = p;
+    r.fi.p = p;
+    r.fi.r = rr;
+    r.fi.x = x;
+  }
+  return r;
+}
+
+// placeholder descriptor of an empty slot: its scalars say "stopped", so every CTA of that
+// slot returns at entry and never dereferences the other (null) pointers
+template <typename T>
+ReqDesc<T> idle_desc(Scalars* idle) {
+  ReqDesc<T> r{};
+  r.sc = idle;
+  return r;
+}
+
+// One batched step of the solver `solver` over n descriptors (Algorithms 1-4; for refinement
+// the FP32 inner step). Geometry from the engine of a representative problem.
+template <typename T>
+void batch_step(const Engine<T>& E, int solver, const ReqDesc<T>* reqs, int n, int red_grid,
+                long long nodes, int d, cudaStream_t st) {
+  switch (solver) {
+    case HOM_RICHARDSON:
+      E.apply_batch(PRE_AFFINE, PROJ_GAMMA, POST_RICH, reqs, n, st);
+      break;
+    case HOM_CG:
+      E.apply_batch(PRE_CG, PROJ_GAMMA, POST_CG, reqs, n, st);
+      Ops<T>::cg_update(nullptr, nullptr, nullptr, nullptr, (long long)d * nodes, nodes, nullptr,
+                        nullptr, nullptr, red_grid, st, reqs, n);
+      break;
+    case HOM_CHEBYSHEV:
+      E.apply_batch(PRE_LINEAR, PROJ_GAMMA, POST_CHEB, reqs, n, st);
+      break;
+    default:
+      E.apply_batch(PRE_EM, PROJ_EM, POST_EM, reqs, n, st);
+      break;
+  }
+}
+
+__global__ void k_gather_done(const Scalars* const* sc, int n, int* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = sc[i] != nullptr ? sc[i]->done : 1;
+}
+
+}  // namespace
+
+// ===========================================================================================
+// hom_batch
+// ===========================================================================================
+struct hom_batch {
+  std::vector<hom_problem*> m;
+  int solver = 0;
+  bool refined = false;
+  cudaStream_t stream = nullptr;
+  ReqDesc<double>* d64 = nullptr;
+  ReqDesc<float>* d32 = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+};
+
+namespace {
+
+int batch_capture(hom_batch* B, int steps) {
+  if (B->graph) {
+    cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+  }
+  hom_problem* P0 = B->m[0];
+  const int n = (int)B->m.size();
+  cudaGraph_t g = nullptr;
+  const bool prof = profiling();
+  if (prof) hom_profile_enable(0);
+  if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    if (prof) hom_profile_enable(1);
+    return HOM_ERR_CUDA;
+  }
+  for (int k = 0; k < steps; ++k) {
+    if (B->refined)
+      batch_step<float>(P0->e32, B->solver, B->d32, n, P0->red_grid, P0->nodes, P0->d, B->stream);
+    else
+      batch_step<double>(P0->e64, B->solver, B->d64, n, P0->red_grid, P0->nodes, P0->d, B->stream);
+  }
+  const cudaError_t e = cudaStreamEndCapture(B->stream, &g);
+  if (prof) hom_profile_enable(1);
+  if (e != cudaSuccess) return HOM_ERR_CUDA;
+  const cudaError_t e2 = cudaGraphInstantiate(&B->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) {
+    B->graph = nullptr;
+    return HOM_ERR_CUDA;
+  }
+  B->graph_steps = steps;
+  return HOM_OK;
+}
+
+}  // namespace
+
+extern "C" int hom_batch_create(hom_problem* const* problems, int count, hom_batch** out) {
+  if (!problems || count < 1 || !out) return HOM_ERR_INVALID;
+  *out = nullptr;
+  hom_problem* P0 = problems[0];
+  if (!P0 || !P0->sv.active) return HOM_ERR_INVALID;
+  for (int i = 0; i < count; ++i) {
+    hom_problem* P = problems[i];
+    if (!P || !P->sv.active || P->sv.solver != P0->sv.solver || P->d != P0->d ||
+        P->precision != P0->precision || P->integration != P0->integration ||
+        P->stream != P0->stream || P->device != P0->device)
+      return HOM_ERR_INVALID;
+    for (int a = 0; a < P->d; ++a)
+      if (P->M[a] != P0->M[a] || P->N[a] != P0->N[a]) return HOM_ERR_INVALID;
+  }
+  auto* B = new hom_batch();
+  B->m.assign(problems, problems + count);
+  B->solver = P0->sv.solver;
+  B->refined = P0->sv.refined;
+  B->stream = P0->stream;
+  if (B->refined) {
+    std::vector<ReqDesc<float>> h;
+    for (auto* P : B->m) h.push_back(desc32(P));
+    if (alloc((void**)&B->d32, sizeof(ReqDesc<float>) * h.size())) { delete B; return HOM_ERR_OOM; }
+    cudaMemcpy(B->d32, h.data(), sizeof(ReqDesc<float>) * h.size(), cudaMemcpyHostToDevice);
+  } else {
+    std::vector<ReqDesc<double>> h;
+    for (auto* P : B->m) h.push_back(desc64(P));
+    if (alloc((void**)&B->d64, sizeof(ReqDesc<double>) * h.size())) { delete B; return HOM_ERR_OOM; }
+    cudaMemcpy(B->d64, h.data(), sizeof(ReqDesc<double>) * h.size(), cudaMemcpyHostToDevice);
+  }
+  if (check_last()) {
+    hom_batch_destroy(B);
+    return HOM_ERR_CUDA;
+  }
+  *out = B;
+  return HOM_OK;
+}
+
+extern "C" int hom_batch_iterate(hom_batch* B, int iterations, int use_graph, int* all_done) {
+  if (!B || iterations < 0) return HOM_ERR_INVALID;
+  hom_problem* P0 = B->m[0];
+  const int n = (int)B->m.size();
+  // graphs need a capturable (non-default) stream; on the default stream launch directly
+  if (use_graph && iterations > 0 && B->stream != nullptr) {
+    const int steps = std::min(iterations, 8);
+    if (!B->graph || B->graph_steps != steps) {
+      int rc = batch_capture(B, steps);
+      if (rc) return rc;
+    }
+    int done_steps = 0;
+    while (done_steps + B->graph_steps <= iterations) {
+      HOM_CUDA(cudaGraphLaunch(B->graph, B->stream));
+      launch_counter() += (long long)B->graph_steps *
+                          ((P0->d == 3 ? 5 : 3) + (B->solver == HOM_CG ? 1 : 0));
+      done_steps += B->graph_steps;
+    }
+    for (; done_steps < iterations; ++done_steps) {
+      if (B->refined)
+        batch_step<float>(P0->e32, B->solver, B->d32, n, P0->red_grid, P0->nodes, P0->d, B->stream);
+      else
+        batch_step<double>(P0->e64, B->solver, B->d64, n, P0->red_grid, P0->nodes, P0->d, B->stream);
+    }
+  } else {
+    for (int k = 0; k < iterations; ++k) {
+      if (B->refined)
+        batch_step<float>(P0->e32, B->solver, B->d32, n, P0->red_grid, P0->nodes, P0->d, B->stream);
+      else
+        batch_step<double>(P0->e64, B->solver, B->d64, n, P0->red_grid, P0->nodes, P0->d, B->stream);
+    }
+  }
+  for (auto* P : B->m) P->sv.issued += iterations;
+  int rc = check_last();
+  if (rc) return rc;
+  if (all_done) {
+    int all = 1;
+    for (auto* P : B->m) {
+      if (B->refined) {
+        if (P->sv.finished) continue;
+        if ((rc = poll(P, P->d_sc2))) return rc;
+        if (P->h_sc->done && (rc = refine_outer_update(P))) return rc;
+        if (!P->sv.finished) all = 0;
+      } else {
+        if ((rc = poll(P, P->d_sc))) return rc;
+        const int cap = P->sv.maxit + (P->sv.solver == HOM_RICHARDSON ? 1 : 0);
+        if (!P->h_sc->done && P->sv.issued < cap) all = 0;
+      }
+    }
+    *all_done = all;
+  }
+  return HOM_OK;
+}
+
+extern "C" void hom_batch_destroy(hom_batch* B) {
+  if (!B) return;
+  if (B->graph) cudaGraphExecDestroy(B->graph);
+  if (B->d64) cudaFree(B->d64);
+  if (B->d32) cudaFree(B->d32);
+  delete B;
+}
+
+// ===========================================================================================
+// hom_server: continuous batching of heterogeneous requests
+// ===========================================================================================
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+struct ServerReq {
+  long long id = 0;
+  hom_request req{};
+  std::vector<unsigned char> data;   // owned copy of the coefficient data (host)
+  std::vector<double> table;
+  size_t bytes = 0;                  // device bytes charged against the budget
+  hom_problem* P = nullptr;
+  int bucket = -1, slot = -1;
+  Clock::time_point t_submit, t_admit;
+};
+
+// a bucket: same grid, integration, precision and solver; fixed-capacity slots
+struct Bucket {
+  int d = 0, M[3] = {1, 1, 1}, N[3] = {1, 1, 1};
+  int integration = 0, precision = 0, solver = 0;
+  int cap = 0;
+  std::vector<ServerReq*> slots;
+  Engine<double>* e64 = nullptr;  // plans and launch geometry of the bucket's shape
+  Engine<float>* e32 = nullptr;
+  long long nodes = 0;
+  int red_grid = 0;
+  ReqDesc<double>* d64 = nullptr;
+  ReqDesc<float>* d32 = nullptr;
+  const Scalars** d_sc = nullptr;  // per-slot scalars for the done-flag gather
+  int* d_done = nullptr;
+  int* h_done = nullptr;
+  bool dirty = true;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+};
+
+size_t estimate_bytes(const hom_request& r) {
+  long long nodes = 1;
+  for (int a = 0; a < r.d; ++a)
+    nodes *= (r.integration == HOM_EXACT) ? (r.material.M[a] > 0 ? r.material.M[a] : 2 * r.N[a] - 1)
+                                          : r.N[a];
+  const long long nl = nodes / ((r.integration == HOM_EXACT)
+                                    ? (r.material.M[r.d - 1] > 0 ? r.material.M[r.d - 1] : 2 * r.N[r.d - 1] - 1)
+                                    : r.N[r.d - 1]);
+  const int nlast = (int)(nodes / nl);
+  size_t b = sizeof(double) * 5 * r.d * nodes;                     // solver vectors
+  b += sizeof(double) * 2 * r.d * nl * ((nlast + 1) / 2);          // half spectrum
+  b += nodes * 2 + sizeof(double) * nodes;                         // phases / coefficient field
+  if (r.precision == HOM_FP32_REFINED) b += sizeof(float) * (4 * r.d + 1) * nodes;
+  return b + (4u << 20);                                           // partials, plans, tables
+}
+
+}  // namespace
+
+struct hom_server {
+  size_t budget = 0, in_use = 0;
+  int max_batch = 16;
+  cudaStream_t stream = nullptr;
+  long long next_id = 1;
+  std::deque<ServerReq*> queue;
+  std::vector<Bucket> buckets;
+  std::vector<hom_result> done;
+  Scalars* d_idle = nullptr;
+  int steps_per_graph = 4;
+  bool own_stream = false;
+};
+
+namespace {
+
+int find_bucket(hom_server* S, const hom_request& r, const int* M) {
+  for (size_t i = 0; i < S->buckets.size(); ++i) {
+    const Bucket& b = S->buckets[i];
+    bool same = b.d == r.d && b.integration == r.integration && b.precision == r.precision &&
+                b.solver == r.solver;
+    for (int a = 0; a < r.d && same; ++a) same = b.M[a] == M[a] && b.N[a] == r.N[a];
+    if (same) return (int)i;
+  }
+  return -1;
+}
+
+int bucket_upload(hom_server* S, Bucket& b) {
+  std::vector<const Scalars*> scs(b.cap, nullptr);
+  if (b.precision == HOM_FP32_REFINED) {
+    std::vector<ReqDesc<float>> h(b.cap, idle_desc<float>(S->d_idle));
+    for (int i = 0; i < b.cap; ++i)
+      if (b.slots[i]) {
+        h[i] = desc32(b.slots[i]->P);
+        scs[i] = b.slots[i]->P->d_sc2;
+      }
+    HOM_CUDA(cudaMemcpyAsync(b.d32, h.data(), sizeof(ReqDesc<float>) * b.cap, cudaMemcpyHostToDevice, S->stream));
+  } else {
+    std::vector<ReqDesc<double>> h(b.cap, idle_desc<double>(S->d_idle));
+    for (int i = 0; i < b.cap; ++i)
+      if (b.slots[i]) {
+        h[i] = desc64(b.slots[i]->P);
+        scs[i] = b.slots[i]->P->d_sc;
+      }
+    HOM_CUDA(cudaMemcpyAsync(b.d64, h.data(), sizeof(ReqDesc<double>) * b.cap, cudaMemcpyHostToDevice, S->stream));
+  }
+  HOM_CUDA(cudaMemcpyAsync(b.d_sc, scs.data(), sizeof(Scalars*) * b.cap, cudaMemcpyHostToDevice, S->stream));
+  HOM_CUDA(cudaStreamSynchronize(S->stream));  // host vectors go out of scope
+  b.dirty = false;
+  return HOM_OK;
+}
+
+void bucket_step(hom_server* S, Bucket& b) {
+  if (b.precision == HOM_FP32_REFINED)
+    batch_step<float>(*b.e32, b.solver, b.d32, b.cap, b.red_grid, b.nodes, b.d, S->stream);
+  else
+    batch_step<double>(*b.e64, b.solver, b.d64, b.cap, b.red_grid, b.nodes, b.d, S->stream);
+}
+
+int bucket_launch(hom_server* S, Bucket& b, int iterations) {
+  if (!b.graph) {
+    cudaGraph_t g = nullptr;
+    const bool prof = profiling();
+    if (prof) hom_profile_enable(0);
+    HOM_CUDA(cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < S->steps_per_graph; ++k) bucket_step(S, b);
+    const cudaError_t e = cudaStreamEndCapture(S->stream, &g);
+    if (prof) hom_profile_enable(1);
+    HOM_CUDA(e);
+    const cudaError_t e2 = cudaGraphInstantiate(&b.graph, g, 0);
+    cudaGraphDestroy(g);
+    HOM_CUDA(e2);
+    b.graph_steps = S->steps_per_graph;
+  }
+  int k = 0;
+  for (; k + b.graph_steps <= iterations; k += b.graph_steps) {
+    HOM_CUDA(cudaGraphLaunch(b.graph, S->stream));
+    launch_counter() += (long long)b.graph_steps * ((b.d == 3 ? 5 : 3) + (b.solver == HOM_CG ? 1 : 0));
+  }
+  for (; k < iterations; ++k) bucket_step(S, b);
+  for (auto* r : b.slots)
+    if (r) r->P->sv.issued += iterations;
+  return check_last();
+}
+
+// move queued requests onto the device while the budget and the slots allow
+int admit(hom_server* S) {
+  while (!S->queue.empty()) {
+    ServerReq* r = S->queue.front();
+    if (S->in_use + r->bytes > S->budget && S->in_use > 0) break;
+    int M[3];
+    for (int a = 0; a < r->req.d; ++a)
+      M[a] = (r->req.integration == HOM_EXACT)
+                 ? (r->req.material.M[a] > 0 ? r->req.material.M[a] : 2 * r->req.N[a] - 1)
+                 : r->req.N[a];
+    int bi = find_bucket(S, r->req, M);
+    if (bi >= 0) {
+      Bucket& b = S->buckets[bi];
+      if (std::find(b.slots.begin(), b.slots.end(), nullptr) == b.slots.end()) break;
+    }
+    // create the problem and start its session
+    hom_material mat = r->req.material;
+    mat.data = r->data.data();
+    mat.table = r->table.empty() ? nullptr : r->table.data();
+    mat.data_on_device = 0;
+    hom_problem* P = nullptr;
+    int rc = hom_create(r->req.d, r->req.N, &mat, r->req.integration, r->req.precision,
+                        S->stream, &P);
+    if (rc == HOM_OK)
+      rc = hom_solve_begin(P, r->req.E, r->req.solver, r->req.tol, &r->req.opts);
+    S->queue.pop_front();
+    if (rc != HOM_OK) {
+      if (P) hom_destroy(P);
+      hom_result res{};
+      res.id = r->id;
+      res.status = rc;
+      res.latency_ms = ms_between(r->t_submit, Clock::now());
+      S->done.push_back(res);
+      delete r;
+      continue;
+    }
+    r->P = P;
+    r->t_admit = Clock::now();
+    S->in_use += r->bytes;
+    if (bi < 0) {
+      Bucket b;
+      b.d = r->req.d;
+      for (int a = 0; a < 3; ++a) {
+        b.M[a] = a < r->req.d ? M[a] : 1;
+        b.N[a] = a < r->req.d ? r->req.N[a] : 1;
+      }
+      b.integration = r->req.integration;
+      b.precision = r->req.precision;
+      b.solver = r->req.solver;
+      b.cap = S->max_batch;
+      b.slots.assign(b.cap, nullptr);
+      if ((rc = alloc((void**)&b.d64, sizeof(ReqDesc<double>) * b.cap)) ||
+          (rc = alloc((void**)&b.d32, sizeof(ReqDesc<float>) * b.cap)) ||
+          (rc = alloc((void**)&b.d_sc, sizeof(Scalars*) * b.cap)) ||
+          (rc = alloc((void**)&b.d_done, sizeof(int) * b.cap)))
+        return rc;
+      if (cudaMallocHost((void**)&b.h_done, sizeof(int) * b.cap) != cudaSuccess) return HOM_ERR_OOM;
+      // the bucket keeps its own plans and geometry (same planner as hom_create)
+      b.nodes = P->nodes;
+      b.red_grid = P->red_grid;
+      b.e64 = new Engine<double>();
+      if ((rc = b.e64->init(b.d, P->M, P->N, smem_budget()))) return rc;
+      if (b.precision == HOM_FP32_REFINED) {
+        b.e32 = new Engine<float>();
+        if ((rc = b.e32->init(b.d, P->M, P->N, smem_budget()))) return rc;
+      }
+      S->buckets.push_back(b);
+      bi = (int)S->buckets.size() - 1;
+    }
+    Bucket& b = S->buckets[bi];
+    const int slot = (int)(std::find(b.slots.begin(), b.slots.end(), nullptr) - b.slots.begin());
+    b.slots[slot] = r;
+    r->bucket = bi;
+    r->slot = slot;
+    b.dirty = true;
+  }
+  return HOM_OK;
+}
+
+// finish a request whose solver stopped: outputs, timing, free its device memory
+void retire(hom_server* S, Bucket& b, int slot) {
+  ServerReq* r = b.slots[slot];
+  hom_result res{};
+  res.id = r->id;
+  res.status = hom_solve_end(r->P, nullptr, &res.AH_EE, res.flux, &res.stats);
+  const auto now = Clock::now();
+  res.latency_ms = ms_between(r->t_submit, now);
+  res.queue_ms = ms_between(r->t_submit, r->t_admit);
+  S->done.push_back(res);
+  hom_destroy(r->P);
+  S->in_use -= r->bytes;
+  b.slots[slot] = nullptr;
+  b.dirty = true;
+  delete r;
+}
+
+}  // namespace
+
+extern "C" int hom_server_create(size_t hbm_budget_bytes, int max_batch, void* stream,
+                                 hom_server** out) {
+  if (!out || max_batch < 1 || hbm_budget_bytes == 0) return HOM_ERR_INVALID;
+  auto* S = new hom_server();
+  S->budget = hbm_budget_bytes;
+  S->max_batch = max_batch;
+  S->stream = (cudaStream_t)stream;
+  if (S->stream == nullptr) {  // graphs cannot be captured on the legacy default stream
+    if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete S;
+      return HOM_ERR_CUDA;
+    }
+    S->own_stream = true;
+  }
+  if (alloc((void**)&S->d_idle, sizeof(Scalars))) {
+    delete S;
+    return HOM_ERR_OOM;
+  }
+  Scalars idle{};
+  idle.done = 1;
+  cudaMemcpy(S->d_idle, &idle, sizeof(Scalars), cudaMemcpyHostToDevice);
+  *out = S;
+  return check_last();
+}
+
+extern "C" int hom_server_submit(hom_server* S, const hom_request* req, long long* id) {
+  if (!S || !req || !id) return HOM_ERR_INVALID;
+  if (req->d != 2 && req->d != 3) return HOM_ERR_INVALID;
+  long long nodes = 1;
+  for (int a = 0; a < req->d; ++a) {
+    if (req->N[a] < 3 || req->N[a] % 2 == 0) return HOM_ERR_INVALID;
+    nodes *= req->N[a];
+  }
+  auto* r = new ServerReq();
+  r->req = *req;
+  r->id = S->next_id++;
+  r->t_submit = Clock::now();
+  const hom_material& m = req->material;
+  if (m.data_on_device || !m.data) {
+    delete r;
+    return HOM_ERR_INVALID;  // the server keeps host copies until admission
+  }
+  if (m.kind == HOM_A_PHASE) {
+    r->data.assign((const unsigned char*)m.data, (const unsigned char*)m.data + nodes * m.index_bytes);
+    r->table.assign(m.table, m.table + (size_t)m.nphase * req->d * req->d);
+  } else if (m.kind == HOM_A_SCALAR) {
+    r->data.assign((const unsigned char*)m.data, (const unsigned char*)m.data + nodes * sizeof(double));
+  } else {
+    long long mnodes = 1;
+    for (int a = 0; a < req->d; ++a) mnodes *= (m.M[a] > 0 ? m.M[a] : 2 * req->N[a] - 1);
+    r->data.assign((const unsigned char*)m.data, (const unsigned char*)m.data + mnodes * 2 * sizeof(double));
+  }
+  r->bytes = estimate_bytes(*req);
+  S->queue.push_back(r);
+  *id = r->id;
+  return HOM_OK;
+}
+
+extern "C" int hom_server_step(hom_server* S, int iterations) {
+  if (!S || iterations < 1) return HOM_ERR_INVALID;
+  int rc = admit(S);
+  if (rc) return rc;
+  // one batched launch per pass and bucket
+  for (auto& b : S->buckets) {
+    bool any = false;
+    for (auto* r : b.slots) any = any || r != nullptr;
+    if (!any) continue;
+    if (b.dirty && (rc = bucket_upload(S, b))) return rc;
+    if ((rc = bucket_launch(S, b, iterations))) return rc;
+  }
+  // stopping flags of every slot in one copy per bucket
+  for (auto& b : S->buckets) {
+    k_gather_done<<<(b.cap + 127) / 128, 128, 0, S->stream>>>(b.d_sc, b.cap, b.d_done);
+    HOM_CUDA(cudaMemcpyAsync(b.h_done, b.d_done, sizeof(int) * b.cap, cudaMemcpyDeviceToHost, S->stream));
+  }
+  HOM_CUDA(cudaStreamSynchronize(S->stream));
+  for (auto& b : S->buckets) {
+    for (int i = 0; i < b.cap; ++i) {
+      ServerReq* r = b.slots[i];
+      if (!r) continue;
+      hom_problem* P = r->P;
+      bool finished;
+      if (P->sv.refined) {
+        if (b.h_done[i] && !P->sv.finished) {
+          if ((rc = refine_outer_update(P))) return rc;
+        }
+        finished = P->sv.finished;
+      } else {
+        const int cap = P->sv.maxit + (P->sv.solver == HOM_RICHARDSON ? 1 : 0);
+        finished = b.h_done[i] || P->sv.issued >= cap;
+      }
+      if (finished) retire(S, b, i);
+    }
+  }
+  return admit(S);
+}
+
+extern "C" int hom_server_poll(hom_server* S, hom_result* out, int max, int* count) {
+  if (!S || !count || (max > 0 && !out)) return HOM_ERR_INVALID;
+  const int n = std::min<int>(max, (int)S->done.size());
+  for (int i = 0; i < n; ++i) out[i] = S->done[i];
+  S->done.erase(S->done.begin(), S->done.begin() + n);
+  *count = n;
+  return HOM_OK;
+}
+
+extern "C" int hom_server_status(hom_server* S, int* active, int* queued, size_t* bytes_in_use) {
+  if (!S) return HOM_ERR_INVALID;
+  int a = 0;
+  for (auto& b : S->buckets)
+    for (auto* r : b.slots) a += r != nullptr;
+  if (active) *active = a;
+  if (queued) *queued = (int)S->queue.size();
+  if (bytes_in_use) *bytes_in_use = S->in_use;
+  return HOM_OK;
+}
+
+extern "C" void hom_server_destroy(hom_server* S) {
+  if (!S) return;
+  if (S->stream) cudaStreamSynchronize(S->stream);
+  for (auto& b : S->buckets) {
+    for (auto* r : b.slots)
+      if (r) {
+        hom_destroy(r->P);
+        delete r;
+      }
+    if (b.graph) cudaGraphExecDestroy(b.graph);
+    if (b.e64) {
+      b.e64->release();
+      delete b.e64;
+    }
+    if (b.e32) {
+      b.e32->release();
+      delete b.e32;
+    }
+    cudaFree(b.d64);
+    cudaFree(b.d32);
+    cudaFree(b.d_sc);
+    cudaFree(b.d_done);
+    cudaFreeHost(b.h_done);
+  }
+  for (auto* r : S->queue) delete r;
+  cudaFree(S->d_idle);
+  if (S->own_stream) cudaStreamDestroy(S->stream);
+  delete S;
+}

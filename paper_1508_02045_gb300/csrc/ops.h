@@ -10,6 +10,7 @@ namespace hom {
 struct OpArgs;
 struct ProjGeom;
 template <typename T> struct Fields;
+template <typename T> struct ReqDesc;
 
 // launch geometry of the kernels of one grid, chosen by the planner in hom_api.cu
 struct PassGeom {
@@ -33,21 +34,27 @@ struct Ops {
   static size_t smem_proj(int n, int D, int TCp);
   static cudaError_t prepare(int maxD);  // raise dynamic shared memory limits
 
+  // reqs / nreq: optional per-request descriptors of a batched launch (grid.z = nreq); the
+  // direct arguments are then ignored where a descriptor provides them
   static void line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
                        const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
-                       const Scalars* sc, const OpArgs& args, cudaStream_t st);
+                       const Scalars* sc, const OpArgs& args, cudaStream_t st,
+                       const ReqDesc<T>* reqs = nullptr, int nreq = 1);
   // strided DFT along axis 1 (D = 3) or axis 0 (no projection) of ncomp components
   static void strided(const PassGeom& g, int axis, int inv, cpx<T>* S, const AxisPlan& P,
-                      const cpx<T>* tw, int ncomp, const Scalars* sc, cudaStream_t st);
+                      const cpx<T>* tw, int ncomp, const Scalars* sc, cudaStream_t st,
+                      const ReqDesc<T>* reqs = nullptr, int nreq = 1);
   static void proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, const cpx<T>* tw,
-                   const ProjGeom& pg, const Scalars* sc, cudaStream_t st);
+                   const ProjGeom& pg, const Scalars* sc, cudaStream_t st,
+                   const ReqDesc<T>* reqs = nullptr, int nreq = 1);
   static void line_inv(const PassGeom& g, int post, const cpx<T>* S, const Fields<T>& f,
                        const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
                        Scalars* sc, const OpArgs& args, double* partials, unsigned* counter,
-                       int negate, cudaStream_t st);
+                       int negate, cudaStream_t st, const ReqDesc<T>* reqs = nullptr,
+                       int nreq = 1);
   static void cg_update(T* x, T* r, const T* p, const T* q, long long len, long long nodes,
                         Scalars* sc, double* partials, unsigned* counter, int grid,
-                        cudaStream_t st);
+                        cudaStream_t st, const ReqDesc<T>* reqs = nullptr, int nreq = 1);
   static void energy(int D, const T* x, long long nodes, const MatView<T>& mat, Scalars* sc,
                      double* partials, unsigned* counter, int grid, cudaStream_t st);
   static void fill_const(T* x, long long nodes, int d, const Scalars* sc, cudaStream_t st);

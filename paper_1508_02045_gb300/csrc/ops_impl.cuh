@@ -96,12 +96,13 @@ cudaError_t Ops<T>::prepare(int) {
 template <typename T, int D>
 static void line_fwd_d(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
                        const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
-                       const Scalars* sc, const OpArgs& args, cudaStream_t st) {
-  const unsigned grid = (unsigned)((g.nlines + g.LB - 1) / g.LB);
+                       const Scalars* sc, const OpArgs& args, cudaStream_t st,
+                       const ReqDesc<T>* reqs, int nreq) {
+  const dim3 grid((unsigned)((g.nlines + g.LB - 1) / g.LB), 1, (unsigned)nreq);
   const size_t sm = Ops<T>::smem_line(P.n, ncomp, g.LB);
   const bool prof = profiling();
   if (prof) prof_mark(KIND_LINE_FWD, st, true);
-#define HOM_LF(PRE_) k_line_fwd<T, D, PRE_><<<grid, kThreads, sm, st>>>(f, S, P, tw, ncomp, g.nlines, g.LB, g.scs, mat, sc, args)
+#define HOM_LF(PRE_) k_line_fwd<T, D, PRE_><<<grid, kThreads, sm, st>>>(f, S, P, tw, ncomp, g.nlines, g.LB, g.scs, mat, sc, args, reqs)
   switch (pre) {
     case PRE_AFFINE: HOM_LF(PRE_AFFINE); break;
     case PRE_LINEAR: HOM_LF(PRE_LINEAR); break;
@@ -117,14 +118,16 @@ static void line_fwd_d(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S
 template <typename T>
 void Ops<T>::line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
                       const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
-                      const Scalars* sc, const OpArgs& args, cudaStream_t st) {
-  if (g.D == 2) line_fwd_d<T, 2>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st);
-  else line_fwd_d<T, 3>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st);
+                      const Scalars* sc, const OpArgs& args, cudaStream_t st,
+                      const ReqDesc<T>* reqs, int nreq) {
+  if (g.D == 2) line_fwd_d<T, 2>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq);
+  else line_fwd_d<T, 3>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq);
 }
 
 template <typename T>
 void Ops<T>::strided(const PassGeom& g, int axis, int inv, cpx<T>* S, const AxisPlan& P,
-                     const cpx<T>* tw, int ncomp, const Scalars* sc, cudaStream_t st) {
+                     const cpx<T>* tw, int ncomp, const Scalars* sc, cudaStream_t st,
+                     const ReqDesc<T>* reqs, int nreq) {
   long long C, es, bs;
   int batches, TC, TCp;
   if (g.D == 3 && axis == 1) {
@@ -142,23 +145,24 @@ void Ops<T>::strided(const PassGeom& g, int axis, int inv, cpx<T>* S, const Axis
     TC = g.TCs0;
     TCp = g.TCs0p;
   }
-  dim3 grid((unsigned)((C + TC - 1) / TC), (unsigned)batches);
+  dim3 grid((unsigned)((C + TC - 1) / TC), (unsigned)batches, (unsigned)nreq);
   const size_t sm = smem_strided(P.n, TCp, P.nst);
   const bool prof = profiling();
   if (prof) prof_mark(KIND_STRIDED, st, true);
-  k_strided<T><<<grid, kThreads, sm, st>>>(S, P, tw, C, es, bs, TC, TCp, inv, sc);
+  k_strided<T><<<grid, kThreads, sm, st>>>(S, P, tw, C, es, bs, TC, TCp, inv, sc, reqs);
   if (prof) prof_mark(KIND_STRIDED, st, false);
   ++launch_counter();
 }
 
 template <typename T>
 void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, const cpx<T>* tw,
-                  const ProjGeom& pg, const Scalars* sc, cudaStream_t st) {
-  const unsigned grid = (unsigned)((pg.C + g.TC0 - 1) / g.TC0);
+                  const ProjGeom& pg, const Scalars* sc, cudaStream_t st,
+                  const ReqDesc<T>* reqs, int nreq) {
+  const dim3 grid((unsigned)((pg.C + g.TC0 - 1) / g.TC0), 1, (unsigned)nreq);
   const size_t sm = smem_proj(P.n, g.D, g.TC0p);
   const bool prof = profiling();
   if (prof) prof_mark(KIND_PROJ, st, true);
-#define HOM_PJ(D_, M_) k_proj<T, D_, M_><<<grid, kThreads, sm, st>>>(S, P, tw, pg, g.TC0, g.TC0p, sc)
+#define HOM_PJ(D_, M_) k_proj<T, D_, M_><<<grid, kThreads, sm, st>>>(S, P, tw, pg, g.TC0, g.TC0p, sc, reqs)
   if (g.D == 2) {
     if (mode == PROJ_EM) HOM_PJ(2, PROJ_EM); else HOM_PJ(2, PROJ_GAMMA);
   } else {
@@ -173,12 +177,12 @@ template <typename T, int D>
 static void line_inv_d(const PassGeom& g, int post, const cpx<T>* S, const Fields<T>& f,
                        const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
                        Scalars* sc, const OpArgs& args, double* partials, unsigned* counter,
-                       int negate, cudaStream_t st) {
-  const unsigned grid = (unsigned)((g.nlines + g.LB - 1) / g.LB);
+                       int negate, cudaStream_t st, const ReqDesc<T>* reqs, int nreq) {
+  const dim3 grid((unsigned)((g.nlines + g.LB - 1) / g.LB), 1, (unsigned)nreq);
   const size_t sm = Ops<T>::smem_line(P.n, ncomp, g.LB);
   const bool prof = profiling();
   if (prof) prof_mark(KIND_LINE_INV, st, true);
-#define HOM_LI(POST_) k_line_inv<T, D, POST_><<<grid, kThreads, sm, st>>>(S, f, P, tw, ncomp, g.nlines, g.LB, g.scs, mat, sc, args, partials, counter, negate)
+#define HOM_LI(POST_) k_line_inv<T, D, POST_><<<grid, kThreads, sm, st>>>(S, f, P, tw, ncomp, g.nlines, g.LB, g.scs, mat, sc, args, partials, counter, negate, reqs)
   switch (post) {
     case POST_RICH: HOM_LI(POST_RICH); break;
     case POST_CG: HOM_LI(POST_CG); break;
@@ -196,20 +200,23 @@ template <typename T>
 void Ops<T>::line_inv(const PassGeom& g, int post, const cpx<T>* S, const Fields<T>& f,
                       const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
                       Scalars* sc, const OpArgs& args, double* partials, unsigned* counter,
-                      int negate, cudaStream_t st) {
+                      int negate, cudaStream_t st, const ReqDesc<T>* reqs, int nreq) {
   if (g.D == 2)
-    line_inv_d<T, 2>(g, post, S, f, P, tw, ncomp, mat, sc, args, partials, counter, negate, st);
+    line_inv_d<T, 2>(g, post, S, f, P, tw, ncomp, mat, sc, args, partials, counter, negate, st,
+                     reqs, nreq);
   else
-    line_inv_d<T, 3>(g, post, S, f, P, tw, ncomp, mat, sc, args, partials, counter, negate, st);
+    line_inv_d<T, 3>(g, post, S, f, P, tw, ncomp, mat, sc, args, partials, counter, negate, st,
+                     reqs, nreq);
 }
 
 template <typename T>
 void Ops<T>::cg_update(T* x, T* r, const T* p, const T* q, long long len, long long nodes,
                        Scalars* sc, double* partials, unsigned* counter, int grid,
-                       cudaStream_t st) {
+                       cudaStream_t st, const ReqDesc<T>* reqs, int nreq) {
   const bool prof = profiling();
   if (prof) prof_mark(KIND_VECTOR, st, true);
-  k_cg_update<T><<<grid, kThreads, 0, st>>>(x, r, p, q, len, nodes, sc, partials, counter);
+  const dim3 g3((unsigned)grid, 1, (unsigned)nreq);
+  k_cg_update<T><<<g3, kThreads, 0, st>>>(x, r, p, q, len, nodes, sc, partials, counter, reqs);
   if (prof) prof_mark(KIND_VECTOR, st, false);
   ++launch_counter();
 }

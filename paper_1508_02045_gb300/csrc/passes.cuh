@@ -208,14 +208,35 @@ struct Fields {
   long long cs;   // component stride (|N|)
 };
 
+// Per-request arguments of a batched launch (blockIdx.z selects the request): several
+// same-shape problems advance through one launch per pass, each with its own buffers,
+// coefficients, device scalars and reduction partials.
+template <typename T>
+struct ReqDesc {
+  Fields<T> ff;        // pre-operator buffers (line_fwd)
+  Fields<T> fi;        // post-operator buffers (line_inv, cg_update)
+  cpx<T>* S;           // half-spectrum work buffer
+  MatView<T> mat;
+  Scalars* sc;
+  double* partials;
+  unsigned* counter;
+};
+
 // ---------------------------------------------------------------------------------------
 // line_fwd: pre-operator + forward real DFT of the contiguous axis
 // ---------------------------------------------------------------------------------------
 template <typename T, int D, int PRE>
 __global__ void __launch_bounds__(kThreads, 2)
-k_line_fwd(Fields<T> f, cpx<T>* __restrict__ S, AxisPlan P, const cpx<T>* __restrict__ twg,
+k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
            int ncomp, long long nlines, int LB, long long scs, MatView<T> mat,
-           const Scalars* __restrict__ sc, OpArgs args) {
+           const Scalars* sc, OpArgs args, const ReqDesc<T>* __restrict__ reqs) {
+  if (reqs != nullptr) {
+    const ReqDesc<T>& R = reqs[blockIdx.z];
+    f = R.ff;
+    S = R.S;
+    mat = R.mat;
+    sc = R.sc;
+  }
   if (sc != nullptr && sc->done) return;
   const int n = P.n, nh = (n + 1) / 2;
   const int half = LB / 2;
@@ -318,8 +339,13 @@ k_line_fwd(Fields<T> f, cpx<T>* __restrict__ S, AxisPlan P, const cpx<T>* __rest
 // ---------------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 2)
-k_strided(cpx<T>* __restrict__ S, AxisPlan P, const cpx<T>* __restrict__ twg, long long C,
-          long long es, long long bs, int TC, int TCp, int inv, const Scalars* __restrict__ sc) {
+k_strided(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, long long C,
+          long long es, long long bs, int TC, int TCp, int inv, const Scalars* sc,
+          const ReqDesc<T>* __restrict__ reqs) {
+  if (reqs != nullptr) {
+    S = reqs[blockIdx.z].S;
+    sc = reqs[blockIdx.z].sc;
+  }
   if (sc != nullptr && sc->done) return;
   const int n = P.n;
   cpx<T>* sm = smem_c<T>();
@@ -355,8 +381,12 @@ struct ProjGeom {
 
 template <typename T, int D, int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
-k_proj(cpx<T>* __restrict__ S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC,
-       int TCp, const Scalars* __restrict__ sc) {
+k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC,
+       int TCp, const Scalars* sc, const ReqDesc<T>* __restrict__ reqs) {
+  if (reqs != nullptr) {
+    S = reqs[blockIdx.z].S;
+    sc = reqs[blockIdx.z].sc;
+  }
   if (sc != nullptr && sc->done) return;
   const int n = P.n;
   cpx<T>* sm = smem_c<T>();
@@ -444,9 +474,19 @@ k_proj(cpx<T>* __restrict__ S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjG
 // ---------------------------------------------------------------------------------------
 template <typename T, int D, int POST>
 __global__ void __launch_bounds__(kThreads, 2)
-k_line_inv(const cpx<T>* __restrict__ S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ twg,
+k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ twg,
            int ncomp, long long nlines, int LB, long long scs, MatView<T> mat, Scalars* sc,
-           OpArgs args, double* partials, unsigned* counter, int negate) {
+           OpArgs args, double* partials, unsigned* counter, int negate,
+           const ReqDesc<T>* __restrict__ reqs) {
+  if (reqs != nullptr) {
+    const ReqDesc<T>& R = reqs[blockIdx.z];
+    f = R.fi;
+    S = R.S;
+    mat = R.mat;
+    sc = R.sc;
+    partials = R.partials;
+    counter = R.counter;
+  }
   if (sc != nullptr && sc->done) return;
   const int n = P.n, nh = (n + 1) / 2;
   const int half = LB / 2;
@@ -652,9 +692,18 @@ k_line_inv(const cpx<T>* __restrict__ S, Fields<T> f, AxisPlan P, const cpx<T>* 
 // ---------------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
-            const T* __restrict__ q, long long len, long long nodes, Scalars* sc,
-            double* partials, unsigned* counter) {
+k_cg_update(T* x, T* r, const T* p, const T* q, long long len, long long nodes, Scalars* sc,
+            double* partials, unsigned* counter, const ReqDesc<T>* __restrict__ reqs) {
+  if (reqs != nullptr) {
+    const ReqDesc<T>& R = reqs[blockIdx.z];
+    x = R.fi.x;
+    r = R.fi.r;
+    p = R.fi.p;
+    q = R.fi.out;
+    sc = R.sc;
+    partials = R.partials;
+    counter = R.counter;
+  }
   if (sc->done) return;
   const T alpha = (T)sc->alpha;
   DotAcc<T> dacc;

@@ -1,0 +1,338 @@
+// Internal definitions shared by the host translation units of libhom (hom_api.cu,
+// hom_serve.cu): launch planning, the per-precision engine, the problem handle and the
+// solver-session helpers. Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <vector>
+
+#include "../../include/hom.h"
+#include "ops.h"
+#include "passes.cuh"
+
+namespace hom {
+namespace detail {
+
+constexpr long long kMaxNodes = 1LL << 31;
+
+#define HOM_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) {                            \
+      last_cuda_error() = e_;                           \
+      return e_ == cudaErrorMemoryAllocation ? HOM_ERR_OOM : HOM_ERR_CUDA; \
+    }                                                   \
+  } while (0)
+
+cudaError_t& last_cuda_error();
+
+// ---------------------------------------------------------------------------------------
+// planning
+// ---------------------------------------------------------------------------------------
+// Radix plan of one axis: the prime factors of n (all <= 31) grouped into register radices of
+// at most rmax (first fit, largest factors first), as few stages as possible.
+inline bool plan_axis(int n, int rmax, AxisPlan* P) {
+  if (n < 3 || n > kMaxAxis || n % 2 == 0) return false;
+  std::vector<int> primes;
+  int rem = n;
+  for (int R : {31, 29, 23, 19, 17, 13, 11, 7, 5, 3})
+    while (rem % R == 0) {
+      primes.push_back(R);
+      rem /= R;
+    }
+  if (rem != 1) return false;
+  std::vector<int> groups;
+  for (int f : primes) {
+    int best = -1;
+    for (size_t gi = 0; gi < groups.size(); ++gi)
+      if (groups[gi] * f <= rmax && (best < 0 || groups[gi] > groups[best])) best = (int)gi;
+    if (best >= 0) groups[best] *= f;
+    else groups.push_back(f);
+  }
+  if ((int)groups.size() > kMaxStages) return false;
+  std::sort(groups.begin(), groups.end(), [](int a, int b) { return a > b; });
+  P->n = n;
+  P->nst = (int)groups.size();
+  int p = 1;
+  for (int s = 0; s < kMaxStages; ++s) {
+    if (s < P->nst) {
+      P->radix[s] = groups[s];
+      P->pprev[s] = p;
+      p *= groups[s];
+    } else {
+      P->radix[s] = P->pprev[s] = 0;
+    }
+  }
+  plan_fastdivs(P);
+  return true;
+}
+
+// largest register radix per precision (FP64 values take twice the registers)
+template <typename T> constexpr int reg_rmax() { return sizeof(T) == 8 ? 15 : 27; }
+
+template <typename T>
+std::vector<cpx<T>> twiddles(int n) {
+  std::vector<cpx<T>> tw(n);
+  const long double twopi = 6.283185307179586476925286766559005768L;
+  for (int j = 0; j < n; ++j) {
+    const long double t = -twopi * (long double)j / (long double)n;
+    tw[j].x = (T)cosl(t);
+    tw[j].y = (T)sinl(t);
+  }
+  return tw;
+}
+
+// Largest even LB (lines per CTA in the line passes) whose buffers fit the budget.
+template <typename T>
+int pick_LB(int n, int ncomp, size_t budget) {
+  int LB = 16;
+  while (LB > 2 && Ops<T>::smem_line(n, ncomp, LB) > budget) LB -= 2;
+  return LB;
+}
+
+// columns per CTA of a column pass: the widest tile (<= 32 columns, 128-byte rows for FP32 at
+// 16) whose shared-memory buffers fit the budget; odd pitch for conflict-free column access
+template <typename T>
+void pick_TC(int n, int nst, size_t budget, int* TC, int* TCp, bool proj, int D) {
+  int tc = 32;
+  auto need = [&](int t) {
+    const int tp = t + ((t % 2 == 0) ? 1 : 0);
+    return proj ? Ops<T>::smem_proj(n, D, tp) : Ops<T>::smem_strided(n, tp, nst);
+  };
+  while (tc > 2 && need(tc) > budget) tc /= 2;
+  *TC = tc;
+  *TCp = tc + ((tc % 2 == 0) ? 1 : 0);
+}
+
+// ---------------------------------------------------------------------------------------
+// per-precision engine: plans, twiddles, geometry, spectrum buffer view
+// ---------------------------------------------------------------------------------------
+template <typename T>
+struct Engine {
+  PassGeom g{};
+  PassGeom g1{};  // same grid, one component (Ga assembly)
+  AxisPlan plan[3]{};
+  cpx<T>* tw[3] = {nullptr, nullptr, nullptr};
+  ProjGeom pg{};
+  MatView<T> mat{};
+  T* field = nullptr;  // MAT_FIELD storage in precision T
+  T* table = nullptr;  // phase table in precision T
+  bool ready = false;
+
+  int init(int D, const int* n, const int* support, size_t budget) {
+    g.D = D;
+    g.nodes = 1;
+    for (int a = 0; a < D; ++a) {
+      g.n[a] = n[a];
+      g.nodes *= n[a];
+      int rmax = reg_rmax<T>();
+      if (const char* e = getenv(sizeof(T) == 4 ? "HOM_RMAX32" : "HOM_RMAX64")) rmax = atoi(e);
+      if (!plan_axis(n[a], rmax, &plan[a])) return HOM_ERR_INVALID;
+    }
+    for (int a = D; a < 3; ++a) g.n[a] = 1;
+    const int nl = n[D - 1];
+    g.nh = (nl + 1) / 2;
+    g.nlines = g.nodes / nl;
+    g.scs = g.nlines * g.nh;
+    g.LB = pick_LB<T>(nl, D, budget);
+    if (D == 3) pick_TC<T>(n[1], plan[1].nst, budget, &g.TC1, &g.TC1p, false, D);
+    pick_TC<T>(n[0], plan[0].nst, budget, &g.TC0, &g.TC0p, true, D);
+    pick_TC<T>(n[0], plan[0].nst, budget, &g.TCs0, &g.TCs0p, false, D);
+    g1 = g;
+    g1.LB = pick_LB<T>(nl, 1, budget);
+    for (int a = 0; a < D; ++a) {
+      auto tw_h = twiddles<T>(n[a]);
+      if (cudaMalloc(&tw[a], sizeof(cpx<T>) * n[a]) != cudaSuccess) return HOM_ERR_OOM;
+      if (cudaMemcpy(tw[a], tw_h.data(), sizeof(cpx<T>) * n[a], cudaMemcpyHostToDevice) != cudaSuccess)
+        return HOM_ERR_CUDA;
+    }
+    pg.C = g.scs / n[0];
+    pg.cs = g.scs;
+    pg.n1 = (D == 3) ? n[1] : 1;
+    pg.nh = g.nh;
+    for (int a = 0; a < 3; ++a) pg.hw[a] = (a < D) ? (support[a] - 1) / 2 : 0;
+    pg.scale = 1.0 / (double)g.nodes;
+    // every pass must fit the per-CTA shared-memory limit
+    const size_t cap = (size_t)dynamic_smem_cap();
+    if (Ops<T>::smem_line(nl, D, g.LB) > cap || Ops<T>::smem_proj(n[0], D, g.TC0p) > cap ||
+        (D == 3 && Ops<T>::smem_strided(n[1], g.TC1p, plan[1].nst) > cap) ||
+        Ops<T>::smem_strided(n[0], g.TCs0p, plan[0].nst) > cap)
+      return HOM_ERR_UNSUPPORTED;
+    ready = true;
+    return HOM_OK;
+  }
+
+  void release() {
+    for (auto& t : tw) {
+      if (t) cudaFree(t);
+      t = nullptr;
+    }
+    if (field) cudaFree(field);
+    field = nullptr;
+    if (table) cudaFree(table);
+    table = nullptr;
+  }
+
+  // forward transform of the contiguous axis and the middle axis (D = 3) up to axis 0
+  // y = post( F^{-1} proj F pre(x) ): one full operator application
+  void apply(int pre, int mode, int post, const Fields<T>& f, cpx<T>* S, Scalars* sc,
+             const OpArgs& args, double* partials, unsigned* counter, int negate,
+             cudaStream_t st) const {
+    apply2(pre, mode, post, f, f, S, sc, args, partials, counter, negate, st);
+  }
+
+  // same, with separate buffer sets for the pre-operator (ff) and the post-operator (fi)
+  void apply2(int pre, int mode, int post, const Fields<T>& ff, const Fields<T>& fi, cpx<T>* S,
+              Scalars* sc, const OpArgs& args, double* partials, unsigned* counter, int negate,
+              cudaStream_t st) const {
+    Ops<T>::line_fwd(g, pre, ff, S, plan[g.D - 1], tw[g.D - 1], g.D, mat, sc, args, st);
+    if (g.D == 3) Ops<T>::strided(g, 1, 0, S, plan[1], tw[1], g.D, sc, st);
+    Ops<T>::proj(g, mode, S, plan[0], tw[0], pg, sc, st);
+    if (g.D == 3) Ops<T>::strided(g, 1, 1, S, plan[1], tw[1], g.D, sc, st);
+    Ops<T>::line_inv(g, post, S, fi, plan[g.D - 1], tw[g.D - 1], g.D, mat, sc, args, partials,
+                     counter, negate, st);
+  }
+
+  // one batched application over the requests of `reqs` (device array of n descriptors that
+  // supply buffers, coefficients, scalars and partials); geometry and plans are shared
+  void apply_batch(int pre, int mode, int post, const ReqDesc<T>* reqs, int n,
+                   cudaStream_t st) const {
+    Fields<T> f{};
+    OpArgs args{};
+    Ops<T>::line_fwd(g, pre, f, nullptr, plan[g.D - 1], tw[g.D - 1], g.D, mat, nullptr, args, st,
+                     reqs, n);
+    if (g.D == 3) Ops<T>::strided(g, 1, 0, nullptr, plan[1], tw[1], g.D, nullptr, st, reqs, n);
+    Ops<T>::proj(g, mode, nullptr, plan[0], tw[0], pg, nullptr, st, reqs, n);
+    if (g.D == 3) Ops<T>::strided(g, 1, 1, nullptr, plan[1], tw[1], g.D, nullptr, st, reqs, n);
+    Ops<T>::line_inv(g, post, nullptr, f, plan[g.D - 1], tw[g.D - 1], g.D, mat, nullptr, args,
+                     nullptr, nullptr, 0, st, reqs, n);
+  }
+
+  // plain forward transform (no projection), result is the unscaled half spectrum
+  void forward(const T* x, cpx<T>* S, int ncomp, cudaStream_t st) const {
+    const PassGeom& gg = (ncomp == 1) ? g1 : g;
+    Fields<T> f{};
+    f.xin = x;
+    f.cs = g.nodes;
+    OpArgs args{};
+    Ops<T>::line_fwd(gg, PRE_IDENT, f, S, plan[g.D - 1], tw[g.D - 1], ncomp, mat, nullptr, args, st);
+    if (g.D == 3) Ops<T>::strided(gg, 1, 0, S, plan[1], tw[1], ncomp, nullptr, st);
+    Ops<T>::strided(gg, 0, 0, S, plan[0], tw[0], ncomp, nullptr, st);
+  }
+
+  // plain inverse transform (no scaling) of a half spectrum into real fields
+  void inverse(cpx<T>* S, T* y, int ncomp, cudaStream_t st) const {
+    const PassGeom& gg = (ncomp == 1) ? g1 : g;
+    Ops<T>::strided(gg, 0, 1, S, plan[0], tw[0], ncomp, nullptr, st);
+    if (g.D == 3) Ops<T>::strided(gg, 1, 1, S, plan[1], tw[1], ncomp, nullptr, st);
+    Fields<T> f{};
+    f.out = y;
+    f.cs = g.nodes;
+    OpArgs args{};
+    Ops<T>::line_inv(gg, POST_STORE, S, f, plan[g.D - 1], tw[g.D - 1], ncomp, mat, nullptr, args,
+                     nullptr, nullptr, 0, st);
+  }
+};
+
+size_t smem_budget();
+int alloc(void** p, size_t bytes);
+int check_last();
+bool spd_eigs(const double* t, int d, double* lo, double* hi);
+
+}  // namespace detail
+}  // namespace hom
+
+struct SolveState {
+  bool active = false;
+  int solver = 0;
+  int stop = 0;
+  bool fixed = false;
+  int maxit = 0;
+  int check = 8;
+  int issued = 0;
+  int matvecs = 0;
+  double E[3] = {0, 0, 0};
+  double nE = 0;
+  // iterative refinement (HOM_FP32_REFINED): FP32 inner solves of C d = r, FP64 outer residual
+  bool refined = false;
+  double tol = 0;
+  double inner_tol = 1e-4;
+  int inner_maxit = 10000;
+  int outer_it = 0;
+  int inner_total = 0;
+  double nb = 0;         // ||b|| (FP64)
+  double res = 0;        // ||b - C x|| (FP64) after the last outer update
+  bool finished = false;
+  bool converged = false;
+  float inner_ms = 0;
+};
+
+struct hom_problem {
+  int d = 0;
+  int N[3] = {1, 1, 1};     // trigonometric order
+  int M[3] = {1, 1, 1};     // solve grid (N for GaNi, double grid for Ga)
+  int integration = HOM_APPROX;
+  int precision = HOM_FP64;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  long long nodes = 0;
+  double cA = 0, CA = 0;
+
+  // coefficients
+  int mat_kind = hom::MAT_PHASE_ISO;
+  void* d_phase = nullptr;
+  int index_bytes = 1;
+  double* d_table = nullptr;
+  int nphase = 0;
+
+  hom::detail::Engine<double> e64;
+  hom::detail::Engine<float> e32;
+
+  // buffers
+  void* S = nullptr;              // half spectrum work buffer (sized for FP64, d components)
+  size_t S_bytes = 0;
+  double* vbase = nullptr;        // one allocation of 5 d |grid| doubles
+  double* vec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // d x |grid| each
+  float* fvec[4] = {nullptr, nullptr, nullptr, nullptr};           // FP32 inner solves
+  double* partials = nullptr;
+  size_t npartials = 0;
+  unsigned* counter = nullptr;
+  hom::Scalars* d_sc = nullptr;        // solver scalars
+  hom::Scalars* d_aux = nullptr;       // scalars of auxiliary evaluations (energy, true residual)
+  hom::Scalars* d_sc2 = nullptr;       // scalars of the FP32 inner solves (refinement)
+  hom::Scalars* h_sc = nullptr;        // pinned host mirror
+  int red_grid = 0;               // grid of the reduction kernels
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  SolveState sv;
+};
+
+namespace hom {
+namespace detail {
+
+template <typename T>
+MatView<T> make_view(const hom_problem* P, const T* field, const T* table) {
+  MatView<T> m{};
+  m.kind = P->mat_kind;
+  m.ph8 = (P->mat_kind != MAT_FIELD && P->index_bytes == 1) ? (const uint8_t*)P->d_phase : nullptr;
+  m.ph16 = (P->mat_kind != MAT_FIELD && P->index_bytes == 2) ? (const uint16_t*)P->d_phase : nullptr;
+  m.table = table;
+  m.field = field;
+  return m;
+}
+
+
+// solver sessions (hom_api.cu)
+int poll(hom_problem* P, Scalars* dst);
+int upload_scalars(hom_problem* P, Scalars* dst, const Scalars& s);
+int energy_eval(hom_problem* P, const double* E, const double* x, double* en, double* flux);
+double true_residual(hom_problem* P, const double* E, const double* x, double* y);
+int solve_stop_mode(int solver, int stop);
+void enqueue_step(hom_problem* P);
+void refine_enqueue_inner(hom_problem* P);
+int refine_outer_update(hom_problem* P);
+
+}  // namespace detail
+}  // namespace hom
