@@ -338,6 +338,93 @@ def run_ours(args, rank, world, local):
     return line
 
 
+# ------------------------------------------------------------------------------------------
+# served mix (continuous batching): FP32 inner solves with FP64 refinement vs plain FP64
+# ------------------------------------------------------------------------------------------
+
+def served_requests(n_req, seed=2024):
+    """Seeded heterogeneous requests: odd grids from {45, 81, 135, 243}^3, periodic random
+    spheres (volume fraction U[0.1, 0.4]), contrast logU[10, 1e4], anisotropic SPD phase
+    tensors R diag(lambda) R^T (Haar R, lambda = scale x logU[1, 3], scale 1 for the matrix and
+    the contrast for every sphere), random unit E, CG or Chebyshev, tolerance 1e-6."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    grids = [45, 81, 135, 243]
+    probs = [0.35, 0.35, 0.2, 0.1]
+    for i in range(n_req):
+        n = int(rng.choice(grids, p=probs))
+        vf = rng.uniform(0.1, 0.4)
+        contrast = float(np.exp(rng.uniform(np.log(10.0), np.log(1e4))))
+        ph, _, radii = ms.rsa_spheres((n,) * 3, seed + i, rmin=0.04, rmax=0.1, vf=vf)
+        scales = np.concatenate([[1.0], np.full(len(radii), contrast)])
+        table = ms.random_spd_table(len(scales), 3, seed + 1000 + i, scales)
+        E = ms.random_unit_vector(3, seed + 2000 + i)
+        solver = "cg" if rng.random() < 0.5 else "chebyshev"
+        reqs.append({"n": n, "phase": ph, "table": table, "E": E, "solver": solver,
+                     "contrast": contrast, "vf": float((ph > 0).mean())})
+    return reqs
+
+
+def run_served(args):
+    import torch
+    import paper_1508_02045_gb300 as H
+
+    reqs = served_requests(args.serve)
+    rng = np.random.default_rng(7)
+    arrivals = np.cumsum(rng.exponential(args.serve_window / len(reqs), size=len(reqs)))
+    out = {}
+    for label, prec in (("fp64", H.HOM_FP64), ("fp32_refined", H.HOM_FP32_REFINED)):
+        S = H.hom_server_create(int(args.serve_budget_gb * (1 << 30)), max_batch=8)
+        mats = [H.phase_material(r["phase"], r["table"]) for r in reqs]
+        submitted, results = {}, {}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nxt = 0
+        steps = 0
+        while len(results) < len(reqs):
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and arrivals[nxt] <= now:
+                r = reqs[nxt]
+                q = H.make_request(3, (r["n"],) * 3, mats[nxt], r["E"], H.SOLVERS[r["solver"]],
+                                   1e-6, precision=prec, opts=H.make_opts(maxit=3000 if prec == H.HOM_FP64 else 50))
+                submitted[H.hom_server_submit(S, q)] = nxt
+                nxt += 1
+            active, queued, _ = H.hom_server_status(S)
+            if active == 0 and queued == 0:
+                if nxt < len(reqs):
+                    time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+                continue
+            H.hom_server_step(S, 8)
+            steps += 1
+            for res in H.hom_server_poll(S):
+                results[submitted[res["id"]]] = res
+        wall = time.perf_counter() - t0
+        H.hom_server_destroy(S)
+        lat = np.array([results[i]["latency_ms"] for i in range(len(reqs))])
+        out[label] = {"solves_per_s": round(len(reqs) / (wall - arrivals[0]), 3),
+                      "p50_ms": round(float(np.percentile(lat, 50)), 1),
+                      "p99_ms": round(float(np.percentile(lat, 99)), 1),
+                      "wall_s": round(wall, 2), "steps": steps,
+                      "converged": int(sum(results[i]["stats"]["converged"] for i in range(len(reqs)))),
+                      "AH": [results[i]["AH_EE"] for i in range(len(reqs))]}
+    a64 = np.array(out["fp64"].pop("AH"))
+    a32 = np.array(out["fp32_refined"].pop("AH"))
+    line = {"metric": "served solves/s (continuous batching, FP32 inner + FP64 refinement)",
+            "value": out["fp32_refined"]["solves_per_s"], "unit": "solves/s",
+            "higher_is_better": True, "n_gpus": 1, "dtype": "f32 inner / f64 outer",
+            "data": "synthetic (seeded random-sphere microstructures)",
+            "config": {"workload": "served mix: grids {45,81,135,243}^3, RSA spheres vf 0.1-0.4, "
+                                   "contrast logU[10,1e4], anisotropic SPD phases, CG/Chebyshev, tol 1e-6",
+                       "requests": len(reqs), "arrival_window_s": args.serve_window,
+                       "hbm_budget_gb": args.serve_budget_gb, "max_batch": 8,
+                       "grid_counts": {str(g): int(sum(r["n"] == g for r in reqs)) for g in (45, 81, 135, 243)}},
+            "p50_ms": out["fp32_refined"]["p50_ms"], "p99_ms": out["fp32_refined"]["p99_ms"],
+            "fp32_refined": out["fp32_refined"], "fp64": out["fp64"],
+            "speedup_vs_fp64": round(out["fp32_refined"]["solves_per_s"] / out["fp64"]["solves_per_s"], 2),
+            "AH_max_rel_diff_fp32_refined_vs_fp64": float(np.max(np.abs(a32 - a64) / np.abs(a64)))}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -369,9 +456,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--grid", type=int, default=0)
+    ap.add_argument("--serve", type=int, default=0, help="run the served mix with this many requests")
+    ap.add_argument("--serve-window", type=float, default=1.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.serve:
+        run_served(args)
+        return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
         world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))

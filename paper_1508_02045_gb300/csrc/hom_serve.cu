@@ -585,21 +585,23 @@ extern "C" int hom_server_step(hom_server* S, int iterations) {
   if (!S || iterations < 1) return HOM_ERR_INVALID;
   int rc = admit(S);
   if (rc) return rc;
-  // one batched launch per pass and bucket
-  for (auto& b : S->buckets) {
-    bool any = false;
-    for (auto* r : b.slots) any = any || r != nullptr;
-    if (!any) continue;
+  // one batched launch per pass and bucket, then the stopping flags of its slots in one copy.
+  // Buckets without active slots are skipped entirely: their device descriptors may still
+  // name the buffers of retired (freed) requests until the next upload.
+  std::vector<char> live(S->buckets.size(), 0);
+  for (size_t bi = 0; bi < S->buckets.size(); ++bi) {
+    Bucket& b = S->buckets[bi];
+    for (auto* r : b.slots) live[bi] = live[bi] || r != nullptr;
+    if (!live[bi]) continue;
     if (b.dirty && (rc = bucket_upload(S, b))) return rc;
     if ((rc = bucket_launch(S, b, iterations))) return rc;
-  }
-  // stopping flags of every slot in one copy per bucket
-  for (auto& b : S->buckets) {
     k_gather_done<<<(b.cap + 127) / 128, 128, 0, S->stream>>>(b.d_sc, b.cap, b.d_done);
     HOM_CUDA(cudaMemcpyAsync(b.h_done, b.d_done, sizeof(int) * b.cap, cudaMemcpyDeviceToHost, S->stream));
   }
   HOM_CUDA(cudaStreamSynchronize(S->stream));
-  for (auto& b : S->buckets) {
+  for (size_t bi = 0; bi < S->buckets.size(); ++bi) {
+    if (!live[bi]) continue;
+    Bucket& b = S->buckets[bi];
     for (int i = 0; i < b.cap; ++i) {
       ServerReq* r = b.slots[i];
       if (!r) continue;

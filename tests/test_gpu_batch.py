@@ -115,3 +115,34 @@ def test_server_results_equal_solo_solves():
         assert r["stats"]["iterations"] == st["iterations"]
         assert abs(r["AH_EE"] - AH_ref) <= 1e-14 * abs(AH_ref), (solver, prec, N)
         assert r["latency_ms"] >= r["queue_ms"] >= 0
+
+
+def test_server_keeps_serving_after_a_bucket_empties():
+    # first wave drains its bucket completely; later steps must only touch live buckets
+    S = H.hom_server_create(1 << 30, max_batch=2)
+    wave1 = [(15, 15, 15)] * 2
+    wave2 = [(13, 11, 9)] * 3
+    seen = {}
+    for i, N in enumerate(wave1):
+        rid = H.hom_server_submit(S, H.make_request(3, N, material(N, 40 + i, 20.0),
+                                                    np.array([1.0, 0.0, 0.0]), H.HOM_CG, 1e-8))
+        seen[rid] = None
+    for _ in range(5000):
+        H.hom_server_step(S, 4)
+        for r in H.hom_server_poll(S):
+            seen[r["id"]] = r
+        if all(v is not None for v in seen.values()):
+            break
+    assert H.hom_server_status(S)[0] == 0
+    for i, N in enumerate(wave2):
+        rid = H.hom_server_submit(S, H.make_request(3, N, material(N, 50 + i, 20.0),
+                                                    np.array([0.0, 1.0, 0.0]), H.HOM_CHEBYSHEV, 1e-8))
+        seen[rid] = None
+    for _ in range(5000):
+        H.hom_server_step(S, 4)
+        for r in H.hom_server_poll(S):
+            seen[r["id"]] = r
+        if all(v is not None for v in seen.values()):
+            break
+    H.hom_server_destroy(S)
+    assert all(v is not None and v["status"] == H.HOM_OK for v in seen.values())

@@ -49,6 +49,19 @@ GRIDS = [(3, 3), (9, 7), (15, 15), (63, 63), (85, 85), (5, 7, 9), (15, 15, 15), 
          (45, 45, 45)]
 
 
+@pytest.mark.parametrize("N", [(135, 135, 135), (81, 81, 81), (161, 7, 9)])
+def test_operator_parity_larger_grids(N):
+    # tile geometry of the served grid sizes (135 = 27*5 / 15*9, 81, 161 = 7*23)
+    d = len(N)
+    ph, table, A = square(N, 0.6, 1.0, 10.0)
+    P = H.Problem(d, N, H.phase_material(ph, table))
+    x = ms.random_field((d,) + N, 9)
+    y = P.field()
+    H.hom_apply(P.h, H.HOM_OP_LINEAR, None, to_dev(x), y)
+    assert rel(y.cpu().numpy(), O.GaNi(A, d).matvec(x)) < OP_TOL
+    P.close()
+
+
 @pytest.mark.parametrize("N", GRIDS)
 @pytest.mark.parametrize("op", ["affine", "linear", "project", "em"])
 def test_operator_parity(N, op):
