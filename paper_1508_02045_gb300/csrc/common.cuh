@@ -39,7 +39,8 @@ inline __host__ __device__ FastDiv make_fastdiv(int d) {
 }
 
 // Radix plan of one axis of odd length n = prod radix[s]; pprev[s] = prod_{t<s} radix[t];
-// fdm[s], fdp[s] divide by n / radix[s] and by pprev[s] (computed on the host).
+// fdm[s], fdp[s] divide by n / radix[s] and by pprev[s]; fdn, fdnh by n and (n + 1) / 2
+// (all computed on the host).
 struct AxisPlan {
   int n;
   int nst;
@@ -47,6 +48,7 @@ struct AxisPlan {
   int pprev[kMaxStages];
   FastDiv fdm[kMaxStages];
   FastDiv fdp[kMaxStages];
+  FastDiv fdn, fdnh;
 };
 
 inline __host__ void plan_fastdivs(AxisPlan* P) {
@@ -54,7 +56,14 @@ inline __host__ void plan_fastdivs(AxisPlan* P) {
     P->fdm[s] = make_fastdiv(P->n / P->radix[s]);
     P->fdp[s] = make_fastdiv(P->pprev[s]);
   }
+  P->fdn = make_fastdiv(P->n);
+  P->fdnh = make_fastdiv((P->n + 1) / 2);
 }
+
+// divisors of the line-pass loops (lines per CTA and its half), computed on the host
+struct LineDiv {
+  FastDiv lb, half;
+};
 
 // Scalars of one solve, resident on the device so that a captured iteration replays without
 // host round trips. Written by the reduction finishers, read by every kernel of a step.

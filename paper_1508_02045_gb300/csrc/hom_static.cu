@@ -241,6 +241,7 @@ extern "C" int hom_apply_static(int d, const int* N, const void* phase_dev, int 
   pg.cs = g.scs;
   pg.n1 = d == 3 ? N[1] : 1;
   pg.nh = g.nh;
+  pg.fdnh = make_fastdiv(g.nh);
   for (int a = 0; a < 3; ++a) pg.hw[a] = a < d ? (N[a] - 1) / 2 : 0;
   pg.scale = 1.0 / (double)g.nodes;
   OpArgs args{};

@@ -102,7 +102,7 @@ static void line_fwd_d(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S
   const size_t sm = Ops<T>::smem_line(P.n, ncomp, g.LB);
   const bool prof = profiling();
   if (prof) prof_mark(KIND_LINE_FWD, st, true);
-#define HOM_LF(PRE_) k_line_fwd<T, D, PRE_><<<grid, kThreads, sm, st>>>(f, S, P, tw, ncomp, g.nlines, g.LB, g.scs, mat, sc, args, reqs)
+#define HOM_LF(PRE_) k_line_fwd<T, D, PRE_><<<grid, kThreads, sm, st>>>(f, S, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, reqs)
   switch (pre) {
     case PRE_AFFINE: HOM_LF(PRE_AFFINE); break;
     case PRE_LINEAR: HOM_LF(PRE_LINEAR); break;
@@ -182,7 +182,7 @@ static void line_inv_d(const PassGeom& g, int post, const cpx<T>* S, const Field
   const size_t sm = Ops<T>::smem_line(P.n, ncomp, g.LB);
   const bool prof = profiling();
   if (prof) prof_mark(KIND_LINE_INV, st, true);
-#define HOM_LI(POST_) k_line_inv<T, D, POST_><<<grid, kThreads, sm, st>>>(S, f, P, tw, ncomp, g.nlines, g.LB, g.scs, mat, sc, args, partials, counter, negate, reqs)
+#define HOM_LI(POST_) k_line_inv<T, D, POST_><<<grid, kThreads, sm, st>>>(S, f, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, counter, negate, reqs)
   switch (post) {
     case POST_RICH: HOM_LI(POST_RICH); break;
     case POST_CG: HOM_LI(POST_CG); break;

@@ -228,7 +228,7 @@ struct ReqDesc {
 template <typename T, int D, int PRE>
 __global__ void __launch_bounds__(kThreads, 2)
 k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
-           int ncomp, long long nlines, int LB, long long scs, MatView<T> mat,
+           int ncomp, long long nlines, int LB, LineDiv ld, long long scs, MatView<T> mat,
            const Scalars* sc, OpArgs args, const ReqDesc<T>* __restrict__ reqs) {
   if (reqs != nullptr) {
     const ReqDesc<T>& R = reqs[blockIdx.z];
@@ -262,7 +262,7 @@ k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int idx = base + k * blockDim.x + threadIdx.x;
-      const int ll = idx / n, j = idx - ll * n;
+      const int ll = fdiv(idx, P.fdn), j = idx - ll * n;
       const long long l = l0 + ll;
       const bool ok = idx < LB * n && l < nlines;
       const long long g = l * n + j;
@@ -277,7 +277,7 @@ k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
     for (int k = 0; k < K; ++k) {
       const int idx = base + k * blockDim.x + threadIdx.x;
       if (idx >= LB * n) continue;
-      const int ll = idx / n, j = idx - ll * n;
+      const int ll = fdiv(idx, P.fdn), j = idx - ll * n;
       const long long l = l0 + ll;
       const bool ok = l < nlines;
       const long long g = l * n + j;
@@ -319,8 +319,8 @@ k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
   __syncthreads();
   const int res = reg_lines<T>(b0, b1, &Ps, nlc, n, 1, false, false, 0);
   for (int idx = threadIdx.x; idx < nlc * nh; idx += blockDim.x) {
-    const int lc = idx / nh, k = idx - lc * nh;
-    const int a = lc / half, pr = lc - a * half;
+    const int lc = fdiv(idx, P.fdnh), k = idx - lc * nh;
+    const int a = fdiv(lc, ld.half), pr = lc - a * half;
     const cpx<T> zk = sm[res + lc * n + k];
     const cpx<T> zm = sm[res + lc * n + (k ? n - k : 0)];
     cpx<T> A, B;
@@ -357,11 +357,13 @@ k_strided(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, long long C,
   const int ncols = (int)min((long long)TC, C - c0);
   cpx<T>* base = S + (long long)blockIdx.y * bs + c0;
   const int ges = (int)es;
-  // stage the whole tile with asynchronous copies (all rows in flight at once)
-  for (int idx = threadIdx.x; idx < n * ncols; idx += blockDim.x) {
-    const int j = idx / ncols, c = idx - j * ncols;
-    cp_async_elem<T>(sm + b0 + j * TCp + c, base + j * ges + c);
-  }
+  // stage the whole tile with asynchronous copies (all rows in flight at once); TC is a power
+  // of two dividing the block, so every thread keeps one column c
+  const int tcl = __ffs(TC) - 1;
+  const int c = threadIdx.x & (TC - 1);
+  if (c < ncols)
+    for (int j = threadIdx.x >> tcl; j < n; j += blockDim.x >> tcl)
+      cp_async_elem<T>(sm + b0 + j * TCp + c, base + j * ges + c);
   cp_async_wait_all();
   __syncthreads();
   reg_columns_out<T>(b0, b1, base, ges, ncols, TCp, &Ps, inv != 0, 0);
@@ -375,6 +377,7 @@ struct ProjGeom {
   long long cs;   // component stride of the spectrum
   int n1;         // middle axis length (D = 3), 1 otherwise
   int nh;         // half length of the last axis
+  FastDiv fdnh;   // division by nh
   int hw[3];      // support half-widths: keep |k_a| <= hw[a] (Z_N inside Z_M); else zero
   double scale;   // 1/|grid| of the forward transform (eq. (DFT))
 };
@@ -399,13 +402,15 @@ k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC
   const long long c0 = (long long)blockIdx.x * TC;
   const int es = (int)g.C;
   const int ncols = (int)min((long long)TC, g.C - c0);
-  // stage the tiles of all components with asynchronous copies
-  for (int idx = threadIdx.x; idx < D * n * ncols; idx += blockDim.x) {
-    const int a = idx / (n * ncols);
-    const int rem = idx - a * n * ncols;
-    const int j = rem / ncols, c = rem - j * ncols;
-    cp_async_elem<T>(sm + n + a * n * TCp + j * TCp + c, S + a * g.cs + c0 + j * es + c);
-  }
+  // stage the tiles of all components with asynchronous copies; TC is a power of two dividing
+  // the block, so every thread keeps one column c
+  const int tcl = __ffs(TC) - 1;
+  const int c = threadIdx.x & (TC - 1);
+  if (c < ncols)
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      for (int j = threadIdx.x >> tcl; j < n; j += blockDim.x >> tcl)
+        cp_async_elem<T>(sm + n + a * n * TCp + j * TCp + c, S + a * g.cs + c0 + j * es + c);
   cp_async_wait_all();
   __syncthreads();
   int spare = buf[D];
@@ -418,19 +423,23 @@ k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC
     }
   }
   const T scale = (T)g.scale;
-  for (int idx = threadIdx.x; idx < n * ncols; idx += blockDim.x) {
-    const int j = idx / ncols, c = idx - j * ncols;
-    const long long cc = c0 + c;
+  // frequencies of this thread's column (fixed over the rows)
+  int kc1 = 0, kc2 = 0;
+  {
+    const int cc = (int)(c0 + c);
+    if (D == 3) {
+      const int i1 = fdiv(cc, g.fdnh);
+      kc1 = (i1 <= (g.n1 - 1) / 2) ? i1 : i1 - g.n1;
+      kc2 = cc - i1 * g.nh;
+    } else {
+      kc1 = cc;
+    }
+  }
+  for (int j = threadIdx.x >> tcl; c < ncols && j < n; j += blockDim.x >> tcl) {
     int k[3];
     k[0] = (j <= (n - 1) / 2) ? j : j - n;
-    if (D == 3) {
-      const int i1 = (int)(cc / g.nh);
-      k[1] = (i1 <= (g.n1 - 1) / 2) ? i1 : i1 - g.n1;
-      k[2] = (int)(cc - (long long)i1 * g.nh);
-    } else {
-      k[1] = (int)cc;
-      k[2] = 0;
-    }
+    k[1] = kc1;
+    k[2] = kc2;
     bool inside = true;
     int kk = 0;
 #pragma unroll
@@ -475,8 +484,8 @@ k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC
 template <typename T, int D, int POST>
 __global__ void __launch_bounds__(kThreads, 2)
 k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ twg,
-           int ncomp, long long nlines, int LB, long long scs, MatView<T> mat, Scalars* sc,
-           OpArgs args, double* partials, unsigned* counter, int negate,
+           int ncomp, long long nlines, int LB, LineDiv ld, long long scs, MatView<T> mat,
+           Scalars* sc, OpArgs args, double* partials, unsigned* counter, int negate,
            const ReqDesc<T>* __restrict__ reqs) {
   if (reqs != nullptr) {
     const ReqDesc<T>& R = reqs[blockIdx.z];
@@ -500,8 +509,8 @@ k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ 
   const cpx<T> zero = {0, 0};
   // stage the half spectra of the CTA's lines (contiguous per line) asynchronously
   for (int idx = threadIdx.x; idx < ncomp * LB * nh; idx += blockDim.x) {
-    const int al = idx / nh, k = idx - al * nh;
-    const int a = al / LB, ll = al - a * LB;
+    const int al = fdiv(idx, P.fdnh), k = idx - al * nh;
+    const int a = fdiv(al, ld.lb), ll = al - a * LB;
     if (l0 + ll < nlines) cp_async_elem<T>(sm + b1 + idx, S + a * scs + (l0 + ll) * nh + k);
     else sm[b1 + idx] = zero;
   }
@@ -509,8 +518,8 @@ k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ 
   __syncthreads();
   // pack two Hermitian half spectra (lines 2 pr, 2 pr + 1) into one complex line
   for (int idx = threadIdx.x; idx < nlc * nh; idx += blockDim.x) {
-    const int lc = idx / nh, k = idx - lc * nh;
-    const int a = lc / half, pr = lc - a * half;
+    const int lc = fdiv(idx, P.fdnh), k = idx - lc * nh;
+    const int a = fdiv(lc, ld.half), pr = lc - a * half;
     const cpx<T> A = sm[b1 + (a * LB + 2 * pr) * nh + k];
     const cpx<T> B = sm[b1 + (a * LB + 2 * pr + 1) * nh + k];
     const int line = b0 + lc * n;
@@ -544,7 +553,7 @@ k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ 
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int idx = base + k * blockDim.x + threadIdx.x;
-      const int ll = idx / n, j = idx - ll * n;
+      const int ll = fdiv(idx, P.fdn), j = idx - ll * n;
       const bool ok = idx < LB * n && l0 + ll < nlines;
       const long long g = (l0 + ll) * n + j;
 #pragma unroll
@@ -559,7 +568,7 @@ k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ 
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int idx = base + k * blockDim.x + threadIdx.x;
-      const int ll = idx / n, j = idx - ll * n;
+      const int ll = fdiv(idx, P.fdn), j = idx - ll * n;
       if (idx >= LB * n || l0 + ll >= nlines) continue;
       const long long g = (l0 + ll) * n + j;
       T y[D];
@@ -707,12 +716,33 @@ k_cg_update(T* x, T* r, const T* p, const T* q, long long len, long long nodes, 
   if (sc->done) return;
   const T alpha = (T)sc->alpha;
   DotAcc<T> dacc;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
-       i += (long long)gridDim.x * blockDim.x) {
-    x[i] += alpha * p[i];
-    const T rn = r[i] - alpha * q[i];
-    r[i] = rn;
-    dacc.add(rn, rn);
+  // restrict-qualified copies: the four vectors never alias, so loads can run ahead of stores
+  T* __restrict__ xr = x;
+  T* __restrict__ rr = r;
+  const T* __restrict__ pr = p;
+  const T* __restrict__ qr = q;
+  constexpr int K = 4;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < len; i0 += K * stride) {
+    T xv[K], rv[K], pv[K], qv[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const long long i = i0 + k * stride;
+      const bool ok = i < len;
+      xv[k] = ok ? xr[i] : (T)0;
+      rv[k] = ok ? rr[i] : (T)0;
+      pv[k] = ok ? pr[i] : (T)0;
+      qv[k] = ok ? qr[i] : (T)0;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const long long i = i0 + k * stride;
+      if (i >= len) continue;
+      xr[i] = xv[k] + alpha * pv[k];
+      const T rn = rv[k] - alpha * qv[k];
+      rr[i] = rn;
+      dacc.add(rn, rn);
+    }
   }
   double acc[1] = {dacc.value()};
   double tot[1];

@@ -153,6 +153,7 @@ struct Engine {
     pg.cs = g.scs;
     pg.n1 = (D == 3) ? n[1] : 1;
     pg.nh = g.nh;
+    pg.fdnh = make_fastdiv(g.nh);
     for (int a = 0; a < 3; ++a) pg.hw[a] = (a < D) ? (support[a] - 1) / 2 : 0;
     pg.scale = 1.0 / (double)g.nodes;
     // every pass must fit the per-CTA shared-memory limit
