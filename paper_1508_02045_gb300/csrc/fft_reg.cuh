@@ -156,7 +156,15 @@ struct Loc {
   int base;
   int ls;
   int es;
+  int lo = 0;        // two-level lines: line l = (l_out << nli_log) + l_in sits at
+  int nli_log = -1;  // l_in * ls + l_out * lo (nli_log < 0: one level, l * ls)
 };
+
+template <typename T>
+__device__ __forceinline__ int line_off(const Loc<T>& L, int l) {
+  return L.nli_log < 0 ? l * L.ls
+                       : (l & ((1 << L.nli_log) - 1)) * L.ls + (l >> L.nli_log) * L.lo;
+}
 
 // One Stockham stage with radix R over nl lines of length n (p = product of earlier radices).
 // Work items: (line, butterfly); colmajor puts the line index fastest.
@@ -183,7 +191,7 @@ __device__ __forceinline__ void reg_stage(Loc<T> in, Loc<T> out, int n, int p, i
     }
     const int k = i - fdiv(i, fd_p) * p;
     cpx<T> u[R];
-    const int io = in.base + l * in.ls + i * in.es;
+    const int io = in.base + line_off(in, l) + i * in.es;
     if (in.g != nullptr) {
 #pragma unroll
       for (int r = 0; r < R; ++r) u[r] = in.g[io + r * istride];
@@ -205,7 +213,7 @@ __device__ __forceinline__ void reg_stage(Loc<T> in, Loc<T> out, int n, int p, i
 #pragma unroll
       for (int r = 0; r < R; ++r) u[r].y = -u[r].y;
     }
-    const int oo = out.base + l * out.ls + ((i - k) * R + k) * out.es;
+    const int oo = out.base + line_off(out, l) + ((i - k) * R + k) * out.es;
     if (out.g != nullptr) {
 #pragma unroll
       for (int r = 0; r < R; ++r) out.g[oo + r * ostride] = u[r];
@@ -252,10 +260,33 @@ __device__ __forceinline__ void stage_any(bool inv, const AxisPlan* P, int st, L
                             P->fdm[st], P->fdp[st]);
 }
 
-// shared-memory location helper
+// shared-memory location helpers
 template <typename T>
 __device__ __forceinline__ Loc<T> sloc(int base, int ls, int es) {
-  return Loc<T>{nullptr, base, ls, es};
+  return Loc<T>{nullptr, base, ls, es, 0, -1};
+}
+template <typename T>
+__device__ __forceinline__ Loc<T> sloc2(int base, int ls, int es, int lo, int nli_log) {
+  return Loc<T>{nullptr, base, ls, es, lo, nli_log};
+}
+
+// All stages of one axis on (2^nli_log inner) x (outer) lines of a two-level layout in shared
+// memory, ping-ponging between the buffers at a and b; returns the offset holding the result.
+// Ends with a __syncthreads().
+template <typename T>
+__device__ __forceinline__ int reg_lines2(int a, int b, const AxisPlan* P, int nl, int es, int lo,
+                                          int nli_log, bool inv, int tw_base) {
+  const int nst = P->nst;
+#pragma unroll 1
+  for (int st = 0; st < nst; ++st) {
+    stage_any<T>(inv, P, st, sloc2<T>(a, 1, es, lo, nli_log), sloc2<T>(b, 1, es, lo, nli_log), nl,
+                 true, tw_base);
+    __syncthreads();
+    const int t = a;
+    a = b;
+    b = t;
+  }
+  return a;
 }
 
 // All stages of one axis on nl lines in shared memory (element j of line l at a + l*ls + j*es,
@@ -293,7 +324,7 @@ __device__ __forceinline__ void reg_columns_out(int src, int spare, cpx<T>* g, i
     a = b;
     b = t;
   }
-  stage_any<T>(inv, P, nst - 1, sloc<T>(a, 1, TCp), Loc<T>{g, 0, 1, ges}, ncols, true, tw_base);
+  stage_any<T>(inv, P, nst - 1, sloc<T>(a, 1, TCp), Loc<T>{g, 0, 1, ges, 0, -1}, ncols, true, tw_base);
   __syncthreads();
 }
 

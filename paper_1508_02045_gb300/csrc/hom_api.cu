@@ -134,6 +134,11 @@ size_t smem_budget() {
   return 110 * 1024;  // two CTAs per SM in every pass
 }
 
+size_t smem_budget32() {
+  if (const char* e = getenv("HOM_SMEM_BUDGET32_KB")) return (size_t)atoi(e) * 1024;
+  return 110 * 1024;  // two CTAs per SM in every pass
+}
+
 }  // namespace detail
 }  // namespace hom
 
@@ -370,7 +375,7 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
   // ---- plans ----
   if ((st = P->e64.init(d, P->M, P->N, smem_budget())) != HOM_OK) { hom_destroy(P); return st; }
   if (precision == HOM_FP32_REFINED) {
-    if ((st = P->e32.init(d, P->M, P->N, smem_budget())) != HOM_OK) { hom_destroy(P); return st; }
+    if ((st = P->e32.init(d, P->M, P->N, smem_budget32())) != HOM_OK) { hom_destroy(P); return st; }
   }
 
   // ---- buffers ----

@@ -489,7 +489,7 @@ int admit(hom_server* S) {
       if ((rc = b.e64->init(b.d, P->M, P->N, smem_budget()))) return rc;
       if (b.precision == HOM_FP32_REFINED) {
         b.e32 = new Engine<float>();
-        if ((rc = b.e32->init(b.d, P->M, P->N, smem_budget()))) return rc;
+        if ((rc = b.e32->init(b.d, P->M, P->N, smem_budget32()))) return rc;
       }
       S->buckets.push_back(b);
       bi = (int)S->buckets.size() - 1;

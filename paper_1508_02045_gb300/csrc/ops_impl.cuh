@@ -42,7 +42,7 @@ size_t Ops<T>::smem_strided(int n, int TCp, int nst) {
 }
 template <typename T>
 size_t Ops<T>::smem_proj(int n, int D, int TCp) {
-  return sizeof(cpx<T>) * ((size_t)n + (size_t)(D + 1) * n * TCp);
+  return sizeof(cpx<T>) * ((size_t)n + (size_t)(2 * D) * n * TCp);
 }
 
 // Opt-in shared memory per CTA minus room for the kernels' static shared variables.

@@ -22,6 +22,11 @@
 
 namespace hom {
 
+// resident CTAs per SM the pass kernels are compiled for (<= 128 registers per thread). Four
+// CTAs (64 registers) were measured slower for FP32: the radix stages spill.
+template <typename T>
+constexpr int kMinBlocks = 2;
+
 // ---------------------------------------------------------------------------------------
 // deterministic block reduction + last-block finisher
 // ---------------------------------------------------------------------------------------
@@ -226,7 +231,7 @@ struct ReqDesc {
 // line_fwd: pre-operator + forward real DFT of the contiguous axis
 // ---------------------------------------------------------------------------------------
 template <typename T, int D, int PRE>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
 k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
            int ncomp, long long nlines, int LB, LineDiv ld, long long scs, MatView<T> mat,
            const Scalars* sc, OpArgs args, const ReqDesc<T>* __restrict__ reqs) {
@@ -338,7 +343,7 @@ k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
 // strided: DFT along a strided axis, in place; blockIdx.y = batch, blockIdx.x = column tile
 // ---------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
 k_strided(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, long long C,
           long long es, long long bs, int TC, int TCp, int inv, const Scalars* sc,
           const ReqDesc<T>* __restrict__ reqs) {
@@ -383,7 +388,7 @@ struct ProjGeom {
 };
 
 template <typename T, int D, int MODE>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
 k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC,
        int TCp, const Scalars* sc, const ReqDesc<T>* __restrict__ reqs) {
   if (reqs != nullptr) {
@@ -393,9 +398,10 @@ k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC
   if (sc != nullptr && sc->done) return;
   const int n = P.n;
   cpx<T>* sm = smem_c<T>();
-  int buf[D + 1];
-#pragma unroll
-  for (int a = 0; a <= D; ++a) buf[a] = n + a * n * TCp;
+  // two buffers, each holding the D component tiles (n x TCp, component stride n * TCp); every
+  // stage transforms all D * TC columns at once
+  const int cstr = n * TCp;
+  const int bufA = n, bufB = n + D * cstr;
   __shared__ AxisPlan Ps;
   if (threadIdx.x == 0) Ps = P;
   for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = twg[i];
@@ -403,25 +409,19 @@ k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC
   const int es = (int)g.C;
   const int ncols = (int)min((long long)TC, g.C - c0);
   // stage the tiles of all components with asynchronous copies; TC is a power of two dividing
-  // the block, so every thread keeps one column c
+  // the block, so every thread keeps one column c (columns >= ncols are zero-filled)
   const int tcl = __ffs(TC) - 1;
   const int c = threadIdx.x & (TC - 1);
-  if (c < ncols)
+  const cpx<T> zero = {0, 0};
 #pragma unroll
-    for (int a = 0; a < D; ++a)
-      for (int j = threadIdx.x >> tcl; j < n; j += blockDim.x >> tcl)
-        cp_async_elem<T>(sm + n + a * n * TCp + j * TCp + c, S + a * g.cs + c0 + j * es + c);
+  for (int a = 0; a < D; ++a)
+    for (int j = threadIdx.x >> tcl; j < n; j += blockDim.x >> tcl) {
+      if (c < ncols) cp_async_elem<T>(sm + bufA + a * cstr + j * TCp + c, S + a * g.cs + c0 + j * es + c);
+      else sm[bufA + a * cstr + j * TCp + c] = zero;
+    }
   cp_async_wait_all();
   __syncthreads();
-  int spare = buf[D];
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    const int res = reg_lines<T>(buf[a], spare, &Ps, ncols, 1, TCp, true, false, 0);
-    if (res != buf[a]) {
-      spare = buf[a];
-      buf[a] = res;
-    }
-  }
+  const int fwd = reg_lines2<T>(bufA, bufB, &Ps, D * TC, TCp, cstr, tcl, false, 0);
   const T scale = (T)g.scale;
   // frequencies of this thread's column (fixed over the rows)
   int kc1 = 0, kc2 = 0;
@@ -435,7 +435,7 @@ k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC
       kc1 = cc;
     }
   }
-  for (int j = threadIdx.x >> tcl; c < ncols && j < n; j += blockDim.x >> tcl) {
+  for (int j = threadIdx.x >> tcl; j < n; j += blockDim.x >> tcl) {
     int k[3];
     k[0] = (j <= (n - 1) / 2) ? j : j - n;
     k[1] = kc1;
@@ -449,7 +449,7 @@ k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC
     }
     cpx<T> v[D];
 #pragma unroll
-    for (int a = 0; a < D; ++a) v[a] = sm[buf[a] + j * TCp + c];
+    for (int a = 0; a < D; ++a) v[a] = sm[fwd + a * cstr + j * TCp + c];
     cpx<T> kv = {0, 0};
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -469,20 +469,24 @@ k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC
         o.x = fma((T)(-2 * k[a]), kv.x, scale * v[a].x);
         o.y = fma((T)(-2 * k[a]), kv.y, scale * v[a].y);
       }
-      sm[buf[a] + j * TCp + c] = o;
+      sm[fwd + a * cstr + j * TCp + c] = o;
     }
   }
   __syncthreads();
+  const int other = (fwd == bufA) ? bufB : bufA;
+  const int res = reg_lines2<T>(fwd, other, &Ps, D * TC, TCp, cstr, tcl, true, 0);
+  if (c < ncols)
 #pragma unroll
-  for (int a = 0; a < D; ++a)
-    reg_columns_out<T>(buf[a], spare, S + a * g.cs + c0, es, ncols, TCp, &Ps, true, 0);
+    for (int a = 0; a < D; ++a)
+      for (int j = threadIdx.x >> tcl; j < n; j += blockDim.x >> tcl)
+        S[a * g.cs + c0 + j * es + c] = sm[res + a * cstr + j * TCp + c];
 }
 
 // ---------------------------------------------------------------------------------------
 // line_inv: inverse real DFT of the contiguous axis + post-operator
 // ---------------------------------------------------------------------------------------
 template <typename T, int D, int POST>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
 k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ twg,
            int ncomp, long long nlines, int LB, LineDiv ld, long long scs, MatView<T> mat,
            Scalars* sc, OpArgs args, double* partials, unsigned* counter, int negate,

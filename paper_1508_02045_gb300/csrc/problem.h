@@ -239,6 +239,7 @@ struct Engine {
 };
 
 size_t smem_budget();
+size_t smem_budget32();
 int alloc(void** p, size_t bytes);
 int check_last();
 bool spd_eigs(const double* t, int d, double* lo, double* hi);
