@@ -425,6 +425,77 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------------------
+# the spec configurations end to end (solver results and times; not the bench line)
+# ------------------------------------------------------------------------------------------
+
+def run_configs(args):
+    import torch
+    import paper_1508_02045_gb300 as H
+
+    out = {}
+    sync = torch.cuda.synchronize
+
+    def solve(P, E, solver, tol, opts=None, x=None):
+        sync()
+        t0 = time.perf_counter()
+        AH, flux, st, status = H.hom_solve(P.h, E, solver, tol, opts, x, allow_not_converged=True)
+        sync()
+        return {"A_H": AH, "iterations": st["iterations"], "inner_iterations": st["inner_iterations"],
+                "converged": bool(st["converged"]), "true_residual": st["true_residual"],
+                "seconds": round(time.perf_counter() - t0, 4)}
+
+    # config 1: 2-D 63^2, square of side 0.6, contrast 10, E = (1, 0), Richardson and CG to 1e-8
+    N = (63, 63)
+    P = H.Problem(2, N, H.phase_material(ms.box_phase(N, 0.6), ms.isotropic_table([1.0, 10.0], 2)))
+    E = np.array([1.0, 0.0])
+    out["c1_63sq"] = {s: solve(P, E, H.SOLVERS[s], 1e-8) for s in ("richardson", "cg")}
+    P.close()
+    # config 2: 243^3 cube vf 0.2, contrast 1e3, all four solvers to 1e-6
+    N = (243,) * 3
+    P = H.Problem(3, N, H.phase_material(ms.box_phase(N, ms.inclusion_side_for_fraction(0.2, 3)),
+                                        ms.isotropic_table([1.0, 1000.0], 3)))
+    E = np.array([1.0, 0.0, 0.0])
+    out["c2_243cube"] = {}
+    for s in ("cg", "chebyshev", "eyre_milton", "richardson"):
+        out["c2_243cube"][s] = solve(P, E, H.SOLVERS[s], 1e-6, H.make_opts(maxit=args.configs_maxit))
+        r = out["c2_243cube"][s]
+        r["matvecs_per_s"] = round(r["iterations"] / r["seconds"], 2)
+    P.close()
+    # config 3: Ga, N = 81^3 on the double grid 161^3, cube vf 0.3, contrast 100, CG to 1e-8,
+    # with the GaNi guaranteed bound via prolongation and the Hashin-Shtrikman lower bound
+    N = (81,) * 3
+    h = ms.inclusion_side_for_fraction(0.3, 3)
+    Pn = H.Problem(3, N, H.phase_material(ms.box_phase(N, h), ms.isotropic_table([1.0, 100.0], 3)))
+    xn = Pn.field()
+    gani = solve(Pn, E, H.HOM_CG, 1e-8, None, xn)
+    M = (161,) * 3
+    Pg = H.Problem(3, N, H.fourier_material(ms.box_fourier_coefficients(M, h, 1.0, 100.0).astype(np.complex128),
+                                            1.0, 100.0), H.HOM_EXACT)
+    bound = H.hom_bound(Pn.h, Pg.h, E, xn)
+    gar = solve(Pg, E, H.HOM_CG, 1e-8)
+    hs = 1.0 + 0.3 / (1.0 / 99.0 + 0.7 / 3.0)
+    out["c3_ga_81_on_161"] = {"gani": gani, "gani_bound": bound, "ga": gar, "hashin_shtrikman_lower": hs,
+                              "ordering_holds": bool(hs < gar["A_H"] < bound)}
+    Pn.close()
+    Pg.close()
+    # config 4: 405^3 random spheres, log-uniform conductivities, CG in FP64 vs FP32 + refinement
+    N = (405,) * 3
+    ph, _, radii = ms.rsa_spheres(N, 1, vf=0.3)
+    rng = np.random.default_rng(101)
+    table = ms.isotropic_table(np.concatenate([[1.0], np.exp(rng.uniform(np.log(10), np.log(1000), len(radii)))]), 3)
+    res = {}
+    for label, prec in (("fp32_refined", H.HOM_FP32_REFINED), ("fp64", H.HOM_FP64)):
+        P = H.Problem(3, N, H.phase_material(ph, table), precision=prec)
+        res[label] = solve(P, E, H.HOM_CG, 1e-8, H.make_opts(maxit=3000 if prec == H.HOM_FP64 else 50))
+        P.close()
+    res["A_H_rel_diff"] = abs(res["fp32_refined"]["A_H"] - res["fp64"]["A_H"]) / res["fp64"]["A_H"]
+    res["speedup"] = round(res["fp64"]["seconds"] / res["fp32_refined"]["seconds"], 2)
+    res["spheres"] = int(len(radii))
+    out["c4_405_spheres"] = res
+    print(json.dumps({"configs": out}), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -459,11 +530,16 @@ def main():
     ap.add_argument("--serve", type=int, default=0, help="run the served mix with this many requests")
     ap.add_argument("--serve-window", type=float, default=1.0)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
+    ap.add_argument("--configs", action="store_true", help="run configurations 1-4 end to end")
+    ap.add_argument("--configs-maxit", type=int, default=20000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.serve:
         run_served(args)
+        return
+    if args.configs:
+        run_configs(args)
         return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
