@@ -271,6 +271,21 @@ int hom_server_poll(hom_server* S, hom_result* out, int max, int* count);
 int hom_server_status(hom_server* S, int* active, int* queued, size_t* bytes_in_use);
 void hom_server_destroy(hom_server* S);
 
+/* Autotuner of the launch plan (build extension). For the grid of P it times `reps` operator
+ * applications (after one warm-up) for every candidate register-radix limit (FP64: 9, 15; FP32:
+ * 9, 15, 27) and shared-memory tile budget per CTA (56, 110, 150, 200 KiB), re-plans P with the
+ * fastest, and records the choice so that every later hom_create of the same grid, integration
+ * support and precision in this process starts with it. Overwrites P's solver vectors (call it
+ * before hom_solve_begin; HOM_ERR_INVALID during a session). report (nullable) receives the
+ * choices and the time of one application. */
+typedef struct {
+  int rmax64, smem_kb64;
+  double ms64;
+  int rmax32, smem_kb32;   /* 0 unless P is HOM_FP32_REFINED */
+  double ms32;
+} hom_tune_report;
+int hom_autotune(hom_problem* P, int reps, hom_tune_report* report);
+
 /* Free everything the handle owns. NULL is accepted. */
 void hom_destroy(hom_problem* P);
 

@@ -34,7 +34,7 @@ EXPORTED = ["hom_create", "hom_grid", "hom_bounds", "hom_apply", "hom_solve", "h
             "hom_profile_enable", "hom_profile_read", "hom_solve_begin", "hom_solve_iterate",
             "hom_solve_end", "hom_apply_static", "hom_batch_create", "hom_batch_iterate",
             "hom_batch_destroy", "hom_server_create", "hom_server_submit", "hom_server_step",
-            "hom_server_poll", "hom_server_status", "hom_server_destroy"]
+            "hom_server_poll", "hom_server_status", "hom_server_destroy", "hom_autotune"]
 PASS_KINDS = ["line_fwd", "strided", "proj", "line_inv", "vector"]
 
 
@@ -74,6 +74,11 @@ class hom_result(ctypes.Structure):
                 ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
 
 
+class hom_tune_report(ctypes.Structure):
+    _fields_ = [("rmax64", ctypes.c_int), ("smem_kb64", ctypes.c_int), ("ms64", ctypes.c_double),
+                ("rmax32", ctypes.c_int), ("smem_kb32", ctypes.c_int), ("ms32", ctypes.c_double)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libhom.so is not built ({LIB_PATH}); run paper_1508_02045_gb300.build.build()")
@@ -89,6 +94,7 @@ def _load():
     lib.hom_energy.argtypes = [vp, dp, vp, dp, dp]
     lib.hom_apply_static.argtypes = [ip, ctypes.POINTER(ctypes.c_int), vp, ip, dp, ip, ip, dp, vp,
                                      vp, vp]
+    lib.hom_autotune.argtypes = [vp, ip, ctypes.POINTER(hom_tune_report)]
     lib.hom_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp)]
     lib.hom_batch_iterate.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_int)]
     lib.hom_batch_destroy.argtypes = [vp]
@@ -255,6 +261,12 @@ def hom_solve_end(P, d, x=None, allow_not_converged=False):
     if not (st == HOM_OK or (allow_not_converged and st == HOM_ERR_NOT_CONVERGED)):
         raise HomError(st, "hom_solve_end")
     return AH.value, [flux[i] for i in range(d)], stats.as_dict(), st
+
+
+def hom_autotune(P, reps=3):
+    rep = hom_tune_report()
+    _check(_lib.hom_autotune(P, int(reps), ctypes.byref(rep)), "hom_autotune")
+    return {k: getattr(rep, k) for k, _ in rep._fields_}
 
 
 def hom_batch_create(problems):

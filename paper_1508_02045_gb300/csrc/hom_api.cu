@@ -7,7 +7,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "../../include/hom.h"
@@ -129,14 +131,29 @@ int check_last() {
   return HOM_OK;
 }
 
-size_t smem_budget() {
-  if (const char* e = getenv("HOM_SMEM_BUDGET_KB")) return (size_t)atoi(e) * 1024;
-  return 110 * 1024;  // two CTAs per SM in every pass
+// ---- autotuned launch plans, per (precision, grid, support) in this process ----
+namespace {
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int>;
+std::map<TuneKey, PlanChoice>& tune_table() {
+  static std::map<TuneKey, PlanChoice> t;
+  return t;
 }
+std::mutex& tune_mu() {
+  static std::mutex m;
+  return m;
+}
+TuneKey tune_key(int pb, int d, const int* M, const int* N) {
+  return TuneKey(pb, d, M[0], d > 1 ? M[1] : 1, d > 2 ? M[2] : 1, N[0], d > 1 ? N[1] : 1,
+                 d > 2 ? N[2] : 1);
+}
+}  // namespace
 
-size_t smem_budget32() {
-  if (const char* e = getenv("HOM_SMEM_BUDGET32_KB")) return (size_t)atoi(e) * 1024;
-  return 110 * 1024;  // two CTAs per SM in every pass
+PlanChoice plan_choice(int pb, int d, const int* M, const int* N) {
+  std::lock_guard<std::mutex> lk(tune_mu());
+  auto it = tune_table().find(tune_key(pb, d, M, N));
+  if (it != tune_table().end()) return it->second;
+  // defaults: two CTAs per SM in every pass; FP64 values take twice the registers
+  return PlanChoice{pb == 8 ? 15 : 27, 110 * 1024};
 }
 
 }  // namespace detail
@@ -373,9 +390,13 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
   if (!(P->cA > 0 && P->CA >= P->cA)) { hom_destroy(P); return HOM_ERR_INVALID; }
 
   // ---- plans ----
-  if ((st = P->e64.init(d, P->M, P->N, smem_budget())) != HOM_OK) { hom_destroy(P); return st; }
+  {
+    const PlanChoice pc = plan_choice(8, d, P->M, P->N);
+    if ((st = P->e64.init(d, P->M, P->N, pc.budget, pc.rmax)) != HOM_OK) { hom_destroy(P); return st; }
+  }
   if (precision == HOM_FP32_REFINED) {
-    if ((st = P->e32.init(d, P->M, P->N, smem_budget32())) != HOM_OK) { hom_destroy(P); return st; }
+    const PlanChoice pc = plan_choice(4, d, P->M, P->N);
+    if ((st = P->e32.init(d, P->M, P->N, pc.budget, pc.rmax)) != HOM_OK) { hom_destroy(P); return st; }
   }
 
   // ---- buffers ----
@@ -1004,4 +1025,88 @@ extern "C" int hom_bound(hom_problem* gani, hom_problem* ga, const double* E,
   if (rc) return rc;
   HOM_CUDA(cudaStreamSynchronize(ga->stream));
   return energy_eval(ga, E, y, UE, nullptr);
+}
+
+// ---------------------------------------------------------------------------------------
+// autotuner: time candidate launch plans of P's grid and keep the fastest
+// ---------------------------------------------------------------------------------------
+namespace {
+
+template <typename T>
+int tune_engine(hom_problem* P, Engine<T>& E, T* x, T* y, int reps, const std::vector<int>& rmaxes,
+                const std::vector<size_t>& budgets, PlanChoice* best, double* best_ms) {
+  const int d = P->d;
+  const size_t cap = (size_t)dynamic_smem_cap();
+  double best_t = 1e300;
+  PlanChoice choice{E.rmax_used, E.budget_used};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  Fields<T> f{};
+  f.xin = x;
+  f.out = y;
+  f.cs = P->nodes;
+  OpArgs args{};
+  for (int rmax : rmaxes)
+    for (size_t budget : budgets) {
+      if (budget > cap) continue;
+      E.release_plan();
+      if (E.init(d, P->M, P->N, budget, rmax) != HOM_OK) continue;
+      E.apply(PRE_LINEAR, PROJ_GAMMA, POST_STORE, f, (cpx<T>*)P->S, nullptr, args, nullptr,
+              nullptr, 0, P->stream);  // warm-up
+      cudaEventRecord(e0, P->stream);
+      for (int r = 0; r < reps; ++r)
+        E.apply(PRE_LINEAR, PROJ_GAMMA, POST_STORE, f, (cpx<T>*)P->S, nullptr, args, nullptr,
+                nullptr, 0, P->stream);
+      cudaEventRecord(e1, P->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return check_last();
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_t) {
+        best_t = ms;
+        choice = PlanChoice{rmax, budget};
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  E.release_plan();
+  const int rc = E.init(d, P->M, P->N, choice.budget, choice.rmax);
+  *best = choice;
+  *best_ms = best_t / reps;
+  return rc ? rc : check_last();
+}
+
+}  // namespace
+
+extern "C" int hom_autotune(hom_problem* P, int reps, hom_tune_report* report) {
+  if (!P || P->sv.active) return HOM_ERR_INVALID;
+  if (reps < 1) reps = 3;
+  hom_tune_report rep{};
+  PlanChoice c{};
+  double ms = 0;
+  const std::vector<size_t> budgets = {56 * 1024, 110 * 1024, 150 * 1024, 200 * 1024};
+  int rc = tune_engine<double>(P, P->e64, P->vec[0], P->vec[1], reps, {9, 15}, budgets, &c, &ms);
+  if (rc) return rc;
+  rep.rmax64 = c.rmax;
+  rep.smem_kb64 = (int)(c.budget / 1024);
+  rep.ms64 = ms;
+  {
+    std::lock_guard<std::mutex> lk(tune_mu());
+    tune_table()[tune_key(8, P->d, P->M, P->N)] = c;
+  }
+  if (P->precision == HOM_FP32_REFINED) {
+    rc = tune_engine<float>(P, P->e32, P->fvec[0], P->fvec[1], reps, {9, 15, 27}, budgets, &c, &ms);
+    if (rc) return rc;
+    rep.rmax32 = c.rmax;
+    rep.smem_kb32 = (int)(c.budget / 1024);
+    rep.ms32 = ms;
+    std::lock_guard<std::mutex> lk(tune_mu());
+    tune_table()[tune_key(4, P->d, P->M, P->N)] = c;
+  }
+  if (report) *report = rep;
+  return HOM_OK;
 }

@@ -122,14 +122,19 @@ struct Engine {
   T* table = nullptr;  // phase table in precision T
   bool ready = false;
 
-  int init(int D, const int* n, const int* support, size_t budget) {
+  int rmax_used = 0;
+  size_t budget_used = 0;
+
+  // plan the axes with register radices <= rmax and tiles within `budget` bytes of shared
+  // memory per CTA; allocates the twiddle tables
+  int init(int D, const int* n, const int* support, size_t budget, int rmax) {
+    rmax_used = rmax;
+    budget_used = budget;
     g.D = D;
     g.nodes = 1;
     for (int a = 0; a < D; ++a) {
       g.n[a] = n[a];
       g.nodes *= n[a];
-      int rmax = reg_rmax<T>();
-      if (const char* e = getenv(sizeof(T) == 4 ? "HOM_RMAX32" : "HOM_RMAX64")) rmax = atoi(e);
       if (!plan_axis(n[a], rmax, &plan[a])) return HOM_ERR_INVALID;
     }
     for (int a = D; a < 3; ++a) g.n[a] = 1;
@@ -166,11 +171,16 @@ struct Engine {
     return HOM_OK;
   }
 
-  void release() {
+  // free the twiddle tables only (re-planning keeps the coefficients)
+  void release_plan() {
     for (auto& t : tw) {
       if (t) cudaFree(t);
       t = nullptr;
     }
+  }
+
+  void release() {
+    release_plan();
     if (field) cudaFree(field);
     field = nullptr;
     if (table) cudaFree(table);
@@ -238,8 +248,13 @@ struct Engine {
   }
 };
 
-size_t smem_budget();
-size_t smem_budget32();
+// launch plan of a grid: register radix limit and shared-memory budget per CTA. Defaults, or
+// what hom_autotune measured fastest for the same grid and precision in this process.
+struct PlanChoice {
+  int rmax;
+  size_t budget;
+};
+PlanChoice plan_choice(int precision_bytes, int d, const int* M, const int* N);
 int alloc(void** p, size_t bytes);
 int check_last();
 bool spd_eigs(const double* t, int d, double* lo, double* hi);

@@ -252,3 +252,27 @@ def test_error_paths():
     assert st == H.HOM_ERR_NOT_CONVERGED and stats["iterations"] == 5
     Pg.close()
     P.close()
+
+
+def test_autotune_keeps_parity():
+    N = (45, 45, 45)
+    d = 3
+    ph, table, A = square(N, 0.6, 1.0, 10.0)
+    P = H.Problem(d, N, H.phase_material(ph, table), precision=H.HOM_FP32_REFINED)
+    rep = H.hom_autotune(P.h, reps=2)
+    assert rep["rmax64"] in (9, 15) and rep["rmax32"] in (9, 15, 27)
+    assert rep["smem_kb64"] in (56, 110, 150, 200) and rep["ms64"] > 0 and rep["ms32"] > 0
+    x = ms.random_field((d,) + N, 6)
+    y = P.field()
+    H.hom_apply(P.h, H.HOM_OP_LINEAR, None, to_dev(x), y)
+    ref = O.GaNi(A, d).matvec(x)
+    assert rel(y.cpu().numpy(), ref) < OP_TOL
+    H.hom_apply(P.h, H.HOM_OP_LINEAR | H.HOM_OP_FP32, None, to_dev(x), y)
+    assert rel(y.cpu().numpy(), ref) < 2e-6
+    # a later problem of the same grid starts from the tuned plan and solves correctly
+    Q = H.Problem(d, N, H.phase_material(ph, table))
+    AH, _, _, _ = H.hom_solve(Q.h, np.eye(d)[0], H.HOM_CG, 1e-10)
+    sysn = O.GaNi(A, d)
+    assert abs(AH - sysn.energy(np.eye(d)[0], O.cg(sysn, np.eye(d)[0], tol=1e-10).x)) < 1e-10 * AH
+    P.close()
+    Q.close()
