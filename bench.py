@@ -49,6 +49,18 @@ def workload():
     return ph, table
 
 
+def measured_peaks():
+    """HBM copy bandwidth measured on the GB300s (generated file), else the
+    recipe's fallback figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "source": "fallback 6.8 TB/s"}
+
+
 def config(extra=None):
     c = {"workload": "GaNi 243^3 FP64 CG step, centred cube vf 0.2, contrast 1e3, E=(1,0,0)",
          "grid": list(N_GRID), "d": D, "integration": "approx (GaNi)", "solver": "cg",
@@ -169,30 +181,65 @@ def cpu_oracle_cg_steps(nsteps=1):
 # roofline bookkeeping of the dominant kernel
 # ------------------------------------------------------------------------------------------
 
-def fft_flops_per_point(n):
-    """FP64 flops per complex point per transform of length n with this library's radix plan
-    (FMA = 2 flops): per radix-R butterfly 8H^2 + 20H flops with twiddles, 8H^2 + 8H without
-    (H = (R-1)/2); the first stage has no twiddles."""
-    rad = []
+def plan_radices(n, rmax):
+    """The library's radix plan of an axis (first-fit grouping of the prime factors, largest
+    first, into register radices <= rmax; stages in decreasing radix order)."""
+    primes = []
     m = n
-    for R in (3, 5, 7, 11, 13, 17, 19, 23, 29, 31):
+    for R in (31, 29, 23, 19, 17, 13, 11, 7, 5, 3):
         while m % R == 0:
-            rad.append(R)
+            primes.append(R)
             m //= R
-    total = 0.0
-    for s, R in enumerate(rad):
+    groups = []
+    for f in primes:
+        best = None
+        for gi, g in enumerate(groups):
+            if g * f <= rmax and (best is None or g > groups[best]):
+                best = gi
+        if best is None:
+            groups.append(f)
+        else:
+            groups[best] *= f
+    return sorted(groups, reverse=True)
+
+
+def _smallest_factor(R):
+    for p in (3, 5, 7, 11, 13, 17, 19, 23, 29, 31):
+        if R % p == 0:
+            return p
+    return R
+
+
+def reg_dft_flops(R):
+    """Flops of the in-register DFT of R points (FMA = 2): prime R by the pairing method
+    (8H^2 + 8H, H = (R-1)/2), composite R = A B as B A-point and A B-point DFTs plus the
+    non-trivial internal twiddles (6 flops each)."""
+    A = _smallest_factor(R)
+    if A == R:
         H = (R - 1) // 2
-        fl = 8 * H * H + (20 * H if s > 0 else 8 * H)
-        total += fl / R
+        return 8 * H * H + 8 * H
+    B = R // A
+    tw = sum(1 for j2 in range(B) for k1 in range(A) if (j2 * k1) % R)
+    return B * reg_dft_flops(A) + A * reg_dft_flops(B) + 6 * tw
+
+
+def fft_flops_per_point(n, rmax):
+    """Flops per complex point of one transform of length n with the library's plan: per stage
+    of radix R, one R-point register DFT per R points plus R - 1 twiddle products (6 flops) when
+    earlier stages exist."""
+    total, p = 0.0, 1
+    for R in plan_radices(n, rmax):
+        total += (reg_dft_flops(R) + (6 * (R - 1) if p > 1 else 0)) / R
+        p *= R
     return total
 
 
-def pass_flops():
-    """Algorithmic FP64 flops of one launch of each pass kind at 243^3, d = 3."""
+def pass_flops(rmax):
+    """Algorithmic flops of one launch of each pass kind (d = 3, FP64 CG step)."""
     n = N_GRID[0]
     nh = (n + 1) // 2
     lines_c = n * n * D / 2.0                 # complex lines of the packed real transforms
-    f1 = fft_flops_per_point(n)
+    f1 = fft_flops_per_point(n, rmax)
     spec = n * n * nh * D                     # half-spectrum points per transform pass
     return {
         "line_fwd": lines_c * n * f1 + n * n * n * D * 2 + n * n * nh * D * 6,
@@ -202,15 +249,17 @@ def pass_flops():
     }
 
 
-def pass_bytes():
-    """Compulsory DRAM bytes of one launch of each pass kind at 243^3 (FP64)."""
+def pass_bytes(word=8):
+    """Compulsory DRAM bytes of one launch of each pass kind in a CG step (word = 8 for FP64,
+    4 for FP32); the CG update reads x, p, r, C p and writes x, r."""
     n = N_GRID[0]
     nh = (n + 1) // 2
-    spec = n * n * nh * D * 16
-    field = n * n * n * D * 8
+    spec = n * n * nh * D * 2 * word
+    field = n * n * n * D * word
     return {"line_fwd": 2 * field + field + n ** 3 + spec,  # r, p read; p written; phase; spectrum
             "strided": 2 * spec, "proj": 2 * spec,
-            "line_inv": spec + 2 * field}                    # spectrum; p read; C p written
+            "line_inv": spec + 2 * field,                    # spectrum; p read; C p written
+            "vector": 6 * field}
 
 
 # ------------------------------------------------------------------------------------------
@@ -228,6 +277,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     ph, table = workload()
     prob = H.Problem(D, N_GRID, H.phase_material(ph, table))
+    tune = H.hom_autotune(prob.h, reps=2)  # the launch plan a user gets from the autotuner
     stream = torch.cuda.current_stream()
     total = args.warmup + args.steps
     opts = H.make_opts(fixed_iters=total + 1)
@@ -262,6 +312,25 @@ def run_ours(args, rank, world, local):
             print(json.dumps({"quick": True, "grid": list(N_GRID), "ms_per_step": ms_step,
                               "passes": passes, "gpu_launches": int(launches)}), flush=True)
         return None
+
+    # ---- the same CG step in FP32 (the inner solver of HOM_FP32_REFINED), HBM-bound ----
+    p32 = H.Problem(D, N_GRID, H.phase_material(ph, table), precision=H.HOM_FP32_REFINED)
+    tune32 = H.hom_autotune(p32.h, reps=2)
+    H.hom_solve_begin(p32.h, E_MACRO, H.HOM_CG, 1e-30, H.make_opts(maxit=2, inner_tol=1e-30))
+    H.hom_solve_iterate(p32.h, args.warmup)
+    torch.cuda.synchronize()
+    H.hom_profile_enable(True)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    H.hom_solve_iterate(p32.h, args.steps)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    H.hom_profile_enable(False)
+    passes32 = H.hom_profile_read()
+    ms_step32 = f0.elapsed_time(f1) / args.steps
+    H.hom_solve_end(p32.h, D, allow_not_converged=True)
+    p32.close()
 
     # ---- end to end: host field -> device, one G A application, result -> host ----
     nfield = D * int(np.prod(N_GRID))
@@ -299,35 +368,58 @@ def run_ours(args, rank, world, local):
 
     if rank != 0:
         return None
-    flops = pass_flops()
-    byts = pass_bytes()
-    per_kind = {}
-    for k, (ms_k, cnt) in passes.items():
-        if cnt:
-            per_kind[k] = {"ms_avg": ms_k / cnt, "launches": cnt, "share": None}
-    tot_ms = sum(v["ms_avg"] * v["launches"] for v in per_kind.values())
-    for v in per_kind.values():
-        v["share"] = round(v["ms_avg"] * v["launches"] / tot_ms, 4) if tot_ms else None
-    dom = max((k for k in per_kind if k in flops), key=lambda k: per_kind[k]["ms_avg"] * per_kind[k]["launches"])
-    dom_ms = per_kind[dom]["ms_avg"]
+    flops = pass_flops(tune["rmax64"])
+    byts = pass_bytes(8)
+    byts32 = pass_bytes(4)
+    peaks = measured_peaks()
+
+    def per_kind(pr):
+        out = {}
+        for k, (ms_k, cnt) in pr.items():
+            if cnt:
+                out[k] = {"ms_avg": round(ms_k / cnt, 4), "launches": cnt}
+        tot = sum(v["ms_avg"] * v["launches"] for v in out.values())
+        for v in out.values():
+            v["share"] = round(v["ms_avg"] * v["launches"] / tot, 4) if tot else None
+        return out
+
+    pk = per_kind(passes)
+    dom = max((k for k in pk if k in flops), key=lambda k: pk[k]["ms_avg"] * pk[k]["launches"])
+    dom_ms = pk[dom]["ms_avg"]
     achieved = flops[dom] / (dom_ms * 1e-3) / 1e12
     peak = 1.25  # FP64 TFLOP/s: 152 SMs x 2 DFMA/clk x 2 flops x ~2.07 GHz (nominal)
+    step_bytes = sum(byts[k] * (2 if k == "strided" else 1) for k in byts)
+    pk32 = per_kind(passes32)
+    dom32 = max((k for k in pk32 if k in byts32), key=lambda k: pk32[k]["ms_avg"] * pk32[k]["launches"])
+    ach32 = byts32[dom32] / (pk32[dom32]["ms_avg"] * 1e-3) / 1e9
+    step_bytes32 = sum(byts32[k] * (2 if k == "strided" else 1) for k in byts32)
     value = world * 1000.0 / ms_step
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded centred-cube phase image)",
-        "config": config({"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+        "config": config({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                          "plan": {"fp64_rmax": tune["rmax64"], "fp64_smem_kb": tune["smem_kb64"]}}),
         "e2e": {"value": round(world * 1000.0 / e2e_ms, 3), "unit": UNIT,
                 "h2d_bytes_per_step": nfield * 8, "d2h_bytes_per_step": nfield * 8,
                 "path": "pinned host field -> hom_apply(HOM_OP_LINEAR) -> pinned host field"},
         "gpu_launches": int(launches),
+        "hbm_gbs": round(step_bytes / (ms_step * 1e-3) / 1e9, 1),
         "roofline": {"bound": "alu", "kernel": f"k_{dom}", "achieved": round(achieved, 4),
                      "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                      "traffic": None, "peak_source": "recipe nominal FP64 (1.25 TFLOP/s)",
                      "hbm_gbs_of_dominant": round(byts[dom] / (dom_ms * 1e-3) / 1e9, 1)},
-        "passes": per_kind,
+        "passes": pk,
+        "fp32_step": {"metric": "G·A matvecs/s at 243^3 (FP32 CG step, inner solver of the refinement)",
+                      "value": round(1000.0 / ms_step32, 3), "unit": UNIT, "ms_per_step": round(ms_step32, 4),
+                      "hbm_gbs": round(step_bytes32 / (ms_step32 * 1e-3) / 1e9, 1),
+                      "plan": {"rmax": tune32["rmax32"], "smem_kb": tune32["smem_kb32"]},
+                      "roofline": {"bound": "hbm", "kernel": f"k_{dom32}", "achieved": round(ach32, 1),
+                                   "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                   "frac": round(ach32 / peaks["hbm_gbs"], 4), "traffic": None,
+                                   "peak_source": peaks["source"]},
+                      "passes": pk32},
         "clocks": clk,
         "cg_to_1e-6": {"iterations": stats["iterations"], "seconds": round(cg_wall, 3),
                        "device_ms": round(stats["time_ms"], 2), "A_H": AH,
