@@ -37,12 +37,24 @@ size_t Ops<T>::smem_line(int n, int ncomp, int LB) {
 }
 template <typename T>
 size_t Ops<T>::smem_strided(int n, int TCp, int nst) {
-  const size_t nbuf = nst >= 2 ? 2 : 1;
-  return sizeof(cpx<T>) * ((size_t)n + nbuf * (size_t)n * TCp);
+  (void)nst;  // two staging buffers (pipelined tiles) + one stage buffer
+  return sizeof(cpx<T>) * ((size_t)n + 3 * (size_t)n * TCp);
 }
 template <typename T>
 size_t Ops<T>::smem_proj(int n, int D, int TCp) {
   return sizeof(cpx<T>) * ((size_t)n + (size_t)(2 * D) * n * TCp);
+}
+
+// number of SMs of the current device (cached per process)
+inline int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
 }
 
 // Opt-in shared memory per CTA minus room for the kernels' static shared variables.
@@ -145,11 +157,13 @@ void Ops<T>::strided(const PassGeom& g, int axis, int inv, cpx<T>* S, const Axis
     TC = g.TCs0;
     TCp = g.TCs0p;
   }
-  dim3 grid((unsigned)((C + TC - 1) / TC), (unsigned)batches, (unsigned)nreq);
+  // persistent grid: at most two CTAs per SM, each walking tiles with a prefetch pipeline
+  const long long tiles = ((C + TC - 1) / TC) * (long long)batches * nreq;
+  const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)num_sms() * 2);
   const size_t sm = smem_strided(P.n, TCp, P.nst);
   const bool prof = profiling();
   if (prof) prof_mark(KIND_STRIDED, st, true);
-  k_strided<T><<<grid, kThreads, sm, st>>>(S, P, tw, C, es, bs, TC, TCp, inv, sc, reqs);
+  k_strided<T><<<grid, kThreads, sm, st>>>(S, P, tw, C, es, bs, TC, TCp, inv, sc, reqs, batches, nreq);
   if (prof) prof_mark(KIND_STRIDED, st, false);
   ++launch_counter();
 }

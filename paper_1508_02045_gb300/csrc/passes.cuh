@@ -342,36 +342,71 @@ k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
 // ---------------------------------------------------------------------------------------
 // strided: DFT along a strided axis, in place; blockIdx.y = batch, blockIdx.x = column tile
 // ---------------------------------------------------------------------------------------
+// Persistent and software-pipelined: each CTA walks tiles t = blockIdx.x, + gridDim.x, ...
+// over all requests, batches and column chunks; while it transforms tile t (staged in buffer
+// A) the asynchronous copies of tile t + gridDim.x fill buffer B.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
 k_strided(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, long long C,
           long long es, long long bs, int TC, int TCp, int inv, const Scalars* sc,
-          const ReqDesc<T>* __restrict__ reqs) {
-  if (reqs != nullptr) {
-    S = reqs[blockIdx.z].S;
-    sc = reqs[blockIdx.z].sc;
-  }
-  if (sc != nullptr && sc->done) return;
+          const ReqDesc<T>* __restrict__ reqs, int nbatch, int nreq) {
   const int n = P.n;
   cpx<T>* sm = smem_c<T>();
-  const int b0 = n, b1 = n + n * TCp;
+  const int tile_elems = n * TCp;
+  int bufA = n, bufB = n + tile_elems;
+  const int bufC = n + 2 * tile_elems;
   __shared__ AxisPlan Ps;
   if (threadIdx.x == 0) Ps = P;
   for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = twg[i];
-  const long long c0 = (long long)blockIdx.x * TC;
-  const int ncols = (int)min((long long)TC, C - c0);
-  cpx<T>* base = S + (long long)blockIdx.y * bs + c0;
-  const int ges = (int)es;
-  // stage the whole tile with asynchronous copies (all rows in flight at once); TC is a power
-  // of two dividing the block, so every thread keeps one column c
+  const int ntc = (int)((C + TC - 1) / TC);
+  const long long total = (long long)nreq * nbatch * ntc;
   const int tcl = __ffs(TC) - 1;
   const int c = threadIdx.x & (TC - 1);
-  if (c < ncols)
-    for (int j = threadIdx.x >> tcl; j < n; j += blockDim.x >> tcl)
-      cp_async_elem<T>(sm + b0 + j * TCp + c, base + j * ges + c);
+  const int ges = (int)es;
+  // tile t -> (request, batch, column chunk); returns the tile's global base (or null when the
+  // request has stopped) and its column count
+  auto locate = [&](long long t, int* ncols) -> cpx<T>* {
+    const int q = (int)(t / ((long long)nbatch * ntc));
+    const int rem = (int)(t - (long long)q * nbatch * ntc);
+    const int b = rem / ntc, chunk = rem - b * ntc;
+    cpx<T>* Sq = S;
+    const Scalars* scq = sc;
+    if (reqs != nullptr) {
+      Sq = reqs[q].S;
+      scq = reqs[q].sc;
+    }
+    if (scq != nullptr && scq->done) return nullptr;
+    const long long c0 = (long long)chunk * TC;
+    *ncols = (int)min((long long)TC, C - c0);
+    return Sq + (long long)b * bs + c0;
+  };
+  auto issue = [&](cpx<T>* base, int ncols, int buf) {
+    if (base != nullptr && c < ncols)
+      for (int j = threadIdx.x >> tcl; j < n; j += blockDim.x >> tcl)
+        cp_async_elem<T>(sm + buf + j * TCp + c, base + j * ges + c);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  long long t = blockIdx.x;
+  int ncols_cur = 0;
+  cpx<T>* base_cur = (t < total) ? locate(t, &ncols_cur) : nullptr;
+  issue(base_cur, ncols_cur, bufA);
+  for (; t < total; t += gridDim.x) {
+    int ncols_next = 0;
+    cpx<T>* base_next = (t + gridDim.x < total) ? locate(t + gridDim.x, &ncols_next) : nullptr;
+    issue(base_next, ncols_next, bufB);
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncthreads();
+    if (base_cur != nullptr)
+      reg_columns_out<T>(bufA, bufC, base_cur, ges, ncols_cur, TCp, &Ps, inv != 0, 0);
+    else
+      __syncthreads();
+    const int tmp = bufA;
+    bufA = bufB;
+    bufB = tmp;
+    base_cur = base_next;
+    ncols_cur = ncols_next;
+  }
   cp_async_wait_all();
-  __syncthreads();
-  reg_columns_out<T>(b0, b1, base, ges, ncols, TCp, &Ps, inv != 0, 0);
 }
 
 // ---------------------------------------------------------------------------------------
