@@ -158,6 +158,8 @@ struct Loc {
   int es;
   int lo = 0;        // two-level lines: line l = (l_out << nli_log) + l_in sits at
   int nli_log = -1;  // l_in * ls + l_out * lo (nli_log < 0: one level, l * ls)
+  int nin = 1 << 30; // global side: lines whose inner index l_in >= nin (the columns past the
+                     // end of a ragged tile) are neither loaded nor stored
 };
 
 template <typename T>
@@ -180,6 +182,10 @@ __device__ __forceinline__ void reg_stage(Loc<T> in, Loc<T> out, int n, int p, i
   cpx<T>* sm = smem_c<T>();
   const int istride = m * in.es;
   const int ostride = p * out.es;
+  // lines past the end of a ragged global tile (inner index >= nin) are skipped
+  const int gnli = in.g != nullptr ? in.nli_log : out.nli_log;
+  const int gnin = in.g != nullptr ? in.nin : (out.g != nullptr ? out.nin : (1 << 30));
+  const int gmask = gnli < 0 ? -1 : (1 << gnli) - 1;
   for (int w = threadIdx.x; w < total; w += blockDim.x) {
     int l, i;
     if (colmajor) {
@@ -189,6 +195,7 @@ __device__ __forceinline__ void reg_stage(Loc<T> in, Loc<T> out, int n, int p, i
       l = fdiv(w, fd_m);
       i = w - l * m;
     }
+    if ((l & gmask) >= gnin) continue;
     const int k = i - fdiv(i, fd_p) * p;
     cpx<T> u[R];
     const int io = in.base + line_off(in, l) + i * in.es;
@@ -269,6 +276,12 @@ template <typename T>
 __device__ __forceinline__ Loc<T> sloc2(int base, int ls, int es, int lo, int nli_log) {
   return Loc<T>{nullptr, base, ls, es, lo, nli_log};
 }
+// a global tile of columns: column l at g + l, row j at g + j*es (one level), or component
+// l_out of a two-level line index at g + l_out*lo; only the first nin columns exist
+template <typename T>
+__device__ __forceinline__ Loc<T> gcols(cpx<T>* g, int es, int lo, int nli_log, int nin) {
+  return Loc<T>{g, 0, 1, es, lo, nli_log, nin};
+}
 
 // All stages of one axis on (2^nli_log inner) x (outer) lines of a two-level layout in shared
 // memory, ping-ponging between the buffers at a and b; returns the offset holding the result.
@@ -307,25 +320,32 @@ __device__ __forceinline__ int reg_lines(int a, int b, const AxisPlan* P, int nl
   return a;
 }
 
-// Column transform of a TC-column tile held in shared memory (natural order, at src, pitch
-// TCp); the last stage writes the global tile g (element (c, j) at g + c + j*ges); spare is the
-// ping-pong partner. Ends with a __syncthreads().
+// Column transform of a global tile in place (gl: nl columns, one- or two-level as in
+// gcols). The first stage loads its butterflies straight from the tile, the stages in between
+// ping-pong between the shared-memory buffers at a and b (element (l, j) at l_in + l_out*cstr +
+// j*TCp), and the last stage stores straight back; a single-stage plan reads and writes the
+// tile directly (each butterfly is then a whole column). No barrier after the final stores.
 template <typename T>
-__device__ __forceinline__ void reg_columns_out(int src, int spare, cpx<T>* g, int ges, int ncols,
-                                                int TCp, const AxisPlan* P, bool inv,
-                                                int tw_base) {
+__device__ __forceinline__ void reg_columns_global(Loc<T> gl, int a, int b, int TCp, int cstr,
+                                                   int nli_log, int nl, const AxisPlan* P,
+                                                   bool inv) {
   const int nst = P->nst;
-  int a = src, b = spare;
+  if (nst == 1) {
+    stage_any<T>(inv, P, 0, gl, gl, nl, true, 0);
+    return;
+  }
+  stage_any<T>(inv, P, 0, gl, sloc2<T>(a, 1, TCp, cstr, nli_log), nl, true, 0);
+  __syncthreads();
 #pragma unroll 1
-  for (int st = 0; st < nst - 1; ++st) {
-    stage_any<T>(inv, P, st, sloc<T>(a, 1, TCp), sloc<T>(b, 1, TCp), ncols, true, tw_base);
+  for (int st = 1; st < nst - 1; ++st) {
+    stage_any<T>(inv, P, st, sloc2<T>(a, 1, TCp, cstr, nli_log),
+                 sloc2<T>(b, 1, TCp, cstr, nli_log), nl, true, 0);
     __syncthreads();
     const int t = a;
     a = b;
     b = t;
   }
-  stage_any<T>(inv, P, nst - 1, sloc<T>(a, 1, TCp), Loc<T>{g, 0, 1, ges, 0, -1}, ncols, true, tw_base);
-  __syncthreads();
+  stage_any<T>(inv, P, nst - 1, sloc2<T>(a, 1, TCp, cstr, nli_log), gl, nl, true, 0);
 }
 
 }  // namespace hom

@@ -185,27 +185,8 @@ extern "C" int hom_apply_static(int d, const int* N, const void* phase_dev, int 
   int rc = static_setup(dev, &base);
   if (rc != HOM_OK) return rc;
 
-  // ---- launch geometry (the budgets of hom_create: two CTAs per SM) ----
-  const size_t budget = 110 * 1024;
-  g.LB = 16;
-  while (g.LB > 2 && Ops<double>::smem_line(nl, d, g.LB) > budget) g.LB -= 2;
-  auto tc_for = [&](int n, int nst, bool proj, int* TC, int* TCp) {
-    int tc = 32;
-    auto need = [&](int t) {
-      const int tp = t + (t % 2 == 0 ? 1 : 0);
-      return proj ? Ops<double>::smem_proj(n, d, tp) : Ops<double>::smem_strided(n, tp, nst);
-    };
-    while (tc > 2 && need(tc) > budget) tc /= 2;
-    *TC = tc;
-    *TCp = tc + (tc % 2 == 0 ? 1 : 0);
-  };
-  if (d == 3) tc_for(N[1], plan[1].nst, false, &g.TC1, &g.TC1p);
-  tc_for(N[0], plan[0].nst, true, &g.TC0, &g.TC0p);
-  tc_for(N[0], plan[0].nst, false, &g.TCs0, &g.TCs0p);
-  const size_t cap = (size_t)dynamic_smem_cap();
-  if (Ops<double>::smem_line(nl, d, g.LB) > cap || Ops<double>::smem_proj(N[0], d, g.TC0p) > cap ||
-      (d == 3 && Ops<double>::smem_strided(N[1], g.TC1p, plan[1].nst) > cap))
-    return HOM_ERR_UNSUPPORTED;
+  // ---- launch geometry (the default budget of hom_create) ----
+  if (!Ops<double>::plan_geometry(d, N, plan, 110 * 1024, &g)) return HOM_ERR_UNSUPPORTED;
 
   // ---- twiddles and table into the scratch (ordered on the caller's stream) ----
   cudaStream_t st = (cudaStream_t)stream;

@@ -21,9 +21,10 @@ struct PassGeom {
   int nh;             // (n[D-1] + 1) / 2
   long long scs;      // spectrum component stride: nlines * nh
   int LB;             // lines per CTA in the line passes (even)
-  int TC1, TC1p;      // strided pass along axis 1 (D = 3): columns per CTA, padded pitch
-  int TCs0, TCs0p;    // plain strided pass along axis 0 (prolongation, Ga assembly)
-  int TC0, TC0p;      // axis-0 passes (projection / plain strided): columns per CTA, pitch
+  int TC1, TC1p, NT1;     // strided pass along axis 1 (D = 3): columns per CTA, padded pitch,
+                          // threads per CTA
+  int TCs0, TCs0p, NTs0;  // plain strided pass along axis 0 (prolongation, Ga assembly)
+  int TC0, TC0p, NT0;     // projection pass (axis 0, all components)
 };
 
 template <typename T>
@@ -31,7 +32,11 @@ struct Ops {
   static cudaError_t upload_constants();
   static size_t smem_line(int n, int ncomp, int LB);
   static size_t smem_strided(int n, int TCp, int nst);
-  static size_t smem_proj(int n, int D, int TCp);
+  static size_t smem_proj(int n, int D, int TCp, int nst);
+  // launch geometry of every pass of a grid with axis plans `plan`, keeping each CTA's shared
+  // memory within `budget` bytes; false if a pass cannot fit the device limit
+  static bool plan_geometry(int D, const int* n, const AxisPlan* plan, size_t budget,
+                            PassGeom* g);
   static cudaError_t prepare(int maxD);  // raise dynamic shared memory limits
 
   // reqs / nreq: optional per-request descriptors of a batched launch (grid.z = nreq); the

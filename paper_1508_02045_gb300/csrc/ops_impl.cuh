@@ -2,7 +2,10 @@
 #pragma once
 #include <cmath>
 #include <vector>
+#include <type_traits>
+
 #include "ops.h"
+#include "pair_fft.cuh"
 #include "passes.cuh"
 
 namespace hom {
@@ -37,12 +40,65 @@ size_t Ops<T>::smem_line(int n, int ncomp, int LB) {
 }
 template <typename T>
 size_t Ops<T>::smem_strided(int n, int TCp, int nst) {
-  (void)nst;  // two staging buffers (pipelined tiles) + one stage buffer
-  return sizeof(cpx<T>) * ((size_t)n + 3 * (size_t)n * TCp);
+  // twiddles + the stage buffers between the first and the last stage
+  const size_t nbuf = nst >= 3 ? 2 : (nst == 2 ? 1 : 0);
+  return sizeof(cpx<T>) * ((size_t)n + nbuf * (size_t)n * TCp);
 }
 template <typename T>
-size_t Ops<T>::smem_proj(int n, int D, int TCp) {
-  return sizeof(cpx<T>) * ((size_t)n + (size_t)(2 * D) * n * TCp);
+size_t Ops<T>::smem_proj(int n, int D, int TCp, int nst) {
+  const size_t nbuf = nst >= 2 ? 2 : 1;
+  return sizeof(cpx<T>) * ((size_t)n + nbuf * (size_t)D * n * TCp);
+}
+
+// Columns per CTA of a column kernel (a power of two <= tcmax, pitch TC + 1) and its threads:
+// the widest tile whose first-stage butterflies (lines x TC x n / R_0) fit the thread limit and
+// whose shared memory fits the budget, but at least one 32-byte sector of every row (unless
+// the device limit forces narrower tiles). Threads:
+// one per butterfly, rounded up to whole warps and to a multiple of TC, at most kColThreads.
+template <typename T>
+static void pick_cols(const AxisPlan& P, int lines, int tcmax, size_t budget, bool proj, int D,
+                      int* TC, int* TCp, int* NT) {
+  const int m1 = P.n / P.radix[0];
+  const int tcmin = std::max(1, 32 / (int)sizeof(cpx<T>));
+  auto smem = [&](int t) {
+    return proj ? Ops<T>::smem_proj(P.n, D, t + 1, P.nst) : Ops<T>::smem_strided(P.n, t + 1, P.nst);
+  };
+  int tc = tcmax;
+  while (tc > tcmin && ((long long)lines * tc * m1 > kColThreads<T> || smem(tc) > budget)) tc /= 2;
+  // long axes: narrower tiles rather than none at all
+  while (tc > 1 && smem(tc) > (size_t)dynamic_smem_cap()) tc /= 2;
+  *TC = tc;
+  *TCp = tc + 1;
+  const int unit = std::max(32, tc);
+  const long long items = (long long)lines * tc * m1;
+  *NT = (int)std::min<long long>(kColThreads<T> / unit * unit, (items + unit - 1) / unit * unit);
+}
+
+template <typename T>
+bool Ops<T>::plan_geometry(int D, const int* n, const AxisPlan* plan, size_t budget,
+                           PassGeom* g) {
+  g->D = D;
+  g->nodes = 1;
+  for (int a = 0; a < D; ++a) {
+    g->n[a] = n[a];
+    g->nodes *= n[a];
+  }
+  for (int a = D; a < 3; ++a) g->n[a] = 1;
+  const int nl = n[D - 1];
+  g->nh = (nl + 1) / 2;
+  g->nlines = g->nodes / nl;
+  g->scs = g->nlines * g->nh;
+  g->LB = 16;
+  while (g->LB > 2 && smem_line(nl, D, g->LB) > budget) g->LB -= 2;
+  if (D == 3) pick_cols<T>(plan[1], 1, 64, budget, false, D, &g->TC1, &g->TC1p, &g->NT1);
+  pick_cols<T>(plan[0], D, 32, budget, true, D, &g->TC0, &g->TC0p, &g->NT0);
+  pick_cols<T>(plan[0], 1, 64, budget, false, D, &g->TCs0, &g->TCs0p, &g->NTs0);
+  // the column kernels address the D component tiles with 32-bit offsets
+  if ((long long)D * g->scs >= (1LL << 31)) return false;
+  const size_t cap = (size_t)dynamic_smem_cap();
+  return smem_line(nl, D, g->LB) <= cap && smem_proj(n[0], D, g->TC0p, plan[0].nst) <= cap &&
+         (D != 3 || smem_strided(n[1], g->TC1p, plan[1].nst) <= cap) &&
+         smem_strided(n[0], g->TCs0p, plan[0].nst) <= cap;
 }
 
 // number of SMs of the current device (cached per process)
@@ -102,6 +158,17 @@ cudaError_t Ops<T>::prepare(int) {
   HOM_SET_SMEM((k_line_inv<T, 3, POST_CG>));
   HOM_SET_SMEM((k_line_inv<T, 3, POST_CHEB>));
   HOM_SET_SMEM((k_line_inv<T, 3, POST_EM>));
+  if constexpr (std::is_same<T, float>::value) {
+#define HOM_PAIR_SMEM(R1_, R2_)                                 \
+  HOM_SET_SMEM((k_pair_strided<T, R1_, R2_, false>));           \
+  HOM_SET_SMEM((k_pair_strided<T, R1_, R2_, true>));            \
+  HOM_SET_SMEM((k_pair_proj<T, 2, PROJ_GAMMA, R1_, R2_>));      \
+  HOM_SET_SMEM((k_pair_proj<T, 2, PROJ_EM, R1_, R2_>));         \
+  HOM_SET_SMEM((k_pair_proj<T, 3, PROJ_GAMMA, R1_, R2_>));      \
+  HOM_SET_SMEM((k_pair_proj<T, 3, PROJ_EM, R1_, R2_>));
+    HOM_PAIR_PLANS(HOM_PAIR_SMEM)
+#undef HOM_PAIR_SMEM
+  }
   return cudaSuccess;
 }
 
@@ -136,12 +203,71 @@ void Ops<T>::line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
   else line_fwd_d<T, 3>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq);
 }
 
+// an FP32 two-stage plan with compile-time column kernels (pair_fft.cuh)
+template <typename T>
+static bool pair_plan(const AxisPlan& P) {
+  if (!std::is_same<T, float>::value || P.nst != 2) return false;
+#define HOM_PAIR_IS(R1_, R2_) \
+  if (P.radix[0] == R1_ && P.radix[1] == R2_) return true;
+  HOM_PAIR_PLANS(HOM_PAIR_IS)
+#undef HOM_PAIR_IS
+  return false;
+}
+
+template <typename T>
+static void pair_strided(const AxisPlan& P, int inv, cpx<T>* S, const cpx<T>* tw, long long C,
+                         long long es, long long bs, int batches, const Scalars* sc,
+                         cudaStream_t st, const ReqDesc<T>* reqs, int nreq) {
+  if constexpr (std::is_same<T, float>::value) {
+#define HOM_PAIR_ST(R1_, R2_)                                                                  \
+  if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
+    constexpr int TC = pair_tc_strided<R2_>();                                                 \
+    const dim3 grid((unsigned)((C + TC - 1) / TC), (unsigned)batches, (unsigned)nreq);        \
+    const size_t sm = sizeof(cpx<T>) * (size_t)(R1_ * R2_) * (TC + 2);                          \
+    if (inv)                                                                                   \
+      k_pair_strided<T, R1_, R2_, true><<<grid, TC * R2_, sm, st>>>(S, tw, C, es, bs, sc, reqs); \
+    else                                                                                       \
+      k_pair_strided<T, R1_, R2_, false><<<grid, TC * R2_, sm, st>>>(S, tw, C, es, bs, sc, reqs); \
+    return;                                                                                    \
+  }
+    HOM_PAIR_PLANS(HOM_PAIR_ST)
+#undef HOM_PAIR_ST
+  }
+}
+
+template <typename T>
+static void pair_proj(int D, int mode, const AxisPlan& P, cpx<T>* S, const cpx<T>* tw,
+                      const ProjGeom& pg, const Scalars* sc, cudaStream_t st,
+                      const ReqDesc<T>* reqs, int nreq) {
+  if constexpr (std::is_same<T, float>::value) {
+#define HOM_PAIR_PJ_D(D_, R1_, R2_)                                                            \
+  {                                                                                            \
+    constexpr int TC = pair_tc_proj<D_, R2_>();                                                \
+    const dim3 grid((unsigned)((pg.C + TC - 1) / TC), 1, (unsigned)nreq);                     \
+    const size_t sm = sizeof(cpx<T>) * ((size_t)(R1_ * R2_) * (1 + 2 * D_ * (TC + 1)));        \
+    if (mode == PROJ_EM)                                                                       \
+      k_pair_proj<T, D_, PROJ_EM, R1_, R2_><<<grid, D_ * TC * R2_, sm, st>>>(S, tw, pg, sc, reqs); \
+    else                                                                                       \
+      k_pair_proj<T, D_, PROJ_GAMMA, R1_, R2_><<<grid, D_ * TC * R2_, sm, st>>>(S, tw, pg, sc, reqs); \
+  }
+#define HOM_PAIR_PJ(R1_, R2_)                               \
+  if (P.radix[0] == R1_ && P.radix[1] == R2_) {             \
+    if (D == 2) HOM_PAIR_PJ_D(2, R1_, R2_)                  \
+    else HOM_PAIR_PJ_D(3, R1_, R2_)                         \
+    return;                                                 \
+  }
+    HOM_PAIR_PLANS(HOM_PAIR_PJ)
+#undef HOM_PAIR_PJ
+#undef HOM_PAIR_PJ_D
+  }
+}
+
 template <typename T>
 void Ops<T>::strided(const PassGeom& g, int axis, int inv, cpx<T>* S, const AxisPlan& P,
                      const cpx<T>* tw, int ncomp, const Scalars* sc, cudaStream_t st,
                      const ReqDesc<T>* reqs, int nreq) {
   long long C, es, bs;
-  int batches, TC, TCp;
+  int batches, TC, TCp, NT;
   if (g.D == 3 && axis == 1) {
     C = g.nh;
     es = g.nh;
@@ -149,6 +275,7 @@ void Ops<T>::strided(const PassGeom& g, int axis, int inv, cpx<T>* S, const Axis
     batches = ncomp * g.n[0];
     TC = g.TC1;
     TCp = g.TC1p;
+    NT = g.NT1;
   } else {  // axis 0
     C = g.scs / g.n[0];
     es = C;
@@ -156,14 +283,17 @@ void Ops<T>::strided(const PassGeom& g, int axis, int inv, cpx<T>* S, const Axis
     batches = ncomp;
     TC = g.TCs0;
     TCp = g.TCs0p;
+    NT = g.NTs0;
   }
-  // persistent grid: at most two CTAs per SM, each walking tiles with a prefetch pipeline
-  const long long tiles = ((C + TC - 1) / TC) * (long long)batches * nreq;
-  const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)num_sms() * 2);
-  const size_t sm = smem_strided(P.n, TCp, P.nst);
   const bool prof = profiling();
   if (prof) prof_mark(KIND_STRIDED, st, true);
-  k_strided<T><<<grid, kThreads, sm, st>>>(S, P, tw, C, es, bs, TC, TCp, inv, sc, reqs, batches, nreq);
+  if (pair_plan<T>(P)) {
+    pair_strided<T>(P, inv, S, tw, C, es, bs, batches, sc, st, reqs, nreq);
+  } else {
+    const dim3 grid((unsigned)((C + TC - 1) / TC), (unsigned)batches, (unsigned)nreq);
+    const size_t sm = smem_strided(P.n, TCp, P.nst);
+    k_strided<T><<<grid, NT, sm, st>>>(S, P, tw, C, es, bs, TC, TCp, inv, sc, reqs);
+  }
   if (prof) prof_mark(KIND_STRIDED, st, false);
   ++launch_counter();
 }
@@ -172,11 +302,17 @@ template <typename T>
 void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, const cpx<T>* tw,
                   const ProjGeom& pg, const Scalars* sc, cudaStream_t st,
                   const ReqDesc<T>* reqs, int nreq) {
-  const dim3 grid((unsigned)((pg.C + g.TC0 - 1) / g.TC0), 1, (unsigned)nreq);
-  const size_t sm = smem_proj(P.n, g.D, g.TC0p);
   const bool prof = profiling();
   if (prof) prof_mark(KIND_PROJ, st, true);
-#define HOM_PJ(D_, M_) k_proj<T, D_, M_><<<grid, kThreads, sm, st>>>(S, P, tw, pg, g.TC0, g.TC0p, sc, reqs)
+  if (pair_plan<T>(P)) {
+    pair_proj<T>(g.D, mode, P, S, tw, pg, sc, st, reqs, nreq);
+    if (prof) prof_mark(KIND_PROJ, st, false);
+    ++launch_counter();
+    return;
+  }
+  const dim3 grid((unsigned)((pg.C + g.TC0 - 1) / g.TC0), 1, (unsigned)nreq);
+  const size_t sm = smem_proj(P.n, g.D, g.TC0p, P.nst);
+#define HOM_PJ(D_, M_) k_proj<T, D_, M_><<<grid, g.NT0, sm, st>>>(S, P, tw, pg, g.TC0, g.TC0p, sc, reqs)
   if (g.D == 2) {
     if (mode == PROJ_EM) HOM_PJ(2, PROJ_EM); else HOM_PJ(2, PROJ_GAMMA);
   } else {

@@ -1,0 +1,224 @@
+// Column passes specialised at compile time for two-stage plans n = R1 * R2 (FP32).
+//
+// The generic column kernels take the radices, strides and work split at run time; for the
+// axis lengths of the usual grids the whole transform is fixed at compile time instead:
+//   stage 1 (radix R1, p = 1): butterfly i < R2 of a column reads rows i + r R2 straight from
+//     the spectrum, and writes rows i R1 + r of a shared-memory tile;
+//   stage 2 (radix R2, p = R1): butterfly i < R1 reads rows i + r R1 of the tile, applies the
+//     twiddles w_n^{r i}, and writes rows i + r R1 (natural order) straight back.
+// The inverse transform is conj(F(conj .)): conjugated on the first load and the last store.
+// Threads map to (column, butterfly) with the column fastest, so every row segment of a
+// warp's global access is contiguous.
+#pragma once
+#include "passes.cuh"
+
+namespace hom {
+
+// the two-stage plans with specialised kernels: (R1, R2), R1 >= R2, as the planner groups
+// the prime factors of 243, 405, 81, 135, 45, 161, 63, 189 and 175
+#define HOM_PAIR_PLANS(X) \
+  X(27, 9)                \
+  X(27, 15)               \
+  X(27, 3)                \
+  X(15, 9)                \
+  X(15, 3)                \
+  X(23, 7)                \
+  X(21, 3)                \
+  X(21, 9)                \
+  X(25, 7)
+
+// columns per CTA: 16 (128-byte rows) for the strided pass; for the projection pass the
+// widest power of two <= 16 with D * TC * R2 <= 256 threads
+template <int R2>
+__host__ __device__ constexpr int pair_tc_strided() {
+  return 16;
+}
+template <int D, int R2>
+__host__ __device__ constexpr int pair_tc_proj() {
+  return D * 16 * R2 <= 256 ? 16 : D * 8 * R2 <= 256 ? 8 : D * 4 * R2 <= 256 ? 4 : 2;
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void conj_all(cpx<T> (&u)[R]) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) u[r].y = -u[r].y;
+}
+
+// stage 1 of one column: g = the column's first row (row stride es), t = its shared-memory
+// column (row stride TCp)
+template <typename T, int R1, int R2, bool INV>
+__device__ __forceinline__ void pair_stage1_from_global(const cpx<T>* g, long long es, cpx<T>* t,
+                                                        int TCp, int i) {
+  cpx<T> u[R1];
+#pragma unroll
+  for (int r = 0; r < R1; ++r) u[r] = g[(long long)(i + r * R2) * es];
+  if (INV) conj_all<T, R1>(u);
+  RegDft<T, R1>::run(u);
+#pragma unroll
+  for (int r = 0; r < R1; ++r) t[(i * R1 + r) * TCp] = u[r];
+}
+
+// stage 1 of one column held in shared memory (natural order in s, result in t)
+template <typename T, int R1, int R2, bool CONJ_IN>
+__device__ __forceinline__ void pair_stage1_shared(const cpx<T>* s, cpx<T>* t, int TCp, int i) {
+  cpx<T> u[R1];
+#pragma unroll
+  for (int r = 0; r < R1; ++r) u[r] = s[(i + r * R2) * TCp];
+  if (CONJ_IN) conj_all<T, R1>(u);
+  RegDft<T, R1>::run(u);
+#pragma unroll
+  for (int r = 0; r < R1; ++r) t[(i * R1 + r) * TCp] = u[r];
+}
+
+// stage 2 of one column into registers: u[r] = X[i + r R1]
+template <typename T, int R1, int R2>
+__device__ __forceinline__ void pair_stage2_regs(const cpx<T>* t, const cpx<T>* tw, int TCp, int i,
+                                                 cpx<T> (&u)[R2]) {
+#pragma unroll
+  for (int r = 0; r < R2; ++r) u[r] = t[(i + r * R1) * TCp];
+#pragma unroll
+  for (int r = 1; r < R2; ++r) u[r] = cmul(u[r], tw[r * i]);
+  RegDft<T, R2>::run(u);
+}
+
+// ---------------------------------------------------------------------------------------
+// strided pass along axis 1 (or a plain pass along axis 0): blockIdx.x = column tile,
+// blockIdx.y = batch, blockIdx.z = request; TC * R2 threads
+// ---------------------------------------------------------------------------------------
+template <typename T, int R1, int R2, bool INV>
+__global__ void __launch_bounds__(pair_tc_strided<R2>() * R2)
+k_pair_strided(cpx<T>* S, const cpx<T>* __restrict__ twg, long long C, long long es,
+               long long bs, const Scalars* sc, const ReqDesc<T>* __restrict__ reqs) {
+  constexpr int n = R1 * R2, TC = pair_tc_strided<R2>(), TCp = TC + 1, NT = TC * R2;
+  if (reqs != nullptr) {
+    S = reqs[blockIdx.z].S;
+    sc = reqs[blockIdx.z].sc;
+  }
+  if (sc != nullptr && sc->done) return;
+  cpx<T>* sm = smem_c<T>();
+  cpx<T>* tw = sm;
+  cpx<T>* tile = sm + n;
+  for (int i = threadIdx.x; i < n; i += NT) tw[i] = twg[i];
+  const long long c0 = (long long)blockIdx.x * TC;
+  const int ncols = (int)min((long long)TC, C - c0);
+  cpx<T>* base = S + (long long)blockIdx.y * bs + c0;
+  {
+    const int c = threadIdx.x % TC, i = threadIdx.x / TC;
+    if (c < ncols) pair_stage1_from_global<T, R1, R2, INV>(base + c, es, tile + c, TCp, i);
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < TC * R1; w += NT) {
+    const int c = w % TC, i = w / TC;
+    if (c >= ncols) continue;
+    cpx<T> u[R2];
+    pair_stage2_regs<T, R1, R2>(tile + c, tw, TCp, i, u);
+    if (INV) conj_all<T, R2>(u);
+#pragma unroll
+    for (int r = 0; r < R2; ++r) base[(long long)(i + r * R1) * es + c] = u[r];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// projection pass: forward DFT of axis 0, Gamma^ (or I - 2 Gamma^), inverse DFT of axis 0, on
+// a tile of TC columns of all D components; D * TC * R2 threads
+// ---------------------------------------------------------------------------------------
+template <typename T, int D, int MODE, int R1, int R2>
+__global__ void __launch_bounds__(D * pair_tc_proj<D, R2>() * R2)
+k_pair_proj(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, const Scalars* sc,
+            const ReqDesc<T>* __restrict__ reqs) {
+  constexpr int n = R1 * R2, TC = pair_tc_proj<D, R2>(), TCp = TC + 1, NT = D * TC * R2;
+  constexpr int cstr = n * TCp;
+  if (reqs != nullptr) {
+    S = reqs[blockIdx.z].S;
+    sc = reqs[blockIdx.z].sc;
+  }
+  if (sc != nullptr && sc->done) return;
+  cpx<T>* sm = smem_c<T>();
+  cpx<T>* tw = sm;
+  cpx<T>* A = sm + n;         // D tiles, component stride cstr
+  cpx<T>* B = A + D * cstr;
+  for (int i = threadIdx.x; i < n; i += NT) tw[i] = twg[i];
+  const long long c0 = (long long)blockIdx.x * TC;
+  const int ncols = (int)min((long long)TC, g.C - c0);
+  const long long es = g.C;
+  // forward stage 1, from the spectrum: item (a, i, c)
+  {
+    const int c = threadIdx.x % TC, i = (threadIdx.x / TC) % R2, a = threadIdx.x / (TC * R2);
+    if (c < ncols)
+      pair_stage1_from_global<T, R1, R2, false>(S + a * g.cs + c0 + c, es, A + a * cstr + c, TCp, i);
+  }
+  __syncthreads();
+  // forward stage 2 of all D components + the projection at the R2 frequencies of item (i, c)
+  const T scale = (T)g.scale;
+  for (int w = threadIdx.x; w < TC * R1; w += NT) {
+    const int c = w % TC, i = w / TC;
+    int kc1 = 0, kc2 = 0;
+    const int cc = (int)(c0 + c);
+    if (D == 3) {
+      const int i1 = fdiv(cc, g.fdnh);
+      kc1 = (i1 <= (g.n1 - 1) / 2) ? i1 : i1 - g.n1;
+      kc2 = cc - i1 * g.nh;
+    } else {
+      kc1 = cc;
+    }
+    cpx<T> v[D][R2];
+#pragma unroll
+    for (int a = 0; a < D; ++a) pair_stage2_regs<T, R1, R2>(A + a * cstr + c, tw, TCp, i, v[a]);
+#pragma unroll
+    for (int r = 0; r < R2; ++r) {
+      const int j = i + r * R1;
+      int k[3];
+      k[0] = (j <= (n - 1) / 2) ? j : j - n;
+      k[1] = kc1;
+      k[2] = kc2;
+      bool inside = true;
+      int kk = 0;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        inside = inside && (abs(k[a]) <= g.hw[a]);
+        kk += k[a] * k[a];
+      }
+      cpx<T> kv = {0, 0};
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        kv.x = fma((T)k[a], v[a][r].x, kv.x);
+        kv.y = fma((T)k[a], v[a][r].y, kv.y);
+      }
+      const T coef = (kk > 0 && inside) ? scale / (T)kk : (T)0;
+      kv.x *= coef;
+      kv.y *= coef;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        cpx<T> o;
+        if (MODE == PROJ_GAMMA) {
+          o.x = (T)k[a] * kv.x;
+          o.y = (T)k[a] * kv.y;
+        } else {  // (I - 2 Gamma^) v
+          o.x = fma((T)(-2 * k[a]), kv.x, scale * v[a][r].x);
+          o.y = fma((T)(-2 * k[a]), kv.y, scale * v[a][r].y);
+        }
+        B[a * cstr + j * TCp + c] = o;
+      }
+    }
+  }
+  __syncthreads();
+  // inverse stage 1 (conjugated input), shared memory to shared memory: item (a, i, c)
+  {
+    const int c = threadIdx.x % TC, i = (threadIdx.x / TC) % R2, a = threadIdx.x / (TC * R2);
+    pair_stage1_shared<T, R1, R2, true>(B + a * cstr + c, A + a * cstr + c, TCp, i);
+  }
+  __syncthreads();
+  // inverse stage 2 into the spectrum (conjugated output): item (a, i, c)
+  for (int w = threadIdx.x; w < D * TC * R1; w += NT) {
+    const int c = w % TC, i = (w / TC) % R1, a = w / (TC * R1);
+    if (c >= ncols) continue;
+    cpx<T> u[R2];
+    pair_stage2_regs<T, R1, R2>(A + a * cstr + c, tw, TCp, i, u);
+    conj_all<T, R2>(u);
+    cpx<T>* out = S + a * g.cs + c0 + c;
+#pragma unroll
+    for (int r = 0; r < R2; ++r) out[(long long)(i + r * R1) * es] = u[r];
+  }
+}
+
+}  // namespace hom

@@ -27,6 +27,12 @@ namespace hom {
 template <typename T>
 constexpr int kMinBlocks = 2;
 
+// thread limit of the column kernels (strided, proj): compiled, like the line kernels, for
+// 128 registers a thread (a radix-27 FP32 or radix-15 FP64 butterfly held in registers); the
+// stage functions they share are compiled once for that budget
+template <typename T>
+constexpr int kColThreads = kThreads;
+
 // ---------------------------------------------------------------------------------------
 // deterministic block reduction + last-block finisher
 // ---------------------------------------------------------------------------------------
@@ -342,71 +348,30 @@ k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
 // ---------------------------------------------------------------------------------------
 // strided: DFT along a strided axis, in place; blockIdx.y = batch, blockIdx.x = column tile
 // ---------------------------------------------------------------------------------------
-// Persistent and software-pipelined: each CTA walks tiles t = blockIdx.x, + gridDim.x, ...
-// over all requests, batches and column chunks; while it transforms tile t (staged in buffer
-// A) the asynchronous copies of tile t + gridDim.x fill buffer B.
+// One CTA per tile of TC columns, one thread per first-stage butterfly (TC x n / R_0, capped at
+// kColThreads): the first stage reads the rows of the tile straight from the spectrum (a warp
+// takes consecutive columns, so each row segment is one coalesced access) and the last stage
+// writes them back, so the tile crosses shared memory only between stages.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
-k_strided(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, long long C,
-          long long es, long long bs, int TC, int TCp, int inv, const Scalars* sc,
-          const ReqDesc<T>* __restrict__ reqs, int nbatch, int nreq) {
+__global__ void __launch_bounds__(kColThreads<T>, 2)
+k_strided(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, long long C, long long es,
+          long long bs, int TC, int TCp, int inv, const Scalars* sc,
+          const ReqDesc<T>* __restrict__ reqs) {
+  if (reqs != nullptr) {
+    S = reqs[blockIdx.z].S;
+    sc = reqs[blockIdx.z].sc;
+  }
+  if (sc != nullptr && sc->done) return;
   const int n = P.n;
   cpx<T>* sm = smem_c<T>();
-  const int tile_elems = n * TCp;
-  int bufA = n, bufB = n + tile_elems;
-  const int bufC = n + 2 * tile_elems;
   __shared__ AxisPlan Ps;
   if (threadIdx.x == 0) Ps = P;
   for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = twg[i];
-  const int ntc = (int)((C + TC - 1) / TC);
-  const long long total = (long long)nreq * nbatch * ntc;
-  const int tcl = __ffs(TC) - 1;
-  const int c = threadIdx.x & (TC - 1);
-  const int ges = (int)es;
-  // tile t -> (request, batch, column chunk); returns the tile's global base (or null when the
-  // request has stopped) and its column count
-  auto locate = [&](long long t, int* ncols) -> cpx<T>* {
-    const int q = (int)(t / ((long long)nbatch * ntc));
-    const int rem = (int)(t - (long long)q * nbatch * ntc);
-    const int b = rem / ntc, chunk = rem - b * ntc;
-    cpx<T>* Sq = S;
-    const Scalars* scq = sc;
-    if (reqs != nullptr) {
-      Sq = reqs[q].S;
-      scq = reqs[q].sc;
-    }
-    if (scq != nullptr && scq->done) return nullptr;
-    const long long c0 = (long long)chunk * TC;
-    *ncols = (int)min((long long)TC, C - c0);
-    return Sq + (long long)b * bs + c0;
-  };
-  auto issue = [&](cpx<T>* base, int ncols, int buf) {
-    if (base != nullptr && c < ncols)
-      for (int j = threadIdx.x >> tcl; j < n; j += blockDim.x >> tcl)
-        cp_async_elem<T>(sm + buf + j * TCp + c, base + j * ges + c);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-  };
-  long long t = blockIdx.x;
-  int ncols_cur = 0;
-  cpx<T>* base_cur = (t < total) ? locate(t, &ncols_cur) : nullptr;
-  issue(base_cur, ncols_cur, bufA);
-  for (; t < total; t += gridDim.x) {
-    int ncols_next = 0;
-    cpx<T>* base_next = (t + gridDim.x < total) ? locate(t + gridDim.x, &ncols_next) : nullptr;
-    issue(base_next, ncols_next, bufB);
-    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-    __syncthreads();
-    if (base_cur != nullptr)
-      reg_columns_out<T>(bufA, bufC, base_cur, ges, ncols_cur, TCp, &Ps, inv != 0, 0);
-    else
-      __syncthreads();
-    const int tmp = bufA;
-    bufA = bufB;
-    bufB = tmp;
-    base_cur = base_next;
-    ncols_cur = ncols_next;
-  }
-  cp_async_wait_all();
+  __syncthreads();
+  const long long c0 = (long long)blockIdx.x * TC;
+  const int ncols = (int)min((long long)TC, C - c0);
+  const Loc<T> gl = gcols<T>(S + (long long)blockIdx.y * bs + c0, (int)es, 0, -1, ncols);
+  reg_columns_global<T>(gl, n, n + n * TCp, TCp, 0, -1, ncols, &Ps, inv != 0);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -422,8 +387,12 @@ struct ProjGeom {
   double scale;   // 1/|grid| of the forward transform (eq. (DFT))
 };
 
+// One CTA per tile of TC columns of all D components (two-level line index: component a,
+// column c), one thread per first-stage butterfly (D x TC x n / R_0, capped at kColThreads).
+// The forward transform loads the tile straight from the spectrum; the projection works in
+// shared memory; the last inverse stage stores straight back.
 template <typename T, int D, int MODE>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
+__global__ void __launch_bounds__(kColThreads<T>, 2)
 k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC,
        int TCp, const Scalars* sc, const ReqDesc<T>* __restrict__ reqs) {
   if (reqs != nullptr) {
@@ -433,32 +402,36 @@ k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC
   if (sc != nullptr && sc->done) return;
   const int n = P.n;
   cpx<T>* sm = smem_c<T>();
-  // two buffers, each holding the D component tiles (n x TCp, component stride n * TCp); every
-  // stage transforms all D * TC columns at once
+  // buffers each hold the D component tiles (n x TCp, component stride cstr)
   const int cstr = n * TCp;
   const int bufA = n, bufB = n + D * cstr;
   __shared__ AxisPlan Ps;
   if (threadIdx.x == 0) Ps = P;
   for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = twg[i];
-  const long long c0 = (long long)blockIdx.x * TC;
-  const int es = (int)g.C;
-  const int ncols = (int)min((long long)TC, g.C - c0);
-  // stage the tiles of all components with asynchronous copies; TC is a power of two dividing
-  // the block, so every thread keeps one column c (columns >= ncols are zero-filled)
-  const int tcl = __ffs(TC) - 1;
-  const int c = threadIdx.x & (TC - 1);
-  const cpx<T> zero = {0, 0};
-#pragma unroll
-  for (int a = 0; a < D; ++a)
-    for (int j = threadIdx.x >> tcl; j < n; j += blockDim.x >> tcl) {
-      if (c < ncols) cp_async_elem<T>(sm + bufA + a * cstr + j * TCp + c, S + a * g.cs + c0 + j * es + c);
-      else sm[bufA + a * cstr + j * TCp + c] = zero;
-    }
-  cp_async_wait_all();
   __syncthreads();
-  const int fwd = reg_lines2<T>(bufA, bufB, &Ps, D * TC, TCp, cstr, tcl, false, 0);
+  const long long c0 = (long long)blockIdx.x * TC;
+  const int ncols = (int)min((long long)TC, g.C - c0);
+  const int tcl = __ffs(TC) - 1;
+  const Loc<T> gl = gcols<T>(S + c0, (int)g.C, (int)g.cs, tcl, ncols);
+  const int nl = D * TC;
+  const int nst = Ps.nst;
+  // forward DFT of axis 0: first stage from the spectrum, the rest in shared memory
+  stage_any<T>(false, &Ps, 0, gl, sloc2<T>(bufA, 1, TCp, cstr, tcl), nl, true, 0);
+  __syncthreads();
+  int fwd = bufA, other = bufB;
+#pragma unroll 1
+  for (int st = 1; st < nst; ++st) {
+    stage_any<T>(false, &Ps, st, sloc2<T>(fwd, 1, TCp, cstr, tcl),
+                 sloc2<T>(other, 1, TCp, cstr, tcl), nl, true, 0);
+    __syncthreads();
+    const int t = fwd;
+    fwd = other;
+    other = t;
+  }
   const T scale = (T)g.scale;
-  // frequencies of this thread's column (fixed over the rows)
+  // frequencies of this thread's column (fixed over the rows); columns past a ragged tile's
+  // end hold stale values that are transformed but never stored
+  const int c = threadIdx.x & (TC - 1);
   int kc1 = 0, kc2 = 0;
   {
     const int cc = (int)(c0 + c);
@@ -508,13 +481,18 @@ k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC
     }
   }
   __syncthreads();
-  const int other = (fwd == bufA) ? bufB : bufA;
-  const int res = reg_lines2<T>(fwd, other, &Ps, D * TC, TCp, cstr, tcl, true, 0);
-  if (c < ncols)
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-      for (int j = threadIdx.x >> tcl; j < n; j += blockDim.x >> tcl)
-        S[a * g.cs + c0 + j * es + c] = sm[res + a * cstr + j * TCp + c];
+  // inverse DFT of axis 0: stages in shared memory, the last one into the spectrum
+  int a = fwd, b = other;
+#pragma unroll 1
+  for (int st = 0; st < nst - 1; ++st) {
+    stage_any<T>(true, &Ps, st, sloc2<T>(a, 1, TCp, cstr, tcl), sloc2<T>(b, 1, TCp, cstr, tcl),
+                 nl, true, 0);
+    __syncthreads();
+    const int t = a;
+    a = b;
+    b = t;
+  }
+  stage_any<T>(true, &Ps, nst - 1, sloc2<T>(a, 1, TCp, cstr, tcl), gl, nl, true, 0);
 }
 
 // ---------------------------------------------------------------------------------------

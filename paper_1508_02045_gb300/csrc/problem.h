@@ -85,28 +85,6 @@ std::vector<cpx<T>> twiddles(int n) {
   return tw;
 }
 
-// Largest even LB (lines per CTA in the line passes) whose buffers fit the budget.
-template <typename T>
-int pick_LB(int n, int ncomp, size_t budget) {
-  int LB = 16;
-  while (LB > 2 && Ops<T>::smem_line(n, ncomp, LB) > budget) LB -= 2;
-  return LB;
-}
-
-// columns per CTA of a column pass: the widest tile (<= 32 columns, 128-byte rows for FP32 at
-// 16) whose shared-memory buffers fit the budget; odd pitch for conflict-free column access
-template <typename T>
-void pick_TC(int n, int nst, size_t budget, int* TC, int* TCp, bool proj, int D) {
-  int tc = 32;
-  auto need = [&](int t) {
-    const int tp = t + ((t % 2 == 0) ? 1 : 0);
-    return proj ? Ops<T>::smem_proj(n, D, tp) : Ops<T>::smem_strided(n, tp, nst);
-  };
-  while (tc > 2 && need(tc) > budget) tc /= 2;
-  *TC = tc;
-  *TCp = tc + ((tc % 2 == 0) ? 1 : 0);
-}
-
 // ---------------------------------------------------------------------------------------
 // per-precision engine: plans, twiddles, geometry, spectrum buffer view
 // ---------------------------------------------------------------------------------------
@@ -130,24 +108,12 @@ struct Engine {
   int init(int D, const int* n, const int* support, size_t budget, int rmax) {
     rmax_used = rmax;
     budget_used = budget;
-    g.D = D;
-    g.nodes = 1;
-    for (int a = 0; a < D; ++a) {
-      g.n[a] = n[a];
-      g.nodes *= n[a];
+    for (int a = 0; a < D; ++a)
       if (!plan_axis(n[a], rmax, &plan[a])) return HOM_ERR_INVALID;
-    }
-    for (int a = D; a < 3; ++a) g.n[a] = 1;
+    if (!Ops<T>::plan_geometry(D, n, plan, budget, &g)) return HOM_ERR_UNSUPPORTED;
     const int nl = n[D - 1];
-    g.nh = (nl + 1) / 2;
-    g.nlines = g.nodes / nl;
-    g.scs = g.nlines * g.nh;
-    g.LB = pick_LB<T>(nl, D, budget);
-    if (D == 3) pick_TC<T>(n[1], plan[1].nst, budget, &g.TC1, &g.TC1p, false, D);
-    pick_TC<T>(n[0], plan[0].nst, budget, &g.TC0, &g.TC0p, true, D);
-    pick_TC<T>(n[0], plan[0].nst, budget, &g.TCs0, &g.TCs0p, false, D);
     g1 = g;
-    g1.LB = pick_LB<T>(nl, 1, budget);
+    while (g1.LB < 16 && Ops<T>::smem_line(nl, 1, g1.LB + 2) <= budget) g1.LB += 2;
     for (int a = 0; a < D; ++a) {
       auto tw_h = twiddles<T>(n[a]);
       if (cudaMalloc(&tw[a], sizeof(cpx<T>) * n[a]) != cudaSuccess) return HOM_ERR_OOM;
@@ -161,12 +127,6 @@ struct Engine {
     pg.fdnh = make_fastdiv(g.nh);
     for (int a = 0; a < 3; ++a) pg.hw[a] = (a < D) ? (support[a] - 1) / 2 : 0;
     pg.scale = 1.0 / (double)g.nodes;
-    // every pass must fit the per-CTA shared-memory limit
-    const size_t cap = (size_t)dynamic_smem_cap();
-    if (Ops<T>::smem_line(nl, D, g.LB) > cap || Ops<T>::smem_proj(n[0], D, g.TC0p) > cap ||
-        (D == 3 && Ops<T>::smem_strided(n[1], g.TC1p, plan[1].nst) > cap) ||
-        Ops<T>::smem_strided(n[0], g.TCs0p, plan[0].nst) > cap)
-      return HOM_ERR_UNSUPPORTED;
     ready = true;
     return HOM_OK;
   }

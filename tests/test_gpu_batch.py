@@ -60,8 +60,8 @@ def test_batch_matches_solo_bitwise(solver):
             P.close()
 
 
-def test_batch_refined_matches_solo():
-    N = (21, 23, 19)
+@pytest.mark.parametrize("N", [(21, 23, 19), (45, 45, 21)])
+def test_batch_refined_matches_solo(N):
     mats = [material(N, s, 1000.0) for s in (11, 12)]
     Es = [np.array([1.0, 0.0, 0.0]), np.array([0.0, 0.6, 0.8])]
     ref = [solo(N, m, E, H.HOM_CG, H.HOM_FP32_REFINED, None, 1e-9) for m, E in zip(mats, Es)]

@@ -47,6 +47,50 @@ def test_fp32_operator_parity(N):
     P.close()
 
 
+# axis lengths whose FP32 column passes run the compile-time two-stage kernels: each appears
+# along axis 0 (projection pass) and along axis 1 (strided pass), with ragged column tiles
+TWO_STAGE_GRIDS = [(243, 7, 5), (5, 243, 3), (405, 3, 3), (3, 405, 5), (81, 9, 5), (7, 81, 9),
+                   (135, 5, 3), (3, 135, 7), (45, 11, 3), (161, 3, 5), (3, 161, 3), (63, 5, 3),
+                   (3, 63, 7), (189, 3, 3), (5, 189, 3), (175, 3, 5), (3, 175, 3), (243, 7)]
+
+
+@pytest.mark.parametrize("N", TWO_STAGE_GRIDS)
+@pytest.mark.parametrize("op", ["linear", "em"])
+def test_fp32_two_stage_plans(N, op):
+    d = len(N)
+    ph = ms.box_phase(N, 0.6)
+    table = ms.isotropic_table([1.0, 10.0], d)
+    A = O.expand_phase(ph, table)[0, 0]
+    P = H.Problem(d, N, H.phase_material(ph, table), precision=H.HOM_FP32_REFINED)
+    x = ms.random_field((d,) + N, 5)
+    y = P.field()
+    opc = H.HOM_OP_LINEAR if op == "linear" else H.HOM_OP_EM
+    H.hom_apply(P.h, opc | H.HOM_OP_FP32, None, torch.from_numpy(x).cuda(), y)
+    sysn = O.GaNi(A, d)
+    ref = sysn.matvec(x) if op == "linear" else sysn.em_project(O.apply_A(A, x) - np.sqrt(10.0) * x)
+    err = rel(y.cpu().numpy(), ref)
+    assert err < 2e-6, err
+    P.close()
+
+
+@pytest.mark.parametrize("N", [(81, 5, 3), (3, 81, 5)])
+def test_fp32_two_stage_plans_exact_integration(N):
+    # double grid 2N - 1 = 161: the truncation to Z_N runs inside the specialised projection
+    d = len(N)
+    M = O.double_grid(N)
+    Ahat = ms.box_fourier_coefficients(M, 0.6, 1.0, 10.0)
+    P = H.Problem(d, N, H.fourier_material(Ahat.astype(np.complex128), 1.0, 10.0), H.HOM_EXACT,
+                  precision=H.HOM_FP32_REFINED)
+    assert P.grid == M
+    A_M = O.ga_coefficients(Ahat, d)
+    x = ms.random_field((d,) + M, 6)
+    y = P.field()
+    H.hom_apply(P.h, H.HOM_OP_LINEAR | H.HOM_OP_FP32, None, torch.from_numpy(x).cuda(), y)
+    err = rel(y.cpu().numpy(), O.Ga(A_M, N, d).matvec(x))
+    assert err < 2e-6, err
+    P.close()
+
+
 @pytest.mark.parametrize("solver", ["cg", "chebyshev"])
 @pytest.mark.parametrize("N", [(85, 85), (33, 35, 31)])
 def test_refined_solve_matches_fp64_oracle(N, solver):
