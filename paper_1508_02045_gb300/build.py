@@ -1,6 +1,7 @@
 """Build libhom.so in-tree for sm_103a (nvcc, no CMake).
 
-The three translation units (FP64 kernels, FP32 kernels, host API) compile in parallel and are
+The translation units (FP64 kernels, FP32 kernels, FP32 compile-time plans, host API, serving,
+no-allocation entry point) compile in parallel and are
 linked into paper_1508_02045_gb300/libhom.so next to this file.
 """
 from __future__ import annotations
@@ -15,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhom.so")
-SOURCES = ["ops_f64.cu", "ops_f32.cu", "hom_api.cu", "hom_serve.cu", "hom_static.cu"]
+SOURCES = ["ops_f64.cu", "ops_f32.cu", "ops_pair_f32.cu", "hom_api.cu", "hom_serve.cu",
+           "hom_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          f"-I{os.path.join(ROOT, 'include')}"]

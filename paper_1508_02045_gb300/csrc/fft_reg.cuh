@@ -13,6 +13,8 @@
 // The inverse transform (eq. (DFT), no scaling) is conj(F(conj(.))): imaginary parts are
 // negated on every load and store of a stage.
 #pragma once
+#include <cmath>
+
 #include "common.cuh"
 
 namespace hom {
@@ -31,6 +33,29 @@ static __constant__ double c_rcos_d[kRegTable];
 static __constant__ double c_rsin_d[kRegTable];
 static __constant__ float c_rcos_f[kRegTable];
 static __constant__ float c_rsin_f[kRegTable];
+
+// Fill this translation unit's copies of the tables (each unit that launches register DFTs
+// calls it once per device), from long double cos / sin.
+static inline cudaError_t upload_reg_tables() {
+  double cd[kRegTable], sd[kRegTable];
+  float cf[kRegTable], sf[kRegTable];
+  const long double twopi = 6.283185307179586476925286766559005768L;
+  for (int R = 3; R <= kRegMax; R += 2) {
+    const int off = reg_offset(R);
+    for (int j = 0; j < R; ++j) {
+      const long double t = twopi * (long double)j / (long double)R;
+      cd[off + j] = (double)cosl(t);
+      sd[off + j] = (double)sinl(t);
+      cf[off + j] = (float)cosl(t);
+      sf[off + j] = (float)sinl(t);
+    }
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpyToSymbol(c_rcos_d, cd, sizeof(cd))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_rsin_d, sd, sizeof(sd))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_rcos_f, cf, sizeof(cf))) != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_rsin_f, sf, sizeof(sf));
+}
 
 template <typename T> __device__ __forceinline__ T rcos(int j);
 template <typename T> __device__ __forceinline__ T rsin(int j);

@@ -73,6 +73,34 @@ struct Ops {
                            cudaStream_t st);
 };
 
+// FP32 kernels specialised at compile time for the two-stage plans of the usual axis lengths
+// (ops_pair_f32.cu); the callers fall back to the runtime-radix kernels for everything else
+bool pair_plan_f32(const AxisPlan& P);
+cudaError_t pair_prepare_f32(int smem_cap);
+void pair_strided_f32(const AxisPlan& P, int inv, cpx<float>* S, const cpx<float>* tw,
+                      long long C, long long es, long long bs, int batches, const Scalars* sc,
+                      cudaStream_t st, const ReqDesc<float>* reqs, int nreq);
+void pair_proj_f32(int D, int mode, const AxisPlan& P, cpx<float>* S, const cpx<float>* tw,
+                   const ProjGeom& pg, const Scalars* sc, cudaStream_t st,
+                   const ReqDesc<float>* reqs, int nreq);
+// the line passes are specialised for D = 3 and the pre-/post-operators of the FP32 inner
+// solves (CG, Chebyshev) and of plain operator applications
+inline bool pair_line_fwd_has(int D, int pre) {
+  return D == 3 && (pre == PRE_CG || pre == PRE_LINEAR);
+}
+inline bool pair_line_inv_has(int D, int post) {
+  return D == 3 && (post == POST_CG || post == POST_CHEB || post == POST_STORE);
+}
+void pair_line_fwd_f32(int D, int pre, const AxisPlan& P, const Fields<float>& f, cpx<float>* S,
+                       const cpx<float>* tw, long long nlines, long long scs,
+                       const MatView<float>& mat, const Scalars* sc, const OpArgs& args,
+                       cudaStream_t st, const ReqDesc<float>* reqs, int nreq);
+void pair_line_inv_f32(int D, int post, const AxisPlan& P, const cpx<float>* S,
+                       const Fields<float>& f, const cpx<float>* tw, long long nlines,
+                       long long scs, const MatView<float>& mat, Scalars* sc, const OpArgs& args,
+                       double* partials, unsigned* counter, int negate, cudaStream_t st,
+                       const ReqDesc<float>* reqs, int nreq);
+
 long long& launch_counter();
 int dynamic_smem_cap();
 

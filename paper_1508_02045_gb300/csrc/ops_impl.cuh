@@ -5,32 +5,21 @@
 #include <type_traits>
 
 #include "ops.h"
-#include "pair_fft.cuh"
 #include "passes.cuh"
 
 namespace hom {
 
+// FP32 plans with compile-time kernels (ops_pair_f32.cu); always false for FP64
+template <typename T>
+static bool pair_plan(const AxisPlan& P) {
+  if constexpr (std::is_same<T, float>::value) return pair_plan_f32(P);
+  return false;
+}
+
+
 template <typename T>
 cudaError_t Ops<T>::upload_constants() {
-  // cos / sin (2 pi j / R) for every odd register radix R <= 31, from long double
-  std::vector<double> cd(kRegTable), sd(kRegTable);
-  std::vector<float> cf(kRegTable), sf(kRegTable);
-  const long double twopi = 6.283185307179586476925286766559005768L;
-  for (int R = 3; R <= kRegMax; R += 2) {
-    const int off = reg_offset(R);
-    for (int j = 0; j < R; ++j) {
-      const long double t = twopi * (long double)j / (long double)R;
-      cd[off + j] = (double)cosl(t);
-      sd[off + j] = (double)sinl(t);
-      cf[off + j] = (float)cosl(t);
-      sf[off + j] = (float)sinl(t);
-    }
-  }
-  cudaError_t e;
-  if ((e = cudaMemcpyToSymbol(c_rcos_d, cd.data(), sizeof(double) * kRegTable)) != cudaSuccess) return e;
-  if ((e = cudaMemcpyToSymbol(c_rsin_d, sd.data(), sizeof(double) * kRegTable)) != cudaSuccess) return e;
-  if ((e = cudaMemcpyToSymbol(c_rcos_f, cf.data(), sizeof(float) * kRegTable)) != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(c_rsin_f, sf.data(), sizeof(float) * kRegTable);
+  return upload_reg_tables();
 }
 
 template <typename T>
@@ -158,17 +147,7 @@ cudaError_t Ops<T>::prepare(int) {
   HOM_SET_SMEM((k_line_inv<T, 3, POST_CG>));
   HOM_SET_SMEM((k_line_inv<T, 3, POST_CHEB>));
   HOM_SET_SMEM((k_line_inv<T, 3, POST_EM>));
-  if constexpr (std::is_same<T, float>::value) {
-#define HOM_PAIR_SMEM(R1_, R2_)                                 \
-  HOM_SET_SMEM((k_pair_strided<T, R1_, R2_, false>));           \
-  HOM_SET_SMEM((k_pair_strided<T, R1_, R2_, true>));            \
-  HOM_SET_SMEM((k_pair_proj<T, 2, PROJ_GAMMA, R1_, R2_>));      \
-  HOM_SET_SMEM((k_pair_proj<T, 2, PROJ_EM, R1_, R2_>));         \
-  HOM_SET_SMEM((k_pair_proj<T, 3, PROJ_GAMMA, R1_, R2_>));      \
-  HOM_SET_SMEM((k_pair_proj<T, 3, PROJ_EM, R1_, R2_>));
-    HOM_PAIR_PLANS(HOM_PAIR_SMEM)
-#undef HOM_PAIR_SMEM
-  }
+  if constexpr (std::is_same<T, float>::value) return pair_prepare_f32(cap);
   return cudaSuccess;
 }
 
@@ -199,67 +178,18 @@ void Ops<T>::line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
                       const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
                       const Scalars* sc, const OpArgs& args, cudaStream_t st,
                       const ReqDesc<T>* reqs, int nreq) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (ncomp == g.D && pair_line_fwd_has(g.D, pre) && pair_plan<T>(P)) {
+      const bool prof = profiling();
+      if (prof) prof_mark(KIND_LINE_FWD, st, true);
+      pair_line_fwd_f32(g.D, pre, P, f, S, tw, g.nlines, g.scs, mat, sc, args, st, reqs, nreq);
+      if (prof) prof_mark(KIND_LINE_FWD, st, false);
+      ++launch_counter();
+      return;
+    }
+  }
   if (g.D == 2) line_fwd_d<T, 2>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq);
   else line_fwd_d<T, 3>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq);
-}
-
-// an FP32 two-stage plan with compile-time column kernels (pair_fft.cuh)
-template <typename T>
-static bool pair_plan(const AxisPlan& P) {
-  if (!std::is_same<T, float>::value || P.nst != 2) return false;
-#define HOM_PAIR_IS(R1_, R2_) \
-  if (P.radix[0] == R1_ && P.radix[1] == R2_) return true;
-  HOM_PAIR_PLANS(HOM_PAIR_IS)
-#undef HOM_PAIR_IS
-  return false;
-}
-
-template <typename T>
-static void pair_strided(const AxisPlan& P, int inv, cpx<T>* S, const cpx<T>* tw, long long C,
-                         long long es, long long bs, int batches, const Scalars* sc,
-                         cudaStream_t st, const ReqDesc<T>* reqs, int nreq) {
-  if constexpr (std::is_same<T, float>::value) {
-#define HOM_PAIR_ST(R1_, R2_)                                                                  \
-  if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
-    constexpr int TC = pair_tc_strided<R2_>();                                                 \
-    const dim3 grid((unsigned)((C + TC - 1) / TC), (unsigned)batches, (unsigned)nreq);        \
-    const size_t sm = sizeof(cpx<T>) * (size_t)(R1_ * R2_) * (TC + 2);                          \
-    if (inv)                                                                                   \
-      k_pair_strided<T, R1_, R2_, true><<<grid, TC * R2_, sm, st>>>(S, tw, C, es, bs, sc, reqs); \
-    else                                                                                       \
-      k_pair_strided<T, R1_, R2_, false><<<grid, TC * R2_, sm, st>>>(S, tw, C, es, bs, sc, reqs); \
-    return;                                                                                    \
-  }
-    HOM_PAIR_PLANS(HOM_PAIR_ST)
-#undef HOM_PAIR_ST
-  }
-}
-
-template <typename T>
-static void pair_proj(int D, int mode, const AxisPlan& P, cpx<T>* S, const cpx<T>* tw,
-                      const ProjGeom& pg, const Scalars* sc, cudaStream_t st,
-                      const ReqDesc<T>* reqs, int nreq) {
-  if constexpr (std::is_same<T, float>::value) {
-#define HOM_PAIR_PJ_D(D_, R1_, R2_)                                                            \
-  {                                                                                            \
-    constexpr int TC = pair_tc_proj<D_, R2_>();                                                \
-    const dim3 grid((unsigned)((pg.C + TC - 1) / TC), 1, (unsigned)nreq);                     \
-    const size_t sm = sizeof(cpx<T>) * ((size_t)(R1_ * R2_) * (1 + 2 * D_ * (TC + 1)));        \
-    if (mode == PROJ_EM)                                                                       \
-      k_pair_proj<T, D_, PROJ_EM, R1_, R2_><<<grid, D_ * TC * R2_, sm, st>>>(S, tw, pg, sc, reqs); \
-    else                                                                                       \
-      k_pair_proj<T, D_, PROJ_GAMMA, R1_, R2_><<<grid, D_ * TC * R2_, sm, st>>>(S, tw, pg, sc, reqs); \
-  }
-#define HOM_PAIR_PJ(R1_, R2_)                               \
-  if (P.radix[0] == R1_ && P.radix[1] == R2_) {             \
-    if (D == 2) HOM_PAIR_PJ_D(2, R1_, R2_)                  \
-    else HOM_PAIR_PJ_D(3, R1_, R2_)                         \
-    return;                                                 \
-  }
-    HOM_PAIR_PLANS(HOM_PAIR_PJ)
-#undef HOM_PAIR_PJ
-#undef HOM_PAIR_PJ_D
-  }
 }
 
 template <typename T>
@@ -288,7 +218,8 @@ void Ops<T>::strided(const PassGeom& g, int axis, int inv, cpx<T>* S, const Axis
   const bool prof = profiling();
   if (prof) prof_mark(KIND_STRIDED, st, true);
   if (pair_plan<T>(P)) {
-    pair_strided<T>(P, inv, S, tw, C, es, bs, batches, sc, st, reqs, nreq);
+    if constexpr (std::is_same<T, float>::value)
+      pair_strided_f32(P, inv, S, tw, C, es, bs, batches, sc, st, reqs, nreq);
   } else {
     const dim3 grid((unsigned)((C + TC - 1) / TC), (unsigned)batches, (unsigned)nreq);
     const size_t sm = smem_strided(P.n, TCp, P.nst);
@@ -305,7 +236,8 @@ void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, con
   const bool prof = profiling();
   if (prof) prof_mark(KIND_PROJ, st, true);
   if (pair_plan<T>(P)) {
-    pair_proj<T>(g.D, mode, P, S, tw, pg, sc, st, reqs, nreq);
+    if constexpr (std::is_same<T, float>::value)
+      pair_proj_f32(g.D, mode, P, S, tw, pg, sc, st, reqs, nreq);
     if (prof) prof_mark(KIND_PROJ, st, false);
     ++launch_counter();
     return;
@@ -351,6 +283,17 @@ void Ops<T>::line_inv(const PassGeom& g, int post, const cpx<T>* S, const Fields
                       const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
                       Scalars* sc, const OpArgs& args, double* partials, unsigned* counter,
                       int negate, cudaStream_t st, const ReqDesc<T>* reqs, int nreq) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (ncomp == g.D && pair_line_inv_has(g.D, post) && pair_plan<T>(P)) {
+      const bool prof = profiling();
+      if (prof) prof_mark(KIND_LINE_INV, st, true);
+      pair_line_inv_f32(g.D, post, P, S, f, tw, g.nlines, g.scs, mat, sc, args, partials, counter,
+                        negate, st, reqs, nreq);
+      if (prof) prof_mark(KIND_LINE_INV, st, false);
+      ++launch_counter();
+      return;
+    }
+  }
   if (g.D == 2)
     line_inv_d<T, 2>(g, post, S, f, P, tw, ncomp, mat, sc, args, partials, counter, negate, st,
                      reqs, nreq);

@@ -1,0 +1,145 @@
+// Launchers of the FP32 kernels specialised at compile time for two-stage plans (pair_fft.cuh),
+// in a translation unit of their own so that they compile in parallel with the rest.
+#include <type_traits>
+
+#include "ops.h"
+#include "pair_fft.cuh"
+
+namespace hom {
+
+bool pair_plan_f32(const AxisPlan& P) {
+  if (P.nst != 2) return false;
+#define HOM_PAIR_IS(R1_, R2_) \
+  if (P.radix[0] == R1_ && P.radix[1] == R2_) return true;
+  HOM_PAIR_PLANS(HOM_PAIR_IS)
+#undef HOM_PAIR_IS
+  return false;
+}
+
+#define HOM_SET_SMEM(kern)                                                                    \
+  do {                                                                                        \
+    cudaError_t e_ = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                          cap);                                               \
+    if (e_ != cudaSuccess) return e_;                                                         \
+  } while (0)
+
+cudaError_t pair_prepare_f32(int cap) {
+  using T = float;
+  // this unit's copies of the register-DFT constants
+  const cudaError_t e = upload_reg_tables();
+  if (e != cudaSuccess) return e;
+#define HOM_PAIR_SMEM(R1_, R2_)                                 \
+  HOM_SET_SMEM((k_pair_strided<T, R1_, R2_, false>));           \
+  HOM_SET_SMEM((k_pair_strided<T, R1_, R2_, true>));            \
+  HOM_SET_SMEM((k_pair_proj<T, 2, PROJ_GAMMA, R1_, R2_>));      \
+  HOM_SET_SMEM((k_pair_proj<T, 2, PROJ_EM, R1_, R2_>));         \
+  HOM_SET_SMEM((k_pair_proj<T, 3, PROJ_GAMMA, R1_, R2_>));      \
+  HOM_SET_SMEM((k_pair_proj<T, 3, PROJ_EM, R1_, R2_>));         \
+  HOM_SET_SMEM((k_pair_line_fwd<T, 3, PRE_CG, R1_, R2_>));      \
+  HOM_SET_SMEM((k_pair_line_fwd<T, 3, PRE_LINEAR, R1_, R2_>));  \
+  HOM_SET_SMEM((k_pair_line_inv<T, 3, POST_CG, R1_, R2_>));     \
+  HOM_SET_SMEM((k_pair_line_inv<T, 3, POST_CHEB, R1_, R2_>));   \
+  HOM_SET_SMEM((k_pair_line_inv<T, 3, POST_STORE, R1_, R2_>));
+  HOM_PAIR_PLANS(HOM_PAIR_SMEM)
+#undef HOM_PAIR_SMEM
+  return cudaSuccess;
+}
+
+void pair_strided_f32(const AxisPlan& P, int inv, cpx<float>* S, const cpx<float>* tw,
+                      long long C, long long es, long long bs, int batches, const Scalars* sc,
+                      cudaStream_t st, const ReqDesc<float>* reqs, int nreq) {
+  using T = float;
+#define HOM_PAIR_ST(R1_, R2_)                                                                  \
+  if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
+    constexpr int TC = pair_tc_strided<R2_>();                                                 \
+    const dim3 grid((unsigned)((C + TC - 1) / TC), (unsigned)batches, (unsigned)nreq);        \
+    const size_t sm = sizeof(cpx<T>) * (size_t)(R1_ * R2_) * (TC + 2);                          \
+    if (inv)                                                                                   \
+      k_pair_strided<T, R1_, R2_, true><<<grid, TC * R2_, sm, st>>>(S, tw, C, es, bs, sc, reqs); \
+    else                                                                                       \
+      k_pair_strided<T, R1_, R2_, false><<<grid, TC * R2_, sm, st>>>(S, tw, C, es, bs, sc, reqs); \
+    return;                                                                                    \
+  }
+  HOM_PAIR_PLANS(HOM_PAIR_ST)
+#undef HOM_PAIR_ST
+}
+
+void pair_proj_f32(int D, int mode, const AxisPlan& P, cpx<float>* S, const cpx<float>* tw,
+                   const ProjGeom& pg, const Scalars* sc, cudaStream_t st,
+                   const ReqDesc<float>* reqs, int nreq) {
+  using T = float;
+#define HOM_PAIR_PJ_D(D_, R1_, R2_)                                                            \
+  {                                                                                            \
+    constexpr int TC = pair_tc_proj<D_, R2_>();                                                \
+    const dim3 grid((unsigned)((pg.C + TC - 1) / TC), 1, (unsigned)nreq);                     \
+    const size_t sm = sizeof(cpx<T>) * ((size_t)(R1_ * R2_) * (1 + 2 * D_ * (TC + 1)));        \
+    if (mode == PROJ_EM)                                                                       \
+      k_pair_proj<T, D_, PROJ_EM, R1_, R2_><<<grid, D_ * TC * R2_, sm, st>>>(S, tw, pg, sc, reqs); \
+    else                                                                                       \
+      k_pair_proj<T, D_, PROJ_GAMMA, R1_, R2_><<<grid, D_ * TC * R2_, sm, st>>>(S, tw, pg, sc, reqs); \
+  }
+#define HOM_PAIR_PJ(R1_, R2_)                   \
+  if (P.radix[0] == R1_ && P.radix[1] == R2_) { \
+    if (D == 2) HOM_PAIR_PJ_D(2, R1_, R2_)      \
+    else HOM_PAIR_PJ_D(3, R1_, R2_)             \
+    return;                                     \
+  }
+  HOM_PAIR_PLANS(HOM_PAIR_PJ)
+#undef HOM_PAIR_PJ
+#undef HOM_PAIR_PJ_D
+}
+
+void pair_line_fwd_f32(int D, int pre, const AxisPlan& P, const Fields<float>& f, cpx<float>* S,
+                       const cpx<float>* tw, long long nlines, long long scs,
+                       const MatView<float>& mat, const Scalars* sc, const OpArgs& args,
+                       cudaStream_t st, const ReqDesc<float>* reqs, int nreq) {
+  using T = float;
+  (void)D;  // D = 3 (pair_line_fwd_has)
+  const FastDiv fdn = make_fastdiv(P.n);
+#define HOM_PAIR_LF(R1_, R2_)                                                                  \
+  if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
+    constexpr int LB = 2 * pair_lbp<3, R2_>();                                                 \
+    const dim3 grid((unsigned)((nlines + LB - 1) / LB), 1, (unsigned)nreq);                   \
+    const size_t sm = sizeof(cpx<T>) * (size_t)(R1_ * R2_) * (1 + 3 * pair_lbp<3, R2_>());      \
+    constexpr int NT = pair_line_threads<3, R2_>();                                            \
+    if (pre == PRE_CG)                                                                         \
+      k_pair_line_fwd<T, 3, PRE_CG, R1_, R2_><<<grid, NT, sm, st>>>(f, S, tw, nlines, scs, mat,  \
+                                                                    sc, args, fdn, reqs);      \
+    else                                                                                       \
+      k_pair_line_fwd<T, 3, PRE_LINEAR, R1_, R2_><<<grid, NT, sm, st>>>(f, S, tw, nlines, scs, \
+                                                                        mat, sc, args, fdn, reqs); \
+    return;                                                                                    \
+  }
+  HOM_PAIR_PLANS(HOM_PAIR_LF)
+#undef HOM_PAIR_LF
+}
+
+void pair_line_inv_f32(int D, int post, const AxisPlan& P, const cpx<float>* S,
+                       const Fields<float>& f, const cpx<float>* tw, long long nlines,
+                       long long scs, const MatView<float>& mat, Scalars* sc, const OpArgs& args,
+                       double* partials, unsigned* counter, int negate, cudaStream_t st,
+                       const ReqDesc<float>* reqs, int nreq) {
+  using T = float;
+  (void)D;  // D = 3 (pair_line_inv_has)
+  const FastDiv fdn = make_fastdiv(P.n);
+#define HOM_PAIR_LI_P(POST_, R1_, R2_)                                                         \
+  k_pair_line_inv<T, 3, POST_, R1_, R2_><<<grid, NT, sm, st>>>(S, f, tw, nlines, scs, mat, sc,   \
+                                                               args, partials, counter, negate, \
+                                                               fdn, reqs)
+#define HOM_PAIR_LI(R1_, R2_)                                                                  \
+  if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
+    constexpr int LB = 2 * pair_lbp<3, R2_>();                                                 \
+    const dim3 grid((unsigned)((nlines + LB - 1) / LB), 1, (unsigned)nreq);                   \
+    const size_t sm = sizeof(cpx<T>) * (size_t)(R1_ * R2_) * (1 + 3 * pair_lbp<3, R2_>());      \
+    constexpr int NT = pair_line_threads<3, R2_>();                                            \
+    if (post == POST_CG) HOM_PAIR_LI_P(POST_CG, R1_, R2_);                                     \
+    else if (post == POST_CHEB) HOM_PAIR_LI_P(POST_CHEB, R1_, R2_);                            \
+    else HOM_PAIR_LI_P(POST_STORE, R1_, R2_);                                                  \
+    return;                                                                                    \
+  }
+  HOM_PAIR_PLANS(HOM_PAIR_LI)
+#undef HOM_PAIR_LI
+#undef HOM_PAIR_LI_P
+}
+
+}  // namespace hom

@@ -221,4 +221,168 @@ k_pair_proj(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, const Scalars
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// line passes (contiguous axis, D = 3, every component): CTA = LBP line pairs of each
+// component, two real lines packed into one complex line (a, q) at n + (a LBP + q) n
+// ---------------------------------------------------------------------------------------
+// line pairs per CTA: as many as keep the first-stage butterflies D x LBP x R2 within 256
+template <int D, int R2>
+__host__ __device__ constexpr int pair_lbp() {
+  return 256 / (D * R2);
+}
+template <int D, int R2>
+__host__ __device__ constexpr int pair_line_threads() {
+  return (D * pair_lbp<D, R2>() * R2 + 31) / 32 * 32;
+}
+
+// pre-operator + forward real DFT of the contiguous axis: the pre-operator fills the complex
+// lines in shared memory, stage 1 runs in place (one butterfly per thread, all loads before a
+// barrier, then all stores), stage 2 in place (each butterfly reads and writes the same R2
+// rows), then the two packed real transforms are split and stored as half spectra
+template <typename T, int D, int PRE, int R1, int R2>
+__global__ void __launch_bounds__(pair_line_threads<D, R2>())
+k_pair_line_fwd(Fields<T> f, cpx<T>* S, const cpx<T>* __restrict__ twg, long long nlines,
+                long long scs, MatView<T> mat, const Scalars* sc, OpArgs args, FastDiv fdn,
+                const ReqDesc<T>* __restrict__ reqs) {
+  constexpr int n = R1 * R2, nh = (n + 1) / 2, LBP = pair_lbp<D, R2>(), LB = 2 * LBP;
+  constexpr int NL = D * LBP, items1 = NL * R2;
+  if (reqs != nullptr) {
+    const ReqDesc<T>& R = reqs[blockIdx.z];
+    f = R.ff;
+    S = R.S;
+    mat = R.mat;
+    sc = R.sc;
+  }
+  if (sc != nullptr && sc->done) return;
+  cpx<T>* sm = smem_c<T>();
+  cpx<T>* tw = sm;
+  cpx<T>* lines = sm + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+  const long long l0 = (long long)blockIdx.x * LB;
+  line_pre_to_smem<T, D, PRE>(f, n, n, LBP, D, l0, LB, nlines, fdn, mat, sc, args);
+  __syncthreads();
+  {
+    const int t = threadIdx.x;
+    const bool act = t < items1;
+    const int i = t % R2;
+    cpx<T>* line = lines + (t / R2) * n;
+    cpx<T> u[R1];
+    if (act) {
+#pragma unroll
+      for (int r = 0; r < R1; ++r) u[r] = line[i + r * R2];
+      RegDft<T, R1>::run(u);
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int r = 0; r < R1; ++r) line[i * R1 + r] = u[r];
+    }
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < NL * R1; w += blockDim.x) {
+    const int i = w % R1;
+    cpx<T>* line = lines + (w / R1) * n;
+    cpx<T> u[R2];
+    pair_stage2_regs<T, R1, R2>(line, tw, 1, i, u);
+#pragma unroll
+    for (int r = 0; r < R2; ++r) line[i + r * R1] = u[r];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < NL * nh; idx += blockDim.x) {
+    const int lc = idx / nh, k = idx - lc * nh;
+    const int a = lc / LBP, q = lc - a * LBP;
+    const cpx<T> zk = lines[lc * n + k];
+    const cpx<T> zm = lines[lc * n + (k ? n - k : 0)];
+    cpx<T> A, B;
+    A.x = (T)0.5 * (zk.x + zm.x);
+    A.y = (T)0.5 * (zk.y - zm.y);
+    B.x = (T)0.5 * (zk.y + zm.y);
+    B.y = (T)-0.5 * (zk.x - zm.x);
+    const long long la = l0 + 2 * q;
+    if (la < nlines) S[a * scs + la * nh + k] = A;
+    if (la + 1 < nlines) S[a * scs + (la + 1) * nh + k] = B;
+  }
+}
+
+// inverse real DFT of the contiguous axis + post-operator: stage 1 reads the two half spectra
+// of each line pair straight from the spectrum and unpacks them on the fly (Hermitian
+// symmetry: X_j = conj X_{n-j} above the half), stage 2 runs in place, and the post-operator
+// reads the real (even line) and imaginary (odd line) parts
+template <typename T, int D, int POST, int R1, int R2>
+__global__ void __launch_bounds__(pair_line_threads<D, R2>())
+k_pair_line_inv(const cpx<T>* S, Fields<T> f, const cpx<T>* __restrict__ twg, long long nlines,
+                long long scs, MatView<T> mat, Scalars* sc, OpArgs args, double* partials,
+                unsigned* counter, int negate, FastDiv fdn, const ReqDesc<T>* __restrict__ reqs) {
+  constexpr int n = R1 * R2, nh = (n + 1) / 2, LBP = pair_lbp<D, R2>(), LB = 2 * LBP;
+  constexpr int NL = D * LBP, items1 = NL * R2;
+  if (reqs != nullptr) {
+    const ReqDesc<T>& R = reqs[blockIdx.z];
+    f = R.fi;
+    S = R.S;
+    mat = R.mat;
+    sc = R.sc;
+    partials = R.partials;
+    counter = R.counter;
+  }
+  if (sc != nullptr && sc->done) return;
+  cpx<T>* sm = smem_c<T>();
+  cpx<T>* tw = sm;
+  cpx<T>* lines = sm + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+  const long long l0 = (long long)blockIdx.x * LB;
+  if (threadIdx.x < items1) {
+    const int t = threadIdx.x;
+    const int i = t % R2, lc = t / R2;
+    const int a = lc / LBP, q = lc - a * LBP;
+    const long long la = l0 + 2 * q;
+    const bool okA = la < nlines, okB = la + 1 < nlines;
+    const cpx<T>* ha = S + a * scs + la * nh;
+    const cpx<T>* hb = ha + nh;
+    cpx<T> u[R1];
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      const int j = i + r * R2;
+      const bool up = j > (n - 1) / 2;
+      const int jj = up ? n - j : j;
+      cpx<T> A = okA ? ha[jj] : cpx<T>{0, 0};
+      cpx<T> B = okB ? hb[jj] : cpx<T>{0, 0};
+      if (up) {
+        A.y = -A.y;
+        B.y = -B.y;
+      }
+      // Z = A + i B, conjugated for the inverse transform; Z_0 = (A_0.x, B_0.x)
+      if (j == 0) {
+        u[r].x = A.x;
+        u[r].y = -B.x;
+      } else {
+        u[r].x = A.x - B.y;
+        u[r].y = -(A.y + B.x);
+      }
+    }
+    RegDft<T, R1>::run(u);
+    cpx<T>* line = lines + lc * n;
+#pragma unroll
+    for (int r = 0; r < R1; ++r) line[i * R1 + r] = u[r];
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < NL * R1; w += blockDim.x) {
+    const int i = w % R1;
+    cpx<T>* line = lines + (w / R1) * n;
+    cpx<T> u[R2];
+    pair_stage2_regs<T, R1, R2>(line, tw, 1, i, u);
+#pragma unroll
+    for (int r = 0; r < R2; ++r) line[i + r * R1] = cpx<T>{u[r].x, -u[r].y};
+  }
+  __syncthreads();
+  DotAcc<T> dacc;
+  line_post_from_smem<T, D, POST>(f, n, n, LBP, D, l0, LB, nlines, fdn, mat, sc, args, negate,
+                                  dacc);
+  if (partials == nullptr) return;
+  double acc[1] = {dacc.value()};
+  double tot[1];
+  if (!reduce_and_last<1>(acc, partials, counter, tot)) return;
+  if (threadIdx.x != 0 || sc == nullptr) return;
+  line_inv_finish<POST>(sc, tot[0], (double)(nlines * n));
+}
+
 }  // namespace hom

@@ -43,6 +43,7 @@ __device__ bool reduce_and_last(double (&acc)[NV], double* partials, unsigned* c
   __shared__ double fin[NV];
   __shared__ int am_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (int)(blockDim.x >> 5);  // blocks are whole warps, at most kThreads threads
   const int nblocks = gridDim.x * gridDim.y;
   const int bid = blockIdx.y * gridDim.x + blockIdx.x;
 #pragma unroll
@@ -57,7 +58,7 @@ __device__ bool reduce_and_last(double (&acc)[NV], double* partials, unsigned* c
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       double s = 0.0;
-      for (int w = 0; w < kThreads / 32; ++w) s += red[v][w];
+      for (int w = 0; w < nw; ++w) s += red[v][w];
       partials[(size_t)bid * NV + v] = s;
     }
     __threadfence();
@@ -78,7 +79,7 @@ __device__ bool reduce_and_last(double (&acc)[NV], double* partials, unsigned* c
     __syncthreads();
     if (threadIdx.x == 0) {
       double f = 0.0;
-      for (int w = 0; w < kThreads / 32; ++w) f += red[v][w];
+      for (int w = 0; w < nw; ++w) f += red[v][w];
       fin[v] = f;
     }
   }
@@ -236,28 +237,16 @@ struct ReqDesc {
 // ---------------------------------------------------------------------------------------
 // line_fwd: pre-operator + forward real DFT of the contiguous axis
 // ---------------------------------------------------------------------------------------
+// Pre-operator of the lines l0 .. l0 + LB - 1 (pointwise, coalesced loads in batches of K
+// nodes): component a of line l0 + ll goes to the real (ll even) or imaginary (ll odd) part of
+// the shared-memory complex line b0 + (a * half + ll / 2) * n, so that two real lines share one
+// complex transform.
 template <typename T, int D, int PRE>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
-k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
-           int ncomp, long long nlines, int LB, LineDiv ld, long long scs, MatView<T> mat,
-           const Scalars* sc, OpArgs args, const ReqDesc<T>* __restrict__ reqs) {
-  if (reqs != nullptr) {
-    const ReqDesc<T>& R = reqs[blockIdx.z];
-    f = R.ff;
-    S = R.S;
-    mat = R.mat;
-    sc = R.sc;
-  }
-  if (sc != nullptr && sc->done) return;
-  const int n = P.n, nh = (n + 1) / 2;
-  const int half = LB / 2;
-  const int nlc = ncomp * half;
+__device__ __forceinline__ void line_pre_to_smem(const Fields<T>& f, int b0, int n, int half,
+                                                 int ncomp, long long l0, int LB, long long nlines,
+                                                 FastDiv fdn, const MatView<T>& mat,
+                                                 const Scalars* sc, const OpArgs& args) {
   cpx<T>* sm = smem_c<T>();
-  const int b0 = n, b1 = n + nlc * n;  // element offsets; twiddles at 0
-  __shared__ AxisPlan Ps;
-  if (threadIdx.x == 0) Ps = P;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = twg[i];
-  const long long l0 = (long long)blockIdx.x * LB;
   const double* Es = sc != nullptr ? sc->E : args.E;
   const T E[3] = {(T)Es[0], (T)Es[1], (T)Es[2]};
   const T omega = (T)(sc != nullptr ? sc->omega : args.omega);
@@ -273,7 +262,7 @@ k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int idx = base + k * blockDim.x + threadIdx.x;
-      const int ll = fdiv(idx, P.fdn), j = idx - ll * n;
+      const int ll = fdiv(idx, fdn), j = idx - ll * n;
       const long long l = l0 + ll;
       const bool ok = idx < LB * n && l < nlines;
       const long long g = l * n + j;
@@ -288,7 +277,7 @@ k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
     for (int k = 0; k < K; ++k) {
       const int idx = base + k * blockDim.x + threadIdx.x;
       if (idx >= LB * n) continue;
-      const int ll = fdiv(idx, P.fdn), j = idx - ll * n;
+      const int ll = fdiv(idx, fdn), j = idx - ll * n;
       const long long l = l0 + ll;
       const bool ok = l < nlines;
       const long long g = l * n + j;
@@ -327,6 +316,31 @@ k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
       }
     }
   }
+}
+
+template <typename T, int D, int PRE>
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
+k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
+           int ncomp, long long nlines, int LB, LineDiv ld, long long scs, MatView<T> mat,
+           const Scalars* sc, OpArgs args, const ReqDesc<T>* __restrict__ reqs) {
+  if (reqs != nullptr) {
+    const ReqDesc<T>& R = reqs[blockIdx.z];
+    f = R.ff;
+    S = R.S;
+    mat = R.mat;
+    sc = R.sc;
+  }
+  if (sc != nullptr && sc->done) return;
+  const int n = P.n, nh = (n + 1) / 2;
+  const int half = LB / 2;
+  const int nlc = ncomp * half;
+  cpx<T>* sm = smem_c<T>();
+  const int b0 = n, b1 = n + nlc * n;  // element offsets; twiddles at 0
+  __shared__ AxisPlan Ps;
+  if (threadIdx.x == 0) Ps = P;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = twg[i];
+  const long long l0 = (long long)blockIdx.x * LB;
+  line_pre_to_smem<T, D, PRE>(f, b0, n, half, ncomp, l0, LB, nlines, P.fdn, mat, sc, args);
   __syncthreads();
   const int res = reg_lines<T>(b0, b1, &Ps, nlc, n, 1, false, false, 0);
   for (int idx = threadIdx.x; idx < nlc * nh; idx += blockDim.x) {
@@ -495,72 +509,24 @@ k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC
   stage_any<T>(true, &Ps, nst - 1, sloc2<T>(a, 1, TCp, cstr, tcl), gl, nl, true, 0);
 }
 
-// ---------------------------------------------------------------------------------------
-// line_inv: inverse real DFT of the contiguous axis + post-operator
-// ---------------------------------------------------------------------------------------
+// Post-operator of the lines l0 .. l0 + LB - 1 after their inverse transform: node j of line
+// l0 + ll is the real (ll even) or imaginary (ll odd) part of shared-memory complex line
+// res + (a * half + ll / 2) * n; the solver's vector update, batches of K nodes whose operands
+// are loaded before any use, and the inner-product partial in dacc.
 template <typename T, int D, int POST>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
-k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ twg,
-           int ncomp, long long nlines, int LB, LineDiv ld, long long scs, MatView<T> mat,
-           Scalars* sc, OpArgs args, double* partials, unsigned* counter, int negate,
-           const ReqDesc<T>* __restrict__ reqs) {
-  if (reqs != nullptr) {
-    const ReqDesc<T>& R = reqs[blockIdx.z];
-    f = R.fi;
-    S = R.S;
-    mat = R.mat;
-    sc = R.sc;
-    partials = R.partials;
-    counter = R.counter;
-  }
-  if (sc != nullptr && sc->done) return;
-  const int n = P.n, nh = (n + 1) / 2;
-  const int half = LB / 2;
-  const int nlc = ncomp * half;
+__device__ __forceinline__ void line_post_from_smem(const Fields<T>& f, int res, int n, int half,
+                                                    int ncomp, long long l0, int LB,
+                                                    long long nlines, FastDiv fdn,
+                                                    const MatView<T>& mat, const Scalars* sc,
+                                                    const OpArgs& args, int negate,
+                                                    DotAcc<T>& dacc) {
   cpx<T>* sm = smem_c<T>();
-  const int b0 = n, b1 = n + nlc * n;  // b1 holds nlc (n + 1): staged half spectra, ping-pong
-  __shared__ AxisPlan Ps;
-  if (threadIdx.x == 0) Ps = P;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = twg[i];
-  const long long l0 = (long long)blockIdx.x * LB;
-  const cpx<T> zero = {0, 0};
-  // stage the half spectra of the CTA's lines (contiguous per line) asynchronously
-  for (int idx = threadIdx.x; idx < ncomp * LB * nh; idx += blockDim.x) {
-    const int al = fdiv(idx, P.fdnh), k = idx - al * nh;
-    const int a = fdiv(al, ld.lb), ll = al - a * LB;
-    if (l0 + ll < nlines) cp_async_elem<T>(sm + b1 + idx, S + a * scs + (l0 + ll) * nh + k);
-    else sm[b1 + idx] = zero;
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  // pack two Hermitian half spectra (lines 2 pr, 2 pr + 1) into one complex line
-  for (int idx = threadIdx.x; idx < nlc * nh; idx += blockDim.x) {
-    const int lc = fdiv(idx, P.fdnh), k = idx - lc * nh;
-    const int a = fdiv(lc, ld.half), pr = lc - a * half;
-    const cpx<T> A = sm[b1 + (a * LB + 2 * pr) * nh + k];
-    const cpx<T> B = sm[b1 + (a * LB + 2 * pr + 1) * nh + k];
-    const int line = b0 + lc * n;
-    if (k == 0) {
-      sm[line].x = A.x;
-      sm[line].y = B.x;
-    } else {
-      sm[line + k].x = A.x - B.y;
-      sm[line + k].y = A.y + B.x;
-      sm[line + n - k].x = A.x + B.y;
-      sm[line + n - k].y = B.x - A.y;
-    }
-  }
-  __syncthreads();
-  const int res = reg_lines<T>(b0, b1, &Ps, nlc, n, 1, false, true, 0);
-
-  // post-operator, in batches of K nodes whose operands are loaded before any use
   const double* Es = sc != nullptr ? sc->E : args.E;
   const T E[3] = {(T)Es[0], (T)Es[1], (T)Es[2]};
   const T omega = (T)(sc != nullptr ? sc->omega : args.omega);
   const T alpha = sc != nullptr ? (T)sc->alpha : (T)0;
   const T beta = sc != nullptr ? (T)sc->beta : (T)0;
   const int which = sc != nullptr ? sc->which : 0;
-  DotAcc<T> dacc;
   const long long cs = f.cs;
   const T* xc = (POST == POST_RICH) ? f.x + (which ? D * cs : 0) : f.x;
   T* xn = (POST == POST_RICH) ? f.x + (which ? 0 : D * cs) : f.x;
@@ -570,7 +536,7 @@ k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ 
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int idx = base + k * blockDim.x + threadIdx.x;
-      const int ll = fdiv(idx, P.fdn), j = idx - ll * n;
+      const int ll = fdiv(idx, fdn), j = idx - ll * n;
       const bool ok = idx < LB * n && l0 + ll < nlines;
       const long long g = (l0 + ll) * n + j;
 #pragma unroll
@@ -585,7 +551,7 @@ k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ 
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int idx = base + k * blockDim.x + threadIdx.x;
-      const int ll = fdiv(idx, P.fdn), j = idx - ll * n;
+      const int ll = fdiv(idx, fdn), j = idx - ll * n;
       if (idx >= LB * n || l0 + ll >= nlines) continue;
       const long long g = (l0 + ll) * n + j;
       T y[D];
@@ -645,13 +611,13 @@ k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ 
       }
     }
   }
-  if (partials == nullptr) return;
-  double acc[1] = {dacc.value()};
-  double tot[1];
-  if (!reduce_and_last<1>(acc, partials, counter, tot)) return;
-  if (threadIdx.x != 0 || sc == nullptr) return;
-  // ---- finisher: the scalar part of the algorithm step ----
-  const double mean = tot[0] / (double)(nlines * n);
+}
+
+// The scalar part of the solver step after a post-operator, run by one thread of the last CTA
+// with the grid's reduced inner product tot0 over `count` nodes (Algorithms 1-4).
+template <int POST>
+__device__ __forceinline__ void line_inv_finish(Scalars* sc, double tot0, double count) {
+  const double mean = tot0 / count;
   if (POST == POST_STORE) {
     // initial residual r_0 = b (x_0 = 0): ||b|| and (r_0, r_0)
     sc->nb = sqrt(mean);
@@ -711,6 +677,76 @@ k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ 
       sc->done = 1;
     }
   }
+}
+
+
+// ---------------------------------------------------------------------------------------
+// line_inv: inverse real DFT of the contiguous axis + post-operator
+// ---------------------------------------------------------------------------------------
+template <typename T, int D, int POST>
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
+k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ twg,
+           int ncomp, long long nlines, int LB, LineDiv ld, long long scs, MatView<T> mat,
+           Scalars* sc, OpArgs args, double* partials, unsigned* counter, int negate,
+           const ReqDesc<T>* __restrict__ reqs) {
+  if (reqs != nullptr) {
+    const ReqDesc<T>& R = reqs[blockIdx.z];
+    f = R.fi;
+    S = R.S;
+    mat = R.mat;
+    sc = R.sc;
+    partials = R.partials;
+    counter = R.counter;
+  }
+  if (sc != nullptr && sc->done) return;
+  const int n = P.n, nh = (n + 1) / 2;
+  const int half = LB / 2;
+  const int nlc = ncomp * half;
+  cpx<T>* sm = smem_c<T>();
+  const int b0 = n, b1 = n + nlc * n;  // b1 holds nlc (n + 1): staged half spectra, ping-pong
+  __shared__ AxisPlan Ps;
+  if (threadIdx.x == 0) Ps = P;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = twg[i];
+  const long long l0 = (long long)blockIdx.x * LB;
+  const cpx<T> zero = {0, 0};
+  // stage the half spectra of the CTA's lines (contiguous per line) asynchronously
+  for (int idx = threadIdx.x; idx < ncomp * LB * nh; idx += blockDim.x) {
+    const int al = fdiv(idx, P.fdnh), k = idx - al * nh;
+    const int a = fdiv(al, ld.lb), ll = al - a * LB;
+    if (l0 + ll < nlines) cp_async_elem<T>(sm + b1 + idx, S + a * scs + (l0 + ll) * nh + k);
+    else sm[b1 + idx] = zero;
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // pack two Hermitian half spectra (lines 2 pr, 2 pr + 1) into one complex line
+  for (int idx = threadIdx.x; idx < nlc * nh; idx += blockDim.x) {
+    const int lc = fdiv(idx, P.fdnh), k = idx - lc * nh;
+    const int a = fdiv(lc, ld.half), pr = lc - a * half;
+    const cpx<T> A = sm[b1 + (a * LB + 2 * pr) * nh + k];
+    const cpx<T> B = sm[b1 + (a * LB + 2 * pr + 1) * nh + k];
+    const int line = b0 + lc * n;
+    if (k == 0) {
+      sm[line].x = A.x;
+      sm[line].y = B.x;
+    } else {
+      sm[line + k].x = A.x - B.y;
+      sm[line + k].y = A.y + B.x;
+      sm[line + n - k].x = A.x + B.y;
+      sm[line + n - k].y = B.x - A.y;
+    }
+  }
+  __syncthreads();
+  const int res = reg_lines<T>(b0, b1, &Ps, nlc, n, 1, false, true, 0);
+
+  DotAcc<T> dacc;
+  line_post_from_smem<T, D, POST>(f, res, n, half, ncomp, l0, LB, nlines, P.fdn, mat, sc, args,
+                                  negate, dacc);
+  if (partials == nullptr) return;
+  double acc[1] = {dacc.value()};
+  double tot[1];
+  if (!reduce_and_last<1>(acc, partials, counter, tot)) return;
+  if (threadIdx.x != 0 || sc == nullptr) return;
+  line_inv_finish<POST>(sc, tot[0], (double)(nlines * n));
 }
 
 // ---------------------------------------------------------------------------------------
