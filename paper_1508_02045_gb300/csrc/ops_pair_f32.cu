@@ -72,7 +72,7 @@ void pair_proj_f32(int D, int mode, const AxisPlan& P, cpx<float>* S, const cpx<
   {                                                                                            \
     constexpr int TC = pair_tc_proj<D_, R2_>();                                                \
     const dim3 grid((unsigned)((pg.C + TC - 1) / TC), 1, (unsigned)nreq);                     \
-    const size_t sm = sizeof(cpx<T>) * ((size_t)(R1_ * R2_) * (1 + 2 * D_ * (TC + 1)));        \
+    const size_t sm = sizeof(cpx<T>) * ((size_t)(R1_ * R2_) * (1 + D_ * (TC + 1)));        \
     if (mode == PROJ_EM)                                                                       \
       k_pair_proj<T, D_, PROJ_EM, R1_, R2_><<<grid, D_ * TC * R2_, sm, st>>>(S, tw, pg, sc, reqs); \
     else                                                                                       \

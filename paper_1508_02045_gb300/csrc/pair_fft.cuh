@@ -120,7 +120,9 @@ k_pair_strided(cpx<T>* S, const cpx<T>* __restrict__ twg, long long C, long long
 
 // ---------------------------------------------------------------------------------------
 // projection pass: forward DFT of axis 0, Gamma^ (or I - 2 Gamma^), inverse DFT of axis 0, on
-// a tile of TC columns of all D components; D * TC * R2 threads
+// a tile of TC columns of all D components; D * TC * R2 threads. One shared-memory tile per
+// component: forward stage 2 and the projection write back the rows they read, and the
+// inverse first stage (one butterfly a thread) loads everything before a barrier.
 // ---------------------------------------------------------------------------------------
 template <typename T, int D, int MODE, int R1, int R2>
 __global__ void __launch_bounds__(D * pair_tc_proj<D, R2>() * R2)
@@ -135,18 +137,17 @@ k_pair_proj(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, const Scalars
   if (sc != nullptr && sc->done) return;
   cpx<T>* sm = smem_c<T>();
   cpx<T>* tw = sm;
-  cpx<T>* A = sm + n;         // D tiles, component stride cstr
-  cpx<T>* B = A + D * cstr;
+  cpx<T>* A = sm + n;  // D tiles, component stride cstr
   for (int i = threadIdx.x; i < n; i += NT) tw[i] = twg[i];
   const long long c0 = (long long)blockIdx.x * TC;
   const int ncols = (int)min((long long)TC, g.C - c0);
   const long long es = g.C;
-  // forward stage 1, from the spectrum: item (a, i, c)
-  {
-    const int c = threadIdx.x % TC, i = (threadIdx.x / TC) % R2, a = threadIdx.x / (TC * R2);
-    if (c < ncols)
-      pair_stage1_from_global<T, R1, R2, false>(S + a * g.cs + c0 + c, es, A + a * cstr + c, TCp, i);
-  }
+  // this thread's first-stage butterfly (a, i, c), forward and inverse
+  const int c1 = threadIdx.x % TC, i1 = (threadIdx.x / TC) % R2, a1 = threadIdx.x / (TC * R2);
+  // forward stage 1, from the spectrum
+  if (c1 < ncols)
+    pair_stage1_from_global<T, R1, R2, false>(S + a1 * g.cs + c0 + c1, es, A + a1 * cstr + c1, TCp,
+                                              i1);
   __syncthreads();
   // forward stage 2 of all D components + the projection at the R2 frequencies of item (i, c)
   const T scale = (T)g.scale;
@@ -155,9 +156,9 @@ k_pair_proj(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, const Scalars
     int kc1 = 0, kc2 = 0;
     const int cc = (int)(c0 + c);
     if (D == 3) {
-      const int i1 = fdiv(cc, g.fdnh);
-      kc1 = (i1 <= (g.n1 - 1) / 2) ? i1 : i1 - g.n1;
-      kc2 = cc - i1 * g.nh;
+      const int i1c = fdiv(cc, g.fdnh);
+      kc1 = (i1c <= (g.n1 - 1) / 2) ? i1c : i1c - g.n1;
+      kc2 = cc - i1c * g.nh;
     } else {
       kc1 = cc;
     }
@@ -197,15 +198,23 @@ k_pair_proj(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, const Scalars
           o.x = fma((T)(-2 * k[a]), kv.x, scale * v[a][r].x);
           o.y = fma((T)(-2 * k[a]), kv.y, scale * v[a][r].y);
         }
-        B[a * cstr + j * TCp + c] = o;
+        A[a * cstr + j * TCp + c] = o;
       }
     }
   }
   __syncthreads();
-  // inverse stage 1 (conjugated input), shared memory to shared memory: item (a, i, c)
+  // inverse stage 1 (conjugated input) in place: all loads, a barrier, all stores
   {
-    const int c = threadIdx.x % TC, i = (threadIdx.x / TC) % R2, a = threadIdx.x / (TC * R2);
-    pair_stage1_shared<T, R1, R2, true>(B + a * cstr + c, A + a * cstr + c, TCp, i);
+    const cpx<T>* s = A + a1 * cstr + c1;
+    cpx<T> u[R1];
+#pragma unroll
+    for (int r = 0; r < R1; ++r) u[r] = s[(i1 + r * R2) * TCp];
+    conj_all<T, R1>(u);
+    RegDft<T, R1>::run(u);
+    __syncthreads();
+    cpx<T>* t = A + a1 * cstr + c1;
+#pragma unroll
+    for (int r = 0; r < R1; ++r) t[(i1 * R1 + r) * TCp] = u[r];
   }
   __syncthreads();
   // inverse stage 2 into the spectrum (conjugated output): item (a, i, c)
@@ -226,6 +235,9 @@ k_pair_proj(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, const Scalars
 // component, two real lines packed into one complex line (a, q) at n + (a LBP + q) n
 // ---------------------------------------------------------------------------------------
 // line pairs per CTA: as many as keep the first-stage butterflies D x LBP x R2 within 256
+// nodes per thread whose pre-operator loads are issued together in the specialised line_fwd
+constexpr int kPairPreBatch = 4;
+
 template <int D, int R2>
 __host__ __device__ constexpr int pair_lbp() {
   return 256 / (D * R2);
@@ -259,7 +271,7 @@ k_pair_line_fwd(Fields<T> f, cpx<T>* S, const cpx<T>* __restrict__ twg, long lon
   cpx<T>* lines = sm + n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
   const long long l0 = (long long)blockIdx.x * LB;
-  line_pre_to_smem<T, D, PRE>(f, n, n, LBP, D, l0, LB, nlines, fdn, mat, sc, args);
+  line_pre_to_smem<T, D, PRE, kPairPreBatch>(f, n, n, LBP, D, l0, LB, nlines, fdn, mat, sc, args);
   __syncthreads();
   {
     const int t = threadIdx.x;
@@ -375,8 +387,9 @@ k_pair_line_inv(const cpx<T>* S, Fields<T> f, const cpx<T>* __restrict__ twg, lo
   }
   __syncthreads();
   DotAcc<T> dacc;
-  line_post_from_smem<T, D, POST>(f, n, n, LBP, D, l0, LB, nlines, fdn, mat, sc, args, negate,
-                                  dacc);
+  // Chebyshev reads three operands a node: smaller batches keep it within the register budget
+  line_post_from_smem<T, D, POST, POST == POST_CHEB ? 2 : 4>(f, n, n, LBP, D, l0, LB, nlines, fdn,
+                                                            mat, sc, args, negate, dacc);
   if (partials == nullptr) return;
   double acc[1] = {dacc.value()};
   double tot[1];

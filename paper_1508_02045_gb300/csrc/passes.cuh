@@ -241,7 +241,7 @@ struct ReqDesc {
 // nodes): component a of line l0 + ll goes to the real (ll even) or imaginary (ll odd) part of
 // the shared-memory complex line b0 + (a * half + ll / 2) * n, so that two real lines share one
 // complex transform.
-template <typename T, int D, int PRE>
+template <typename T, int D, int PRE, int K = (sizeof(T) == 4 ? 8 : 4)>
 __device__ __forceinline__ void line_pre_to_smem(const Fields<T>& f, int b0, int n, int half,
                                                  int ncomp, long long l0, int LB, long long nlines,
                                                  FastDiv fdn, const MatView<T>& mat,
@@ -255,7 +255,6 @@ __device__ __forceinline__ void line_pre_to_smem(const Fields<T>& f, int b0, int
   const T* xin = f.xin;
   if (f.x != nullptr && sc != nullptr) xin = f.x + (sc->which ? D * f.cs : 0);
   // batches of K nodes per thread: every global load of a batch is issued before any use
-  constexpr int K = sizeof(T) == 4 ? 8 : 4;
   const T* __restrict__ pin = f.p;
   for (int base = 0; base < LB * n; base += K * blockDim.x) {
     T xv[K][D], pv[K][D], ms[K];
@@ -513,7 +512,7 @@ k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC
 // l0 + ll is the real (ll even) or imaginary (ll odd) part of shared-memory complex line
 // res + (a * half + ll / 2) * n; the solver's vector update, batches of K nodes whose operands
 // are loaded before any use, and the inner-product partial in dacc.
-template <typename T, int D, int POST>
+template <typename T, int D, int POST, int K = (sizeof(T) == 4 ? 4 : 2)>
 __device__ __forceinline__ void line_post_from_smem(const Fields<T>& f, int res, int n, int half,
                                                     int ncomp, long long l0, int LB,
                                                     long long nlines, FastDiv fdn,
@@ -530,7 +529,6 @@ __device__ __forceinline__ void line_post_from_smem(const Fields<T>& f, int res,
   const long long cs = f.cs;
   const T* xc = (POST == POST_RICH) ? f.x + (which ? D * cs : 0) : f.x;
   T* xn = (POST == POST_RICH) ? f.x + (which ? 0 : D * cs) : f.x;
-  constexpr int K = sizeof(T) == 4 ? 4 : 2;
   for (int base = 0; base < LB * n; base += K * blockDim.x) {
     T o1[K][D], o2[K][D], o3[K][D], ms[K];
 #pragma unroll
