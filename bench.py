@@ -11,7 +11,8 @@ so no flush is needed between steps.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Profiling helpers (not bench lines): --quick skips the end-to-end, CG-to-tolerance and CPU
-legs; --grid n runs the same step on an n^3 grid (used for ncu captures on a smaller case).
+legs; --precision fp32 (with --quick) times the FP32 inner CG step instead; --grid n runs the
+same step on an n^3 grid (used for ncu captures on a smaller case).
 """
 from __future__ import annotations
 
@@ -159,6 +160,42 @@ class ClockSampler:
 # CPU oracle leg (test infrastructure, timed as it stands)
 # ------------------------------------------------------------------------------------------
 
+def cufft_matvec(ph, table, x_dev, dtype, steps):
+    """The same G A x on the same grid with PyTorch's FFTs (cuFFT), as a timed comparison only:
+    A x pointwise, rfftn over the three axes, Gamma^ = k k^T / |k|^2 (k = 0 zeroed), irfftn.
+    torch's rfftn is unscaled and irfftn carries 1/|N|, the normalisation of eq. (DFT) up to
+    where the factor sits. Returns (ms per matvec, result)."""
+    import torch
+    dev = x_dev.device
+    n0, n1, n2 = N_GRID
+    a = torch.as_tensor(np.asarray(table)[:, 0, 0], device=dev, dtype=dtype)[
+        torch.as_tensor(ph.astype(np.int64), device=dev)]
+    k0 = torch.fft.fftfreq(n0, 1.0 / n0, device=dev, dtype=dtype).view(n0, 1, 1)
+    k1 = torch.fft.fftfreq(n1, 1.0 / n1, device=dev, dtype=dtype).view(1, n1, 1)
+    k2 = torch.fft.rfftfreq(n2, 1.0 / n2, device=dev, dtype=dtype).view(1, 1, -1)
+    kk = k0 * k0 + k1 * k1 + k2 * k2
+    inv = torch.where(kk > 0, 1.0 / torch.where(kk > 0, kk, torch.ones_like(kk)), torch.zeros_like(kk))
+    x = x_dev.to(dtype)
+
+    def matvec(xx):
+        vh = torch.fft.rfftn(a * xx, dim=(1, 2, 3))
+        s = (k0 * vh[0] + k1 * vh[1] + k2 * vh[2]) * inv
+        yh = torch.stack((k0 * s, k1 * s, k2 * s))
+        return torch.fft.irfftn(yh, s=(n0, n1, n2), dim=(1, 2, 3))
+
+    for _ in range(2):
+        y = matvec(x)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        y = matvec(x)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, y
+
+
 def cpu_oracle_cg_steps(nsteps=1):
     """Time CG iterations of the FP64 NumPy oracle on this host at the bench workload."""
     import oracle as O
@@ -276,12 +313,18 @@ def run_ours(args, rank, world, local):
 
     torch.cuda.set_device(local)
     ph, table = workload()
-    prob = H.Problem(D, N_GRID, H.phase_material(ph, table))
+    fp32_only = args.quick and args.precision == "fp32"
+    prob = H.Problem(D, N_GRID, H.phase_material(ph, table),
+                     precision=H.HOM_FP32_REFINED if fp32_only else H.HOM_FP64)
     tune = H.hom_autotune(prob.h, reps=2)  # the launch plan a user gets from the autotuner
     stream = torch.cuda.current_stream()
     total = args.warmup + args.steps
-    opts = H.make_opts(fixed_iters=total + 1)
-    H.hom_solve_begin(prob.h, E_MACRO, H.HOM_CG, 0.0, opts)
+    if fp32_only:  # the FP32 inner CG step of the refinement (profiling helper)
+        opts = H.make_opts(maxit=2, inner_tol=1e-30)
+        H.hom_solve_begin(prob.h, E_MACRO, H.HOM_CG, 1e-30, opts)
+    else:
+        opts = H.make_opts(fixed_iters=total + 1)
+        H.hom_solve_begin(prob.h, E_MACRO, H.HOM_CG, 0.0, opts)
     H.hom_solve_iterate(prob.h, args.warmup)
     torch.cuda.synchronize()
 
@@ -309,7 +352,8 @@ def run_ours(args, rank, world, local):
     if args.quick:
         prob.close()
         if rank == 0:
-            print(json.dumps({"quick": True, "grid": list(N_GRID), "ms_per_step": ms_step,
+            print(json.dumps({"quick": True, "precision": args.precision, "grid": list(N_GRID),
+                              "ms_per_step": ms_step,
                               "passes": passes, "gpu_launches": int(launches)}), flush=True)
         return None
 
@@ -356,6 +400,18 @@ def run_ours(args, rank, world, local):
     f1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(f0.elapsed_time(f1), world) / e_steps
+
+    # ---- the same matvec with cuFFT (torch.fft), a timed comparison only ----
+    xr = torch.from_numpy(ms.random_field((D,) + tuple(N_GRID), 12)).cuda()
+    ours = prob.field()
+    H.hom_apply(prob.h, H.HOM_OP_LINEAR, None, xr, ours)
+    cmp_steps = max(3, min(args.steps, 10))
+    cu64_ms, cu64_y = cufft_matvec(ph, table, xr, torch.float64, cmp_steps)
+    cu_rel = float(torch.linalg.vector_norm(cu64_y - ours) / torch.linalg.vector_norm(ours))
+    del cu64_y
+    cu32_ms, cu32_y = cufft_matvec(ph, table, xr, torch.float32, cmp_steps)
+    del cu32_y, xr, ours
+    torch.cuda.synchronize()
 
     # ---- CG time to 1e-6 (outside the timed region) ----
     torch.cuda.synchronize()
@@ -421,6 +477,12 @@ def run_ours(args, rank, world, local):
                                    "peak_source": peaks["source"]},
                       "passes": pk32},
         "clocks": clk,
+        "cufft_comparison": {
+            "what": "G A x with torch.fft (cuFFT rfftn/irfftn) + elementwise torch ops, same grid "
+                    "and coefficients; timed comparison, not the product path",
+            "fp64_ms": round(cu64_ms, 4), "fp64_matvec_per_s": round(1000.0 / cu64_ms, 3),
+            "fp32_ms": round(cu32_ms, 4), "fp32_matvec_per_s": round(1000.0 / cu32_ms, 3),
+            "fp64_rel_diff_vs_ours": cu_rel},
         "cg_to_1e-6": {"iterations": stats["iterations"], "seconds": round(cg_wall, 3),
                        "device_ms": round(stats["time_ms"], 2), "A_H": AH,
                        "converged": bool(stats["converged"])},
@@ -619,6 +681,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--grid", type=int, default=0)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                    help="with --quick: time the FP64 CG step or the FP32 inner CG step")
     ap.add_argument("--serve", type=int, default=0, help="run the served mix with this many requests")
     ap.add_argument("--serve-window", type=float, default=1.0)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
