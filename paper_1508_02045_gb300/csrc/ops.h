@@ -25,6 +25,7 @@ struct PassGeom {
                           // threads per CTA
   int TCs0, TCs0p, NTs0;  // plain strided pass along axis 0 (prolongation, Ga assembly)
   int TC0, TC0p, NT0;     // projection pass (axis 0, all components)
+  int TCq, TCqp, NTq;     // projection pass of the 3-D scalar problem (two lines a column)
 };
 
 template <typename T>
@@ -33,6 +34,7 @@ struct Ops {
   static size_t smem_line(int n, int ncomp, int LB);
   static size_t smem_strided(int n, int TCp, int nst);
   static size_t smem_proj(int n, int D, int TCp, int nst);
+  static size_t smem_proj_scalar(int n, int TCp);
   // launch geometry of every pass of a grid with axis plans `plan`, keeping each CTA's shared
   // memory within `budget` bytes; false if a pass cannot fit the device limit
   static bool plan_geometry(int D, const int* n, const AxisPlan* plan, size_t budget,

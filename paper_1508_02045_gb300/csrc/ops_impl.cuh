@@ -39,18 +39,27 @@ size_t Ops<T>::smem_proj(int n, int D, int TCp, int nst) {
   return sizeof(cpx<T>) * ((size_t)n + nbuf * (size_t)D * n * TCp);
 }
 
+template <typename T>
+size_t Ops<T>::smem_proj_scalar(int n, int TCp) {
+  return sizeof(cpx<T>) * ((size_t)n + 2 * 2 * (size_t)n * TCp);
+}
+
 // Columns per CTA of a column kernel (a power of two <= tcmax, pitch TC + 1) and its threads:
 // the widest tile whose first-stage butterflies (lines x TC x n / R_0) fit the thread limit and
 // whose shared memory fits the budget, but at least one 32-byte sector of every row (unless
 // the device limit forces narrower tiles). Threads:
 // one per butterfly, rounded up to whole warps and to a multiple of TC, at most kColThreads.
+enum ColKind { COL_STRIDED = 0, COL_PROJ = 1, COL_PROJ_SCALAR = 2 };
+
 template <typename T>
-static void pick_cols(const AxisPlan& P, int lines, int tcmax, size_t budget, bool proj, int D,
+static void pick_cols(const AxisPlan& P, int lines, int tcmax, size_t budget, int kind, int D,
                       int* TC, int* TCp, int* NT) {
   const int m1 = P.n / P.radix[0];
   const int tcmin = std::max(1, 32 / (int)sizeof(cpx<T>));
   auto smem = [&](int t) {
-    return proj ? Ops<T>::smem_proj(P.n, D, t + 1, P.nst) : Ops<T>::smem_strided(P.n, t + 1, P.nst);
+    return kind == COL_PROJ ? Ops<T>::smem_proj(P.n, D, t + 1, P.nst)
+         : kind == COL_PROJ_SCALAR ? Ops<T>::smem_proj_scalar(P.n, t + 1)
+                                   : Ops<T>::smem_strided(P.n, t + 1, P.nst);
   };
   int tc = tcmax;
   while (tc > tcmin && ((long long)lines * tc * m1 > kColThreads<T> || smem(tc) > budget)) tc /= 2;
@@ -79,13 +88,15 @@ bool Ops<T>::plan_geometry(int D, const int* n, const AxisPlan* plan, size_t bud
   g->scs = g->nlines * g->nh;
   g->LB = 16;
   while (g->LB > 2 && smem_line(nl, D, g->LB) > budget) g->LB -= 2;
-  if (D == 3) pick_cols<T>(plan[1], 1, 64, budget, false, D, &g->TC1, &g->TC1p, &g->NT1);
-  pick_cols<T>(plan[0], D, 32, budget, true, D, &g->TC0, &g->TC0p, &g->NT0);
-  pick_cols<T>(plan[0], 1, 64, budget, false, D, &g->TCs0, &g->TCs0p, &g->NTs0);
+  if (D == 3) pick_cols<T>(plan[1], 1, 64, budget, COL_STRIDED, D, &g->TC1, &g->TC1p, &g->NT1);
+  pick_cols<T>(plan[0], D, 32, budget, COL_PROJ, D, &g->TC0, &g->TC0p, &g->NT0);
+  pick_cols<T>(plan[0], 2, 32, budget, COL_PROJ_SCALAR, D, &g->TCq, &g->TCqp, &g->NTq);
+  pick_cols<T>(plan[0], 1, 64, budget, COL_STRIDED, D, &g->TCs0, &g->TCs0p, &g->NTs0);
   // the column kernels address the D component tiles with 32-bit offsets
   if ((long long)D * g->scs >= (1LL << 31)) return false;
   const size_t cap = (size_t)dynamic_smem_cap();
   return smem_line(nl, D, g->LB) <= cap && smem_proj(n[0], D, g->TC0p, plan[0].nst) <= cap &&
+         smem_proj_scalar(n[0], g->TCqp) <= cap &&
          (D != 3 || smem_strided(n[1], g->TC1p, plan[1].nst) <= cap) &&
          smem_strided(n[0], g->TCs0p, plan[0].nst) <= cap;
 }
@@ -135,6 +146,7 @@ cudaError_t Ops<T>::prepare(int) {
   HOM_SET_SMEM((k_proj<T, 2, PROJ_EM>));
   HOM_SET_SMEM((k_proj<T, 3, PROJ_GAMMA>));
   HOM_SET_SMEM((k_proj<T, 3, PROJ_EM>));
+  HOM_SET_SMEM((k_proj_scalar<T>));
   HOM_SET_SMEM((k_line_inv<T, 2, POST_STORE>));
   HOM_SET_SMEM((k_line_inv<T, 2, POST_RICH>));
   HOM_SET_SMEM((k_line_inv<T, 2, POST_CG>));
@@ -238,6 +250,14 @@ void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, con
   if (pair_plan<T>(P)) {
     if constexpr (std::is_same<T, float>::value)
       pair_proj_f32(g.D, mode, P, S, tw, pg, sc, st, reqs, nreq);
+    if (prof) prof_mark(KIND_PROJ, st, false);
+    ++launch_counter();
+    return;
+  }
+  if (g.D == 3 && mode == PROJ_GAMMA) {
+    const dim3 grid((unsigned)((pg.C + g.TCq - 1) / g.TCq), 1, (unsigned)nreq);
+    const size_t sm = smem_proj_scalar(P.n, g.TCqp);
+    k_proj_scalar<T><<<grid, g.NTq, sm, st>>>(S, P, tw, pg, g.TCq, g.TCqp, sc, reqs);
     if (prof) prof_mark(KIND_PROJ, st, false);
     ++launch_counter();
     return;

@@ -35,6 +35,7 @@ cudaError_t pair_prepare_f32(int cap) {
   HOM_SET_SMEM((k_pair_proj<T, 2, PROJ_EM, R1_, R2_>));         \
   HOM_SET_SMEM((k_pair_proj<T, 3, PROJ_GAMMA, R1_, R2_>));      \
   HOM_SET_SMEM((k_pair_proj<T, 3, PROJ_EM, R1_, R2_>));         \
+  HOM_SET_SMEM((k_pair_proj_scalar<T, R1_, R2_>));              \
   HOM_SET_SMEM((k_pair_line_fwd<T, 3, PRE_CG, R1_, R2_>));      \
   HOM_SET_SMEM((k_pair_line_fwd<T, 3, PRE_LINEAR, R1_, R2_>));  \
   HOM_SET_SMEM((k_pair_line_inv<T, 3, POST_CG, R1_, R2_>));     \
@@ -78,11 +79,19 @@ void pair_proj_f32(int D, int mode, const AxisPlan& P, cpx<float>* S, const cpx<
     else                                                                                       \
       k_pair_proj<T, D_, PROJ_GAMMA, R1_, R2_><<<grid, D_ * TC * R2_, sm, st>>>(S, tw, pg, sc, reqs); \
   }
-#define HOM_PAIR_PJ(R1_, R2_)                   \
-  if (P.radix[0] == R1_ && P.radix[1] == R2_) { \
-    if (D == 2) HOM_PAIR_PJ_D(2, R1_, R2_)      \
-    else HOM_PAIR_PJ_D(3, R1_, R2_)             \
-    return;                                     \
+#define HOM_PAIR_PJ(R1_, R2_)                                                                  \
+  if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
+    if (D == 2) {                                                                              \
+      HOM_PAIR_PJ_D(2, R1_, R2_)                                                               \
+    } else if (mode == PROJ_GAMMA) {                                                           \
+      constexpr int TC = pair_tc_proj_scalar<R2_>();                                           \
+      const dim3 grid((unsigned)((pg.C + TC - 1) / TC), 1, (unsigned)nreq);                   \
+      const size_t sm = sizeof(cpx<T>) * ((size_t)(R1_ * R2_) * (1 + 2 * (TC + 1)));           \
+      k_pair_proj_scalar<T, R1_, R2_><<<grid, 2 * TC * R2_, sm, st>>>(S, tw, pg, sc, reqs);    \
+    } else {                                                                                   \
+      HOM_PAIR_PJ_D(3, R1_, R2_)                                                               \
+    }                                                                                          \
+    return;                                                                                    \
   }
   HOM_PAIR_PLANS(HOM_PAIR_PJ)
 #undef HOM_PAIR_PJ

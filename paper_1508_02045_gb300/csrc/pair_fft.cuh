@@ -231,6 +231,123 @@ k_pair_proj(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, const Scalars
 }
 
 // ---------------------------------------------------------------------------------------
+// projection pass of the 3-D scalar problem (Gamma^ only): two lines a column, X_0 and
+// Y = k_1 X_1 + k_2 X_2 forward, k_0 s and s inverse (see k_proj_scalar); 2 * TC * R2 threads
+// ---------------------------------------------------------------------------------------
+// columns per CTA: the widest power of two <= 32 with 2 * TC * R2 <= 320 threads (128-byte rows
+// for 243 = 27 * 9; measured 25 % faster than 64-byte rows there)
+template <int R2>
+__host__ __device__ constexpr int pair_tc_proj_scalar() {
+  return 2 * 32 * R2 <= 320 ? 32 : 2 * 16 * R2 <= 320 ? 16 : 2 * 8 * R2 <= 320 ? 8 : 4;
+}
+
+template <typename T, int R1, int R2>
+__global__ void __launch_bounds__(2 * pair_tc_proj_scalar<R2>() * R2)
+k_pair_proj_scalar(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, const Scalars* sc,
+                   const ReqDesc<T>* __restrict__ reqs) {
+  constexpr int n = R1 * R2, TC = pair_tc_proj_scalar<R2>(), TCp = TC + 1, NT = 2 * TC * R2;
+  constexpr int cstr = n * TCp;
+  if (reqs != nullptr) {
+    S = reqs[blockIdx.z].S;
+    sc = reqs[blockIdx.z].sc;
+  }
+  if (sc != nullptr && sc->done) return;
+  cpx<T>* sm = smem_c<T>();
+  cpx<T>* tw = sm;
+  cpx<T>* A = sm + n;  // line t of column c at A + t * cstr + c (row stride TCp)
+  for (int i = threadIdx.x; i < n; i += NT) tw[i] = twg[i];
+  const long long c0 = (long long)blockIdx.x * TC;
+  const int ncols = (int)min((long long)TC, g.C - c0);
+  const long long es = g.C;
+  // this thread's first-stage butterfly (t, i, c), forward and inverse
+  const int c1 = threadIdx.x % TC, i1 = (threadIdx.x / TC) % R2, t1 = threadIdx.x / (TC * R2);
+  {
+    int kc1, kc2;
+    column_freqs(g, c0 + c1, &kc1, &kc2);
+    cpx<T> u[R1];
+    const cpx<T>* col = S + c0 + c1;
+    if (c1 < ncols) {
+      if (t1 == 0) {
+#pragma unroll
+        for (int r = 0; r < R1; ++r) u[r] = col[(long long)(i1 + r * R2) * es];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R1; ++r) {
+          const cpx<T>* e = col + (long long)(i1 + r * R2) * es;
+          const cpx<T> x1 = e[g.cs], x2 = e[2 * g.cs];
+          u[r].x = (T)kc1 * x1.x + (T)kc2 * x2.x;
+          u[r].y = (T)kc1 * x1.y + (T)kc2 * x2.y;
+        }
+      }
+      RegDft<T, R1>::run(u);
+      cpx<T>* t = A + t1 * cstr + c1;
+#pragma unroll
+      for (int r = 0; r < R1; ++r) t[(i1 * R1 + r) * TCp] = u[r];
+    }
+  }
+  __syncthreads();
+  // forward stage 2 of both lines, then s at the R2 frequencies of item (i, c), in place
+  const T scale = (T)g.scale;
+  for (int w = threadIdx.x; w < TC * R1; w += NT) {
+    const int c = w % TC, i = w / TC;
+    int kc1, kc2;
+    column_freqs(g, c0 + c, &kc1, &kc2);
+    cpx<T> v0[R2], vy[R2];
+    pair_stage2_regs<T, R1, R2>(A + c, tw, TCp, i, v0);
+    pair_stage2_regs<T, R1, R2>(A + cstr + c, tw, TCp, i, vy);
+    const bool in12 = abs(kc1) <= g.hw[1] && abs(kc2) <= g.hw[2];
+#pragma unroll
+    for (int r = 0; r < R2; ++r) {
+      const int j = i + r * R1;
+      const int k0 = (j <= (n - 1) / 2) ? j : j - n;
+      const int kk = k0 * k0 + kc1 * kc1 + kc2 * kc2;
+      const T coef = (kk > 0 && in12 && abs(k0) <= g.hw[0]) ? scale / (T)kk : (T)0;
+      cpx<T> sv;
+      sv.x = fma((T)k0, v0[r].x, vy[r].x) * coef;
+      sv.y = fma((T)k0, v0[r].y, vy[r].y) * coef;
+      A[j * TCp + c] = cpx<T>{(T)k0 * sv.x, (T)k0 * sv.y};
+      A[cstr + j * TCp + c] = sv;
+    }
+  }
+  __syncthreads();
+  // inverse stage 1 (conjugated input) in place: all loads, a barrier, all stores
+  {
+    const cpx<T>* s0 = A + t1 * cstr + c1;
+    cpx<T> u[R1];
+#pragma unroll
+    for (int r = 0; r < R1; ++r) u[r] = s0[(i1 + r * R2) * TCp];
+    conj_all<T, R1>(u);
+    RegDft<T, R1>::run(u);
+    __syncthreads();
+    cpx<T>* t = A + t1 * cstr + c1;
+#pragma unroll
+    for (int r = 0; r < R1; ++r) t[(i1 * R1 + r) * TCp] = u[r];
+  }
+  __syncthreads();
+  // inverse stage 2 into the spectrum: line 0 -> component 0, line 1 -> k_1 U, k_2 U
+  for (int w = threadIdx.x; w < 2 * TC * R1; w += NT) {
+    const int c = w % TC, i = (w / TC) % R1, t = w / (TC * R1);
+    if (c >= ncols) continue;
+    cpx<T> u[R2];
+    pair_stage2_regs<T, R1, R2>(A + t * cstr + c, tw, TCp, i, u);
+    cpx<T>* out = S + c0 + c;
+    if (t == 0) {
+#pragma unroll
+      for (int r = 0; r < R2; ++r) out[(long long)(i + r * R1) * es] = cpx<T>{u[r].x, -u[r].y};
+    } else {
+      int kc1, kc2;
+      column_freqs(g, c0 + c, &kc1, &kc2);
+#pragma unroll
+      for (int r = 0; r < R2; ++r) {
+        cpx<T>* e = out + (long long)(i + r * R1) * es;
+        e[g.cs] = cpx<T>{(T)kc1 * u[r].x, -(T)kc1 * u[r].y};
+        e[2 * g.cs] = cpx<T>{(T)kc2 * u[r].x, -(T)kc2 * u[r].y};
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // line passes (contiguous axis, D = 3, every component): CTA = LBP line pairs of each
 // component, two real lines packed into one complex line (a, q) at n + (a LBP + q) n
 // ---------------------------------------------------------------------------------------

@@ -508,6 +508,101 @@ k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC
   stage_any<T>(true, &Ps, nst - 1, sloc2<T>(a, 1, TCp, cstr, tcl), gl, nl, true, 0);
 }
 
+// Projection pass of the 3-D scalar problem (Gamma^ only). Gamma^(k) v = k s(k) with
+// s = (k . v) / |k|^2 (eq. (proj)), and k_1, k_2 are constant along axis 0: of the three forward
+// axis-0 transforms two remain, of X_0 and of Y = k_1 X_1 + k_2 X_2 (combined on load), and of
+// the three inverse ones also two, of k_0 s and of s; the outputs of components 1 and 2 are
+// k_1 U and k_2 U with U = F_0^{-1} s. One CTA per tile of TC columns, two lines per column.
+__device__ __forceinline__ void column_freqs(const ProjGeom& g, long long cc, int* kc1, int* kc2) {
+  const int i1 = fdiv((int)cc, g.fdnh);
+  *kc1 = (i1 <= (g.n1 - 1) / 2) ? i1 : i1 - g.n1;
+  *kc2 = (int)cc - i1 * g.nh;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kColThreads<T>, 2)
+k_proj_scalar(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC,
+              int TCp, const Scalars* sc, const ReqDesc<T>* __restrict__ reqs) {
+  if (reqs != nullptr) {
+    S = reqs[blockIdx.z].S;
+    sc = reqs[blockIdx.z].sc;
+  }
+  if (sc != nullptr && sc->done) return;
+  const int n = P.n;
+  cpx<T>* sm = smem_c<T>();
+  const int cstr = n * TCp;  // line t of column c, row j at buf + t * cstr + j * TCp + c
+  const int bufA = n, bufB = n + 2 * cstr;
+  __shared__ AxisPlan Ps;
+  if (threadIdx.x == 0) Ps = P;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = twg[i];
+  const long long c0 = (long long)blockIdx.x * TC;
+  const int ncols = (int)min((long long)TC, g.C - c0);
+  const int tcl = __ffs(TC) - 1;
+  const int c = threadIdx.x & (TC - 1);
+  const long long es = g.C;
+  int kc1, kc2;
+  column_freqs(g, c0 + c, &kc1, &kc2);
+  // load X_0 and Y = k_1 X_1 + k_2 X_2 (columns past a ragged end are zero)
+  for (int j = threadIdx.x >> tcl; j < n; j += blockDim.x >> tcl) {
+    cpx<T> x0 = {0, 0}, y = {0, 0};
+    if (c < ncols) {
+      const cpx<T>* col = S + c0 + c + (long long)j * es;
+      const cpx<T> x1 = col[g.cs], x2 = col[2 * g.cs];
+      x0 = col[0];
+      y.x = (T)kc1 * x1.x + (T)kc2 * x2.x;
+      y.y = (T)kc1 * x1.y + (T)kc2 * x2.y;
+    }
+    sm[bufA + j * TCp + c] = x0;
+    sm[bufA + cstr + j * TCp + c] = y;
+  }
+  __syncthreads();
+  const int nl = 2 * TC;
+  int a = bufA, b = bufB;
+#pragma unroll 1
+  for (int st = 0; st < Ps.nst; ++st) {
+    stage_any<T>(false, &Ps, st, sloc2<T>(a, 1, TCp, cstr, tcl), sloc2<T>(b, 1, TCp, cstr, tcl),
+                 nl, true, 0);
+    __syncthreads();
+    const int t = a;
+    a = b;
+    b = t;
+  }
+  // s = (k_0 v_0 + v_Y) scale / |k|^2 (zero at k = 0 and outside Z_N on a double grid); the
+  // lines become k_0 s and s
+  const T scale = (T)g.scale;
+  for (int j = threadIdx.x >> tcl; j < n; j += blockDim.x >> tcl) {
+    const int k0 = (j <= (n - 1) / 2) ? j : j - n;
+    const bool inside = abs(k0) <= g.hw[0] && abs(kc1) <= g.hw[1] && abs(kc2) <= g.hw[2];
+    const int kk = k0 * k0 + kc1 * kc1 + kc2 * kc2;
+    const T coef = (kk > 0 && inside) ? scale / (T)kk : (T)0;
+    const cpx<T> v0 = sm[a + j * TCp + c], vy = sm[a + cstr + j * TCp + c];
+    cpx<T> sv;
+    sv.x = fma((T)k0, v0.x, vy.x) * coef;
+    sv.y = fma((T)k0, v0.y, vy.y) * coef;
+    sm[a + j * TCp + c] = cpx<T>{(T)k0 * sv.x, (T)k0 * sv.y};
+    sm[a + cstr + j * TCp + c] = sv;
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int st = 0; st < Ps.nst; ++st) {
+    stage_any<T>(true, &Ps, st, sloc2<T>(a, 1, TCp, cstr, tcl), sloc2<T>(b, 1, TCp, cstr, tcl),
+                 nl, true, 0);
+    __syncthreads();
+    const int t = a;
+    a = b;
+    b = t;
+  }
+  // components 0, 1, 2 = F_0^{-1}(k_0 s), k_1 U, k_2 U
+  if (c < ncols)
+    for (int j = threadIdx.x >> tcl; j < n; j += blockDim.x >> tcl) {
+      cpx<T>* col = S + c0 + c + (long long)j * es;
+      const cpx<T> t0 = sm[a + j * TCp + c], u = sm[a + cstr + j * TCp + c];
+      col[0] = t0;
+      col[g.cs] = cpx<T>{(T)kc1 * u.x, (T)kc1 * u.y};
+      col[2 * g.cs] = cpx<T>{(T)kc2 * u.x, (T)kc2 * u.y};
+    }
+}
+
 // Post-operator of the lines l0 .. l0 + LB - 1 after their inverse transform: node j of line
 // l0 + ll is the real (ll even) or imaginary (ll odd) part of shared-memory complex line
 // res + (a * half + ll / 2) * n; the solver's vector update, batches of K nodes whose operands
