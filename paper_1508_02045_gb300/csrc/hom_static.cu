@@ -186,7 +186,8 @@ extern "C" int hom_apply_static(int d, const int* N, const void* phase_dev, int 
   if (rc != HOM_OK) return rc;
 
   // ---- launch geometry (the default budget of hom_create) ----
-  if (!Ops<double>::plan_geometry(d, N, plan, 110 * 1024, &g)) return HOM_ERR_UNSUPPORTED;
+  if (!Ops<double>::plan_geometry(d, N, plan, 110 * 1024, kThreads, &g))
+    return HOM_ERR_UNSUPPORTED;
 
   // ---- twiddles and table into the scratch (ordered on the caller's stream) ----
   cudaStream_t st = (cudaStream_t)stream;

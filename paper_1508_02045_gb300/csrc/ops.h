@@ -21,6 +21,7 @@ struct PassGeom {
   int nh;             // (n[D-1] + 1) / 2
   long long scs;      // spectrum component stride: nlines * nh
   int LB;             // lines per CTA in the line passes (even)
+  int NTl;            // threads per CTA of the runtime-radix line passes (128 or 256)
   int TC1, TC1p, NT1;     // strided pass along axis 1 (D = 3): columns per CTA, padded pitch,
                           // threads per CTA
   int TCs0, TCs0p, NTs0;  // plain strided pass along axis 0 (prolongation, Ga assembly)
@@ -36,9 +37,10 @@ struct Ops {
   static size_t smem_proj(int n, int D, int TCp, int nst);
   static size_t smem_proj_scalar(int n, int TCp);
   // launch geometry of every pass of a grid with axis plans `plan`, keeping each CTA's shared
-  // memory within `budget` bytes; false if a pass cannot fit the device limit
+  // memory within `budget` bytes and its threads within `threads` (<= kThreads); false if a
+  // pass cannot fit the device limit
   static bool plan_geometry(int D, const int* n, const AxisPlan* plan, size_t budget,
-                            PassGeom* g);
+                            int threads, PassGeom* g);
   static cudaError_t prepare(int maxD);  // raise dynamic shared memory limits
 
   // reqs / nreq: optional per-request descriptors of a batched launch (grid.z = nreq); the

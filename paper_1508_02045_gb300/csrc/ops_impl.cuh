@@ -53,7 +53,7 @@ enum ColKind { COL_STRIDED = 0, COL_PROJ = 1, COL_PROJ_SCALAR = 2 };
 
 template <typename T>
 static void pick_cols(const AxisPlan& P, int lines, int tcmax, size_t budget, int kind, int D,
-                      int* TC, int* TCp, int* NT) {
+                      int ncap, int* TC, int* TCp, int* NT) {
   const int m1 = P.n / P.radix[0];
   const int tcmin = std::max(1, 32 / (int)sizeof(cpx<T>));
   auto smem = [&](int t) {
@@ -62,19 +62,21 @@ static void pick_cols(const AxisPlan& P, int lines, int tcmax, size_t budget, in
                                    : Ops<T>::smem_strided(P.n, t + 1, P.nst);
   };
   int tc = tcmax;
-  while (tc > tcmin && ((long long)lines * tc * m1 > kColThreads<T> || smem(tc) > budget)) tc /= 2;
+  while (tc > tcmin && ((long long)lines * tc * m1 > ncap || smem(tc) > budget)) tc /= 2;
   // long axes: narrower tiles rather than none at all
   while (tc > 1 && smem(tc) > (size_t)dynamic_smem_cap()) tc /= 2;
   *TC = tc;
   *TCp = tc + 1;
   const int unit = std::max(32, tc);
   const long long items = (long long)lines * tc * m1;
-  *NT = (int)std::min<long long>(kColThreads<T> / unit * unit, (items + unit - 1) / unit * unit);
+  *NT = (int)std::min<long long>(std::max(ncap / unit, 1) * unit, (items + unit - 1) / unit * unit);
 }
 
 template <typename T>
 bool Ops<T>::plan_geometry(int D, const int* n, const AxisPlan* plan, size_t budget,
-                           PassGeom* g) {
+                           int threads, PassGeom* g) {
+  if (threads < 32 || threads > kColThreads<T> || threads % 32) return false;
+  g->NTl = threads;
   g->D = D;
   g->nodes = 1;
   for (int a = 0; a < D; ++a) {
@@ -88,10 +90,11 @@ bool Ops<T>::plan_geometry(int D, const int* n, const AxisPlan* plan, size_t bud
   g->scs = g->nlines * g->nh;
   g->LB = 16;
   while (g->LB > 2 && smem_line(nl, D, g->LB) > budget) g->LB -= 2;
-  if (D == 3) pick_cols<T>(plan[1], 1, 64, budget, COL_STRIDED, D, &g->TC1, &g->TC1p, &g->NT1);
-  pick_cols<T>(plan[0], D, 32, budget, COL_PROJ, D, &g->TC0, &g->TC0p, &g->NT0);
-  pick_cols<T>(plan[0], 2, 32, budget, COL_PROJ_SCALAR, D, &g->TCq, &g->TCqp, &g->NTq);
-  pick_cols<T>(plan[0], 1, 64, budget, COL_STRIDED, D, &g->TCs0, &g->TCs0p, &g->NTs0);
+  if (D == 3)
+    pick_cols<T>(plan[1], 1, 64, budget, COL_STRIDED, D, threads, &g->TC1, &g->TC1p, &g->NT1);
+  pick_cols<T>(plan[0], D, 32, budget, COL_PROJ, D, threads, &g->TC0, &g->TC0p, &g->NT0);
+  pick_cols<T>(plan[0], 2, 32, budget, COL_PROJ_SCALAR, D, threads, &g->TCq, &g->TCqp, &g->NTq);
+  pick_cols<T>(plan[0], 1, 64, budget, COL_STRIDED, D, threads, &g->TCs0, &g->TCs0p, &g->NTs0);
   // the column kernels address the D component tiles with 32-bit offsets
   if ((long long)D * g->scs >= (1LL << 31)) return false;
   const size_t cap = (size_t)dynamic_smem_cap();
@@ -172,7 +175,7 @@ static void line_fwd_d(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S
   const size_t sm = Ops<T>::smem_line(P.n, ncomp, g.LB);
   const bool prof = profiling();
   if (prof) prof_mark(KIND_LINE_FWD, st, true);
-#define HOM_LF(PRE_) k_line_fwd<T, D, PRE_><<<grid, kThreads, sm, st>>>(f, S, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, reqs)
+#define HOM_LF(PRE_) k_line_fwd<T, D, PRE_><<<grid, g.NTl, sm, st>>>(f, S, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, reqs)
   switch (pre) {
     case PRE_AFFINE: HOM_LF(PRE_AFFINE); break;
     case PRE_LINEAR: HOM_LF(PRE_LINEAR); break;
@@ -284,7 +287,7 @@ static void line_inv_d(const PassGeom& g, int post, const cpx<T>* S, const Field
   const size_t sm = Ops<T>::smem_line(P.n, ncomp, g.LB);
   const bool prof = profiling();
   if (prof) prof_mark(KIND_LINE_INV, st, true);
-#define HOM_LI(POST_) k_line_inv<T, D, POST_><<<grid, kThreads, sm, st>>>(S, f, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, counter, negate, reqs)
+#define HOM_LI(POST_) k_line_inv<T, D, POST_><<<grid, g.NTl, sm, st>>>(S, f, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, counter, negate, reqs)
   switch (post) {
     case POST_RICH: HOM_LI(POST_RICH); break;
     case POST_CG: HOM_LI(POST_CG); break;

@@ -102,15 +102,17 @@ struct Engine {
 
   int rmax_used = 0;
   size_t budget_used = 0;
+  int threads_used = 0;
 
   // plan the axes with register radices <= rmax and tiles within `budget` bytes of shared
-  // memory per CTA; allocates the twiddle tables
-  int init(int D, const int* n, const int* support, size_t budget, int rmax) {
+  // memory and `threads` threads per CTA; allocates the twiddle tables
+  int init(int D, const int* n, const int* support, size_t budget, int rmax, int threads) {
     rmax_used = rmax;
     budget_used = budget;
+    threads_used = threads;
     for (int a = 0; a < D; ++a)
       if (!plan_axis(n[a], rmax, &plan[a])) return HOM_ERR_INVALID;
-    if (!Ops<T>::plan_geometry(D, n, plan, budget, &g)) return HOM_ERR_UNSUPPORTED;
+    if (!Ops<T>::plan_geometry(D, n, plan, budget, threads, &g)) return HOM_ERR_UNSUPPORTED;
     const int nl = n[D - 1];
     g1 = g;
     while (g1.LB < 16 && Ops<T>::smem_line(nl, 1, g1.LB + 2) <= budget) g1.LB += 2;
@@ -213,6 +215,7 @@ struct Engine {
 struct PlanChoice {
   int rmax;
   size_t budget;
+  int threads;  // threads per CTA of the runtime-radix passes
 };
 PlanChoice plan_choice(int precision_bytes, int d, const int* M, const int* N);
 int alloc(void** p, size_t bytes);
