@@ -286,6 +286,18 @@ def pass_flops(rmax):
     }
 
 
+# DRAM bytes (read + write) of one launch of the dominant kernels of the 243^3 CG steps, from
+# one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum on GB300; other kernels and
+# grids have no capture (null)
+NCU_TRAFFIC = {("fp64", "strided"): 649.1e6, ("fp32", "line_fwd"): 644.9e6}
+
+
+def ncu_traffic(precision, kind):
+    if tuple(N_GRID) != (243, 243, 243):
+        return None
+    return NCU_TRAFFIC.get((precision, kind))
+
+
 def pass_bytes(word=8):
     """Compulsory DRAM bytes of one launch of each pass kind in a CG step (word = 8 for FP64,
     4 for FP32); the CG update reads x, p, r, C p and writes x, r."""
@@ -464,7 +476,7 @@ def run_ours(args, rank, world, local):
         "hbm_gbs": round(step_bytes / (ms_step * 1e-3) / 1e9, 1),
         "roofline": {"bound": "alu", "kernel": f"k_{dom}", "achieved": round(achieved, 4),
                      "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                     "traffic": None, "peak_source": "recipe nominal FP64 (1.25 TFLOP/s)",
+                     "traffic": ncu_traffic("fp64", dom), "peak_source": "recipe nominal FP64 (1.25 TFLOP/s)",
                      "hbm_gbs_of_dominant": round(byts[dom] / (dom_ms * 1e-3) / 1e9, 1)},
         "passes": pk,
         "fp32_step": {"metric": "G·A matvecs/s at 243^3 (FP32 CG step, inner solver of the refinement)",
@@ -473,7 +485,8 @@ def run_ours(args, rank, world, local):
                       "plan": {"rmax": tune32["rmax32"], "smem_kb": tune32["smem_kb32"]},
                       "roofline": {"bound": "hbm", "kernel": f"k_{dom32}", "achieved": round(ach32, 1),
                                    "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                                   "frac": round(ach32 / peaks["hbm_gbs"], 4), "traffic": None,
+                                   "frac": round(ach32 / peaks["hbm_gbs"], 4),
+                                   "traffic": ncu_traffic("fp32", dom32),
                                    "peak_source": peaks["source"]},
                       "passes": pk32},
         "clocks": clk,
