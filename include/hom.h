@@ -273,8 +273,9 @@ void hom_server_destroy(hom_server* S);
 
 /* Autotuner of the launch plan (build extension). For the grid of P it times `reps` operator
  * applications (after one warm-up) for every candidate register-radix limit (FP64: 9, 15; FP32:
- * 9, 15, 27), shared-memory tile budget per CTA (56, 110, 150, 200 KiB) and thread count per CTA
- * of the runtime-radix passes (128, 256), re-plans P with the
+ * 9, 15, 27), shared-memory tile budget per CTA (56, 110, 150, 200 KiB), thread count per CTA
+ * of the runtime-radix passes (128, 256) and, in FP32, the two-line chain of the 3-D scalar
+ * projection (on, off) where both column axes have specialised plans, re-plans P with the
  * fastest, and records the choice so that every later hom_create of the same grid, integration
  * support and precision in this process starts with it. Overwrites P's solver vectors (call it
  * before hom_solve_begin; HOM_ERR_INVALID during a session). report (nullable) receives the
@@ -285,6 +286,8 @@ typedef struct {
   int rmax32, smem_kb32;   /* 0 unless P is HOM_FP32_REFINED */
   double ms32;
   int threads64, threads32;/* threads per CTA of the runtime-radix passes (128 or 256) */
+  int two_line32;          /* 1: the FP32 3-D scalar projection keeps two spectrum lines
+                              between its column passes (specialised plans on axes 0 and 1) */
 } hom_tune_report;
 int hom_autotune(hom_problem* P, int reps, hom_tune_report* report);
 

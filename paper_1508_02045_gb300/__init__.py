@@ -77,7 +77,7 @@ class hom_result(ctypes.Structure):
 class hom_tune_report(ctypes.Structure):
     _fields_ = [("rmax64", ctypes.c_int), ("smem_kb64", ctypes.c_int), ("ms64", ctypes.c_double),
                 ("rmax32", ctypes.c_int), ("smem_kb32", ctypes.c_int), ("ms32", ctypes.c_double),
-                ("threads64", ctypes.c_int), ("threads32", ctypes.c_int)]
+                ("threads64", ctypes.c_int), ("threads32", ctypes.c_int), ("two_line32", ctypes.c_int)]
 
 
 def _load():

@@ -153,7 +153,7 @@ PlanChoice plan_choice(int pb, int d, const int* M, const int* N) {
   auto it = tune_table().find(tune_key(pb, d, M, N));
   if (it != tune_table().end()) return it->second;
   // defaults: two CTAs per SM in every pass; FP64 values take twice the registers
-  return PlanChoice{pb == 8 ? 15 : 27, 110 * 1024, kThreads};
+  return PlanChoice{pb == 8 ? 15 : 27, 110 * 1024, kThreads, true};
 }
 
 }  // namespace detail
@@ -392,11 +392,11 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
   // ---- plans ----
   {
     const PlanChoice pc = plan_choice(8, d, P->M, P->N);
-    if ((st = P->e64.init(d, P->M, P->N, pc.budget, pc.rmax, pc.threads)) != HOM_OK) { hom_destroy(P); return st; }
+    if ((st = P->e64.init(d, P->M, P->N, pc.budget, pc.rmax, pc.threads, pc.two_line)) != HOM_OK) { hom_destroy(P); return st; }
   }
   if (precision == HOM_FP32_REFINED) {
     const PlanChoice pc = plan_choice(4, d, P->M, P->N);
-    if ((st = P->e32.init(d, P->M, P->N, pc.budget, pc.rmax, pc.threads)) != HOM_OK) { hom_destroy(P); return st; }
+    if ((st = P->e32.init(d, P->M, P->N, pc.budget, pc.rmax, pc.threads, pc.two_line)) != HOM_OK) { hom_destroy(P); return st; }
   }
 
   // ---- buffers ----
@@ -1038,7 +1038,7 @@ int tune_engine(hom_problem* P, Engine<T>& E, T* x, T* y, int reps, const std::v
   const int d = P->d;
   const size_t cap = (size_t)dynamic_smem_cap();
   double best_t = 1e300;
-  PlanChoice choice{E.rmax_used, E.budget_used, E.threads_used};
+  PlanChoice choice{E.rmax_used, E.budget_used, E.threads_used, E.two_line};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -1049,10 +1049,12 @@ int tune_engine(hom_problem* P, Engine<T>& E, T* x, T* y, int reps, const std::v
   OpArgs args{};
   for (int rmax : rmaxes)
     for (size_t budget : budgets)
-      for (int threads : {kThreads / 2, kThreads}) {
+      for (int threads : {kThreads / 2, kThreads})
+        for (bool two : {true, false}) {
       if (budget > cap) continue;
       E.release_plan();
-      if (E.init(d, P->M, P->N, budget, rmax, threads) != HOM_OK) continue;
+      if (E.init(d, P->M, P->N, budget, rmax, threads, two) != HOM_OK) continue;
+      if (!two && !Ops<T>::two_line_ok(E.g, E.plan[0], E.plan[1])) continue;  // same plan
       E.apply(PRE_LINEAR, PROJ_GAMMA, POST_STORE, f, (cpx<T>*)P->S, nullptr, args, nullptr,
               nullptr, 0, P->stream);  // warm-up
       cudaEventRecord(e0, P->stream);
@@ -1069,13 +1071,14 @@ int tune_engine(hom_problem* P, Engine<T>& E, T* x, T* y, int reps, const std::v
       cudaEventElapsedTime(&ms, e0, e1);
       if (ms < best_t) {
         best_t = ms;
-        choice = PlanChoice{rmax, budget, threads};
+        choice = PlanChoice{rmax, budget, threads, E.two_line};
       }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   E.release_plan();
-  const int rc = E.init(d, P->M, P->N, choice.budget, choice.rmax, choice.threads);
+  const int rc = E.init(d, P->M, P->N, choice.budget, choice.rmax, choice.threads,
+                        choice.two_line);
   *best = choice;
   *best_ms = best_t / reps;
   return rc ? rc : check_last();
@@ -1106,6 +1109,7 @@ extern "C" int hom_autotune(hom_problem* P, int reps, hom_tune_report* report) {
     rep.rmax32 = c.rmax;
     rep.smem_kb32 = (int)(c.budget / 1024);
     rep.threads32 = c.threads;
+    rep.two_line32 = c.two_line ? 1 : 0;
     rep.ms32 = ms;
     std::lock_guard<std::mutex> lk(tune_mu());
     tune_table()[tune_key(4, P->d, P->M, P->N)] = c;

@@ -487,11 +487,11 @@ int admit(hom_server* S) {
       b.red_grid = P->red_grid;
       b.e64 = new Engine<double>();
       if ((rc = b.e64->init(b.d, P->M, P->N, P->e64.budget_used, P->e64.rmax_used,
-                                 P->e64.threads_used))) return rc;
+                                 P->e64.threads_used, P->e64.two_line))) return rc;
       if (b.precision == HOM_FP32_REFINED) {
         b.e32 = new Engine<float>();
         if ((rc = b.e32->init(b.d, P->M, P->N, P->e32.budget_used, P->e32.rmax_used,
-                                   P->e32.threads_used))) return rc;
+                                   P->e32.threads_used, P->e32.two_line))) return rc;
       }
       S->buckets.push_back(b);
       bi = (int)S->buckets.size() - 1;

@@ -56,6 +56,17 @@ struct Ops {
   static void proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, const cpx<T>* tw,
                    const ProjGeom& pg, const Scalars* sc, cudaStream_t st,
                    const ReqDesc<T>* reqs = nullptr, int nreq = 1);
+  // The 3-D scalar projection (PROJ_GAMMA) with two spectrum lines between the column passes
+  // when both column axes have compile-time FP32 plans: axis-1 forward writes X_0 and
+  // Y = k_1 X_1 + k_2 X_2, the projection reads and writes two lines, axis-1 inverse expands
+  // them to three components. two_line_ok says whether the chain applies.
+  static bool two_line_ok(const PassGeom& g, const AxisPlan& P0, const AxisPlan& P1);
+  static void strided_two_line(const PassGeom& g, int inv, cpx<T>* S, const AxisPlan& P,
+                               const cpx<T>* tw, const Scalars* sc, cudaStream_t st,
+                               const ReqDesc<T>* reqs = nullptr, int nreq = 1);
+  static void proj_two_line(const PassGeom& g, cpx<T>* S, const AxisPlan& P, const cpx<T>* tw,
+                            const ProjGeom& pg, const Scalars* sc, cudaStream_t st,
+                            const ReqDesc<T>* reqs = nullptr, int nreq = 1);
   static void line_inv(const PassGeom& g, int post, const cpx<T>* S, const Fields<T>& f,
                        const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
                        Scalars* sc, const OpArgs& args, double* partials, unsigned* counter,
@@ -84,9 +95,13 @@ cudaError_t pair_prepare_f32(int smem_cap);
 void pair_strided_f32(const AxisPlan& P, int inv, cpx<float>* S, const cpx<float>* tw,
                       long long C, long long es, long long bs, int batches, const Scalars* sc,
                       cudaStream_t st, const ReqDesc<float>* reqs, int nreq);
-void pair_proj_f32(int D, int mode, const AxisPlan& P, cpx<float>* S, const cpx<float>* tw,
-                   const ProjGeom& pg, const Scalars* sc, cudaStream_t st,
+void pair_proj_f32(int D, int mode, bool two, const AxisPlan& P, cpx<float>* S,
+                   const cpx<float>* tw, const ProjGeom& pg, const Scalars* sc, cudaStream_t st,
                    const ReqDesc<float>* reqs, int nreq);
+// axis-1 pass of components 1 and 2 in the two-line chain of the 3-D scalar projection
+void pair_strided2_f32(const AxisPlan& P, int inv, cpx<float>* S, const cpx<float>* tw,
+                       long long C, long long es, long long bs, long long cs, int planes,
+                       const Scalars* sc, cudaStream_t st, const ReqDesc<float>* reqs, int nreq);
 // the line passes are specialised for D = 3 and the pre-/post-operators of the FP32 inner
 // solves (CG, Chebyshev) and of plain operator applications
 inline bool pair_line_fwd_has(int D, int pre) {

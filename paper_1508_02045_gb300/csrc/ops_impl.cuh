@@ -252,7 +252,7 @@ void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, con
   if (prof) prof_mark(KIND_PROJ, st, true);
   if (pair_plan<T>(P)) {
     if constexpr (std::is_same<T, float>::value)
-      pair_proj_f32(g.D, mode, P, S, tw, pg, sc, st, reqs, nreq);
+      pair_proj_f32(g.D, mode, false, P, S, tw, pg, sc, st, reqs, nreq);
     if (prof) prof_mark(KIND_PROJ, st, false);
     ++launch_counter();
     return;
@@ -276,6 +276,41 @@ void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, con
 #undef HOM_PJ
   if (prof) prof_mark(KIND_PROJ, st, false);
   ++launch_counter();
+}
+
+template <typename T>
+bool Ops<T>::two_line_ok(const PassGeom& g, const AxisPlan& P0, const AxisPlan& P1) {
+  return std::is_same<T, float>::value && g.D == 3 && pair_plan<T>(P0) && pair_plan<T>(P1);
+}
+
+// axis-1 pass of the two-line chain: component 0 by the plain pass over its n0 planes,
+// components 1 and 2 together (one profiled pass)
+template <typename T>
+void Ops<T>::strided_two_line(const PassGeom& g, int inv, cpx<T>* S, const AxisPlan& P,
+                              const cpx<T>* tw, const Scalars* sc, cudaStream_t st,
+                              const ReqDesc<T>* reqs, int nreq) {
+  if constexpr (std::is_same<T, float>::value) {
+    const bool prof = profiling();
+    if (prof) prof_mark(KIND_STRIDED, st, true);
+    const long long C = g.nh, es = g.nh, bs = (long long)g.n[1] * g.nh;
+    pair_strided_f32(P, inv, S, tw, C, es, bs, g.n[0], sc, st, reqs, nreq);
+    pair_strided2_f32(P, inv, S, tw, C, es, bs, g.scs, g.n[0], sc, st, reqs, nreq);
+    if (prof) prof_mark(KIND_STRIDED, st, false);
+    launch_counter() += 2;
+  }
+}
+
+template <typename T>
+void Ops<T>::proj_two_line(const PassGeom& g, cpx<T>* S, const AxisPlan& P, const cpx<T>* tw,
+                           const ProjGeom& pg, const Scalars* sc, cudaStream_t st,
+                           const ReqDesc<T>* reqs, int nreq) {
+  if constexpr (std::is_same<T, float>::value) {
+    const bool prof = profiling();
+    if (prof) prof_mark(KIND_PROJ, st, true);
+    pair_proj_f32(g.D, PROJ_GAMMA, true, P, S, tw, pg, sc, st, reqs, nreq);
+    if (prof) prof_mark(KIND_PROJ, st, false);
+    ++launch_counter();
+  }
 }
 
 template <typename T, int D>

@@ -35,7 +35,10 @@ cudaError_t pair_prepare_f32(int cap) {
   HOM_SET_SMEM((k_pair_proj<T, 2, PROJ_EM, R1_, R2_>));         \
   HOM_SET_SMEM((k_pair_proj<T, 3, PROJ_GAMMA, R1_, R2_>));      \
   HOM_SET_SMEM((k_pair_proj<T, 3, PROJ_EM, R1_, R2_>));         \
-  HOM_SET_SMEM((k_pair_proj_scalar<T, R1_, R2_>));              \
+  HOM_SET_SMEM((k_pair_proj_scalar<T, R1_, R2_, false>));       \
+  HOM_SET_SMEM((k_pair_proj_scalar<T, R1_, R2_, true>));        \
+  HOM_SET_SMEM((k_pair_strided2<T, R1_, R2_, false>));          \
+  HOM_SET_SMEM((k_pair_strided2<T, R1_, R2_, true>));           \
   HOM_SET_SMEM((k_pair_line_fwd<T, 3, PRE_CG, R1_, R2_>));      \
   HOM_SET_SMEM((k_pair_line_fwd<T, 3, PRE_LINEAR, R1_, R2_>));  \
   HOM_SET_SMEM((k_pair_line_inv<T, 3, POST_CG, R1_, R2_>));     \
@@ -65,8 +68,27 @@ void pair_strided_f32(const AxisPlan& P, int inv, cpx<float>* S, const cpx<float
 #undef HOM_PAIR_ST
 }
 
-void pair_proj_f32(int D, int mode, const AxisPlan& P, cpx<float>* S, const cpx<float>* tw,
-                   const ProjGeom& pg, const Scalars* sc, cudaStream_t st,
+void pair_strided2_f32(const AxisPlan& P, int inv, cpx<float>* S, const cpx<float>* tw,
+                       long long C, long long es, long long bs, long long cs, int planes,
+                       const Scalars* sc, cudaStream_t st, const ReqDesc<float>* reqs, int nreq) {
+  using T = float;
+#define HOM_PAIR_ST2(R1_, R2_)                                                                 \
+  if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
+    constexpr int TC = pair_tc_strided<R2_>();                                                 \
+    const dim3 grid((unsigned)((C + TC - 1) / TC), (unsigned)planes, (unsigned)nreq);         \
+    const size_t sm = sizeof(cpx<T>) * (size_t)(R1_ * R2_) * (1 + 2 * (TC + 1));               \
+    if (inv)                                                                                   \
+      k_pair_strided2<T, R1_, R2_, true><<<grid, 2 * TC * R2_, sm, st>>>(S, tw, C, es, bs, cs, sc, reqs); \
+    else                                                                                       \
+      k_pair_strided2<T, R1_, R2_, false><<<grid, 2 * TC * R2_, sm, st>>>(S, tw, C, es, bs, cs, sc, reqs); \
+    return;                                                                                    \
+  }
+  HOM_PAIR_PLANS(HOM_PAIR_ST2)
+#undef HOM_PAIR_ST2
+}
+
+void pair_proj_f32(int D, int mode, bool two, const AxisPlan& P, cpx<float>* S,
+                   const cpx<float>* tw, const ProjGeom& pg, const Scalars* sc, cudaStream_t st,
                    const ReqDesc<float>* reqs, int nreq) {
   using T = float;
 #define HOM_PAIR_PJ_D(D_, R1_, R2_)                                                            \
@@ -87,7 +109,10 @@ void pair_proj_f32(int D, int mode, const AxisPlan& P, cpx<float>* S, const cpx<
       constexpr int TC = pair_tc_proj_scalar<R2_>();                                           \
       const dim3 grid((unsigned)((pg.C + TC - 1) / TC), 1, (unsigned)nreq);                   \
       const size_t sm = sizeof(cpx<T>) * ((size_t)(R1_ * R2_) * (1 + 2 * (TC + 1)));           \
-      k_pair_proj_scalar<T, R1_, R2_><<<grid, 2 * TC * R2_, sm, st>>>(S, tw, pg, sc, reqs);    \
+      if (two)                                                                                 \
+        k_pair_proj_scalar<T, R1_, R2_, true><<<grid, 2 * TC * R2_, sm, st>>>(S, tw, pg, sc, reqs); \
+      else                                                                                     \
+        k_pair_proj_scalar<T, R1_, R2_, false><<<grid, 2 * TC * R2_, sm, st>>>(S, tw, pg, sc, reqs); \
     } else {                                                                                   \
       HOM_PAIR_PJ_D(3, R1_, R2_)                                                               \
     }                                                                                          \

@@ -119,6 +119,80 @@ k_pair_strided(cpx<T>* S, const cpx<T>* __restrict__ twg, long long C, long long
 }
 
 // ---------------------------------------------------------------------------------------
+// axis-1 pass of components 1 and 2 in the two-line chain of the 3-D scalar projection
+// (blockIdx.x = column tile, blockIdx.y = plane i0, blockIdx.z = request; 2 * TC * R2 threads).
+// k_1 is the axis-1 frequency of a row, k_2 = the column index (the half axis).
+//   forward: component 1 <- Y = k_1 F_1[X_1] + k_2 F_1[X_2] (only Y reaches the projection)
+//   inverse: component 1 <- F_1^{-1}[k_1 U], component 2 <- k_2 F_1^{-1}[U], U read from
+//            component 1 (the projection left U = F_0^{-1} s there)
+// ---------------------------------------------------------------------------------------
+template <typename T, int R1, int R2, bool INV>
+__global__ void __launch_bounds__(2 * pair_tc_strided<R2>() * R2)
+k_pair_strided2(cpx<T>* S, const cpx<T>* __restrict__ twg, long long C, long long es,
+                long long bs, long long cs, const Scalars* sc,
+                const ReqDesc<T>* __restrict__ reqs) {
+  constexpr int n = R1 * R2, TC = pair_tc_strided<R2>(), TCp = TC + 1, NT = 2 * TC * R2;
+  constexpr int tstr = n * TCp;
+  if (reqs != nullptr) {
+    S = reqs[blockIdx.z].S;
+    sc = reqs[blockIdx.z].sc;
+  }
+  if (sc != nullptr && sc->done) return;
+  cpx<T>* sm = smem_c<T>();
+  cpx<T>* tw = sm;
+  cpx<T>* A = sm + n;  // tile t (0, 1) of column c at A + t * tstr + c (row stride TCp)
+  for (int i = threadIdx.x; i < n; i += NT) tw[i] = twg[i];
+  const long long c0 = (long long)blockIdx.x * TC;
+  const int ncols = (int)min((long long)TC, C - c0);
+  cpx<T>* base = S + cs + (long long)blockIdx.y * bs + c0;  // component 1, plane i0
+  {
+    const int c = threadIdx.x % TC, i = (threadIdx.x / TC) % R2, t = threadIdx.x / (TC * R2);
+    if (c < ncols) {
+      const cpx<T>* src = base + c + (INV ? 0 : t * cs);
+      cpx<T> u[R1];
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        u[r] = src[(long long)(i + r * R2) * es];
+        if (INV) {
+          u[r].y = -u[r].y;
+          if (t == 0) {  // k_1 U: the row is the axis-1 frequency
+            const int j = i + r * R2;
+            const T k1 = (T)(j <= (n - 1) / 2 ? j : j - n);
+            u[r].x *= k1;
+            u[r].y *= k1;
+          }
+        }
+      }
+      RegDft<T, R1>::run(u);
+      cpx<T>* dst = A + t * tstr + c;
+#pragma unroll
+      for (int r = 0; r < R1; ++r) dst[(i * R1 + r) * TCp] = u[r];
+    }
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < TC * R1; w += NT) {
+    const int c = w % TC, i = w / TC;
+    if (c >= ncols) continue;
+    cpx<T> u0[R2], u1[R2];
+    pair_stage2_regs<T, R1, R2>(A + c, tw, TCp, i, u0);
+    pair_stage2_regs<T, R1, R2>(A + tstr + c, tw, TCp, i, u1);
+    const T k2 = (T)(c0 + c);
+#pragma unroll
+    for (int r = 0; r < R2; ++r) {
+      const int j = i + r * R1;
+      cpx<T>* e = base + (long long)j * es + c;
+      if (!INV) {
+        const T k1 = (T)(j <= (n - 1) / 2 ? j : j - n);
+        e[0] = cpx<T>{fma(k1, u0[r].x, k2 * u1[r].x), fma(k1, u0[r].y, k2 * u1[r].y)};
+      } else {
+        e[0] = cpx<T>{u0[r].x, -u0[r].y};
+        e[cs] = cpx<T>{k2 * u1[r].x, -k2 * u1[r].y};
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // projection pass: forward DFT of axis 0, Gamma^ (or I - 2 Gamma^), inverse DFT of axis 0, on
 // a tile of TC columns of all D components; D * TC * R2 threads. One shared-memory tile per
 // component: forward stage 2 and the projection write back the rows they read, and the
@@ -241,7 +315,9 @@ __host__ __device__ constexpr int pair_tc_proj_scalar() {
   return 2 * 32 * R2 <= 320 ? 32 : 2 * 16 * R2 <= 320 ? 16 : 2 * 8 * R2 <= 320 ? 8 : 4;
 }
 
-template <typename T, int R1, int R2>
+// TWO: the two-line chain (k_pair_strided2 on both sides): line 1 is read as Y from component 1
+// and U is written back to component 1 alone
+template <typename T, int R1, int R2, bool TWO>
 __global__ void __launch_bounds__(2 * pair_tc_proj_scalar<R2>() * R2)
 k_pair_proj_scalar(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, const Scalars* sc,
                    const ReqDesc<T>* __restrict__ reqs) {
@@ -267,9 +343,10 @@ k_pair_proj_scalar(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, const 
     cpx<T> u[R1];
     const cpx<T>* col = S + c0 + c1;
     if (c1 < ncols) {
-      if (t1 == 0) {
+      if (t1 == 0 || TWO) {
+        const cpx<T>* src = col + (t1 == 0 ? 0 : g.cs);
 #pragma unroll
-        for (int r = 0; r < R1; ++r) u[r] = col[(long long)(i1 + r * R2) * es];
+        for (int r = 0; r < R1; ++r) u[r] = src[(long long)(i1 + r * R2) * es];
       } else {
 #pragma unroll
         for (int r = 0; r < R1; ++r) {
@@ -331,9 +408,10 @@ k_pair_proj_scalar(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, const 
     cpx<T> u[R2];
     pair_stage2_regs<T, R1, R2>(A + t * cstr + c, tw, TCp, i, u);
     cpx<T>* out = S + c0 + c;
-    if (t == 0) {
+    if (t == 0 || TWO) {
+      cpx<T>* dst = out + (t == 0 ? 0 : g.cs);
 #pragma unroll
-      for (int r = 0; r < R2; ++r) out[(long long)(i + r * R1) * es] = cpx<T>{u[r].x, -u[r].y};
+      for (int r = 0; r < R2; ++r) dst[(long long)(i + r * R1) * es] = cpx<T>{u[r].x, -u[r].y};
     } else {
       int kc1, kc2;
       column_freqs(g, c0 + c, &kc1, &kc2);

@@ -103,16 +103,19 @@ struct Engine {
   int rmax_used = 0;
   size_t budget_used = 0;
   int threads_used = 0;
+  bool two_line = false;  // the 3-D scalar projection runs the two-line chain (FP32 plans)
 
   // plan the axes with register radices <= rmax and tiles within `budget` bytes of shared
   // memory and `threads` threads per CTA; allocates the twiddle tables
-  int init(int D, const int* n, const int* support, size_t budget, int rmax, int threads) {
+  int init(int D, const int* n, const int* support, size_t budget, int rmax, int threads,
+           bool allow_two_line = true) {
     rmax_used = rmax;
     budget_used = budget;
     threads_used = threads;
     for (int a = 0; a < D; ++a)
       if (!plan_axis(n[a], rmax, &plan[a])) return HOM_ERR_INVALID;
     if (!Ops<T>::plan_geometry(D, n, plan, budget, threads, &g)) return HOM_ERR_UNSUPPORTED;
+    two_line = allow_two_line && Ops<T>::two_line_ok(g, plan[0], plan[1]);
     const int nl = n[D - 1];
     g1 = g;
     while (g1.LB < 16 && Ops<T>::smem_line(nl, 1, g1.LB + 2) <= budget) g1.LB += 2;
@@ -162,9 +165,15 @@ struct Engine {
               Scalars* sc, const OpArgs& args, double* partials, unsigned* counter, int negate,
               cudaStream_t st) const {
     Ops<T>::line_fwd(g, pre, ff, S, plan[g.D - 1], tw[g.D - 1], g.D, mat, sc, args, st);
-    if (g.D == 3) Ops<T>::strided(g, 1, 0, S, plan[1], tw[1], g.D, sc, st);
-    Ops<T>::proj(g, mode, S, plan[0], tw[0], pg, sc, st);
-    if (g.D == 3) Ops<T>::strided(g, 1, 1, S, plan[1], tw[1], g.D, sc, st);
+    if (mode == PROJ_GAMMA && two_line) {
+      Ops<T>::strided_two_line(g, 0, S, plan[1], tw[1], sc, st);
+      Ops<T>::proj_two_line(g, S, plan[0], tw[0], pg, sc, st);
+      Ops<T>::strided_two_line(g, 1, S, plan[1], tw[1], sc, st);
+    } else {
+      if (g.D == 3) Ops<T>::strided(g, 1, 0, S, plan[1], tw[1], g.D, sc, st);
+      Ops<T>::proj(g, mode, S, plan[0], tw[0], pg, sc, st);
+      if (g.D == 3) Ops<T>::strided(g, 1, 1, S, plan[1], tw[1], g.D, sc, st);
+    }
     Ops<T>::line_inv(g, post, S, fi, plan[g.D - 1], tw[g.D - 1], g.D, mat, sc, args, partials,
                      counter, negate, st);
   }
@@ -177,9 +186,15 @@ struct Engine {
     OpArgs args{};
     Ops<T>::line_fwd(g, pre, f, nullptr, plan[g.D - 1], tw[g.D - 1], g.D, mat, nullptr, args, st,
                      reqs, n);
-    if (g.D == 3) Ops<T>::strided(g, 1, 0, nullptr, plan[1], tw[1], g.D, nullptr, st, reqs, n);
-    Ops<T>::proj(g, mode, nullptr, plan[0], tw[0], pg, nullptr, st, reqs, n);
-    if (g.D == 3) Ops<T>::strided(g, 1, 1, nullptr, plan[1], tw[1], g.D, nullptr, st, reqs, n);
+    if (mode == PROJ_GAMMA && two_line) {
+      Ops<T>::strided_two_line(g, 0, nullptr, plan[1], tw[1], nullptr, st, reqs, n);
+      Ops<T>::proj_two_line(g, nullptr, plan[0], tw[0], pg, nullptr, st, reqs, n);
+      Ops<T>::strided_two_line(g, 1, nullptr, plan[1], tw[1], nullptr, st, reqs, n);
+    } else {
+      if (g.D == 3) Ops<T>::strided(g, 1, 0, nullptr, plan[1], tw[1], g.D, nullptr, st, reqs, n);
+      Ops<T>::proj(g, mode, nullptr, plan[0], tw[0], pg, nullptr, st, reqs, n);
+      if (g.D == 3) Ops<T>::strided(g, 1, 1, nullptr, plan[1], tw[1], g.D, nullptr, st, reqs, n);
+    }
     Ops<T>::line_inv(g, post, nullptr, f, plan[g.D - 1], tw[g.D - 1], g.D, mat, nullptr, args,
                      nullptr, nullptr, 0, st, reqs, n);
   }
@@ -215,7 +230,8 @@ struct Engine {
 struct PlanChoice {
   int rmax;
   size_t budget;
-  int threads;  // threads per CTA of the runtime-radix passes
+  int threads;    // threads per CTA of the runtime-radix passes
+  bool two_line;  // FP32 3-D scalar projection: two-line chain where the plans allow it
 };
 PlanChoice plan_choice(int precision_bytes, int d, const int* M, const int* N);
 int alloc(void** p, size_t bytes);

@@ -51,11 +51,13 @@ def test_fp32_operator_parity(N):
 # along axis 0 (projection pass) and along axis 1 (strided pass), with ragged column tiles
 TWO_STAGE_GRIDS = [(243, 7, 5), (5, 243, 3), (405, 3, 3), (3, 405, 5), (81, 9, 5), (7, 81, 9),
                    (135, 5, 3), (3, 135, 7), (45, 11, 3), (161, 3, 5), (3, 161, 3), (63, 5, 3),
-                   (3, 63, 7), (189, 3, 3), (5, 189, 3), (175, 3, 5), (3, 175, 3), (243, 7)]
+                   (3, 63, 7), (189, 3, 3), (5, 189, 3), (175, 3, 5), (3, 175, 3), (243, 7),
+                   # both column axes specialised: the scalar projection's two-line chain
+                   (63, 45, 5), (45, 243, 3), (243, 45, 3), (135, 81, 7), (175, 161, 3)]
 
 
 @pytest.mark.parametrize("N", TWO_STAGE_GRIDS)
-@pytest.mark.parametrize("op", ["linear", "em"])
+@pytest.mark.parametrize("op", ["linear", "em", "project"])
 def test_fp32_two_stage_plans(N, op):
     d = len(N)
     ph = ms.box_phase(N, 0.6)
@@ -64,16 +66,21 @@ def test_fp32_two_stage_plans(N, op):
     P = H.Problem(d, N, H.phase_material(ph, table), precision=H.HOM_FP32_REFINED)
     x = ms.random_field((d,) + N, 5)
     y = P.field()
-    opc = H.HOM_OP_LINEAR if op == "linear" else H.HOM_OP_EM
+    opc = {"linear": H.HOM_OP_LINEAR, "em": H.HOM_OP_EM, "project": H.HOM_OP_PROJECT}[op]
     H.hom_apply(P.h, opc | H.HOM_OP_FP32, None, torch.from_numpy(x).cuda(), y)
     sysn = O.GaNi(A, d)
-    ref = sysn.matvec(x) if op == "linear" else sysn.em_project(O.apply_A(A, x) - np.sqrt(10.0) * x)
+    if op == "linear":
+        ref = sysn.matvec(x)
+    elif op == "em":
+        ref = sysn.em_project(O.apply_A(A, x) - np.sqrt(10.0) * x)
+    else:
+        ref = O.project(x)
     err = rel(y.cpu().numpy(), ref)
     assert err < 2e-6, err
     P.close()
 
 
-@pytest.mark.parametrize("N", [(81, 5, 3), (3, 81, 5)])
+@pytest.mark.parametrize("N", [(81, 5, 3), (3, 81, 5), (81, 81, 3)])
 def test_fp32_two_stage_plans_exact_integration(N):
     # double grid 2N - 1 = 161: the truncation to Z_N runs inside the specialised projection
     d = len(N)
