@@ -91,8 +91,13 @@ struct Scalars {
   int result;         // Richardson: buffer holding the returned iterate
 };
 
-enum PreOp { PRE_AFFINE = 0, PRE_LINEAR = 1, PRE_CG = 2, PRE_EM = 3, PRE_IDENT = 4 };
-enum PostOp { POST_STORE = 0, POST_RICH = 1, POST_CG = 2, POST_CHEB = 3, POST_EM = 4, POST_ADD = 5 };
+// PRE_CG_DOT / POST_CG_FUSED: the CG step of the FP32 inner solves with the vector update
+// fused into the operator passes. In exact arithmetic (p, G A p) = (p, A p) for p in the range
+// of the orthogonal projection G (every CG direction is), so (p, C p) and alpha come from the
+// pre-operator pass and the inverse pass can update x and r and form (r, r) itself.
+enum PreOp { PRE_AFFINE = 0, PRE_LINEAR = 1, PRE_CG = 2, PRE_EM = 3, PRE_IDENT = 4, PRE_CG_DOT = 5 };
+enum PostOp { POST_STORE = 0, POST_RICH = 1, POST_CG = 2, POST_CHEB = 3, POST_EM = 4, POST_ADD = 5,
+              POST_CG_FUSED = 6 };
 enum ProjMode { PROJ_GAMMA = 0, PROJ_EM = 1 };
 enum MatKind { MAT_PHASE_ISO = 0, MAT_PHASE_TENSOR = 1, MAT_FIELD = 2 };
 

@@ -689,18 +689,19 @@ void refine_enqueue_inner(hom_problem* P) {
   float* x = P->fvec[0];
   float* r = P->fvec[1];
   float* p = P->fvec[2];
-  float* q = P->fvec[3];
   OpArgs args{};
   Fields<float> f{};
   f.cs = nodes;
   if (P->sv.solver == HOM_CG) {
+    // the CG step with the vector update fused into the operator passes (PRE_CG_DOT computes
+    // (p, A p) and alpha, POST_CG_FUSED updates x and r and forms (r, r) and beta)
     f.xin = r;
     f.p = p;
-    f.out = q;
-    P->e32.apply(PRE_CG, PROJ_GAMMA, POST_CG, f, S, P->d_sc2, args, P->partials, P->counter, 0,
-                 P->stream);
-    Ops<float>::cg_update(x, r, p, q, (long long)P->d * nodes, nodes, P->d_sc2, P->partials,
-                          P->counter, P->red_grid, P->stream);
+    Fields<float> fi = f;
+    fi.x = x;
+    fi.r = r;
+    P->e32.apply2(PRE_CG_DOT, PROJ_GAMMA, POST_CG_FUSED, f, fi, S, P->d_sc2, args, P->partials,
+                  P->counter, 0, P->stream);
   } else {
     f.xin = p;
     Fields<float> fi = f;

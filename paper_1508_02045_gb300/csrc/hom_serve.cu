@@ -11,6 +11,7 @@
 #include <map>
 #include <memory>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "problem.h"
@@ -110,9 +111,13 @@ void batch_step(const Engine<T>& E, int solver, const ReqDesc<T>* reqs, int n, i
       E.apply_batch(PRE_AFFINE, PROJ_GAMMA, POST_RICH, reqs, n, st);
       break;
     case HOM_CG:
-      E.apply_batch(PRE_CG, PROJ_GAMMA, POST_CG, reqs, n, st);
-      Ops<T>::cg_update(nullptr, nullptr, nullptr, nullptr, (long long)d * nodes, nodes, nullptr,
-                        nullptr, nullptr, red_grid, st, reqs, n);
+      if (std::is_same<T, float>::value) {  // FP32 inner step: the fused form of hom_solve
+        E.apply_batch(PRE_CG_DOT, PROJ_GAMMA, POST_CG_FUSED, reqs, n, st);
+      } else {
+        E.apply_batch(PRE_CG, PROJ_GAMMA, POST_CG, reqs, n, st);
+        Ops<T>::cg_update(nullptr, nullptr, nullptr, nullptr, (long long)d * nodes, nodes, nullptr,
+                          nullptr, nullptr, red_grid, st, reqs, n);
+      }
       break;
     case HOM_CHEBYSHEV:
       E.apply_batch(PRE_LINEAR, PROJ_GAMMA, POST_CHEB, reqs, n, st);

@@ -45,10 +45,12 @@ struct Ops {
 
   // reqs / nreq: optional per-request descriptors of a batched launch (grid.z = nreq); the
   // direct arguments are then ignored where a descriptor provides them
+  // partials / counter: the grid reduction of PRE_CG_DOT (unused by the other pre-operators)
   static void line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
                        const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
-                       const Scalars* sc, const OpArgs& args, cudaStream_t st,
-                       const ReqDesc<T>* reqs = nullptr, int nreq = 1);
+                       Scalars* sc, const OpArgs& args, cudaStream_t st,
+                       const ReqDesc<T>* reqs = nullptr, int nreq = 1,
+                       double* partials = nullptr, unsigned* counter = nullptr);
   // strided DFT along axis 1 (D = 3) or axis 0 (no projection) of ncomp components
   static void strided(const PassGeom& g, int axis, int inv, cpx<T>* S, const AxisPlan& P,
                       const cpx<T>* tw, int ncomp, const Scalars* sc, cudaStream_t st,
@@ -105,15 +107,17 @@ void pair_strided2_f32(const AxisPlan& P, int inv, cpx<float>* S, const cpx<floa
 // the line passes are specialised for D = 3 and the pre-/post-operators of the FP32 inner
 // solves (CG, Chebyshev) and of plain operator applications
 inline bool pair_line_fwd_has(int D, int pre) {
-  return D == 3 && (pre == PRE_CG || pre == PRE_LINEAR);
+  return D == 3 && (pre == PRE_CG || pre == PRE_CG_DOT || pre == PRE_LINEAR);
 }
 inline bool pair_line_inv_has(int D, int post) {
-  return D == 3 && (post == POST_CG || post == POST_CHEB || post == POST_STORE);
+  return D == 3 && (post == POST_CG || post == POST_CG_FUSED || post == POST_CHEB ||
+                    post == POST_STORE);
 }
 void pair_line_fwd_f32(int D, int pre, const AxisPlan& P, const Fields<float>& f, cpx<float>* S,
                        const cpx<float>* tw, long long nlines, long long scs,
-                       const MatView<float>& mat, const Scalars* sc, const OpArgs& args,
-                       cudaStream_t st, const ReqDesc<float>* reqs, int nreq);
+                       const MatView<float>& mat, Scalars* sc, const OpArgs& args,
+                       double* partials, unsigned* counter, cudaStream_t st,
+                       const ReqDesc<float>* reqs, int nreq);
 void pair_line_inv_f32(int D, int post, const AxisPlan& P, const cpx<float>* S,
                        const Fields<float>& f, const cpx<float>* tw, long long nlines,
                        long long scs, const MatView<float>& mat, Scalars* sc, const OpArgs& args,

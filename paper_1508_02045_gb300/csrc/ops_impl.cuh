@@ -162,24 +162,33 @@ cudaError_t Ops<T>::prepare(int) {
   HOM_SET_SMEM((k_line_inv<T, 3, POST_CG>));
   HOM_SET_SMEM((k_line_inv<T, 3, POST_CHEB>));
   HOM_SET_SMEM((k_line_inv<T, 3, POST_EM>));
-  if constexpr (std::is_same<T, float>::value) return pair_prepare_f32(cap);
+  if constexpr (std::is_same<T, float>::value) {
+    HOM_SET_SMEM((k_line_fwd<T, 2, PRE_CG_DOT>));
+    HOM_SET_SMEM((k_line_fwd<T, 3, PRE_CG_DOT>));
+    HOM_SET_SMEM((k_line_inv<T, 2, POST_CG_FUSED>));
+    HOM_SET_SMEM((k_line_inv<T, 3, POST_CG_FUSED>));
+    return pair_prepare_f32(cap);
+  }
   return cudaSuccess;
 }
 
 template <typename T, int D>
 static void line_fwd_d(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
                        const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
-                       const Scalars* sc, const OpArgs& args, cudaStream_t st,
-                       const ReqDesc<T>* reqs, int nreq) {
+                       Scalars* sc, const OpArgs& args, cudaStream_t st,
+                       const ReqDesc<T>* reqs, int nreq, double* partials, unsigned* counter) {
   const dim3 grid((unsigned)((g.nlines + g.LB - 1) / g.LB), 1, (unsigned)nreq);
   const size_t sm = Ops<T>::smem_line(P.n, ncomp, g.LB);
   const bool prof = profiling();
   if (prof) prof_mark(KIND_LINE_FWD, st, true);
-#define HOM_LF(PRE_) k_line_fwd<T, D, PRE_><<<grid, g.NTl, sm, st>>>(f, S, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, reqs)
+#define HOM_LF(PRE_) k_line_fwd<T, D, PRE_><<<grid, g.NTl, sm, st>>>(f, S, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, counter, reqs)
   switch (pre) {
     case PRE_AFFINE: HOM_LF(PRE_AFFINE); break;
     case PRE_LINEAR: HOM_LF(PRE_LINEAR); break;
     case PRE_CG: HOM_LF(PRE_CG); break;
+    case PRE_CG_DOT:
+      if constexpr (std::is_same<T, float>::value) HOM_LF(PRE_CG_DOT);
+      break;
     case PRE_EM: HOM_LF(PRE_EM); break;
     default: HOM_LF(PRE_IDENT); break;
   }
@@ -191,20 +200,23 @@ static void line_fwd_d(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S
 template <typename T>
 void Ops<T>::line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
                       const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
-                      const Scalars* sc, const OpArgs& args, cudaStream_t st,
-                      const ReqDesc<T>* reqs, int nreq) {
+                      Scalars* sc, const OpArgs& args, cudaStream_t st,
+                      const ReqDesc<T>* reqs, int nreq, double* partials, unsigned* counter) {
   if constexpr (std::is_same<T, float>::value) {
     if (ncomp == g.D && pair_line_fwd_has(g.D, pre) && pair_plan<T>(P)) {
       const bool prof = profiling();
       if (prof) prof_mark(KIND_LINE_FWD, st, true);
-      pair_line_fwd_f32(g.D, pre, P, f, S, tw, g.nlines, g.scs, mat, sc, args, st, reqs, nreq);
+      pair_line_fwd_f32(g.D, pre, P, f, S, tw, g.nlines, g.scs, mat, sc, args, partials, counter,
+                        st, reqs, nreq);
       if (prof) prof_mark(KIND_LINE_FWD, st, false);
       ++launch_counter();
       return;
     }
   }
-  if (g.D == 2) line_fwd_d<T, 2>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq);
-  else line_fwd_d<T, 3>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq);
+  if (g.D == 2)
+    line_fwd_d<T, 2>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq, partials, counter);
+  else
+    line_fwd_d<T, 3>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq, partials, counter);
 }
 
 template <typename T>
@@ -326,6 +338,9 @@ static void line_inv_d(const PassGeom& g, int post, const cpx<T>* S, const Field
   switch (post) {
     case POST_RICH: HOM_LI(POST_RICH); break;
     case POST_CG: HOM_LI(POST_CG); break;
+    case POST_CG_FUSED:
+      if constexpr (std::is_same<T, float>::value) HOM_LI(POST_CG_FUSED);
+      break;
     case POST_CHEB: HOM_LI(POST_CHEB); break;
     case POST_EM: HOM_LI(POST_EM); break;
     case POST_ADD: HOM_LI(POST_ADD); break;

@@ -40,6 +40,8 @@ cudaError_t pair_prepare_f32(int cap) {
   HOM_SET_SMEM((k_pair_strided2<T, R1_, R2_, false>));          \
   HOM_SET_SMEM((k_pair_strided2<T, R1_, R2_, true>));           \
   HOM_SET_SMEM((k_pair_line_fwd<T, 3, PRE_CG, R1_, R2_>));      \
+  HOM_SET_SMEM((k_pair_line_fwd<T, 3, PRE_CG_DOT, R1_, R2_>));  \
+  HOM_SET_SMEM((k_pair_line_inv<T, 3, POST_CG_FUSED, R1_, R2_>)); \
   HOM_SET_SMEM((k_pair_line_fwd<T, 3, PRE_LINEAR, R1_, R2_>));  \
   HOM_SET_SMEM((k_pair_line_inv<T, 3, POST_CG, R1_, R2_>));     \
   HOM_SET_SMEM((k_pair_line_inv<T, 3, POST_CHEB, R1_, R2_>));   \
@@ -125,27 +127,29 @@ void pair_proj_f32(int D, int mode, bool two, const AxisPlan& P, cpx<float>* S,
 
 void pair_line_fwd_f32(int D, int pre, const AxisPlan& P, const Fields<float>& f, cpx<float>* S,
                        const cpx<float>* tw, long long nlines, long long scs,
-                       const MatView<float>& mat, const Scalars* sc, const OpArgs& args,
-                       cudaStream_t st, const ReqDesc<float>* reqs, int nreq) {
+                       const MatView<float>& mat, Scalars* sc, const OpArgs& args,
+                       double* partials, unsigned* counter, cudaStream_t st,
+                       const ReqDesc<float>* reqs, int nreq) {
   using T = float;
   (void)D;  // D = 3 (pair_line_fwd_has)
   const FastDiv fdn = make_fastdiv(P.n);
+#define HOM_PAIR_LF_P(PRE_, R1_, R2_)                                                          \
+  k_pair_line_fwd<T, 3, PRE_, R1_, R2_><<<grid, NT, sm, st>>>(f, S, tw, nlines, scs, mat, sc,    \
+                                                             args, fdn, partials, counter, reqs)
 #define HOM_PAIR_LF(R1_, R2_)                                                                  \
   if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
     constexpr int LB = 2 * pair_lbp<3, R2_>();                                                 \
     const dim3 grid((unsigned)((nlines + LB - 1) / LB), 1, (unsigned)nreq);                   \
     const size_t sm = sizeof(cpx<T>) * (size_t)(R1_ * R2_) * (1 + 3 * pair_lbp<3, R2_>());      \
     constexpr int NT = pair_line_threads<3, R2_>();                                            \
-    if (pre == PRE_CG)                                                                         \
-      k_pair_line_fwd<T, 3, PRE_CG, R1_, R2_><<<grid, NT, sm, st>>>(f, S, tw, nlines, scs, mat,  \
-                                                                    sc, args, fdn, reqs);      \
-    else                                                                                       \
-      k_pair_line_fwd<T, 3, PRE_LINEAR, R1_, R2_><<<grid, NT, sm, st>>>(f, S, tw, nlines, scs, \
-                                                                        mat, sc, args, fdn, reqs); \
+    if (pre == PRE_CG) HOM_PAIR_LF_P(PRE_CG, R1_, R2_);                                        \
+    else if (pre == PRE_CG_DOT) HOM_PAIR_LF_P(PRE_CG_DOT, R1_, R2_);                           \
+    else HOM_PAIR_LF_P(PRE_LINEAR, R1_, R2_);                                                  \
     return;                                                                                    \
   }
   HOM_PAIR_PLANS(HOM_PAIR_LF)
 #undef HOM_PAIR_LF
+#undef HOM_PAIR_LF_P
 }
 
 void pair_line_inv_f32(int D, int post, const AxisPlan& P, const cpx<float>* S,
@@ -167,6 +171,7 @@ void pair_line_inv_f32(int D, int post, const AxisPlan& P, const cpx<float>* S,
     const size_t sm = sizeof(cpx<T>) * (size_t)(R1_ * R2_) * (1 + 3 * pair_lbp<3, R2_>());      \
     constexpr int NT = pair_line_threads<3, R2_>();                                            \
     if (post == POST_CG) HOM_PAIR_LI_P(POST_CG, R1_, R2_);                                     \
+    else if (post == POST_CG_FUSED) HOM_PAIR_LI_P(POST_CG_FUSED, R1_, R2_);                    \
     else if (post == POST_CHEB) HOM_PAIR_LI_P(POST_CHEB, R1_, R2_);                            \
     else HOM_PAIR_LI_P(POST_STORE, R1_, R2_);                                                  \
     return;                                                                                    \

@@ -451,8 +451,8 @@ __host__ __device__ constexpr int pair_line_threads() {
 template <typename T, int D, int PRE, int R1, int R2>
 __global__ void __launch_bounds__(pair_line_threads<D, R2>(), 4)
 k_pair_line_fwd(Fields<T> f, cpx<T>* S, const cpx<T>* __restrict__ twg, long long nlines,
-                long long scs, MatView<T> mat, const Scalars* sc, OpArgs args, FastDiv fdn,
-                const ReqDesc<T>* __restrict__ reqs) {
+                long long scs, MatView<T> mat, Scalars* sc, OpArgs args, FastDiv fdn,
+                double* partials, unsigned* counter, const ReqDesc<T>* __restrict__ reqs) {
   constexpr int n = R1 * R2, nh = (n + 1) / 2, LBP = pair_lbp<D, R2>(), LB = 2 * LBP;
   constexpr int NL = D * LBP, items1 = NL * R2;
   if (reqs != nullptr) {
@@ -461,6 +461,8 @@ k_pair_line_fwd(Fields<T> f, cpx<T>* S, const cpx<T>* __restrict__ twg, long lon
     S = R.S;
     mat = R.mat;
     sc = R.sc;
+    partials = R.partials;
+    counter = R.counter;
   }
   if (sc != nullptr && sc->done) return;
   cpx<T>* sm = smem_c<T>();
@@ -468,7 +470,9 @@ k_pair_line_fwd(Fields<T> f, cpx<T>* S, const cpx<T>* __restrict__ twg, long lon
   cpx<T>* lines = sm + n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
   const long long l0 = (long long)blockIdx.x * LB;
-  line_pre_to_smem<T, D, PRE, kPairPreBatch>(f, n, n, LBP, D, l0, LB, nlines, fdn, mat, sc, args);
+  DotAcc<T> dacc;
+  line_pre_to_smem<T, D, PRE, kPairPreBatch>(f, n, n, LBP, D, l0, LB, nlines, fdn, mat, sc, args,
+                                             &dacc);
   __syncthreads();
   {
     const int t = threadIdx.x;
@@ -511,6 +515,7 @@ k_pair_line_fwd(Fields<T> f, cpx<T>* S, const cpx<T>* __restrict__ twg, long lon
     if (la < nlines) S[a * scs + la * nh + k] = A;
     if (la + 1 < nlines) S[a * scs + (la + 1) * nh + k] = B;
   }
+  if (PRE == PRE_CG_DOT) line_fwd_finish_cg(dacc, sc, partials, counter, nlines * n);
 }
 
 // inverse real DFT of the contiguous axis + post-operator: stage 1 reads the two half spectra
@@ -584,8 +589,9 @@ k_pair_line_inv(const cpx<T>* S, Fields<T> f, const cpx<T>* __restrict__ twg, lo
   }
   __syncthreads();
   DotAcc<T> dacc;
-  // Chebyshev reads three operands a node: smaller batches keep it within the register budget
-  line_post_from_smem<T, D, POST, POST == POST_CHEB ? 2 : 4>(f, n, n, LBP, D, l0, LB, nlines, fdn,
+  // Chebyshev and fused CG read three operands a node: smaller batches keep them within the
+  // register budget
+  line_post_from_smem<T, D, POST, (POST == POST_CHEB || POST == POST_CG_FUSED) ? 2 : 4>(f, n, n, LBP, D, l0, LB, nlines, fdn,
                                                             mat, sc, args, negate, dacc);
   if (partials == nullptr) return;
   double acc[1] = {dacc.value()};

@@ -237,6 +237,21 @@ struct ReqDesc {
 // ---------------------------------------------------------------------------------------
 // line_fwd: pre-operator + forward real DFT of the contiguous axis
 // ---------------------------------------------------------------------------------------
+// PRE_CG_DOT: (p, A p) over the grid (deterministic, last CTA) and the step length
+// alpha = (r, r) / (p, A p) of Algorithm 2, set before the transforms of C p run
+template <typename T>
+__device__ __forceinline__ void line_fwd_finish_cg(const DotAcc<T>& dacc, Scalars* sc,
+                                                   double* partials, unsigned* counter,
+                                                   long long count) {
+  double acc[1] = {dacc.value()};
+  double tot[1];
+  if (!reduce_and_last<1>(acc, partials, counter, tot)) return;
+  if (threadIdx.x != 0) return;
+  const double pAp = tot[0] / (double)count;
+  sc->pAp = pAp;
+  sc->alpha = sc->rr / pAp;
+}
+
 // Pre-operator of the lines l0 .. l0 + LB - 1 (pointwise, coalesced loads in batches of K
 // nodes): component a of line l0 + ll goes to the real (ll even) or imaginary (ll odd) part of
 // the shared-memory complex line b0 + (a * half + ll / 2) * n, so that two real lines share one
@@ -245,7 +260,9 @@ template <typename T, int D, int PRE, int K = (sizeof(T) == 4 ? 8 : 4)>
 __device__ __forceinline__ void line_pre_to_smem(const Fields<T>& f, int b0, int n, int half,
                                                  int ncomp, long long l0, int LB, long long nlines,
                                                  FastDiv fdn, const MatView<T>& mat,
-                                                 const Scalars* sc, const OpArgs& args) {
+                                                 const Scalars* sc, const OpArgs& args,
+                                                 DotAcc<T>* dacc = nullptr) {
+  constexpr bool CG = PRE == PRE_CG || PRE == PRE_CG_DOT;
   cpx<T>* sm = smem_c<T>();
   const double* Es = sc != nullptr ? sc->E : args.E;
   const T E[3] = {(T)Es[0], (T)Es[1], (T)Es[2]};
@@ -268,7 +285,7 @@ __device__ __forceinline__ void line_pre_to_smem(const Fields<T>& f, int b0, int
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         xv[k][a] = (ok && a < ncomp) ? xin[a * f.cs + g] : (T)0;
-        pv[k][a] = (PRE == PRE_CG && ok) ? pin[a * f.cs + g] : (T)0;
+        pv[k][a] = (CG && ok) ? pin[a * f.cs + g] : (T)0;
       }
       ms[k] = (PRE != PRE_IDENT && ok) ? mat_fetch<T>(mat, g) : (T)0;
     }
@@ -288,7 +305,7 @@ __device__ __forceinline__ void line_pre_to_smem(const Fields<T>& f, int b0, int
         T w[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-          if (PRE == PRE_CG) {
+          if (CG) {
             w[a] = xv[k][a] + beta * pv[k][a];
             if (ok) f.p[a * f.cs + g] = w[a];
           } else {
@@ -299,6 +316,10 @@ __device__ __forceinline__ void line_pre_to_smem(const Fields<T>& f, int b0, int
         if (PRE == PRE_EM) {
 #pragma unroll
           for (int a = 0; a < D; ++a) v[a] -= omega * w[a];
+        }
+        if (PRE == PRE_CG_DOT && ok) {
+#pragma unroll
+          for (int a = 0; a < D; ++a) dacc->add(w[a], v[a]);
         }
         if (!ok) {
 #pragma unroll
@@ -321,13 +342,16 @@ template <typename T, int D, int PRE>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
 k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
            int ncomp, long long nlines, int LB, LineDiv ld, long long scs, MatView<T> mat,
-           const Scalars* sc, OpArgs args, const ReqDesc<T>* __restrict__ reqs) {
+           Scalars* sc, OpArgs args, double* partials, unsigned* counter,
+           const ReqDesc<T>* __restrict__ reqs) {
   if (reqs != nullptr) {
     const ReqDesc<T>& R = reqs[blockIdx.z];
     f = R.ff;
     S = R.S;
     mat = R.mat;
     sc = R.sc;
+    partials = R.partials;
+    counter = R.counter;
   }
   if (sc != nullptr && sc->done) return;
   const int n = P.n, nh = (n + 1) / 2;
@@ -339,7 +363,8 @@ k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
   if (threadIdx.x == 0) Ps = P;
   for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = twg[i];
   const long long l0 = (long long)blockIdx.x * LB;
-  line_pre_to_smem<T, D, PRE>(f, b0, n, half, ncomp, l0, LB, nlines, P.fdn, mat, sc, args);
+  DotAcc<T> dacc;
+  line_pre_to_smem<T, D, PRE>(f, b0, n, half, ncomp, l0, LB, nlines, P.fdn, mat, sc, args, &dacc);
   __syncthreads();
   const int res = reg_lines<T>(b0, b1, &Ps, nlc, n, 1, false, false, 0);
   for (int idx = threadIdx.x; idx < nlc * nh; idx += blockDim.x) {
@@ -356,6 +381,7 @@ k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
     if (la < nlines) S[a * scs + la * nh + k] = A;
     if (la + 1 < nlines) S[a * scs + (la + 1) * nh + k] = B;
   }
+  if (PRE == PRE_CG_DOT) line_fwd_finish_cg(dacc, sc, partials, counter, nlines * n);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -634,10 +660,12 @@ __device__ __forceinline__ void line_post_from_smem(const Fields<T>& f, int res,
       const long long g = (l0 + ll) * n + j;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        o1[k][a] = (ok && (POST == POST_RICH || POST == POST_CHEB || POST == POST_EM || POST == POST_ADD))
+        o1[k][a] = (ok && (POST == POST_RICH || POST == POST_CHEB || POST == POST_EM ||
+                           POST == POST_ADD || POST == POST_CG_FUSED))
                        ? xc[a * cs + g] : (T)0;
-        o2[k][a] = (ok && (POST == POST_CG || POST == POST_CHEB)) ? f.p[a * cs + g] : (T)0;
-        o3[k][a] = (ok && POST == POST_CHEB) ? f.r[a * cs + g] : (T)0;
+        o2[k][a] = (ok && (POST == POST_CG || POST == POST_CHEB || POST == POST_CG_FUSED))
+                       ? f.p[a * cs + g] : (T)0;
+        o3[k][a] = (ok && (POST == POST_CHEB || POST == POST_CG_FUSED)) ? f.r[a * cs + g] : (T)0;
       }
       ms[k] = (ok && POST == POST_EM) ? mat_fetch<T>(mat, g) : (T)0;
     }
@@ -685,6 +713,14 @@ __device__ __forceinline__ void line_post_from_smem(const Fields<T>& f, int res,
           f.r[a * cs + g] = rn;
           f.x[a * cs + g] = o1[k][a] + alpha * pv;
           f.p[a * cs + g] = rn - beta * pv;
+          dacc.add(rn, rn);
+        }
+      } else if (POST == POST_CG_FUSED) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const T rn = o3[k][a] - alpha * y[a];
+          f.r[a * cs + g] = rn;
+          f.x[a * cs + g] = o1[k][a] + alpha * o2[k][a];
           dacc.add(rn, rn);
         }
       } else if (POST == POST_ADD) {
@@ -741,6 +777,21 @@ __device__ __forceinline__ void line_inv_finish(Scalars* sc, double tot0, double
   } else if (POST == POST_CG) {
     sc->pAp = mean;
     sc->alpha = sc->rr / mean;
+  } else if (POST == POST_CG_FUSED) {
+    // x += alpha p, r -= alpha C p done above; (r, r), the stopping test and beta
+    const double res = sqrt(mean);
+    sc->last_res = res;
+    sc->it += 1;
+    if (sc->fixed) {
+      if (sc->it >= sc->maxit) sc->done = 1;
+    } else if (res <= sc->tol * sc->nb) {
+      sc->done = 1;
+      sc->converged = 1;
+    } else if (sc->it >= sc->maxit) {
+      sc->done = 1;
+    }
+    sc->beta = mean / sc->rr;
+    sc->rr = mean;
   } else if (POST == POST_CHEB) {
     const double res = sqrt(mean);
     sc->last_res = res;
