@@ -289,7 +289,7 @@ def pass_flops(rmax):
 # DRAM bytes (read + write) of one launch of the dominant kernels of the 243^3 CG steps, from
 # one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum on GB300; other kernels and
 # grids have no capture (null)
-NCU_TRAFFIC = {("fp64", "strided"): 649.1e6, ("fp32", "line_fwd"): 644.9e6}
+NCU_TRAFFIC = {("fp64", "strided"): 649.1e6}
 
 
 def ncu_traffic(precision, kind):
@@ -298,17 +298,28 @@ def ncu_traffic(precision, kind):
     return NCU_TRAFFIC.get((precision, kind))
 
 
-def pass_bytes(word=8):
+def pass_bytes(word=8, two_line=False, fused_cg=False):
     """Compulsory DRAM bytes of one launch of each pass kind in a CG step (word = 8 for FP64,
-    4 for FP32); the CG update reads x, p, r, C p and writes x, r."""
+    4 for FP32). two_line: the 3-D scalar projection keeps two spectrum lines between its column
+    passes (the axis-1 passes read or write two components of three, the projection two and
+    two). fused_cg: the FP32 inner CG step, whose inverse pass reads the spectrum and x, r, p and
+    writes x, r (no separate vector update); otherwise line_inv reads the spectrum and p and
+    writes C p, and the vector update reads x, p, r, C p and writes x, r."""
     n = N_GRID[0]
     nh = (n + 1) // 2
-    spec = n * n * nh * D * 2 * word
+    spec = n * n * nh * D * 2 * word  # all D components of the half spectrum
     field = n * n * n * D * word
-    return {"line_fwd": 2 * field + field + n ** 3 + spec,  # r, p read; p written; phase; spectrum
-            "strided": 2 * spec, "proj": 2 * spec,
-            "line_inv": spec + 2 * field,                    # spectrum; p read; C p written
-            "vector": 6 * field}
+    out = {"line_fwd": 2 * field + field + n ** 3 + spec,  # r, p read; p written; phase; spectrum
+           "strided": 2 * spec, "proj": 2 * spec}
+    if two_line:
+        out["strided"] = spec * 5 // 3   # forward 3 read + 2 written, inverse 2 read + 3 written
+        out["proj"] = spec * 4 // 3
+    if fused_cg:
+        out["line_inv"] = spec + 3 * field + 2 * field
+    else:
+        out["line_inv"] = spec + 2 * field                # spectrum; p read; C p written
+        out["vector"] = 6 * field
+    return out
 
 
 # ------------------------------------------------------------------------------------------
@@ -438,7 +449,7 @@ def run_ours(args, rank, world, local):
         return None
     flops = pass_flops(tune["rmax64"])
     byts = pass_bytes(8)
-    byts32 = pass_bytes(4)
+    byts32 = pass_bytes(4, two_line=bool(tune32.get("two_line32")), fused_cg=True)
     peaks = measured_peaks()
 
     def per_kind(pr):
@@ -456,11 +467,12 @@ def run_ours(args, rank, world, local):
     dom_ms = pk[dom]["ms_avg"]
     achieved = flops[dom] / (dom_ms * 1e-3) / 1e12
     peak = 1.25  # FP64 TFLOP/s: 152 SMs x 2 DFMA/clk x 2 flops x ~2.07 GHz (nominal)
-    step_bytes = sum(byts[k] * (2 if k == "strided" else 1) for k in byts)
+    # compulsory bytes of one step: per kind, bytes per launch x launches per step (measured)
+    step_bytes = sum(byts[k] * pk[k]["launches"] / args.steps for k in pk if k in byts)
     pk32 = per_kind(passes32)
     dom32 = max((k for k in pk32 if k in byts32), key=lambda k: pk32[k]["ms_avg"] * pk32[k]["launches"])
     ach32 = byts32[dom32] / (pk32[dom32]["ms_avg"] * 1e-3) / 1e9
-    step_bytes32 = sum(byts32[k] * (2 if k == "strided" else 1) for k in byts32)
+    step_bytes32 = sum(byts32[k] * pk32[k]["launches"] / args.steps for k in pk32 if k in byts32)
     value = world * 1000.0 / ms_step
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
