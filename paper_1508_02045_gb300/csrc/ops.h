@@ -113,11 +113,12 @@ inline bool pair_line_inv_has(int D, int post) {
   return D == 3 && (post == POST_CG || post == POST_CG_FUSED || post == POST_CHEB ||
                     post == POST_STORE);
 }
-void pair_line_fwd_f32(int D, int pre, const AxisPlan& P, const Fields<float>& f, cpx<float>* S,
-                       const cpx<float>* tw, long long nlines, long long scs,
-                       const MatView<float>& mat, Scalars* sc, const OpArgs& args,
-                       double* partials, unsigned* counter, cudaStream_t st,
-                       const ReqDesc<float>* reqs, int nreq);
+// returns the number of CTAs (the partials a PRE_CG_DOT pass writes)
+int pair_line_fwd_f32(int D, int pre, const AxisPlan& P, const Fields<float>& f, cpx<float>* S,
+                      const cpx<float>* tw, long long nlines, long long scs,
+                      const MatView<float>& mat, Scalars* sc, const OpArgs& args,
+                      double* partials, unsigned* counter, cudaStream_t st,
+                      const ReqDesc<float>* reqs, int nreq);
 void pair_line_inv_f32(int D, int post, const AxisPlan& P, const cpx<float>* S,
                        const Fields<float>& f, const cpx<float>* tw, long long nlines,
                        long long scs, const MatView<float>& mat, Scalars* sc, const OpArgs& args,

@@ -181,7 +181,7 @@ static void line_fwd_d(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S
   const size_t sm = Ops<T>::smem_line(P.n, ncomp, g.LB);
   const bool prof = profiling();
   if (prof) prof_mark(KIND_LINE_FWD, st, true);
-#define HOM_LF(PRE_) k_line_fwd<T, D, PRE_><<<grid, g.NTl, sm, st>>>(f, S, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, counter, reqs)
+#define HOM_LF(PRE_) k_line_fwd<T, D, PRE_><<<grid, g.NTl, sm, st>>>(f, S, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, reqs)
   switch (pre) {
     case PRE_AFFINE: HOM_LF(PRE_AFFINE); break;
     case PRE_LINEAR: HOM_LF(PRE_LINEAR); break;
@@ -206,10 +206,15 @@ void Ops<T>::line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
     if (ncomp == g.D && pair_line_fwd_has(g.D, pre) && pair_plan<T>(P)) {
       const bool prof = profiling();
       if (prof) prof_mark(KIND_LINE_FWD, st, true);
-      pair_line_fwd_f32(g.D, pre, P, f, S, tw, g.nlines, g.scs, mat, sc, args, partials, counter,
-                        st, reqs, nreq);
-      if (prof) prof_mark(KIND_LINE_FWD, st, false);
+      const int nb = pair_line_fwd_f32(g.D, pre, P, f, S, tw, g.nlines, g.scs, mat, sc, args,
+                                       partials, counter, st, reqs, nreq);
       ++launch_counter();
+      if (pre == PRE_CG_DOT) {
+        k_cg_alpha<T><<<dim3(1, 1, (unsigned)nreq), kThreads, 0, st>>>(partials, nb,
+                                                                      g.nodes, sc, reqs);
+        ++launch_counter();
+      }
+      if (prof) prof_mark(KIND_LINE_FWD, st, false);
       return;
     }
   }
@@ -217,6 +222,12 @@ void Ops<T>::line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
     line_fwd_d<T, 2>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq, partials, counter);
   else
     line_fwd_d<T, 3>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq, partials, counter);
+  if (pre == PRE_CG_DOT) {
+    const int nb = (int)((g.nlines + g.LB - 1) / g.LB);
+    k_cg_alpha<T><<<dim3(1, 1, (unsigned)nreq), kThreads, 0, st>>>(partials, nb, g.nodes, sc,
+                                                                  reqs);
+    ++launch_counter();
+  }
 }
 
 template <typename T>

@@ -125,17 +125,17 @@ void pair_proj_f32(int D, int mode, bool two, const AxisPlan& P, cpx<float>* S,
 #undef HOM_PAIR_PJ_D
 }
 
-void pair_line_fwd_f32(int D, int pre, const AxisPlan& P, const Fields<float>& f, cpx<float>* S,
-                       const cpx<float>* tw, long long nlines, long long scs,
-                       const MatView<float>& mat, Scalars* sc, const OpArgs& args,
-                       double* partials, unsigned* counter, cudaStream_t st,
-                       const ReqDesc<float>* reqs, int nreq) {
+int pair_line_fwd_f32(int D, int pre, const AxisPlan& P, const Fields<float>& f, cpx<float>* S,
+                      const cpx<float>* tw, long long nlines, long long scs,
+                      const MatView<float>& mat, Scalars* sc, const OpArgs& args,
+                      double* partials, unsigned* counter, cudaStream_t st,
+                      const ReqDesc<float>* reqs, int nreq) {
   using T = float;
   (void)D;  // D = 3 (pair_line_fwd_has)
   const FastDiv fdn = make_fastdiv(P.n);
 #define HOM_PAIR_LF_P(PRE_, R1_, R2_)                                                          \
   k_pair_line_fwd<T, 3, PRE_, R1_, R2_><<<grid, NT, sm, st>>>(f, S, tw, nlines, scs, mat, sc,    \
-                                                             args, fdn, partials, counter, reqs)
+                                                             args, fdn, partials, reqs)
 #define HOM_PAIR_LF(R1_, R2_)                                                                  \
   if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
     constexpr int LB = 2 * pair_lbp<3, R2_>();                                                 \
@@ -145,9 +145,10 @@ void pair_line_fwd_f32(int D, int pre, const AxisPlan& P, const Fields<float>& f
     if (pre == PRE_CG) HOM_PAIR_LF_P(PRE_CG, R1_, R2_);                                        \
     else if (pre == PRE_CG_DOT) HOM_PAIR_LF_P(PRE_CG_DOT, R1_, R2_);                           \
     else HOM_PAIR_LF_P(PRE_LINEAR, R1_, R2_);                                                  \
-    return;                                                                                    \
+    return (int)grid.x;                                                                        \
   }
   HOM_PAIR_PLANS(HOM_PAIR_LF)
+  return 0;
 #undef HOM_PAIR_LF
 #undef HOM_PAIR_LF_P
 }

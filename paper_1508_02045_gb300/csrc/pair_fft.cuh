@@ -452,7 +452,7 @@ template <typename T, int D, int PRE, int R1, int R2>
 __global__ void __launch_bounds__(pair_line_threads<D, R2>(), 4)
 k_pair_line_fwd(Fields<T> f, cpx<T>* S, const cpx<T>* __restrict__ twg, long long nlines,
                 long long scs, MatView<T> mat, Scalars* sc, OpArgs args, FastDiv fdn,
-                double* partials, unsigned* counter, const ReqDesc<T>* __restrict__ reqs) {
+                double* partials, const ReqDesc<T>* __restrict__ reqs) {
   constexpr int n = R1 * R2, nh = (n + 1) / 2, LBP = pair_lbp<D, R2>(), LB = 2 * LBP;
   constexpr int NL = D * LBP, items1 = NL * R2;
   if (reqs != nullptr) {
@@ -462,7 +462,6 @@ k_pair_line_fwd(Fields<T> f, cpx<T>* S, const cpx<T>* __restrict__ twg, long lon
     mat = R.mat;
     sc = R.sc;
     partials = R.partials;
-    counter = R.counter;
   }
   if (sc != nullptr && sc->done) return;
   cpx<T>* sm = smem_c<T>();
@@ -515,7 +514,7 @@ k_pair_line_fwd(Fields<T> f, cpx<T>* S, const cpx<T>* __restrict__ twg, long lon
     if (la < nlines) S[a * scs + la * nh + k] = A;
     if (la + 1 < nlines) S[a * scs + (la + 1) * nh + k] = B;
   }
-  if (PRE == PRE_CG_DOT) line_fwd_finish_cg(dacc, sc, partials, counter, nlines * n);
+  if (PRE == PRE_CG_DOT) line_fwd_partial_cg(dacc, partials);
 }
 
 // inverse real DFT of the contiguous axis + post-operator: stage 1 reads the two half spectra

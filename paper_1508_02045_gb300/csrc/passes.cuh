@@ -90,6 +90,33 @@ __device__ bool reduce_and_last(double (&acc)[NV], double* partials, unsigned* c
   return true;
 }
 
+// Per-CTA partial of a grid reduction without the completion ticket: the CTA writes its sum
+// and a later kernel (k_cg_alpha) adds the partials in a fixed order, so the producing kernel
+// needs no fence or atomic at its end.
+template <int NV>
+__device__ void block_partial(double (&acc)[NV], double* partials) {
+  __shared__ double redp[NV][kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (int)(blockDim.x >> 5);
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double s = acc[v];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) redp[v][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += redp[v][w];
+      partials[(size_t)bid * NV + v] = s;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // coefficient products
 // ---------------------------------------------------------------------------------------
@@ -237,19 +264,40 @@ struct ReqDesc {
 // ---------------------------------------------------------------------------------------
 // line_fwd: pre-operator + forward real DFT of the contiguous axis
 // ---------------------------------------------------------------------------------------
-// PRE_CG_DOT: (p, A p) over the grid (deterministic, last CTA) and the step length
-// alpha = (r, r) / (p, A p) of Algorithm 2, set before the transforms of C p run
+// PRE_CG_DOT: the CTA's partial of (p, A p); k_cg_alpha completes the sum
 template <typename T>
-__device__ __forceinline__ void line_fwd_finish_cg(const DotAcc<T>& dacc, Scalars* sc,
-                                                   double* partials, unsigned* counter,
-                                                   long long count) {
+__device__ __forceinline__ void line_fwd_partial_cg(const DotAcc<T>& dacc, double* partials) {
   double acc[1] = {dacc.value()};
-  double tot[1];
-  if (!reduce_and_last<1>(acc, partials, counter, tot)) return;
-  if (threadIdx.x != 0) return;
-  const double pAp = tot[0] / (double)count;
-  sc->pAp = pAp;
-  sc->alpha = sc->rr / pAp;
+  block_partial<1>(acc, partials);
+}
+
+// (p, A p) from the nblocks partials of the PRE_CG_DOT pass, summed in a fixed order by one
+// CTA per request (blockIdx.z), and the step length alpha = (r, r) / (p, A p) of Algorithm 2,
+// set before the transforms of C p run
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_cg_alpha(const double* partials, int nblocks, long long count, Scalars* sc,
+           const ReqDesc<T>* __restrict__ reqs) {
+  __shared__ double red[kThreads / 32];
+  if (reqs != nullptr) {
+    partials = reqs[blockIdx.z].partials;
+    sc = reqs[blockIdx.z].sc;
+  }
+  if (sc->done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) red[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double f = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) f += red[w];
+    const double pAp = f / (double)count;
+    sc->pAp = pAp;
+    sc->alpha = sc->rr / pAp;
+  }
 }
 
 // Pre-operator of the lines l0 .. l0 + LB - 1 (pointwise, coalesced loads in batches of K
@@ -342,8 +390,7 @@ template <typename T, int D, int PRE>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
 k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
            int ncomp, long long nlines, int LB, LineDiv ld, long long scs, MatView<T> mat,
-           Scalars* sc, OpArgs args, double* partials, unsigned* counter,
-           const ReqDesc<T>* __restrict__ reqs) {
+           Scalars* sc, OpArgs args, double* partials, const ReqDesc<T>* __restrict__ reqs) {
   if (reqs != nullptr) {
     const ReqDesc<T>& R = reqs[blockIdx.z];
     f = R.ff;
@@ -351,7 +398,6 @@ k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
     mat = R.mat;
     sc = R.sc;
     partials = R.partials;
-    counter = R.counter;
   }
   if (sc != nullptr && sc->done) return;
   const int n = P.n, nh = (n + 1) / 2;
@@ -381,7 +427,7 @@ k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
     if (la < nlines) S[a * scs + la * nh + k] = A;
     if (la + 1 < nlines) S[a * scs + (la + 1) * nh + k] = B;
   }
-  if (PRE == PRE_CG_DOT) line_fwd_finish_cg(dacc, sc, partials, counter, nlines * n);
+  if (PRE == PRE_CG_DOT) line_fwd_partial_cg(dacc, partials);
 }
 
 // ---------------------------------------------------------------------------------------
