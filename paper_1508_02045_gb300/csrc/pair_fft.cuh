@@ -430,7 +430,7 @@ k_pair_proj_scalar(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, const 
 // component, two real lines packed into one complex line (a, q) at n + (a LBP + q) n
 // ---------------------------------------------------------------------------------------
 // nodes per thread whose pre-operator loads are issued together in the specialised line_fwd
-constexpr int kPairPreBatch = 4;
+constexpr int kPairPreBatch = 2;
 
 // line pairs per CTA: as many as keep the first-stage butterflies D x LBP x R2 within 224
 // threads; the line kernels are compiled for four CTAs per SM (at most 72 registers a thread),
@@ -470,8 +470,8 @@ k_pair_line_fwd(Fields<T> f, cpx<T>* S, const cpx<T>* __restrict__ twg, long lon
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
   const long long l0 = (long long)blockIdx.x * LB;
   DotAcc<T> dacc;
-  line_pre_to_smem<T, D, PRE, kPairPreBatch>(f, n, n, LBP, D, l0, LB, nlines, fdn, mat, sc, args,
-                                             &dacc);
+  line_pre_to_smem<T, D, PRE, kPairPreBatch, n>(f, n, n, LBP, D, l0, LB, nlines, fdn, mat, sc,
+                                                args, &dacc);
   __syncthreads();
   {
     const int t = threadIdx.x;
@@ -590,7 +590,7 @@ k_pair_line_inv(const cpx<T>* S, Fields<T> f, const cpx<T>* __restrict__ twg, lo
   DotAcc<T> dacc;
   // Chebyshev and fused CG read three operands a node: smaller batches keep them within the
   // register budget
-  line_post_from_smem<T, D, POST, (POST == POST_CHEB || POST == POST_CG_FUSED) ? 2 : 4>(f, n, n, LBP, D, l0, LB, nlines, fdn,
+  line_post_from_smem<T, D, POST, (POST == POST_CHEB || POST == POST_CG_FUSED) ? 2 : 4, n>(f, n, n, LBP, D, l0, LB, nlines, fdn,
                                                             mat, sc, args, negate, dacc);
   if (partials == nullptr) return;
   double acc[1] = {dacc.value()};

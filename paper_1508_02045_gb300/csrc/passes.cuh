@@ -304,13 +304,15 @@ k_cg_alpha(const double* partials, int nblocks, long long count, Scalars* sc,
 // nodes): component a of line l0 + ll goes to the real (ll even) or imaginary (ll odd) part of
 // the shared-memory complex line b0 + (a * half + ll / 2) * n, so that two real lines share one
 // complex transform.
-template <typename T, int D, int PRE, int K = (sizeof(T) == 4 ? 8 : 4)>
+template <typename T, int D, int PRE, int K = (sizeof(T) == 4 ? 8 : 4), int NC = 0>
 __device__ __forceinline__ void line_pre_to_smem(const Fields<T>& f, int b0, int n, int half,
                                                  int ncomp, long long l0, int LB, long long nlines,
                                                  FastDiv fdn, const MatView<T>& mat,
                                                  const Scalars* sc, const OpArgs& args,
                                                  DotAcc<T>* dacc = nullptr) {
   constexpr bool CG = PRE == PRE_CG || PRE == PRE_CG_DOT;
+  // NC > 0: the line length as a compile-time constant (specialised kernels)
+  if (NC > 0) n = NC;
   cpx<T>* sm = smem_c<T>();
   const double* Es = sc != nullptr ? sc->E : args.E;
   const T E[3] = {(T)Es[0], (T)Es[1], (T)Es[2]};
@@ -319,32 +321,33 @@ __device__ __forceinline__ void line_pre_to_smem(const Fields<T>& f, int b0, int
   // Richardson keeps x_m and x_{m-1} in a buffer pair; the operand is the current one
   const T* xin = f.xin;
   if (f.x != nullptr && sc != nullptr) xin = f.x + (sc->which ? D * f.cs : 0);
+  // the CTA's lines are contiguous: node idx of the tile is node g0 + idx of the grid
+  const long long g0 = l0 * n;
+  const int ntile = LB * n;
+  const int nvalid = (int)min((long long)ntile, (nlines - l0) * n);
+  const T* __restrict__ xb = xin + g0;
+  const T* __restrict__ pb = f.p + g0;
+  T* pw = f.p + g0;
   // batches of K nodes per thread: every global load of a batch is issued before any use
-  const T* __restrict__ pin = f.p;
-  for (int base = 0; base < LB * n; base += K * blockDim.x) {
+  for (int base = 0; base < ntile; base += K * blockDim.x) {
     T xv[K][D], pv[K][D], ms[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int idx = base + k * blockDim.x + threadIdx.x;
-      const int ll = fdiv(idx, fdn), j = idx - ll * n;
-      const long long l = l0 + ll;
-      const bool ok = idx < LB * n && l < nlines;
-      const long long g = l * n + j;
+      const bool ok = idx < nvalid;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        xv[k][a] = (ok && a < ncomp) ? xin[a * f.cs + g] : (T)0;
-        pv[k][a] = (CG && ok) ? pin[a * f.cs + g] : (T)0;
+        xv[k][a] = (ok && a < ncomp) ? xb[a * f.cs + idx] : (T)0;
+        pv[k][a] = (CG && ok) ? pb[a * f.cs + idx] : (T)0;
       }
-      ms[k] = (PRE != PRE_IDENT && ok) ? mat_fetch<T>(mat, g) : (T)0;
+      ms[k] = (PRE != PRE_IDENT && ok) ? mat_fetch<T>(mat, g0 + idx) : (T)0;
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int idx = base + k * blockDim.x + threadIdx.x;
-      if (idx >= LB * n) continue;
-      const int ll = fdiv(idx, fdn), j = idx - ll * n;
-      const long long l = l0 + ll;
-      const bool ok = l < nlines;
-      const long long g = l * n + j;
+      if (idx >= ntile) continue;
+      const bool ok = idx < nvalid;
+      const int ll = NC > 0 ? idx / NC : fdiv(idx, fdn), j = idx - ll * n;
       T v[D];
       if (PRE == PRE_IDENT) {
 #pragma unroll
@@ -355,7 +358,7 @@ __device__ __forceinline__ void line_pre_to_smem(const Fields<T>& f, int b0, int
         for (int a = 0; a < D; ++a) {
           if (CG) {
             w[a] = xv[k][a] + beta * pv[k][a];
-            if (ok) f.p[a * f.cs + g] = w[a];
+            if (ok) pw[a * f.cs + idx] = w[a];
           } else {
             w[a] = xv[k][a] + (PRE == PRE_AFFINE && ok ? E[a] : (T)0);
           }
@@ -679,7 +682,7 @@ k_proj_scalar(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g,
 // l0 + ll is the real (ll even) or imaginary (ll odd) part of shared-memory complex line
 // res + (a * half + ll / 2) * n; the solver's vector update, batches of K nodes whose operands
 // are loaded before any use, and the inner-product partial in dacc.
-template <typename T, int D, int POST, int K = (sizeof(T) == 4 ? 4 : 2)>
+template <typename T, int D, int POST, int K = (sizeof(T) == 4 ? 4 : 2), int NC = 0>
 __device__ __forceinline__ void line_post_from_smem(const Fields<T>& f, int res, int n, int half,
                                                     int ncomp, long long l0, int LB,
                                                     long long nlines, FastDiv fdn,
@@ -696,14 +699,19 @@ __device__ __forceinline__ void line_post_from_smem(const Fields<T>& f, int res,
   const long long cs = f.cs;
   const T* xc = (POST == POST_RICH) ? f.x + (which ? D * cs : 0) : f.x;
   T* xn = (POST == POST_RICH) ? f.x + (which ? 0 : D * cs) : f.x;
-  for (int base = 0; base < LB * n; base += K * blockDim.x) {
+  // NC > 0: the line length as a compile-time constant (specialised kernels); the CTA's lines
+  // are contiguous, node idx of the tile is node g0 + idx of the grid
+  if (NC > 0) n = NC;
+  const long long g0 = l0 * n;
+  const int ntile = LB * n;
+  const int nvalid = (int)min((long long)ntile, (nlines - l0) * n);
+  for (int base = 0; base < ntile; base += K * blockDim.x) {
     T o1[K][D], o2[K][D], o3[K][D], ms[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int idx = base + k * blockDim.x + threadIdx.x;
-      const int ll = fdiv(idx, fdn), j = idx - ll * n;
-      const bool ok = idx < LB * n && l0 + ll < nlines;
-      const long long g = (l0 + ll) * n + j;
+      const bool ok = idx < nvalid;
+      const long long g = g0 + idx;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         o1[k][a] = (ok && (POST == POST_RICH || POST == POST_CHEB || POST == POST_EM ||
@@ -718,9 +726,9 @@ __device__ __forceinline__ void line_post_from_smem(const Fields<T>& f, int res,
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int idx = base + k * blockDim.x + threadIdx.x;
-      const int ll = fdiv(idx, fdn), j = idx - ll * n;
-      if (idx >= LB * n || l0 + ll >= nlines) continue;
-      const long long g = (l0 + ll) * n + j;
+      if (idx >= nvalid) continue;
+      const int ll = NC > 0 ? idx / NC : fdiv(idx, fdn), j = idx - ll * n;
+      const long long g = g0 + idx;
       T y[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) {
