@@ -94,13 +94,23 @@ def barrier(world):
 
 
 def max_over_ranks(v, world):
+    """The largest of the ranks' values (the timed region of a replica run ends when the slowest
+    rank ends); on the process group's own device (NCCL: the GPU, gloo: the host)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_value(ms_step_local, world):
+    """Whole-job matvecs/s of N replicas: every rank runs one step per ms_step of its own, the
+    job's step time is the slowest rank's, and N steps complete per job step."""
+    ms = max_over_ranks(ms_step_local, world)
+    return ms, world * 1000.0 / ms
 
 
 # ------------------------------------------------------------------------------------------
