@@ -11,7 +11,8 @@
 // registers with compile-time indices and constant twiddles. The planner groups the prime
 // factors of n into as few such radices as fit in registers, so most axes need two stages.
 // The inverse transform (eq. (DFT), no scaling) is conj(F(conj(.))): imaginary parts are
-// negated on every load and store of a stage.
+// negated on the load of a transform's first stage and the store of its last (bit 0 / bit 1 of
+// a stage's cj flags).
 #pragma once
 #include <cmath>
 
@@ -197,7 +198,8 @@ __device__ __forceinline__ int line_off(const Loc<T>& L, int l) {
 // Work items: (line, butterfly); colmajor puts the line index fastest.
 template <typename T, int R, bool INV>
 __device__ __forceinline__ void reg_stage(Loc<T> in, Loc<T> out, int n, int p, int nl,
-                                         bool colmajor, int tw_base, FastDiv fd_m, FastDiv fd_p) {
+                                         bool colmajor, int tw_base, FastDiv fd_m, FastDiv fd_p,
+                                         int cj) {
   const int m = n / R;
   const int total = nl * m;
   const int ts = n / (p * R);
@@ -231,7 +233,7 @@ __device__ __forceinline__ void reg_stage(Loc<T> in, Loc<T> out, int n, int p, i
 #pragma unroll
       for (int r = 0; r < R; ++r) u[r] = sm[io + r * istride];
     }
-    if (INV) {
+    if (INV && (cj & 1)) {
 #pragma unroll
       for (int r = 0; r < R; ++r) u[r].y = -u[r].y;
     }
@@ -241,7 +243,7 @@ __device__ __forceinline__ void reg_stage(Loc<T> in, Loc<T> out, int n, int p, i
       for (int r = 1; r < R; ++r) u[r] = cmul(u[r], sm[tw_base + r * step]);
     }
     RegDft<T, R>::run(u);
-    if (INV) {
+    if (INV && (cj & 2)) {
 #pragma unroll
       for (int r = 0; r < R; ++r) u[r].y = -u[r].y;
     }
@@ -259,37 +261,41 @@ __device__ __forceinline__ void reg_stage(Loc<T> in, Loc<T> out, int n, int p, i
 // Dispatch of one stage on the runtime radix (not inlined: one copy per precision/direction).
 template <typename T, bool INV>
 __device__ __noinline__ void reg_stage_any(int R, Loc<T> in, Loc<T> out, int n, int p, int nl,
-                                           bool colmajor, int tw_base, FastDiv fm, FastDiv fp) {
+                                           bool colmajor, int tw_base, FastDiv fm, FastDiv fp,
+                                           int cj) {
   switch (R) {
-    case 3: reg_stage<T, 3, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
-    case 5: reg_stage<T, 5, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
-    case 7: reg_stage<T, 7, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
-    case 9: reg_stage<T, 9, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
-    case 11: reg_stage<T, 11, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
-    case 13: reg_stage<T, 13, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
-    case 15: reg_stage<T, 15, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
-    case 17: reg_stage<T, 17, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
-    case 19: reg_stage<T, 19, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
-    case 21: reg_stage<T, 21, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
-    case 23: reg_stage<T, 23, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
-    case 25: reg_stage<T, 25, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
-    case 27: reg_stage<T, 27, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
-    case 29: reg_stage<T, 29, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
-    case 31: reg_stage<T, 31, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp); break;
+    case 3: reg_stage<T, 3, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    case 5: reg_stage<T, 5, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    case 7: reg_stage<T, 7, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    case 9: reg_stage<T, 9, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    case 11: reg_stage<T, 11, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    case 13: reg_stage<T, 13, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    case 15: reg_stage<T, 15, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    case 17: reg_stage<T, 17, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    case 19: reg_stage<T, 19, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    case 21: reg_stage<T, 21, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    case 23: reg_stage<T, 23, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    case 25: reg_stage<T, 25, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    case 27: reg_stage<T, 27, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    case 29: reg_stage<T, 29, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    case 31: reg_stage<T, 31, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
     default: break;
   }
 }
 
-// stage st of plan P
+// stage st of plan P (an inverse transform is conj(F(conj .)) over the whole sequence of stages
+// 0 .. nst - 1: the first stage conjugates what it loads, the last what it stores, the ones
+// between neither)
 template <typename T>
 __device__ __forceinline__ void stage_any(bool inv, const AxisPlan* P, int st, Loc<T> in,
                                           Loc<T> out, int nl, bool colmajor, int tw_base) {
+  const int cj = (st == 0 ? 1 : 0) | (st == P->nst - 1 ? 2 : 0);
   if (inv)
     reg_stage_any<T, true>(P->radix[st], in, out, P->n, P->pprev[st], nl, colmajor, tw_base,
-                           P->fdm[st], P->fdp[st]);
+                           P->fdm[st], P->fdp[st], cj);
   else
     reg_stage_any<T, false>(P->radix[st], in, out, P->n, P->pprev[st], nl, colmajor, tw_base,
-                            P->fdm[st], P->fdp[st]);
+                            P->fdm[st], P->fdp[st], cj);
 }
 
 // shared-memory location helpers

@@ -45,12 +45,12 @@ struct Ops {
 
   // reqs / nreq: optional per-request descriptors of a batched launch (grid.z = nreq); the
   // direct arguments are then ignored where a descriptor provides them
-  // partials / counter: the grid reduction of PRE_CG_DOT (unused by the other pre-operators)
+  // partials: the per-CTA partials of (p, A p) written by PRE_CG_DOT (unused otherwise)
   static void line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
                        const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
                        Scalars* sc, const OpArgs& args, cudaStream_t st,
                        const ReqDesc<T>* reqs = nullptr, int nreq = 1,
-                       double* partials = nullptr, unsigned* counter = nullptr);
+                       double* partials = nullptr);
   // strided DFT along axis 1 (D = 3) or axis 0 (no projection) of ncomp components
   static void strided(const PassGeom& g, int axis, int inv, cpx<T>* S, const AxisPlan& P,
                       const cpx<T>* tw, int ncomp, const Scalars* sc, cudaStream_t st,
@@ -117,8 +117,7 @@ inline bool pair_line_inv_has(int D, int post) {
 int pair_line_fwd_f32(int D, int pre, const AxisPlan& P, const Fields<float>& f, cpx<float>* S,
                       const cpx<float>* tw, long long nlines, long long scs,
                       const MatView<float>& mat, Scalars* sc, const OpArgs& args,
-                      double* partials, unsigned* counter, cudaStream_t st,
-                      const ReqDesc<float>* reqs, int nreq);
+                      double* partials, cudaStream_t st, const ReqDesc<float>* reqs, int nreq);
 void pair_line_inv_f32(int D, int post, const AxisPlan& P, const cpx<float>* S,
                        const Fields<float>& f, const cpx<float>* tw, long long nlines,
                        long long scs, const MatView<float>& mat, Scalars* sc, const OpArgs& args,

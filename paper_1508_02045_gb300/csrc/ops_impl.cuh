@@ -176,7 +176,7 @@ template <typename T, int D>
 static void line_fwd_d(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
                        const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
                        Scalars* sc, const OpArgs& args, cudaStream_t st,
-                       const ReqDesc<T>* reqs, int nreq, double* partials, unsigned* counter) {
+                       const ReqDesc<T>* reqs, int nreq, double* partials) {
   const dim3 grid((unsigned)((g.nlines + g.LB - 1) / g.LB), 1, (unsigned)nreq);
   const size_t sm = Ops<T>::smem_line(P.n, ncomp, g.LB);
   const bool prof = profiling();
@@ -201,13 +201,13 @@ template <typename T>
 void Ops<T>::line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
                       const AxisPlan& P, const cpx<T>* tw, int ncomp, const MatView<T>& mat,
                       Scalars* sc, const OpArgs& args, cudaStream_t st,
-                      const ReqDesc<T>* reqs, int nreq, double* partials, unsigned* counter) {
+                      const ReqDesc<T>* reqs, int nreq, double* partials) {
   if constexpr (std::is_same<T, float>::value) {
     if (ncomp == g.D && pair_line_fwd_has(g.D, pre) && pair_plan<T>(P)) {
       const bool prof = profiling();
       if (prof) prof_mark(KIND_LINE_FWD, st, true);
       const int nb = pair_line_fwd_f32(g.D, pre, P, f, S, tw, g.nlines, g.scs, mat, sc, args,
-                                       partials, counter, st, reqs, nreq);
+                                       partials, st, reqs, nreq);
       ++launch_counter();
       if (pre == PRE_CG_DOT) {
         k_cg_alpha<T><<<dim3(1, 1, (unsigned)nreq), kThreads, 0, st>>>(partials, nb,
@@ -219,9 +219,9 @@ void Ops<T>::line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
     }
   }
   if (g.D == 2)
-    line_fwd_d<T, 2>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq, partials, counter);
+    line_fwd_d<T, 2>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq, partials);
   else
-    line_fwd_d<T, 3>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq, partials, counter);
+    line_fwd_d<T, 3>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq, partials);
   if (pre == PRE_CG_DOT) {
     const int nb = (int)((g.nlines + g.LB - 1) / g.LB);
     k_cg_alpha<T><<<dim3(1, 1, (unsigned)nreq), kThreads, 0, st>>>(partials, nb, g.nodes, sc,

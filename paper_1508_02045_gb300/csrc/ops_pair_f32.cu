@@ -128,8 +128,7 @@ void pair_proj_f32(int D, int mode, bool two, const AxisPlan& P, cpx<float>* S,
 int pair_line_fwd_f32(int D, int pre, const AxisPlan& P, const Fields<float>& f, cpx<float>* S,
                       const cpx<float>* tw, long long nlines, long long scs,
                       const MatView<float>& mat, Scalars* sc, const OpArgs& args,
-                      double* partials, unsigned* counter, cudaStream_t st,
-                      const ReqDesc<float>* reqs, int nreq) {
+                      double* partials, cudaStream_t st, const ReqDesc<float>* reqs, int nreq) {
   using T = float;
   (void)D;  // D = 3 (pair_line_fwd_has)
   const FastDiv fdn = make_fastdiv(P.n);

@@ -165,7 +165,7 @@ struct Engine {
               Scalars* sc, const OpArgs& args, double* partials, unsigned* counter, int negate,
               cudaStream_t st) const {
     Ops<T>::line_fwd(g, pre, ff, S, plan[g.D - 1], tw[g.D - 1], g.D, mat, sc, args, st, nullptr,
-                     1, partials, counter);
+                     1, partials);
     if (mode == PROJ_GAMMA && two_line) {
       Ops<T>::strided_two_line(g, 0, S, plan[1], tw[1], sc, st);
       Ops<T>::proj_two_line(g, S, plan[0], tw[0], pg, sc, st);
