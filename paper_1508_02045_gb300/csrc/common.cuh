@@ -105,6 +105,7 @@ enum MatKind { MAT_PHASE_ISO = 0, MAT_PHASE_TENSOR = 1, MAT_FIELD = 2 };
 template <typename T>
 struct MatView {
   int kind;
+  int nphase;            // entries of the phase table (0: not known to the kernel)
   const uint8_t* ph8;
   const uint16_t* ph16;
   const T* table;        // nphase * d * d (tensor) or nphase (isotropic)

@@ -344,7 +344,9 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
       tab.assign(A->table, A->table + (size_t)A->nphase * d * d);
     }
     if ((st = alloc((void**)&P->d_table, sizeof(double) * tab.size())) != HOM_OK) { hom_destroy(P); return st; }
-    if ((st = alloc(&P->d_phase, (size_t)nodes * A->index_bytes)) != HOM_OK) { hom_destroy(P); return st; }
+    // 16 zero bytes past the end: kernels may read the phase indices in aligned words
+    if ((st = alloc(&P->d_phase, (size_t)nodes * A->index_bytes + 16)) != HOM_OK) { hom_destroy(P); return st; }
+    cudaMemset((char*)P->d_phase + (size_t)nodes * A->index_bytes, 0, 16);
     cudaMemcpy(P->d_table, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(P->d_phase, A->data, (size_t)nodes * A->index_bytes,
                A->data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);

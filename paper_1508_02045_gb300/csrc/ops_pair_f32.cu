@@ -139,7 +139,7 @@ int pair_line_fwd_f32(int D, int pre, const AxisPlan& P, const Fields<float>& f,
   if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
     constexpr int LB = 2 * pair_lbp<3, R2_>();                                                 \
     const dim3 grid((unsigned)((nlines + LB - 1) / LB), 1, (unsigned)nreq);                   \
-    const size_t sm = sizeof(cpx<T>) * (size_t)(R1_ * R2_) * (1 + 3 * pair_lbp<3, R2_>());      \
+    const size_t sm = PairFwdSmem<3, R1_, R2_>::bytes;                                         \
     constexpr int NT = pair_line_threads<3, R2_>();                                            \
     if (pre == PRE_CG) HOM_PAIR_LF_P(PRE_CG, R1_, R2_);                                        \
     else if (pre == PRE_CG_DOT) HOM_PAIR_LF_P(PRE_CG_DOT, R1_, R2_);                           \
@@ -168,7 +168,7 @@ void pair_line_inv_f32(int D, int post, const AxisPlan& P, const cpx<float>* S,
   if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
     constexpr int LB = 2 * pair_lbp<3, R2_>();                                                 \
     const dim3 grid((unsigned)((nlines + LB - 1) / LB), 1, (unsigned)nreq);                   \
-    const size_t sm = sizeof(cpx<T>) * (size_t)(R1_ * R2_) * (1 + 3 * pair_lbp<3, R2_>());      \
+    const size_t sm = PairFwdSmem<3, R1_, R2_>::bytes;                                         \
     constexpr int NT = pair_line_threads<3, R2_>();                                            \
     if (post == POST_CG) HOM_PAIR_LI_P(POST_CG, R1_, R2_);                                     \
     else if (post == POST_CG_FUSED) HOM_PAIR_LI_P(POST_CG_FUSED, R1_, R2_);                    \

@@ -10,6 +10,8 @@
 // Threads map to (column, butterfly) with the column fastest, so every row segment of a
 // warp's global access is contiguous.
 #pragma once
+#include <type_traits>
+
 #include "passes.cuh"
 
 namespace hom {
@@ -444,10 +446,126 @@ __host__ __device__ constexpr int pair_line_threads() {
   return (D * pair_lbp<D, R2>() * R2 + 31) / 32 * 32;
 }
 
-// pre-operator + forward real DFT of the contiguous axis: the pre-operator fills the complex
-// lines in shared memory, stage 1 runs in place (one butterfly per thread, all loads before a
-// barrier, then all stores), stage 2 in place (each butterfly reads and writes the same R2
-// rows), then the two packed real transforms are split and stored as half spectra
+// Shared memory of the specialised line_fwd pass, in floats from the 16-byte aligned base: the
+// n twiddles; the D x LBP complex lines, which the pre-operator first fills with the D real
+// tiles of LB x n nodes, component a at raw0 + a rstride + s_a where s_a (< 4) is the position
+// of the tile's first node within its 16-byte segment of the field, so that aligned 16-byte
+// vectors of the field are aligned in shared memory too (the tiles end at most 20 floats past
+// the complex lines); then a phase table of up to kPairTab entries. The whole stays within
+// 48 KiB for the 243-point plans, so that four CTAs fit the SM's 196 KiB shared-memory
+// configuration: a larger one leaves the kernels that follow with less L1 (a 228 KiB line_fwd
+// was measured to slow the next line_inv pass by a third).
+constexpr int kPairTab = 64;
+template <int D, int R1, int R2>
+struct PairFwdSmem {
+  static constexpr int n = R1 * R2, LBP = pair_lbp<D, R2>(), ntile = 2 * LBP * n;
+  static constexpr int raw0 = (2 * n + 3) / 4 * 4;
+  static constexpr int rstride = (ntile + 3) / 4 * 4 + 4;
+  static constexpr int tab = (2 * n + D * ntile + 20 + 3) / 4 * 4;
+  static constexpr int bytes = 4 * (tab + kPairTab);
+  static_assert(raw0 + (D - 1) * rstride + 3 + ntile <= 2 * n + D * ntile + 20,
+                "raw tiles overrun the line buffer's slack");
+};
+
+// v[a] for a runtime index a < D, by selects (no local-memory copy of v)
+template <int D>
+__device__ __forceinline__ int pick(const int (&v)[D], int a) {
+  int r = v[0];
+#pragma unroll
+  for (int i = 1; i < D; ++i) r = a == i ? v[i] : r;
+  return r;
+}
+
+// Pre-operator of the specialised line_fwd pass for isotropic phase materials with one-byte
+// phase indices and at most kPairTab phases, FP32: v = a(phase) w with w = x (PRE_LINEAR) or
+// w = r + beta p (CG, w stored as the new p). Each component's tile is one contiguous run of
+// nvalid floats of the field, read (and p written) as aligned 16-byte vectors, its unaligned
+// head and tail (at most 3 + 3 nodes) node by node; the four phase indices of a vector come from
+// the two aligned words that hold them (the phase array is padded by 16 bytes), the table is
+// staged in shared memory. x and p must lie at the same offset within 16 bytes (checked by the
+// caller).
+template <int D, int PRE, int K>
+__device__ __forceinline__ void pair_pre_vec(const Fields<float>& f, const float* xin,
+                                             float* smf, const int (&Fo)[D], long long g0,
+                                             int nvalid, int ntile, const MatView<float>& mat,
+                                             float beta, float* stab, DotAcc<float>* dacc) {
+  constexpr bool CG = PRE == PRE_CG || PRE == PRE_CG_DOT;
+  const int NT = blockDim.x, t = threadIdx.x;
+  for (int i = t; i < kPairTab; i += NT) stab[i] = i < mat.nphase ? mat.table[i] : 0.f;
+  // nodes of the last tile beyond the grid transform as zeros
+  for (int idx = nvalid + t; idx < ntile; idx += NT) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) smf[Fo[a] + idx] = 0.f;
+  }
+  __syncthreads();
+  const uint8_t* phg = mat.ph8 + g0;
+  const int phs = (int)((uintptr_t)phg & 3);
+  const uint32_t* phw = reinterpret_cast<const uint32_t*>(phg - phs);
+#pragma unroll 1
+  for (int a = 0; a < D; ++a) {
+    const float* xa = xin + a * f.cs + g0;
+    float* pa = CG ? f.p + a * f.cs + g0 : nullptr;
+    float* sa = smf + pick<D>(Fo, a);
+    const int h = min(nvalid, (int)((4 - (((uintptr_t)xa >> 2) & 3)) & 3));
+    const int nb = (nvalid - h) >> 2;
+    for (int c0 = t; c0 < nb; c0 += K * NT) {
+      float4 xv[K], pv[K];
+      uint32_t lo[K], hi[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int c = c0 + k * NT;
+        if (c < nb) {
+          xv[k] = __ldg(reinterpret_cast<const float4*>(xa + h + 4 * c));
+          if (CG) pv[k] = *reinterpret_cast<const float4*>(pa + h + 4 * c);
+          const int wi = (phs + h + 4 * c) >> 2;
+          lo[k] = __ldg(phw + wi);
+          hi[k] = __ldg(phw + wi + 1);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int c = c0 + k * NT;
+        if (c >= nb) continue;
+        const int idx = h + 4 * c;
+        const uint32_t ph4 = __funnelshift_r(lo[k], hi[k], ((phs + idx) & 3) * 8);
+        float w[4] = {xv[k].x, xv[k].y, xv[k].z, xv[k].w};
+        if (CG) {
+          w[0] = fmaf(beta, pv[k].x, w[0]);
+          w[1] = fmaf(beta, pv[k].y, w[1]);
+          w[2] = fmaf(beta, pv[k].z, w[2]);
+          w[3] = fmaf(beta, pv[k].w, w[3]);
+          *reinterpret_cast<float4*>(pa + idx) = make_float4(w[0], w[1], w[2], w[3]);
+        }
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          v[e] = stab[(ph4 >> (8 * e)) & (kPairTab - 1)] * w[e];
+          if (PRE == PRE_CG_DOT) dacc->add(w[e], v[e]);
+        }
+        *reinterpret_cast<float4*>(sa + idx) = make_float4(v[0], v[1], v[2], v[3]);
+      }
+    }
+    // head [0, h) and tail [h + 4 nb, nvalid), node by node
+    const int tail0 = h + 4 * nb, nedge = h + nvalid - tail0;
+    if (t < nedge) {
+      const int idx = t < h ? t : tail0 + (t - h);
+      float w = __ldg(xa + idx);
+      if (CG) {
+        w = fmaf(beta, pa[idx], w);
+        pa[idx] = w;
+      }
+      const float v = stab[phg[idx] & (kPairTab - 1)] * w;
+      if (PRE == PRE_CG_DOT) dacc->add(w, v);
+      sa[idx] = v;
+    }
+  }
+}
+
+// pre-operator + forward real DFT of the contiguous axis: the pre-operator fills the real tiles
+// in shared memory, stage 1 packs each line pair into one complex line on load and runs in
+// place (one butterfly per thread, all loads before a barrier, then all stores), stage 2 in
+// place (each butterfly reads and writes the same R2 rows), then the two packed real transforms
+// are split and stored as half spectra
 template <typename T, int D, int PRE, int R1, int R2>
 __global__ void __launch_bounds__(pair_line_threads<D, R2>(), 4)
 k_pair_line_fwd(Fields<T> f, cpx<T>* S, const cpx<T>* __restrict__ twg, long long nlines,
@@ -464,24 +582,45 @@ k_pair_line_fwd(Fields<T> f, cpx<T>* S, const cpx<T>* __restrict__ twg, long lon
     partials = R.partials;
   }
   if (sc != nullptr && sc->done) return;
+  using L = PairFwdSmem<D, R1, R2>;
+  constexpr bool CG = PRE == PRE_CG || PRE == PRE_CG_DOT;
   cpx<T>* sm = smem_c<T>();
   cpx<T>* tw = sm;
   cpx<T>* lines = sm + n;
+  T* smf = reinterpret_cast<T*>(sm);
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
   const long long l0 = (long long)blockIdx.x * LB;
+  const long long g0 = l0 * n;
+  const int nvalid = (int)min((long long)L::ntile, (nlines - l0) * n);
+  // the operand (as the pre-operator picks it: Richardson's current buffer of a pair)
+  const T* xin = (f.x != nullptr && sc != nullptr) ? f.x + (sc->which ? D * f.cs : 0) : f.xin;
+  int Fo[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+    Fo[a] = L::raw0 + a * L::rstride + (int)(((uintptr_t)(xin + a * f.cs + g0) >> 2) & 3);
   DotAcc<T> dacc;
-  line_pre_to_smem<T, D, PRE, kPairPreBatch, n>(f, n, n, LBP, D, l0, LB, nlines, fdn, mat, sc,
-                                                args, &dacc);
+  static_assert(std::is_same<T, float>::value, "the specialised line passes are FP32");
+  const bool vec = mat.kind == MAT_PHASE_ISO &&
+                   mat.ph8 != nullptr && mat.nphase >= 1 && mat.nphase <= kPairTab &&
+                   (!CG || ((((uintptr_t)xin ^ (uintptr_t)f.p) & 15) == 0));
+  if (vec) {
+    pair_pre_vec<D, PRE, kPairPreBatch>(f, xin, smf, Fo, g0, nvalid, L::ntile, mat,
+                                        sc != nullptr ? (T)sc->beta : (T)0, smf + L::tab, &dacc);
+  } else {
+    line_pre_to_smem<T, D, PRE, kPairPreBatch, n, true>(f, n, n, LBP, D, l0, LB, nlines, fdn, mat,
+                                                        sc, args, &dacc, Fo);
+  }
   __syncthreads();
   {
     const int t = threadIdx.x;
     const bool act = t < items1;
-    const int i = t % R2;
-    cpx<T>* line = lines + (t / R2) * n;
+    const int i = t % R2, lc = t / R2, a = lc / LBP, q = lc - a * LBP;
+    const T* re = smf + pick<D>(Fo, a) + 2 * q * n + i;  // even line of the pair: real part
+    cpx<T>* line = lines + lc * n;
     cpx<T> u[R1];
     if (act) {
 #pragma unroll
-      for (int r = 0; r < R1; ++r) u[r] = line[i + r * R2];
+      for (int r = 0; r < R1; ++r) u[r] = cpx<T>{re[r * R2], re[n + r * R2]};
       RegDft<T, R1>::run(u);
     }
     __syncthreads();

@@ -303,13 +303,17 @@ k_cg_alpha(const double* partials, int nblocks, long long count, Scalars* sc,
 // Pre-operator of the lines l0 .. l0 + LB - 1 (pointwise, coalesced loads in batches of K
 // nodes): component a of line l0 + ll goes to the real (ll even) or imaginary (ll odd) part of
 // the shared-memory complex line b0 + (a * half + ll / 2) * n, so that two real lines share one
-// complex transform.
-template <typename T, int D, int PRE, int K = (sizeof(T) == 4 ? 8 : 4), int NC = 0>
+// complex transform. RAW: component a of the tile is instead stored as it lies in the field,
+// node idx of the tile at element raw[a] + idx of shared memory (the specialised FP32 line pass
+// packs the line pairs when its first stage loads them).
+template <typename T, int D, int PRE, int K = (sizeof(T) == 4 ? 8 : 4), int NC = 0,
+          bool RAW = false>
 __device__ __forceinline__ void line_pre_to_smem(const Fields<T>& f, int b0, int n, int half,
                                                  int ncomp, long long l0, int LB, long long nlines,
                                                  FastDiv fdn, const MatView<T>& mat,
                                                  const Scalars* sc, const OpArgs& args,
-                                                 DotAcc<T>* dacc = nullptr) {
+                                                 DotAcc<T>* dacc = nullptr,
+                                                 const int* raw = nullptr) {
   constexpr bool CG = PRE == PRE_CG || PRE == PRE_CG_DOT;
   // NC > 0: the line length as a compile-time constant (specialised kernels)
   if (NC > 0) n = NC;
@@ -347,7 +351,6 @@ __device__ __forceinline__ void line_pre_to_smem(const Fields<T>& f, int b0, int
       const int idx = base + k * blockDim.x + threadIdx.x;
       if (idx >= ntile) continue;
       const bool ok = idx < nvalid;
-      const int ll = NC > 0 ? idx / NC : fdiv(idx, fdn), j = idx - ll * n;
       T v[D];
       if (PRE == PRE_IDENT) {
 #pragma unroll
@@ -377,12 +380,20 @@ __device__ __forceinline__ void line_pre_to_smem(const Fields<T>& f, int b0, int
           for (int a = 0; a < D; ++a) v[a] = 0;
         }
       }
+      if (RAW) {
+        T* smt = reinterpret_cast<T*>(sm);
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        if (a < ncomp) {
-          cpx<T>& e = sm[b0 + (a * half + (ll >> 1)) * n + j];
-          if (ll & 1) e.y = v[a];
-          else e.x = v[a];
+        for (int a = 0; a < D; ++a)
+          if (a < ncomp) smt[raw[a] + idx] = v[a];
+      } else {
+        const int ll = NC > 0 ? idx / NC : fdiv(idx, fdn), j = idx - ll * n;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          if (a < ncomp) {
+            cpx<T>& e = sm[b0 + (a * half + (ll >> 1)) * n + j];
+            if (ll & 1) e.y = v[a];
+            else e.x = v[a];
+          }
         }
       }
     }

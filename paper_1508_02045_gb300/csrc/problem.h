@@ -313,6 +313,7 @@ template <typename T>
 MatView<T> make_view(const hom_problem* P, const T* field, const T* table) {
   MatView<T> m{};
   m.kind = P->mat_kind;
+  m.nphase = P->mat_kind == MAT_FIELD ? 0 : P->nphase;
   m.ph8 = (P->mat_kind != MAT_FIELD && P->index_bytes == 1) ? (const uint8_t*)P->d_phase : nullptr;
   m.ph16 = (P->mat_kind != MAT_FIELD && P->index_bytes == 2) ? (const uint16_t*)P->d_phase : nullptr;
   m.table = table;
