@@ -159,6 +159,28 @@ int hom_solve_begin(hom_problem* P, const double* E, int solver, double tol, con
 int hom_solve_iterate(hom_problem* P, int iterations, int* done);
 int hom_solve_end(hom_problem* P, double* x_dev, double* AH_EE, double* flux, hom_stats* stats);
 
+/* Per-iteration diagnostics of the current (or last) session: the quantities behind the
+ * convergence studies of Section 4 (residual norms, 4.2; guaranteed upper bound, 4.3).
+ *
+ * hom_solve_history copies into the HOST array out (cap entries) the stopping quantity of
+ * every iteration, in the grid norm ||a||^2 = (1/|N|) sum_k |a^k|^2 of Section 1:
+ *   - CG and Chebyshev (Algorithms 2-3): ||r_m||, the recursively updated residual;
+ *   - Eyre-Milton, and Richardson stopping on the increment (Algorithms 4, 1): ||x_m - x_{m-1}||;
+ *   - Richardson stopping on the residual: ||C x_{m-1} - b|| as formed at the start of step m
+ *     (the last entry belongs to the returned iterate);
+ *   - HOM_FP32_REFINED: the FP64 residual ||b - C x|| after each outer update.
+ * *count receives the number of entries recorded (at most 2^20 are kept; none beyond cap are
+ * written); 0 before any solve. Synchronises the stream.
+ *
+ * hom_solve_current writes the current iterate (d x |M| doubles, device x_dev) of an active
+ * session, as hom_solve_end would return it at this point: x_m for Richardson, CG and
+ * Chebyshev, G x_m for Eyre-Milton (Section 4.4), the FP64 iterate of the last outer update in
+ * HOM_FP32_REFINED mode. With hom_energy and hom_bound it gives the energy and the guaranteed
+ * upper bound of every iterate (eq. (guar_upper_bound_m)). Synchronises the stream;
+ * HOM_ERR_INVALID without an active session. */
+int hom_solve_history(hom_problem* P, double* out, int cap, int* count);
+int hom_solve_current(hom_problem* P, double* x_dev);
+
 /* Energy (A(E + x), E + x) and flux <A(E + x)> of a device field x_dev on the solve grid
  * (x_dev may be NULL for x = 0, the Voigt value of Section 4.3). Synchronises the stream. */
 int hom_energy(hom_problem* P, const double* E, const double* x_dev, double* energy, double* flux);

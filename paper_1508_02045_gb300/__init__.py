@@ -34,7 +34,8 @@ EXPORTED = ["hom_create", "hom_grid", "hom_bounds", "hom_apply", "hom_solve", "h
             "hom_profile_enable", "hom_profile_read", "hom_solve_begin", "hom_solve_iterate",
             "hom_solve_end", "hom_apply_static", "hom_batch_create", "hom_batch_iterate",
             "hom_batch_destroy", "hom_server_create", "hom_server_submit", "hom_server_step",
-            "hom_server_poll", "hom_server_status", "hom_server_destroy", "hom_autotune"]
+            "hom_server_poll", "hom_server_status", "hom_server_destroy", "hom_autotune",
+            "hom_solve_history", "hom_solve_current"]
 PASS_KINDS = ["line_fwd", "strided", "proj", "line_inv", "vector"]
 
 
@@ -111,6 +112,8 @@ def _load():
     lib.hom_solve_begin.argtypes = [vp, dp, ip, ctypes.c_double, ctypes.POINTER(hom_opts)]
     lib.hom_solve_iterate.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]
     lib.hom_solve_end.argtypes = [vp, vp, dp, dp, ctypes.POINTER(hom_stats)]
+    lib.hom_solve_history.argtypes = [vp, dp, ip, ctypes.POINTER(ctypes.c_int)]
+    lib.hom_solve_current.argtypes = [vp, vp]
     lib.hom_prolongate.argtypes = [vp, vp, vp, vp]
     lib.hom_bound.argtypes = [vp, vp, dp, vp, dp]
     lib.hom_destroy.argtypes = [vp]
@@ -252,6 +255,22 @@ def hom_solve_iterate(P, iterations, poll=False):
     _check(_lib.hom_solve_iterate(P, int(iterations), ctypes.byref(done) if poll else None),
            "hom_solve_iterate")
     return bool(done.value) if poll else None
+
+
+def hom_solve_history(P, cap=1 << 20):
+    """The per-iteration stopping quantity of the current or last solve (numpy array)."""
+    import numpy as np
+    count = ctypes.c_int(0)
+    _check(_lib.hom_solve_history(P, None, 0, ctypes.byref(count)), "hom_solve_history")
+    n = min(count.value, int(cap))
+    buf = (ctypes.c_double * max(n, 1))()
+    _check(_lib.hom_solve_history(P, buf, n, ctypes.byref(count)), "hom_solve_history")
+    return np.array(buf[:n], dtype=np.float64)
+
+
+def hom_solve_current(P, x):
+    """Write the current iterate of the active session into the device tensor x."""
+    return _check(_lib.hom_solve_current(P, _ptr(x)), "hom_solve_current")
 
 
 def hom_solve_end(P, d, x=None, allow_not_converged=False):

@@ -89,6 +89,9 @@ struct Scalars {
   int stop;           // 1 residual, 2 increment
   int which;          // Richardson: which of the two x buffers holds x_m
   int result;         // Richardson: buffer holding the returned iterate
+  double* hist;       // per-iteration stopping quantity (device, hist_cap entries) or null
+  int hist_cap;
+  int nhist;          // entries recorded (may exceed hist_cap; the excess is not stored)
 };
 
 // PRE_CG_DOT / POST_CG_FUSED: the CG step of the FP32 inner solves with the vector update

@@ -232,6 +232,7 @@ void hom_destroy(hom_problem* P) {
   for (auto& v : P->fvec)
     if (v) cudaFree(v);
   if (P->partials) cudaFree(P->partials);
+  if (P->d_hist) cudaFree(P->d_hist);
   if (P->counter) cudaFree(P->counter);
   if (P->d_sc) cudaFree(P->d_sc);
   if (P->d_aux) cudaFree(P->d_aux);
@@ -736,6 +737,7 @@ int refine_outer_update(hom_problem* P) {
                 nullptr, nullptr, 0, P->stream);
   S_.matvecs += 1;
   if ((rc = refine_residual(P, &S_.res))) return rc;
+  S_.outer_hist.push_back(S_.res);
   S_.outer_it += 1;
   if (S_.res <= S_.tol * S_.nb) {
     S_.finished = true;
@@ -829,8 +831,22 @@ extern "C" int hom_solve_begin(hom_problem* P, const double* E, int solver, doub
     s.alpha = 1.0 / s.cheb_d;
     s.beta = -0.5 * (s.cheb_c / s.cheb_d) * (s.cheb_c / s.cheb_d);
   }
+  // the history of the stopping quantity: one entry an iteration (Richardson on the residual:
+  // one more, the residual of the last iterate), at most kHistMax kept
+  const int hcap = (int)std::min<long long>((long long)S_.maxit + 2, kHistMax);
+  if (hcap > P->hist_alloc) {
+    if (P->d_hist) cudaFree(P->d_hist);
+    P->d_hist = nullptr;
+    P->hist_alloc = 0;
+    int ar = alloc((void**)&P->d_hist, sizeof(double) * (size_t)hcap);
+    if (ar != HOM_OK) return ar;
+    P->hist_alloc = hcap;
+  }
+  s.hist = P->d_hist;
+  s.hist_cap = P->hist_alloc;
   int rc = upload_scalars(P, P->d_sc, s);
   if (rc) return rc;
+  S_.solver_begun = true;
   HOM_CUDA(cudaEventRecord(P->ev0, st));
   if (solver == HOM_EYRE_MILTON) {
     Ops<double>::fill_const(x, nodes, d, P->d_sc, st);  // x_0 = E
@@ -973,6 +989,57 @@ extern "C" int hom_solve_end(hom_problem* P, double* x_dev, double* AH_EE, doubl
   }
   if ((rc = check_last())) return rc;
   return (fin.converged || S_.fixed) ? HOM_OK : HOM_ERR_NOT_CONVERGED;
+}
+
+extern "C" int hom_solve_history(hom_problem* P, double* out, int cap, int* count) {
+  if (!P || cap < 0 || (cap > 0 && !out)) return HOM_ERR_INVALID;
+  SolveState& S_ = P->sv;
+  int n = 0;
+  if (S_.refined) {
+    n = (int)S_.outer_hist.size();
+    for (int i = 0; i < std::min(n, cap); ++i) out[i] = S_.outer_hist[i];
+  } else if (S_.solver_begun) {
+    int rc = poll(P, P->d_sc);
+    if (rc) return rc;
+    n = P->h_sc->nhist;
+    const int m = std::min(std::min(n, cap), P->hist_alloc);
+    if (m > 0) {
+      HOM_CUDA(cudaMemcpyAsync(out, P->d_hist, sizeof(double) * (size_t)m,
+                               cudaMemcpyDeviceToHost, P->stream));
+      HOM_CUDA(cudaStreamSynchronize(P->stream));
+    }
+  }
+  if (count) *count = n;
+  return check_last();
+}
+
+extern "C" int hom_solve_current(hom_problem* P, double* x_dev) {
+  if (!P || !x_dev || !P->sv.active) return HOM_ERR_INVALID;
+  SolveState& S_ = P->sv;
+  const long long nodes = P->nodes;
+  const long long len = (long long)P->d * nodes;
+  cudaStream_t st = P->stream;
+  const double* cur = P->vec[0];
+  if (!S_.refined) {
+    int rc = poll(P, P->d_sc);
+    if (rc) return rc;
+    if (S_.solver == HOM_RICHARDSON) cur = P->vec[0] + (P->h_sc->result ? len : 0);
+    if (S_.solver == HOM_EYRE_MILTON) {
+      // e = G x_m (Section 4.4), as the end of the solve returns it
+      Fields<double> fp{};
+      fp.xin = P->vec[0];
+      fp.out = x_dev;
+      fp.cs = nodes;
+      OpArgs args{};
+      P->e64.apply(PRE_IDENT, PROJ_GAMMA, POST_STORE, fp, (cpx<double>*)P->S, nullptr, args,
+                   nullptr, nullptr, 0, st);
+      HOM_CUDA(cudaStreamSynchronize(st));
+      return check_last();
+    }
+  }
+  HOM_CUDA(cudaMemcpyAsync(x_dev, cur, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
+  HOM_CUDA(cudaStreamSynchronize(st));
+  return check_last();
 }
 
 extern "C" int hom_solve(hom_problem* P, const double* E, int solver, double tol,

@@ -341,6 +341,9 @@ size_t estimate_bytes(const hom_request& r) {
   b += sizeof(double) * 2 * r.d * nl * ((nlast + 1) / 2);          // half spectrum
   b += nodes * 2 + sizeof(double) * nodes;                         // phases / coefficient field
   if (r.precision == HOM_FP32_REFINED) b += sizeof(float) * (4 * r.d + 1) * nodes;
+  const long long maxit = r.opts.fixed_iters > 0 ? r.opts.fixed_iters
+                                                 : (r.opts.maxit > 0 ? r.opts.maxit : 100000);
+  b += sizeof(double) * (size_t)std::min<long long>(maxit + 2, kHistMax);  // iteration history
   return b + (4u << 20);                                           // partials, plans, tables
 }
 

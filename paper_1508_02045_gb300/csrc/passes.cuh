@@ -807,6 +807,12 @@ __device__ __forceinline__ void line_post_from_smem(const Fields<T>& f, int res,
   }
 }
 
+// the stopping quantity of one iteration into the solve's history (if it keeps one)
+__device__ __forceinline__ void record_history(Scalars* sc, double v) {
+  if (sc->hist != nullptr && sc->nhist < sc->hist_cap) sc->hist[sc->nhist] = v;
+  sc->nhist += 1;
+}
+
 // The scalar part of the solver step after a post-operator, run by one thread of the last CTA
 // with the grid's reduced inner product tot0 over `count` nodes (Algorithms 1-4).
 template <int POST>
@@ -820,6 +826,7 @@ __device__ __forceinline__ void line_inv_finish(Scalars* sc, double tot0, double
   } else if (POST == POST_RICH) {
     const double res = sqrt(mean);  // ||C x_{m-1} - b||
     sc->last_res = res;
+    if (sc->stop == 1) record_history(sc, res);
     if (!sc->fixed && sc->stop == 1 && res <= sc->tol * sc->nb) {
       sc->done = 1;
       sc->converged = 1;
@@ -831,6 +838,7 @@ __device__ __forceinline__ void line_inv_finish(Scalars* sc, double tot0, double
     sc->result = sc->which;
     const double inc = sc->omega * res;  // ||x_m - x_{m-1}||
     sc->last_inc = inc;
+    if (sc->stop == 2) record_history(sc, inc);
     if (sc->fixed) {
       if (sc->it >= sc->maxit) sc->done = 1;
     } else if (sc->stop == 2 && inc <= sc->tol * sc->nE) {
@@ -846,6 +854,7 @@ __device__ __forceinline__ void line_inv_finish(Scalars* sc, double tot0, double
     // x += alpha p, r -= alpha C p done above; (r, r), the stopping test and beta
     const double res = sqrt(mean);
     sc->last_res = res;
+    record_history(sc, res);
     sc->it += 1;
     if (sc->fixed) {
       if (sc->it >= sc->maxit) sc->done = 1;
@@ -860,6 +869,7 @@ __device__ __forceinline__ void line_inv_finish(Scalars* sc, double tot0, double
   } else if (POST == POST_CHEB) {
     const double res = sqrt(mean);
     sc->last_res = res;
+    record_history(sc, res);
     sc->it += 1;
     if (sc->fixed) {
       if (sc->it >= sc->maxit) sc->done = 1;
@@ -876,6 +886,7 @@ __device__ __forceinline__ void line_inv_finish(Scalars* sc, double tot0, double
   } else if (POST == POST_EM) {
     const double inc = sqrt(mean);
     sc->last_inc = inc;
+    record_history(sc, inc);
     sc->it += 1;
     if (sc->fixed) {
       if (sc->it >= sc->maxit) sc->done = 1;
@@ -1013,6 +1024,7 @@ k_cg_update(T* x, T* r, const T* p, const T* q, long long len, long long nodes, 
   const double rr_new = tot[0] / (double)nodes;
   const double res = sqrt(rr_new);
   sc->last_res = res;
+  record_history(sc, res);
   sc->it += 1;
   if (sc->fixed) {
     if (sc->it >= sc->maxit) sc->done = 1;

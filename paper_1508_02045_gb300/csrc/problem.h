@@ -242,8 +242,12 @@ bool spd_eigs(const double* t, int d, double* lo, double* hi);
 }  // namespace detail
 }  // namespace hom
 
+// entries of the per-iteration history a solve keeps at most (8 MiB of doubles)
+constexpr int kHistMax = 1 << 20;
+
 struct SolveState {
   bool active = false;
+  bool solver_begun = false;  // the FP64 scalars (and history) belong to this solve
   int solver = 0;
   int stop = 0;
   bool fixed = false;
@@ -262,6 +266,7 @@ struct SolveState {
   int inner_total = 0;
   double nb = 0;         // ||b|| (FP64)
   double res = 0;        // ||b - C x|| (FP64) after the last outer update
+  std::vector<double> outer_hist;  // res after each outer update
   bool finished = false;
   bool converged = false;
   float inner_ms = 0;
@@ -295,6 +300,8 @@ struct hom_problem {
   double* vec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // d x |grid| each
   float* fvec[4] = {nullptr, nullptr, nullptr, nullptr};           // FP32 inner solves
   double* partials = nullptr;
+  double* d_hist = nullptr;  // per-iteration history of the FP64 solvers
+  int hist_alloc = 0;
   size_t npartials = 0;
   unsigned* counter = nullptr;
   hom::Scalars* d_sc = nullptr;        // solver scalars
