@@ -150,3 +150,85 @@ def test_refined_history_is_the_outer_residual():
     assert abs(hist[-1] / nb - stats["residual"]) < 1e-6 * stats["residual"]
     assert hist[-1] <= tol * nb and hist[-2] > tol * nb
     P.close()
+
+
+def ga_square(N, h, lo, hi):
+    d = len(N)
+    M = O.double_grid(N)
+    Ahat = ms.box_fourier_coefficients(M, h, lo, hi)
+    P = H.Problem(d, N, H.fourier_material(Ahat.astype(np.complex128), lo, hi, M), H.HOM_EXACT)
+    return P, O.Ga(O.ga_coefficients(Ahat, d), N, d)
+
+
+@pytest.mark.parametrize("solver,monotone", [("cg", True), ("richardson", True),
+                                             ("chebyshev", False)])
+def test_ga_upper_bound_monotonicity(solver, monotone):
+    # Table of Section 5: on Ga the bound U_E(x_m) decreases monotonically for Richardson and
+    # CG and not for Chebyshev (23^2 square on 45^2, contrast 100), on both sides, iterate by
+    # iterate
+    N = (23, 23)
+    lo, hi = 1.0, 100.0
+    P, sysg = ga_square(N, 0.6, lo, hi)
+    E = np.array([1.0, 0.0])
+    steps = 25
+    H.hom_solve_begin(P.h, E, H.SOLVERS[solver], 0.0, H.make_opts(fixed_iters=steps))
+    if solver == "cg":
+        r = O.cg(sysg, E, fixed_iters=steps, keep_iterates=True)
+    elif solver == "richardson":
+        r = O.richardson(sysg, E, lo, hi, fixed_iters=steps, keep_iterates=True)
+    else:
+        r = O.chebyshev(sysg, E, lo, hi, fixed_iters=steps, keep_iterates=True)
+    x = P.field()
+    u, u_ref = [], []
+    for m in range(steps):
+        H.hom_solve_iterate(P.h, 1)
+        H.hom_solve_current(P.h, x)
+        u.append(H.hom_energy(P.h, E, x)[0])
+        u_ref.append(sysg.energy(E, r.iterates[m]))
+    H.hom_solve_end(P.h, 2)
+    u, u_ref = np.array(u), np.array(u_ref)
+    assert np.max(np.abs(u - u_ref) / u_ref) < 1e-10
+    rise = np.max(np.diff(u)) / u[0]
+    if monotone:
+        assert rise <= 1e-13
+    else:
+        assert rise > 1e-3 and np.max(np.diff(u_ref)) / u_ref[0] > 1e-3
+    P.close()
+
+
+def test_iterations_against_contrast_match_oracle():
+    # Section 4.6 on the square inclusion: iterations to the relative residual 1e-6 (Eyre-Milton
+    # on its increment) for contrast 10 and 1000, GaNi and Ga, against the oracle's counts; and
+    # the O(kappa) / O(sqrt(kappa)) growth
+    N = (15, 15)
+    E = np.array([1.0, 0.0])
+    tol = 1e-6
+    its = {}
+    for kappa in (10.0, 1000.0):
+        ph, table, A = square(N, 0.6, 1.0, kappa)
+        Pn = H.Problem(2, N, H.phase_material(ph, table))
+        Pg, sysg = ga_square(N, 0.6, 1.0, kappa)
+        sysn = O.GaNi(A, 2)
+        for disc, P, sy in (("gani", Pn, sysn), ("ga", Pg, sysg)):
+            for s in ("richardson", "cg", "chebyshev", "eyre_milton"):
+                if disc == "ga" and s == "eyre_milton":
+                    continue
+                stop = H.HOM_STOP_INCREMENT if s == "eyre_milton" else H.HOM_STOP_RESIDUAL
+                _, _, st, _ = H.hom_solve(P.h, E, H.SOLVERS[s], tol, H.make_opts(stop=stop))
+                if s == "richardson":
+                    ref = O.richardson(sy, E, 1.0, kappa, tol=tol, stop="residual").iterations
+                elif s == "cg":
+                    ref = O.cg(sy, E, tol=tol).iterations
+                elif s == "chebyshev":
+                    ref = O.chebyshev(sy, E, 1.0, kappa, tol=tol).iterations
+                else:
+                    ref = O.eyre_milton(sy, E, 1.0, kappa, tol=tol).iterations
+                assert abs(st["iterations"] - ref) <= 1, (disc, s, kappa, st["iterations"], ref)
+                its[(disc, s, kappa)] = st["iterations"]
+        Pn.close()
+        Pg.close()
+    growth = {k[:2]: its[k[:2] + (1000.0,)] / its[k[:2] + (10.0,)] for k in its if k[2] == 10.0}
+    assert growth[("gani", "richardson")] > 30 and growth[("ga", "richardson")] > 30
+    for k, g in growth.items():
+        if k[1] != "richardson":
+            assert g < 15, (k, g)
