@@ -16,7 +16,7 @@ __all__ = [
     "signed_index", "dft_matrix", "dft", "idft", "frequencies", "gamma_apply", "project",
     "apply_A", "expand_phase", "GaNi", "Ga", "prolongate", "energy", "richardson", "cg",
     "chebyshev", "eyre_milton", "SolveResult", "spectral_bounds", "double_grid",
-    "ga_coefficients",
+    "ga_coefficients", "voxel_fourier_coefficients",
 ]
 
 
@@ -134,6 +134,33 @@ def ga_coefficients(Ahat: np.ndarray, nspatial: int) -> np.ndarray:
     coefficients A^(n) given on Z_M; scalar (M...) or tensor (d, d, M...). Real part kept (the
     coefficients of a real field are Hermitian)."""
     return idft(Ahat, nspatial).real
+
+
+def voxel_fourier_coefficients(a: np.ndarray, M) -> np.ndarray:
+    """Fourier coefficients A^(n), n in Z_M (FFT-natural order), of the voxel-wise constant
+    scalar coefficient that takes the value a[k] on the cell of side 1/N_a centred at the node
+    x = k/N (the pixel/voxel images for which Section 2.2 assembles eq. (Ga_exact_integration)
+    by FFT). Integrating exp(-2 pi i n.x) (eq. (FT_def)) over one cell gives
+    prod_a sinc(pi n_a / N_a) exp(-2 pi i n.k/N) / |N|, so
+    A^(n) = prod_a sinc(pi n_a / N_a) (F_N a)(n mod N), with F_N the DFT of eq. (DFT) and
+    sinc(t) = sin(t)/t. Parity pinned by brute-force quadrature and by the analytic box
+    coefficients of an inclusion made of whole voxels (tests/test_oracle_transforms.py)."""
+    N = a.shape
+    d = len(N)
+    ah = dft(np.asarray(a, dtype=np.float64), d)
+    pos, sinc = [], []
+    for ax in range(d):
+        n = signed_index(int(M[ax]))
+        if M[ax] < N[ax]:
+            raise ValueError("the coefficient grid must contain Z_N")
+        pos.append(np.mod(n, N[ax]))                    # storage position of n mod N
+        s = [1] * d
+        s[ax] = int(M[ax])
+        sinc.append(np.sinc(n / N[ax]).reshape(s))       # numpy sinc(u) = sin(pi u)/(pi u)
+    out = ah[np.ix_(*pos)]
+    for f in sinc:
+        out = out * f
+    return out
 
 
 def spectral_bounds(A: np.ndarray, d: int) -> tuple[float, float]:

@@ -155,3 +155,45 @@ def test_ga_coefficients_mean_is_exact_voigt():
     M = O.double_grid(N)
     A_M = O.ga_coefficients(ms.box_fourier_coefficients(M, 0.6, 1.0, 100.0), 2)
     assert abs(A_M.mean() - (1.0 + 99.0 * 0.36)) < 1e-12
+
+
+def test_voxel_fourier_coefficients_quadrature():
+    # eq. (FT_def) for a random voxel image on (3, 5), integrated by a fine midpoint rule whose
+    # sub-cells tile every voxel cell [k/N - 1/(2N), k/N + 1/(2N)) (no reuse of the sinc form)
+    N = (3, 5)
+    M = (7, 11)
+    a = np.random.default_rng(3).uniform(1.0, 10.0, N)
+    coef = O.voxel_fourier_coefficients(a, M)
+    S = 200
+    xs = [(np.arange(n * S) + 0.5) / (n * S) - 0.5 / n for n in N]  # sub-cell midpoints
+    cell = [np.mod(np.floor(x * n + 0.5).astype(int), n) for x, n in zip(xs, N)]
+    f = a[np.ix_(cell[0], cell[1])]
+    for j0, n0 in enumerate(O.signed_index(M[0])):
+        e0 = np.exp(-2j * np.pi * n0 * xs[0])
+        for j1, n1 in enumerate(O.signed_index(M[1])):
+            e1 = np.exp(-2j * np.pi * n1 * xs[1])
+            ref = np.mean(f * np.outer(e0, e1))
+            assert abs(coef[j0, j1] - ref) < 2e-4 * abs(a).max(), (n0, n1)
+    assert abs(coef[0, 0] - a.mean()) < 1e-14 * a.mean()
+
+
+@pytest.mark.parametrize("N,h", [((15, 15), 0.6), ((9, 7, 5), 5 / 9)])
+def test_voxel_coefficients_of_whole_voxel_box_are_analytic(N, h):
+    # a centred box of whole voxels (side s_a = count_a / N_a on axis a): its voxel image and
+    # the analytic coefficients of the box, delta_{n0} a_m + (a_i - a_m) prod_a s_a sinc(pi n_a
+    # s_a), are the same function
+    d = len(N)
+    M = O.double_grid(N)
+    ph = ms.box_phase(N, h)
+    sides = [int(np.count_nonzero(np.abs(O.signed_index(n)) / n < h / 2)) / n for n in N]
+    a = np.where(ph > 0, 10.0, 1.0)
+    got = O.voxel_fourier_coefficients(a, M)
+    k = O.frequencies(M)
+    box = np.ones(M)
+    for ax, s_ in enumerate(sides):
+        box = box * (s_ * np.sinc(k[ax] * s_))
+    delta = np.zeros(M)
+    delta[(0,) * d] = 1.0
+    np.testing.assert_allclose(got, delta + 9.0 * box, atol=1e-13)
+    if np.allclose(sides, h):  # the microstructure module's analytic box coefficients
+        np.testing.assert_allclose(got, ms.box_fourier_coefficients(M, h, 1.0, 10.0), atol=1e-13)
