@@ -124,7 +124,12 @@ typedef enum {
  * A_M^k = sum_n omega_M^{kn} A^(n) with the library's inverse FFT, eq. (Ga_exact_integration)),
  * plans the odd-length FFTs and allocates the solver state (Section 3 storage) and one
  * half-spectrum work buffer. stream: a cudaStream_t or NULL for the legacy default stream.
- * Errors: HOM_ERR_INVALID, HOM_ERR_OOM, HOM_ERR_CUDA; *out is set only on HOM_OK. */
+ * Ga takes A^(n) directly (HOM_A_FOURIER) or an image: with HOM_A_PHASE (scalar tables only) or
+ * HOM_A_SCALAR the coefficient is constant on the cell of side 1/N around each node, whose
+ * coefficients are A^(n) = prod_a sinc(pi n_a / N_a) (F_N a)(n mod N) (the cell integral of
+ * eq. (FT_def); the image's DFT F_N of eq. (DFT) runs on the device). Errors: HOM_ERR_INVALID,
+ * HOM_ERR_OOM, HOM_ERR_CUDA, HOM_ERR_UNSUPPORTED (Ga of a tensor table); *out is set only on
+ * HOM_OK. */
 int hom_create(int d, const int* N, const hom_material* A, int integration, int precision,
                void* stream, hom_problem** out);
 

@@ -391,7 +391,9 @@ def hom_destroy(P):
 # material descriptors (marshalling of host arrays; the arrays must outlive hom_create)
 # ------------------------------------------------------------------------------------------
 
-def phase_material(phase: np.ndarray, table: np.ndarray, cA=0.0, CA=0.0):
+def phase_material(phase: np.ndarray, table: np.ndarray, cA=0.0, CA=0.0, M=None):
+    """Phase image + table. With HOM_EXACT (scalar tables): the voxel-wise constant coefficient,
+    integrated exactly on the grid M (default 2N - 1)."""
     phase = np.ascontiguousarray(phase)
     if phase.dtype not in (np.uint8, np.uint16):
         raise ValueError("phase image must be uint8 or uint16")
@@ -403,16 +405,22 @@ def phase_material(phase: np.ndarray, table: np.ndarray, cA=0.0, CA=0.0):
     m.table = table.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     m.nphase = table.shape[0]
     m.cA, m.CA = cA, CA
+    if M is not None:
+        for i, v in enumerate(M):
+            m.M[i] = int(v)
     m._keep = (phase, table)
     return m
 
 
-def scalar_material(a: np.ndarray, cA=0.0, CA=0.0):
+def scalar_material(a: np.ndarray, cA=0.0, CA=0.0, M=None):
     a = np.ascontiguousarray(a, dtype=np.float64)
     m = hom_material()
     m.kind = HOM_A_SCALAR
     m.data = a.ctypes.data
     m.cA, m.CA = cA, CA
+    if M is not None:
+        for i, v in enumerate(M):
+            m.M[i] = int(v)
     m._keep = (a,)
     return m
 

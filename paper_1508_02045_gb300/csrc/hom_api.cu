@@ -156,6 +156,82 @@ PlanChoice plan_choice(int pb, int d, const int* M, const int* N) {
   return PlanChoice{pb == 8 ? 15 : 27, 110 * 1024, kThreads, true};
 }
 
+// Half spectrum on the grid M of the Fourier coefficients of a voxel-wise constant scalar
+// coefficient a on the grid N (value a[k] on the cell of side 1/N centred at x = k/N): the cell
+// integral of exp(-2 pi i n.x) (eq. (FT_def)) gives A^(n) = prod_a sinc(pi n_a / N_a)
+// (F_N a)(n mod N), F_N the DFT of eq. (DFT) with its 1/|N|. F_N a comes from the library's
+// forward transform on N; n mod N above the stored half of the last axis is read through
+// Hermitian symmetry. Layout of `half`: M-grid lines (axes 0 .. d-2, row-major) x (M_last+1)/2.
+int voxel_coefficients(hom_problem* P, const std::vector<double>& a,
+                       std::vector<cpx<double>>& half) {
+  const int d = P->d;
+  const int* N = P->N;
+  const int* M = P->M;
+  long long nN = 1;
+  for (int ax = 0; ax < d; ++ax) nN *= N[ax];
+  const int nhN = (N[d - 1] + 1) / 2, mh = (M[d - 1] + 1) / 2;
+  const long long nlN = nN / N[d - 1];
+  Engine<double> eN;
+  const PlanChoice pc = plan_choice(8, d, N, N);
+  int st = eN.init(d, N, N, pc.budget, pc.rmax, pc.threads, pc.two_line);
+  double* a_dev = nullptr;
+  cpx<double>* s_dev = nullptr;
+  if (st == HOM_OK) st = alloc((void**)&a_dev, sizeof(double) * nN);
+  if (st == HOM_OK) st = alloc((void**)&s_dev, sizeof(cpx<double>) * nlN * nhN);
+  std::vector<cpx<double>> sN((size_t)nlN * nhN);
+  if (st == HOM_OK) {
+    cudaMemcpy(a_dev, a.data(), sizeof(double) * nN, cudaMemcpyHostToDevice);
+    eN.forward(a_dev, s_dev, 1, P->stream);
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess || check_last() != HOM_OK) st = HOM_ERR_CUDA;
+    else cudaMemcpy(sN.data(), s_dev, sizeof(cpx<double>) * sN.size(), cudaMemcpyDeviceToHost);
+  }
+  if (a_dev) cudaFree(a_dev);
+  if (s_dev) cudaFree(s_dev);
+  eN.release();
+  if (st != HOM_OK) return st;
+  const double inv = 1.0 / (double)nN;
+  const double pi = 3.14159265358979323846;
+  // per-axis factors of the M-grid storage positions: n mod N and sinc(pi n / N)
+  std::vector<int> pos[3];
+  std::vector<double> sinc[3];
+  for (int ax = 0; ax < d; ++ax) {
+    pos[ax].resize(M[ax]);
+    sinc[ax].resize(M[ax]);
+    for (int j = 0; j < M[ax]; ++j) {
+      const int n = j <= (M[ax] - 1) / 2 ? j : j - M[ax];
+      pos[ax][j] = ((n % N[ax]) + N[ax]) % N[ax];
+      const double t = pi * (double)n / (double)N[ax];
+      sinc[ax][j] = n == 0 ? 1.0 : std::sin(t) / t;
+    }
+  }
+  const long long nlM = (long long)half.size() / mh;
+  for (long long l = 0; l < nlM; ++l) {
+    // M-grid line l -> storage positions j_0 .. j_{d-2}
+    int j[2] = {0, 0};
+    if (d == 2) j[0] = (int)l;
+    else { j[0] = (int)(l / M[1]); j[1] = (int)(l % M[1]); }
+    double f = 1.0;
+    for (int ax = 0; ax < d - 1; ++ax) f *= sinc[ax][j[ax]];
+    for (int k = 0; k < mh; ++k) {
+      const int ml = pos[d - 1][k];
+      cpx<double> v;
+      if (ml < nhN) {
+        long long lN = d == 2 ? pos[0][j[0]] : (long long)pos[0][j[0]] * N[1] + pos[1][j[1]];
+        v = sN[lN * nhN + ml];
+      } else {  // X(m) = conj X(-m) for the real image
+        const int q0 = (N[0] - pos[0][j[0]]) % N[0];
+        long long lN = q0;
+        if (d == 3) lN = (long long)q0 * N[1] + (N[1] - pos[1][j[1]]) % N[1];
+        v = sN[lN * nhN + (N[d - 1] - ml)];
+        v.y = -v.y;
+      }
+      const double c = f * sinc[d - 1][k] * inv;
+      half[l * mh + k] = cpx<double>{v.x * c, v.y * c};
+    }
+  }
+  return HOM_OK;
+}
+
 }  // namespace detail
 }  // namespace hom
 
@@ -268,8 +344,22 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
   if (precision != HOM_FP64 && precision != HOM_FP32_REFINED) return HOM_ERR_INVALID;
   for (int a = 0; a < d; ++a)
     if (N[a] < 3 || N[a] % 2 == 0 || N[a] > kMaxAxis) return HOM_ERR_INVALID;
-  if (integration == HOM_EXACT && A->kind != HOM_A_FOURIER) return HOM_ERR_UNSUPPORTED;
   if (integration == HOM_APPROX && A->kind == HOM_A_FOURIER) return HOM_ERR_INVALID;
+  // exact integration of an image (voxel-wise constant coefficients): scalar coefficients only
+  const bool voxel_ga = integration == HOM_EXACT && A->kind != HOM_A_FOURIER;
+  if (voxel_ga) {
+    if (A->kind != HOM_A_PHASE && A->kind != HOM_A_SCALAR) return HOM_ERR_INVALID;
+    if (A->kind == HOM_A_PHASE) {
+      if (!A->table || A->nphase < 1) return HOM_ERR_INVALID;
+      for (int p = 0; p < A->nphase; ++p) {
+        const double* t = A->table + (size_t)p * d * d;
+        for (int i = 0; i < d; ++i)
+          for (int j = 0; j < d; ++j)
+            if ((i != j && t[i * d + j] != 0.0) || (i == j && t[i * d + j] != t[0]))
+              return HOM_ERR_UNSUPPORTED;
+      }
+    }
+  }
 
   std::call_once(g_const_once, [] {
     g_const_err = Ops<double>::upload_constants();
@@ -310,9 +400,44 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
   }
   const long long nodes = P->nodes;
   int st;
+  long long nN = 1;  // nodes of the image grid N
+  for (int a = 0; a < d; ++a) nN *= P->N[a];
+  std::vector<double> voxel;  // voxel_ga: the image's scalar coefficient on the N grid
 
   // ---- coefficients ----
-  if (A->kind == HOM_A_PHASE) {
+  if (voxel_ga) {
+    if (!A->data || (A->kind == HOM_A_PHASE && A->index_bytes != 1 && A->index_bytes != 2)) {
+      delete P;
+      return HOM_ERR_INVALID;
+    }
+    voxel.resize(nN);
+    if (A->kind == HOM_A_SCALAR) {
+      if (A->data_on_device)
+        cudaMemcpy(voxel.data(), A->data, sizeof(double) * nN, cudaMemcpyDeviceToHost);
+      else
+        std::memcpy(voxel.data(), A->data, sizeof(double) * nN);
+    } else {
+      std::vector<unsigned char> ph((size_t)nN * A->index_bytes);
+      if (A->data_on_device)
+        cudaMemcpy(ph.data(), A->data, ph.size(), cudaMemcpyDeviceToHost);
+      else
+        std::memcpy(ph.data(), A->data, ph.size());
+      for (long long g = 0; g < nN; ++g) {
+        const int i = A->index_bytes == 1 ? ph[g] : ((const uint16_t*)ph.data())[g];
+        if (i >= A->nphase) { delete P; return HOM_ERR_INVALID; }
+        voxel[g] = A->table[(size_t)i * d * d];
+      }
+    }
+    double lo = 1e300, hi = -1e300;
+    for (double v : voxel) {
+      lo = std::min(lo, v);
+      hi = std::max(hi, v);
+    }
+    if (!(lo > 0)) { delete P; return HOM_ERR_INVALID; }
+    P->cA = lo;
+    P->CA = hi;
+    P->mat_kind = MAT_FIELD;
+  } else if (A->kind == HOM_A_PHASE) {
     if (!A->data || !A->table || A->nphase < 1 || (A->index_bytes != 1 && A->index_bytes != 2) ||
         (A->index_bytes == 1 && A->nphase > 256)) {
       delete P;
@@ -426,23 +551,27 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
   P->e64.mat = make_view<double>(P, P->e64.field, P->d_table);
 
   // ---- Ga: A_M^k = sum_n omega_M^{kn} A^(n) (eq. (Ga_exact_integration)) ----
-  if (A->kind == HOM_A_FOURIER) {
+  if (A->kind == HOM_A_FOURIER || voxel_ga) {
     if ((st = alloc((void**)&P->e64.field, sizeof(double) * nodes)) != HOM_OK) { hom_destroy(P); return st; }
     const int D = d;
     const long long mh = P->e64.g.nh;
     const long long nl = P->e64.g.nlines;
-    std::vector<double> full((size_t)nodes * 2);
-    if (A->data_on_device)
-      cudaMemcpy(full.data(), A->data, sizeof(double) * 2 * nodes, cudaMemcpyDeviceToHost);
-    else
-      std::memcpy(full.data(), A->data, sizeof(double) * 2 * nodes);
     std::vector<cpx<double>> half((size_t)nl * mh);
     const int mlast = P->M[D - 1];
-    for (long long l = 0; l < nl; ++l)
-      for (long long k = 0; k < mh; ++k) {
-        half[l * mh + k].x = full[2 * (l * mlast + k)];
-        half[l * mh + k].y = full[2 * (l * mlast + k) + 1];
-      }
+    if (voxel_ga) {
+      if ((st = voxel_coefficients(P, voxel, half)) != HOM_OK) { hom_destroy(P); return st; }
+    } else {
+      std::vector<double> full((size_t)nodes * 2);
+      if (A->data_on_device)
+        cudaMemcpy(full.data(), A->data, sizeof(double) * 2 * nodes, cudaMemcpyDeviceToHost);
+      else
+        std::memcpy(full.data(), A->data, sizeof(double) * 2 * nodes);
+      for (long long l = 0; l < nl; ++l)
+        for (long long k = 0; k < mh; ++k) {
+          half[l * mh + k].x = full[2 * (l * mlast + k)];
+          half[l * mh + k].y = full[2 * (l * mlast + k) + 1];
+        }
+    }
     cudaMemcpy(P->S, half.data(), sizeof(cpx<double>) * half.size(), cudaMemcpyHostToDevice);
     P->e64.inverse((cpx<double>*)P->S, P->e64.field, 1, P->stream);
     if (cudaStreamSynchronize(P->stream) != cudaSuccess || check_last() != HOM_OK) {

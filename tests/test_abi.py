@@ -40,8 +40,11 @@ def test_invalid_arguments_rejected_on_host():
     with pytest.raises(H.HomError) as ei:
         H.hom_create(2, (9, 9), fm, H.HOM_APPROX, stream=0)
     assert ei.value.status == H.HOM_ERR_INVALID
+    # exact integration of an image takes scalar coefficients only: a tensor table is refused
+    # before the device is touched
+    tmat = H.phase_material(ph, ms.random_spd_table(2, 2, seed=1, scales=[1.0, 10.0]))
     with pytest.raises(H.HomError) as ei:
-        H.hom_create(2, (9, 9), mat, H.HOM_EXACT, stream=0)
+        H.hom_create(2, (9, 9), tmat, H.HOM_EXACT, stream=0)
     assert ei.value.status == H.HOM_ERR_UNSUPPORTED
 
 
