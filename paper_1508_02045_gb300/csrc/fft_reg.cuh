@@ -194,6 +194,15 @@ __device__ __forceinline__ int line_off(const Loc<T>& L, int l) {
                        : (l & ((1 << L.nli_log) - 1)) * L.ls + (l >> L.nli_log) * L.lo;
 }
 
+// v with its sign bit xor-ed with m (0 or the sign bit): the conjugations of the inverse
+// transform as one integer operation, off the floating-point pipes
+__device__ __forceinline__ double flip_sign(double v, unsigned m) {
+  return __hiloint2double(__double2hiint(v) ^ (int)m, __double2loint(v));
+}
+__device__ __forceinline__ float flip_sign(float v, unsigned m) {
+  return __int_as_float(__float_as_int(v) ^ (int)m);
+}
+
 // One Stockham stage with radix R over nl lines of length n (p = product of earlier radices).
 // Work items: (line, butterfly); colmajor puts the line index fastest.
 template <typename T, int R, bool INV>
@@ -213,6 +222,8 @@ __device__ __forceinline__ void reg_stage(Loc<T> in, Loc<T> out, int n, int p, i
   const int gnli = in.g != nullptr ? in.nli_log : out.nli_log;
   const int gnin = in.g != nullptr ? in.nin : (out.g != nullptr ? out.nin : (1 << 30));
   const int gmask = gnli < 0 ? -1 : (1 << gnli) - 1;
+  const unsigned m_in = (INV && (cj & 1)) ? 0x80000000u : 0u;
+  const unsigned m_out = (INV && (cj & 2)) ? 0x80000000u : 0u;
   for (int w = threadIdx.x; w < total; w += blockDim.x) {
     int l, i;
     if (colmajor) {
@@ -233,9 +244,9 @@ __device__ __forceinline__ void reg_stage(Loc<T> in, Loc<T> out, int n, int p, i
 #pragma unroll
       for (int r = 0; r < R; ++r) u[r] = sm[io + r * istride];
     }
-    if (INV && (cj & 1)) {
+    if (INV) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) u[r].y = -u[r].y;
+      for (int r = 0; r < R; ++r) u[r].y = flip_sign(u[r].y, m_in);
     }
     if (p > 1) {
       const int step = k * ts;
@@ -243,9 +254,9 @@ __device__ __forceinline__ void reg_stage(Loc<T> in, Loc<T> out, int n, int p, i
       for (int r = 1; r < R; ++r) u[r] = cmul(u[r], sm[tw_base + r * step]);
     }
     RegDft<T, R>::run(u);
-    if (INV && (cj & 2)) {
+    if (INV) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) u[r].y = -u[r].y;
+      for (int r = 0; r < R; ++r) u[r].y = flip_sign(u[r].y, m_out);
     }
     const int oo = out.base + line_off(out, l) + ((i - k) * R + k) * out.es;
     if (out.g != nullptr) {
