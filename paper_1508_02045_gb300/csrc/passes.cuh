@@ -151,21 +151,30 @@ __device__ __forceinline__ void mat_apply(const MatView<T>& m, long long g, cons
 
 // the coefficient of node g in two steps, so that the loads of a batch of nodes can be issued
 // before any of them is used: fetch (phase index or field value), then evaluate v = A w
+// a phase index carried through a value of the working precision by its bits (a numeric
+// conversion would cost two FP64-pipe instructions a node)
+__device__ __forceinline__ double phase_bits(int ph, double) {
+  return __longlong_as_double((long long)ph);
+}
+__device__ __forceinline__ float phase_bits(int ph, float) { return __int_as_float(ph); }
+__device__ __forceinline__ int phase_of(double s) { return (int)__double_as_longlong(s); }
+__device__ __forceinline__ int phase_of(float s) { return __float_as_int(s); }
+
 template <typename T>
 __device__ __forceinline__ T mat_fetch(const MatView<T>& m, long long g) {
   if (m.kind == MAT_FIELD) return m.field[g];
-  return (T)phase_at(m, g);
+  return phase_bits(phase_at(m, g), T());
 }
 
 template <typename T, int D>
 __device__ __forceinline__ void mat_eval(const MatView<T>& m, T sample, const T (&w)[D],
                                          T (&v)[D]) {
   if (m.kind == MAT_FIELD || m.kind == MAT_PHASE_ISO) {
-    const T a = (m.kind == MAT_FIELD) ? sample : __ldg(&m.table[(int)sample]);
+    const T a = (m.kind == MAT_FIELD) ? sample : __ldg(&m.table[phase_of(sample)]);
 #pragma unroll
     for (int i = 0; i < D; ++i) v[i] = a * w[i];
   } else {
-    const T* t = m.table + (int)sample * D * D;
+    const T* t = m.table + phase_of(sample) * D * D;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       T s = 0;
@@ -194,13 +203,13 @@ template <typename T, int D>
 __device__ __forceinline__ void mat_shift_solve_s(const MatView<T>& m, T sample, T omega,
                                                   const T (&w)[D], T (&v)[D]) {
   if (m.kind == MAT_FIELD || m.kind == MAT_PHASE_ISO) {
-    const T a = (m.kind == MAT_FIELD) ? sample : __ldg(&m.table[(int)sample]);
+    const T a = (m.kind == MAT_FIELD) ? sample : __ldg(&m.table[phase_of(sample)]);
     const T inv = (T)1 / (a + omega);
 #pragma unroll
     for (int i = 0; i < D; ++i) v[i] = w[i] * inv;
     return;
   }
-  const int ph = (int)sample;
+  const int ph = phase_of(sample);
   const T* t = m.table + ph * D * D;
   T M[D][D];
 #pragma unroll
@@ -484,7 +493,17 @@ struct ProjGeom {
   FastDiv fdnh;   // division by nh
   int hw[3];      // support half-widths: keep |k_a| <= hw[a] (Z_N inside Z_M); else zero
   double scale;   // 1/|grid| of the forward transform (eq. (DFT))
+  const void* rk; // scale / q for q = k.k = 0 .. kkmax in the working precision (entry 0 unused),
+                  // the value the division below would give, or null (divide)
+  int kkmax;      // sum of hw[a]^2
 };
+
+// scale / k.k of a frequency inside the support (kk > 0): from the table when the engine has one
+// (a load instead of an FP64 division), else divided
+template <typename T>
+__device__ __forceinline__ T inv_kk(const ProjGeom& g, T scale, int kk) {
+  return g.rk != nullptr ? __ldg(static_cast<const T*>(g.rk) + min(kk, g.kkmax)) : scale / (T)kk;
+}
 
 // One CTA per tile of TC columns of all D components (two-level line index: component a,
 // column c), one thread per first-stage butterfly (D x TC x n / R_0, capped at kColThreads).
@@ -563,7 +582,7 @@ k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC
       kv.x = fma((T)k[a], v[a].x, kv.x);
       kv.y = fma((T)k[a], v[a].y, kv.y);
     }
-    const T coef = (kk > 0 && inside) ? scale / (T)kk : (T)0;
+    const T coef = (kk > 0 && inside) ? inv_kk<T>(g, scale, kk) : (T)0;
     kv.x *= coef;
     kv.y *= coef;
 #pragma unroll
@@ -660,7 +679,7 @@ k_proj_scalar(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g,
     const int k0 = (j <= (n - 1) / 2) ? j : j - n;
     const bool inside = abs(k0) <= g.hw[0] && abs(kc1) <= g.hw[1] && abs(kc2) <= g.hw[2];
     const int kk = k0 * k0 + kc1 * kc1 + kc2 * kc2;
-    const T coef = (kk > 0 && inside) ? scale / (T)kk : (T)0;
+    const T coef = (kk > 0 && inside) ? inv_kk<T>(g, scale, kk) : (T)0;
     const cpx<T> v0 = sm[a + j * TCp + c], vy = sm[a + cstr + j * TCp + c];
     cpx<T> sv;
     sv.x = fma((T)k0, v0.x, vy.x) * coef;

@@ -98,6 +98,7 @@ struct Engine {
   MatView<T> mat{};
   T* field = nullptr;  // MAT_FIELD storage in precision T
   T* table = nullptr;  // phase table in precision T
+  T* rk = nullptr;     // projection table scale / k.k (pg.rk)
   bool ready = false;
 
   int rmax_used = 0;
@@ -132,6 +133,22 @@ struct Engine {
     pg.fdnh = make_fastdiv(g.nh);
     for (int a = 0; a < 3; ++a) pg.hw[a] = (a < D) ? (support[a] - 1) / 2 : 0;
     pg.scale = 1.0 / (double)g.nodes;
+    // scale / q for every q = k.k inside the support, divided in precision T as the projection
+    // kernels would (host and device divisions are both correctly rounded)
+    pg.kkmax = 0;
+    for (int a = 0; a < D; ++a) pg.kkmax += pg.hw[a] * pg.hw[a];
+    {
+      std::vector<T> rk_h((size_t)pg.kkmax + 1);
+      const T sc = (T)pg.scale;
+      rk_h[0] = (T)0;
+      for (int q = 1; q <= pg.kkmax; ++q) rk_h[q] = sc / (T)q;
+      void* d = nullptr;
+      if (cudaMalloc(&d, sizeof(T) * rk_h.size()) != cudaSuccess) return HOM_ERR_OOM;
+      rk = static_cast<T*>(d);
+      if (cudaMemcpy(d, rk_h.data(), sizeof(T) * rk_h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return HOM_ERR_CUDA;
+      pg.rk = d;
+    }
     ready = true;
     return HOM_OK;
   }
@@ -142,6 +159,9 @@ struct Engine {
       if (t) cudaFree(t);
       t = nullptr;
     }
+    if (rk) cudaFree(rk);
+    rk = nullptr;
+    pg.rk = nullptr;
   }
 
   void release() {
