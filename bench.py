@@ -299,7 +299,8 @@ def pass_flops(rmax):
 # DRAM bytes (read + write) of one launch of the dominant kernels of the 243^3 CG steps, from
 # one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum on GB300; other kernels and
 # grids have no capture (null)
-NCU_TRAFFIC = {("fp64", "strided"): 649.1e6}
+NCU_TRAFFIC = {("fp64", "strided"): 650.0e6, ("fp32", "line_fwd"): 643.2e6,
+               ("fp32", "line_inv"): 987.0e6}
 
 
 def ncu_traffic(precision, kind):
@@ -312,9 +313,9 @@ def pass_bytes(word=8, two_line=False, fused_cg=False):
     """Compulsory DRAM bytes of one launch of each pass kind in a CG step (word = 8 for FP64,
     4 for FP32). two_line: the 3-D scalar projection keeps two spectrum lines between its column
     passes (the axis-1 passes read or write two components of three, the projection two and
-    two). fused_cg: the FP32 inner CG step, whose inverse pass reads the spectrum and x, r, p and
-    writes x, r (no separate vector update); otherwise line_inv reads the spectrum and p and
-    writes C p, and the vector update reads x, p, r, C p and writes x, r."""
+    two). fused_cg: the fused CG step of both precisions, whose inverse pass reads the spectrum
+    and x, r, p and writes x, r (no separate vector update); otherwise line_inv reads the
+    spectrum and p and writes C p, and the vector update reads x, p, r, C p and writes x, r."""
     n = N_GRID[0]
     nh = (n + 1) // 2
     spec = n * n * nh * D * 2 * word  # all D components of the half spectrum
@@ -458,7 +459,7 @@ def run_ours(args, rank, world, local):
     if rank != 0:
         return None
     flops = pass_flops(tune["rmax64"])
-    byts = pass_bytes(8)
+    byts = pass_bytes(8, fused_cg=True)
     byts32 = pass_bytes(4, two_line=bool(tune32.get("two_line32")), fused_cg=True)
     peaks = measured_peaks()
 

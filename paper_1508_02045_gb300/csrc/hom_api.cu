@@ -711,7 +711,6 @@ int solve_stop_mode(int solver, int stop) {
 // device stopping flag is set
 void enqueue_step(hom_problem* P) {
   SolveState& S_ = P->sv;
-  const int d = P->d;
   const long long nodes = P->nodes;
   cpx<double>* S = (cpx<double>*)P->S;
   cudaStream_t st = P->stream;
@@ -719,7 +718,6 @@ void enqueue_step(hom_problem* P) {
   double* x = P->vec[0];
   double* r = P->vec[2];
   double* p = P->vec[3];
-  double* q = P->vec[4];
   Fields<double> f{};
   f.cs = nodes;
   switch (S_.solver) {
@@ -728,14 +726,19 @@ void enqueue_step(hom_problem* P) {
       P->e64.apply(PRE_AFFINE, PROJ_GAMMA, POST_RICH, f, S, P->d_sc, args, P->partials,
                    P->counter, 0, st);
       break;
-    case HOM_CG:
+    case HOM_CG: {
+      // Algorithm 2 with the vector update fused into the operator passes (as the FP32 inner
+      // solves do): the pre-operator pass forms p = r + beta p, A p and (p, A p) = (p, C p) (p
+      // lies in the range of G), then alpha; the inverse pass updates x and r and forms (r, r)
       f.xin = r;
       f.p = p;
-      f.out = q;
-      P->e64.apply(PRE_CG, PROJ_GAMMA, POST_CG, f, S, P->d_sc, args, P->partials, P->counter, 0, st);
-      Ops<double>::cg_update(x, r, p, q, (long long)d * nodes, nodes, P->d_sc, P->partials,
-                             P->counter, P->red_grid, st);
+      Fields<double> fi = f;
+      fi.x = x;
+      fi.r = r;
+      P->e64.apply2(PRE_CG_DOT, PROJ_GAMMA, POST_CG_FUSED, f, fi, S, P->d_sc, args, P->partials,
+                    P->counter, 0, st);
       break;
+    }
     case HOM_CHEBYSHEV: {
       f.xin = p;
       Fields<double> fi = f;

@@ -110,14 +110,8 @@ void batch_step(const Engine<T>& E, int solver, const ReqDesc<T>* reqs, int n, i
     case HOM_RICHARDSON:
       E.apply_batch(PRE_AFFINE, PROJ_GAMMA, POST_RICH, reqs, n, st);
       break;
-    case HOM_CG:
-      if (std::is_same<T, float>::value) {  // FP32 inner step: the fused form of hom_solve
-        E.apply_batch(PRE_CG_DOT, PROJ_GAMMA, POST_CG_FUSED, reqs, n, st);
-      } else {
-        E.apply_batch(PRE_CG, PROJ_GAMMA, POST_CG, reqs, n, st);
-        Ops<T>::cg_update(nullptr, nullptr, nullptr, nullptr, (long long)d * nodes, nodes, nullptr,
-                          nullptr, nullptr, red_grid, st, reqs, n);
-      }
+    case HOM_CG:  // the fused step of hom_solve (vector update inside the operator passes)
+      E.apply_batch(PRE_CG_DOT, PROJ_GAMMA, POST_CG_FUSED, reqs, n, st);
       break;
     case HOM_CHEBYSHEV:
       E.apply_batch(PRE_LINEAR, PROJ_GAMMA, POST_CHEB, reqs, n, st);

@@ -162,13 +162,11 @@ cudaError_t Ops<T>::prepare(int) {
   HOM_SET_SMEM((k_line_inv<T, 3, POST_CG>));
   HOM_SET_SMEM((k_line_inv<T, 3, POST_CHEB>));
   HOM_SET_SMEM((k_line_inv<T, 3, POST_EM>));
-  if constexpr (std::is_same<T, float>::value) {
-    HOM_SET_SMEM((k_line_fwd<T, 2, PRE_CG_DOT>));
-    HOM_SET_SMEM((k_line_fwd<T, 3, PRE_CG_DOT>));
-    HOM_SET_SMEM((k_line_inv<T, 2, POST_CG_FUSED>));
-    HOM_SET_SMEM((k_line_inv<T, 3, POST_CG_FUSED>));
-    return pair_prepare_f32(cap);
-  }
+  HOM_SET_SMEM((k_line_fwd<T, 2, PRE_CG_DOT>));
+  HOM_SET_SMEM((k_line_fwd<T, 3, PRE_CG_DOT>));
+  HOM_SET_SMEM((k_line_inv<T, 2, POST_CG_FUSED>));
+  HOM_SET_SMEM((k_line_inv<T, 3, POST_CG_FUSED>));
+  if constexpr (std::is_same<T, float>::value) return pair_prepare_f32(cap);
   return cudaSuccess;
 }
 
@@ -186,9 +184,7 @@ static void line_fwd_d(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S
     case PRE_AFFINE: HOM_LF(PRE_AFFINE); break;
     case PRE_LINEAR: HOM_LF(PRE_LINEAR); break;
     case PRE_CG: HOM_LF(PRE_CG); break;
-    case PRE_CG_DOT:
-      if constexpr (std::is_same<T, float>::value) HOM_LF(PRE_CG_DOT);
-      break;
+    case PRE_CG_DOT: HOM_LF(PRE_CG_DOT); break;
     case PRE_EM: HOM_LF(PRE_EM); break;
     default: HOM_LF(PRE_IDENT); break;
   }
@@ -349,9 +345,7 @@ static void line_inv_d(const PassGeom& g, int post, const cpx<T>* S, const Field
   switch (post) {
     case POST_RICH: HOM_LI(POST_RICH); break;
     case POST_CG: HOM_LI(POST_CG); break;
-    case POST_CG_FUSED:
-      if constexpr (std::is_same<T, float>::value) HOM_LI(POST_CG_FUSED);
-      break;
+    case POST_CG_FUSED: HOM_LI(POST_CG_FUSED); break;
     case POST_CHEB: HOM_LI(POST_CHEB); break;
     case POST_EM: HOM_LI(POST_EM); break;
     case POST_ADD: HOM_LI(POST_ADD); break;
