@@ -299,7 +299,7 @@ def pass_flops(rmax):
 # DRAM bytes (read + write) of one launch of the dominant kernels of the 243^3 CG steps, from
 # one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum on GB300; other kernels and
 # grids have no capture (null)
-NCU_TRAFFIC = {("fp64", "strided"): 650.0e6, ("fp32", "line_fwd"): 643.2e6,
+NCU_TRAFFIC = {("fp64", "strided"): 650.4e6, ("fp32", "line_fwd"): 643.2e6,
                ("fp32", "line_inv"): 987.0e6}
 
 

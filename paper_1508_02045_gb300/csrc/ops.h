@@ -74,9 +74,6 @@ struct Ops {
                        Scalars* sc, const OpArgs& args, double* partials, unsigned* counter,
                        int negate, cudaStream_t st, const ReqDesc<T>* reqs = nullptr,
                        int nreq = 1);
-  static void cg_update(T* x, T* r, const T* p, const T* q, long long len, long long nodes,
-                        Scalars* sc, double* partials, unsigned* counter, int grid,
-                        cudaStream_t st, const ReqDesc<T>* reqs = nullptr, int nreq = 1);
   static void energy(int D, const T* x, long long nodes, const MatView<T>& mat, Scalars* sc,
                      double* partials, unsigned* counter, int grid, cudaStream_t st);
   static void fill_const(T* x, long long nodes, int d, const Scalars* sc, cudaStream_t st);

@@ -381,18 +381,6 @@ void Ops<T>::line_inv(const PassGeom& g, int post, const cpx<T>* S, const Fields
 }
 
 template <typename T>
-void Ops<T>::cg_update(T* x, T* r, const T* p, const T* q, long long len, long long nodes,
-                       Scalars* sc, double* partials, unsigned* counter, int grid,
-                       cudaStream_t st, const ReqDesc<T>* reqs, int nreq) {
-  const bool prof = profiling();
-  if (prof) prof_mark(KIND_VECTOR, st, true);
-  const dim3 g3((unsigned)grid, 1, (unsigned)nreq);
-  k_cg_update<T><<<g3, kThreads, 0, st>>>(x, r, p, q, len, nodes, sc, partials, counter, reqs);
-  if (prof) prof_mark(KIND_VECTOR, st, false);
-  ++launch_counter();
-}
-
-template <typename T>
 void Ops<T>::energy(int D, const T* x, long long nodes, const MatView<T>& mat, Scalars* sc,
                     double* partials, unsigned* counter, int grid, cudaStream_t st) {
   if (D == 2) k_energy<T, 2><<<grid, kThreads, 0, st>>>(x, nodes, mat, sc, partials, counter);

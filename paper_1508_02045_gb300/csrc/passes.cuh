@@ -262,7 +262,7 @@ struct Fields {
 template <typename T>
 struct ReqDesc {
   Fields<T> ff;        // pre-operator buffers (line_fwd)
-  Fields<T> fi;        // post-operator buffers (line_inv, cg_update)
+  Fields<T> fi;        // post-operator buffers (line_inv)
   cpx<T>* S;           // half-spectrum work buffer
   MatView<T> mat;
   Scalars* sc;
@@ -986,75 +986,6 @@ k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ 
   if (!reduce_and_last<1>(acc, partials, counter, tot)) return;
   if (threadIdx.x != 0 || sc == nullptr) return;
   line_inv_finish<POST>(sc, tot[0], (double)(nlines * n));
-}
-
-// ---------------------------------------------------------------------------------------
-// CG update (Algorithm 2): x += alpha p, r -= alpha C p, (r, r); then beta and the test
-// ---------------------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_cg_update(T* x, T* r, const T* p, const T* q, long long len, long long nodes, Scalars* sc,
-            double* partials, unsigned* counter, const ReqDesc<T>* __restrict__ reqs) {
-  if (reqs != nullptr) {
-    const ReqDesc<T>& R = reqs[blockIdx.z];
-    x = R.fi.x;
-    r = R.fi.r;
-    p = R.fi.p;
-    q = R.fi.out;
-    sc = R.sc;
-    partials = R.partials;
-    counter = R.counter;
-  }
-  if (sc->done) return;
-  const T alpha = (T)sc->alpha;
-  DotAcc<T> dacc;
-  // restrict-qualified copies: the four vectors never alias, so loads can run ahead of stores
-  T* __restrict__ xr = x;
-  T* __restrict__ rr = r;
-  const T* __restrict__ pr = p;
-  const T* __restrict__ qr = q;
-  constexpr int K = 4;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < len; i0 += K * stride) {
-    T xv[K], rv[K], pv[K], qv[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const long long i = i0 + k * stride;
-      const bool ok = i < len;
-      xv[k] = ok ? xr[i] : (T)0;
-      rv[k] = ok ? rr[i] : (T)0;
-      pv[k] = ok ? pr[i] : (T)0;
-      qv[k] = ok ? qr[i] : (T)0;
-    }
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const long long i = i0 + k * stride;
-      if (i >= len) continue;
-      xr[i] = xv[k] + alpha * pv[k];
-      const T rn = rv[k] - alpha * qv[k];
-      rr[i] = rn;
-      dacc.add(rn, rn);
-    }
-  }
-  double acc[1] = {dacc.value()};
-  double tot[1];
-  if (!reduce_and_last<1>(acc, partials, counter, tot)) return;
-  if (threadIdx.x != 0) return;
-  const double rr_new = tot[0] / (double)nodes;
-  const double res = sqrt(rr_new);
-  sc->last_res = res;
-  record_history(sc, res);
-  sc->it += 1;
-  if (sc->fixed) {
-    if (sc->it >= sc->maxit) sc->done = 1;
-  } else if (res <= sc->tol * sc->nb) {
-    sc->done = 1;
-    sc->converged = 1;
-  } else if (sc->it >= sc->maxit) {
-    sc->done = 1;
-  }
-  sc->beta = rr_new / sc->rr;
-  sc->rr = rr_new;
 }
 
 // ---------------------------------------------------------------------------------------
