@@ -186,6 +186,12 @@ int hom_solve_end(hom_problem* P, double* x_dev, double* AH_EE, double* flux, ho
 int hom_solve_history(hom_problem* P, double* out, int cap, int* count);
 int hom_solve_current(hom_problem* P, double* x_dev);
 
+/* Non-conformity of the current iterate of an active session (Section 4.4), in the grid norm:
+ * ||G x_m + E - x_m|| for Eyre-Milton (x_m approximates E + e) and ||G x_m - x_m|| for the
+ * conforming solvers (round-off; Ga: G_{N,M}). Writes one double to the host pointer `value`;
+ * synchronises the stream; HOM_ERR_INVALID without an active session. */
+int hom_solve_nonconformity(hom_problem* P, double* value);
+
 /* Energy (A(E + x), E + x) and flux <A(E + x)> of a device field x_dev on the solve grid
  * (x_dev may be NULL for x = 0, the Voigt value of Section 4.3). Synchronises the stream. */
 int hom_energy(hom_problem* P, const double* E, const double* x_dev, double* energy, double* flux);

@@ -35,7 +35,7 @@ EXPORTED = ["hom_create", "hom_grid", "hom_bounds", "hom_apply", "hom_solve", "h
             "hom_solve_end", "hom_apply_static", "hom_batch_create", "hom_batch_iterate",
             "hom_batch_destroy", "hom_server_create", "hom_server_submit", "hom_server_step",
             "hom_server_poll", "hom_server_status", "hom_server_destroy", "hom_autotune",
-            "hom_solve_history", "hom_solve_current"]
+            "hom_solve_history", "hom_solve_current", "hom_solve_nonconformity"]
 PASS_KINDS = ["line_fwd", "strided", "proj", "line_inv", "vector"]
 
 
@@ -114,6 +114,7 @@ def _load():
     lib.hom_solve_end.argtypes = [vp, vp, dp, dp, ctypes.POINTER(hom_stats)]
     lib.hom_solve_history.argtypes = [vp, dp, ip, ctypes.POINTER(ctypes.c_int)]
     lib.hom_solve_current.argtypes = [vp, vp]
+    lib.hom_solve_nonconformity.argtypes = [vp, dp]
     lib.hom_prolongate.argtypes = [vp, vp, vp, vp]
     lib.hom_bound.argtypes = [vp, vp, dp, vp, dp]
     lib.hom_destroy.argtypes = [vp]
@@ -271,6 +272,13 @@ def hom_solve_history(P, cap=1 << 20):
 def hom_solve_current(P, x):
     """Write the current iterate of the active session into the device tensor x."""
     return _check(_lib.hom_solve_current(P, _ptr(x)), "hom_solve_current")
+
+
+def hom_solve_nonconformity(P):
+    """Non-conformity of the current iterate of the active session (Section 4.4)."""
+    v = ctypes.c_double()
+    _check(_lib.hom_solve_nonconformity(P, ctypes.byref(v)), "hom_solve_nonconformity")
+    return v.value
 
 
 def hom_solve_end(P, d, x=None, allow_not_converged=False):

@@ -1174,6 +1174,39 @@ extern "C" int hom_solve_current(hom_problem* P, double* x_dev) {
   return check_last();
 }
 
+extern "C" int hom_solve_nonconformity(hom_problem* P, double* value) {
+  if (!P || !value || !P->sv.active) return HOM_ERR_INVALID;
+  SolveState& S_ = P->sv;
+  const long long nodes = P->nodes;
+  const long long len = (long long)P->d * nodes;
+  cudaStream_t st = P->stream;
+  const double* cur = P->vec[0];
+  double e[3] = {0.0, 0.0, 0.0};
+  int rc;
+  if (!S_.refined) {
+    if ((rc = poll(P, P->d_sc))) return rc;
+    if (S_.solver == HOM_RICHARDSON) cur = P->vec[0] + (P->h_sc->result ? len : 0);
+    if (S_.solver == HOM_EYRE_MILTON)
+      for (int a = 0; a < P->d; ++a) e[a] = S_.E[a];
+  }
+  // G x into the solver's free vector (no solver keeps state there between steps)
+  double* g = P->vec[4];
+  Fields<double> f{};
+  f.xin = cur;
+  f.out = g;
+  f.cs = nodes;
+  OpArgs args{};
+  P->e64.apply(PRE_IDENT, PROJ_GAMMA, POST_STORE, f, (cpx<double>*)P->S, nullptr, args, nullptr,
+               nullptr, 0, st);
+  Scalars s{};
+  if ((rc = upload_scalars(P, P->d_aux, s))) return rc;
+  k_nonconf<double><<<P->red_grid, kThreads, 0, st>>>(g, cur, P->d, nodes, e[0], e[1], e[2],
+                                                       P->partials, P->counter, P->d_aux);
+  if ((rc = check_last()) || (rc = poll(P, P->d_aux))) return rc;
+  *value = P->h_sc->last_res;
+  return HOM_OK;
+}
+
 extern "C" int hom_solve(hom_problem* P, const double* E, int solver, double tol,
                          const hom_opts* opts, double* x_dev, double* AH_EE, double* flux,
                          hom_stats* stats) {

@@ -989,6 +989,29 @@ k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------------------
+// non-conformity of an iterate (Section 4.4): sqrt of the grid mean of |g - x + e|^2 summed
+// over the d components, with g = G x and e = E for the Eyre-Milton iterate (0 for the
+// conforming solvers); the last CTA writes it to sc->last_res
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_nonconf(const T* __restrict__ g, const T* __restrict__ x, int d, long long nodes, double e0,
+          double e1, double e2, double* partials, unsigned* counter, Scalars* sc) {
+  double acc[1] = {0.0};
+  const long long len = (long long)d * nodes;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long a = i / nodes;
+    const double e = a == 0 ? e0 : (a == 1 ? e1 : e2);
+    const double v = (double)g[i] - (double)x[i] + e;
+    acc[0] = fma(v, v, acc[0]);
+  }
+  double tot[1];
+  if (!reduce_and_last<1>(acc, partials, counter, tot)) return;
+  if (threadIdx.x == 0) sc->last_res = sqrt(tot[0] / (double)nodes);
+}
+
+// ---------------------------------------------------------------------------------------
 // energy (A(E + x), E + x) and flux <A(E + x)> (eqs. (GaNi), (ev_bounds))
 // ---------------------------------------------------------------------------------------
 template <typename T, int D>

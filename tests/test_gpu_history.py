@@ -232,3 +232,40 @@ def test_iterations_against_contrast_match_oracle():
     for k, g in growth.items():
         if k[1] != "richardson":
             assert g < 15, (k, g)
+
+
+@pytest.mark.parametrize("solver", ["eyre_milton", "cg", "richardson"])
+def test_nonconformity_every_iterate(solver):
+    # Section 4.4: ||G x_m + E - x_m|| (Eyre-Milton) and ||G x_m - x_m|| (conforming solvers,
+    # round-off) after each of 10 single steps, against the oracle's iterates
+    N = (15, 15)
+    lo, hi = 1.0, 100.0
+    ph, table, A = square(N, 0.6, lo, hi)
+    P = H.Problem(2, N, H.phase_material(ph, table))
+    E = np.array([1.0, 0.0])
+    steps = 10
+    H.hom_solve_begin(P.h, E, H.SOLVERS[solver], 0.0, H.make_opts(fixed_iters=steps))
+    sysn = O.GaNi(A, 2)
+    if solver == "eyre_milton":
+        r = O.eyre_milton(sysn, E, lo, hi, fixed_iters=steps, keep_iterates=True)
+    elif solver == "cg":
+        r = O.cg(sysn, E, fixed_iters=steps, keep_iterates=True)
+    else:
+        r = O.richardson(sysn, E, lo, hi, fixed_iters=steps, keep_iterates=True)
+    Ec = sysn.const(E)
+    got = []
+    for m in range(steps):
+        H.hom_solve_iterate(P.h, 1)
+        got.append(H.hom_solve_nonconformity(P.h))
+        x = r.iterates[m]
+        if solver == "eyre_milton":
+            ref = gnorm(O.project(x) + Ec - x)
+            assert abs(got[-1] - ref) < 1e-9 * ref, m
+        else:
+            assert got[-1] < 1e-12 * gnorm(x), m
+    if solver == "eyre_milton":
+        assert int(np.argmax(got)) == 0  # largest at the first iteration (Section 4.4)
+    H.hom_solve_end(P.h, 2)
+    with pytest.raises(H.HomError):
+        H.hom_solve_nonconformity(P.h)
+    P.close()

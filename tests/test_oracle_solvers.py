@@ -272,3 +272,34 @@ def test_eyre_milton_rejects_ga():
     A_M = O.ga_coefficients(ms.box_fourier_coefficients(M, 0.6, 1.0, 10.0), 2)
     with pytest.raises(ValueError):
         O.eyre_milton(O.Ga(A_M, N, 2), np.array([1.0, 0.0]), 1.0, 10.0)
+
+
+def _gnorm(v):
+    return float(np.sqrt(np.mean(np.sum(v * v, axis=0))))
+
+
+def test_nonconformity_of_iterates_section_4_4():
+    # Section 4.4 on the square inclusion (15^2, contrast 100): the Eyre-Milton iterate's
+    # distance ||G x_m + E - x_m|| is largest at the first iteration and then falls, not
+    # monotonically; it splits into orthogonal parts (squared norms add: Helmholtz
+    # decomposition, the paper prints the split without the squares); the conforming solvers'
+    # ||G x_m - x_m|| is round-off that grows with m
+    N = (15, 15)
+    a = _square(N, 0.6, 1.0, 100.0)
+    sysn = O.GaNi(a, 2)
+    E = np.array([1.0, 0.0])
+    Ec = sysn.const(E)
+    r = O.eyre_milton(sysn, E, 1.0, 100.0, fixed_iters=30, keep_iterates=True)
+    nc = [_gnorm(O.project(x) + Ec - x) for x in r.iterates]
+    assert int(np.argmax(nc)) == 0
+    assert nc[-1] < 0.2 * nc[0]
+    assert any(nc[m + 1] > nc[m] for m in range(len(nc) - 1))
+    for x in r.iterates[:5]:
+        mean = x.reshape(2, -1).mean(axis=1).reshape(2, 1, 1) * np.ones_like(x)
+        lhs = _gnorm(O.project(x) + Ec - x) ** 2
+        rhs = _gnorm(Ec - mean) ** 2 + _gnorm(O.project(x) - x + mean) ** 2
+        assert abs(lhs - rhs) < 1e-12 * lhs
+    for res in (O.cg(sysn, E, fixed_iters=30, keep_iterates=True),
+                O.richardson(sysn, E, 1.0, 100.0, fixed_iters=30, keep_iterates=True)):
+        rel = [_gnorm(O.project(x) - x) / _gnorm(x) for x in res.iterates]
+        assert max(rel) < 1e-12
