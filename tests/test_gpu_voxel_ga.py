@@ -115,3 +115,20 @@ def test_random_spheres_bound_ordering():
     assert abs(ub - ub_ref) < 1e-10 * ub_ref
     Pn.close()
     Pg.close()
+
+
+def test_voxel_ga_refined_matches_fp64():
+    # the FP32 operator of an exactly integrated image inside FP64 refinement reaches the FP64
+    # A_H (1e-8, the mixed-precision bar)
+    N = (15, 13, 11)
+    ph, values = random_image(N, 3, 9)
+    table = ms.isotropic_table(values, 3)
+    E = np.array([0.0, 1.0, 0.0])
+    P64 = H.Problem(3, N, H.phase_material(ph, table), H.HOM_EXACT)
+    P32 = H.Problem(3, N, H.phase_material(ph, table), H.HOM_EXACT, precision=H.HOM_FP32_REFINED)
+    AH64, _, _, _ = H.hom_solve(P64.h, E, H.HOM_CG, 1e-11)
+    AH32, _, st, _ = H.hom_solve(P32.h, E, H.HOM_CG, 1e-11)
+    assert st["converged"]
+    assert abs(AH32 - AH64) < 1e-8 * AH64
+    P64.close()
+    P32.close()
