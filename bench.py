@@ -642,7 +642,7 @@ def run_served(args):
 
 
 # ------------------------------------------------------------------------------------------
-# the spec configurations end to end (solver results and times; not the bench line)
+# configurations 1-4 end to end (solver results and times; not the bench line)
 # ------------------------------------------------------------------------------------------
 
 def run_configs(args):

@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, through the C ABI (libhom.so).
 
-Per operator application the spec bar is 1e-12 relative (norm-wise); per solve 1e-10 on
+Per operator application the bar is 1e-12 relative (norm-wise); per solve 1e-10 on
 A_H. Iterates are compared at fixed iteration counts first (Section 3 algorithms taken step by
 step), then at tolerance.
 """
