@@ -139,3 +139,39 @@ def test_refined_rejects_other_solvers():
         H.hom_solve(P.h, np.array([1.0, 0.0]), H.HOM_RICHARDSON, 1e-6)
     assert ei.value.status == H.HOM_ERR_UNSUPPORTED
     P.close()
+
+
+@pytest.mark.parametrize("kind", ["iso8_vector", "iso8_many", "iso16", "tensor", "field"])
+def test_fp32_line_pass_material_branches(kind):
+    # the specialised FP32 line pass streams 16-byte vectors for isotropic one-byte phase images
+    # with at most 64 phases and takes the node-by-node pre-operator otherwise: every branch
+    # against the oracle, on a grid whose contiguous axis has a compile-time plan (81 = 27 x 3)
+    N = (9, 11, 81)
+    d = 3
+    rng = np.random.default_rng(17)
+    nph = {"iso8_vector": 40, "iso8_many": 100, "iso16": 300, "tensor": 5, "field": 0}[kind]
+    if kind == "field":
+        a = rng.uniform(1.0, 30.0, N)
+        mat, A = H.scalar_material(a), a
+    else:
+        ph = rng.integers(0, nph, size=N).astype(np.uint16 if kind == "iso16" else np.uint8)
+        if kind == "tensor":
+            table = ms.random_spd_table(nph, d, seed=3, scales=np.linspace(1.0, 20.0, nph))
+            A = O.expand_phase(ph, table)
+        else:
+            table = ms.isotropic_table(rng.uniform(1.0, 30.0, nph), d)
+            A = O.expand_phase(ph, table)[0, 0]
+        mat = H.phase_material(ph, table)
+    P = H.Problem(d, N, mat, precision=H.HOM_FP32_REFINED)
+    x = ms.random_field((d,) + N, 8)
+    y = P.field()
+    H.hom_apply(P.h, H.HOM_OP_LINEAR | H.HOM_OP_FP32, None, torch.from_numpy(x).cuda(), y)
+    err = rel(y.cpu().numpy(), O.GaNi(A, d).matvec(x))
+    assert err < 2e-6, err
+    # the fused CG step of the refined solve on the same material reaches the FP64 A_H
+    E = np.array([0.0, 0.0, 1.0])
+    AH, _, st, _ = H.hom_solve(P.h, E, H.HOM_CG, 1e-10)
+    sysn = O.GaNi(A, d)
+    ref = sysn.energy(E, O.cg(sysn, E, tol=1e-11).x)
+    assert st["converged"] and abs(AH - ref) < AH_TOL_MIXED * ref
+    P.close()
