@@ -94,8 +94,8 @@ struct Scalars {
   int nhist;          // entries recorded (may exceed hist_cap; the excess is not stored)
 };
 
-// PRE_CG_DOT / POST_CG_FUSED: the CG step of the FP32 inner solves with the vector update
-// fused into the operator passes. In exact arithmetic (p, G A p) = (p, A p) for p in the range
+// PRE_CG_DOT / POST_CG_FUSED: the CG step (both precisions) with the vector update fused into
+// the operator passes. In exact arithmetic (p, G A p) = (p, A p) for p in the range
 // of the orthogonal projection G (every CG direction is), so (p, C p) and alpha come from the
 // pre-operator pass and the inverse pass can update x and r and form (r, r) itself.
 enum PreOp { PRE_AFFINE = 0, PRE_LINEAR = 1, PRE_CG = 2, PRE_EM = 3, PRE_IDENT = 4, PRE_CG_DOT = 5 };
