@@ -531,7 +531,8 @@ def run_ours(args, rank, world, local):
         "fp32_step": {"metric": "G·A matvecs/s at 243^3 (FP32 CG step, inner solver of the refinement)",
                       "value": round(1000.0 / ms_step32, 3), "unit": UNIT, "ms_per_step": round(ms_step32, 4),
                       "hbm_gbs": round(step_bytes32 / (ms_step32 * 1e-3) / 1e9, 1),
-                      "plan": {"rmax": tune32["rmax32"], "smem_kb": tune32["smem_kb32"]},
+                      "plan": {"rmax": tune32["rmax32"], "smem_kb": tune32["smem_kb32"],
+                               "two_line": bool(tune32.get("two_line32"))},
                       "roofline": {"bound": "hbm", "kernel": f"k_{dom32}", "achieved": round(ach32, 1),
                                    "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                    "frac": round(ach32 / peaks["hbm_gbs"], 4),

@@ -1,0 +1,75 @@
+"""The benchmark's bookkeeping without a GPU: the radix plans it models, the compulsory bytes
+and FFT flops it divides by the measured times (the numerators of `roofline.achieved`), checked
+against counts made here from the definitions."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_radix_plans(bench):
+    # the prime factors of n grouped first-fit into register radices <= rmax, largest first
+    assert bench.plan_radices(243, 27) == [27, 9]
+    assert bench.plan_radices(243, 15) == [9, 9, 3]
+    assert bench.plan_radices(405, 27) == [27, 15]
+    assert bench.plan_radices(161, 27) == [23, 7]
+    assert bench.plan_radices(63, 27) == [21, 3]
+    for n in (45, 81, 135, 175, 189, 243, 405, 161, 63):
+        for rmax in (9, 15, 27):
+            p = bench.plan_radices(n, rmax)
+            prod = 1
+            for r in p:
+                prod *= r
+            assert prod == n and all(r <= max(rmax, 31) for r in p)
+
+
+def test_compulsory_bytes_of_the_cg_step(bench):
+    n = 243
+    nh = (n + 1) // 2
+    field32 = 3 * n ** 3 * 4                   # d components of a real field, FP32
+    spec32 = 3 * n * n * nh * 8                # d half spectra, complex FP32
+    b = bench.pass_bytes(4, fused_cg=True)
+    # line_fwd: r, p read, p written, one-byte phases, spectrum written
+    assert b["line_fwd"] == 3 * field32 + n ** 3 + spec32
+    # each column pass reads and writes the spectrum once
+    assert b["strided"] == b["proj"] == 2 * spec32
+    # fused line_inv: spectrum, x, r, p read; x, r written
+    assert b["line_inv"] == spec32 + 5 * field32
+    step = b["line_fwd"] + 2 * b["strided"] + b["proj"] + b["line_inv"]
+    assert abs(step / 1e9 - 2.78) < 0.01       # a fused FP32 step with three spectrum lines
+    # two spectrum lines between the column passes: 5/3 and 4/3 of a spectrum, 2.55 GB a step
+    b2 = bench.pass_bytes(4, two_line=True, fused_cg=True)
+    assert b2["strided"] == spec32 * 5 // 3 and b2["proj"] == spec32 * 4 // 3
+    step2 = b2["line_fwd"] + 2 * b2["strided"] + b2["proj"] + b2["line_inv"]
+    assert abs(step2 / 1e9 - 2.55) < 0.01
+    # the unfused step adds the vector update and is heavier
+    bu = bench.pass_bytes(4)
+    stepu = bu["line_fwd"] + 2 * bu["strided"] + bu["proj"] + bu["line_inv"] + bu["vector"]
+    assert abs(stepu / 1e9 - 3.29) < 0.01
+    # FP64 doubles every field and spectrum word
+    b64 = bench.pass_bytes(8, fused_cg=True)
+    assert b64["strided"] == 2 * b["strided"]
+
+
+def test_fft_flop_model(bench):
+    # radix-3 stage: 9.33 flops per point with twiddles; a plan without twiddles on its first
+    # stage costs less than one with them on every stage
+    f = bench.fft_flops_per_point(3, 15)
+    assert f > 0
+    f243 = bench.fft_flops_per_point(243, 15)
+    assert 5 * 8.0 < f243 < 5 * 9.34 + 1e-9    # five radix-3 levels, the first without twiddles
+    flops = bench.pass_flops(15)
+    n = 243
+    spec = n * n * ((n + 1) // 2) * 3
+    assert flops["strided"] == spec * f243
+    assert flops["proj"] > 2 * flops["strided"]  # four transforms of two lines + Gamma^
