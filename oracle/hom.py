@@ -16,7 +16,7 @@ __all__ = [
     "signed_index", "dft_matrix", "dft", "idft", "frequencies", "gamma_apply", "project",
     "apply_A", "expand_phase", "GaNi", "Ga", "prolongate", "energy", "richardson", "cg",
     "chebyshev", "eyre_milton", "SolveResult", "spectral_bounds", "double_grid",
-    "ga_coefficients", "voxel_fourier_coefficients",
+    "ga_coefficients", "voxel_fourier_coefficients", "restrict",
 ]
 
 
@@ -168,7 +168,8 @@ def spectral_bounds(A: np.ndarray, d: int) -> tuple[float, float]:
     field with d spatial axes, or a (d, d, N...) tensor field)."""
     if A.ndim == d:
         return float(A.min()), float(A.max())
-    mats = np.moveaxis(np.moveaxis(A, 0, -1), 0, -1).reshape(-1, d, d)
+    nc = A.shape[0]  # d, or d (d + 1) / 2 for a stiffness in Mandel form (oracle/elastic.py)
+    mats = np.moveaxis(np.moveaxis(A, 0, -1), 0, -1).reshape(-1, nc, nc)
     ev = np.linalg.eigvalsh(mats)
     return float(ev.min()), float(ev.max())
 
@@ -251,6 +252,18 @@ def prolongate(v: np.ndarray, M) -> np.ndarray:
         idx.append(np.mod(signed_index(N[a]), M[a]))
     out[(slice(None),) + np.ix_(*idx)] = vh
     return idft(out, d).real
+
+
+def restrict(v: np.ndarray, N) -> np.ndarray:
+    """Samples on the grid N of the trigonometric polynomial of order N given by its nodal values
+    v on a grid M >= N (every Ga iterate is one, Section 2.3): F_M, the coefficients of Z_N
+    (eq. (DFT); a polynomial of order N has no others), F_N^{-1}. The inverse of prolongate on
+    such fields."""
+    d = v.shape[0]
+    M = v.shape[1:]
+    vh = dft(v, d)
+    idx = [np.mod(signed_index(int(N[a])), M[a]) for a in range(d)]
+    return idft(vh[(slice(None),) + np.ix_(*idx)], d).real
 
 
 # ----------------------------------------------------------------------------------------
@@ -379,16 +392,17 @@ def eyre_milton(sys: GaNi, E, cA, CA, tol=1e-6, maxit=100000, fixed_iters=None,
     fixed-point equation by (A + omega) and apply G). The default reading takes
     q = +2 omega (A + omega)^{-1} E, whose fixed point is E + e~; literal_sign=True keeps the
     printed sign. The returned x approximates E + e~ (not e~)."""
-    if not isinstance(sys, GaNi):
+    if not (isinstance(sys, GaNi) or hasattr(sys, "nc")):
         raise ValueError("Eyre-Milton is defined for the GaNi system only (Section 3.4)")
     omega = math.sqrt(cA * CA)
     d = sys.d
+    nc = getattr(sys, "nc", d)  # components: d, or d (d + 1) / 2 for strains
     A = sys.A
     Econst = sys.const(E)
     if A.ndim == d:
         inv = lambda v: v / (A[None] + omega)  # noqa: E731
     else:
-        Ap = A + omega * np.eye(d).reshape((d, d) + (1,) * d)
+        Ap = A + omega * np.eye(nc).reshape((nc, nc) + (1,) * d)
         Am = np.moveaxis(np.moveaxis(Ap, 0, -1), 0, -1)
         Ainv = np.linalg.inv(Am)
         Ainv = np.moveaxis(np.moveaxis(Ainv, -1, 0), -1, 0)

@@ -197,3 +197,38 @@ def test_voxel_coefficients_of_whole_voxel_box_are_analytic(N, h):
     np.testing.assert_allclose(got, delta + 9.0 * box, atol=1e-13)
     if np.allclose(sides, h):  # the microstructure module's analytic box coefficients
         np.testing.assert_allclose(got, ms.box_fourier_coefficients(M, h, 1.0, 10.0), atol=1e-13)
+
+
+def _trig_field_on(shape_eval, N, seed, d):
+    """A closed-form vector field of trigonometric order N (sum of a few modes k in Z_N with
+    random amplitudes) evaluated at the nodes of the grid `shape_eval`."""
+    rng = np.random.default_rng(seed)
+    xs = ms.node_coords(shape_eval)
+    out = np.zeros((d,) + tuple(shape_eval))
+    for _ in range(5):
+        k = np.array([rng.integers(-(n - 1) // 2, (n - 1) // 2 + 1) for n in N])
+        amp = rng.standard_normal((d, 2))
+        t = np.broadcast_to(sum(2 * np.pi * k[i] * xs[i] for i in range(d)), shape_eval)
+        for i in range(d):
+            out[i] += amp[i, 0] * np.cos(t) + amp[i, 1] * np.sin(t)
+    return out
+
+
+@pytest.mark.parametrize("N,M", [((7, 9), (13, 17)), ((5, 3, 7), (9, 5, 13)), ((9,), (19,))])
+def test_restriction_samples_the_trigonometric_polynomial(N, M):
+    # R^{-1}: values of a polynomial of order N on the grid M -> its values at the N nodes,
+    # checked against the closed form evaluated directly on both grids
+    d = len(N)
+    vM = _trig_field_on(M, N, 31, d)
+    vN = _trig_field_on(N, N, 31, d)
+    np.testing.assert_allclose(O.restrict(vM, N), vN, atol=1e-11)
+
+
+def test_restriction_inverts_prolongation():
+    N, M = (7, 5, 9), (13, 11, 17)
+    x = ms.random_field((3,) + N, 4)
+    np.testing.assert_allclose(O.restrict(O.prolongate(x, M), N), x, atol=1e-12)
+    # and the M-grid field of an exact-integration solve lies in the range of G_{N,M}: its
+    # restriction, prolonged again, returns it
+    y = O.project(ms.random_field((3,) + M, 5), support=N)
+    np.testing.assert_allclose(O.prolongate(O.restrict(y, N), M), y, atol=1e-12)
