@@ -295,6 +295,40 @@ def pass_flops(rmax):
     }
 
 
+def pass_flops_model(n=None):
+    """Algorithmic flops of one launch of each pass kind by the standard model of an FFT,
+    2.5 n log2 n per real transform of length n along each axis: a pass that transforms one
+    axis of the d components counts d x 2.5 |N| log2(n_axis); the projection pass transforms
+    axis 0 forward and inverse. One matvec sums to 2 d x 2.5 |N| log2 |N| (5.1 GFLOP at
+    243^3)."""
+    import math
+    n0, n1, n2 = N_GRID if n is None else n
+    nodes = n0 * n1 * n2
+    per_axis = lambda m: D * 2.5 * nodes * math.log2(m)  # noqa: E731
+    return {"line_fwd": per_axis(n2), "strided": per_axis(n1), "proj": 2 * per_axis(n0),
+            "line_inv": per_axis(n2)}
+
+
+def measure_fp64_peak(H, local):
+    """FP64 rate of this GPU, measured with the library's DFMA / DADD chain kernel
+    (hom_measure_fp64): best of three timed waves each, SM clock sampled meanwhile."""
+    import torch
+    clocks = ClockSampler(local)
+    clocks.start()
+    best_fma, best_add = 0.0, 0.0
+    for _ in range(3):
+        ms_, ops = H.hom_measure_fp64(0, 1500)
+        best_fma = max(best_fma, ops / ms_ / 1e9)
+        ms_, ops = H.hom_measure_fp64(1, 1500)
+        best_add = max(best_add, ops / ms_ / 1e9)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    return {"dfma_tflops": round(best_fma, 4), "dadd_tinstr_per_s": round(best_add, 4),
+            "sm_mhz": clk.get("sm_mhz"), "reasons": clk.get("reasons"),
+            "how": "hom_measure_fp64: 8 independent FP64 FMA (or add) chains per thread, one "
+                   "full wave of resident CTAs on every SM, CUDA events, best of 3"}
+
+
 # DRAM bytes (read + write) of one launch of the dominant kernels of the 243^3 CG steps, from
 # one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum on GB300; other kernels and
 # grids have no capture (null)
@@ -350,6 +384,7 @@ def run_ours(args, rank, world, local):
     prob = H.Problem(D, N_GRID, H.phase_material(ph, table),
                      precision=H.HOM_FP32_REFINED if fp32_only else H.HOM_FP64)
     tune = H.hom_autotune(prob.h, reps=2)  # the launch plan a user gets from the autotuner
+    fp64_peak = None if args.quick else measure_fp64_peak(H, local)
     stream = torch.cuda.current_stream()
     total = args.warmup + args.steps
     if fp32_only:  # the FP32 inner CG step of the refinement (profiling helper)
@@ -409,55 +444,42 @@ def run_ours(args, rank, world, local):
     H.hom_solve_end(p32.h, D, allow_not_converged=True)
     p32.close()
 
-    # ---- end to end: host field -> device, one G A application, result -> host, every step;
-    # the uploads and downloads run on their own streams with two device buffers each, so
-    # step k+1's upload and step k-1's download overlap step k's operator ----
+    # ---- end to end through the C ABI: every step hom_apply reads the field from pinned host
+    # memory and writes the result back to pinned host memory (HOM_OP_X_HOST | HOM_OP_Y_HOST:
+    # the pass kernels load and store the host buffers through their device mapping), and the
+    # call returns once the result is in host memory ----
     nfield = D * int(np.prod(N_GRID))
-    xh = torch.empty(nfield, dtype=torch.float64).pin_memory()
-    yh = [torch.empty(nfield, dtype=torch.float64).pin_memory() for _ in range(2)]
-    xh.copy_(torch.from_numpy(ms.random_field((nfield,), 11)))
-    xd = [prob.field(), prob.field()]
-    yd = [prob.field(), prob.field()]
-    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-
-    def e2e_steps(nsteps, start):
-        s_in.wait_event(start)
-        s_out.wait_event(start)
-        ev_in = [torch.cuda.Event() for _ in range(nsteps)]
-        ev_done = [torch.cuda.Event() for _ in range(nsteps)]
-        ev_out = [torch.cuda.Event() for _ in range(nsteps)]
-        for k in range(nsteps):
-            b = k % 2
-            if k >= 2:
-                s_in.wait_event(ev_done[k - 2])   # xd[b] is free once step k-2 has run
-            with torch.cuda.stream(s_in):
-                xd[b].view(-1).copy_(xh, non_blocking=True)
-            ev_in[k].record(s_in)
-            stream.wait_event(ev_in[k])
-            if k >= 2:
-                stream.wait_event(ev_out[k - 2])  # yd[b] is free once step k-2 is downloaded
-            H.hom_apply(prob.h, H.HOM_OP_LINEAR, None, xd[b], yd[b])
-            ev_done[k].record(stream)
-            s_out.wait_event(ev_done[k])
-            with torch.cuda.stream(s_out):
-                yh[b].copy_(yd[b].view(-1), non_blocking=True)
-            ev_out[k].record(s_out)
-        stream.wait_event(ev_out[nsteps - 1])
-
-    w0 = torch.cuda.Event()
-    w0.record(stream)
-    e2e_steps(2, w0)
+    xh = torch.from_numpy(ms.random_field((D,) + tuple(N_GRID), 11)).pin_memory()
+    yh = torch.empty((D,) + tuple(N_GRID), dtype=torch.float64).pin_memory()
+    for _ in range(args.warmup):
+        H.hom_apply(prob.h, H.HOM_OP_LINEAR, None, xh, yh)
     torch.cuda.synchronize()
-    e_steps = max(3, min(args.steps, 10))
     barrier(world)
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
+    t_e2e = time.perf_counter()
     f0.record(stream)
-    e2e_steps(e_steps, f0)
+    for _ in range(args.steps):
+        H.hom_apply(prob.h, H.HOM_OP_LINEAR, None, xh, yh)
     f1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(f0.elapsed_time(f1), world) / e_steps
-    del xd, yd
+    e2e_wall_ms = (time.perf_counter() - t_e2e) * 1e3 / args.steps
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1), world) / args.steps
+    # the same application on device-resident fields, for the cost of the host traffic
+    xdev = xh.cuda()
+    ydev = torch.empty_like(xdev)
+    H.hom_apply(prob.h, H.HOM_OP_LINEAR, None, xdev, ydev)
+    torch.cuda.synchronize()
+    d0 = torch.cuda.Event(enable_timing=True)
+    d1 = torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    for _ in range(args.steps):
+        H.hom_apply(prob.h, H.HOM_OP_LINEAR, None, xdev, ydev)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    dev_apply_ms = d0.elapsed_time(d1) / args.steps
+    e2e_equal = bool(torch.equal(ydev.cpu(), yh))
+    del xdev, ydev
 
     # ---- the same matvec with cuFFT (torch.fft), a timed comparison only ----
     xr = torch.from_numpy(ms.random_field((D,) + tuple(N_GRID), 12)).cuda()
@@ -482,7 +504,8 @@ def run_ours(args, rank, world, local):
 
     if rank != 0:
         return None
-    flops = pass_flops(tune["rmax64"])
+    flops = pass_flops_model()
+    flops_radix = pass_flops(tune["rmax64"])
     byts = pass_bytes(8, fused_cg=True)
     byts32 = pass_bytes(4, two_line=bool(tune32.get("two_line32")), fused_cg=True)
     peaks = measured_peaks()
@@ -501,7 +524,7 @@ def run_ours(args, rank, world, local):
     dom = max((k for k in pk if k in flops), key=lambda k: pk[k]["ms_avg"] * pk[k]["launches"])
     dom_ms = pk[dom]["ms_avg"]
     achieved = flops[dom] / (dom_ms * 1e-3) / 1e12
-    peak = 1.25  # FP64 TFLOP/s: 152 SMs x 2 DFMA/clk x 2 flops x ~2.07 GHz (nominal)
+    peak = fp64_peak["dfma_tflops"]  # measured on this GPU before the timed region
     # compulsory bytes of one step: per kind, bytes per launch x launches per step (measured)
     step_bytes = sum(byts[k] * pk[k]["launches"] / args.steps for k in pk if k in byts)
     pk32 = per_kind(passes32)
@@ -518,14 +541,23 @@ def run_ours(args, rank, world, local):
                           "plan": {"fp64_rmax": tune["rmax64"], "fp64_smem_kb": tune["smem_kb64"]}}),
         "e2e": {"value": round(world * 1000.0 / e2e_ms, 3), "unit": UNIT,
                 "h2d_bytes_per_step": nfield * 8, "d2h_bytes_per_step": nfield * 8,
-                "path": "pinned host field -> hom_apply(HOM_OP_LINEAR) -> pinned host field, every "
-                        "step; uploads and downloads on their own streams overlap the neighbouring "
-                        "steps' operators"},
+                "ms_per_step": round(e2e_ms, 4), "host_wall_ms_per_step": round(e2e_wall_ms, 4),
+                "device_fields_ms_per_matvec": round(dev_apply_ms, 4),
+                "result_equals_device_path": e2e_equal,
+                "path": "C ABI hom_apply(HOM_OP_LINEAR | HOM_OP_X_HOST | HOM_OP_Y_HOST) on pinned "
+                        "host buffers, every step: the first pass reads x from host memory and "
+                        "the last writes y to host memory (over the GPU's host link), the call "
+                        "returns with y in host memory; K steps between CUDA events"},
         "gpu_launches": int(launches),
         "hbm_gbs": round(step_bytes / (ms_step * 1e-3) / 1e9, 1),
         "roofline": {"bound": "alu", "kernel": f"k_{dom}", "achieved": round(achieved, 4),
                      "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                     "traffic": ncu_traffic("fp64", dom), "peak_source": "recipe nominal FP64 (1.25 TFLOP/s)",
+                     "traffic": ncu_traffic("fp64", dom),
+                     "peak_source": "measured FP64 FMA rate of this GPU (hom_measure_fp64, burst)",
+                     "peak_nominal": 1.25, "flop_model": "2.5 n log2 n per real transform and axis",
+                     "flops_per_launch": round(flops[dom]),
+                     "achieved_radix_model": round(flops_radix[dom] / (dom_ms * 1e-3) / 1e12, 4),
+                     "fp64_probe": fp64_peak,
                      "hbm_gbs_of_dominant": round(byts[dom] / (dom_ms * 1e-3) / 1e9, 1)},
         "passes": pk,
         "fp32_step": {"metric": "G·A matvecs/s at 243^3 (FP32 CG step, inner solver of the refinement)",
@@ -550,6 +582,18 @@ def run_ours(args, rank, world, local):
                        "device_ms": round(stats["time_ms"], 2), "A_H": AH,
                        "converged": bool(stats["converged"])},
     }
+    if not args.no_elastic:
+        line["elastic"] = elastic_step(min(args.steps, 10), 3)
+    if not args.no_served:
+        # a short served run (driver-visible): 12 requests over 0.5 s, Richardson capped at
+        # 2000 iterations (--serve runs longer mixes with the cap at 1e5)
+        sv = served_mix(12, 0.5, 64.0, 2000)
+        line["served"] = {k: sv[k] for k in ("value", "unit", "p50_ms", "p99_ms", "fp32_refined",
+                                             "fp64", "speedup_vs_fp64",
+                                             "AH_max_rel_diff_fp32_refined_vs_fp64",
+                                             "AH_compared_requests", "config")}
+    if not args.no_c4:
+        line["c4_405_refined"] = c4_check()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_cg_steps(1)
     return line
@@ -561,37 +605,52 @@ def run_ours(args, rank, world, local):
 
 def served_requests(n_req, seed=2024):
     """Seeded heterogeneous requests: odd grids from {45, 81, 135, 243}^3, periodic random
-    spheres (volume fraction U[0.1, 0.4]), contrast logU[10, 1e4], anisotropic SPD phase
-    tensors R diag(lambda) R^T (Haar R, lambda = scale x logU[1, 3], scale 1 for the matrix and
-    the contrast for every sphere), random unit E, CG or Chebyshev, tolerance 1e-6."""
+    spheres (volume fraction U[0.1, 0.4], radii U[0.02, 0.06] of the cell but at least 1.5
+    nodes, so that a sphere on the 45^3 grid covers more than one node), contrast
+    logU[10, 1e4], anisotropic SPD phase tensors R diag(lambda) R^T (Haar R,
+    lambda = scale x logU[1, 3], scale 1 for the matrix and the contrast for every sphere),
+    random unit E, solver uniform over Richardson, CG, Chebyshev and Eyre-Milton, tolerance
+    1e-6."""
     rng = np.random.default_rng(seed)
     reqs = []
     grids = [45, 81, 135, 243]
     probs = [0.35, 0.35, 0.2, 0.1]
+    solvers = ["richardson", "cg", "chebyshev", "eyre_milton"]
     for i in range(n_req):
         n = int(rng.choice(grids, p=probs))
         vf = rng.uniform(0.1, 0.4)
         contrast = float(np.exp(rng.uniform(np.log(10.0), np.log(1e4))))
-        ph, _, radii = ms.rsa_spheres((n,) * 3, seed + i, rmin=0.04, rmax=0.1, vf=vf)
+        rmin = max(0.02, 1.5 / n)
+        rmax = max(0.06, rmin + 0.02)
+        ph, _, radii = ms.rsa_spheres((n,) * 3, seed + i, rmin=rmin, rmax=rmax, vf=vf)
         scales = np.concatenate([[1.0], np.full(len(radii), contrast)])
         table = ms.random_spd_table(len(scales), 3, seed + 1000 + i, scales)
         E = ms.random_unit_vector(3, seed + 2000 + i)
-        solver = "cg" if rng.random() < 0.5 else "chebyshev"
+        solver = solvers[int(rng.integers(0, 4))]
         reqs.append({"n": n, "phase": ph, "table": table, "E": E, "solver": solver,
                      "contrast": contrast, "vf": float((ph > 0).mean())})
     return reqs
 
 
-def run_served(args):
+# the FP32-refined arm runs the two solvers it has inner FP32 kernels for: CG for requests
+# drawn as CG or Richardson, Chebyshev for Chebyshev or Eyre-Milton
+REFINED_SOLVER = {"richardson": "cg", "cg": "cg", "chebyshev": "chebyshev",
+                  "eyre_milton": "chebyshev"}
+
+
+def served_mix(n_req, window, budget_gb, rich_maxit, seed=2024):
+    """Serve the seeded mix through hom_server (Poisson arrivals over `window` seconds), once
+    in plain FP64 with the drawn solvers and once FP32-refined; solves/s, p50/p99 latency,
+    converged and non-converged requests, and the A_H agreement of the two arms."""
     import torch
     import paper_1508_02045_gb300 as H
 
-    reqs = served_requests(args.serve)
-    rng = np.random.default_rng(7)
-    arrivals = np.cumsum(rng.exponential(args.serve_window / len(reqs), size=len(reqs)))
+    reqs = served_requests(n_req, seed)
+    rng = np.random.default_rng(seed + 7)
+    arrivals = np.cumsum(rng.exponential(window / len(reqs), size=len(reqs)))
     out = {}
     for label, prec in (("fp64", H.HOM_FP64), ("fp32_refined", H.HOM_FP32_REFINED)):
-        S = H.hom_server_create(int(args.serve_budget_gb * (1 << 30)), max_batch=8)
+        S = H.hom_server_create(int(budget_gb * (1 << 30)), max_batch=8)
         mats = [H.phase_material(r["phase"], r["table"]) for r in reqs]
         submitted, results = {}, {}
         torch.cuda.synchronize()
@@ -602,8 +661,14 @@ def run_served(args):
             now = time.perf_counter() - t0
             while nxt < len(reqs) and arrivals[nxt] <= now:
                 r = reqs[nxt]
-                q = H.make_request(3, (r["n"],) * 3, mats[nxt], r["E"], H.SOLVERS[r["solver"]],
-                                   1e-6, precision=prec, opts=H.make_opts(maxit=3000 if prec == H.HOM_FP64 else 50))
+                if prec == H.HOM_FP64:
+                    solver = r["solver"]
+                    maxit = rich_maxit if solver == "richardson" else 20000
+                else:
+                    solver = REFINED_SOLVER[r["solver"]]
+                    maxit = 50
+                q = H.make_request(3, (r["n"],) * 3, mats[nxt], r["E"], H.SOLVERS[solver], 1e-6,
+                                   precision=prec, opts=H.make_opts(maxit=maxit))
                 submitted[H.hom_server_submit(S, q)] = nxt
                 nxt += 1
             active, queued, _ = H.hom_server_status(S)
@@ -618,28 +683,149 @@ def run_served(args):
         wall = time.perf_counter() - t0
         H.hom_server_destroy(S)
         lat = np.array([results[i]["latency_ms"] for i in range(len(reqs))])
+        conv = [bool(results[i]["stats"]["converged"]) for i in range(len(reqs))]
+        by_solver = {}
+        for i, r in enumerate(reqs):
+            sv = r["solver"] if prec == H.HOM_FP64 else REFINED_SOLVER[r["solver"]]
+            e = by_solver.setdefault(sv, {"requests": 0, "converged": 0})
+            e["requests"] += 1
+            e["converged"] += int(conv[i])
         out[label] = {"solves_per_s": round(len(reqs) / (wall - arrivals[0]), 3),
                       "p50_ms": round(float(np.percentile(lat, 50)), 1),
                       "p99_ms": round(float(np.percentile(lat, 99)), 1),
                       "wall_s": round(wall, 2), "steps": steps,
-                      "converged": int(sum(results[i]["stats"]["converged"] for i in range(len(reqs)))),
-                      "AH": [results[i]["AH_EE"] for i in range(len(reqs))]}
+                      "converged": int(sum(conv)), "not_converged": int(len(conv) - sum(conv)),
+                      "by_solver": by_solver,
+                      "AH": [results[i]["AH_EE"] for i in range(len(reqs))], "conv": conv}
     a64 = np.array(out["fp64"].pop("AH"))
     a32 = np.array(out["fp32_refined"].pop("AH"))
-    line = {"metric": "served solves/s (continuous batching, FP32 inner + FP64 refinement)",
+    c64 = out["fp64"].pop("conv")
+    c32 = out["fp32_refined"].pop("conv")
+    both = [i for i in range(len(reqs)) if c64[i] and c32[i]]
+    diff = float(np.max(np.abs(a32[both] - a64[both]) / np.abs(a64[both]))) if both else None
+    return {"metric": "served solves/s (continuous batching, FP32 inner + FP64 refinement)",
             "value": out["fp32_refined"]["solves_per_s"], "unit": "solves/s",
             "higher_is_better": True, "n_gpus": 1, "dtype": "f32 inner / f64 outer",
             "data": "synthetic (seeded random-sphere microstructures)",
             "config": {"workload": "served mix: grids {45,81,135,243}^3, RSA spheres vf 0.1-0.4, "
-                                   "contrast logU[10,1e4], anisotropic SPD phases, CG/Chebyshev, tol 1e-6",
-                       "requests": len(reqs), "arrival_window_s": args.serve_window,
-                       "hbm_budget_gb": args.serve_budget_gb, "max_batch": 8,
+                                   "radii 0.02-0.06 (>= 1.5 nodes), contrast logU[10,1e4], "
+                                   "anisotropic SPD phases, solver uniform over the four (FP64 "
+                                   "arm; the refined arm runs CG for CG/Richardson and Chebyshev "
+                                   "for Chebyshev/Eyre-Milton), tol 1e-6",
+                       "requests": len(reqs), "arrival_window_s": window,
+                       "hbm_budget_gb": budget_gb, "max_batch": 8,
+                       "richardson_maxit": rich_maxit,
                        "grid_counts": {str(g): int(sum(r["n"] == g for r in reqs)) for g in (45, 81, 135, 243)}},
             "p50_ms": out["fp32_refined"]["p50_ms"], "p99_ms": out["fp32_refined"]["p99_ms"],
             "fp32_refined": out["fp32_refined"], "fp64": out["fp64"],
             "speedup_vs_fp64": round(out["fp32_refined"]["solves_per_s"] / out["fp64"]["solves_per_s"], 2),
-            "AH_max_rel_diff_fp32_refined_vs_fp64": float(np.max(np.abs(a32 - a64) / np.abs(a64)))}
-    print(json.dumps(line), flush=True)
+            "AH_max_rel_diff_fp32_refined_vs_fp64": diff,
+            "AH_compared_requests": len(both)}
+
+
+def elastic_step(steps, warmup, n=243):
+    """Linear elasticity (the strain form, six Mandel components) on the bench geometry: the
+    243^3 cube of volume fraction 0.2, isotropic phases (lambda, mu) = (1, 1) and (1000, 1000),
+    E = e_11; `steps` FP64 CG steps timed with CUDA events (inputs larger than L2: 688 MB a
+    field), the operator's passes by kind."""
+    import torch
+    import paper_1508_02045_gb300 as H
+    N = (n,) * 3
+    ph = ms.box_phase(N, ms.inclusion_side_for_fraction(VF, D))
+    table = np.array([elastic_stiffness(1.0, 1.0), elastic_stiffness(CONTRAST, CONTRAST)])
+    P = H.Problem(3, N, H.stiffness_material(ph, table))
+    E = np.array([1.0, 0, 0, 0, 0, 0])
+    H.hom_solve_begin(P.h, E, H.HOM_CG, 0.0, H.make_opts(fixed_iters=steps + warmup + 1))
+    H.hom_solve_iterate(P.h, warmup)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    H.hom_profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    H.hom_solve_iterate(P.h, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    H.hom_profile_enable(False)
+    passes = H.hom_profile_read()
+    ms_step = e0.elapsed_time(e1) / steps
+    H.hom_solve_end(P.h, 6, allow_not_converged=True)
+    P.close()
+    return {"metric": "G·C matvecs/s at 243^3, linear elasticity (FP64 CG step, 6 components)",
+            "value": round(1000.0 / ms_step, 3), "unit": UNIT, "ms_per_step": round(ms_step, 4),
+            "steps": steps, "grid": list(N),
+            "passes": {k: {"ms_avg": round(v[0] / v[1], 4), "launches": v[1]}
+                       for k, v in passes.items() if v[1]}}
+
+
+def elastic_stiffness(lam, mu):
+    """Mandel matrix (3-D) of the isotropic stiffness lam tr(e) I + 2 mu e (an input table)."""
+    C = np.zeros((6, 6))
+    C[:3, :3] = lam
+    for a in range(3):
+        C[a, a] += 2 * mu
+    for m in range(3, 6):
+        C[m, m] = 2 * mu
+    return C
+
+
+def run_served(args):
+    print(json.dumps(served_mix(args.serve, args.serve_window, args.serve_budget_gb,
+                                args.serve_rich_maxit)), flush=True)
+
+
+def c4_check():
+    """Configuration 4 (405^3 random spheres, FP32 inner CG in FP64 refinement, tolerance 1e-8)
+    with its error stated against the FP64 oracle: the oracle evaluates, at the refined
+    solution x, the residual ||C x - b|| (one oracle matvec) and the energy. Since C is SPD on
+    the conforming space with smallest eigenvalue >= c_A and x - x* lies in that space, the
+    A_H of x exceeds the exact discrete A_H by (C(x - x*), x - x*) <= ||C x - b||^2 / c_A, a
+    bound computed by the oracle alone. The plain FP64 solve runs beside it."""
+    import torch
+    import oracle as O
+    import paper_1508_02045_gb300 as H
+
+    N = (405,) * 3
+    E = np.array([1.0, 0.0, 0.0])
+    ph, _, radii = ms.rsa_spheres(N, 1, vf=0.3)
+    rng = np.random.default_rng(101)
+    table = ms.isotropic_table(np.concatenate(
+        [[1.0], np.exp(rng.uniform(np.log(10), np.log(1000), len(radii)))]), 3)
+    out = {"grid": list(N), "spheres": int(len(radii)), "vf": float((ph > 0).mean()), "tol": 1e-8}
+    for label, prec, maxit in (("fp32_refined", H.HOM_FP32_REFINED, 50), ("fp64", H.HOM_FP64, 3000)):
+        P = H.Problem(3, N, H.phase_material(ph, table), precision=prec)
+        x = P.field() if label == "fp32_refined" else None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        AH, _, st, _ = H.hom_solve(P.h, E, H.HOM_CG, 1e-8, H.make_opts(maxit=maxit), x,
+                                   allow_not_converged=True)
+        torch.cuda.synchronize()
+        out[label] = {"A_H": AH, "seconds": round(time.perf_counter() - t0, 3),
+                      "iterations": st["iterations"], "inner_iterations": st["inner_iterations"],
+                      "converged": bool(st["converged"]), "true_residual": st["true_residual"]}
+        if x is not None:
+            xh = x.cpu().numpy()
+        del x
+        P.close()
+    t0 = time.perf_counter()
+    A = O.expand_phase(ph, table)[0, 0]
+    sysn = O.GaNi(A, 3)
+    v = sysn.const(E) + xh
+    res = sysn.matvec(v)                       # C x - b = G A (E + x)
+    rn = float(np.sqrt(np.mean(np.sum(res * res, axis=0))))
+    en = O.energy(A, v)
+    cA = float(A.min())
+    AH32 = out["fp32_refined"]["A_H"]
+    out["oracle_check"] = {
+        "residual_norm": rn, "energy_at_x": en,
+        "A_H_minus_oracle_energy_rel": abs(AH32 - en) / en,
+        "A_H_error_bound_rel": rn * rn / cA / en,
+        "seconds": round(time.perf_counter() - t0, 1),
+        "what": "FP64 NumPy oracle at the refined solution x: ||C x - b|| (one matvec), its "
+                "energy, and the bound ||C x - b||^2 / c_A on A_H(x) - A_H(x*)"}
+    out["A_H_rel_diff_fp32_refined_vs_fp64"] = abs(AH32 - out["fp64"]["A_H"]) / out["fp64"]["A_H"]
+    out["speedup"] = round(out["fp64"]["seconds"] / out["fp32_refined"]["seconds"], 2)
+    return out
 
 
 # ------------------------------------------------------------------------------------------
@@ -840,6 +1026,10 @@ def main():
     ap.add_argument("--serve", type=int, default=0, help="run the served mix with this many requests")
     ap.add_argument("--serve-window", type=float, default=1.0)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
+    ap.add_argument("--serve-rich-maxit", type=int, default=100000)
+    ap.add_argument("--no-served", action="store_true", help="skip the short served run")
+    ap.add_argument("--no-c4", action="store_true", help="skip the 405^3 refinement check")
+    ap.add_argument("--no-elastic", action="store_true", help="skip the elasticity step")
     ap.add_argument("--configs", action="store_true", help="run configurations 1-4 end to end")
     ap.add_argument("--configs-maxit", type=int, default=20000)
     ap.add_argument("--kappa", type=int, default=0,

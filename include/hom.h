@@ -28,6 +28,14 @@
  *  - Every entry point returns a hom_status. On an error no output is written unless stated.
  *  - Ownership: hom_create copies the coefficient data; the caller keeps its buffers. The
  *    problem handle owns all device memory it allocates; hom_destroy frees it.
+ *  - Elasticity (HOM_A_STIFFNESS; Section 1 names it among the "more involved applications"):
+ *    fields are symmetric strain tensors with nc = d (d + 1) / 2 components in Mandel order
+ *    (d = 2: e_11, e_22, sqrt2 e_12; d = 3: e_11, e_22, e_33, sqrt2 e_23, sqrt2 e_13,
+ *    sqrt2 e_12), so the Frobenius product is the Euclidean product of the components; the
+ *    projection G of eq. (discrete_proj) becomes the orthogonal projection onto compatible
+ *    strains, Gamma^(k) e = (k q^T + q k^T)/|k|^2 - (k.e.k) k k^T/|k|^4 with q = e k, and
+ *    (A_H E, E) the energy (C(E + e), E + e). Wherever this header says "d components" or
+ *    "d doubles" for a field, E or a flux, read nc for such a problem.
  */
 #ifndef HOM_H
 #define HOM_H
@@ -48,7 +56,9 @@ typedef enum {
   HOM_ERR_UNSUPPORTED = 3,    /* e.g. Eyre-Milton with exact integration (Section 3.4)     */
   HOM_ERR_NOT_CONVERGED = 4,  /* iteration limit reached; results are still written        */
   HOM_ERR_CUDA = 5,           /* a CUDA call failed                                        */
-  HOM_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired                        */
+  HOM_ERR_TIMEOUT = 6,        /* reserved: no entry point waits on the device (the grid
+                                 reductions take a completion ticket and never spin), so
+                                 none returns it                                           */
   HOM_ERR_SCRATCH = 7         /* problem larger than the static scratch of hom_apply_static */
 } hom_status;
 
@@ -67,16 +77,20 @@ typedef enum { HOM_FP64 = 0 /* all arithmetic in FP64 */,
 typedef enum {
   HOM_A_PHASE = 0,   /* phase index per node (uint8 or uint16) + nphase x d x d SPD table   */
   HOM_A_SCALAR = 1,  /* one isotropic conductivity (double) per node                         */
-  HOM_A_FOURIER = 2  /* exact integration only: isotropic coefficients A^(n), n in Z_M, as
+  HOM_A_FOURIER = 2, /* exact integration only: isotropic coefficients A^(n), n in Z_M, as
                         interleaved complex doubles (re, im) in FFT-natural order on the
                         double grid M (eq. (Ga_exact_integration))                           */
+  HOM_A_STIFFNESS = 3 /* linear elasticity (GaNi, FP64): phase index per node + nphase
+                        symmetric positive definite stiffness matrices nc x nc in Mandel form,
+                        nc = d (d + 1) / 2; see "Elasticity" below                          */
 } hom_material_kind;
 
 typedef struct {
   int kind;              /* hom_material_kind                                                */
   const void* data;      /* PHASE: |N| indices; SCALAR: |N| doubles; FOURIER: |M| complex    */
   int index_bytes;       /* PHASE: 1 (uint8) or 2 (uint16)                                    */
-  const double* table;   /* PHASE: nphase row-major symmetric d x d tensors (host)            */
+  const double* table;   /* PHASE: nphase row-major symmetric d x d tensors (host);
+                            STIFFNESS: nphase row-major symmetric nc x nc Mandel matrices     */
   int nphase;            /* PHASE: table length                                               */
   int data_on_device;    /* 1 if data is a device pointer                                     */
   double cA, CA;         /* bounds of eq. (A); 0 = derive from the table / field. Required for
@@ -98,7 +112,19 @@ typedef struct {
                       /* HOM_FP32_REFINED uses maxit as the outer limit (0 = 50); only CG
                          and Chebyshev run as inner solvers                                 */
   int check_every;    /* host polls the device stopping flag every this many iterations (0=8) */
+  int out_flags;      /* hom_out_flag bits for the corrector output of hom_solve, hom_solve_end
+                         and hom_solve_current                                                */
 } hom_opts;
+
+/* Where and on which grid the solve returns the corrector e (field of hom_opts.out_flags). */
+typedef enum {
+  HOM_OUT_HOST = 1,   /* the corrector argument is a HOST pointer (any host memory; the field is
+                         copied out before the call returns)                                  */
+  HOM_OUT_NGRID = 2   /* exact integration: return the samples of the corrector on the nodes of
+                         the N grid (d x |N| doubles) instead of its values on the solve grid M
+                         (d x |M|). The Ga iterate is a trigonometric polynomial of order N
+                         (Section 2.3), so its N-grid samples determine it; no effect for GaNi */
+} hom_out_flag;
 
 typedef struct {
   int iterations;     /* iterations of the (outer) solver                                      */
@@ -115,8 +141,10 @@ typedef enum {
   HOM_OP_LINEAR = 1,  /* y = G A x = C x                                                        */
   HOM_OP_PROJECT = 2, /* y = G x                                   eq. (discrete_proj)          */
   HOM_OP_EM = 3,      /* y = F^{-1}(I - 2 G^)F (A - omega I) x     Algorithm 4, omega = sqrt(cA CA)*/
-  HOM_OP_FP32 = 16    /* flag, or-ed into the above: apply the FP32 operator of a
+  HOM_OP_FP32 = 16,   /* flag, or-ed into the above: apply the FP32 operator of a
                          HOM_FP32_REFINED problem (x rounded to FP32, y widened to FP64)     */
+  HOM_OP_X_HOST = 32, /* flag: x is a HOST pointer                                             */
+  HOM_OP_Y_HOST = 64  /* flag: y is a HOST pointer                                             */
 } hom_op;
 
 /* Create a problem on grid N (GaNi: the solve grid; Ga: the trigonometric order, the solve grid
@@ -139,14 +167,25 @@ int hom_grid(const hom_problem* P, int* M_out, long long* nodes);
 /* Spectral bounds c_A, C_A used by the solvers (eq. (A)). */
 int hom_bounds(const hom_problem* P, double* cA, double* CA);
 
-/* One application of the FFT-based operator (see hom_op) on device fields x_dev -> y_dev
- * (d x |grid| doubles each; x_dev may equal y_dev). E (host, d doubles) is read by
- * HOM_OP_AFFINE only. Enqueued on the problem's stream; does not synchronise. */
+/* One application of the FFT-based operator (see hom_op) on fields x -> y (d x |grid| doubles
+ * each; x may equal y). E (host, d doubles) is read by HOM_OP_AFFINE only.
+ * x and y are device pointers unless flagged HOM_OP_X_HOST / HOM_OP_Y_HOST in op:
+ *  - page-locked host memory (cudaHostAlloc, cudaHostRegister, torch pin_memory) is read and
+ *    written by the pass kernels themselves through its device mapping (over the host link
+ *    of the GPU, no staging copy); x is read once by the first pass and y written once by
+ *    the last;
+ *  - any other host memory is staged through one of the problem's device vectors with copies
+ *    on the stream (those copies wait for the host).
+ * With device pointers only, the call is enqueued on the problem's stream and does not
+ * synchronise; with a host y it returns once y holds the result. During a solve session the
+ * staging vector is the one the solvers leave free between steps. */
 int hom_apply(hom_problem* P, int op, const double* E, const double* x_dev, double* y_dev);
 
 /* Solve C x = b (eq. (linsys)) for macroscopic field E (host, d doubles) with the given solver
  * and tolerance, starting from x_0 = 0 (Eyre-Milton: x_0 = E). Writes, when non-NULL:
- * x_dev (device, d x |grid|): the corrector e (Eyre-Milton: e = G x_m, Section 4.4);
+ * x_dev: the corrector e (Eyre-Milton: e = G x_m, Section 4.4), d x |grid| doubles on the
+ * device (opts->out_flags: HOM_OUT_HOST for a host pointer, HOM_OUT_NGRID for the N-grid
+ * samples of a Ga corrector, d x |N| doubles);
  * AH_EE: (A_H E, E) as the energy (A(E + e), E + e) on the solve grid (eqs. (GaNi),
  * (ev_bounds_Ga)); flux (d doubles): <A(E + e)>; stats. Eyre-Milton with HOM_EXACT returns
  * HOM_ERR_UNSUPPORTED (Section 3.4). Returns HOM_ERR_NOT_CONVERGED, with outputs written, when
@@ -219,11 +258,14 @@ int hom_bound(hom_problem* gani, hom_problem* ga, const double* E, const double*
  *
  * Arguments: d = 2 or 3, N (d odd orders, as hom_create), phase_dev a DEVICE array of |N|
  * phase indices (index_bytes 1 = uint8, 2 = uint16), table a HOST array of nphase row-major
- * SPD d x d tensors (validated like hom_create), op one of hom_op (HOM_OP_EM uses
- * omega = sqrt(c_A C_A) of the table), E (host, d doubles; read by HOM_OP_AFFINE only),
- * x_dev / y_dev device fields of d x |N| doubles in the layout of hom_apply (distinct
- * buffers), stream a cudaStream_t or NULL. The result equals hom_apply's for the same
- * problem (same kernels).
+ * SPD d x d tensors (symmetry and positive definiteness checked as in hom_create), op one of
+ * hom_op (HOM_OP_EM uses omega = sqrt(c_A C_A) of the table), E (host, d doubles; read by
+ * HOM_OP_AFFINE only), x_dev / y_dev device fields of d x |N| doubles in the layout of
+ * hom_apply (distinct buffers), stream a cudaStream_t or NULL. The result equals hom_apply's
+ * for the same problem (same plans, tables and kernels).
+ * Precondition: every phase index is below nphase. The indices live on the device and are
+ * not checked (hom_create reads them back and rejects them; this call does not); an index
+ * out of range reads past the coefficient table and gives a wrong result.
  *
  * Limits and errors: the half spectrum (16 d |N| (N_d + 1) / (2 N_d) bytes) must fit in
  * HOM_STATIC_SCRATCH_BYTES minus 576 KiB (e.g. 135^3 with d = 3 fits, 243^3 does not); larger
@@ -234,8 +276,10 @@ int hom_bound(hom_problem* gani, hom_problem* ga, const double* E, const double*
  * spectrum entry before reading them). Calls whose work overlaps on the GPU (different
  * streams or threads without ordering) race on the scratch and give wrong results; issue them
  * on one stream or order them. Set-up: the first call on each device resolves the scratch
- * address (cudaGetSymbolAddress) and uploads constants, so make that first call before any
- * stream capture. Enqueued on `stream`; does not synchronise. */
+ * address (cudaGetSymbolAddress), uploads the DFT constants and sets the kernels'
+ * shared-memory limits, so make that first call before any stream capture. Every call then
+ * only enqueues kernels on `stream` (the twiddles and the table travel as kernel parameters,
+ * not by host-to-device copies) and returns without waiting for the GPU. */
 int hom_apply_static(int d, const int* N, const void* phase_dev, int index_bytes,
                      const double* table, int nphase, int op, const double* E,
                      const double* x_dev, double* y_dev, void* stream);
@@ -323,6 +367,25 @@ typedef struct {
                               between its column passes (specialised plans on axes 0 and 1) */
 } hom_tune_report;
 int hom_autotune(hom_problem* P, int reps, hom_tune_report* report);
+
+/* Samples on the N grid (d x |N| doubles, device y_dev) of a field x_dev on the solve grid M of
+ * an exact-integration problem whose spectrum lies in Z_N (every Ga iterate, Section 2.3):
+ * F_M, the coefficients of Z_N, F_N^{-1} (eq. (DFT)); the inverse of hom_prolongate. For
+ * GaNi problems (M = N) a copy. Enqueued on the problem's stream. */
+int hom_restrict(hom_problem* P, const double* x_dev, double* y_dev);
+
+/* Measurement utility (the paper has no counterpart): the FP64 rate of the current device.
+ * Launches one untimed and one timed wave of chains of independent FP64 instructions on every
+ * SM (kind 0: fused multiply-add, 2 flops each; kind 1: add, 1 flop), iters x 16 x 8 of them
+ * per thread, timed with CUDA events on `stream`. Writes the timed launch's milliseconds and
+ * its floating-point operations. Synchronises the stream. */
+int hom_measure_fp64(int kind, int iters, void* stream, double* ms, double* ops);
+
+/* Testing hook (the paper has no counterpart): make the n-th device allocation of the library
+ * from now on fail (n = 0: the next one) as cudaMalloc does on a device without free memory;
+ * the entry point that needed it frees what it had allocated and returns HOM_ERR_OOM. The
+ * failure fires once; n < 0 disarms. Process-wide. */
+int hom_debug_fail_alloc(int n);
 
 /* Free everything the handle owns. NULL is accepted. */
 void hom_destroy(hom_problem* P);

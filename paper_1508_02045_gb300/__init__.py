@@ -21,10 +21,12 @@ HOM_STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
 HOM_APPROX, HOM_EXACT = 0, 1
 HOM_RICHARDSON, HOM_CG, HOM_CHEBYSHEV, HOM_EYRE_MILTON = range(4)
 HOM_FP64, HOM_FP32_REFINED = 0, 1
-HOM_A_PHASE, HOM_A_SCALAR, HOM_A_FOURIER = range(3)
+HOM_A_PHASE, HOM_A_SCALAR, HOM_A_FOURIER, HOM_A_STIFFNESS = range(4)
 HOM_STOP_DEFAULT, HOM_STOP_RESIDUAL, HOM_STOP_INCREMENT = range(3)
 HOM_OP_AFFINE, HOM_OP_LINEAR, HOM_OP_PROJECT, HOM_OP_EM = range(4)
 HOM_OP_FP32 = 16
+HOM_OP_X_HOST, HOM_OP_Y_HOST = 32, 64
+HOM_OUT_HOST, HOM_OUT_NGRID = 1, 2
 
 SOLVERS = {"richardson": HOM_RICHARDSON, "cg": HOM_CG, "chebyshev": HOM_CHEBYSHEV,
            "eyre_milton": HOM_EYRE_MILTON}
@@ -35,7 +37,8 @@ EXPORTED = ["hom_create", "hom_grid", "hom_bounds", "hom_apply", "hom_solve", "h
             "hom_solve_end", "hom_apply_static", "hom_batch_create", "hom_batch_iterate",
             "hom_batch_destroy", "hom_server_create", "hom_server_submit", "hom_server_step",
             "hom_server_poll", "hom_server_status", "hom_server_destroy", "hom_autotune",
-            "hom_solve_history", "hom_solve_current", "hom_solve_nonconformity"]
+            "hom_solve_history", "hom_solve_current", "hom_solve_nonconformity", "hom_restrict",
+            "hom_measure_fp64", "hom_debug_fail_alloc"]
 PASS_KINDS = ["line_fwd", "strided", "proj", "line_inv", "vector"]
 
 
@@ -49,7 +52,7 @@ class hom_material(ctypes.Structure):
 class hom_opts(ctypes.Structure):
     _fields_ = [("maxit", ctypes.c_int), ("fixed_iters", ctypes.c_int), ("stop", ctypes.c_int),
                 ("cA", ctypes.c_double), ("CA", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("check_every", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("out_flags", ctypes.c_int)]
 
 
 class hom_stats(ctypes.Structure):
@@ -116,6 +119,9 @@ def _load():
     lib.hom_solve_current.argtypes = [vp, vp]
     lib.hom_solve_nonconformity.argtypes = [vp, dp]
     lib.hom_prolongate.argtypes = [vp, vp, vp, vp]
+    lib.hom_restrict.argtypes = [vp, vp, vp]
+    lib.hom_measure_fp64.argtypes = [ip, ip, vp, dp, dp]
+    lib.hom_debug_fail_alloc.argtypes = [ip]
     lib.hom_bound.argtypes = [vp, vp, dp, vp, dp]
     lib.hom_destroy.argtypes = [vp]
     lib.hom_destroy.restype = None
@@ -159,6 +165,18 @@ def _ptr(t):
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("expected a contiguous CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_or_dev(t):
+    """(pointer, on_host) of a contiguous float64 torch tensor (CUDA or CPU, pinned or not) or
+    NumPy array."""
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"] or t.dtype != np.float64:
+            raise ValueError("expected a C-contiguous float64 array")
+        return ctypes.c_void_p(t.ctypes.data), True
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr()), not t.is_cuda
 
 
 def _stream():
@@ -215,17 +233,44 @@ def hom_bounds(P):
 
 
 def hom_apply(P, op, E, x, y):
+    """x, y: CUDA tensors, or host tensors / arrays (flagged HOM_OP_X_HOST / HOM_OP_Y_HOST)."""
     Ep = _dvec(E) if E is not None else None
-    return _check(_lib.hom_apply(P, int(op), Ep, _ptr(x), _ptr(y)), "hom_apply")
+    xp, xh = _host_or_dev(x)
+    yp, yh = _host_or_dev(y)
+    flags = (HOM_OP_X_HOST if xh else 0) | (HOM_OP_Y_HOST if yh else 0)
+    return _check(_lib.hom_apply(P, int(op) | flags, Ep, xp, yp), "hom_apply")
+
+
+def hom_restrict(P, x, y):
+    return _check(_lib.hom_restrict(P, _ptr(x), _ptr(y)), "hom_restrict")
+
+
+def hom_measure_fp64(kind=0, iters=2000, stream=None):
+    """(milliseconds, floating-point operations) of one timed FP64 throughput wave."""
+    ms, ops = ctypes.c_double(), ctypes.c_double()
+    st = _stream() if stream is None else ctypes.c_void_p(stream)
+    _check(_lib.hom_measure_fp64(int(kind), int(iters), st, ctypes.byref(ms), ctypes.byref(ops)),
+           "hom_measure_fp64")
+    return ms.value, ops.value
+
+
+def hom_debug_fail_alloc(n):
+    return _check(_lib.hom_debug_fail_alloc(int(n)), "hom_debug_fail_alloc")
 
 
 def hom_solve(P, E, solver, tol, opts: hom_opts | None = None, x=None, allow_not_converged=False):
     AH = ctypes.c_double()
     d = len(E)
-    flux = (ctypes.c_double * 3)()
+    flux = (ctypes.c_double * 6)()
     stats = hom_stats()
+    xp = None
+    if x is not None:
+        xp, xh = _host_or_dev(x)
+        if xh:  # a host corrector output is flagged in the options
+            opts = make_opts() if opts is None else opts
+            opts.out_flags |= HOM_OUT_HOST
     o = ctypes.byref(opts) if opts is not None else None
-    st = _lib.hom_solve(P, _dvec(E), int(solver), float(tol), o, _ptr(x), ctypes.byref(AH), flux,
+    st = _lib.hom_solve(P, _dvec(E), int(solver), float(tol), o, xp, ctypes.byref(AH), flux,
                         ctypes.byref(stats))
     if not (st == HOM_OK or (allow_not_converged and st == HOM_ERR_NOT_CONVERGED)):
         raise HomError(st, "hom_solve")
@@ -283,7 +328,7 @@ def hom_solve_nonconformity(P):
 
 def hom_solve_end(P, d, x=None, allow_not_converged=False):
     AH = ctypes.c_double()
-    flux = (ctypes.c_double * 3)()
+    flux = (ctypes.c_double * 6)()
     stats = hom_stats()
     st = _lib.hom_solve_end(P, _ptr(x), ctypes.byref(AH), flux, ctypes.byref(stats))
     if not (st == HOM_OK or (allow_not_converged and st == HOM_ERR_NOT_CONVERGED)):
@@ -375,7 +420,7 @@ def hom_server_destroy(S):
 
 def hom_energy(P, E, x=None):
     en = ctypes.c_double()
-    flux = (ctypes.c_double * 3)()
+    flux = (ctypes.c_double * 6)()
     _check(_lib.hom_energy(P, _dvec(E), _ptr(x), ctypes.byref(en), flux), "hom_energy")
     return en.value, [flux[i] for i in range(len(E))]
 
@@ -420,6 +465,24 @@ def phase_material(phase: np.ndarray, table: np.ndarray, cA=0.0, CA=0.0, M=None)
     return m
 
 
+def stiffness_material(phase: np.ndarray, table: np.ndarray, cA=0.0, CA=0.0):
+    """Linear elasticity: phase image + (nphase, nc, nc) Mandel stiffness matrices,
+    nc = d (d + 1) / 2 (fields then have nc components, see include/hom.h)."""
+    phase = np.ascontiguousarray(phase)
+    if phase.dtype not in (np.uint8, np.uint16):
+        raise ValueError("phase image must be uint8 or uint16")
+    table = np.ascontiguousarray(table, dtype=np.float64)
+    m = hom_material()
+    m.kind = HOM_A_STIFFNESS
+    m.data = phase.ctypes.data
+    m.index_bytes = phase.dtype.itemsize
+    m.table = table.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    m.nphase = table.shape[0]
+    m.cA, m.CA = cA, CA
+    m._keep = (phase, table)
+    return m
+
+
 def scalar_material(a: np.ndarray, cA=0.0, CA=0.0, M=None):
     a = np.ascontiguousarray(a, dtype=np.float64)
     m = hom_material()
@@ -447,10 +510,11 @@ def fourier_material(Ahat: np.ndarray, cA, CA, M=None):
 
 
 def make_opts(maxit=0, fixed_iters=0, stop=HOM_STOP_DEFAULT, cA=0.0, CA=0.0, inner_tol=0.0,
-              check_every=0):
+              check_every=0, out_flags=0):
     o = hom_opts()
     o.maxit, o.fixed_iters, o.stop = maxit, fixed_iters, stop
     o.cA, o.CA, o.inner_tol, o.check_every = cA, CA, inner_tol, check_every
+    o.out_flags = out_flags
     return o
 
 
@@ -459,6 +523,8 @@ class Problem:
 
     def __init__(self, d, N, material, integration=HOM_APPROX, precision=HOM_FP64):
         self.d = d
+        # components of a field: d, or d (d + 1) / 2 for strains (elasticity)
+        self.nc = d * (d + 1) // 2 if material.kind == HOM_A_STIFFNESS else d
         self.N = tuple(N)
         self.material = material
         self.h = hom_create(d, N, material, integration, precision)
@@ -467,7 +533,7 @@ class Problem:
 
     def field(self, dtype=None):
         import torch
-        return torch.zeros((self.d,) + self.grid, dtype=dtype or torch.float64, device="cuda")
+        return torch.zeros((self.nc,) + self.grid, dtype=dtype or torch.float64, device="cuda")
 
     def close(self):
         if self.h:

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhom.so")
 SOURCES = ["ops_f64.cu", "ops_f32.cu", "ops_pair_f32.cu", "hom_api.cu", "hom_serve.cu",
-           "hom_static.cu"]
+           "hom_static.cu", "hom_diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          f"-I{os.path.join(ROOT, 'include')}"]

@@ -67,8 +67,12 @@ struct LineDiv {
 
 // Scalars of one solve, resident on the device so that a captured iteration replays without
 // host round trips. Written by the reduction finishers, read by every kernel of a step.
+// components of a field: d for the vector fields of conductivity, d (d + 1) / 2 for the
+// symmetric strain fields of elasticity (Mandel storage)
+constexpr int kMaxComp = 6;
+
 struct Scalars {
-  double E[3];        // macroscopic field
+  double E[kMaxComp]; // macroscopic field (one entry per component)
   double omega;       // Richardson / Eyre-Milton parameter
   double alpha, beta; // CG / Chebyshev coefficients of the current step
   double rr;          // (r, r) of the current residual
@@ -80,7 +84,7 @@ struct Scalars {
   double last_res;    // last residual norm seen
   double last_inc;    // last increment norm seen
   double energy;      // (A(E+x), E+x) of the last energy evaluation
-  double flux[3];     // <A(E+x)>
+  double flux[kMaxComp];  // <A(E+x)>
   int it;             // completed iterations
   int done;           // 1 once stopped (converged or iteration limit)
   int converged;
@@ -111,8 +115,10 @@ struct MatView {
   int nphase;            // entries of the phase table (0: not known to the kernel)
   const uint8_t* ph8;
   const uint16_t* ph16;
-  const T* table;        // nphase * d * d (tensor) or nphase (isotropic)
+  const T* table;        // nphase * nc * nc (tensor) or nphase (isotropic)
   const T* field;        // one scalar per node
+  const T* inv;          // tensor phases with more than 3 components: nphase * nc * nc entries
+                         // of (A_p + omega I)^{-1} for the Eyre-Milton post-operator, or null
 };
 
 // Accumulator of a dot product in FP64 accuracy. FP64 kernels accumulate in double; FP32

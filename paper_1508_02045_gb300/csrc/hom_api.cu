@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -72,8 +73,9 @@ cudaError_t& last_cuda_error() {
 }
 
 bool spd_eigs(const double* t, int d, double* lo, double* hi) {
-  // symmetric check + eigenvalue bounds via Jacobi sweeps on a copy
-  double a[3][3];
+  // symmetric check + eigenvalue bounds via Jacobi sweeps on a copy (d <= kMaxComp)
+  if (d < 1 || d > kMaxComp) return false;
+  double a[kMaxComp][kMaxComp];
   for (int i = 0; i < d; ++i)
     for (int j = 0; j < d; ++j) a[i][j] = t[i * d + j];
   for (int i = 0; i < d; ++i)
@@ -113,7 +115,58 @@ bool spd_eigs(const double* t, int d, double* lo, double* hi) {
   return mn > 0;
 }
 
+// (C_p + omega I)^{-1} of every phase of a stiffness table (n x n Mandel matrices, SPD, so
+// Gauss-Jordan without pivoting is stable), uploaded for the Eyre-Milton post-operator
+int shifted_inverse_table(hom_problem* P, double omega) {
+  const int n = P->nc;
+  const size_t cnt = (size_t)P->nphase * n * n;
+  if (P->d_inv && P->inv_omega == omega) return HOM_OK;
+  std::vector<double> tab(cnt), inv(cnt);
+  HOM_CUDA(cudaMemcpy(tab.data(), P->d_table, sizeof(double) * cnt, cudaMemcpyDeviceToHost));
+  for (int p = 0; p < P->nphase; ++p) {
+    double m[kMaxComp][2 * kMaxComp];
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        m[i][j] = tab[(size_t)p * n * n + i * n + j] + (i == j ? omega : 0.0);
+        m[i][n + j] = i == j ? 1.0 : 0.0;
+      }
+    for (int c = 0; c < n; ++c) {
+      const double piv = m[c][c];
+      for (int j = 0; j < 2 * n; ++j) m[c][j] /= piv;
+      for (int r = 0; r < n; ++r)
+        if (r != c) {
+          const double f = m[r][c];
+          for (int j = 0; j < 2 * n; ++j) m[r][j] -= f * m[c][j];
+        }
+    }
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) inv[(size_t)p * n * n + i * n + j] = m[i][n + j];
+  }
+  if (!P->d_inv) {
+    int rc = alloc((void**)&P->d_inv, sizeof(double) * cnt);
+    if (rc) return rc;
+  }
+  HOM_CUDA(cudaMemcpy(P->d_inv, inv.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice));
+  P->inv_omega = omega;
+  P->e64.mat.inv = P->d_inv;
+  return HOM_OK;
+}
+
+// allocation-failure injection (hom_debug_fail_alloc): allocations still to pass before one
+// fails, or -1 when disarmed
+std::atomic<long long>& fail_countdown() {
+  static std::atomic<long long> c{-1};
+  return c;
+}
+
 int alloc(void** p, size_t bytes) {
+  long long c = fail_countdown().load();
+  while (c >= 0 && !fail_countdown().compare_exchange_weak(c, c - 1)) {
+  }
+  if (c == 0) {  // the injected failure: the allocation cudaMalloc would refuse on a full device
+    *p = nullptr;
+    return HOM_ERR_OOM;
+  }
   if (cudaMalloc(p, bytes) != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -133,7 +186,7 @@ int check_last() {
 
 // ---- autotuned launch plans, per (precision, grid, support) in this process ----
 namespace {
-using TuneKey = std::tuple<int, int, int, int, int, int, int, int>;
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int>;
 std::map<TuneKey, PlanChoice>& tune_table() {
   static std::map<TuneKey, PlanChoice> t;
   return t;
@@ -142,15 +195,15 @@ std::mutex& tune_mu() {
   static std::mutex m;
   return m;
 }
-TuneKey tune_key(int pb, int d, const int* M, const int* N) {
+TuneKey tune_key(int pb, int d, const int* M, const int* N, int nc) {
   return TuneKey(pb, d, M[0], d > 1 ? M[1] : 1, d > 2 ? M[2] : 1, N[0], d > 1 ? N[1] : 1,
-                 d > 2 ? N[2] : 1);
+                 d > 2 ? N[2] : 1, nc > 0 ? nc : d);
 }
 }  // namespace
 
-PlanChoice plan_choice(int pb, int d, const int* M, const int* N) {
+PlanChoice plan_choice(int pb, int d, const int* M, const int* N, int nc) {
   std::lock_guard<std::mutex> lk(tune_mu());
-  auto it = tune_table().find(tune_key(pb, d, M, N));
+  auto it = tune_table().find(tune_key(pb, d, M, N, nc));
   if (it != tune_table().end()) return it->second;
   // defaults: two CTAs per SM in every pass; FP64 values take twice the registers
   return PlanChoice{pb == 8 ? 15 : 27, 110 * 1024, kThreads, true};
@@ -238,8 +291,39 @@ int voxel_coefficients(hom_problem* P, const std::vector<double>& a,
 using namespace hom::detail;
 
 namespace {
-std::once_flag g_const_once;
-cudaError_t g_const_err = cudaSuccess;
+// Device address of a host pointer into page-locked memory (its mapping in the unified address
+// space), or null for memory the device cannot address (pageable, or not host memory).
+const void* mapped_host(const void* h) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr) return at.devicePointer;
+  return nullptr;
+}
+
+// Per-device set-up of the kernels: the register-DFT constants live in __constant__ memory and
+// the shared-memory limits are function attributes, both state of the device that was current
+// when they were set. Done once per device, with that device current.
+constexpr int kMaxDevices = 64;
+std::once_flag g_const_once[kMaxDevices];
+cudaError_t g_const_err[kMaxDevices] = {};
+
+cudaError_t device_setup() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::call_once(g_const_once[dev], [dev] {
+    cudaError_t r = Ops<double>::upload_constants();
+    if (r == cudaSuccess) r = Ops<float>::upload_constants();
+    if (r == cudaSuccess) r = Ops<double>::prepare(3);
+    if (r == cudaSuccess) r = Ops<float>::prepare(3);
+    g_const_err[dev] = r;
+  });
+  return g_const_err[dev];
+}
 }  // namespace
 
 
@@ -264,6 +348,11 @@ const char* hom_strerror(int s) {
 }
 
 long long hom_kernel_launches(void) { return launch_counter(); }
+
+int hom_debug_fail_alloc(int n) {
+  fail_countdown().store(n >= 0 ? (long long)n : -1LL);
+  return HOM_OK;
+}
 
 int hom_profile_enable(int on) {
   ProfState& ps = prof_state();
@@ -301,8 +390,12 @@ void hom_destroy(hom_problem* P) {
   if (P->stream) cudaStreamSynchronize(P->stream);
   P->e64.release();
   P->e32.release();
+  P->eN.release();
+  if (P->SN) cudaFree(P->SN);
+  if (P->yN) cudaFree(P->yN);
   if (P->d_phase) cudaFree(P->d_phase);
   if (P->d_table) cudaFree(P->d_table);
+  if (P->d_inv) cudaFree(P->d_inv);
   if (P->S) cudaFree(P->S);
   if (P->vbase) cudaFree(P->vbase);
   for (auto& v : P->fvec)
@@ -345,6 +438,11 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
   for (int a = 0; a < d; ++a)
     if (N[a] < 3 || N[a] % 2 == 0 || N[a] > kMaxAxis) return HOM_ERR_INVALID;
   if (integration == HOM_APPROX && A->kind == HOM_A_FOURIER) return HOM_ERR_INVALID;
+  // linear elasticity: symmetric strain fields of nc = d (d + 1) / 2 components (Mandel),
+  // sampled stiffness (GaNi) in FP64
+  const bool elastic = A->kind == HOM_A_STIFFNESS;
+  const int nc = elastic ? d * (d + 1) / 2 : d;
+  if (elastic && (integration != HOM_APPROX || precision != HOM_FP64)) return HOM_ERR_UNSUPPORTED;
   // exact integration of an image (voxel-wise constant coefficients): scalar coefficients only
   const bool voxel_ga = integration == HOM_EXACT && A->kind != HOM_A_FOURIER;
   if (voxel_ga) {
@@ -361,19 +459,17 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
     }
   }
 
-  std::call_once(g_const_once, [] {
-    g_const_err = Ops<double>::upload_constants();
-    if (g_const_err == cudaSuccess) g_const_err = Ops<float>::upload_constants();
-    if (g_const_err == cudaSuccess) g_const_err = Ops<double>::prepare(3);
-    if (g_const_err == cudaSuccess) g_const_err = Ops<float>::prepare(3);
-  });
-  if (g_const_err != cudaSuccess) {
-    last_cuda_error() = g_const_err;
-    return HOM_ERR_CUDA;
+  {
+    const cudaError_t ce = device_setup();
+    if (ce != cudaSuccess) {
+      last_cuda_error() = ce;
+      return HOM_ERR_CUDA;
+    }
   }
 
   hom_problem* P = new hom_problem();
   P->d = d;
+  P->nc = nc;
   P->integration = integration;
   P->precision = precision;
   P->stream = (cudaStream_t)stream;
@@ -437,26 +533,27 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
     P->cA = lo;
     P->CA = hi;
     P->mat_kind = MAT_FIELD;
-  } else if (A->kind == HOM_A_PHASE) {
+  } else if (A->kind == HOM_A_PHASE || elastic) {
     if (!A->data || !A->table || A->nphase < 1 || (A->index_bytes != 1 && A->index_bytes != 2) ||
         (A->index_bytes == 1 && A->nphase > 256)) {
       delete P;
       return HOM_ERR_INVALID;
     }
-    bool iso = true;
+    // tables of d x d conductivities or nc x nc Mandel stiffnesses (never taken as isotropic)
+    bool iso = !elastic;
     double lo = 1e300, hi = -1e300;
     for (int p = 0; p < A->nphase; ++p) {
-      const double* t = A->table + (size_t)p * d * d;
+      const double* t = A->table + (size_t)p * nc * nc;
       double l, h;
-      if (!spd_eigs(t, d, &l, &h)) {
+      if (!spd_eigs(t, nc, &l, &h)) {
         delete P;
         return HOM_ERR_INVALID;
       }
       lo = std::min(lo, l);
       hi = std::max(hi, h);
-      for (int i = 0; i < d; ++i)
-        for (int j = 0; j < d; ++j)
-          if ((i != j && t[i * d + j] != 0.0) || (i == j && t[i * d + j] != t[0])) iso = false;
+      for (int i = 0; i < nc; ++i)
+        for (int j = 0; j < nc; ++j)
+          if ((i != j && t[i * nc + j] != 0.0) || (i == j && t[i * nc + j] != t[0])) iso = false;
     }
     P->cA = lo;
     P->CA = hi;
@@ -467,7 +564,7 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
     if (iso) {
       for (int p = 0; p < A->nphase; ++p) tab.push_back(A->table[(size_t)p * d * d]);
     } else {
-      tab.assign(A->table, A->table + (size_t)A->nphase * d * d);
+      tab.assign(A->table, A->table + (size_t)A->nphase * nc * nc);
     }
     if ((st = alloc((void**)&P->d_table, sizeof(double) * tab.size())) != HOM_OK) { hom_destroy(P); return st; }
     // 16 zero bytes past the end: kernels may read the phase indices in aligned words
@@ -519,8 +616,8 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
 
   // ---- plans ----
   {
-    const PlanChoice pc = plan_choice(8, d, P->M, P->N);
-    if ((st = P->e64.init(d, P->M, P->N, pc.budget, pc.rmax, pc.threads, pc.two_line)) != HOM_OK) { hom_destroy(P); return st; }
+    const PlanChoice pc = plan_choice(8, d, P->M, P->N, nc);
+    if ((st = P->e64.init(d, P->M, P->N, pc.budget, pc.rmax, pc.threads, pc.two_line, nc)) != HOM_OK) { hom_destroy(P); return st; }
   }
   if (precision == HOM_FP32_REFINED) {
     const PlanChoice pc = plan_choice(4, d, P->M, P->N);
@@ -528,16 +625,17 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
   }
 
   // ---- buffers ----
-  P->S_bytes = sizeof(cpx<double>) * (size_t)d * P->e64.g.scs;
+  P->S_bytes = sizeof(cpx<double>) * (size_t)P->nc * P->e64.g.scs;
   if ((st = alloc(&P->S, P->S_bytes)) != HOM_OK) { hom_destroy(P); return st; }
-  if ((st = alloc((void**)&P->vbase, sizeof(double) * 5 * d * nodes)) != HOM_OK) { hom_destroy(P); return st; }
-  for (int i = 0; i < 5; ++i) P->vec[i] = P->vbase + (size_t)i * d * nodes;
+  if ((st = alloc((void**)&P->vbase, sizeof(double) * 5 * P->nc * nodes)) != HOM_OK) { hom_destroy(P); return st; }
+  for (int i = 0; i < 5; ++i) P->vec[i] = P->vbase + (size_t)i * P->nc * nodes;
   if (precision == HOM_FP32_REFINED)
     for (int i = 0; i < 4; ++i)
-      if ((st = alloc((void**)&P->fvec[i], sizeof(float) * d * nodes)) != HOM_OK) { hom_destroy(P); return st; }
-  P->red_grid = (int)std::min<long long>((nodes * d + kThreads - 1) / kThreads, 152 * 8);
+      if ((st = alloc((void**)&P->fvec[i], sizeof(float) * P->nc * nodes)) != HOM_OK) { hom_destroy(P); return st; }
+  P->red_grid = (int)std::min<long long>((nodes * P->nc + kThreads - 1) / kThreads, 152 * 8);
   long long maxblocks = std::max<long long>(P->red_grid, (P->e64.g.nlines + 1) / 2 + 1);
-  P->npartials = (size_t)maxblocks * 4;
+  // k_energy reduces nc + 1 values per CTA (energy and the nc flux components)
+  P->npartials = (size_t)maxblocks * (size_t)std::max(4, P->nc + 1);
   if ((st = alloc((void**)&P->partials, sizeof(double) * P->npartials)) != HOM_OK) { hom_destroy(P); return st; }
   if ((st = alloc((void**)&P->counter, sizeof(unsigned) * 4)) != HOM_OK) { hom_destroy(P); return st; }
   cudaMemset(P->counter, 0, sizeof(unsigned) * 4);
@@ -608,19 +706,49 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
 int hom_apply(hom_problem* P, int op, const double* E, const double* x_dev, double* y_dev) {
   if (!P || !x_dev || !y_dev) return HOM_ERR_INVALID;
   const bool fp32 = (op & HOM_OP_FP32) != 0;
-  op &= ~HOM_OP_FP32;
+  const bool x_host = (op & HOM_OP_X_HOST) != 0, y_host = (op & HOM_OP_Y_HOST) != 0;
+  op &= ~(HOM_OP_FP32 | HOM_OP_X_HOST | HOM_OP_Y_HOST);
+  if (x_host || y_host) {
+    if (op < HOM_OP_AFFINE || op > HOM_OP_EM) return HOM_ERR_INVALID;
+    // page-locked host memory through its device mapping; anything else staged through the
+    // free solver vector vec[4] (the operator may run in place)
+    const size_t bytes = sizeof(double) * (size_t)P->nc * (size_t)P->nodes;
+    double* stage = P->vec[4];
+    const double* xd = x_dev;
+    double* yd = y_dev;
+    if (x_host) {
+      xd = static_cast<const double*>(mapped_host(x_dev));
+      if (!xd) {
+        HOM_CUDA(cudaMemcpyAsync(stage, x_dev, bytes, cudaMemcpyHostToDevice, P->stream));
+        xd = stage;
+      }
+    }
+    bool y_staged = false;
+    if (y_host) {
+      yd = static_cast<double*>(const_cast<void*>(mapped_host(y_dev)));
+      if (!yd) {
+        yd = stage;
+        y_staged = true;
+      }
+    }
+    int rc = hom_apply(P, op | (fp32 ? HOM_OP_FP32 : 0), E, xd, yd);
+    if (rc) return rc;
+    if (y_staged) HOM_CUDA(cudaMemcpyAsync(y_dev, stage, bytes, cudaMemcpyDeviceToHost, P->stream));
+    if (y_host) HOM_CUDA(cudaStreamSynchronize(P->stream));
+    return check_last();
+  }
   if (op < HOM_OP_AFFINE || op > HOM_OP_EM) return HOM_ERR_INVALID;
   if (op == HOM_OP_AFFINE && !E) return HOM_ERR_INVALID;
   if (op == HOM_OP_EM && P->integration == HOM_EXACT) return HOM_ERR_UNSUPPORTED;
   if (fp32 && P->precision != HOM_FP32_REFINED) return HOM_ERR_UNSUPPORTED;
   OpArgs args{};
-  for (int a = 0; a < P->d; ++a) args.E[a] = E ? E[a] : 0.0;
+  for (int a = 0; a < P->nc; ++a) args.E[a] = E ? E[a] : 0.0;
   args.omega = std::sqrt(P->cA * P->CA);
   const int pre = op == HOM_OP_AFFINE ? PRE_AFFINE : op == HOM_OP_LINEAR ? PRE_LINEAR
                 : op == HOM_OP_PROJECT ? PRE_IDENT : PRE_EM;
   const int mode = op == HOM_OP_EM ? PROJ_EM : PROJ_GAMMA;
   if (fp32) {
-    const long long len = (long long)P->d * P->nodes;
+    const long long len = (long long)P->nc * P->nodes;
     Ops<float>::convert_in(x_dev, P->fvec[0], len, P->stream);
     Fields<float> f{};
     f.xin = P->fvec[0];
@@ -664,23 +792,23 @@ int upload_scalars(hom_problem* P, Scalars* dst, const Scalars& s) {
 // (A(E + x), E + x) and <A(E + x)> into P->d_aux
 int energy_eval(hom_problem* P, const double* E, const double* x, double* en, double* flux) {
   Scalars s{};
-  for (int a = 0; a < P->d; ++a) s.E[a] = E[a];
+  for (int a = 0; a < P->nc; ++a) s.E[a] = E[a];
   int st = upload_scalars(P, P->d_aux, s);
   if (st) return st;
-  Ops<double>::energy(P->d, x, P->nodes, P->e64.mat, P->d_aux, P->partials, P->counter,
+  Ops<double>::energy(P->nc, x, P->nodes, P->e64.mat, P->d_aux, P->partials, P->counter,
                       P->red_grid, P->stream);
   if ((st = check_last())) return st;
   if ((st = poll(P, P->d_aux))) return st;
   if (en) *en = P->h_sc->energy;
   if (flux)
-    for (int a = 0; a < P->d; ++a) flux[a] = P->h_sc->flux[a];
+    for (int a = 0; a < P->nc; ++a) flux[a] = P->h_sc->flux[a];
   return HOM_OK;
 }
 
 // ||G A (E + x)|| (the residual b - C x up to sign) into P->d_aux; y is scratch
 double true_residual(hom_problem* P, const double* E, const double* x, double* y) {
   Scalars s{};
-  for (int a = 0; a < P->d; ++a) s.E[a] = E[a];
+  for (int a = 0; a < P->nc; ++a) s.E[a] = E[a];
   if (upload_scalars(P, P->d_aux, s)) return -1;
   Fields<double> f{};
   f.xin = x;
@@ -691,6 +819,79 @@ double true_residual(hom_problem* P, const double* E, const double* x, double* y
                P->partials, P->counter, 0, P->stream);
   if (poll(P, P->d_aux)) return -1;
   return P->h_sc->nb;
+}
+
+// the N-grid engine, spectrum and field of an exact-integration problem (first use)
+int ensure_ngrid(hom_problem* P) {
+  if (P->eN.ready && P->SN && P->yN) return HOM_OK;
+  const PlanChoice pc = plan_choice(8, P->d, P->N, P->N);
+  int st = HOM_OK;
+  if (!P->eN.ready) {
+    st = P->eN.init(P->d, P->N, P->N, pc.budget, pc.rmax, pc.threads, pc.two_line);
+    if (st != HOM_OK) {
+      P->eN.release();
+      P->eN.ready = false;
+      return st;
+    }
+  }
+  long long nN = 1;
+  for (int a = 0; a < P->d; ++a) nN *= P->N[a];
+  if (!P->SN && (st = alloc(&P->SN, sizeof(cpx<double>) * (size_t)P->d * P->eN.g.scs)) != HOM_OK)
+    return st;
+  if (!P->yN && (st = alloc((void**)&P->yN, sizeof(double) * (size_t)P->d * nN)) != HOM_OK)
+    return st;
+  return HOM_OK;
+}
+
+// y (N grid) = samples of the trigonometric polynomial of order N with values x on the solve
+// grid M: F_M (unscaled), the coefficients of Z_N times 1/|M|, F_N^{-1} (eq. (DFT))
+int restrict_field(hom_problem* P, const double* x, double* y) {
+  const int d = P->d;
+  cudaStream_t st = P->stream;
+  if (P->integration != HOM_EXACT) {
+    if (x != y)
+      HOM_CUDA(cudaMemcpyAsync(y, x, sizeof(double) * P->nc * P->nodes, cudaMemcpyDeviceToDevice, st));
+    return check_last();
+  }
+  int rc = ensure_ngrid(P);
+  if (rc) return rc;
+  P->e64.forward(x, (cpx<double>*)P->S, d, st);
+  const PassGeom& gm = P->e64.g;
+  const PassGeom& gn = P->eN.g;
+  const int n1 = d == 3 ? gn.n[1] : 1, m1 = d == 3 ? gm.n[1] : 1;
+  Ops<double>::crop_spectrum((const cpx<double>*)P->S, (cpx<double>*)P->SN, d, gn.n[0], n1, gn.nh,
+                             gm.n[0], m1, gm.nh, 1.0 / (double)gm.nodes, gn.scs, gm.scs, st);
+  P->eN.inverse((cpx<double>*)P->SN, y, d, st);
+  return check_last();
+}
+
+// The corrector output of a session from the device field src on the solve grid: on the
+// device or the host (HOM_OUT_HOST), on the solve grid or as N-grid samples (HOM_OUT_NGRID,
+// exact integration). Synchronises the stream.
+int write_corrector(hom_problem* P, const double* src, double* out) {
+  const int f = P->sv.out_flags;
+  const bool ngrid = (f & HOM_OUT_NGRID) && P->integration == HOM_EXACT;
+  const bool host = (f & HOM_OUT_HOST) != 0;
+  long long n = P->nodes;
+  if (ngrid) {
+    n = 1;
+    for (int a = 0; a < P->d; ++a) n *= P->N[a];
+  }
+  const size_t bytes = sizeof(double) * (size_t)P->nc * (size_t)n;
+  const double* res = src;
+  if (ngrid) {
+    int rc = ensure_ngrid(P);
+    if (rc) return rc;
+    double* dst = host ? P->yN : out;
+    if ((rc = restrict_field(P, src, dst))) return rc;
+    res = dst;
+  }
+  if (host)
+    HOM_CUDA(cudaMemcpyAsync(out, res, bytes, cudaMemcpyDeviceToHost, P->stream));
+  else if (res != out)
+    HOM_CUDA(cudaMemcpyAsync(out, res, bytes, cudaMemcpyDeviceToDevice, P->stream));
+  HOM_CUDA(cudaStreamSynchronize(P->stream));
+  return check_last();
 }
 
 }  // namespace detail
@@ -771,7 +972,7 @@ namespace detail {
 int refine_residual(hom_problem* P, double* res) {
   SolveState& S_ = P->sv;
   Scalars s{};
-  for (int a = 0; a < P->d; ++a) s.E[a] = S_.E[a];
+  for (int a = 0; a < P->nc; ++a) s.E[a] = S_.E[a];
   int rc = upload_scalars(P, P->d_aux, s);
   if (rc) return rc;
   Fields<double> f{};
@@ -801,7 +1002,7 @@ int refine_start_inner(hom_problem* P) {
   }
   int rc = upload_scalars(P, P->d_sc2, s);
   if (rc) return rc;
-  const long long len = (long long)P->d * P->nodes;
+  const long long len = (long long)P->nc * P->nodes;
   Ops<float>::demote(P->vec[2], P->fvec[1], P->fvec[2], P->fvec[0], len, P->nodes, P->d_sc2,
                      P->partials, P->counter, P->red_grid, P->stream);
   if (S_.solver == HOM_CHEBYSHEV) {
@@ -851,7 +1052,7 @@ void refine_enqueue_inner(hom_problem* P) {
 // after an inner solve stopped: x += d (FP64), new FP64 residual, stopping test
 int refine_outer_update(hom_problem* P) {
   SolveState& S_ = P->sv;
-  const long long len = (long long)P->d * P->nodes;
+  const long long len = (long long)P->nc * P->nodes;
   int rc = poll(P, P->d_sc2);
   if (rc) return rc;
   S_.inner_total += P->h_sc->it;
@@ -884,7 +1085,7 @@ int refine_outer_update(hom_problem* P) {
 
 int refine_begin(hom_problem* P) {
   SolveState& S_ = P->sv;
-  const long long len = (long long)P->d * P->nodes;
+  const long long len = (long long)P->nc * P->nodes;
   HOM_CUDA(cudaEventRecord(P->ev0, P->stream));
   HOM_CUDA(cudaMemsetAsync(P->vec[0], 0, sizeof(double) * len, P->stream));
   int rc = refine_residual(P, &S_.nb);
@@ -902,9 +1103,8 @@ int refine_begin(hom_problem* P) {
 }  // namespace detail
 }  // namespace hom
 
-extern "C" int hom_solve_begin(hom_problem* P, const double* E, int solver, double tol,
-                               const hom_opts* opts) {
-  if (!P || !E) return HOM_ERR_INVALID;
+static int solve_begin_impl(hom_problem* P, const double* E, int solver, double tol,
+                            const hom_opts* opts) {
   if (solver < HOM_RICHARDSON || solver > HOM_EYRE_MILTON) return HOM_ERR_INVALID;
   hom_opts o{};
   if (opts) o = *opts;
@@ -913,7 +1113,7 @@ extern "C" int hom_solve_begin(hom_problem* P, const double* E, int solver, doub
   const int stop = solve_stop_mode(solver, o.stop);
   if ((solver == HOM_CG || solver == HOM_CHEBYSHEV) && stop == HOM_STOP_INCREMENT) return HOM_ERR_UNSUPPORTED;
   if (solver == HOM_EYRE_MILTON && stop == HOM_STOP_RESIDUAL) return HOM_ERR_UNSUPPORTED;
-  const int d = P->d;
+  const int d = P->nc;  // components of the fields and of E
   const long long nodes = P->nodes;
   const long long len = (long long)d * nodes;
   const double cA = o.cA > 0 ? o.cA : P->cA;
@@ -926,6 +1126,7 @@ extern "C" int hom_solve_begin(hom_problem* P, const double* E, int solver, doub
   S_.fixed = o.fixed_iters > 0;
   S_.maxit = o.fixed_iters > 0 ? o.fixed_iters : (o.maxit > 0 ? o.maxit : 100000);
   S_.check = o.check_every > 0 ? o.check_every : 8;
+  S_.out_flags = o.out_flags;
   for (int a = 0; a < d; ++a) S_.E[a] = E[a];
   double nE = 0;
   for (int a = 0; a < d; ++a) nE += E[a] * E[a];
@@ -956,7 +1157,13 @@ extern "C" int hom_solve_begin(hom_problem* P, const double* E, int solver, doub
   double* q = P->vec[4];
   OpArgs args{};
   if (solver == HOM_RICHARDSON) s.omega = 2.0 / (cA + CA);
-  if (solver == HOM_EYRE_MILTON) s.omega = std::sqrt(cA * CA);
+  if (solver == HOM_EYRE_MILTON) {
+    s.omega = std::sqrt(cA * CA);
+    if (P->nc > 3) {  // six-component stiffness: the post-operator reads (C_p + omega I)^{-1}
+      int rc0 = shifted_inverse_table(P, s.omega);
+      if (rc0) return rc0;
+    }
+  }
   if (solver == HOM_CHEBYSHEV) {
     s.cheb_c = 0.5 * (CA - cA);
     s.cheb_d = 0.5 * (cA + CA);
@@ -1005,6 +1212,15 @@ extern "C" int hom_solve_begin(hom_problem* P, const double* E, int solver, doub
   return check_last();
 }
 
+// a session that failed to begin (argument, allocation or CUDA error) is not active
+extern "C" int hom_solve_begin(hom_problem* P, const double* E, int solver, double tol,
+                               const hom_opts* opts) {
+  if (!P || !E) return HOM_ERR_INVALID;
+  const int rc = solve_begin_impl(P, E, solver, tol, opts);
+  if (rc != HOM_OK) P->sv.active = false;
+  return rc;
+}
+
 extern "C" int hom_solve_iterate(hom_problem* P, int iterations, int* done) {
   if (!P || !P->sv.active || iterations < 0) return HOM_ERR_INVALID;
   SolveState& S_ = P->sv;
@@ -1038,7 +1254,7 @@ extern "C" int hom_solve_end(hom_problem* P, double* x_dev, double* AH_EE, doubl
   if (!P || !P->sv.active) return HOM_ERR_INVALID;
   SolveState& S_ = P->sv;
   S_.active = false;
-  const int d = P->d;
+  const int d = P->nc;
   const long long nodes = P->nodes;
   const long long len = (long long)d * nodes;
   cudaStream_t st = P->stream;
@@ -1063,10 +1279,7 @@ extern "C" int hom_solve_end(hom_problem* P, double* x_dev, double* AH_EE, doubl
       stats->true_residual = stats->residual;  // the outer residual is formed in FP64
       stats->time_ms = ms;
     }
-    if (x_dev) {
-      HOM_CUDA(cudaMemcpyAsync(x_dev, P->vec[0], sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
-      HOM_CUDA(cudaStreamSynchronize(st));
-    }
+    if (x_dev && (rc = write_corrector(P, P->vec[0], x_dev))) return rc;
     if ((rc = check_last())) return rc;
     return S_.converged ? HOM_OK : HOM_ERR_NOT_CONVERGED;
   }
@@ -1115,10 +1328,7 @@ extern "C" int hom_solve_end(hom_problem* P, double* x_dev, double* AH_EE, doubl
     else
       stats->true_residual = (fin.nb > 0 && tr >= 0) ? tr / fin.nb : tr;
   }
-  if (x_dev) {
-    HOM_CUDA(cudaMemcpyAsync(x_dev, result, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
-    HOM_CUDA(cudaStreamSynchronize(st));
-  }
+  if (x_dev && (rc = write_corrector(P, result, x_dev))) return rc;
   if ((rc = check_last())) return rc;
   return (fin.converged || S_.fixed) ? HOM_OK : HOM_ERR_NOT_CONVERGED;
 }
@@ -1149,7 +1359,7 @@ extern "C" int hom_solve_current(hom_problem* P, double* x_dev) {
   if (!P || !x_dev || !P->sv.active) return HOM_ERR_INVALID;
   SolveState& S_ = P->sv;
   const long long nodes = P->nodes;
-  const long long len = (long long)P->d * nodes;
+  const long long len = (long long)P->nc * nodes;
   cudaStream_t st = P->stream;
   const double* cur = P->vec[0];
   if (!S_.refined) {
@@ -1157,37 +1367,35 @@ extern "C" int hom_solve_current(hom_problem* P, double* x_dev) {
     if (rc) return rc;
     if (S_.solver == HOM_RICHARDSON) cur = P->vec[0] + (P->h_sc->result ? len : 0);
     if (S_.solver == HOM_EYRE_MILTON) {
-      // e = G x_m (Section 4.4), as the end of the solve returns it
+      // e = G x_m (Section 4.4), as the end of the solve returns it, into the free vector
       Fields<double> fp{};
       fp.xin = P->vec[0];
-      fp.out = x_dev;
+      fp.out = P->vec[4];
       fp.cs = nodes;
       OpArgs args{};
       P->e64.apply(PRE_IDENT, PROJ_GAMMA, POST_STORE, fp, (cpx<double>*)P->S, nullptr, args,
                    nullptr, nullptr, 0, st);
-      HOM_CUDA(cudaStreamSynchronize(st));
-      return check_last();
+      cur = P->vec[4];
     }
   }
-  HOM_CUDA(cudaMemcpyAsync(x_dev, cur, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
-  HOM_CUDA(cudaStreamSynchronize(st));
-  return check_last();
+  (void)len;
+  return write_corrector(P, cur, x_dev);
 }
 
 extern "C" int hom_solve_nonconformity(hom_problem* P, double* value) {
   if (!P || !value || !P->sv.active) return HOM_ERR_INVALID;
   SolveState& S_ = P->sv;
   const long long nodes = P->nodes;
-  const long long len = (long long)P->d * nodes;
+  const long long len = (long long)P->nc * nodes;
   cudaStream_t st = P->stream;
   const double* cur = P->vec[0];
-  double e[3] = {0.0, 0.0, 0.0};
+  Scalars s{};  // E for the Eyre-Milton iterate, zero for the conforming solvers
   int rc;
   if (!S_.refined) {
     if ((rc = poll(P, P->d_sc))) return rc;
     if (S_.solver == HOM_RICHARDSON) cur = P->vec[0] + (P->h_sc->result ? len : 0);
     if (S_.solver == HOM_EYRE_MILTON)
-      for (int a = 0; a < P->d; ++a) e[a] = S_.E[a];
+      for (int a = 0; a < P->nc; ++a) s.E[a] = S_.E[a];
   }
   // G x into the solver's free vector (no solver keeps state there between steps)
   double* g = P->vec[4];
@@ -1198,10 +1406,9 @@ extern "C" int hom_solve_nonconformity(hom_problem* P, double* value) {
   OpArgs args{};
   P->e64.apply(PRE_IDENT, PROJ_GAMMA, POST_STORE, f, (cpx<double>*)P->S, nullptr, args, nullptr,
                nullptr, 0, st);
-  Scalars s{};
   if ((rc = upload_scalars(P, P->d_aux, s))) return rc;
-  k_nonconf<double><<<P->red_grid, kThreads, 0, st>>>(g, cur, P->d, nodes, e[0], e[1], e[2],
-                                                       P->partials, P->counter, P->d_aux);
+  k_nonconf<double><<<P->red_grid, kThreads, 0, st>>>(g, cur, P->nc, nodes, P->partials,
+                                                       P->counter, P->d_aux);
   if ((rc = check_last()) || (rc = poll(P, P->d_aux))) return rc;
   *value = P->h_sc->last_res;
   return HOM_OK;
@@ -1248,6 +1455,11 @@ extern "C" int hom_prolongate(hom_problem* Cp, hom_problem* Fp, const double* x_
   return check_last();
 }
 
+extern "C" int hom_restrict(hom_problem* P, const double* x_dev, double* y_dev) {
+  if (!P || !x_dev || !y_dev) return HOM_ERR_INVALID;
+  return restrict_field(P, x_dev, y_dev);
+}
+
 extern "C" int hom_bound(hom_problem* gani, hom_problem* ga, const double* E,
                          const double* x_dev, double* UE) {
   if (!gani || !ga || !E || !x_dev || !UE) return HOM_ERR_INVALID;
@@ -1288,7 +1500,7 @@ int tune_engine(hom_problem* P, Engine<T>& E, T* x, T* y, int reps, const std::v
         for (bool two : {true, false}) {
       if (budget > cap) continue;
       E.release_plan();
-      if (E.init(d, P->M, P->N, budget, rmax, threads, two) != HOM_OK) continue;
+      if (E.init(d, P->M, P->N, budget, rmax, threads, two, P->nc) != HOM_OK) continue;
       if (!two && !Ops<T>::two_line_ok(E.g, E.plan[0], E.plan[1])) continue;  // same plan
       E.apply(PRE_LINEAR, PROJ_GAMMA, POST_STORE, f, (cpx<T>*)P->S, nullptr, args, nullptr,
               nullptr, 0, P->stream);  // warm-up
@@ -1313,7 +1525,7 @@ int tune_engine(hom_problem* P, Engine<T>& E, T* x, T* y, int reps, const std::v
   cudaEventDestroy(e1);
   E.release_plan();
   const int rc = E.init(d, P->M, P->N, choice.budget, choice.rmax, choice.threads,
-                        choice.two_line);
+                        choice.two_line, P->nc);
   *best = choice;
   *best_ms = best_t / reps;
   return rc ? rc : check_last();
@@ -1336,7 +1548,7 @@ extern "C" int hom_autotune(hom_problem* P, int reps, hom_tune_report* report) {
   rep.ms64 = ms;
   {
     std::lock_guard<std::mutex> lk(tune_mu());
-    tune_table()[tune_key(8, P->d, P->M, P->N)] = c;
+    tune_table()[tune_key(8, P->d, P->M, P->N, P->nc)] = c;
   }
   if (P->precision == HOM_FP32_REFINED) {
     rc = tune_engine<float>(P, P->e32, P->fvec[0], P->fvec[1], reps, {9, 15, 27}, budgets, &c, &ms);
@@ -1347,7 +1559,7 @@ extern "C" int hom_autotune(hom_problem* P, int reps, hom_tune_report* report) {
     rep.two_line32 = c.two_line ? 1 : 0;
     rep.ms32 = ms;
     std::lock_guard<std::mutex> lk(tune_mu());
-    tune_table()[tune_key(4, P->d, P->M, P->N)] = c;
+    tune_table()[tune_key(4, P->d, P->M, P->N, P->nc)] = c;
   }
   if (report) *report = rep;
   return HOM_OK;

@@ -320,7 +320,71 @@ struct Bucket {
   bool dirty = true;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  cudaStream_t stream = nullptr;  // the bucket's own stream: buckets overlap on the device
 };
+
+void bucket_release(Bucket& b) {
+  if (b.stream) cudaStreamSynchronize(b.stream);
+  if (b.graph) cudaGraphExecDestroy(b.graph);
+  if (b.e64) {
+    b.e64->release();
+    delete b.e64;
+  }
+  if (b.e32) {
+    b.e32->release();
+    delete b.e32;
+  }
+  if (b.d64) cudaFree(b.d64);
+  if (b.d32) cudaFree(b.d32);
+  if (b.d_sc) cudaFree(b.d_sc);
+  if (b.d_done) cudaFree(b.d_done);
+  if (b.h_done) cudaFreeHost(b.h_done);
+  if (b.stream) cudaStreamDestroy(b.stream);
+  b = Bucket{};
+}
+
+// a bucket for requests of grid M (order N), with its plans (the planner's choice for that
+// grid, as hom_create makes it), descriptor arrays and stream
+int bucket_init(Bucket& b, const hom_request& r, const int* M, int cap) {
+  b.d = r.d;
+  for (int a = 0; a < 3; ++a) {
+    b.M[a] = a < r.d ? M[a] : 1;
+    b.N[a] = a < r.d ? r.N[a] : 1;
+  }
+  b.integration = r.integration;
+  b.precision = r.precision;
+  b.solver = r.solver;
+  b.cap = cap;
+  b.slots.assign(b.cap, nullptr);
+  b.nodes = 1;
+  for (int a = 0; a < r.d; ++a) b.nodes *= M[a];
+  b.red_grid = (int)std::min<long long>((b.nodes * b.d + kThreads - 1) / kThreads, 152 * 8);
+  int rc;
+  if ((rc = alloc((void**)&b.d64, sizeof(ReqDesc<double>) * b.cap)) ||
+      (rc = alloc((void**)&b.d32, sizeof(ReqDesc<float>) * b.cap)) ||
+      (rc = alloc((void**)&b.d_sc, sizeof(Scalars*) * b.cap)) ||
+      (rc = alloc((void**)&b.d_done, sizeof(int) * b.cap)))
+    return rc;
+  if (cudaMallocHost((void**)&b.h_done, sizeof(int) * b.cap) != cudaSuccess) {
+    b.h_done = nullptr;
+    return HOM_ERR_OOM;
+  }
+  if (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess) {
+    b.stream = nullptr;
+    return HOM_ERR_CUDA;
+  }
+  const PlanChoice p64 = plan_choice(8, b.d, b.M, b.N);
+  b.e64 = new Engine<double>();
+  if ((rc = b.e64->init(b.d, b.M, b.N, p64.budget, p64.rmax, p64.threads, p64.two_line)))
+    return rc;
+  if (b.precision == HOM_FP32_REFINED) {
+    const PlanChoice p32 = plan_choice(4, b.d, b.M, b.N);
+    b.e32 = new Engine<float>();
+    if ((rc = b.e32->init(b.d, b.M, b.N, p32.budget, p32.rmax, p32.threads, p32.two_line)))
+      return rc;
+  }
+  return HOM_OK;
+}
 
 size_t estimate_bytes(const hom_request& r) {
   long long nodes = 1;
@@ -346,14 +410,12 @@ size_t estimate_bytes(const hom_request& r) {
 struct hom_server {
   size_t budget = 0, in_use = 0;
   int max_batch = 16;
-  cudaStream_t stream = nullptr;
   long long next_id = 1;
   std::deque<ServerReq*> queue;
   std::vector<Bucket> buckets;
   std::vector<hom_result> done;
   Scalars* d_idle = nullptr;
   int steps_per_graph = 4;
-  bool own_stream = false;
 };
 
 namespace {
@@ -378,7 +440,7 @@ int bucket_upload(hom_server* S, Bucket& b) {
         h[i] = desc32(b.slots[i]->P);
         scs[i] = b.slots[i]->P->d_sc2;
       }
-    HOM_CUDA(cudaMemcpyAsync(b.d32, h.data(), sizeof(ReqDesc<float>) * b.cap, cudaMemcpyHostToDevice, S->stream));
+    HOM_CUDA(cudaMemcpyAsync(b.d32, h.data(), sizeof(ReqDesc<float>) * b.cap, cudaMemcpyHostToDevice, b.stream));
   } else {
     std::vector<ReqDesc<double>> h(b.cap, idle_desc<double>(S->d_idle));
     for (int i = 0; i < b.cap; ++i)
@@ -386,19 +448,19 @@ int bucket_upload(hom_server* S, Bucket& b) {
         h[i] = desc64(b.slots[i]->P);
         scs[i] = b.slots[i]->P->d_sc;
       }
-    HOM_CUDA(cudaMemcpyAsync(b.d64, h.data(), sizeof(ReqDesc<double>) * b.cap, cudaMemcpyHostToDevice, S->stream));
+    HOM_CUDA(cudaMemcpyAsync(b.d64, h.data(), sizeof(ReqDesc<double>) * b.cap, cudaMemcpyHostToDevice, b.stream));
   }
-  HOM_CUDA(cudaMemcpyAsync(b.d_sc, scs.data(), sizeof(Scalars*) * b.cap, cudaMemcpyHostToDevice, S->stream));
-  HOM_CUDA(cudaStreamSynchronize(S->stream));  // host vectors go out of scope
+  HOM_CUDA(cudaMemcpyAsync(b.d_sc, scs.data(), sizeof(Scalars*) * b.cap, cudaMemcpyHostToDevice, b.stream));
+  HOM_CUDA(cudaStreamSynchronize(b.stream));  // host vectors go out of scope
   b.dirty = false;
   return HOM_OK;
 }
 
-void bucket_step(hom_server* S, Bucket& b) {
+void bucket_step(Bucket& b) {
   if (b.precision == HOM_FP32_REFINED)
-    batch_step<float>(*b.e32, b.solver, b.d32, b.cap, b.red_grid, b.nodes, b.d, S->stream);
+    batch_step<float>(*b.e32, b.solver, b.d32, b.cap, b.red_grid, b.nodes, b.d, b.stream);
   else
-    batch_step<double>(*b.e64, b.solver, b.d64, b.cap, b.red_grid, b.nodes, b.d, S->stream);
+    batch_step<double>(*b.e64, b.solver, b.d64, b.cap, b.red_grid, b.nodes, b.d, b.stream);
 }
 
 int bucket_launch(hom_server* S, Bucket& b, int iterations) {
@@ -406,9 +468,9 @@ int bucket_launch(hom_server* S, Bucket& b, int iterations) {
     cudaGraph_t g = nullptr;
     const bool prof = profiling();
     if (prof) hom_profile_enable(0);
-    HOM_CUDA(cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < S->steps_per_graph; ++k) bucket_step(S, b);
-    const cudaError_t e = cudaStreamEndCapture(S->stream, &g);
+    HOM_CUDA(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < S->steps_per_graph; ++k) bucket_step(b);
+    const cudaError_t e = cudaStreamEndCapture(b.stream, &g);
     if (prof) hom_profile_enable(1);
     HOM_CUDA(e);
     const cudaError_t e2 = cudaGraphInstantiate(&b.graph, g, 0);
@@ -418,16 +480,27 @@ int bucket_launch(hom_server* S, Bucket& b, int iterations) {
   }
   int k = 0;
   for (; k + b.graph_steps <= iterations; k += b.graph_steps) {
-    HOM_CUDA(cudaGraphLaunch(b.graph, S->stream));
+    HOM_CUDA(cudaGraphLaunch(b.graph, b.stream));
     launch_counter() += (long long)b.graph_steps * ((b.d == 3 ? 5 : 3) + (b.solver == HOM_CG ? 1 : 0));
   }
-  for (; k < iterations; ++k) bucket_step(S, b);
+  for (; k < iterations; ++k) bucket_step(b);
   for (auto* r : b.slots)
     if (r) r->P->sv.issued += iterations;
   return check_last();
 }
 
-// move queued requests onto the device while the budget and the slots allow
+// a request that could not start: its result carries the status
+void fail_request(hom_server* S, ServerReq* r, int status) {
+  hom_result res{};
+  res.id = r->id;
+  res.status = status;
+  res.latency_ms = ms_between(r->t_submit, Clock::now());
+  S->done.push_back(res);
+  delete r;
+}
+
+// move queued requests onto the device while the budget and the slots allow; each request's
+// problem lives on its bucket's stream
 int admit(hom_server* S) {
   while (!S->queue.empty()) {
     ServerReq* r = S->queue.front();
@@ -442,63 +515,37 @@ int admit(hom_server* S) {
       Bucket& b = S->buckets[bi];
       if (std::find(b.slots.begin(), b.slots.end(), nullptr) == b.slots.end()) break;
     }
+    S->queue.pop_front();
+    int rc = HOM_OK;
+    if (bi < 0) {
+      Bucket nb;
+      rc = bucket_init(nb, r->req, M, S->max_batch);
+      if (rc != HOM_OK) {
+        bucket_release(nb);
+        fail_request(S, r, rc);
+        continue;
+      }
+      S->buckets.push_back(nb);
+      bi = (int)S->buckets.size() - 1;
+    }
+    Bucket& b = S->buckets[bi];
     // create the problem and start its session
     hom_material mat = r->req.material;
     mat.data = r->data.data();
     mat.table = r->table.empty() ? nullptr : r->table.data();
     mat.data_on_device = 0;
     hom_problem* P = nullptr;
-    int rc = hom_create(r->req.d, r->req.N, &mat, r->req.integration, r->req.precision,
-                        S->stream, &P);
+    rc = hom_create(r->req.d, r->req.N, &mat, r->req.integration, r->req.precision, b.stream, &P);
     if (rc == HOM_OK)
       rc = hom_solve_begin(P, r->req.E, r->req.solver, r->req.tol, &r->req.opts);
-    S->queue.pop_front();
     if (rc != HOM_OK) {
       if (P) hom_destroy(P);
-      hom_result res{};
-      res.id = r->id;
-      res.status = rc;
-      res.latency_ms = ms_between(r->t_submit, Clock::now());
-      S->done.push_back(res);
-      delete r;
+      fail_request(S, r, rc);
       continue;
     }
     r->P = P;
     r->t_admit = Clock::now();
     S->in_use += r->bytes;
-    if (bi < 0) {
-      Bucket b;
-      b.d = r->req.d;
-      for (int a = 0; a < 3; ++a) {
-        b.M[a] = a < r->req.d ? M[a] : 1;
-        b.N[a] = a < r->req.d ? r->req.N[a] : 1;
-      }
-      b.integration = r->req.integration;
-      b.precision = r->req.precision;
-      b.solver = r->req.solver;
-      b.cap = S->max_batch;
-      b.slots.assign(b.cap, nullptr);
-      if ((rc = alloc((void**)&b.d64, sizeof(ReqDesc<double>) * b.cap)) ||
-          (rc = alloc((void**)&b.d32, sizeof(ReqDesc<float>) * b.cap)) ||
-          (rc = alloc((void**)&b.d_sc, sizeof(Scalars*) * b.cap)) ||
-          (rc = alloc((void**)&b.d_done, sizeof(int) * b.cap)))
-        return rc;
-      if (cudaMallocHost((void**)&b.h_done, sizeof(int) * b.cap) != cudaSuccess) return HOM_ERR_OOM;
-      // the bucket keeps its own plans and geometry (same planner as hom_create)
-      b.nodes = P->nodes;
-      b.red_grid = P->red_grid;
-      b.e64 = new Engine<double>();
-      if ((rc = b.e64->init(b.d, P->M, P->N, P->e64.budget_used, P->e64.rmax_used,
-                                 P->e64.threads_used, P->e64.two_line))) return rc;
-      if (b.precision == HOM_FP32_REFINED) {
-        b.e32 = new Engine<float>();
-        if ((rc = b.e32->init(b.d, P->M, P->N, P->e32.budget_used, P->e32.rmax_used,
-                                   P->e32.threads_used, P->e32.two_line))) return rc;
-      }
-      S->buckets.push_back(b);
-      bi = (int)S->buckets.size() - 1;
-    }
-    Bucket& b = S->buckets[bi];
     const int slot = (int)(std::find(b.slots.begin(), b.slots.end(), nullptr) - b.slots.begin());
     b.slots[slot] = r;
     r->bucket = bi;
@@ -530,17 +577,10 @@ void retire(hom_server* S, Bucket& b, int slot) {
 extern "C" int hom_server_create(size_t hbm_budget_bytes, int max_batch, void* stream,
                                  hom_server** out) {
   if (!out || max_batch < 1 || hbm_budget_bytes == 0) return HOM_ERR_INVALID;
+  (void)stream;  // every bucket runs on a stream of its own (see hom.h)
   auto* S = new hom_server();
   S->budget = hbm_budget_bytes;
   S->max_batch = max_batch;
-  S->stream = (cudaStream_t)stream;
-  if (S->stream == nullptr) {  // graphs cannot be captured on the legacy default stream
-    if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) {
-      delete S;
-      return HOM_ERR_CUDA;
-    }
-    S->own_stream = true;
-  }
   if (alloc((void**)&S->d_idle, sizeof(Scalars))) {
     delete S;
     return HOM_ERR_OOM;
@@ -555,6 +595,7 @@ extern "C" int hom_server_create(size_t hbm_budget_bytes, int max_batch, void* s
 extern "C" int hom_server_submit(hom_server* S, const hom_request* req, long long* id) {
   if (!S || !req || !id) return HOM_ERR_INVALID;
   if (req->d != 2 && req->d != 3) return HOM_ERR_INVALID;
+  if (req->material.kind == HOM_A_STIFFNESS) return HOM_ERR_UNSUPPORTED;  // E, flux: d entries
   long long nodes = 1;
   for (int a = 0; a < req->d; ++a) {
     if (req->N[a] < 3 || req->N[a] % 2 == 0) return HOM_ERR_INVALID;
@@ -599,10 +640,12 @@ extern "C" int hom_server_step(hom_server* S, int iterations) {
     if (!live[bi]) continue;
     if (b.dirty && (rc = bucket_upload(S, b))) return rc;
     if ((rc = bucket_launch(S, b, iterations))) return rc;
-    k_gather_done<<<(b.cap + 127) / 128, 128, 0, S->stream>>>(b.d_sc, b.cap, b.d_done);
-    HOM_CUDA(cudaMemcpyAsync(b.h_done, b.d_done, sizeof(int) * b.cap, cudaMemcpyDeviceToHost, S->stream));
+    k_gather_done<<<(b.cap + 127) / 128, 128, 0, b.stream>>>(b.d_sc, b.cap, b.d_done);
+    HOM_CUDA(cudaMemcpyAsync(b.h_done, b.d_done, sizeof(int) * b.cap, cudaMemcpyDeviceToHost, b.stream));
   }
-  HOM_CUDA(cudaStreamSynchronize(S->stream));
+  // every live bucket's step is in flight on its own stream before the host waits for any
+  for (size_t bi = 0; bi < S->buckets.size(); ++bi)
+    if (live[bi]) HOM_CUDA(cudaStreamSynchronize(S->buckets[bi].stream));
   for (size_t bi = 0; bi < S->buckets.size(); ++bi) {
     if (!live[bi]) continue;
     Bucket& b = S->buckets[bi];
@@ -648,30 +691,16 @@ extern "C" int hom_server_status(hom_server* S, int* active, int* queued, size_t
 
 extern "C" void hom_server_destroy(hom_server* S) {
   if (!S) return;
-  if (S->stream) cudaStreamSynchronize(S->stream);
   for (auto& b : S->buckets) {
+    if (b.stream) cudaStreamSynchronize(b.stream);
     for (auto* r : b.slots)
       if (r) {
         hom_destroy(r->P);
         delete r;
       }
-    if (b.graph) cudaGraphExecDestroy(b.graph);
-    if (b.e64) {
-      b.e64->release();
-      delete b.e64;
-    }
-    if (b.e32) {
-      b.e32->release();
-      delete b.e32;
-    }
-    cudaFree(b.d64);
-    cudaFree(b.d32);
-    cudaFree(b.d_sc);
-    cudaFree(b.d_done);
-    cudaFreeHost(b.h_done);
+    bucket_release(b);
   }
   for (auto* r : S->queue) delete r;
   cudaFree(S->d_idle);
-  if (S->own_stream) cudaStreamDestroy(S->stream);
   delete S;
 }

@@ -18,6 +18,7 @@
 #include "../../include/hom.h"
 #include "ops.h"
 #include "passes.cuh"
+#include "problem.h"
 
 using namespace hom;
 
@@ -62,70 +63,29 @@ int static_setup(int dev, unsigned char** base) {
   return HOM_OK;
 }
 
-// radix plan of one axis: prime factors (<= 31) grouped first-fit into register radices <= 15
-bool plan_static_axis(int n, AxisPlan* P) {
-  if (n < 3 || n > kMaxAxis || n % 2 == 0) return false;
-  int groups[kMaxStages];
-  int ng = 0, rem = n;
-  for (int R : {31, 29, 23, 19, 17, 13, 11, 7, 5, 3})
-    while (rem % R == 0) {
-      rem /= R;
-      int best = -1;
-      for (int gi = 0; gi < ng; ++gi)
-        if (groups[gi] * R <= 15 && (best < 0 || groups[gi] > groups[best])) best = gi;
-      if (best >= 0) {
-        groups[best] *= R;
-      } else {
-        if (ng >= kMaxStages) return false;
-        groups[ng++] = R;
-      }
-    }
-  if (rem != 1) return false;
-  std::sort(groups, groups + ng, [](int a, int b) { return a > b; });
-  P->n = n;
-  P->nst = ng;
-  int p = 1;
-  for (int s = 0; s < kMaxStages; ++s) {
-    P->pprev[s] = s < ng ? p : 0;
-    P->radix[s] = s < ng ? groups[s] : 0;
-    if (s < ng) p *= groups[s];
-  }
-  plan_fastdivs(P);
-  return true;
+// Values written into the scratch by a kernel whose parameters carry them: a launch copies
+// its parameters when it is enqueued, so the call needs no host staging buffer that must
+// outlive it and no pageable host-to-device copy (which would wait for the stream's earlier
+// work before returning).
+constexpr int kFillChunk = 496;  // doubles per launch (kernel parameters stay under 4 KiB)
+struct FillChunk {
+  int count;
+  double v[kFillChunk];
+};
+
+__global__ void k_static_fill(double* __restrict__ dst, FillChunk c) {
+  for (int i = threadIdx.x; i < c.count; i += blockDim.x) dst[i] = c.v[i];
 }
 
-// extreme eigenvalues of a symmetric d x d tensor (d <= 3) by Jacobi rotations; false unless SPD
-bool static_spd(const double* t, int d, double* lo, double* hi) {
-  double a[3][3];
-  for (int i = 0; i < d; ++i)
-    for (int j = 0; j < d; ++j) a[i][j] = t[i * d + j];
-  for (int i = 0; i < d; ++i)
-    for (int j = 0; j < i; ++j)
-      if (std::fabs(a[i][j] - a[j][i]) > 1e-12 * (std::fabs(a[i][j]) + std::fabs(a[j][i]) + 1e-300))
-        return false;
-  for (int sweep = 0; sweep < 50; ++sweep)
-    for (int p = 0; p < d; ++p)
-      for (int q = p + 1; q < d; ++q) {
-        if (std::fabs(a[p][q]) < 1e-300) continue;
-        const double th = 0.5 * std::atan2(2 * a[p][q], a[q][q] - a[p][p]);
-        const double c = std::cos(th), s = std::sin(th);
-        for (int k = 0; k < d; ++k) {
-          const double akp = a[k][p], akq = a[k][q];
-          a[k][p] = c * akp - s * akq;
-          a[k][q] = s * akp + c * akq;
-        }
-        for (int k = 0; k < d; ++k) {
-          const double apk = a[p][k], aqk = a[q][k];
-          a[p][k] = c * apk - s * aqk;
-          a[q][k] = s * apk + c * aqk;
-        }
-      }
-  *lo = *hi = a[0][0];
-  for (int i = 1; i < d; ++i) {
-    *lo = std::min(*lo, a[i][i]);
-    *hi = std::max(*hi, a[i][i]);
+bool fill_device(double* dst, const double* src, size_t n, cudaStream_t st) {
+  for (size_t o = 0; o < n; o += kFillChunk) {
+    FillChunk c;
+    c.count = (int)std::min<size_t>(kFillChunk, n - o);
+    std::memcpy(c.v, src + o, sizeof(double) * (size_t)c.count);
+    k_static_fill<<<1, 128, 0, st>>>(dst + o, c);
+    ++launch_counter();
   }
-  return *lo > 0;
+  return cudaGetLastError() == cudaSuccess;
 }
 
 }  // namespace
@@ -142,7 +102,8 @@ extern "C" int hom_apply_static(int d, const int* N, const void* phase_dev, int 
   g.D = d;
   g.nodes = 1;
   for (int a = 0; a < d; ++a) {
-    if (!plan_static_axis(N[a], &plan[a])) return HOM_ERR_INVALID;
+    if (!hom::detail::plan_axis(N[a], hom::detail::reg_rmax<double>(), &plan[a]))
+      return HOM_ERR_INVALID;
     g.n[a] = N[a];
     g.nodes *= N[a];
   }
@@ -172,7 +133,7 @@ extern "C" int hom_apply_static(int d, const int* N, const void* phase_dev, int 
   std::vector<double> tab;
   for (int p = 0; p < nphase; ++p) {
     double lo, hi;
-    if (!static_spd(table + (size_t)p * d * d, d, &lo, &hi)) return HOM_ERR_INVALID;
+    if (!hom::detail::spd_eigs(table + (size_t)p * d * d, d, &lo, &hi)) return HOM_ERR_INVALID;
     cA = std::min(cA, lo);
     CA = std::max(CA, hi);
     if (iso_table) tab.push_back(table[(size_t)p * d * d]);
@@ -189,28 +150,19 @@ extern "C" int hom_apply_static(int d, const int* N, const void* phase_dev, int 
   if (!Ops<double>::plan_geometry(d, N, plan, 110 * 1024, kThreads, &g))
     return HOM_ERR_UNSUPPORTED;
 
-  // ---- twiddles and table into the scratch (ordered on the caller's stream) ----
+  // ---- twiddles (the long-double tables of hom_create) and table into the scratch, by
+  // kernels on the caller's stream ----
   cudaStream_t st = (cudaStream_t)stream;
   cpx<double>* tw[3] = {nullptr, nullptr, nullptr};
-  std::vector<cpx<double>> tw_h((size_t)3 * kMaxAxis);
-  const long double twopi = 6.283185307179586476925286766559005768L;
   for (int a = 0; a < d; ++a) {
     tw[a] = reinterpret_cast<cpx<double>*>(base) + (size_t)a * kMaxAxis;
-    for (int j = 0; j < N[a]; ++j) {
-      const long double t = -twopi * (long double)j / (long double)N[a];
-      tw_h[(size_t)a * kMaxAxis + j].x = (double)cosl(t);
-      tw_h[(size_t)a * kMaxAxis + j].y = (double)sinl(t);
-    }
+    const std::vector<cpx<double>> tw_h = hom::detail::twiddles<double>(N[a]);
+    if (!fill_device(reinterpret_cast<double*>(tw[a]), &tw_h[0].x, 2 * tw_h.size(), st))
+      return HOM_ERR_CUDA;
   }
   double* tab_dev = reinterpret_cast<double*>(base + kTwBytes);
   cpx<double>* S = reinterpret_cast<cpx<double>*>(base + kSpecOff);
-  if (cudaMemcpyAsync(base, tw_h.data(), sizeof(cpx<double>) * 3 * kMaxAxis,
-                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(tab_dev, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice,
-                      st) != cudaSuccess) {
-    cudaGetLastError();
-    return HOM_ERR_CUDA;
-  }
+  if (!fill_device(tab_dev, tab.data(), tab.size(), st)) return HOM_ERR_CUDA;
 
   // ---- one application: the same passes as hom_apply ----
   MatView<double> mat{};

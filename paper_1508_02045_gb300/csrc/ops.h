@@ -15,6 +15,7 @@ template <typename T> struct ReqDesc;
 // launch geometry of the kernels of one grid, chosen by the planner in hom_api.cu
 struct PassGeom {
   int D;              // spatial dimension
+  int NC;             // components of a field: D (vectors) or D (D + 1) / 2 (symmetric strains)
   int n[3];           // solve-grid order
   long long nodes;    // |grid|
   long long nlines;   // lines of the contiguous axis per component (|grid| / n[D-1])
@@ -36,11 +37,11 @@ struct Ops {
   static size_t smem_strided(int n, int TCp, int nst);
   static size_t smem_proj(int n, int D, int TCp, int nst);
   static size_t smem_proj_scalar(int n, int TCp);
-  // launch geometry of every pass of a grid with axis plans `plan`, keeping each CTA's shared
-  // memory within `budget` bytes and its threads within `threads` (<= kThreads); false if a
-  // pass cannot fit the device limit
+  // launch geometry of every pass of a grid with axis plans `plan` for fields of nc components,
+  // keeping each CTA's shared memory within `budget` bytes and its threads within `threads`
+  // (<= kThreads); false if a pass cannot fit the device limit
   static bool plan_geometry(int D, const int* n, const AxisPlan* plan, size_t budget,
-                            int threads, PassGeom* g);
+                            int threads, PassGeom* g, int nc = 0);
   static cudaError_t prepare(int maxD);  // raise dynamic shared memory limits
 
   // reqs / nreq: optional per-request descriptors of a batched launch (grid.z = nreq); the
@@ -74,7 +75,8 @@ struct Ops {
                        Scalars* sc, const OpArgs& args, double* partials, unsigned* counter,
                        int negate, cudaStream_t st, const ReqDesc<T>* reqs = nullptr,
                        int nreq = 1);
-  static void energy(int D, const T* x, long long nodes, const MatView<T>& mat, Scalars* sc,
+  // ncomp: components of x (the coefficient acts on ncomp-vectors)
+  static void energy(int ncomp, const T* x, long long nodes, const MatView<T>& mat, Scalars* sc,
                      double* partials, unsigned* counter, int grid, cudaStream_t st);
   static void fill_const(T* x, long long nodes, int d, const Scalars* sc, cudaStream_t st);
   static void demote(const double* r64, T* r, T* p, T* x, long long len, long long nodes,
@@ -82,6 +84,9 @@ struct Ops {
   static void promote(double* x64, const T* dx, long long len, cudaStream_t st);
   static void convert_in(const double* src, T* dst, long long len, cudaStream_t st);
   static void convert_out(const T* src, double* dst, long long len, cudaStream_t st);
+  static void crop_spectrum(const cpx<T>* Sm, cpx<T>* Sn, int D, int n0, int n1, int nh, int m0,
+                            int m1, int mh, double scale, long long nlen, long long mlen,
+                            cudaStream_t st);
   static void pad_spectrum(const cpx<T>* Sn, cpx<T>* Sm, int D, int n0, int n1, int nh, int m0,
                            int m1, int mh, double scale, long long nlen, long long mlen,
                            cudaStream_t st);

@@ -74,10 +74,13 @@ static void pick_cols(const AxisPlan& P, int lines, int tcmax, size_t budget, in
 
 template <typename T>
 bool Ops<T>::plan_geometry(int D, const int* n, const AxisPlan* plan, size_t budget,
-                           int threads, PassGeom* g) {
+                           int threads, PassGeom* g, int nc) {
   if (threads < 32 || threads > kColThreads<T> || threads % 32) return false;
+  const int NC = nc > 0 ? nc : D;
+  if (NC != D && NC != D * (D + 1) / 2) return false;
   g->NTl = threads;
   g->D = D;
+  g->NC = NC;
   g->nodes = 1;
   for (int a = 0; a < D; ++a) {
     g->n[a] = n[a];
@@ -89,31 +92,19 @@ bool Ops<T>::plan_geometry(int D, const int* n, const AxisPlan* plan, size_t bud
   g->nlines = g->nodes / nl;
   g->scs = g->nlines * g->nh;
   g->LB = 16;
-  while (g->LB > 2 && smem_line(nl, D, g->LB) > budget) g->LB -= 2;
+  while (g->LB > 2 && smem_line(nl, NC, g->LB) > budget) g->LB -= 2;
   if (D == 3)
-    pick_cols<T>(plan[1], 1, 64, budget, COL_STRIDED, D, threads, &g->TC1, &g->TC1p, &g->NT1);
-  pick_cols<T>(plan[0], D, 32, budget, COL_PROJ, D, threads, &g->TC0, &g->TC0p, &g->NT0);
+    pick_cols<T>(plan[1], 1, 64, budget, COL_STRIDED, NC, threads, &g->TC1, &g->TC1p, &g->NT1);
+  pick_cols<T>(plan[0], NC, 32, budget, COL_PROJ, NC, threads, &g->TC0, &g->TC0p, &g->NT0);
   pick_cols<T>(plan[0], 2, 32, budget, COL_PROJ_SCALAR, D, threads, &g->TCq, &g->TCqp, &g->NTq);
-  pick_cols<T>(plan[0], 1, 64, budget, COL_STRIDED, D, threads, &g->TCs0, &g->TCs0p, &g->NTs0);
-  // the column kernels address the D component tiles with 32-bit offsets
-  if ((long long)D * g->scs >= (1LL << 31)) return false;
+  pick_cols<T>(plan[0], 1, 64, budget, COL_STRIDED, NC, threads, &g->TCs0, &g->TCs0p, &g->NTs0);
+  // the column kernels address the NC component tiles with 32-bit offsets
+  if ((long long)NC * g->scs >= (1LL << 31)) return false;
   const size_t cap = (size_t)dynamic_smem_cap();
-  return smem_line(nl, D, g->LB) <= cap && smem_proj(n[0], D, g->TC0p, plan[0].nst) <= cap &&
+  return smem_line(nl, NC, g->LB) <= cap && smem_proj(n[0], NC, g->TC0p, plan[0].nst) <= cap &&
          smem_proj_scalar(n[0], g->TCqp) <= cap &&
          (D != 3 || smem_strided(n[1], g->TC1p, plan[1].nst) <= cap) &&
          smem_strided(n[0], g->TCs0p, plan[0].nst) <= cap;
-}
-
-// number of SMs of the current device (cached per process)
-inline int num_sms() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
 }
 
 // Opt-in shared memory per CTA minus room for the kernels' static shared variables.
@@ -145,10 +136,10 @@ cudaError_t Ops<T>::prepare(int) {
   HOM_SET_SMEM((k_line_fwd<T, 3, PRE_EM>));
   HOM_SET_SMEM((k_line_fwd<T, 3, PRE_IDENT>));
   HOM_SET_SMEM((k_strided<T>));
-  HOM_SET_SMEM((k_proj<T, 2, PROJ_GAMMA>));
-  HOM_SET_SMEM((k_proj<T, 2, PROJ_EM>));
-  HOM_SET_SMEM((k_proj<T, 3, PROJ_GAMMA>));
-  HOM_SET_SMEM((k_proj<T, 3, PROJ_EM>));
+  HOM_SET_SMEM((k_proj<T, 2, 2, PROJ_GAMMA>));
+  HOM_SET_SMEM((k_proj<T, 2, 2, PROJ_EM>));
+  HOM_SET_SMEM((k_proj<T, 3, 3, PROJ_GAMMA>));
+  HOM_SET_SMEM((k_proj<T, 3, 3, PROJ_EM>));
   HOM_SET_SMEM((k_proj_scalar<T>));
   HOM_SET_SMEM((k_line_inv<T, 2, POST_STORE>));
   HOM_SET_SMEM((k_line_inv<T, 2, POST_RICH>));
@@ -166,8 +157,30 @@ cudaError_t Ops<T>::prepare(int) {
   HOM_SET_SMEM((k_line_fwd<T, 3, PRE_CG_DOT>));
   HOM_SET_SMEM((k_line_inv<T, 2, POST_CG_FUSED>));
   HOM_SET_SMEM((k_line_inv<T, 3, POST_CG_FUSED>));
-  if constexpr (std::is_same<T, float>::value) return pair_prepare_f32(cap);
-  return cudaSuccess;
+  if constexpr (std::is_same<T, float>::value) {
+    return pair_prepare_f32(cap);
+  } else {
+    // elasticity (FP64): strain fields of 3 (2-D, the 3-component line kernels above) or 6
+    // components, and their projection passes
+    HOM_SET_SMEM((k_proj<T, 2, 3, PROJ_GAMMA>));
+    HOM_SET_SMEM((k_proj<T, 2, 3, PROJ_EM>));
+    HOM_SET_SMEM((k_proj<T, 3, 6, PROJ_GAMMA>));
+    HOM_SET_SMEM((k_proj<T, 3, 6, PROJ_EM>));
+    HOM_SET_SMEM((k_line_fwd<T, 6, PRE_CG>));
+    HOM_SET_SMEM((k_line_inv<T, 6, POST_CG>));
+    HOM_SET_SMEM((k_line_fwd<T, 6, PRE_AFFINE>));
+    HOM_SET_SMEM((k_line_fwd<T, 6, PRE_LINEAR>));
+    HOM_SET_SMEM((k_line_fwd<T, 6, PRE_EM>));
+    HOM_SET_SMEM((k_line_fwd<T, 6, PRE_IDENT>));
+    HOM_SET_SMEM((k_line_fwd<T, 6, PRE_CG_DOT>));
+    HOM_SET_SMEM((k_line_inv<T, 6, POST_STORE>));
+    HOM_SET_SMEM((k_line_inv<T, 6, POST_RICH>));
+    HOM_SET_SMEM((k_line_inv<T, 6, POST_CHEB>));
+    HOM_SET_SMEM((k_line_inv<T, 6, POST_EM>));
+    HOM_SET_SMEM((k_line_inv<T, 6, POST_ADD>));
+    HOM_SET_SMEM((k_line_inv<T, 6, POST_CG_FUSED>));
+    return cudaSuccess;
+  }
 }
 
 template <typename T, int D>
@@ -214,10 +227,14 @@ void Ops<T>::line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
       return;
     }
   }
-  if (g.D == 2)
+  if (ncomp > 3) {  // six-component strains (elasticity, FP64 only)
+    if constexpr (sizeof(T) == 8)
+      line_fwd_d<T, 6>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq, partials);
+  } else if (g.D == 2 && ncomp <= 2) {
     line_fwd_d<T, 2>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq, partials);
-  else
+  } else {
     line_fwd_d<T, 3>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq, partials);
+  }
   if (pre == PRE_CG_DOT) {
     const int nb = (int)((g.nlines + g.LB - 1) / g.LB);
     k_cg_alpha<T><<<dim3(1, 1, (unsigned)nreq), kThreads, 0, st>>>(partials, nb, g.nodes, sc,
@@ -276,6 +293,22 @@ void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, con
     ++launch_counter();
     return;
   }
+  if (g.NC != g.D) {  // symmetric strain fields (elasticity, FP64 only)
+    if constexpr (sizeof(T) == 8) {
+      const dim3 grid((unsigned)((pg.C + g.TC0 - 1) / g.TC0), 1, (unsigned)nreq);
+      const size_t sm = smem_proj(P.n, g.NC, g.TC0p, P.nst);
+#define HOM_PJE(D_, NC_, M_) k_proj<T, D_, NC_, M_><<<grid, g.NT0, sm, st>>>(S, P, tw, pg, g.TC0, g.TC0p, sc, reqs)
+      if (g.D == 2) {
+        if (mode == PROJ_EM) HOM_PJE(2, 3, PROJ_EM); else HOM_PJE(2, 3, PROJ_GAMMA);
+      } else {
+        if (mode == PROJ_EM) HOM_PJE(3, 6, PROJ_EM); else HOM_PJE(3, 6, PROJ_GAMMA);
+      }
+#undef HOM_PJE
+    }
+    if (prof) prof_mark(KIND_PROJ, st, false);
+    ++launch_counter();
+    return;
+  }
   if (g.D == 3 && mode == PROJ_GAMMA) {
     const dim3 grid((unsigned)((pg.C + g.TCq - 1) / g.TCq), 1, (unsigned)nreq);
     const size_t sm = smem_proj_scalar(P.n, g.TCqp);
@@ -286,7 +319,7 @@ void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, con
   }
   const dim3 grid((unsigned)((pg.C + g.TC0 - 1) / g.TC0), 1, (unsigned)nreq);
   const size_t sm = smem_proj(P.n, g.D, g.TC0p, P.nst);
-#define HOM_PJ(D_, M_) k_proj<T, D_, M_><<<grid, g.NT0, sm, st>>>(S, P, tw, pg, g.TC0, g.TC0p, sc, reqs)
+#define HOM_PJ(D_, M_) k_proj<T, D_, D_, M_><<<grid, g.NT0, sm, st>>>(S, P, tw, pg, g.TC0, g.TC0p, sc, reqs)
   if (g.D == 2) {
     if (mode == PROJ_EM) HOM_PJ(2, PROJ_EM); else HOM_PJ(2, PROJ_GAMMA);
   } else {
@@ -372,19 +405,26 @@ void Ops<T>::line_inv(const PassGeom& g, int post, const cpx<T>* S, const Fields
       return;
     }
   }
-  if (g.D == 2)
+  if (ncomp > 3) {  // six-component strains (elasticity, FP64 only)
+    if constexpr (sizeof(T) == 8)
+      line_inv_d<T, 6>(g, post, S, f, P, tw, ncomp, mat, sc, args, partials, counter, negate, st,
+                       reqs, nreq);
+  } else if (g.D == 2 && ncomp <= 2) {
     line_inv_d<T, 2>(g, post, S, f, P, tw, ncomp, mat, sc, args, partials, counter, negate, st,
                      reqs, nreq);
-  else
+  } else {
     line_inv_d<T, 3>(g, post, S, f, P, tw, ncomp, mat, sc, args, partials, counter, negate, st,
                      reqs, nreq);
+  }
 }
 
 template <typename T>
-void Ops<T>::energy(int D, const T* x, long long nodes, const MatView<T>& mat, Scalars* sc,
+void Ops<T>::energy(int ncomp, const T* x, long long nodes, const MatView<T>& mat, Scalars* sc,
                     double* partials, unsigned* counter, int grid, cudaStream_t st) {
-  if (D == 2) k_energy<T, 2><<<grid, kThreads, 0, st>>>(x, nodes, mat, sc, partials, counter);
-  else k_energy<T, 3><<<grid, kThreads, 0, st>>>(x, nodes, mat, sc, partials, counter);
+  if (ncomp == 2) k_energy<T, 2><<<grid, kThreads, 0, st>>>(x, nodes, mat, sc, partials, counter);
+  else if (ncomp == 3) k_energy<T, 3><<<grid, kThreads, 0, st>>>(x, nodes, mat, sc, partials, counter);
+  else if constexpr (sizeof(T) == 8)
+    k_energy<T, 6><<<grid, kThreads, 0, st>>>(x, nodes, mat, sc, partials, counter);
   ++launch_counter();
 }
 
@@ -437,6 +477,16 @@ void Ops<T>::pad_spectrum(const cpx<T>* Sn, cpx<T>* Sm, int D, int n0, int n1, i
   const long long len = (long long)n0 * n1 * nh * D;
   const unsigned grid = (unsigned)std::min<long long>((len + kThreads - 1) / kThreads, 152 * 16);
   k_pad_spectrum<T><<<grid, kThreads, 0, st>>>(Sn, Sm, D, n0, n1, nh, m0, m1, mh, (T)scale, nlen, mlen);
+  ++launch_counter();
+}
+
+template <typename T>
+void Ops<T>::crop_spectrum(const cpx<T>* Sm, cpx<T>* Sn, int D, int n0, int n1, int nh, int m0,
+                           int m1, int mh, double scale, long long nlen, long long mlen,
+                           cudaStream_t st) {
+  const long long len = (long long)n0 * n1 * nh * D;
+  const unsigned grid = (unsigned)std::min<long long>((len + kThreads - 1) / kThreads, 152 * 16);
+  k_crop_spectrum<T><<<grid, kThreads, 0, st>>>(Sm, Sn, D, n0, n1, nh, m0, m1, mh, (T)scale, nlen, mlen);
   ++launch_counter();
 }
 

@@ -210,6 +210,17 @@ __device__ __forceinline__ void mat_shift_solve_s(const MatView<T>& m, T sample,
     return;
   }
   const int ph = phase_of(sample);
+  if (D > 3) {  // precomputed (A_p + omega I)^{-1} of every phase
+    const T* ti = m.inv + ph * D * D;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      T acc = 0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) acc = fma(__ldg(&ti[i * D + j]), w[j], acc);
+      v[i] = acc;
+    }
+    return;
+  }
   const T* t = m.table + ph * D * D;
   T M[D][D];
 #pragma unroll
@@ -242,7 +253,7 @@ __device__ __forceinline__ void mat_shift_solve_s(const MatView<T>& m, T sample,
 // ---------------------------------------------------------------------------------------
 // Scalars of a single operator application outside a solve (Scalars pointer is then null).
 struct OpArgs {
-  double E[3];
+  double E[kMaxComp];
   double omega;
 };
 
@@ -315,7 +326,7 @@ k_cg_alpha(const double* partials, int nblocks, long long count, Scalars* sc,
 // complex transform. RAW: component a of the tile is instead stored as it lies in the field,
 // node idx of the tile at element raw[a] + idx of shared memory (the specialised FP32 line pass
 // packs the line pairs when its first stage loads them).
-template <typename T, int D, int PRE, int K = (sizeof(T) == 4 ? 8 : 4), int NC = 0,
+template <typename T, int D, int PRE, int K = (sizeof(T) == 4 ? 8 : (D > 3 ? 2 : 4)), int NC = 0,
           bool RAW = false>
 __device__ __forceinline__ void line_pre_to_smem(const Fields<T>& f, int b0, int n, int half,
                                                  int ncomp, long long l0, int LB, long long nlines,
@@ -328,7 +339,9 @@ __device__ __forceinline__ void line_pre_to_smem(const Fields<T>& f, int b0, int
   if (NC > 0) n = NC;
   cpx<T>* sm = smem_c<T>();
   const double* Es = sc != nullptr ? sc->E : args.E;
-  const T E[3] = {(T)Es[0], (T)Es[1], (T)Es[2]};
+  T E[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) E[a] = (T)Es[a];
   const T omega = (T)(sc != nullptr ? sc->omega : args.omega);
   const T beta = sc != nullptr ? (T)sc->beta : (T)0;
   // Richardson keeps x_m and x_{m-1} in a buffer pair; the operand is the current one
@@ -505,11 +518,100 @@ __device__ __forceinline__ T inv_kk(const ProjGeom& g, T scale, int kk) {
   return g.rk != nullptr ? __ldg(static_cast<const T*>(g.rk) + min(kk, g.kkmax)) : scale / (T)kk;
 }
 
-// One CTA per tile of TC columns of all D components (two-level line index: component a,
-// column c), one thread per first-stage butterfly (D x TC x n / R_0, capped at kColThreads).
+// Mandel storage of a symmetric D x D tensor: component m holds (i, j) = (mandel_i, mandel_j),
+// off-diagonal entries scaled by sqrt 2 (D = 2: 11, 22, 12; D = 3: 11, 22, 33, 23, 13, 12)
+template <int D>
+__host__ __device__ constexpr int mandel_i(int m) {
+  return D == 2 ? (m == 2 ? 0 : m) : (m < 3 ? m : (m == 3 ? 1 : 0));
+}
+template <int D>
+__host__ __device__ constexpr int mandel_j(int m) {
+  return D == 2 ? (m == 2 ? 1 : m) : (m < 3 ? m : (m == 5 ? 1 : 2));
+}
+
+// The projection of one frequency k (row j of a column) on the NC transformed components v:
+//  NC == D (vector fields, eq. (proj)): Gamma^ v = k (k . v) / |k|^2;
+//  NC == D (D + 1) / 2 (symmetric strains in Mandel storage, the elasticity form): with
+//  e the tensor of v and q = e k, Gamma^ e = (k q^T + q k^T) / |k|^2 - (k.e.k) k k^T / |k|^4,
+//  the orthogonal projection onto the compatible strains sym(k u^T);
+// c1 = scale / |k|^2 (0 at k = 0 and outside the support); MODE PROJ_EM gives scale v - 2 Gamma^ v.
+template <typename T, int D, int NC, int MODE>
+__device__ __forceinline__ void proj_point(const int (&k)[3], T c1, int kk, T scale,
+                                           const cpx<T> (&v)[NC], cpx<T> (&o)[NC]) {
+  if (NC == D) {
+    cpx<T> kv = {0, 0};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      kv.x = fma((T)k[a], v[a].x, kv.x);
+      kv.y = fma((T)k[a], v[a].y, kv.y);
+    }
+    kv.x *= c1;
+    kv.y *= c1;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      if (MODE == PROJ_GAMMA) {
+        o[a].x = (T)k[a] * kv.x;
+        o[a].y = (T)k[a] * kv.y;
+      } else {  // (I - 2 Gamma^) v
+        o[a].x = fma((T)(-2 * k[a]), kv.x, scale * v[a].x);
+        o[a].y = fma((T)(-2 * k[a]), kv.y, scale * v[a].y);
+      }
+    }
+  } else {
+    const T r2 = (T)0.70710678118654752440;  // 1 / sqrt 2
+    const T s2 = (T)1.41421356237309504880;  // sqrt 2
+    const T c2 = kk > 0 ? c1 / (T)kk : (T)0;
+    // q = e k
+    cpx<T> q[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) q[i] = cpx<T>{0, 0};
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const int i = mandel_i<D>(m), j = mandel_j<D>(m);
+      if (i == j) {
+        q[i].x = fma((T)k[i], v[m].x, q[i].x);
+        q[i].y = fma((T)k[i], v[m].y, q[i].y);
+      } else {
+        const T ex = v[m].x * r2, ey = v[m].y * r2;
+        q[i].x = fma((T)k[j], ex, q[i].x);
+        q[i].y = fma((T)k[j], ey, q[i].y);
+        q[j].x = fma((T)k[i], ex, q[j].x);
+        q[j].y = fma((T)k[i], ey, q[j].y);
+      }
+    }
+    cpx<T> kek = {0, 0};
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      kek.x = fma((T)k[i], q[i].x, kek.x);
+      kek.y = fma((T)k[i], q[i].y, kek.y);
+    }
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const int i = mandel_i<D>(m), j = mandel_j<D>(m);
+      const T kij = (T)(k[i] * k[j]);
+      cpx<T> g;
+      g.x = ((T)k[i] * q[j].x + q[i].x * (T)k[j]) * c1 - kij * kek.x * c2;
+      g.y = ((T)k[i] * q[j].y + q[i].y * (T)k[j]) * c1 - kij * kek.y * c2;
+      if (i != j) {
+        g.x *= s2;
+        g.y *= s2;
+      }
+      if (MODE == PROJ_GAMMA) {
+        o[m] = g;
+      } else {
+        o[m].x = fma((T)-2, g.x, scale * v[m].x);
+        o[m].y = fma((T)-2, g.y, scale * v[m].y);
+      }
+    }
+  }
+}
+
+// One CTA per tile of TC columns of all NC components (two-level line index: component a,
+// column c), one thread per first-stage butterfly (NC x TC x n / R_0, capped at kColThreads).
 // The forward transform loads the tile straight from the spectrum; the projection works in
-// shared memory; the last inverse stage stores straight back.
-template <typename T, int D, int MODE>
+// shared memory; the last inverse stage stores straight back. D is the spatial dimension,
+// NC the field's components (D for vector fields, D (D + 1) / 2 for strains).
+template <typename T, int D, int NC, int MODE>
 __global__ void __launch_bounds__(kColThreads<T>, 2)
 k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC,
        int TCp, const Scalars* sc, const ReqDesc<T>* __restrict__ reqs) {
@@ -520,9 +622,9 @@ k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC
   if (sc != nullptr && sc->done) return;
   const int n = P.n;
   cpx<T>* sm = smem_c<T>();
-  // buffers each hold the D component tiles (n x TCp, component stride cstr)
+  // buffers each hold the NC component tiles (n x TCp, component stride cstr)
   const int cstr = n * TCp;
-  const int bufA = n, bufB = n + D * cstr;
+  const int bufA = n, bufB = n + NC * cstr;
   __shared__ AxisPlan Ps;
   if (threadIdx.x == 0) Ps = P;
   for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = twg[i];
@@ -531,7 +633,7 @@ k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC
   const int ncols = (int)min((long long)TC, g.C - c0);
   const int tcl = __ffs(TC) - 1;
   const Loc<T> gl = gcols<T>(S + c0, (int)g.C, (int)g.cs, tcl, ncols);
-  const int nl = D * TC;
+  const int nl = NC * TC;
   const int nst = Ps.nst;
   // forward DFT of axis 0: first stage from the spectrum, the rest in shared memory
   stage_any<T>(false, &Ps, 0, gl, sloc2<T>(bufA, 1, TCp, cstr, tcl), nl, true, 0);
@@ -573,30 +675,13 @@ k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC
       inside = inside && (abs(k[a]) <= g.hw[a]);
       kk += k[a] * k[a];
     }
-    cpx<T> v[D];
+    cpx<T> v[NC], o[NC];
 #pragma unroll
-    for (int a = 0; a < D; ++a) v[a] = sm[fwd + a * cstr + j * TCp + c];
-    cpx<T> kv = {0, 0};
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      kv.x = fma((T)k[a], v[a].x, kv.x);
-      kv.y = fma((T)k[a], v[a].y, kv.y);
-    }
+    for (int a = 0; a < NC; ++a) v[a] = sm[fwd + a * cstr + j * TCp + c];
     const T coef = (kk > 0 && inside) ? inv_kk<T>(g, scale, kk) : (T)0;
-    kv.x *= coef;
-    kv.y *= coef;
+    proj_point<T, D, NC, MODE>(k, coef, kk, scale, v, o);
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      cpx<T> o;
-      if (MODE == PROJ_GAMMA) {
-        o.x = (T)k[a] * kv.x;
-        o.y = (T)k[a] * kv.y;
-      } else {  // (I - 2 Gamma^) v
-        o.x = fma((T)(-2 * k[a]), kv.x, scale * v[a].x);
-        o.y = fma((T)(-2 * k[a]), kv.y, scale * v[a].y);
-      }
-      sm[fwd + a * cstr + j * TCp + c] = o;
-    }
+    for (int a = 0; a < NC; ++a) sm[fwd + a * cstr + j * TCp + c] = o[a];
   }
   __syncthreads();
   // inverse DFT of axis 0: stages in shared memory, the last one into the spectrum
@@ -712,7 +797,7 @@ k_proj_scalar(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g,
 // l0 + ll is the real (ll even) or imaginary (ll odd) part of shared-memory complex line
 // res + (a * half + ll / 2) * n; the solver's vector update, batches of K nodes whose operands
 // are loaded before any use, and the inner-product partial in dacc.
-template <typename T, int D, int POST, int K = (sizeof(T) == 4 ? 4 : 2), int NC = 0>
+template <typename T, int D, int POST, int K = (sizeof(T) == 4 ? 4 : (D > 3 ? 1 : 2)), int NC = 0>
 __device__ __forceinline__ void line_post_from_smem(const Fields<T>& f, int res, int n, int half,
                                                     int ncomp, long long l0, int LB,
                                                     long long nlines, FastDiv fdn,
@@ -721,7 +806,9 @@ __device__ __forceinline__ void line_post_from_smem(const Fields<T>& f, int res,
                                                     DotAcc<T>& dacc) {
   cpx<T>* sm = smem_c<T>();
   const double* Es = sc != nullptr ? sc->E : args.E;
-  const T E[3] = {(T)Es[0], (T)Es[1], (T)Es[2]};
+  T E[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) E[a] = (T)Es[a];
   const T omega = (T)(sc != nullptr ? sc->omega : args.omega);
   const T alpha = sc != nullptr ? (T)sc->alpha : (T)0;
   const T beta = sc != nullptr ? (T)sc->beta : (T)0;
@@ -995,14 +1082,14 @@ k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ 
 // ---------------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_nonconf(const T* __restrict__ g, const T* __restrict__ x, int d, long long nodes, double e0,
-          double e1, double e2, double* partials, unsigned* counter, Scalars* sc) {
+k_nonconf(const T* __restrict__ g, const T* __restrict__ x, int d, long long nodes,
+          double* partials, unsigned* counter, Scalars* sc) {
   double acc[1] = {0.0};
   const long long len = (long long)d * nodes;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
        i += (long long)gridDim.x * blockDim.x) {
     const long long a = i / nodes;
-    const double e = a == 0 ? e0 : (a == 1 ? e1 : e2);
+    const double e = sc->E[a];  // the macroscopic field of component a (0 for the conforming)
     const double v = (double)g[i] - (double)x[i] + e;
     acc[0] = fma(v, v, acc[0]);
   }
@@ -1124,6 +1211,33 @@ __global__ void k_pad_spectrum(const cpx<T>* __restrict__ Sn, cpx<T>* __restrict
     v.x *= scale;
     v.y *= scale;
     Sm[a * mlen + ((long long)t0 * m1 + t1) * mh + k2] = v;
+  }
+}
+
+// half spectrum of grid N taken from the half spectrum of grid M (M >= N per axis) at the same
+// signed frequencies, scaled by `scale` (restriction of a trigonometric polynomial of order N,
+// the inverse of k_pad_spectrum); D = 2 or 3
+template <typename T>
+__global__ void k_crop_spectrum(const cpx<T>* __restrict__ Sm, cpx<T>* __restrict__ Sn, int D,
+                                int n0, int n1, int nh, int m0, int m1, int mh, T scale,
+                                long long nlen, long long mlen) {
+  const long long per = (long long)n0 * n1 * nh;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < per * D;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(i / per);
+    long long r = i - a * per;
+    const int k2 = (int)(r % nh);
+    r /= nh;
+    const int j1 = (int)(r % n1);
+    const int j0 = (int)(r / n1);
+    const int s0 = j0 <= (n0 - 1) / 2 ? j0 : j0 - n0;
+    const int s1 = j1 <= (n1 - 1) / 2 ? j1 : j1 - n1;
+    const int t0 = s0 >= 0 ? s0 : s0 + m0;
+    const int t1 = s1 >= 0 ? s1 : s1 + m1;
+    cpx<T> v = Sm[a * mlen + ((long long)t0 * m1 + t1) * mh + k2];
+    v.x *= scale;
+    v.y *= scale;
+    Sn[a * nlen + i - a * per] = v;
   }
 }
 

@@ -70,6 +70,10 @@ inline bool plan_axis(int n, int rmax, AxisPlan* P) {
   return true;
 }
 
+// cudaMalloc behind the allocation-failure injector of hom_debug_fail_alloc (hom_api.cu):
+// HOM_OK, or HOM_ERR_OOM with *p = nullptr
+int alloc(void** p, size_t bytes);
+
 // largest register radix per precision (FP64 values take twice the registers)
 template <typename T> constexpr int reg_rmax() { return sizeof(T) == 8 ? 15 : 27; }
 
@@ -107,22 +111,23 @@ struct Engine {
   bool two_line = false;  // the 3-D scalar projection runs the two-line chain (FP32 plans)
 
   // plan the axes with register radices <= rmax and tiles within `budget` bytes of shared
-  // memory and `threads` threads per CTA; allocates the twiddle tables
+  // memory and `threads` threads per CTA, for fields of nc components (0: D); allocates the
+  // twiddle tables
   int init(int D, const int* n, const int* support, size_t budget, int rmax, int threads,
-           bool allow_two_line = true) {
+           bool allow_two_line = true, int nc = 0) {
     rmax_used = rmax;
     budget_used = budget;
     threads_used = threads;
     for (int a = 0; a < D; ++a)
       if (!plan_axis(n[a], rmax, &plan[a])) return HOM_ERR_INVALID;
-    if (!Ops<T>::plan_geometry(D, n, plan, budget, threads, &g)) return HOM_ERR_UNSUPPORTED;
-    two_line = allow_two_line && Ops<T>::two_line_ok(g, plan[0], plan[1]);
+    if (!Ops<T>::plan_geometry(D, n, plan, budget, threads, &g, nc)) return HOM_ERR_UNSUPPORTED;
+    two_line = allow_two_line && g.NC == D && Ops<T>::two_line_ok(g, plan[0], plan[1]);
     const int nl = n[D - 1];
     g1 = g;
     while (g1.LB < 16 && Ops<T>::smem_line(nl, 1, g1.LB + 2) <= budget) g1.LB += 2;
     for (int a = 0; a < D; ++a) {
       auto tw_h = twiddles<T>(n[a]);
-      if (cudaMalloc(&tw[a], sizeof(cpx<T>) * n[a]) != cudaSuccess) return HOM_ERR_OOM;
+      if (alloc((void**)&tw[a], sizeof(cpx<T>) * n[a]) != HOM_OK) return HOM_ERR_OOM;
       if (cudaMemcpy(tw[a], tw_h.data(), sizeof(cpx<T>) * n[a], cudaMemcpyHostToDevice) != cudaSuccess)
         return HOM_ERR_CUDA;
     }
@@ -143,7 +148,7 @@ struct Engine {
       rk_h[0] = (T)0;
       for (int q = 1; q <= pg.kkmax; ++q) rk_h[q] = sc / (T)q;
       void* d = nullptr;
-      if (cudaMalloc(&d, sizeof(T) * rk_h.size()) != cudaSuccess) return HOM_ERR_OOM;
+      if (alloc(&d, sizeof(T) * rk_h.size()) != HOM_OK) return HOM_ERR_OOM;
       rk = static_cast<T*>(d);
       if (cudaMemcpy(d, rk_h.data(), sizeof(T) * rk_h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return HOM_ERR_CUDA;
@@ -184,18 +189,18 @@ struct Engine {
   void apply2(int pre, int mode, int post, const Fields<T>& ff, const Fields<T>& fi, cpx<T>* S,
               Scalars* sc, const OpArgs& args, double* partials, unsigned* counter, int negate,
               cudaStream_t st) const {
-    Ops<T>::line_fwd(g, pre, ff, S, plan[g.D - 1], tw[g.D - 1], g.D, mat, sc, args, st, nullptr,
+    Ops<T>::line_fwd(g, pre, ff, S, plan[g.D - 1], tw[g.D - 1], g.NC, mat, sc, args, st, nullptr,
                      1, partials);
     if (mode == PROJ_GAMMA && two_line) {
       Ops<T>::strided_two_line(g, 0, S, plan[1], tw[1], sc, st);
       Ops<T>::proj_two_line(g, S, plan[0], tw[0], pg, sc, st);
       Ops<T>::strided_two_line(g, 1, S, plan[1], tw[1], sc, st);
     } else {
-      if (g.D == 3) Ops<T>::strided(g, 1, 0, S, plan[1], tw[1], g.D, sc, st);
+      if (g.D == 3) Ops<T>::strided(g, 1, 0, S, plan[1], tw[1], g.NC, sc, st);
       Ops<T>::proj(g, mode, S, plan[0], tw[0], pg, sc, st);
-      if (g.D == 3) Ops<T>::strided(g, 1, 1, S, plan[1], tw[1], g.D, sc, st);
+      if (g.D == 3) Ops<T>::strided(g, 1, 1, S, plan[1], tw[1], g.NC, sc, st);
     }
-    Ops<T>::line_inv(g, post, S, fi, plan[g.D - 1], tw[g.D - 1], g.D, mat, sc, args, partials,
+    Ops<T>::line_inv(g, post, S, fi, plan[g.D - 1], tw[g.D - 1], g.NC, mat, sc, args, partials,
                      counter, negate, st);
   }
 
@@ -205,22 +210,23 @@ struct Engine {
                    cudaStream_t st) const {
     Fields<T> f{};
     OpArgs args{};
-    Ops<T>::line_fwd(g, pre, f, nullptr, plan[g.D - 1], tw[g.D - 1], g.D, mat, nullptr, args, st,
+    Ops<T>::line_fwd(g, pre, f, nullptr, plan[g.D - 1], tw[g.D - 1], g.NC, mat, nullptr, args, st,
                      reqs, n);
     if (mode == PROJ_GAMMA && two_line) {
       Ops<T>::strided_two_line(g, 0, nullptr, plan[1], tw[1], nullptr, st, reqs, n);
       Ops<T>::proj_two_line(g, nullptr, plan[0], tw[0], pg, nullptr, st, reqs, n);
       Ops<T>::strided_two_line(g, 1, nullptr, plan[1], tw[1], nullptr, st, reqs, n);
     } else {
-      if (g.D == 3) Ops<T>::strided(g, 1, 0, nullptr, plan[1], tw[1], g.D, nullptr, st, reqs, n);
+      if (g.D == 3) Ops<T>::strided(g, 1, 0, nullptr, plan[1], tw[1], g.NC, nullptr, st, reqs, n);
       Ops<T>::proj(g, mode, nullptr, plan[0], tw[0], pg, nullptr, st, reqs, n);
-      if (g.D == 3) Ops<T>::strided(g, 1, 1, nullptr, plan[1], tw[1], g.D, nullptr, st, reqs, n);
+      if (g.D == 3) Ops<T>::strided(g, 1, 1, nullptr, plan[1], tw[1], g.NC, nullptr, st, reqs, n);
     }
-    Ops<T>::line_inv(g, post, nullptr, f, plan[g.D - 1], tw[g.D - 1], g.D, mat, nullptr, args,
+    Ops<T>::line_inv(g, post, nullptr, f, plan[g.D - 1], tw[g.D - 1], g.NC, mat, nullptr, args,
                      nullptr, nullptr, 0, st, reqs, n);
   }
 
-  // plain forward transform (no projection), result is the unscaled half spectrum
+  // plain forward transform (no projection) of ncomp (1 or NC) components, result is the
+  // unscaled half spectrum
   void forward(const T* x, cpx<T>* S, int ncomp, cudaStream_t st) const {
     const PassGeom& gg = (ncomp == 1) ? g1 : g;
     Fields<T> f{};
@@ -254,10 +260,9 @@ struct PlanChoice {
   int threads;    // threads per CTA of the runtime-radix passes
   bool two_line;  // FP32 3-D scalar projection: two-line chain where the plans allow it
 };
-PlanChoice plan_choice(int precision_bytes, int d, const int* M, const int* N);
-int alloc(void** p, size_t bytes);
+PlanChoice plan_choice(int precision_bytes, int d, const int* M, const int* N, int nc = 0);
 int check_last();
-bool spd_eigs(const double* t, int d, double* lo, double* hi);
+bool spd_eigs(const double* t, int d, double* lo, double* hi);  // d <= kMaxComp
 
 }  // namespace detail
 }  // namespace hom
@@ -275,7 +280,7 @@ struct SolveState {
   int check = 8;
   int issued = 0;
   int matvecs = 0;
-  double E[3] = {0, 0, 0};
+  double E[hom::kMaxComp] = {0, 0, 0, 0, 0, 0};
   double nE = 0;
   // iterative refinement (HOM_FP32_REFINED): FP32 inner solves of C d = r, FP64 outer residual
   bool refined = false;
@@ -290,10 +295,12 @@ struct SolveState {
   bool finished = false;
   bool converged = false;
   float inner_ms = 0;
+  int out_flags = 0;  // hom_opts.out_flags of the session
 };
 
 struct hom_problem {
   int d = 0;
+  int nc = 0;               // components of a field: d, or d (d + 1) / 2 for elasticity
   int N[3] = {1, 1, 1};     // trigonometric order
   int M[3] = {1, 1, 1};     // solve grid (N for GaNi, double grid for Ga)
   int integration = HOM_APPROX;
@@ -308,10 +315,17 @@ struct hom_problem {
   void* d_phase = nullptr;
   int index_bytes = 1;
   double* d_table = nullptr;
+  double* d_inv = nullptr;        // elasticity: (C_p + omega I)^{-1} per phase (Eyre-Milton)
+  double inv_omega = 0;           // the omega d_inv was formed with
   int nphase = 0;
 
   hom::detail::Engine<double> e64;
   hom::detail::Engine<float> e32;
+  // exact integration: engine of the N grid, its half spectrum and an N-grid field, created by
+  // the first hom_restrict (or HOM_OUT_NGRID output)
+  hom::detail::Engine<double> eN;
+  void* SN = nullptr;
+  double* yN = nullptr;
 
   // buffers
   void* S = nullptr;              // half spectrum work buffer (sized for FP64, d components)

@@ -73,3 +73,13 @@ def test_fft_flop_model(bench):
     spec = n * n * ((n + 1) // 2) * 3
     assert flops["strided"] == spec * f243
     assert flops["proj"] > 2 * flops["strided"]  # four transforms of two lines + Gamma^
+
+
+def test_flop_model_sums_to_the_fft_count_of_a_matvec(bench):
+    # one operator application = d forward and d inverse real 3-D transforms of 2.5 |N| log2 |N|
+    import math
+    flops = bench.pass_flops_model((243, 243, 243))
+    per_step = flops["line_fwd"] + 2 * flops["strided"] + flops["proj"] + flops["line_inv"]
+    nodes = 243 ** 3
+    assert abs(per_step - 2 * 3 * 2.5 * nodes * math.log2(nodes)) < 1e-6 * per_step
+    assert abs(flops["strided"] / 1e9 - 0.8526) < 1e-3  # one axis of three transforms
