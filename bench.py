@@ -383,7 +383,9 @@ def run_ours(args, rank, world, local):
     fp32_only = args.quick and args.precision == "fp32"
     prob = H.Problem(D, N_GRID, H.phase_material(ph, table),
                      precision=H.HOM_FP32_REFINED if fp32_only else H.HOM_FP64)
-    tune = H.hom_autotune(prob.h, reps=2)  # the launch plan a user gets from the autotuner
+    # the launch plan a user gets from the autotuner (--no-tune: the default plan, for
+    # profiler captures that should not see the candidates' launches)
+    tune = H.hom_autotune(prob.h, reps=2) if not args.no_tune else {"rmax64": 15, "smem_kb64": 110}
     fp64_peak = None if args.quick else measure_fp64_peak(H, local)
     stream = torch.cuda.current_stream()
     total = args.warmup + args.steps
@@ -1030,6 +1032,8 @@ def main():
     ap.add_argument("--no-served", action="store_true", help="skip the short served run")
     ap.add_argument("--no-c4", action="store_true", help="skip the 405^3 refinement check")
     ap.add_argument("--no-elastic", action="store_true", help="skip the elasticity step")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="with --quick: keep the default launch plan (profiler captures)")
     ap.add_argument("--configs", action="store_true", help="run configurations 1-4 end to end")
     ap.add_argument("--configs-maxit", type=int, default=20000)
     ap.add_argument("--kappa", type=int, default=0,
