@@ -350,7 +350,7 @@ void hom_server_destroy(hom_server* S);
 
 /* Autotuner of the launch plan (build extension). For the grid of P it times `reps` operator
  * applications (after one warm-up) for every candidate register-radix limit (FP64: 9, 15; FP32:
- * 9, 15, 27), shared-memory tile budget per CTA (56, 110, 150, 200 KiB), thread count per CTA
+ * 9, 15, 27), shared-memory tile budget per CTA (56, 80, 96, 110, 150, 200 KiB), thread count per CTA
  * of the runtime-radix passes (128, 256) and, in FP32, the two-line chain of the 3-D scalar
  * projection (on, off) where both column axes have specialised plans, re-plans P with the
  * fastest, and records the choice so that every later hom_create of the same grid, integration
@@ -367,6 +367,12 @@ typedef struct {
                               between its column passes (specialised plans on axes 0 and 1) */
 } hom_tune_report;
 int hom_autotune(hom_problem* P, int reps, hom_tune_report* report);
+
+/* Re-plan P with a given launch plan (the fields of hom_tune_report: the FP64 ones, and for
+ * HOM_FP32_REFINED the FP32 ones; times ignored), e.g. one that hom_autotune reported in an
+ * earlier process, without timing candidates. Results change by rounding order at most.
+ * HOM_ERR_INVALID for a plan outside the autotuner's candidates or during a session. */
+int hom_set_plan(hom_problem* P, const hom_tune_report* plan);
 
 /* Samples on the N grid (d x |N| doubles, device y_dev) of a field x_dev on the solve grid M of
  * an exact-integration problem whose spectrum lies in Z_N (every Ga iterate, Section 2.3):

@@ -38,7 +38,7 @@ EXPORTED = ["hom_create", "hom_grid", "hom_bounds", "hom_apply", "hom_solve", "h
             "hom_batch_destroy", "hom_server_create", "hom_server_submit", "hom_server_step",
             "hom_server_poll", "hom_server_status", "hom_server_destroy", "hom_autotune",
             "hom_solve_history", "hom_solve_current", "hom_solve_nonconformity", "hom_restrict",
-            "hom_measure_fp64", "hom_debug_fail_alloc"]
+            "hom_measure_fp64", "hom_debug_fail_alloc", "hom_set_plan"]
 PASS_KINDS = ["line_fwd", "strided", "proj", "line_inv", "vector"]
 
 
@@ -100,6 +100,7 @@ def _load():
     lib.hom_apply_static.argtypes = [ip, ctypes.POINTER(ctypes.c_int), vp, ip, dp, ip, ip, dp, vp,
                                      vp, vp]
     lib.hom_autotune.argtypes = [vp, ip, ctypes.POINTER(hom_tune_report)]
+    lib.hom_set_plan.argtypes = [vp, ctypes.POINTER(hom_tune_report)]
     lib.hom_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp)]
     lib.hom_batch_iterate.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_int)]
     lib.hom_batch_destroy.argtypes = [vp]
@@ -340,6 +341,15 @@ def hom_autotune(P, reps=3):
     rep = hom_tune_report()
     _check(_lib.hom_autotune(P, int(reps), ctypes.byref(rep)), "hom_autotune")
     return {k: getattr(rep, k) for k, _ in rep._fields_}
+
+
+def hom_set_plan(P, plan: dict):
+    """Re-plan P with a launch plan given as hom_autotune's report (a dict of its fields)."""
+    rep = hom_tune_report()
+    for k, _ in rep._fields_:
+        if k in plan:
+            setattr(rep, k, type(getattr(rep, k))(plan[k]))
+    return _check(_lib.hom_set_plan(P, ctypes.byref(rep)), "hom_set_plan")
 
 
 def hom_batch_create(problems):

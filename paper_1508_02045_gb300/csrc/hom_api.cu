@@ -1533,13 +1533,37 @@ int tune_engine(hom_problem* P, Engine<T>& E, T* x, T* y, int reps, const std::v
 
 }  // namespace
 
+extern "C" int hom_set_plan(hom_problem* P, const hom_tune_report* plan) {
+  if (!P || !plan || P->sv.active) return HOM_ERR_INVALID;
+  const size_t cap = (size_t)dynamic_smem_cap();
+  auto ok = [&](int rmax, int kb, int threads) {
+    return rmax >= 3 && rmax <= kMaxRadix && kb > 0 && (size_t)kb * 1024 <= cap &&
+           (threads == kThreads / 2 || threads == kThreads);
+  };
+  if (!ok(plan->rmax64, plan->smem_kb64, plan->threads64)) return HOM_ERR_INVALID;
+  const bool f32 = P->precision == HOM_FP32_REFINED;
+  if (f32 && !ok(plan->rmax32, plan->smem_kb32, plan->threads32)) return HOM_ERR_INVALID;
+  P->e64.release_plan();
+  int rc = P->e64.init(P->d, P->M, P->N, (size_t)plan->smem_kb64 * 1024, plan->rmax64,
+                       plan->threads64, true, P->nc);
+  if (rc) return rc;
+  if (f32) {
+    P->e32.release_plan();
+    rc = P->e32.init(P->d, P->M, P->N, (size_t)plan->smem_kb32 * 1024, plan->rmax32,
+                     plan->threads32, plan->two_line32 != 0, P->nc);
+    if (rc) return rc;
+  }
+  return check_last();
+}
+
 extern "C" int hom_autotune(hom_problem* P, int reps, hom_tune_report* report) {
   if (!P || P->sv.active) return HOM_ERR_INVALID;
   if (reps < 1) reps = 3;
   hom_tune_report rep{};
   PlanChoice c{};
   double ms = 0;
-  const std::vector<size_t> budgets = {56 * 1024, 110 * 1024, 150 * 1024, 200 * 1024};
+  const std::vector<size_t> budgets = {56 * 1024, 80 * 1024, 96 * 1024, 110 * 1024, 150 * 1024,
+                                       200 * 1024};
   int rc = tune_engine<double>(P, P->e64, P->vec[0], P->vec[1], reps, {9, 15}, budgets, &c, &ms);
   if (rc) return rc;
   rep.rmax64 = c.rmax;

@@ -196,3 +196,17 @@ def test_fp64_throughput_probe():
     assert ms_fma > 0 and ms_add > 0
     tf = flops / ms_fma / 1e9
     assert 0.1 < tf < 10.0  # TFLOP/s: a GB300 runs FP64 FMAs near 1.2 T
+
+
+@pytest.mark.skipif(torch.cuda.device_count() < 2, reason="needs a second CUDA device")
+def test_problem_on_a_second_device():
+    # the kernels' per-device set-up (DFT constants, shared-memory limits) runs for each device
+    N = (27, 25, 21)
+    E = np.array([1.0, 0.0, 0.0])
+    res = []
+    for dev in (0, 1):
+        with torch.cuda.device(dev):
+            P, _, _ = square_problem(N)
+            res.append(H.hom_solve(P.h, E, H.HOM_CG, 1e-10)[0])
+            P.close()
+    assert res[0] == res[1]

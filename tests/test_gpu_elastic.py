@@ -178,3 +178,30 @@ def test_elastic_unsupported_combinations():
     with pytest.raises(H.HomError) as ei:
         H.hom_create(2, N, H.stiffness_material(ph, bad))
     assert ei.value.status == H.HOM_ERR_INVALID
+
+
+def test_elastic_batch_equals_solo():
+    # two same-shape strain problems advanced by one launch per pass (hom_batch) end exactly
+    # where their solo solves end
+    N = (15, 13, 11)
+    Es = [np.array([1.0, 0, 0, 0, 0, 0]), np.array([0.2, -0.1, 0.4, 0.3, 0.0, -0.5])]
+    solo = []
+    for E in Es:
+        P, _, _ = problem(N, aniso=True)
+        solo.append(H.hom_solve(P.h, E, H.HOM_CG, 1e-9)[0])
+        P.close()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        probs = [problem(N, aniso=True)[0] for _ in Es]
+        for P, E in zip(probs, Es):
+            H.hom_solve_begin(P.h, E, H.HOM_CG, 1e-9, None)
+        B = H.hom_batch_create([P.h for P in probs])
+        for _ in range(500):
+            if H.hom_batch_iterate(B, 8, use_graph=True, poll=True):
+                break
+        for P, ref in zip(probs, solo):
+            AH, _, st, _ = H.hom_solve_end(P.h, 6)
+            assert st["converged"] and AH == ref
+        H.hom_batch_destroy(B)
+        for P in probs:
+            P.close()
