@@ -371,6 +371,16 @@ def pass_bytes(word=8, two_line=False, fused_cg=False):
 # ------------------------------------------------------------------------------------------
 
 def run_ours(args, rank, world, local):
+    """Everything on a stream of its own: the library launches its pass kernels there with a
+    programmatic dependency on the kernel before them (on the legacy default stream it cannot),
+    so each pass's launch overlaps the previous pass's drain."""
+    import torch
+    torch.cuda.set_device(local)
+    with torch.cuda.stream(torch.cuda.Stream()):
+        return _run_ours(args, rank, world, local)
+
+
+def _run_ours(args, rank, world, local):
     import torch
     import paper_1508_02045_gb300 as H
 

@@ -5,6 +5,15 @@
 
 namespace hom {
 
+// Programmatic dependent launch: the pass kernels are launched (launch_pass, ops.h) so that
+// their CTAs may be scheduled while the kernel before them on the stream drains; each calls
+// this before its first access to global memory and waits there until that kernel has
+// completed and its writes are visible. For a kernel launched without that dependency the
+// wait returns at once.
+__device__ __forceinline__ void wait_prior_grid() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
 // complex value; aligned to its size so that loads and stores are single vector accesses
 template <typename T>
 struct __align__(2 * sizeof(T)) cpx {

@@ -129,6 +129,26 @@ void pair_line_inv_f32(int D, int post, const AxisPlan& P, const cpx<float>* S,
 long long& launch_counter();
 int dynamic_smem_cap();
 
+// Launch of a pass kernel with a programmatic dependency on the kernel before it on the stream
+// (its CTAs may be scheduled while that one drains; the kernel itself waits in
+// wait_prior_grid before touching global memory). On the legacy default stream, which such
+// launches are not used on, a plain launch.
+template <typename... KArgs, typename... Args>
+inline void launch_pass(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                        cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = st != nullptr ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, ((KArgs)args)...);
+}
+
 // Optional per-pass event timing (hom_profile_enable): kinds of launches
 enum PassKind { KIND_LINE_FWD = 0, KIND_STRIDED = 1, KIND_PROJ = 2, KIND_LINE_INV = 3,
                 KIND_VECTOR = 4, KIND_COUNT = 5 };

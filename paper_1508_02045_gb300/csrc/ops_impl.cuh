@@ -192,7 +192,7 @@ static void line_fwd_d(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S
   const size_t sm = Ops<T>::smem_line(P.n, ncomp, g.LB);
   const bool prof = profiling();
   if (prof) prof_mark(KIND_LINE_FWD, st, true);
-#define HOM_LF(PRE_) k_line_fwd<T, D, PRE_><<<grid, g.NTl, sm, st>>>(f, S, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, reqs)
+#define HOM_LF(PRE_) launch_pass(k_line_fwd<T, D, PRE_>, grid, g.NTl, sm, st, f, S, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, reqs)
   switch (pre) {
     case PRE_AFFINE: HOM_LF(PRE_AFFINE); break;
     case PRE_LINEAR: HOM_LF(PRE_LINEAR); break;
@@ -219,7 +219,7 @@ void Ops<T>::line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
                                        partials, st, reqs, nreq);
       ++launch_counter();
       if (pre == PRE_CG_DOT) {
-        k_cg_alpha<T><<<dim3(1, 1, (unsigned)nreq), kThreads, 0, st>>>(partials, nb,
+        launch_pass(k_cg_alpha<T>, dim3(1, 1, (unsigned)nreq), kThreads, 0, st, partials, nb,
                                                                       g.nodes, sc, reqs);
         ++launch_counter();
       }
@@ -237,7 +237,7 @@ void Ops<T>::line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
   }
   if (pre == PRE_CG_DOT) {
     const int nb = (int)((g.nlines + g.LB - 1) / g.LB);
-    k_cg_alpha<T><<<dim3(1, 1, (unsigned)nreq), kThreads, 0, st>>>(partials, nb, g.nodes, sc,
+    launch_pass(k_cg_alpha<T>, dim3(1, 1, (unsigned)nreq), kThreads, 0, st, partials, nb, g.nodes, sc,
                                                                   reqs);
     ++launch_counter();
   }
@@ -274,7 +274,7 @@ void Ops<T>::strided(const PassGeom& g, int axis, int inv, cpx<T>* S, const Axis
   } else {
     const dim3 grid((unsigned)((C + TC - 1) / TC), (unsigned)batches, (unsigned)nreq);
     const size_t sm = smem_strided(P.n, TCp, P.nst);
-    k_strided<T><<<grid, NT, sm, st>>>(S, P, tw, C, es, bs, TC, TCp, inv, sc, reqs);
+    launch_pass(k_strided<T>, grid, NT, sm, st, S, P, tw, C, es, bs, TC, TCp, inv, sc, reqs);
   }
   if (prof) prof_mark(KIND_STRIDED, st, false);
   ++launch_counter();
@@ -297,7 +297,7 @@ void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, con
     if constexpr (sizeof(T) == 8) {
       const dim3 grid((unsigned)((pg.C + g.TC0 - 1) / g.TC0), 1, (unsigned)nreq);
       const size_t sm = smem_proj(P.n, g.NC, g.TC0p, P.nst);
-#define HOM_PJE(D_, NC_, M_) k_proj<T, D_, NC_, M_><<<grid, g.NT0, sm, st>>>(S, P, tw, pg, g.TC0, g.TC0p, sc, reqs)
+#define HOM_PJE(D_, NC_, M_) launch_pass(k_proj<T, D_, NC_, M_>, grid, g.NT0, sm, st, S, P, tw, pg, g.TC0, g.TC0p, sc, reqs)
       if (g.D == 2) {
         if (mode == PROJ_EM) HOM_PJE(2, 3, PROJ_EM); else HOM_PJE(2, 3, PROJ_GAMMA);
       } else {
@@ -312,14 +312,14 @@ void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, con
   if (g.D == 3 && mode == PROJ_GAMMA) {
     const dim3 grid((unsigned)((pg.C + g.TCq - 1) / g.TCq), 1, (unsigned)nreq);
     const size_t sm = smem_proj_scalar(P.n, g.TCqp);
-    k_proj_scalar<T><<<grid, g.NTq, sm, st>>>(S, P, tw, pg, g.TCq, g.TCqp, sc, reqs);
+    launch_pass(k_proj_scalar<T>, grid, g.NTq, sm, st, S, P, tw, pg, g.TCq, g.TCqp, sc, reqs);
     if (prof) prof_mark(KIND_PROJ, st, false);
     ++launch_counter();
     return;
   }
   const dim3 grid((unsigned)((pg.C + g.TC0 - 1) / g.TC0), 1, (unsigned)nreq);
   const size_t sm = smem_proj(P.n, g.D, g.TC0p, P.nst);
-#define HOM_PJ(D_, M_) k_proj<T, D_, D_, M_><<<grid, g.NT0, sm, st>>>(S, P, tw, pg, g.TC0, g.TC0p, sc, reqs)
+#define HOM_PJ(D_, M_) launch_pass(k_proj<T, D_, D_, M_>, grid, g.NT0, sm, st, S, P, tw, pg, g.TC0, g.TC0p, sc, reqs)
   if (g.D == 2) {
     if (mode == PROJ_EM) HOM_PJ(2, PROJ_EM); else HOM_PJ(2, PROJ_GAMMA);
   } else {
@@ -374,7 +374,7 @@ static void line_inv_d(const PassGeom& g, int post, const cpx<T>* S, const Field
   const size_t sm = Ops<T>::smem_line(P.n, ncomp, g.LB);
   const bool prof = profiling();
   if (prof) prof_mark(KIND_LINE_INV, st, true);
-#define HOM_LI(POST_) k_line_inv<T, D, POST_><<<grid, g.NTl, sm, st>>>(S, f, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, counter, negate, reqs)
+#define HOM_LI(POST_) launch_pass(k_line_inv<T, D, POST_>, grid, g.NTl, sm, st, S, f, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, counter, negate, reqs)
   switch (post) {
     case POST_RICH: HOM_LI(POST_RICH); break;
     case POST_CG: HOM_LI(POST_CG); break;

@@ -68,9 +68,9 @@ void pair_strided_f32(const AxisPlan& P, int inv, cpx<float>* S, const cpx<float
     size_t sm = sizeof(cpx<T>) * (size_t)(R1_ * R2_) * (TC + 2);                                \
     if (TC * R2_ >= 128 && sm < kPairStridedMinSmem) sm = kPairStridedMinSmem;                 \
     if (inv)                                                                                   \
-      k_pair_strided<T, R1_, R2_, true><<<grid, TC * R2_, sm, st>>>(S, tw, C, es, bs, sc, reqs); \
+      launch_pass(k_pair_strided<T, R1_, R2_, true>, grid, TC * R2_, sm, st, S, tw, C, es, bs, sc, reqs); \
     else                                                                                       \
-      k_pair_strided<T, R1_, R2_, false><<<grid, TC * R2_, sm, st>>>(S, tw, C, es, bs, sc, reqs); \
+      launch_pass(k_pair_strided<T, R1_, R2_, false>, grid, TC * R2_, sm, st, S, tw, C, es, bs, sc, reqs); \
     return;                                                                                    \
   }
   HOM_PAIR_PLANS(HOM_PAIR_ST)
@@ -87,9 +87,9 @@ void pair_strided2_f32(const AxisPlan& P, int inv, cpx<float>* S, const cpx<floa
     const dim3 grid((unsigned)((C + TC - 1) / TC), (unsigned)planes, (unsigned)nreq);         \
     const size_t sm = sizeof(cpx<T>) * (size_t)(R1_ * R2_) * (1 + 2 * (TC + 1));               \
     if (inv)                                                                                   \
-      k_pair_strided2<T, R1_, R2_, true><<<grid, 2 * TC * R2_, sm, st>>>(S, tw, C, es, bs, cs, sc, reqs); \
+      launch_pass(k_pair_strided2<T, R1_, R2_, true>, grid, 2 * TC * R2_, sm, st, S, tw, C, es, bs, cs, sc, reqs); \
     else                                                                                       \
-      k_pair_strided2<T, R1_, R2_, false><<<grid, 2 * TC * R2_, sm, st>>>(S, tw, C, es, bs, cs, sc, reqs); \
+      launch_pass(k_pair_strided2<T, R1_, R2_, false>, grid, 2 * TC * R2_, sm, st, S, tw, C, es, bs, cs, sc, reqs); \
     return;                                                                                    \
   }
   HOM_PAIR_PLANS(HOM_PAIR_ST2)
@@ -106,9 +106,9 @@ void pair_proj_f32(int D, int mode, bool two, const AxisPlan& P, cpx<float>* S,
     const dim3 grid((unsigned)((pg.C + TC - 1) / TC), 1, (unsigned)nreq);                     \
     const size_t sm = sizeof(cpx<T>) * ((size_t)(R1_ * R2_) * (1 + D_ * (TC + 1)));        \
     if (mode == PROJ_EM)                                                                       \
-      k_pair_proj<T, D_, PROJ_EM, R1_, R2_><<<grid, D_ * TC * R2_, sm, st>>>(S, tw, pg, sc, reqs); \
+      launch_pass(k_pair_proj<T, D_, PROJ_EM, R1_, R2_>, grid, D_ * TC * R2_, sm, st, S, tw, pg, sc, reqs); \
     else                                                                                       \
-      k_pair_proj<T, D_, PROJ_GAMMA, R1_, R2_><<<grid, D_ * TC * R2_, sm, st>>>(S, tw, pg, sc, reqs); \
+      launch_pass(k_pair_proj<T, D_, PROJ_GAMMA, R1_, R2_>, grid, D_ * TC * R2_, sm, st, S, tw, pg, sc, reqs); \
   }
 #define HOM_PAIR_PJ(R1_, R2_)                                                                  \
   if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
@@ -119,9 +119,9 @@ void pair_proj_f32(int D, int mode, bool two, const AxisPlan& P, cpx<float>* S,
       const dim3 grid((unsigned)((pg.C + TC - 1) / TC), 1, (unsigned)nreq);                   \
       const size_t sm = sizeof(cpx<T>) * ((size_t)(R1_ * R2_) * (1 + 2 * (TC + 1)));           \
       if (two)                                                                                 \
-        k_pair_proj_scalar<T, R1_, R2_, true><<<grid, 2 * TC * R2_, sm, st>>>(S, tw, pg, sc, reqs); \
+        launch_pass(k_pair_proj_scalar<T, R1_, R2_, true>, grid, 2 * TC * R2_, sm, st, S, tw, pg, sc, reqs); \
       else                                                                                     \
-        k_pair_proj_scalar<T, R1_, R2_, false><<<grid, 2 * TC * R2_, sm, st>>>(S, tw, pg, sc, reqs); \
+        launch_pass(k_pair_proj_scalar<T, R1_, R2_, false>, grid, 2 * TC * R2_, sm, st, S, tw, pg, sc, reqs); \
     } else {                                                                                   \
       HOM_PAIR_PJ_D(3, R1_, R2_)                                                               \
     }                                                                                          \
@@ -140,7 +140,7 @@ int pair_line_fwd_f32(int D, int pre, const AxisPlan& P, const Fields<float>& f,
   (void)D;  // D = 3 (pair_line_fwd_has)
   const FastDiv fdn = make_fastdiv(P.n);
 #define HOM_PAIR_LF_P(PRE_, R1_, R2_)                                                          \
-  k_pair_line_fwd<T, 3, PRE_, R1_, R2_><<<grid, NT, sm, st>>>(f, S, tw, nlines, scs, mat, sc,    \
+  launch_pass(k_pair_line_fwd<T, 3, PRE_, R1_, R2_>, grid, NT, sm, st, f, S, tw, nlines, scs, mat, sc,    \
                                                              args, fdn, partials, reqs)
 #define HOM_PAIR_LF(R1_, R2_)                                                                  \
   if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
@@ -168,7 +168,7 @@ void pair_line_inv_f32(int D, int post, const AxisPlan& P, const cpx<float>* S,
   (void)D;  // D = 3 (pair_line_inv_has)
   const FastDiv fdn = make_fastdiv(P.n);
 #define HOM_PAIR_LI_P(POST_, R1_, R2_)                                                         \
-  k_pair_line_inv<T, 3, POST_, R1_, R2_><<<grid, NT, sm, st>>>(S, f, tw, nlines, scs, mat, sc,   \
+  launch_pass(k_pair_line_inv<T, 3, POST_, R1_, R2_>, grid, NT, sm, st, S, f, tw, nlines, scs, mat, sc,   \
                                                                args, partials, counter, negate, \
                                                                fdn, reqs)
 #define HOM_PAIR_LI(R1_, R2_)                                                                  \

@@ -91,6 +91,7 @@ template <typename T, int R1, int R2, bool INV>
 __global__ void __launch_bounds__(pair_tc_strided<R2>() * R2)
 k_pair_strided(cpx<T>* S, const cpx<T>* __restrict__ twg, long long C, long long es,
                long long bs, const Scalars* sc, const ReqDesc<T>* __restrict__ reqs) {
+  wait_prior_grid();
   constexpr int n = R1 * R2, TC = pair_tc_strided<R2>(), TCp = TC + 1, NT = TC * R2;
   if (reqs != nullptr) {
     S = reqs[blockIdx.z].S;
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(2 * pair_tc_strided<R2>() * R2)
 k_pair_strided2(cpx<T>* S, const cpx<T>* __restrict__ twg, long long C, long long es,
                 long long bs, long long cs, const Scalars* sc,
                 const ReqDesc<T>* __restrict__ reqs) {
+  wait_prior_grid();
   constexpr int n = R1 * R2, TC = pair_tc_strided<R2>(), TCp = TC + 1, NT = 2 * TC * R2;
   constexpr int tstr = n * TCp;
   if (reqs != nullptr) {
@@ -204,6 +206,7 @@ template <typename T, int D, int MODE, int R1, int R2>
 __global__ void __launch_bounds__(D * pair_tc_proj<D, R2>() * R2)
 k_pair_proj(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, const Scalars* sc,
             const ReqDesc<T>* __restrict__ reqs) {
+  wait_prior_grid();
   constexpr int n = R1 * R2, TC = pair_tc_proj<D, R2>(), TCp = TC + 1, NT = D * TC * R2;
   constexpr int cstr = n * TCp;
   if (reqs != nullptr) {
@@ -323,6 +326,7 @@ template <typename T, int R1, int R2, bool TWO>
 __global__ void __launch_bounds__(2 * pair_tc_proj_scalar<R2>() * R2)
 k_pair_proj_scalar(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, const Scalars* sc,
                    const ReqDesc<T>* __restrict__ reqs) {
+  wait_prior_grid();
   constexpr int n = R1 * R2, TC = pair_tc_proj_scalar<R2>(), TCp = TC + 1, NT = 2 * TC * R2;
   constexpr int cstr = n * TCp;
   if (reqs != nullptr) {
@@ -571,6 +575,7 @@ __global__ void __launch_bounds__(pair_line_threads<D, R2>(), 4)
 k_pair_line_fwd(Fields<T> f, cpx<T>* S, const cpx<T>* __restrict__ twg, long long nlines,
                 long long scs, MatView<T> mat, Scalars* sc, OpArgs args, FastDiv fdn,
                 double* partials, const ReqDesc<T>* __restrict__ reqs) {
+  wait_prior_grid();
   constexpr int n = R1 * R2, nh = (n + 1) / 2, LBP = pair_lbp<D, R2>(), LB = 2 * LBP;
   constexpr int NL = D * LBP, items1 = NL * R2;
   if (reqs != nullptr) {
@@ -665,6 +670,7 @@ __global__ void __launch_bounds__(pair_line_threads<D, R2>(), 4)
 k_pair_line_inv(const cpx<T>* S, Fields<T> f, const cpx<T>* __restrict__ twg, long long nlines,
                 long long scs, MatView<T> mat, Scalars* sc, OpArgs args, double* partials,
                 unsigned* counter, int negate, FastDiv fdn, const ReqDesc<T>* __restrict__ reqs) {
+  wait_prior_grid();
   constexpr int n = R1 * R2, nh = (n + 1) / 2, LBP = pair_lbp<D, R2>(), LB = 2 * LBP;
   constexpr int NL = D * LBP, items1 = NL * R2;
   if (reqs != nullptr) {

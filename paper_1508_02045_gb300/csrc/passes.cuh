@@ -298,6 +298,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_cg_alpha(const double* partials, int nblocks, long long count, Scalars* sc,
            const ReqDesc<T>* __restrict__ reqs) {
+  wait_prior_grid();
   __shared__ double red[kThreads / 32];
   if (reqs != nullptr) {
     partials = reqs[blockIdx.z].partials;
@@ -427,6 +428,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
 k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
            int ncomp, long long nlines, int LB, LineDiv ld, long long scs, MatView<T> mat,
            Scalars* sc, OpArgs args, double* partials, const ReqDesc<T>* __restrict__ reqs) {
+  wait_prior_grid();
   if (reqs != nullptr) {
     const ReqDesc<T>& R = reqs[blockIdx.z];
     f = R.ff;
@@ -478,6 +480,7 @@ __global__ void __launch_bounds__(kColThreads<T>, 2)
 k_strided(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, long long C, long long es,
           long long bs, int TC, int TCp, int inv, const Scalars* sc,
           const ReqDesc<T>* __restrict__ reqs) {
+  wait_prior_grid();
   if (reqs != nullptr) {
     S = reqs[blockIdx.z].S;
     sc = reqs[blockIdx.z].sc;
@@ -615,6 +618,7 @@ template <typename T, int D, int NC, int MODE>
 __global__ void __launch_bounds__(kColThreads<T>, 2)
 k_proj(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC,
        int TCp, const Scalars* sc, const ReqDesc<T>* __restrict__ reqs) {
+  wait_prior_grid();
   if (reqs != nullptr) {
     S = reqs[blockIdx.z].S;
     sc = reqs[blockIdx.z].sc;
@@ -713,6 +717,7 @@ template <typename T>
 __global__ void __launch_bounds__(kColThreads<T>, 2)
 k_proj_scalar(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC,
               int TCp, const Scalars* sc, const ReqDesc<T>* __restrict__ reqs) {
+  wait_prior_grid();
   if (reqs != nullptr) {
     S = reqs[blockIdx.z].S;
     sc = reqs[blockIdx.z].sc;
@@ -1015,6 +1020,7 @@ k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ 
            int ncomp, long long nlines, int LB, LineDiv ld, long long scs, MatView<T> mat,
            Scalars* sc, OpArgs args, double* partials, unsigned* counter, int negate,
            const ReqDesc<T>* __restrict__ reqs) {
+  wait_prior_grid();
   if (reqs != nullptr) {
     const ReqDesc<T>& R = reqs[blockIdx.z];
     f = R.fi;
