@@ -366,6 +366,18 @@ def pass_bytes(word=8, two_line=False, fused_cg=False):
     return out
 
 
+def pot_bytes(word=4):
+    """Compulsory DRAM bytes of one launch of each pass of the CG step in potential coordinates
+    (the FP32 inner solver): u, r, p are one complex component on the half spectrum (c bytes
+    each); pot_inv reads r, p and writes p and two spectrum lines; the axis-1 passes move two
+    and three lines; pot_line reads and writes three lines and reads the phase image; pot_fwd
+    reads two lines and u, p, r and writes u, r."""
+    n = N_GRID[0]
+    nh = (n + 1) // 2
+    c = n * n * nh * 2 * word
+    return {"pot_inv": 5 * c, "strided": 5 * c, "pot_line": 6 * c + n ** 3, "pot_fwd": 7 * c}
+
+
 # ------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------
@@ -389,6 +401,11 @@ def _run_ours(args, rank, world, local):
         N_GRID = (args.grid,) * 3
 
     torch.cuda.set_device(local)
+    if args.quick and args.precision == "elastic":  # profiling helper: the elasticity step alone
+        line = elastic_step(args.steps, args.warmup, N_GRID[0])
+        if rank == 0:
+            print(json.dumps({"quick": True, "precision": "elastic", **line}), flush=True)
+        return None
     ph, table = workload()
     fp32_only = args.quick and args.precision == "fp32"
     prob = H.Problem(D, N_GRID, H.phase_material(ph, table),
@@ -400,7 +417,7 @@ def _run_ours(args, rank, world, local):
     stream = torch.cuda.current_stream()
     total = args.warmup + args.steps
     if fp32_only:  # the FP32 inner CG step of the refinement (profiling helper)
-        opts = H.make_opts(maxit=2, inner_tol=1e-30)
+        opts = H.make_opts(maxit=2, inner_tol=1e-30, inner_form=args.inner_form)
         H.hom_solve_begin(prob.h, E_MACRO, H.HOM_CG, 1e-30, opts)
     else:
         opts = H.make_opts(fixed_iters=total + 1)
@@ -437,23 +454,38 @@ def _run_ours(args, rank, world, local):
                               "passes": passes, "gpu_launches": int(launches)}), flush=True)
         return None
 
-    # ---- the same CG step in FP32 (the inner solver of HOM_FP32_REFINED), HBM-bound ----
+    # ---- the same CG step in FP32 (the inner solver of HOM_FP32_REFINED): in potential
+    # coordinates (the default inner form of refined CG) and in the field form ----
     p32 = H.Problem(D, N_GRID, H.phase_material(ph, table), precision=H.HOM_FP32_REFINED)
     tune32 = H.hom_autotune(p32.h, reps=2)
-    H.hom_solve_begin(p32.h, E_MACRO, H.HOM_CG, 1e-30, H.make_opts(maxit=2, inner_tol=1e-30))
-    H.hom_solve_iterate(p32.h, args.warmup)
-    torch.cuda.synchronize()
-    H.hom_profile_enable(True)
-    f0 = torch.cuda.Event(enable_timing=True)
-    f1 = torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    H.hom_solve_iterate(p32.h, args.steps)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    H.hom_profile_enable(False)
-    passes32 = H.hom_profile_read()
-    ms_step32 = f0.elapsed_time(f1) / args.steps
-    H.hom_solve_end(p32.h, D, allow_not_converged=True)
+    fp32_forms = {}
+    for form in (0, 1):
+        H.hom_solve_begin(p32.h, E_MACRO, H.HOM_CG, 1e-30,
+                          H.make_opts(maxit=2, inner_tol=1e-30, inner_form=form))
+        H.hom_solve_iterate(p32.h, args.warmup)
+        torch.cuda.synchronize()
+        H.hom_profile_enable(True)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        H.hom_solve_iterate(p32.h, args.steps)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        H.hom_profile_enable(False)
+        fp32_forms[form] = (f0.elapsed_time(f1) / args.steps, H.hom_profile_read())
+        H.hom_solve_end(p32.h, D, allow_not_converged=True)
+    # a refined CG solve of the same problem to 1e-8 in either inner form (outside the timed
+    # region): in potential coordinates the FP32 iterates stay exact gradients
+    refined_solves = {}
+    for form, name in ((0, "potential"), (1, "field")):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        AHr, _, str_, _ = H.hom_solve(p32.h, E_MACRO, H.HOM_CG, 1e-8,
+                                      H.make_opts(maxit=50, inner_form=form))
+        torch.cuda.synchronize()
+        refined_solves[name] = {"seconds": round(time.perf_counter() - t0, 4), "A_H": AHr,
+                                "outer": str_["iterations"], "inner": str_["inner_iterations"],
+                                "converged": bool(str_["converged"])}
     p32.close()
 
     # ---- end to end through the C ABI: every step hom_apply reads the field from pinned host
@@ -539,10 +571,21 @@ def _run_ours(args, rank, world, local):
     peak = fp64_peak["dfma_tflops"]  # measured on this GPU before the timed region
     # compulsory bytes of one step: per kind, bytes per launch x launches per step (measured)
     step_bytes = sum(byts[k] * pk[k]["launches"] / args.steps for k in pk if k in byts)
-    pk32 = per_kind(passes32)
-    dom32 = max((k for k in pk32 if k in byts32), key=lambda k: pk32[k]["ms_avg"] * pk32[k]["launches"])
-    ach32 = byts32[dom32] / (pk32[dom32]["ms_avg"] * 1e-3) / 1e9
-    step_bytes32 = sum(byts32[k] * pk32[k]["launches"] / args.steps for k in pk32 if k in byts32)
+    fp32 = {}
+    for form, bb in ((0, pot_bytes(4)), (1, byts32)):
+        ms32, pr32 = fp32_forms[form]
+        pk32 = per_kind(pr32)
+        dom32 = max((k for k in pk32 if k in bb), key=lambda k: pk32[k]["ms_avg"] * pk32[k]["launches"])
+        ach32 = bb[dom32] / (pk32[dom32]["ms_avg"] * 1e-3) / 1e9
+        sb32 = sum(bb[k] * pk32[k]["launches"] / args.steps for k in pk32 if k in bb)
+        fp32[form] = {"value": round(1000.0 / ms32, 3), "unit": UNIT, "ms_per_step": round(ms32, 4),
+                      "step_bytes": int(sb32), "hbm_gbs": round(sb32 / (ms32 * 1e-3) / 1e9, 1),
+                      "roofline": {"bound": "hbm", "kernel": f"k_{dom32}", "achieved": round(ach32, 1),
+                                   "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                   "frac": round(ach32 / peaks["hbm_gbs"], 4),
+                                   "traffic": ncu_traffic("fp32", dom32),
+                                   "peak_source": peaks["source"]},
+                      "passes": pk32}
     value = world * 1000.0 / ms_step
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
@@ -572,17 +615,13 @@ def _run_ours(args, rank, world, local):
                      "fp64_probe": fp64_peak,
                      "hbm_gbs_of_dominant": round(byts[dom] / (dom_ms * 1e-3) / 1e9, 1)},
         "passes": pk,
-        "fp32_step": {"metric": "G·A matvecs/s at 243^3 (FP32 CG step, inner solver of the refinement)",
-                      "value": round(1000.0 / ms_step32, 3), "unit": UNIT, "ms_per_step": round(ms_step32, 4),
-                      "hbm_gbs": round(step_bytes32 / (ms_step32 * 1e-3) / 1e9, 1),
+        "fp32_step": {"metric": "G·A matvecs/s at 243^3 (FP32 CG step, inner solver of the refinement, "
+                                "in potential coordinates)",
+                      **fp32[0],
                       "plan": {"rmax": tune32["rmax32"], "smem_kb": tune32["smem_kb32"],
                                "two_line": bool(tune32.get("two_line32"))},
-                      "roofline": {"bound": "hbm", "kernel": f"k_{dom32}", "achieved": round(ach32, 1),
-                                   "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                                   "frac": round(ach32 / peaks["hbm_gbs"], 4),
-                                   "traffic": ncu_traffic("fp32", dom32),
-                                   "peak_source": peaks["source"]},
-                      "passes": pk32},
+                      "field_form": fp32[1],
+                      "refined_cg_to_1e-8": refined_solves},
         "clocks": clk,
         "cufft_comparison": {
             "what": "G A x with torch.fft (cuFFT rfftn/irfftn) + elementwise torch ops, same grid "
@@ -1045,8 +1084,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--grid", type=int, default=0)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
-                    help="with --quick: time the FP64 CG step or the FP32 inner CG step")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "elastic"],
+                    help="with --quick: time the FP64 CG step, the FP32 inner CG step or the "
+                         "elasticity CG step")
     ap.add_argument("--serve", type=int, default=0, help="run the served mix with this many requests")
     ap.add_argument("--serve-window", type=float, default=1.0)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
@@ -1055,6 +1095,8 @@ def main():
     ap.add_argument("--no-c4", action="store_true", help="skip the 405^3 refinement check")
     ap.add_argument("--no-elastic", action="store_true", help="skip the elasticity step")
     ap.add_argument("--no-kappa", action="store_true", help="skip the reduced contrast study")
+    ap.add_argument("--inner-form", type=int, default=0, choices=[0, 1],
+                    help="--quick --precision fp32: 0 potential coordinates, 1 field form")
     ap.add_argument("--no-tune", action="store_true",
                     help="with --quick: keep the default launch plan (profiler captures)")
     ap.add_argument("--configs", action="store_true", help="run configurations 1-4 end to end")

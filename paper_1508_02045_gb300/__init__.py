@@ -39,7 +39,8 @@ EXPORTED = ["hom_create", "hom_grid", "hom_bounds", "hom_apply", "hom_solve", "h
             "hom_server_poll", "hom_server_status", "hom_server_destroy", "hom_autotune",
             "hom_solve_history", "hom_solve_current", "hom_solve_nonconformity", "hom_restrict",
             "hom_measure_fp64", "hom_debug_fail_alloc", "hom_set_plan"]
-PASS_KINDS = ["line_fwd", "strided", "proj", "line_inv", "vector"]
+PASS_KINDS = ["line_fwd", "strided", "proj", "line_inv", "vector", "pot_inv", "pot_line",
+              "pot_fwd"]
 
 
 class hom_material(ctypes.Structure):
@@ -52,7 +53,8 @@ class hom_material(ctypes.Structure):
 class hom_opts(ctypes.Structure):
     _fields_ = [("maxit", ctypes.c_int), ("fixed_iters", ctypes.c_int), ("stop", ctypes.c_int),
                 ("cA", ctypes.c_double), ("CA", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("check_every", ctypes.c_int), ("out_flags", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("out_flags", ctypes.c_int),
+                ("inner_form", ctypes.c_int)]
 
 
 class hom_stats(ctypes.Structure):
@@ -520,11 +522,11 @@ def fourier_material(Ahat: np.ndarray, cA, CA, M=None):
 
 
 def make_opts(maxit=0, fixed_iters=0, stop=HOM_STOP_DEFAULT, cA=0.0, CA=0.0, inner_tol=0.0,
-              check_every=0, out_flags=0):
+              check_every=0, out_flags=0, inner_form=0):
     o = hom_opts()
     o.maxit, o.fixed_iters, o.stop = maxit, fixed_iters, stop
     o.cA, o.CA, o.inner_tol, o.check_every = cA, CA, inner_tol, check_every
-    o.out_flags = out_flags
+    o.out_flags, o.inner_form = out_flags, inner_form
     return o
 
 

@@ -117,6 +117,20 @@ enum PostOp { POST_STORE = 0, POST_RICH = 1, POST_CG = 2, POST_CHEB = 3, POST_EM
 enum ProjMode { PROJ_GAMMA = 0, PROJ_EM = 1 };
 enum MatKind { MAT_PHASE_ISO = 0, MAT_PHASE_TENSOR = 1, MAT_FIELD = 2 };
 
+// Conjugate gradients in potential coordinates (pcg_pot.cuh): the step's vectors u (iterate),
+// r (residual), p (direction), complex half spectra in the layout of one spectrum component,
+// and the modes of its two axis-0 kernels
+template <typename T>
+struct PotVecs {
+  cpx<T>* u;
+  cpx<T>* r;
+  cpx<T>* p;
+};
+enum PotInvMode { POT_STEP = 0 /* p = z + beta p, lines of s = i p */,
+                  POT_FIELD = 1 /* lines of s = i u (x = D u, no update) */ };
+enum PotFwdMode { POT_UPDATE = 0 /* u += alpha p, r -= alpha q */,
+                  POT_INIT = 1 /* r = q (the right-hand side D* r_field), u = p = 0 */ };
+
 // Coefficient view used by the pre/post operators, in the working precision T.
 template <typename T>
 struct MatView {

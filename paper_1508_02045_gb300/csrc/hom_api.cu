@@ -968,6 +968,13 @@ void enqueue_step(hom_problem* P) {
 namespace hom {
 namespace detail {
 
+// the vectors of the FP32 inner CG in potential coordinates: u, r, p in fvec[0..2] (each
+// holds the one-component half spectrum, at most half of its d |N| floats)
+PotVecs<float> pot_vecs(hom_problem* P) {
+  return PotVecs<float>{(cpx<float>*)P->fvec[0], (cpx<float>*)P->fvec[1],
+                        (cpx<float>*)P->fvec[2]};
+}
+
 // r = b - C x = -G A (E + x) in FP64 into vec[2]; returns ||r|| (host synchronises)
 int refine_residual(hom_problem* P, double* res) {
   SolveState& S_ = P->sv;
@@ -1002,6 +1009,14 @@ int refine_start_inner(hom_problem* P) {
   }
   int rc = upload_scalars(P, P->d_sc2, s);
   if (rc) return rc;
+  if (S_.pot) {
+    // r = D* r_field in potential coordinates (from the FP32 rounding of the FP64 residual)
+    const long long n3 = (long long)P->nc * P->nodes;
+    Ops<float>::convert_in(P->vec[2], P->fvec[3], n3, P->stream);
+    P->e32.pot_init(P->fvec[3], pot_vecs(P), (cpx<float>*)P->S, P->d_sc2, P->partials,
+                    P->counter, P->stream);
+    return check_last();
+  }
   const long long len = (long long)P->nc * P->nodes;
   Ops<float>::demote(P->vec[2], P->fvec[1], P->fvec[2], P->fvec[0], len, P->nodes, P->d_sc2,
                      P->partials, P->counter, P->red_grid, P->stream);
@@ -1020,6 +1035,11 @@ int refine_start_inner(hom_problem* P) {
 }
 
 void refine_enqueue_inner(hom_problem* P) {
+  if (P->sv.pot) {
+    P->e32.pot_step(pot_vecs(P), (cpx<float>*)P->S, P->d_sc2, P->partials, P->counter,
+                    P->stream);
+    return;
+  }
   const long long nodes = P->nodes;
   cpx<float>* S = (cpx<float>*)P->S;
   float* x = P->fvec[0];
@@ -1057,8 +1077,14 @@ int refine_outer_update(hom_problem* P) {
   if (rc) return rc;
   S_.inner_total += P->h_sc->it;
   // x += G d: the FP32 correction carries round-off outside the conforming space E (Section
-  // 4.4); C does not see that part but the energy does, so it is projected out in FP64
-  Ops<float>::convert_out(P->fvec[0], P->vec[4], len, P->stream);
+  // 4.4); C does not see that part but the energy does, so it is projected out in FP64. In
+  // potential coordinates d = D u is formed first (into fvec[3]).
+  const float* dfield = P->fvec[0];
+  if (S_.pot) {
+    P->e32.pot_field(pot_vecs(P), (cpx<float>*)P->S, P->fvec[3], P->stream);
+    dfield = P->fvec[3];
+  }
+  Ops<float>::convert_out(dfield, P->vec[4], len, P->stream);
   Fields<double> f{};
   f.xin = P->vec[4];
   f.x = P->vec[0];
@@ -1139,6 +1165,7 @@ static int solve_begin_impl(hom_problem* P, const double* E, int solver, double 
     S_.tol = tol;
     S_.inner_tol = o.inner_tol > 0 ? o.inner_tol : 1e-4;
     S_.maxit = o.maxit > 0 ? o.maxit : 50;
+    S_.pot = solver == HOM_CG && o.inner_form == 0 && P->e32.pot_ok();
     return refine_begin(P);
   }
 

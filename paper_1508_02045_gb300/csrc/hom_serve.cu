@@ -76,6 +76,12 @@ ReqDesc<float> desc32(hom_problem* P) {
   float* rr = P->fvec[1];
   float* p = P->fvec[2];
   float* q = P->fvec[3];
+  if (P->sv.pot) {  // CG in potential coordinates: u, r, p as one-component half spectra
+    r.fi.x = x;
+    r.fi.r = rr;
+    r.fi.p = p;
+    return r;
+  }
   if (P->sv.solver == HOM_CG) {
     r.ff.xin = rr;
     r.ff.p = p;
@@ -105,7 +111,11 @@ ReqDesc<T> idle_desc(Scalars* idle) {
 // the FP32 inner step). Geometry from the engine of a representative problem.
 template <typename T>
 void batch_step(const Engine<T>& E, int solver, const ReqDesc<T>* reqs, int n, int red_grid,
-                long long nodes, int d, cudaStream_t st) {
+                long long nodes, int d, cudaStream_t st, bool pot = false) {
+  if (pot) {  // the FP32 inner CG in potential coordinates (buffers from the descriptors)
+    E.pot_step(PotVecs<T>{}, nullptr, nullptr, nullptr, nullptr, st, reqs, n);
+    return;
+  }
   switch (solver) {
     case HOM_RICHARDSON:
       E.apply_batch(PRE_AFFINE, PROJ_GAMMA, POST_RICH, reqs, n, st);
@@ -141,6 +151,7 @@ struct hom_batch {
   ReqDesc<float>* d32 = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  bool pot = false;  // refined CG members run their inner solves in potential coordinates
 };
 
 namespace {
@@ -161,7 +172,8 @@ int batch_capture(hom_batch* B, int steps) {
   }
   for (int k = 0; k < steps; ++k) {
     if (B->refined)
-      batch_step<float>(P0->e32, B->solver, B->d32, n, P0->red_grid, P0->nodes, P0->d, B->stream);
+      batch_step<float>(P0->e32, B->solver, B->d32, n, P0->red_grid, P0->nodes, P0->d, B->stream,
+                        B->pot);
     else
       batch_step<double>(P0->e64, B->solver, B->d64, n, P0->red_grid, P0->nodes, P0->d, B->stream);
   }
@@ -189,7 +201,7 @@ extern "C" int hom_batch_create(hom_problem* const* problems, int count, hom_bat
     hom_problem* P = problems[i];
     if (!P || !P->sv.active || P->sv.solver != P0->sv.solver || P->d != P0->d ||
         P->precision != P0->precision || P->integration != P0->integration ||
-        P->stream != P0->stream || P->device != P0->device)
+        P->stream != P0->stream || P->device != P0->device || P->sv.pot != P0->sv.pot)
       return HOM_ERR_INVALID;
     for (int a = 0; a < P->d; ++a)
       if (P->M[a] != P0->M[a] || P->N[a] != P0->N[a]) return HOM_ERR_INVALID;
@@ -198,6 +210,7 @@ extern "C" int hom_batch_create(hom_problem* const* problems, int count, hom_bat
   B->m.assign(problems, problems + count);
   B->solver = P0->sv.solver;
   B->refined = P0->sv.refined;
+  B->pot = P0->sv.pot;
   B->stream = P0->stream;
   if (B->refined) {
     std::vector<ReqDesc<float>> h;
@@ -238,14 +251,16 @@ extern "C" int hom_batch_iterate(hom_batch* B, int iterations, int use_graph, in
     }
     for (; done_steps < iterations; ++done_steps) {
       if (B->refined)
-        batch_step<float>(P0->e32, B->solver, B->d32, n, P0->red_grid, P0->nodes, P0->d, B->stream);
+        batch_step<float>(P0->e32, B->solver, B->d32, n, P0->red_grid, P0->nodes, P0->d, B->stream,
+                        B->pot);
       else
         batch_step<double>(P0->e64, B->solver, B->d64, n, P0->red_grid, P0->nodes, P0->d, B->stream);
     }
   } else {
     for (int k = 0; k < iterations; ++k) {
       if (B->refined)
-        batch_step<float>(P0->e32, B->solver, B->d32, n, P0->red_grid, P0->nodes, P0->d, B->stream);
+        batch_step<float>(P0->e32, B->solver, B->d32, n, P0->red_grid, P0->nodes, P0->d, B->stream,
+                        B->pot);
       else
         batch_step<double>(P0->e64, B->solver, B->d64, n, P0->red_grid, P0->nodes, P0->d, B->stream);
     }
@@ -321,6 +336,8 @@ struct Bucket {
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
   cudaStream_t stream = nullptr;  // the bucket's own stream: buckets overlap on the device
+  int inner_form = 0;             // hom_opts.inner_form of its requests
+  bool pot = false;               // their FP32 inner CG runs in potential coordinates
 };
 
 void bucket_release(Bucket& b) {
@@ -354,6 +371,7 @@ int bucket_init(Bucket& b, const hom_request& r, const int* M, int cap) {
   b.integration = r.integration;
   b.precision = r.precision;
   b.solver = r.solver;
+  b.inner_form = r.opts.inner_form;
   b.cap = cap;
   b.slots.assign(b.cap, nullptr);
   b.nodes = 1;
@@ -424,7 +442,7 @@ int find_bucket(hom_server* S, const hom_request& r, const int* M) {
   for (size_t i = 0; i < S->buckets.size(); ++i) {
     const Bucket& b = S->buckets[i];
     bool same = b.d == r.d && b.integration == r.integration && b.precision == r.precision &&
-                b.solver == r.solver;
+                b.solver == r.solver && b.inner_form == r.opts.inner_form;
     for (int a = 0; a < r.d && same; ++a) same = b.M[a] == M[a] && b.N[a] == r.N[a];
     if (same) return (int)i;
   }
@@ -458,7 +476,7 @@ int bucket_upload(hom_server* S, Bucket& b) {
 
 void bucket_step(Bucket& b) {
   if (b.precision == HOM_FP32_REFINED)
-    batch_step<float>(*b.e32, b.solver, b.d32, b.cap, b.red_grid, b.nodes, b.d, b.stream);
+    batch_step<float>(*b.e32, b.solver, b.d32, b.cap, b.red_grid, b.nodes, b.d, b.stream, b.pot);
   else
     batch_step<double>(*b.e64, b.solver, b.d64, b.cap, b.red_grid, b.nodes, b.d, b.stream);
 }
@@ -546,6 +564,7 @@ int admit(hom_server* S) {
     r->P = P;
     r->t_admit = Clock::now();
     S->in_use += r->bytes;
+    b.pot = P->sv.pot;  // equal for every request of the bucket (same grid, solver, form)
     const int slot = (int)(std::find(b.slots.begin(), b.slots.end(), nullptr) - b.slots.begin());
     b.slots[slot] = r;
     r->bucket = bi;

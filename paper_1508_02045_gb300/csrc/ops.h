@@ -76,6 +76,9 @@ struct Ops {
                        int negate, cudaStream_t st, const ReqDesc<T>* reqs = nullptr,
                        int nreq = 1);
   // ncomp: components of x (the coefficient acts on ncomp-vectors)
+  // alpha = (r, r) / (p, A p) from the nb per-CTA partials of (p, A p) (one CTA per request)
+  static void cg_alpha(const double* partials, int nb, long long count, Scalars* sc,
+                       cudaStream_t st, const ReqDesc<T>* reqs = nullptr, int nreq = 1);
   static void energy(int ncomp, const T* x, long long nodes, const MatView<T>& mat, Scalars* sc,
                      double* partials, unsigned* counter, int grid, cudaStream_t st);
   static void fill_const(T* x, long long nodes, int d, const Scalars* sc, cudaStream_t st);
@@ -126,6 +129,21 @@ void pair_line_inv_f32(int D, int post, const AxisPlan& P, const cpx<float>* S,
                        double* partials, unsigned* counter, int negate, cudaStream_t st,
                        const ReqDesc<float>* reqs, int nreq);
 
+// Conjugate gradients in potential coordinates for the FP32 inner solves (pcg_pot.cuh), on
+// 3-D grids whose three axes have specialised two-stage plans: the axis-0 inverse with the
+// direction update (mode POT_STEP) or of the iterate (POT_FIELD), the fused line pass (returns
+// its CTA count, the partials of (p, K p)), and the axis-0 forward with the vector update
+// (POT_UPDATE) or the right-hand side (POT_INIT)
+void pot_inv_f32(int mode, const AxisPlan& P, cpx<float>* S, const cpx<float>* tw,
+                 const ProjGeom& pg, const PotVecs<float>& V, const Scalars* sc, cudaStream_t st,
+                 const ReqDesc<float>* reqs, int nreq);
+void pot_fwd_f32(int mode, const AxisPlan& P, const cpx<float>* S, const cpx<float>* tw,
+                 const ProjGeom& pg, const PotVecs<float>& V, Scalars* sc, double* partials,
+                 unsigned* counter, cudaStream_t st, const ReqDesc<float>* reqs, int nreq);
+int pot_line_f32(const AxisPlan& P, cpx<float>* S, const cpx<float>* tw, long long nlines,
+                 long long scs, const MatView<float>& mat, Scalars* sc, double* partials,
+                 cudaStream_t st, const ReqDesc<float>* reqs, int nreq);
+
 long long& launch_counter();
 int dynamic_smem_cap();
 
@@ -151,7 +169,8 @@ inline void launch_pass(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t 
 
 // Optional per-pass event timing (hom_profile_enable): kinds of launches
 enum PassKind { KIND_LINE_FWD = 0, KIND_STRIDED = 1, KIND_PROJ = 2, KIND_LINE_INV = 3,
-                KIND_VECTOR = 4, KIND_COUNT = 5 };
+                KIND_VECTOR = 4, KIND_POT_INV = 5, KIND_POT_LINE = 6, KIND_POT_FWD = 7,
+                KIND_COUNT = 8 };
 bool profiling();
 void prof_mark(int kind, cudaStream_t st, bool start);
 

@@ -419,6 +419,14 @@ void Ops<T>::line_inv(const PassGeom& g, int post, const cpx<T>* S, const Fields
 }
 
 template <typename T>
+void Ops<T>::cg_alpha(const double* partials, int nb, long long count, Scalars* sc,
+                      cudaStream_t st, const ReqDesc<T>* reqs, int nreq) {
+  launch_pass(k_cg_alpha<T>, dim3(1, 1, (unsigned)nreq), kThreads, 0, st, partials, nb, count, sc,
+              reqs);
+  ++launch_counter();
+}
+
+template <typename T>
 void Ops<T>::energy(int ncomp, const T* x, long long nodes, const MatView<T>& mat, Scalars* sc,
                     double* partials, unsigned* counter, int grid, cudaStream_t st) {
   if (ncomp == 2) k_energy<T, 2><<<grid, kThreads, 0, st>>>(x, nodes, mat, sc, partials, counter);

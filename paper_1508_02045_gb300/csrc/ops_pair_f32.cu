@@ -4,6 +4,7 @@
 
 #include "ops.h"
 #include "pair_fft.cuh"
+#include "pcg_pot.cuh"
 
 namespace hom {
 
@@ -48,7 +49,82 @@ cudaError_t pair_prepare_f32(int cap) {
   HOM_SET_SMEM((k_pair_line_inv<T, 3, POST_STORE, R1_, R2_>));
   HOM_PAIR_PLANS(HOM_PAIR_SMEM)
 #undef HOM_PAIR_SMEM
+#define HOM_POT_SMEM(R1_, R2_)                                  \
+  HOM_SET_SMEM((k_pot_inv<T, R1_, R2_, POT_STEP>));             \
+  HOM_SET_SMEM((k_pot_inv<T, R1_, R2_, POT_FIELD>));            \
+  HOM_SET_SMEM((k_pot_fwd<T, R1_, R2_, POT_UPDATE>));           \
+  HOM_SET_SMEM((k_pot_fwd<T, R1_, R2_, POT_INIT>));             \
+  HOM_SET_SMEM((k_pot_line<T, 3, R1_, R2_>));
+  HOM_PAIR_PLANS(HOM_POT_SMEM)
+#undef HOM_POT_SMEM
   return cudaSuccess;
+}
+
+// ---- conjugate gradients in potential coordinates (pcg_pot.cuh) ----
+void pot_inv_f32(int mode, const AxisPlan& P, cpx<float>* S, const cpx<float>* tw,
+                 const ProjGeom& pg, const PotVecs<float>& V, const Scalars* sc, cudaStream_t st,
+                 const ReqDesc<float>* reqs, int nreq) {
+  using T = float;
+  const bool prof = profiling();
+#define HOM_POT_INV(R1_, R2_)                                                                  \
+  if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
+    constexpr int TC = pot_tc_inv<R2_>();                                             \
+    const dim3 grid((unsigned)((pg.C + TC - 1) / TC), 1, (unsigned)nreq);                     \
+    const size_t sm = sizeof(cpx<T>) * ((size_t)(R1_ * R2_) * (1 + 2 * (TC + 1)));             \
+    if (prof) prof_mark(KIND_POT_INV, st, true);                                               \
+    if (mode == POT_FIELD)                                                                     \
+      launch_pass(k_pot_inv<T, R1_, R2_, POT_FIELD>, grid, 2 * TC * R2_, sm, st, S, tw, pg, V, sc, reqs); \
+    else                                                                                       \
+      launch_pass(k_pot_inv<T, R1_, R2_, POT_STEP>, grid, 2 * TC * R2_, sm, st, S, tw, pg, V, sc, reqs); \
+    if (prof) prof_mark(KIND_POT_INV, st, false);                                              \
+    return;                                                                                    \
+  }
+  HOM_PAIR_PLANS(HOM_POT_INV)
+#undef HOM_POT_INV
+}
+
+void pot_fwd_f32(int mode, const AxisPlan& P, const cpx<float>* S, const cpx<float>* tw,
+                 const ProjGeom& pg, const PotVecs<float>& V, Scalars* sc, double* partials,
+                 unsigned* counter, cudaStream_t st, const ReqDesc<float>* reqs, int nreq) {
+  using T = float;
+  const bool prof = profiling();
+#define HOM_POT_FWD(R1_, R2_)                                                                  \
+  if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
+    constexpr int TC = pot_tc_fwd<R2_>();                                             \
+    const dim3 grid((unsigned)((pg.C + TC - 1) / TC), 1, (unsigned)nreq);                     \
+    const size_t sm = sizeof(cpx<T>) * ((size_t)(R1_ * R2_) * (1 + 2 * (TC + 1)));             \
+    if (prof) prof_mark(KIND_POT_FWD, st, true);                                               \
+    if (mode == POT_INIT)                                                                      \
+      launch_pass(k_pot_fwd<T, R1_, R2_, POT_INIT>, grid, pot_fwd_threads<R2_>(), sm, st, S, tw, pg, V, sc, partials, counter, reqs); \
+    else                                                                                       \
+      launch_pass(k_pot_fwd<T, R1_, R2_, POT_UPDATE>, grid, pot_fwd_threads<R2_>(), sm, st, S, tw, pg, V, sc, partials, counter, reqs); \
+    if (prof) prof_mark(KIND_POT_FWD, st, false);                                              \
+    return;                                                                                    \
+  }
+  HOM_PAIR_PLANS(HOM_POT_FWD)
+#undef HOM_POT_FWD
+}
+
+int pot_line_f32(const AxisPlan& P, cpx<float>* S, const cpx<float>* tw, long long nlines,
+                 long long scs, const MatView<float>& mat, Scalars* sc, double* partials,
+                 cudaStream_t st, const ReqDesc<float>* reqs, int nreq) {
+  using T = float;
+  const bool prof = profiling();
+#define HOM_POT_LINE(R1_, R2_)                                                                 \
+  if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
+    constexpr int LB = 2 * pair_lbp<3, R2_>();                                                 \
+    const dim3 grid((unsigned)((nlines + LB - 1) / LB), 1, (unsigned)nreq);                   \
+    const size_t sm = PairFwdSmem<3, R1_, R2_>::bytes;                                         \
+    constexpr int NT = pair_line_threads<3, R2_>();                                            \
+    if (prof) prof_mark(KIND_POT_LINE, st, true);                                              \
+    launch_pass(k_pot_line<T, 3, R1_, R2_>, grid, NT, sm, st, S, tw, nlines, scs, mat, sc,       \
+                partials, reqs);                                                               \
+    if (prof) prof_mark(KIND_POT_LINE, st, false);                                             \
+    return (int)grid.x;                                                                        \
+  }
+  HOM_PAIR_PLANS(HOM_POT_LINE)
+#undef HOM_POT_LINE
+  return 0;
 }
 
 // Shared memory requested by a strided CTA of 128 threads or more: 39424 bytes a CTA with the

@@ -36,14 +36,14 @@ constexpr int kColThreads = kThreads;
 // ---------------------------------------------------------------------------------------
 // deterministic block reduction + last-block finisher
 // ---------------------------------------------------------------------------------------
-template <int NV>
+template <int NV, int MAXW = kThreads / 32>
 __device__ bool reduce_and_last(double (&acc)[NV], double* partials, unsigned* counter,
                                 double (&tot)[NV]) {
-  __shared__ double red[NV][kThreads / 32];
+  __shared__ double red[NV][MAXW];
   __shared__ double fin[NV];
   __shared__ int am_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = (int)(blockDim.x >> 5);  // blocks are whole warps, at most kThreads threads
+  const int nw = (int)(blockDim.x >> 5);  // blocks are whole warps, at most MAXW of them
   const int nblocks = gridDim.x * gridDim.y;
   const int bid = blockIdx.y * gridDim.x + blockIdx.x;
 #pragma unroll

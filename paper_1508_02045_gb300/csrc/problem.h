@@ -204,6 +204,59 @@ struct Engine {
                      counter, negate, st);
   }
 
+  // Conjugate gradients in potential coordinates (pcg_pot.cuh) for the FP32 inner solves:
+  // available for 3-D vector fields with specialised two-stage plans on all three axes
+  bool pot_ok() const {
+    if constexpr (sizeof(T) == 4)
+      return g.D == 3 && g.NC == 3 && Ops<T>::two_line_ok(g, plan[0], plan[1]) &&
+             pair_plan_f32(plan[2]);
+    return false;
+  }
+  // the right-hand side D* x of a real field x in potential coordinates (r), u = p = 0 and
+  // (r, M^{-1} r) into sc (nb, rr)
+  void pot_init(const T* x, const PotVecs<T>& V, cpx<T>* S, Scalars* sc, double* partials,
+                unsigned* counter, cudaStream_t st) const {
+    if constexpr (sizeof(T) == 4) {
+      Fields<T> f{};
+      f.xin = x;
+      f.cs = g.nodes;
+      OpArgs args{};
+      Ops<T>::line_fwd(g, PRE_IDENT, f, S, plan[2], tw[2], 3, mat, nullptr, args, st);
+      Ops<T>::strided_two_line(g, 0, S, plan[1], tw[1], nullptr, st);
+      pot_fwd_f32(POT_INIT, plan[0], S, tw[0], pg, V, sc, partials, counter, st, nullptr, 1);
+      ++launch_counter();
+    }
+  }
+  // one CG step in potential coordinates (several requests with reqs / n)
+  void pot_step(const PotVecs<T>& V, cpx<T>* S, Scalars* sc, double* partials, unsigned* counter,
+                cudaStream_t st, const ReqDesc<T>* reqs = nullptr, int n = 1) const {
+    if constexpr (sizeof(T) == 4) {
+      pot_inv_f32(POT_STEP, plan[0], S, tw[0], pg, V, sc, st, reqs, n);
+      Ops<T>::strided_two_line(g, 1, S, plan[1], tw[1], sc, st, reqs, n);
+      const int nb = pot_line_f32(plan[2], S, tw[2], g.nlines, g.scs, mat, sc, partials, st,
+                                  reqs, n);
+      ++launch_counter();
+      Ops<T>::cg_alpha(partials, nb, g.nodes, sc, st, reqs, n);
+      Ops<T>::strided_two_line(g, 0, S, plan[1], tw[1], sc, st, reqs, n);
+      pot_fwd_f32(POT_UPDATE, plan[0], S, tw[0], pg, V, sc, partials, counter, st, reqs, n);
+      launch_counter() += 2;
+    }
+  }
+  // the field x = D u of the iterate (three real components into out)
+  void pot_field(const PotVecs<T>& V, cpx<T>* S, T* out, cudaStream_t st) const {
+    if constexpr (sizeof(T) == 4) {
+      pot_inv_f32(POT_FIELD, plan[0], S, tw[0], pg, V, nullptr, st, nullptr, 1);
+      ++launch_counter();
+      Ops<T>::strided_two_line(g, 1, S, plan[1], tw[1], nullptr, st);
+      Fields<T> f{};
+      f.out = out;
+      f.cs = g.nodes;
+      OpArgs args{};
+      Ops<T>::line_inv(g, POST_STORE, S, f, plan[2], tw[2], 3, mat, nullptr, args, nullptr,
+                       nullptr, 0, st);
+    }
+  }
+
   // one batched application over the requests of `reqs` (device array of n descriptors that
   // supply buffers, coefficients, scalars and partials); geometry and plans are shared
   void apply_batch(int pre, int mode, int post, const ReqDesc<T>* reqs, int n,
@@ -296,6 +349,7 @@ struct SolveState {
   bool converged = false;
   float inner_ms = 0;
   int out_flags = 0;  // hom_opts.out_flags of the session
+  bool pot = false;   // the FP32 inner CG runs in potential coordinates (pcg_pot.cuh)
 };
 
 struct hom_problem {
