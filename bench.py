@@ -369,13 +369,13 @@ def pass_bytes(word=8, two_line=False, fused_cg=False):
 def pot_bytes(word=4):
     """Compulsory DRAM bytes of one launch of each pass of the CG step in potential coordinates
     (the FP32 inner solver): u, r, p are one complex component on the half spectrum (c bytes
-    each); pot_inv reads r, p and writes p and two spectrum lines; the axis-1 passes move two
-    and three lines; pot_line reads and writes three lines and reads the phase image; pot_fwd
-    reads two lines and u, p, r and writes u, r."""
+    each); pot_inv reads r, p, u and writes p, u (the deferred u += alpha p) and two spectrum
+    lines; the axis-1 passes move two and three lines; pot_line reads and writes three lines
+    and reads the phase image; pot_fwd reads two lines and r and writes r."""
     n = N_GRID[0]
     nh = (n + 1) // 2
     c = n * n * nh * 2 * word
-    return {"pot_inv": 5 * c, "strided": 5 * c, "pot_line": 6 * c + n ** 3, "pot_fwd": 7 * c}
+    return {"pot_inv": 7 * c, "strided": 5 * c, "pot_line": 6 * c + n ** 3, "pot_fwd": 4 * c}
 
 
 # ------------------------------------------------------------------------------------------

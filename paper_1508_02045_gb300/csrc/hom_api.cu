@@ -1081,7 +1081,7 @@ int refine_outer_update(hom_problem* P) {
   // potential coordinates d = D u is formed first (into fvec[3]).
   const float* dfield = P->fvec[0];
   if (S_.pot) {
-    P->e32.pot_field(pot_vecs(P), (cpx<float>*)P->S, P->fvec[3], P->stream);
+    P->e32.pot_field(pot_vecs(P), (cpx<float>*)P->S, P->d_sc2, P->fvec[3], P->stream);
     dfield = P->fvec[3];
   }
   Ops<float>::convert_out(dfield, P->vec[4], len, P->stream);

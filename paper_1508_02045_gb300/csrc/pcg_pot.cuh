@@ -8,14 +8,17 @@
 // b = D z_0, (p, C p) in field form is (D p, A D p). The potential's vectors are one complex
 // component on the half spectrum instead of d real components, and the passes of one step
 // are the two-line chain of the scalar projection taken in the other order:
-//   k_pot_inv  : p = z + beta p (the direction update of Algorithm 2), then the inverse axis-0
-//                transforms of k_0 s and s with s = i p (component 0, component 1)
+//   k_pot_inv  : u += alpha p (the previous step's iterate update, deferred to where p is
+//                read anyway), p = z + beta p (the direction update of Algorithm 2), then the
+//                inverse axis-0 transforms of k_0 s and s with s = i p (components 0 and 1)
 //   strided    : inverse axis 1, two lines -> three components (k_pair_strided + strided2)
 //   k_pot_line : inverse axis 2, v = A w and the partial of (w, A w) = (p, K p), forward axis 2
 //   (k_cg_alpha: alpha = (r, z) / (p, K p))
 //   strided    : forward axis 1, three components -> X_0 and Y = k_1 X_1 + k_2 X_2
-//   k_pot_fwd  : forward axis 0, q = K p = -i (k_0 X_0 + Y) / |N|, u += alpha p,
-//                r -= alpha q, z = r / |k|^2 and (r, z) (the last CTA: beta, the stopping test)
+//   k_pot_fwd  : forward axis 0, q = K p = -i (k_0 X_0 + Y) / |N|, r -= alpha q,
+//                z = r / |k|^2 and (r, z) (the last CTA: beta, the stopping test)
+// After a step the stored u lacks that step's alpha p; the field of the iterate (POT_FIELD)
+// adds it as it reads u.
 // Inner products over the half spectrum count k_2 > 0 twice (Hermitian symmetry of real fields).
 // With exact integration (Section 2.3) the solve grid is the double grid and Gamma^ keeps only
 // the frequencies of Z_N: the preconditioner is zero outside Z_N, so z, the directions and the
@@ -44,9 +47,9 @@ __device__ __forceinline__ void pot_prefetch_l2(const void* p, long long bytes) 
     asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
 }
 
-// columns per tile of the two axis-0 kernels (2 TC R2 threads a CTA): the forward kernel, whose
-// vector loads follow its transforms, runs narrower tiles and more CTAs a SM (243 points:
-// 0.125 ms with 8 columns against 0.141 ms with 16 on a GB300)
+// columns per tile of the two axis-0 kernels (2 TC R2 threads a CTA): the forward kernel runs
+// narrower tiles and more CTAs a SM (243 points on a GB300: 0.097 ms with 8 columns against
+// 0.100 ms with 16)
 template <int R2>
 __host__ __device__ constexpr int pot_tc_inv() {
   return pair_tc_proj_scalar<R2>();
@@ -77,9 +80,10 @@ __device__ __forceinline__ float pot_zw(int k0, int kk12c, int hw0) {
   return (kk12c >= 0 && abs(k0) <= hw0) ? pot_inv_kk(k0 * k0 + kk12c) : 0.0f;
 }
 
-// axis-0 inverse of the potential step: per column tile, the direction update p = z + beta p
-// (z = r / |k|^2; in POT_FIELD mode v = u), s = i v staged in shared memory, then the inverse
-// axis-0 transforms of k_0 s and s into spectrum components 0 and 1; 2 TC R2 threads
+// axis-0 inverse of the potential step: per column tile, the deferred update u += alpha p and
+// the direction update p = z + beta p (z = r / |k|^2; in POT_FIELD mode v = u + alpha p, nothing
+// stored), s = i v staged in shared memory, then the inverse axis-0 transforms of k_0 s and s
+// into spectrum components 0 and 1; 2 TC R2 threads
 template <typename T, int R1, int R2, int MODE>
 __global__ void __launch_bounds__(2 * pot_tc_inv<R2>() * R2)
 k_pot_inv(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, PotVecs<T> V,
@@ -97,7 +101,7 @@ k_pot_inv(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, PotVecs<T> V,
     V.r = reinterpret_cast<cpx<T>*>(R.fi.r);
     V.p = reinterpret_cast<cpx<T>*>(R.fi.p);
   }
-  if (MODE == POT_STEP && sc != nullptr && sc->done) return;
+  if (MODE == POT_STEP && sc->done) return;
   cpx<T>* sm = smem_c<T>();
   cpx<T>* tw = sm;
   cpx<T>* A = sm + n;
@@ -108,38 +112,42 @@ k_pot_inv(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, PotVecs<T> V,
   const long long es = g.C;
   pot_tile_cols<TC>(g, c0, ncols, kk12, hwc);
   __syncthreads();
-  const T beta = (MODE == POT_STEP && sc != nullptr) ? (T)sc->beta : (T)0;
+  // the previous step's u update, u += alpha p, is applied here (and in POT_FIELD mode to the
+  // value read), where p is loaded anyway: alpha and p are still those of that step
+  const T beta = MODE == POT_STEP ? (T)sc->beta : (T)0;
+  const T alpha = (T)sc->alpha;
   const cpx<T>* __restrict__ rg = V.r;
-  const cpx<T>* __restrict__ ug = V.u;
+  cpx<T>* __restrict__ ug = V.u;
   cpx<T>* __restrict__ pg = V.p;
   for (int e0 = threadIdx.x; e0 < n * TC; e0 += kPotU * NT) {
-    cpx<T> a[kPotU], b[kPotU];
+    cpx<T> rr[kPotU], pp[kPotU], uu[kPotU];
 #pragma unroll
     for (int q = 0; q < kPotU; ++q) {
       const int e = e0 + q * NT, j = e / TC, c = e % TC;
-      a[q] = cpx<T>{0, 0};
-      b[q] = cpx<T>{0, 0};
+      rr[q] = pp[q] = uu[q] = cpx<T>{0, 0};
       if (e < n * TC && c < ncols) {
         const long long ge = (long long)j * es + c0 + c;
-        if (MODE == POT_FIELD) {
-          a[q] = ug[ge];
-        } else {
-          a[q] = rg[ge];
-          b[q] = pg[ge];
-        }
+        uu[q] = ug[ge];
+        pp[q] = pg[ge];
+        if (MODE == POT_STEP) rr[q] = rg[ge];
       }
     }
 #pragma unroll
     for (int q = 0; q < kPotU; ++q) {
       const int e = e0 + q * NT, j = e / TC, c = e % TC;
       if (e >= n * TC) continue;
-      cpx<T> v = a[q];
+      const cpx<T> un = {fma(alpha, pp[q].x, uu[q].x), fma(alpha, pp[q].y, uu[q].y)};
+      cpx<T> v = un;
       if (MODE == POT_STEP) {
         const int k0 = (j <= (n - 1) / 2) ? j : j - n;
         const T w = (T)pot_zw(k0, kk12[c], g.hw[0]);
-        v.x = fma(beta, b[q].x, a[q].x * w);
-        v.y = fma(beta, b[q].y, a[q].y * w);
-        if (c < ncols) pg[(long long)j * es + c0 + c] = v;
+        v.x = fma(beta, pp[q].x, rr[q].x * w);
+        v.y = fma(beta, pp[q].y, rr[q].y * w);
+        if (c < ncols) {
+          const long long ge = (long long)j * es + c0 + c;
+          pg[ge] = v;
+          ug[ge] = un;
+        }
       }
       stage[j * TCp + c] = cpx<T>{-v.y, v.x};
     }
@@ -180,7 +188,7 @@ k_pot_inv(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, PotVecs<T> V,
 
 // axis-0 forward of the potential step: per column tile, the forward axis-0 transforms of X_0
 // (component 0) and Y (component 1), stage 2 in place in the tile, then element by element
-// q = -i (k_0 X_0 + Y) / |N| = K p (or D* of the field in POT_INIT mode), the vector updates,
+// q = -i (k_0 X_0 + Y) / |N| = K p (or D* of the field in POT_INIT mode), r -= alpha q,
 // z = r / |k|^2 and the partial of (r, z); the last CTA completes the step (beta and the
 // stopping test of Algorithm 2 on sqrt((r, z))). The block is rounded up to whole warps for
 // the reduction; the threads past 2 TC R2 take no line in stage 1.
@@ -240,18 +248,13 @@ k_pot_fwd(const cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, PotVecs<T
   cpx<T>* __restrict__ pg = V.p;
   DotAcc<T> dacc;
   for (int e0 = threadIdx.x; e0 < n * TC; e0 += kPotU * NTW) {
-    cpx<T> uu[kPotU], pp[kPotU], rr[kPotU];
+    cpx<T> rr[kPotU];
     if (MODE == POT_UPDATE) {
 #pragma unroll
       for (int q = 0; q < kPotU; ++q) {
         const int e = e0 + q * NTW, j = e / TC, c = e % TC;
-        uu[q] = pp[q] = rr[q] = cpx<T>{0, 0};
-        if (e < n * TC && c < ncols) {
-          const long long ge = (long long)j * es + c0 + c;
-          uu[q] = ug[ge];
-          pp[q] = pg[ge];
-          rr[q] = rg[ge];
-        }
+        rr[q] = cpx<T>{0, 0};
+        if (e < n * TC && c < ncols) rr[q] = rg[(long long)j * es + c0 + c];
       }
     }
 #pragma unroll
@@ -271,7 +274,6 @@ k_pot_fwd(const cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, PotVecs<T
         ug[ge] = cpx<T>{0, 0};
         pg[ge] = cpx<T>{0, 0};
       } else {
-        ug[ge] = cpx<T>{fma(alpha, pp[q].x, uu[q].x), fma(alpha, pp[q].y, uu[q].y)};
         rn = cpx<T>{fma(-alpha, kq.x, rr[q].x), fma(-alpha, kq.y, rr[q].y)};
       }
       rg[ge] = rn;
@@ -380,48 +382,92 @@ k_pot_line(cpx<T>* S, const cpx<T>* __restrict__ twg, long long nlines, long lon
     for (int r = 0; r < R1; ++r) line[i * R1 + r] = u[r];
   }
   __syncthreads();
-  for (int w = threadIdx.x; w < NL * R1; w += blockDim.x) {
-    const int i = w % R1;
-    cpx<T>* line = lines + (w / R1) * n;
-    cpx<T> u[R2];
-    pair_stage2_regs<T, R1, R2>(line, tw, 1, i, u);
-#pragma unroll
-    for (int r = 0; r < R2; ++r) line[i + r * R1] = cpx<T>{u[r].x, -u[r].y};
-  }
-  __syncthreads();
-  // v = A w at every node of the tile: node j of line 2q (real part) or 2q + 1 (imaginary
-  // part) of the packed lines (a, q); rows past the grid's end hold zeros and stay zero
   DotAcc<T> dacc;
-  constexpr int KM = 4;  // material samples a thread has in flight
-  for (int base = threadIdx.x; base < LB * n; base += KM * blockDim.x) {
-    T smp[KM];
+  if constexpr (R2 <= 9) {
+    // inverse stage 2 of the three components of a line pair, and on the nodes it produces
+    // v = A w with the partial of (w, v): item (q, i) owns rows i + r R1 of the packed lines
+    // (a, q) of every component (real part: line 2q, imaginary part: line 2q + 1) and writes v
+    // back where it read; nodes past the grid's end hold zeros and stay zero
+    for (int w = threadIdx.x; w < LBP * R1; w += blockDim.x) {
+      const int i = w % R1, q = w / R1;
+      cpx<T> u[D][R2];
 #pragma unroll
-    for (int k = 0; k < KM; ++k) {
-      const int idx = base + k * blockDim.x;
-      smp[k] = idx < nvalid ? mat_fetch<T>(mat, g0 + idx) : (T)0;
-    }
+      for (int a = 0; a < D; ++a)
+        pair_stage2_regs<T, R1, R2>(lines + (a * LBP + q) * n, tw, 1, i, u[a]);
 #pragma unroll
-    for (int k = 0; k < KM; ++k) {
-      const int idx = base + k * blockDim.x;
-      if (idx >= nvalid) continue;
-      const int ll = idx / n, j = idx - ll * n, q = ll >> 1, odd = ll & 1;
-      T w[D], v[D];
+      for (int r = 0; r < R2; ++r) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int idx = (2 * q + h) * n + i + r * R1;
+          T wv[D], v[D];
+#pragma unroll
+          for (int a = 0; a < D; ++a) wv[a] = h ? -u[a][r].y : u[a][r].x;  // conjugated output
+          if (idx < nvalid) {
+            mat_eval<T, D>(mat, mat_fetch<T>(mat, g0 + idx), wv, v);
+#pragma unroll
+            for (int a = 0; a < D; ++a) dacc.add(wv[a], v[a]);
+          } else {
+#pragma unroll
+            for (int a = 0; a < D; ++a) v[a] = (T)0;
+          }
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            if (h) u[a][r].y = v[a];
+            else u[a][r].x = v[a];
+          }
+        }
+      }
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        const cpx<T> z = lines[(a * LBP + q) * n + j];
-        w[a] = odd ? z.y : z.x;
-      }
-      mat_eval<T, D>(mat, smp[k], w, v);
+        cpx<T>* line = lines + (a * LBP + q) * n;
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        dacc.add(w[a], v[a]);
-        cpx<T>& z = lines[(a * LBP + q) * n + j];
-        if (odd) z.y = v[a];
-        else z.x = v[a];
+        for (int r = 0; r < R2; ++r) line[i + r * R1] = u[a][r];
       }
     }
+    __syncthreads();
+  } else {
+    // wider second stages (R2 > 9) hold too many registers for the fused form: stage 2 of
+    // every line, then the material product node by node
+    for (int w = threadIdx.x; w < NL * R1; w += blockDim.x) {
+      const int i = w % R1;
+      cpx<T>* line = lines + (w / R1) * n;
+      cpx<T> u[R2];
+      pair_stage2_regs<T, R1, R2>(line, tw, 1, i, u);
+#pragma unroll
+      for (int r = 0; r < R2; ++r) line[i + r * R1] = cpx<T>{u[r].x, -u[r].y};
+    }
+    __syncthreads();
+    constexpr int KM = 4;  // material samples a thread has in flight
+    for (int base = threadIdx.x; base < LB * n; base += KM * blockDim.x) {
+      T smp[KM];
+#pragma unroll
+      for (int k = 0; k < KM; ++k) {
+        const int idx = base + k * blockDim.x;
+        smp[k] = idx < nvalid ? mat_fetch<T>(mat, g0 + idx) : (T)0;
+      }
+#pragma unroll
+      for (int k = 0; k < KM; ++k) {
+        const int idx = base + k * blockDim.x;
+        if (idx >= nvalid) continue;
+        const int ll = idx / n, j = idx - ll * n, q = ll >> 1, odd = ll & 1;
+        T w[D], v[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const cpx<T> z = lines[(a * LBP + q) * n + j];
+          w[a] = odd ? z.y : z.x;
+        }
+        mat_eval<T, D>(mat, smp[k], w, v);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          dacc.add(w[a], v[a]);
+          cpx<T>& z = lines[(a * LBP + q) * n + j];
+          if (odd) z.y = v[a];
+          else z.x = v[a];
+        }
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
   // forward stage 1 on the packed lines, in place: all loads, a barrier, all stores
   {
     const int t = threadIdx.x;

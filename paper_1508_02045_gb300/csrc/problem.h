@@ -242,10 +242,12 @@ struct Engine {
       launch_counter() += 2;
     }
   }
-  // the field x = D u of the iterate (three real components into out)
-  void pot_field(const PotVecs<T>& V, cpx<T>* S, T* out, cudaStream_t st) const {
+  // the field x = D u of the iterate (three real components into out); sc holds the last
+  // step's alpha, whose update of u the kernels defer
+  void pot_field(const PotVecs<T>& V, cpx<T>* S, const Scalars* sc, T* out,
+                 cudaStream_t st) const {
     if constexpr (sizeof(T) == 4) {
-      pot_inv_f32(POT_FIELD, plan[0], S, tw[0], pg, V, nullptr, st, nullptr, 1);
+      pot_inv_f32(POT_FIELD, plan[0], S, tw[0], pg, V, sc, st, nullptr, 1);
       ++launch_counter();
       Ops<T>::strided_two_line(g, 1, S, plan[1], tw[1], nullptr, st);
       Fields<T> f{};
