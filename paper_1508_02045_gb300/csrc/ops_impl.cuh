@@ -101,7 +101,8 @@ bool Ops<T>::plan_geometry(int D, const int* n, const AxisPlan* plan, size_t bud
   // the column kernels address the NC component tiles with 32-bit offsets
   if ((long long)NC * g->scs >= (1LL << 31)) return false;
   const size_t cap = (size_t)dynamic_smem_cap();
-  return smem_line(nl, NC, g->LB) <= cap && smem_proj(n[0], NC, g->TC0p, plan[0].nst) <= cap &&
+  return smem_line(nl, NC, g->LB) <= cap &&
+         (NC != D || smem_proj(n[0], NC, g->TC0p, plan[0].nst) <= cap) &&
          smem_proj_scalar(n[0], g->TCqp) <= cap &&
          (D != 3 || smem_strided(n[1], g->TC1p, plan[1].nst) <= cap) &&
          smem_strided(n[0], g->TCs0p, plan[0].nst) <= cap;
@@ -161,11 +162,7 @@ cudaError_t Ops<T>::prepare(int) {
     return pair_prepare_f32(cap);
   } else {
     // elasticity (FP64): strain fields of 3 (2-D, the 3-component line kernels above) or 6
-    // components, and their projection passes
-    HOM_SET_SMEM((k_proj<T, 2, 3, PROJ_GAMMA>));
-    HOM_SET_SMEM((k_proj<T, 2, 3, PROJ_EM>));
-    HOM_SET_SMEM((k_proj<T, 3, 6, PROJ_GAMMA>));
-    HOM_SET_SMEM((k_proj<T, 3, 6, PROJ_EM>));
+    // components (their projection pass is two strided passes around k_proj_point)
     HOM_SET_SMEM((k_line_fwd<T, 6, PRE_CG>));
     HOM_SET_SMEM((k_line_inv<T, 6, POST_CG>));
     HOM_SET_SMEM((k_line_fwd<T, 6, PRE_AFFINE>));
@@ -295,18 +292,28 @@ void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, con
   }
   if (g.NC != g.D) {  // symmetric strain fields (elasticity, FP64 only)
     if constexpr (sizeof(T) == 8) {
-      const dim3 grid((unsigned)((pg.C + g.TC0 - 1) / g.TC0), 1, (unsigned)nreq);
-      const size_t sm = smem_proj(P.n, g.NC, g.TC0p, P.nst);
-#define HOM_PJE(D_, NC_, M_) launch_pass(k_proj<T, D_, NC_, M_>, grid, g.NT0, sm, st, S, P, tw, pg, g.TC0, g.TC0p, sc, reqs)
+      // the axis-0 transforms of the NC components as column passes (one CTA per component
+      // tile, the tile shared memory of the strided pass), the strain projection node by node
+      // between them: a one-kernel pass would hold all NC component tiles of its columns in
+      // shared memory and run one CTA per SM
+      const long long C = g.scs / g.n[0];
+      const dim3 gs((unsigned)((C + g.TCs0 - 1) / g.TCs0), (unsigned)g.NC, (unsigned)nreq);
+      const size_t sms = smem_strided(P.n, g.TCs0p, P.nst);
+      launch_pass(k_strided<T>, gs, g.NTs0, sms, st, S, P, tw, C, C, g.scs, g.TCs0, g.TCs0p, 0,
+                  sc, reqs);
+      const dim3 gp((unsigned)((pg.C + kThreads - 1) / kThreads), (unsigned)P.n, (unsigned)nreq);
+#define HOM_PJE(D_, NC_, M_) launch_pass(k_proj_point<T, D_, NC_, M_>, gp, kThreads, 0, st, S, pg, P.n, (T)g.nodes, sc, reqs)
       if (g.D == 2) {
         if (mode == PROJ_EM) HOM_PJE(2, 3, PROJ_EM); else HOM_PJE(2, 3, PROJ_GAMMA);
       } else {
         if (mode == PROJ_EM) HOM_PJE(3, 6, PROJ_EM); else HOM_PJE(3, 6, PROJ_GAMMA);
       }
 #undef HOM_PJE
+      launch_pass(k_strided<T>, gs, g.NTs0, sms, st, S, P, tw, C, C, g.scs, g.TCs0, g.TCs0p, 1,
+                  sc, reqs);
     }
     if (prof) prof_mark(KIND_PROJ, st, false);
-    ++launch_counter();
+    launch_counter() += 3;
     return;
   }
   if (g.D == 3 && mode == PROJ_GAMMA) {

@@ -540,7 +540,8 @@ __host__ __device__ constexpr int mandel_j(int m) {
 // c1 = scale / |k|^2 (0 at k = 0 and outside the support); MODE PROJ_EM gives scale v - 2 Gamma^ v.
 template <typename T, int D, int NC, int MODE>
 __device__ __forceinline__ void proj_point(const int (&k)[3], T c1, int kk, T scale,
-                                           const cpx<T> (&v)[NC], cpx<T> (&o)[NC]) {
+                                           const cpx<T> (&v)[NC], cpx<T> (&o)[NC],
+                                           T nodes = (T)0) {
   if (NC == D) {
     cpx<T> kv = {0, 0};
 #pragma unroll
@@ -563,7 +564,8 @@ __device__ __forceinline__ void proj_point(const int (&k)[3], T c1, int kk, T sc
   } else {
     const T r2 = (T)0.70710678118654752440;  // 1 / sqrt 2
     const T s2 = (T)1.41421356237309504880;  // sqrt 2
-    const T c2 = kk > 0 ? c1 / (T)kk : (T)0;
+    // c2 = scale / |k|^4 = c1^2 |N| (c1 = scale / |k|^2, scale = 1 / |N|): no division
+    const T c2 = nodes > (T)0 ? c1 * c1 * nodes : (kk > 0 ? c1 / (T)kk : (T)0);
     // q = e k
     cpx<T> q[D];
 #pragma unroll
@@ -588,13 +590,18 @@ __device__ __forceinline__ void proj_point(const int (&k)[3], T c1, int kk, T sc
       kek.x = fma((T)k[i], q[i].x, kek.x);
       kek.y = fma((T)k[i], q[i].y, kek.y);
     }
+    // Gamma^ e = k (x) Q + Q (x) k - S k (x) k with Q = c1 q and S = c2 (k . e . k)
+    cpx<T> Q[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) Q[i] = cpx<T>{q[i].x * c1, q[i].y * c1};
+    const cpx<T> Sk = {kek.x * c2, kek.y * c2};
 #pragma unroll
     for (int m = 0; m < NC; ++m) {
       const int i = mandel_i<D>(m), j = mandel_j<D>(m);
-      const T kij = (T)(k[i] * k[j]);
+      const T ki = (T)k[i], kj = (T)k[j], mkij = (T)(-k[i] * k[j]);
       cpx<T> g;
-      g.x = ((T)k[i] * q[j].x + q[i].x * (T)k[j]) * c1 - kij * kek.x * c2;
-      g.y = ((T)k[i] * q[j].y + q[i].y * (T)k[j]) * c1 - kij * kek.y * c2;
+      g.x = fma(mkij, Sk.x, fma(ki, Q[j].x, Q[i].x * kj));
+      g.y = fma(mkij, Sk.y, fma(ki, Q[j].y, Q[i].y * kj));
       if (i != j) {
         g.x *= s2;
         g.y *= s2;
@@ -711,6 +718,46 @@ __device__ __forceinline__ void column_freqs(const ProjGeom& g, long long cc, in
   const int i1 = fdiv((int)cc, g.fdnh);
   *kc1 = (i1 <= (g.n1 - 1) / 2) ? i1 : i1 - g.n1;
   *kc2 = (int)cc - i1 * g.nh;
+}
+
+// Gamma^ (or I - 2 Gamma^ for PROJ_EM) node by node on a spectrum already transformed along all
+// axes (the strain projection of elasticity, between the forward and the inverse axis-0 column
+// passes): blockIdx.y = row j of axis 0, x over the columns, blockIdx.z = request
+template <typename T, int D, int NC, int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_proj_point(cpx<T>* S, ProjGeom g, int n0, T nodes, const Scalars* sc,
+             const ReqDesc<T>* __restrict__ reqs) {
+  wait_prior_grid();
+  if (reqs != nullptr) {
+    S = reqs[blockIdx.z].S;
+    sc = reqs[blockIdx.z].sc;
+  }
+  if (sc != nullptr && sc->done) return;
+  const long long cc = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cc >= g.C) return;
+  const int j = blockIdx.y;
+  int k[3] = {(j <= (n0 - 1) / 2) ? j : j - n0, 0, 0};
+  if (D == 3) {
+    column_freqs(g, cc, &k[1], &k[2]);
+  } else {
+    k[1] = (int)cc;
+  }
+  bool inside = true;
+  int kk = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    inside = inside && (abs(k[a]) <= g.hw[a]);
+    kk += k[a] * k[a];
+  }
+  const T scale = (T)g.scale;
+  const T coef = (kk > 0 && inside) ? inv_kk<T>(g, scale, kk) : (T)0;
+  cpx<T>* p = S + (long long)j * g.C + cc;
+  cpx<T> v[NC], o[NC];
+#pragma unroll
+  for (int a = 0; a < NC; ++a) v[a] = p[(long long)a * g.cs];
+  proj_point<T, D, NC, MODE>(k, coef, kk, scale, v, o, nodes);
+#pragma unroll
+  for (int a = 0; a < NC; ++a) p[(long long)a * g.cs] = o[a];
 }
 
 template <typename T>
