@@ -694,65 +694,79 @@ REFINED_SOLVER = {"richardson": "cg", "cg": "cg", "chebyshev": "chebyshev",
                   "eyre_milton": "chebyshev"}
 
 
+def serve_arm(reqs, mats, arrivals, prec, budget_gb, rich_maxit):
+    """Serve `reqs` through hom_server with the given arrival times (seconds from the start), in
+    plain FP64 with the drawn solvers or FP32-refined; per-request latency, throughput from the
+    first arrival to the last completion, converged and non-converged requests, A_H."""
+    import torch
+    import paper_1508_02045_gb300 as H
+
+    S = H.hom_server_create(int(budget_gb * (1 << 30)), max_batch=8)
+    submitted, results = {}, {}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nxt = 0
+    steps = 0
+    while len(results) < len(reqs):
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and arrivals[nxt] <= now:
+            r = reqs[nxt]
+            if prec == H.HOM_FP64:
+                solver = r["solver"]
+                maxit = rich_maxit if solver == "richardson" else 20000
+            else:
+                solver = REFINED_SOLVER[r["solver"]]
+                maxit = 50
+            q = H.make_request(3, (r["n"],) * 3, mats[nxt], r["E"], H.SOLVERS[solver], 1e-6,
+                               precision=prec, opts=H.make_opts(maxit=maxit))
+            submitted[H.hom_server_submit(S, q)] = nxt
+            nxt += 1
+        active, queued, _ = H.hom_server_status(S)
+        if active == 0 and queued == 0:
+            if nxt < len(reqs):
+                time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+            continue
+        H.hom_server_step(S, 8)
+        steps += 1
+        for res in H.hom_server_poll(S):
+            results[submitted[res["id"]]] = res
+    wall = time.perf_counter() - t0
+    H.hom_server_destroy(S)
+    lat = np.array([results[i]["latency_ms"] for i in range(len(reqs))])
+    conv = [bool(results[i]["stats"]["converged"]) for i in range(len(reqs))]
+    by_solver = {}
+    for i, r in enumerate(reqs):
+        sv = r["solver"] if prec == H.HOM_FP64 else REFINED_SOLVER[r["solver"]]
+        e = by_solver.setdefault(sv, {"requests": 0, "converged": 0})
+        e["requests"] += 1
+        e["converged"] += int(conv[i])
+    return {"solves_per_s": round(len(reqs) / (wall - arrivals[0]), 3),
+            "p50_ms": round(float(np.percentile(lat, 50)), 1),
+            "p99_ms": round(float(np.percentile(lat, 99)), 1),
+            "wall_s": round(wall, 2), "steps": steps,
+            "converged": int(sum(conv)), "not_converged": int(len(conv) - sum(conv)),
+            "by_solver": by_solver,
+            "AH": [results[i]["AH_EE"] for i in range(len(reqs))], "conv": conv}
+
+
+SERVE_WORKLOAD = ("served mix: grids {45,81,135,243}^3, RSA spheres vf 0.1-0.4, radii 0.02-0.06 "
+                  "(>= 1.5 nodes), contrast logU[10,1e4], anisotropic SPD phases, solver uniform "
+                  "over the four (FP64 arm; the refined arm runs CG for CG/Richardson and "
+                  "Chebyshev for Chebyshev/Eyre-Milton), tol 1e-6")
+
+
 def served_mix(n_req, window, budget_gb, rich_maxit, seed=2024):
     """Serve the seeded mix through hom_server (Poisson arrivals over `window` seconds), once
     in plain FP64 with the drawn solvers and once FP32-refined; solves/s, p50/p99 latency,
     converged and non-converged requests, and the A_H agreement of the two arms."""
-    import torch
     import paper_1508_02045_gb300 as H
 
     reqs = served_requests(n_req, seed)
     rng = np.random.default_rng(seed + 7)
     arrivals = np.cumsum(rng.exponential(window / len(reqs), size=len(reqs)))
-    out = {}
-    for label, prec in (("fp64", H.HOM_FP64), ("fp32_refined", H.HOM_FP32_REFINED)):
-        S = H.hom_server_create(int(budget_gb * (1 << 30)), max_batch=8)
-        mats = [H.phase_material(r["phase"], r["table"]) for r in reqs]
-        submitted, results = {}, {}
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        nxt = 0
-        steps = 0
-        while len(results) < len(reqs):
-            now = time.perf_counter() - t0
-            while nxt < len(reqs) and arrivals[nxt] <= now:
-                r = reqs[nxt]
-                if prec == H.HOM_FP64:
-                    solver = r["solver"]
-                    maxit = rich_maxit if solver == "richardson" else 20000
-                else:
-                    solver = REFINED_SOLVER[r["solver"]]
-                    maxit = 50
-                q = H.make_request(3, (r["n"],) * 3, mats[nxt], r["E"], H.SOLVERS[solver], 1e-6,
-                                   precision=prec, opts=H.make_opts(maxit=maxit))
-                submitted[H.hom_server_submit(S, q)] = nxt
-                nxt += 1
-            active, queued, _ = H.hom_server_status(S)
-            if active == 0 and queued == 0:
-                if nxt < len(reqs):
-                    time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
-                continue
-            H.hom_server_step(S, 8)
-            steps += 1
-            for res in H.hom_server_poll(S):
-                results[submitted[res["id"]]] = res
-        wall = time.perf_counter() - t0
-        H.hom_server_destroy(S)
-        lat = np.array([results[i]["latency_ms"] for i in range(len(reqs))])
-        conv = [bool(results[i]["stats"]["converged"]) for i in range(len(reqs))]
-        by_solver = {}
-        for i, r in enumerate(reqs):
-            sv = r["solver"] if prec == H.HOM_FP64 else REFINED_SOLVER[r["solver"]]
-            e = by_solver.setdefault(sv, {"requests": 0, "converged": 0})
-            e["requests"] += 1
-            e["converged"] += int(conv[i])
-        out[label] = {"solves_per_s": round(len(reqs) / (wall - arrivals[0]), 3),
-                      "p50_ms": round(float(np.percentile(lat, 50)), 1),
-                      "p99_ms": round(float(np.percentile(lat, 99)), 1),
-                      "wall_s": round(wall, 2), "steps": steps,
-                      "converged": int(sum(conv)), "not_converged": int(len(conv) - sum(conv)),
-                      "by_solver": by_solver,
-                      "AH": [results[i]["AH_EE"] for i in range(len(reqs))], "conv": conv}
+    mats = [H.phase_material(r["phase"], r["table"]) for r in reqs]
+    out = {label: serve_arm(reqs, mats, arrivals, prec, budget_gb, rich_maxit)
+           for label, prec in (("fp64", H.HOM_FP64), ("fp32_refined", H.HOM_FP32_REFINED))}
     a64 = np.array(out["fp64"].pop("AH"))
     a32 = np.array(out["fp32_refined"].pop("AH"))
     c64 = out["fp64"].pop("conv")
@@ -763,11 +777,7 @@ def served_mix(n_req, window, budget_gb, rich_maxit, seed=2024):
             "value": out["fp32_refined"]["solves_per_s"], "unit": "solves/s",
             "higher_is_better": True, "n_gpus": 1, "dtype": "f32 inner / f64 outer",
             "data": "synthetic (seeded random-sphere microstructures)",
-            "config": {"workload": "served mix: grids {45,81,135,243}^3, RSA spheres vf 0.1-0.4, "
-                                   "radii 0.02-0.06 (>= 1.5 nodes), contrast logU[10,1e4], "
-                                   "anisotropic SPD phases, solver uniform over the four (FP64 "
-                                   "arm; the refined arm runs CG for CG/Richardson and Chebyshev "
-                                   "for Chebyshev/Eyre-Milton), tol 1e-6",
+            "config": {"workload": SERVE_WORKLOAD,
                        "requests": len(reqs), "arrival_window_s": window,
                        "hbm_budget_gb": budget_gb, "max_batch": 8,
                        "richardson_maxit": rich_maxit,
@@ -777,6 +787,42 @@ def served_mix(n_req, window, budget_gb, rich_maxit, seed=2024):
             "speedup_vs_fp64": round(out["fp32_refined"]["solves_per_s"] / out["fp64"]["solves_per_s"], 2),
             "AH_max_rel_diff_fp32_refined_vs_fp64": diff,
             "AH_compared_requests": len(both)}
+
+
+def serve_load(n_req, factors, budget_gb, rich_maxit, seed=2024):
+    """The served mix at fixed offered loads: each arm's capacity is measured with every request
+    queued at t = 0, then the FP32-refined arm serves the same requests with Poisson arrivals at
+    factor x its capacity (seeded); throughput, p50 and p99 per load."""
+    import paper_1508_02045_gb300 as H
+
+    reqs = served_requests(n_req, seed)
+    mats = [H.phase_material(r["phase"], r["table"]) for r in reqs]
+    at_once = np.zeros(len(reqs))
+    cap = {}
+    ah = {}
+    for label, prec in (("fp32_refined", H.HOM_FP32_REFINED), ("fp64", H.HOM_FP64)):
+        res = serve_arm(reqs, mats, at_once, prec, budget_gb, rich_maxit)
+        ah[label] = (np.array(res.pop("AH")), res.pop("conv"))
+        cap[label] = res
+    both = [i for i in range(len(reqs)) if ah["fp64"][1][i] and ah["fp32_refined"][1][i]]
+    diff = (float(np.max(np.abs(ah["fp32_refined"][0][both] - ah["fp64"][0][both])
+                         / np.abs(ah["fp64"][0][both]))) if both else None)
+    c = cap["fp32_refined"]["solves_per_s"]
+    rows = []
+    for k, f in enumerate(factors):
+        rng = np.random.default_rng(seed + 100 + k)
+        arrivals = np.cumsum(rng.exponential(1.0 / (f * c), size=len(reqs)))
+        res = serve_arm(reqs, mats, arrivals, H.HOM_FP32_REFINED, budget_gb, rich_maxit)
+        res.pop("AH"), res.pop("conv")
+        rows.append({"load": f, "offered_per_s": round(f * c, 3), **res})
+    return {"metric": "served solves/s at offered loads (FP32 inner + FP64 refinement)",
+            "unit": "solves/s", "n_gpus": 1, "data": "synthetic (seeded random-sphere microstructures)",
+            "config": {"workload": SERVE_WORKLOAD, "requests": len(reqs), "hbm_budget_gb": budget_gb,
+                       "max_batch": 8, "richardson_maxit": rich_maxit,
+                       "grid_counts": {str(g): int(sum(r["n"] == g for r in reqs)) for g in (45, 81, 135, 243)}},
+            "capacity": cap, "capacity_speedup_vs_fp64": round(c / cap["fp64"]["solves_per_s"], 2),
+            "AH_max_rel_diff_fp32_refined_vs_fp64": diff, "AH_compared_requests": len(both),
+            "loads": rows}
 
 
 def elastic_step(steps, warmup, n=243):
@@ -826,6 +872,10 @@ def elastic_stiffness(lam, mu):
 
 
 def run_served(args):
+    if args.serve_load:
+        print(json.dumps(serve_load(args.serve, (0.5, 0.8, 1.0, 1.2), args.serve_budget_gb,
+                                    args.serve_rich_maxit)), flush=True)
+        return
     print(json.dumps(served_mix(args.serve, args.serve_window, args.serve_budget_gb,
                                 args.serve_rich_maxit)), flush=True)
 
@@ -1089,6 +1139,9 @@ def main():
                          "elasticity CG step")
     ap.add_argument("--serve", type=int, default=0, help="run the served mix with this many requests")
     ap.add_argument("--serve-window", type=float, default=1.0)
+    ap.add_argument("--serve-load", action="store_true",
+                    help="with --serve N: capacity of both arms, then the refined arm at 0.5, 0.8, "
+                         "1.0 and 1.2 x its capacity")
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--serve-rich-maxit", type=int, default=100000)
     ap.add_argument("--no-served", action="store_true", help="skip the short served run")
