@@ -105,6 +105,12 @@ struct Scalars {
   double* hist;       // per-iteration stopping quantity (device, hist_cap entries) or null
   int hist_cap;
   int nhist;          // entries recorded (may exceed hist_cap; the excess is not stored)
+  // inner solves in potential coordinates (pcg_pot.cuh): the step length of the iterate update
+  // u += alpha_u p and the coefficient of the direction update p = z + beta_p p that the next
+  // step applies first, and 1 for Algorithm 3's coefficients (Chebyshev) instead of
+  // Algorithm 2's
+  double alpha_u, beta_p;
+  int pot_cheb;
 };
 
 // PRE_CG_DOT / POST_CG_FUSED: the CG step (both precisions) with the vector update fused into
@@ -126,9 +132,9 @@ struct PotVecs {
   cpx<T>* r;
   cpx<T>* p;
 };
-enum PotInvMode { POT_STEP = 0 /* p = z + beta p, lines of s = i p */,
-                  POT_FIELD = 1 /* lines of s = i u (x = D u, no update) */ };
-enum PotFwdMode { POT_UPDATE = 0 /* u += alpha p, r -= alpha q */,
+enum PotInvMode { POT_STEP = 0 /* u += alpha_u p, p = z +- beta p, lines of s = i p */,
+                  POT_FIELD = 1 /* lines of s = i (u + alpha_u p) (x = D u, no update) */ };
+enum PotFwdMode { POT_UPDATE = 0 /* r -= alpha q, (r, z), the step's coefficients */,
                   POT_INIT = 1 /* r = q (the right-hand side D* r_field), u = p = 0 */ };
 
 // Coefficient view used by the pre/post operators, in the working precision T.

@@ -1007,6 +1007,7 @@ int refine_start_inner(hom_problem* P) {
     s.alpha = 1.0 / s.cheb_d;
     s.beta = -0.5 * (s.cheb_c / s.cheb_d) * (s.cheb_c / s.cheb_d);
   }
+  s.pot_cheb = S_.pot && S_.solver == HOM_CHEBYSHEV;
   int rc = upload_scalars(P, P->d_sc2, s);
   if (rc) return rc;
   if (S_.pot) {
@@ -1037,7 +1038,7 @@ int refine_start_inner(hom_problem* P) {
 void refine_enqueue_inner(hom_problem* P) {
   if (P->sv.pot) {
     P->e32.pot_step(pot_vecs(P), (cpx<float>*)P->S, P->d_sc2, P->partials, P->counter,
-                    P->stream);
+                    P->stream, nullptr, 1, P->sv.solver == HOM_CHEBYSHEV);
     return;
   }
   const long long nodes = P->nodes;
@@ -1165,7 +1166,8 @@ static int solve_begin_impl(hom_problem* P, const double* E, int solver, double 
     S_.tol = tol;
     S_.inner_tol = o.inner_tol > 0 ? o.inner_tol : 1e-4;
     S_.maxit = o.maxit > 0 ? o.maxit : 50;
-    S_.pot = solver == HOM_CG && o.inner_form == 0 && P->e32.pot_ok();
+    S_.pot = (solver == HOM_CG || solver == HOM_CHEBYSHEV) && o.inner_form == 0 &&
+             P->e32.pot_ok();
     return refine_begin(P);
   }
 

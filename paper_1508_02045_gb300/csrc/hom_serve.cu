@@ -112,8 +112,10 @@ ReqDesc<T> idle_desc(Scalars* idle) {
 template <typename T>
 void batch_step(const Engine<T>& E, int solver, const ReqDesc<T>* reqs, int n, int red_grid,
                 long long nodes, int d, cudaStream_t st, bool pot = false) {
-  if (pot) {  // the FP32 inner CG in potential coordinates (buffers from the descriptors)
-    E.pot_step(PotVecs<T>{}, nullptr, nullptr, nullptr, nullptr, st, reqs, n);
+  if (pot) {  // the FP32 inner CG or Chebyshev in potential coordinates (buffers from the
+              // descriptors)
+    E.pot_step(PotVecs<T>{}, nullptr, nullptr, nullptr, nullptr, st, reqs, n,
+               solver == HOM_CHEBYSHEV);
     return;
   }
   switch (solver) {
@@ -151,6 +153,7 @@ struct hom_batch {
   ReqDesc<float>* d32 = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  long long graph_launches = 0;  // kernels in one replay of the graph
   bool pot = false;  // refined CG members run their inner solves in potential coordinates
 };
 
@@ -170,6 +173,7 @@ int batch_capture(hom_batch* B, int steps) {
     if (prof) hom_profile_enable(1);
     return HOM_ERR_CUDA;
   }
+  const long long c0 = launch_counter();
   for (int k = 0; k < steps; ++k) {
     if (B->refined)
       batch_step<float>(P0->e32, B->solver, B->d32, n, P0->red_grid, P0->nodes, P0->d, B->stream,
@@ -177,6 +181,9 @@ int batch_capture(hom_batch* B, int steps) {
     else
       batch_step<double>(P0->e64, B->solver, B->d64, n, P0->red_grid, P0->nodes, P0->d, B->stream);
   }
+  // the kernels recorded into the graph run once per replay: count them there
+  B->graph_launches = launch_counter() - c0;
+  launch_counter() = c0;
   const cudaError_t e = cudaStreamEndCapture(B->stream, &g);
   if (prof) hom_profile_enable(1);
   if (e != cudaSuccess) return HOM_ERR_CUDA;
@@ -245,8 +252,7 @@ extern "C" int hom_batch_iterate(hom_batch* B, int iterations, int use_graph, in
     int done_steps = 0;
     while (done_steps + B->graph_steps <= iterations) {
       HOM_CUDA(cudaGraphLaunch(B->graph, B->stream));
-      launch_counter() += (long long)B->graph_steps *
-                          ((P0->d == 3 ? 5 : 3) + (B->solver == HOM_CG ? 1 : 0));
+      launch_counter() += B->graph_launches;
       done_steps += B->graph_steps;
     }
     for (; done_steps < iterations; ++done_steps) {
@@ -335,6 +341,7 @@ struct Bucket {
   bool dirty = true;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  long long graph_launches = 0;  // kernels in one replay of the graph
   cudaStream_t stream = nullptr;  // the bucket's own stream: buckets overlap on the device
   int inner_form = 0;             // hom_opts.inner_form of its requests
   bool pot = false;               // their FP32 inner CG runs in potential coordinates
@@ -487,7 +494,10 @@ int bucket_launch(hom_server* S, Bucket& b, int iterations) {
     const bool prof = profiling();
     if (prof) hom_profile_enable(0);
     HOM_CUDA(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
+    const long long c0 = launch_counter();
     for (int k = 0; k < S->steps_per_graph; ++k) bucket_step(b);
+    b.graph_launches = launch_counter() - c0;  // recorded, not run: counted per replay
+    launch_counter() = c0;
     const cudaError_t e = cudaStreamEndCapture(b.stream, &g);
     if (prof) hom_profile_enable(1);
     HOM_CUDA(e);
@@ -499,7 +509,7 @@ int bucket_launch(hom_server* S, Bucket& b, int iterations) {
   int k = 0;
   for (; k + b.graph_steps <= iterations; k += b.graph_steps) {
     HOM_CUDA(cudaGraphLaunch(b.graph, b.stream));
-    launch_counter() += (long long)b.graph_steps * ((b.d == 3 ? 5 : 3) + (b.solver == HOM_CG ? 1 : 0));
+    launch_counter() += b.graph_launches;
   }
   for (; k < iterations; ++k) bucket_step(b);
   for (auto* r : b.slots)

@@ -13,12 +13,15 @@
 //                inverse axis-0 transforms of k_0 s and s with s = i p (components 0 and 1)
 //   strided    : inverse axis 1, two lines -> three components (k_pair_strided + strided2)
 //   k_pot_line : inverse axis 2, v = A w and the partial of (w, A w) = (p, K p), forward axis 2
-//   (k_cg_alpha: alpha = (r, z) / (p, K p))
+//   (k_cg_alpha: alpha = (r, z) / (p, K p); Chebyshev, Algorithm 3, has its alpha already)
 //   strided    : forward axis 1, three components -> X_0 and Y = k_1 X_1 + k_2 X_2
 //   k_pot_fwd  : forward axis 0, q = K p = -i (k_0 X_0 + Y) / |N|, r -= alpha q,
 //                z = r / |k|^2 and (r, z) (the last CTA: beta, the stopping test)
 // After a step the stored u lacks that step's alpha p; the field of the iterate (POT_FIELD)
-// adds it as it reads u.
+// adds it as it reads u. Chebyshev (Algorithm 3) runs the same passes with p = z - beta p (the
+// beta of the step that formed r) and its own coefficient recurrence in the last CTA of
+// k_pot_fwd: on M^{-1} K it is the field-form iteration on G A, whose spectrum on the range of
+// G it shares.
 // Inner products over the half spectrum count k_2 > 0 twice (Hermitian symmetry of real fields).
 // With exact integration (Section 2.3) the solve grid is the double grid and Gamma^ keeps only
 // the frequencies of Z_N: the preconditioner is zero outside Z_N, so z, the directions and the
@@ -112,10 +115,11 @@ k_pot_inv(cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, PotVecs<T> V,
   const long long es = g.C;
   pot_tile_cols<TC>(g, c0, ncols, kk12, hwc);
   __syncthreads();
-  // the previous step's u update, u += alpha p, is applied here (and in POT_FIELD mode to the
-  // value read), where p is loaded anyway: alpha and p are still those of that step
-  const T beta = MODE == POT_STEP ? (T)sc->beta : (T)0;
-  const T alpha = (T)sc->alpha;
+  // the previous step's u update, u += alpha_u p, is applied here (and in POT_FIELD mode to
+  // the value read), where p is loaded anyway: p is still that step's direction. The new
+  // direction is z + beta_p p (Algorithm 2: beta_p = beta; Algorithm 3: -beta of that step).
+  const T beta = MODE == POT_STEP ? (T)sc->beta_p : (T)0;
+  const T alpha = (T)sc->alpha_u;
   const cpx<T>* __restrict__ rg = V.r;
   cpx<T>* __restrict__ ug = V.u;
   cpx<T>* __restrict__ pg = V.p;
@@ -288,14 +292,16 @@ k_pot_fwd(const cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, PotVecs<T
   if (threadIdx.x != 0) return;
   const double rz = tot[0];
   if (MODE == POT_INIT) {
-    // r_0 = b, z_0 = M^{-1} r_0: ||b|| = sqrt((r_0, z_0)); beta = 0 makes p_1 = z_0
+    // r_0 = b, z_0 = M^{-1} r_0: ||b|| = sqrt((r_0, z_0)); u = p = 0, so the first direction
+    // is p_1 = z_0 whatever beta is (CG: beta = 0; Chebyshev keeps its initial coefficients)
     sc->nb = sqrt(rz);
     sc->rr = rz;
     sc->last_res = sqrt(rz);
-    sc->beta = 0.0;
+    sc->alpha_u = 0.0;
+    sc->beta_p = 0.0;
     return;
   }
-  // the CG step's scalar part (Algorithm 2): ||r_m|| of the field form is sqrt((r, z))
+  // the step's scalar part: ||r_m|| of the field form is sqrt((r, z))
   const double res = sqrt(rz);
   sc->last_res = res;
   record_history(sc, res);
@@ -308,7 +314,19 @@ k_pot_fwd(const cpx<T>* S, const cpx<T>* __restrict__ twg, ProjGeom g, PotVecs<T
   } else if (sc->it >= sc->maxit) {
     sc->done = 1;
   }
-  sc->beta = rz / sc->rr;
+  sc->alpha_u = sc->alpha;  // u += alpha p of this step, applied by the next direction update
+  if (sc->pot_cheb) {
+    // Algorithm 3: p_{m+1} = r_{m+1} - beta_m p_m with this step's beta, then the
+    // coefficients of the next step
+    sc->beta_p = -sc->beta;
+    const double an = 1.0 / (sc->cheb_d + sc->beta / sc->alpha);
+    sc->alpha = an;
+    sc->beta = -(sc->cheb_c * an * 0.5) * (sc->cheb_c * an * 0.5);
+  } else {
+    // Algorithm 2: beta = (r_m, z_m) / (r_{m-1}, z_{m-1})
+    sc->beta = rz / sc->rr;
+    sc->beta_p = sc->beta;
+  }
   sc->rr = rz;
 }
 

@@ -227,16 +227,18 @@ struct Engine {
       ++launch_counter();
     }
   }
-  // one CG step in potential coordinates (several requests with reqs / n)
+  // one CG (or, with cheb, Chebyshev) step in potential coordinates (several requests with
+  // reqs / n); Chebyshev's step length comes from its recurrence, not from (p, K p)
   void pot_step(const PotVecs<T>& V, cpx<T>* S, Scalars* sc, double* partials, unsigned* counter,
-                cudaStream_t st, const ReqDesc<T>* reqs = nullptr, int n = 1) const {
+                cudaStream_t st, const ReqDesc<T>* reqs = nullptr, int n = 1,
+                bool cheb = false) const {
     if constexpr (sizeof(T) == 4) {
       pot_inv_f32(POT_STEP, plan[0], S, tw[0], pg, V, sc, st, reqs, n);
       Ops<T>::strided_two_line(g, 1, S, plan[1], tw[1], sc, st, reqs, n);
       const int nb = pot_line_f32(plan[2], S, tw[2], g.nlines, g.scs, mat, sc, partials, st,
                                   reqs, n);
       ++launch_counter();
-      Ops<T>::cg_alpha(partials, nb, g.nodes, sc, st, reqs, n);
+      if (!cheb) Ops<T>::cg_alpha(partials, nb, g.nodes, sc, st, reqs, n);
       Ops<T>::strided_two_line(g, 0, S, plan[1], tw[1], sc, st, reqs, n);
       pot_fwd_f32(POT_UPDATE, plan[0], S, tw[0], pg, V, sc, partials, counter, st, reqs, n);
       launch_counter() += 2;

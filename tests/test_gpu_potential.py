@@ -57,6 +57,57 @@ def test_potential_inner_cg_reaches_the_fp64_oracle(N):
     assert abs(a - b) <= max(3, 0.1 * b), (a, b)
 
 
+@pytest.mark.parametrize("N", [(45, 45, 45), (81, 63, 45)])
+def test_potential_inner_chebyshev_reaches_the_fp64_oracle(N):
+    # Algorithm 3 on M^{-1} K with the bounds [c_A, C_A] of A: the field-form iteration on G A
+    # in exact arithmetic, so both inner forms reach the oracle, in about as many inner steps
+    ph, table = spheres(N, 4)
+    E = np.array([0.5, -0.4, 0.7])
+    sysn = O.GaNi(O.expand_phase(ph, table)[0, 0], 3)
+    xr = O.cg(sysn, E, tol=1e-12).x
+    ref = sysn.energy(E, xr)
+    res = {}
+    for form in (0, 1):
+        P = H.Problem(3, N, H.phase_material(ph, table), precision=H.HOM_FP32_REFINED)
+        x = P.field()
+        AH, _, st, _ = H.hom_solve(P.h, E, H.HOM_CHEBYSHEV, 1e-10, H.make_opts(inner_form=form), x)
+        assert st["converged"] and st["true_residual"] <= 1e-10
+        assert abs(AH - ref) < AH_TOL_MIXED * ref
+        assert rel(x.cpu().numpy(), xr) < 1e-8
+        res[form] = st["inner_iterations"]
+        P.close()
+    assert abs(res[0] - res[1]) <= max(3, 0.1 * res[1]), res
+
+
+@pytest.mark.parametrize("solver", [H.HOM_CG, H.HOM_CHEBYSHEV])
+def test_potential_batch_of_both_solvers_equals_solo(solver):
+    N = (45, 63, 81)
+    mats = [spheres(N, s) for s in (8, 9, 10)]
+    Es = [np.array([1.0, 0.0, 0.0]), np.array([0.0, 0.6, 0.8]), np.array([0.3, 0.3, -0.9])]
+    solo = []
+    for (ph, table), E in zip(mats, Es):
+        P = H.Problem(3, N, H.phase_material(ph, table), precision=H.HOM_FP32_REFINED)
+        solo.append(H.hom_solve(P.h, E, solver, 1e-9)[:3])
+        P.close()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        probs = [H.Problem(3, N, H.phase_material(ph, table), precision=H.HOM_FP32_REFINED)
+                 for ph, table in mats]
+        for P, E in zip(probs, Es):
+            H.hom_solve_begin(P.h, E, solver, 1e-9, None)
+        B = H.hom_batch_create([P.h for P in probs])
+        for _ in range(1000):
+            if H.hom_batch_iterate(B, 8, use_graph=True, poll=True):
+                break
+        for P, (AH, _, st) in zip(probs, solo):
+            AHb, _, stb, _ = H.hom_solve_end(P.h, 3)
+            assert stb["converged"] and AHb == AH
+            assert stb["inner_iterations"] == st["inner_iterations"]
+        H.hom_batch_destroy(B)
+        for P in probs:
+            P.close()
+
+
 @pytest.mark.parametrize("N", [(23, 23, 23), (41, 23, 23)])
 def test_potential_inner_cg_exact_integration(N):
     # Ga on the double grid 2N - 1 (45, 81: specialised plans on every axis): the preconditioner
