@@ -114,11 +114,11 @@ typedef struct {
   int check_every;    /* host polls the device stopping flag every this many iterations (0=8) */
   int out_flags;      /* hom_out_flag bits for the corrector output of hom_solve, hom_solve_end
                          and hom_solve_current                                                */
-  int inner_form;     /* HOM_FP32_REFINED with CG: 0 = the FP32 inner solves run Algorithm 2 in
-                         potential coordinates (x = grad u: one-component vectors, operator
-                         D* A D, Laplacian preconditioner; the same iterates in exact
-                         arithmetic) on 3-D grids whose axes all have specialised FP32 plans,
-                         else in field form; 1 = always in field form                      */
+  int inner_form;     /* HOM_FP32_REFINED (CG or Chebyshev): 0 = the FP32 inner solves run
+                         Algorithm 2 or 3 in potential coordinates (x = grad u: one-component
+                         vectors, operator D* A D, Laplacian preconditioner; the same iterates
+                         in exact arithmetic) on 3-D grids whose axes all have specialised FP32
+                         plans, else in field form; 1 = always in field form               */
 } hom_opts;
 
 /* Where and on which grid the solve returns the corrector e (field of hom_opts.out_flags). */
@@ -411,9 +411,10 @@ long long hom_kernel_launches(void);
  * CUDA events on its stream. Enabling clears earlier records. Not thread-safe; intended for
  * benchmarks. Pass kinds: 0 pre-operator + forward DFT of the contiguous axis, 1 strided-axis
  * DFT, 2 axis-0 DFT with the projection, 3 inverse DFT of the contiguous axis + solver update,
- * 4 vector update / reduction kernels; the inner CG in potential coordinates (HOM_FP32_REFINED,
- * inner_form 0): 5 axis-0 direction update + inverse DFT, 6 contiguous-axis inverse DFT +
- * material + forward DFT, 7 axis-0 forward DFT + vector update. */
+ * 4 vector update / reduction kernels; the inner solves in potential coordinates
+ * (HOM_FP32_REFINED, inner_form 0): 5 axis-0 iterate and direction update + inverse DFT,
+ * 6 contiguous-axis inverse DFT + material + forward DFT, 7 axis-0 forward DFT + residual
+ * update. */
 int hom_profile_enable(int on);
 
 /* Total milliseconds and launch counts per pass kind recorded since the last enable
