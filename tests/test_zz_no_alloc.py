@@ -6,6 +6,10 @@ cudaMalloc/cudaFree) get the same operator as hom_apply, with the work memory in
 device array of the library. This file runs last so that a failure here leaves every other
 test already run; it must also pass on its own in a fresh process.
 """
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -61,3 +65,38 @@ def test_static_rejects_problems_beyond_the_scratch():
         H.hom_apply_static(3, N, ph_dev, ms.isotropic_table([1.0, 2.0], 3), H.HOM_OP_LINEAR,
                            None, x, x)
     assert ei.value.status == H.HOM_ERR_SCRATCH
+
+
+FRESH = """
+import sys
+import numpy as np
+import torch
+import microstructure as ms
+import oracle as O
+import paper_1508_02045_gb300 as H
+N = (27, 25, 21)
+ph = ms.box_phase(N, 0.6)
+table = ms.random_spd_table(2, 3, seed=4, scales=[1.0, 30.0])
+x = ms.random_field((3,) + N, 9)
+E = ms.random_unit_vector(3, 2)
+xd = torch.from_numpy(x).cuda()
+y = torch.full_like(xd, float("nan"))
+# the first call of the library in this process: the set-up runs inside it
+H.hom_apply_static(3, N, torch.from_numpy(ph).cuda(), table, H.HOM_OP_AFFINE, E, xd, y)
+torch.cuda.synchronize()
+sysn = O.GaNi(O.expand_phase(ph, table), 3)
+ref = sysn.matvec(sysn.const(E) + x)
+err = np.linalg.norm((y.cpu().numpy() - ref).ravel()) / np.linalg.norm(ref.ravel())
+print("rel", err)
+sys.exit(0 if err < 1e-12 else 1)
+"""
+
+
+def test_static_first_in_a_fresh_process():
+    # hom_apply_static before any hom_create in a new process (its own set-up path), against
+    # the oracle's GaNi operator
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PYTHONPATH=root + os.pathsep + os.environ.get("PYTHONPATH", ""))
+    r = subprocess.run([sys.executable, "-c", FRESH], cwd=root, env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
