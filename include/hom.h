@@ -80,7 +80,8 @@ typedef enum {
   HOM_A_FOURIER = 2, /* exact integration only: isotropic coefficients A^(n), n in Z_M, as
                         interleaved complex doubles (re, im) in FFT-natural order on the
                         double grid M (eq. (Ga_exact_integration))                           */
-  HOM_A_STIFFNESS = 3 /* linear elasticity (GaNi, FP64): phase index per node + nphase
+  HOM_A_STIFFNESS = 3 /* linear elasticity (GaNi; FP64, or HOM_FP32_REFINED with CG or
+                        Chebyshev inner solves in field form): phase index per node + nphase
                         symmetric positive definite stiffness matrices nc x nc in Mandel form,
                         nc = d (d + 1) / 2; see "Elasticity" below                          */
 } hom_material_kind;

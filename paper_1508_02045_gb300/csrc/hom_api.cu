@@ -439,10 +439,10 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
     if (N[a] < 3 || N[a] % 2 == 0 || N[a] > kMaxAxis) return HOM_ERR_INVALID;
   if (integration == HOM_APPROX && A->kind == HOM_A_FOURIER) return HOM_ERR_INVALID;
   // linear elasticity: symmetric strain fields of nc = d (d + 1) / 2 components (Mandel),
-  // sampled stiffness (GaNi) in FP64
+  // sampled stiffness (GaNi), FP64 or FP32 inner solves with FP64 refinement
   const bool elastic = A->kind == HOM_A_STIFFNESS;
   const int nc = elastic ? d * (d + 1) / 2 : d;
-  if (elastic && (integration != HOM_APPROX || precision != HOM_FP64)) return HOM_ERR_UNSUPPORTED;
+  if (elastic && integration != HOM_APPROX) return HOM_ERR_UNSUPPORTED;
   // exact integration of an image (voxel-wise constant coefficients): scalar coefficients only
   const bool voxel_ga = integration == HOM_EXACT && A->kind != HOM_A_FOURIER;
   if (voxel_ga) {
@@ -620,8 +620,8 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
     if ((st = P->e64.init(d, P->M, P->N, pc.budget, pc.rmax, pc.threads, pc.two_line, nc)) != HOM_OK) { hom_destroy(P); return st; }
   }
   if (precision == HOM_FP32_REFINED) {
-    const PlanChoice pc = plan_choice(4, d, P->M, P->N);
-    if ((st = P->e32.init(d, P->M, P->N, pc.budget, pc.rmax, pc.threads, pc.two_line)) != HOM_OK) { hom_destroy(P); return st; }
+    const PlanChoice pc = plan_choice(4, d, P->M, P->N, nc);
+    if ((st = P->e32.init(d, P->M, P->N, pc.budget, pc.rmax, pc.threads, pc.two_line, nc)) != HOM_OK) { hom_destroy(P); return st; }
   }
 
   // ---- buffers ----
@@ -680,7 +680,7 @@ int hom_create(int d, const int* N, const hom_material* A, int integration, int 
   }
   if (precision == HOM_FP32_REFINED) {
     if (P->d_table) {
-      const size_t ntab = (P->mat_kind == MAT_PHASE_ISO) ? (size_t)P->nphase : (size_t)P->nphase * d * d;
+      const size_t ntab = (P->mat_kind == MAT_PHASE_ISO) ? (size_t)P->nphase : (size_t)P->nphase * nc * nc;
       std::vector<double> h(ntab);
       std::vector<float> hf(ntab);
       cudaMemcpy(h.data(), P->d_table, sizeof(double) * ntab, cudaMemcpyDeviceToHost);

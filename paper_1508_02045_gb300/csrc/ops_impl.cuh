@@ -158,10 +158,8 @@ cudaError_t Ops<T>::prepare(int) {
   HOM_SET_SMEM((k_line_fwd<T, 3, PRE_CG_DOT>));
   HOM_SET_SMEM((k_line_inv<T, 2, POST_CG_FUSED>));
   HOM_SET_SMEM((k_line_inv<T, 3, POST_CG_FUSED>));
-  if constexpr (std::is_same<T, float>::value) {
-    return pair_prepare_f32(cap);
-  } else {
-    // elasticity (FP64): strain fields of 3 (2-D, the 3-component line kernels above) or 6
+  {
+    // elasticity: strain fields of 3 (2-D, the 3-component line kernels above) or 6
     // components (their projection pass is two strided passes around k_proj_point)
     HOM_SET_SMEM((k_line_fwd<T, 6, PRE_CG>));
     HOM_SET_SMEM((k_line_inv<T, 6, POST_CG>));
@@ -176,8 +174,9 @@ cudaError_t Ops<T>::prepare(int) {
     HOM_SET_SMEM((k_line_inv<T, 6, POST_EM>));
     HOM_SET_SMEM((k_line_inv<T, 6, POST_ADD>));
     HOM_SET_SMEM((k_line_inv<T, 6, POST_CG_FUSED>));
-    return cudaSuccess;
   }
+  if constexpr (std::is_same<T, float>::value) return pair_prepare_f32(cap);
+  return cudaSuccess;
 }
 
 template <typename T, int D>
@@ -224,9 +223,8 @@ void Ops<T>::line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
       return;
     }
   }
-  if (ncomp > 3) {  // six-component strains (elasticity, FP64 only)
-    if constexpr (sizeof(T) == 8)
-      line_fwd_d<T, 6>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq, partials);
+  if (ncomp > 3) {  // six-component strains (elasticity)
+    line_fwd_d<T, 6>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq, partials);
   } else if (g.D == 2 && ncomp <= 2) {
     line_fwd_d<T, 2>(g, pre, f, S, P, tw, ncomp, mat, sc, args, st, reqs, nreq, partials);
   } else {
@@ -283,37 +281,35 @@ void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, con
                   const ReqDesc<T>* reqs, int nreq) {
   const bool prof = profiling();
   if (prof) prof_mark(KIND_PROJ, st, true);
+  if (g.NC != g.D) {  // symmetric strain fields (elasticity)
+    // the axis-0 transforms of the NC components as column passes (one CTA per component
+    // tile, the tile shared memory of the strided pass), the strain projection node by node
+    // between them: a one-kernel pass would hold all NC component tiles of its columns in
+    // shared memory and run one CTA per SM
+    const long long C = g.scs / g.n[0];
+    const dim3 gs((unsigned)((C + g.TCs0 - 1) / g.TCs0), (unsigned)g.NC, (unsigned)nreq);
+    const size_t sms = smem_strided(P.n, g.TCs0p, P.nst);
+    launch_pass(k_strided<T>, gs, g.NTs0, sms, st, S, P, tw, C, C, g.scs, g.TCs0, g.TCs0p, 0,
+                sc, reqs);
+    const dim3 gp((unsigned)((pg.C + kThreads - 1) / kThreads), (unsigned)P.n, (unsigned)nreq);
+#define HOM_PJE(D_, NC_, M_) launch_pass(k_proj_point<T, D_, NC_, M_>, gp, kThreads, 0, st, S, pg, P.n, (T)g.nodes, sc, reqs)
+    if (g.D == 2) {
+      if (mode == PROJ_EM) HOM_PJE(2, 3, PROJ_EM); else HOM_PJE(2, 3, PROJ_GAMMA);
+    } else {
+      if (mode == PROJ_EM) HOM_PJE(3, 6, PROJ_EM); else HOM_PJE(3, 6, PROJ_GAMMA);
+    }
+#undef HOM_PJE
+    launch_pass(k_strided<T>, gs, g.NTs0, sms, st, S, P, tw, C, C, g.scs, g.TCs0, g.TCs0p, 1,
+                sc, reqs);
+    if (prof) prof_mark(KIND_PROJ, st, false);
+    launch_counter() += 3;
+    return;
+  }
   if (pair_plan<T>(P)) {
     if constexpr (std::is_same<T, float>::value)
       pair_proj_f32(g.D, mode, false, P, S, tw, pg, sc, st, reqs, nreq);
     if (prof) prof_mark(KIND_PROJ, st, false);
     ++launch_counter();
-    return;
-  }
-  if (g.NC != g.D) {  // symmetric strain fields (elasticity, FP64 only)
-    if constexpr (sizeof(T) == 8) {
-      // the axis-0 transforms of the NC components as column passes (one CTA per component
-      // tile, the tile shared memory of the strided pass), the strain projection node by node
-      // between them: a one-kernel pass would hold all NC component tiles of its columns in
-      // shared memory and run one CTA per SM
-      const long long C = g.scs / g.n[0];
-      const dim3 gs((unsigned)((C + g.TCs0 - 1) / g.TCs0), (unsigned)g.NC, (unsigned)nreq);
-      const size_t sms = smem_strided(P.n, g.TCs0p, P.nst);
-      launch_pass(k_strided<T>, gs, g.NTs0, sms, st, S, P, tw, C, C, g.scs, g.TCs0, g.TCs0p, 0,
-                  sc, reqs);
-      const dim3 gp((unsigned)((pg.C + kThreads - 1) / kThreads), (unsigned)P.n, (unsigned)nreq);
-#define HOM_PJE(D_, NC_, M_) launch_pass(k_proj_point<T, D_, NC_, M_>, gp, kThreads, 0, st, S, pg, P.n, (T)g.nodes, sc, reqs)
-      if (g.D == 2) {
-        if (mode == PROJ_EM) HOM_PJE(2, 3, PROJ_EM); else HOM_PJE(2, 3, PROJ_GAMMA);
-      } else {
-        if (mode == PROJ_EM) HOM_PJE(3, 6, PROJ_EM); else HOM_PJE(3, 6, PROJ_GAMMA);
-      }
-#undef HOM_PJE
-      launch_pass(k_strided<T>, gs, g.NTs0, sms, st, S, P, tw, C, C, g.scs, g.TCs0, g.TCs0p, 1,
-                  sc, reqs);
-    }
-    if (prof) prof_mark(KIND_PROJ, st, false);
-    launch_counter() += 3;
     return;
   }
   if (g.D == 3 && mode == PROJ_GAMMA) {
@@ -412,10 +408,9 @@ void Ops<T>::line_inv(const PassGeom& g, int post, const cpx<T>* S, const Fields
       return;
     }
   }
-  if (ncomp > 3) {  // six-component strains (elasticity, FP64 only)
-    if constexpr (sizeof(T) == 8)
-      line_inv_d<T, 6>(g, post, S, f, P, tw, ncomp, mat, sc, args, partials, counter, negate, st,
-                       reqs, nreq);
+  if (ncomp > 3) {  // six-component strains (elasticity)
+    line_inv_d<T, 6>(g, post, S, f, P, tw, ncomp, mat, sc, args, partials, counter, negate, st,
+                     reqs, nreq);
   } else if (g.D == 2 && ncomp <= 2) {
     line_inv_d<T, 2>(g, post, S, f, P, tw, ncomp, mat, sc, args, partials, counter, negate, st,
                      reqs, nreq);
@@ -438,7 +433,7 @@ void Ops<T>::energy(int ncomp, const T* x, long long nodes, const MatView<T>& ma
                     double* partials, unsigned* counter, int grid, cudaStream_t st) {
   if (ncomp == 2) k_energy<T, 2><<<grid, kThreads, 0, st>>>(x, nodes, mat, sc, partials, counter);
   else if (ncomp == 3) k_energy<T, 3><<<grid, kThreads, 0, st>>>(x, nodes, mat, sc, partials, counter);
-  else if constexpr (sizeof(T) == 8)
+  else
     k_energy<T, 6><<<grid, kThreads, 0, st>>>(x, nodes, mat, sc, partials, counter);
   ++launch_counter();
 }
