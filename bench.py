@@ -636,7 +636,7 @@ def _run_ours(args, rank, world, local):
                        "converged": bool(stats["converged"])},
     }
     if not args.no_elastic:
-        line["elastic"] = elastic_step(min(args.steps, 10), 3)
+        line["elastic"] = elastic_step(min(args.steps, 10), 3, solves=True)
     if not args.no_kappa:
         # Section 4.6 in 3-D, reduced: 63^3 and its double grid 125^3, kappa 10, 100, 1000, all
         # four solvers (Richardson where its O(kappa) count stays within 8000 iterations)
@@ -827,11 +827,11 @@ def serve_load(n_req, factors, budget_gb, rich_maxit, seed=2024):
             "loads": rows}
 
 
-def elastic_step(steps, warmup, n=243):
+def elastic_step(steps, warmup, n=243, solves=False):
     """Linear elasticity (the strain form, six Mandel components) on the bench geometry: the
     243^3 cube of volume fraction 0.2, isotropic phases (lambda, mu) = (1, 1) and (1000, 1000),
     E = e_11; `steps` FP64 CG steps timed with CUDA events (inputs larger than L2: 688 MB a
-    field), the operator's passes by kind."""
+    field), the operator's passes by kind; with `solves`, CG to 1e-8 in FP64 and FP32-refined."""
     import torch
     import paper_1508_02045_gb300 as H
     N = (n,) * 3
@@ -854,12 +854,36 @@ def elastic_step(steps, warmup, n=243):
     passes = H.hom_profile_read()
     ms_step = e0.elapsed_time(e1) / steps
     H.hom_solve_end(P.h, 6, allow_not_converged=True)
+    out = {"metric": "G·C matvecs/s at 243^3, linear elasticity (FP64 CG step, 6 components)",
+           "value": round(1000.0 / ms_step, 3), "unit": UNIT, "ms_per_step": round(ms_step, 4),
+           "steps": steps, "grid": list(N),
+           "passes": {k: {"ms_avg": round(v[0] / v[1], 4), "launches": v[1]}
+                      for k, v in passes.items() if v[1]}}
+    if solves:
+        # CG to 1e-8 in FP64 and with FP32 inner solves in FP64 refinement (outside the timed
+        # region of the step)
+        res = {}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        AH, _, st, _ = H.hom_solve(P.h, E, H.HOM_CG, 1e-8, H.make_opts(maxit=5000))
+        torch.cuda.synchronize()
+        res["fp64"] = {"seconds": round(time.perf_counter() - t0, 3), "A_H": AH,
+                       "iterations": st["iterations"], "converged": bool(st["converged"])}
+        P.close()
+        P = H.Problem(3, N, H.stiffness_material(ph, table), precision=H.HOM_FP32_REFINED)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        AH32, _, st, _ = H.hom_solve(P.h, E, H.HOM_CG, 1e-8, H.make_opts(maxit=50))
+        torch.cuda.synchronize()
+        res["fp32_refined"] = {"seconds": round(time.perf_counter() - t0, 3), "A_H": AH32,
+                               "iterations": st["iterations"],
+                               "inner_iterations": st["inner_iterations"],
+                               "converged": bool(st["converged"])}
+        res["A_H_rel_diff"] = abs(AH32 - AH) / AH
+        res["speedup"] = round(res["fp64"]["seconds"] / res["fp32_refined"]["seconds"], 2)
+        out["cg_to_1e-8"] = res
     P.close()
-    return {"metric": "G·C matvecs/s at 243^3, linear elasticity (FP64 CG step, 6 components)",
-            "value": round(1000.0 / ms_step, 3), "unit": UNIT, "ms_per_step": round(ms_step, 4),
-            "steps": steps, "grid": list(N),
-            "passes": {k: {"ms_avg": round(v[0] / v[1], 4), "launches": v[1]}
-                       for k, v in passes.items() if v[1]}}
+    return out
 
 
 def elastic_stiffness(lam, mu):
