@@ -505,28 +505,72 @@ k_pot_line(cpx<T>* S, const cpx<T>* __restrict__ twg, long long nlines, long lon
     }
   }
   __syncthreads();
-  for (int w = threadIdx.x; w < NL * R1; w += blockDim.x) {
-    const int i = w % R1;
-    cpx<T>* line = lines + (w / R1) * n;
-    cpx<T> u[R2];
-    pair_stage2_regs<T, R1, R2>(line, tw, 1, i, u);
+  // (the 21 x 9 plan of 189 points spills registers in the fused form)
+  if constexpr (R2 <= 9 && !(R1 == 21 && R2 == 9)) {
+    // forward stage 2 and the split into half spectra together: item (lc, i) runs stage 2 for
+    // the rows of residue i and of its mirror R1 - i (mod R1), which between them hold Z[k] and
+    // Z[n - k] for every output k of either residue: n - (i + R1 r) = (R1 - i) + R1 (R2 - 1 - r)
+    constexpr int R1h = (R1 + 1) / 2;
+    for (int w = threadIdx.x; w < NL * R1h; w += blockDim.x) {
+      const int i = w % R1h, lc = w / R1h;
+      const int a = lc / LBP, q = lc - a * LBP;
+      const cpx<T>* line = lines + lc * n;
+      cpx<T> u[R2], v[R2];
+      pair_stage2_regs<T, R1, R2>(line, tw, 1, i, u);
+      if (i > 0) {
+        pair_stage2_regs<T, R1, R2>(line, tw, 1, R1 - i, v);
+      } else {
 #pragma unroll
-    for (int r = 0; r < R2; ++r) line[i + r * R1] = u[r];
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < NL * nh; idx += blockDim.x) {
-    const int lc = idx / nh, k = idx - lc * nh;
-    const int a = lc / LBP, q = lc - a * LBP;
-    const cpx<T> zk = lines[lc * n + k];
-    const cpx<T> zm = lines[lc * n + (k ? n - k : 0)];
-    cpx<T> Ah, Bh;
-    Ah.x = (T)0.5 * (zk.x + zm.x);
-    Ah.y = (T)0.5 * (zk.y - zm.y);
-    Bh.x = (T)0.5 * (zk.y + zm.y);
-    Bh.y = (T)-0.5 * (zk.x - zm.x);
-    const long long la = l0 + 2 * q;
-    if (la < nlines) S[a * scs + la * nh + k] = Ah;
-    if (la + 1 < nlines) S[a * scs + (la + 1) * nh + k] = Bh;
+        for (int r = 0; r < R2; ++r) v[r] = cpx<T>{0, 0};
+      }
+      const long long la = l0 + 2 * q;
+      const bool okA = la < nlines, okB = la + 1 < nlines;
+      cpx<T>* outA = S + a * scs + la * nh;
+      cpx<T>* outB = outA + nh;
+#pragma unroll
+      for (int r = 0; r < R2; ++r) {
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+          if (m == 1 && i == 0) continue;
+          const int k = m == 0 ? i + r * R1 : (R1 - i) + r * R1;
+          if (k >= nh) continue;
+          // Z[k] and Z[n - k]; residue 0 is its own mirror (Z[n - R1 r] = Z[R1 (R2 - r)])
+          const cpx<T> zk = m == 0 ? u[r] : v[r];
+          const cpx<T> zm = m == 1 ? u[R2 - 1 - r] : (i == 0 ? u[(R2 - r) % R2] : v[R2 - 1 - r]);
+          cpx<T> Ah, Bh;
+          Ah.x = (T)0.5 * (zk.x + zm.x);
+          Ah.y = (T)0.5 * (zk.y - zm.y);
+          Bh.x = (T)0.5 * (zk.y + zm.y);
+          Bh.y = (T)-0.5 * (zk.x - zm.x);
+          if (okA) outA[k] = Ah;
+          if (okB) outB[k] = Bh;
+        }
+      }
+    }
+  } else {
+    for (int w = threadIdx.x; w < NL * R1; w += blockDim.x) {
+      const int i = w % R1;
+      cpx<T>* line = lines + (w / R1) * n;
+      cpx<T> u[R2];
+      pair_stage2_regs<T, R1, R2>(line, tw, 1, i, u);
+#pragma unroll
+      for (int r = 0; r < R2; ++r) line[i + r * R1] = u[r];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NL * nh; idx += blockDim.x) {
+      const int lc = idx / nh, k = idx - lc * nh;
+      const int a = lc / LBP, q = lc - a * LBP;
+      const cpx<T> zk = lines[lc * n + k];
+      const cpx<T> zm = lines[lc * n + (k ? n - k : 0)];
+      cpx<T> Ah, Bh;
+      Ah.x = (T)0.5 * (zk.x + zm.x);
+      Ah.y = (T)0.5 * (zk.y - zm.y);
+      Bh.x = (T)0.5 * (zk.y + zm.y);
+      Bh.y = (T)-0.5 * (zk.x - zm.x);
+      const long long la = l0 + 2 * q;
+      if (la < nlines) S[a * scs + la * nh + k] = Ah;
+      if (la + 1 < nlines) S[a * scs + (la + 1) * nh + k] = Bh;
+    }
   }
   line_fwd_partial_cg(dacc, partials);
 }
