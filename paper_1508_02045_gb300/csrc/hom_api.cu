@@ -1293,7 +1293,7 @@ extern "C" int hom_solve_end(hom_problem* P, double* x_dev, double* AH_EE, doubl
     HOM_CUDA(cudaEventSynchronize(P->ev1));
     float ms = 0;
     cudaEventElapsedTime(&ms, P->ev0, P->ev1);
-    double en = 0, fl[3] = {0, 0, 0};
+    double en = 0, fl[kMaxComp] = {};
     if ((rc = energy_eval(P, S_.E, P->vec[0], &en, fl))) return rc;
     if (AH_EE) *AH_EE = en;
     if (flux)
@@ -1335,7 +1335,7 @@ extern "C" int hom_solve_end(hom_problem* P, double* x_dev, double* AH_EE, doubl
   HOM_CUDA(cudaEventSynchronize(P->ev1));
   float ms = 0;
   cudaEventElapsedTime(&ms, P->ev0, P->ev1);
-  double en = 0, fl[3] = {0, 0, 0};
+  double en = 0, fl[kMaxComp] = {};
   rc = energy_eval(P, S_.E, result, &en, fl);
   if (rc) return rc;
   if (AH_EE) *AH_EE = en;
