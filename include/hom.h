@@ -104,7 +104,9 @@ typedef enum { HOM_STOP_DEFAULT = 0, HOM_STOP_RESIDUAL = 1, HOM_STOP_INCREMENT =
 
 typedef struct {
   int maxit;          /* iteration limit (0 = 100000)                                         */
-  int fixed_iters;    /* > 0: run exactly this many iterations, no stopping test              */
+  int fixed_iters;    /* > 0: run exactly this many iterations, no stopping test; with
+                         HOM_FP32_REFINED one inner solve of exactly this many FP32 steps from
+                         zero and its FP64 update (tol is then ignored)                     */
   int stop;           /* hom_stop. DEFAULT: residual ||b - C x|| <= tol ||b|| for Richardson,
                          CG and Chebyshev; increment ||x_m - x_{m-1}|| <= tol ||E|| for
                          Eyre-Milton (Algorithms 1-4 print the increment test for Richardson) */
@@ -243,12 +245,14 @@ int hom_energy(hom_problem* P, const double* E, const double* x_dev, double* ene
 
 /* Prolongation R_{N,M} = I_M o I_N^{-1} (eq. (ev_bounds)): the trigonometric polynomial with
  * nodal values x_dev on the grid of `coarse` sampled on the solve grid of `fine`
- * (every M_a >= N_a, odd). Output y_dev: d x |M| doubles on the device. */
+ * (every M_a >= N_a, odd). Output y_dev: d x |M| doubles on the device. Vector fields only:
+ * HOM_ERR_UNSUPPORTED for strain fields (elasticity). */
 int hom_prolongate(hom_problem* coarse, hom_problem* fine, const double* x_dev, double* y_dev);
 
 /* Guaranteed upper bound of eq. (ev_bounds_GaNi): U_E(R_{N,M}[E + x]) with x_dev a GaNi field
  * of problem `gani` and A_M of the exact-integration problem `ga` built for the same N.
- * Synchronises the stream. */
+ * Synchronises the stream. HOM_ERR_UNSUPPORTED for an elasticity problem (no exact
+ * integration of stiffness). */
 int hom_bound(hom_problem* gani, hom_problem* ga, const double* E, const double* x_dev,
               double* UE);
 

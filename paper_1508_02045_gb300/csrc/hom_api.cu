@@ -1161,11 +1161,21 @@ static int solve_begin_impl(hom_problem* P, const double* E, int solver, double 
   S_.nE = nE;
   if (P->precision == HOM_FP32_REFINED) {
     if (solver != HOM_CG && solver != HOM_CHEBYSHEV) return HOM_ERR_UNSUPPORTED;
-    if (!(tol > 0)) return HOM_ERR_INVALID;
     S_.refined = true;
-    S_.tol = tol;
-    S_.inner_tol = o.inner_tol > 0 ? o.inner_tol : 1e-4;
-    S_.maxit = o.maxit > 0 ? o.maxit : 50;
+    if (S_.fixed) {
+      // one inner solve of exactly fixed_iters FP32 steps from zero and its FP64 update:
+      // the inner iteration itself, comparable with Algorithm 2 or 3 at that step count
+      S_.tol = 0.0;
+      S_.inner_tol = 0.0;
+      S_.inner_maxit = o.fixed_iters;
+      S_.maxit = 1;
+    } else {
+      if (!(tol > 0)) return HOM_ERR_INVALID;
+      S_.tol = tol;
+      S_.inner_tol = o.inner_tol > 0 ? o.inner_tol : 1e-4;
+      S_.inner_maxit = 10000;
+      S_.maxit = o.maxit > 0 ? o.maxit : 50;
+    }
     S_.pot = (solver == HOM_CG || solver == HOM_CHEBYSHEV) && o.inner_form == 0 &&
              P->e32.pot_ok();
     return refine_begin(P);
@@ -1310,7 +1320,7 @@ extern "C" int hom_solve_end(hom_problem* P, double* x_dev, double* AH_EE, doubl
     }
     if (x_dev && (rc = write_corrector(P, P->vec[0], x_dev))) return rc;
     if ((rc = check_last())) return rc;
-    return S_.converged ? HOM_OK : HOM_ERR_NOT_CONVERGED;
+    return (S_.converged || S_.fixed) ? HOM_OK : HOM_ERR_NOT_CONVERGED;
   }
   rc = poll(P, P->d_sc);
   if (rc) return rc;
@@ -1465,6 +1475,7 @@ extern "C" int hom_energy(hom_problem* P, const double* E, const double* x_dev, 
 extern "C" int hom_prolongate(hom_problem* Cp, hom_problem* Fp, const double* x_dev,
                               double* y_dev) {
   if (!Cp || !Fp || !x_dev || !y_dev || Cp->d != Fp->d) return HOM_ERR_INVALID;
+  if (Cp->nc != Cp->d || Fp->nc != Fp->d) return HOM_ERR_UNSUPPORTED;  // strain fields
   const int d = Cp->d;
   for (int a = 0; a < d; ++a)
     if (Fp->M[a] < Cp->M[a]) return HOM_ERR_INVALID;
@@ -1494,6 +1505,7 @@ extern "C" int hom_bound(hom_problem* gani, hom_problem* ga, const double* E,
   if (!gani || !ga || !E || !x_dev || !UE) return HOM_ERR_INVALID;
   if (gani->integration != HOM_APPROX || ga->integration != HOM_EXACT || gani->d != ga->d)
     return HOM_ERR_INVALID;
+  if (gani->nc != gani->d) return HOM_ERR_UNSUPPORTED;  // strain fields (no exact integration)
   for (int a = 0; a < gani->d; ++a)
     if (ga->N[a] != gani->N[a]) return HOM_ERR_INVALID;
   double* y = ga->vec[4];

@@ -173,6 +173,15 @@ def test_elastic_unsupported_combinations():
         with pytest.raises(H.HomError) as ei:
             H.hom_create(2, N, mat, integ, prec)
         assert ei.value.status == H.HOM_ERR_UNSUPPORTED
+    # prolongation and the GaNi bound take vector fields only
+    Pe = H.Problem(2, N, mat)
+    Pf = H.Problem(2, (17, 17), H.stiffness_material(ms.box_phase((17, 17), 0.6), table))
+    y = Pf.field()
+    with pytest.raises(H.HomError) as ei:
+        H.hom_prolongate(Pe.h, Pf.h, Pe.field(), y)
+    assert ei.value.status == H.HOM_ERR_UNSUPPORTED
+    Pe.close()
+    Pf.close()
     bad = table.copy()
     bad[1, 0, 1] += 1.0  # not symmetric
     with pytest.raises(H.HomError) as ei:

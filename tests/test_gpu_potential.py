@@ -108,6 +108,32 @@ def test_potential_batch_of_both_solvers_equals_solo(solver):
             P.close()
 
 
+@pytest.mark.parametrize("solver", ["cg", "chebyshev"])
+@pytest.mark.parametrize("form", [0, 1])
+def test_fp32_inner_iterates_follow_the_algorithms(solver, form):
+    # one inner solve of exactly k FP32 steps from zero (fixed_iters) is Algorithm 2 or 3 run
+    # k steps on C x = b: the iterate of the FP64 oracle at k steps, up to FP32 rounding
+    N = (45, 63, 81)
+    ph = ms.box_phase(N, 0.6)
+    table = ms.isotropic_table([1.0, 30.0], 3)
+    E = np.array([0.2, 0.9, -0.4])
+    A = O.expand_phase(ph, table)[0, 0]
+    sysn = O.GaNi(A, 3)
+    cA, CA = O.spectral_bounds(A, 3)
+    for k in (1, 4, 12):
+        P = H.Problem(3, N, H.phase_material(ph, table), precision=H.HOM_FP32_REFINED)
+        x = P.field()
+        AH, _, st, _ = H.hom_solve(P.h, E, H.SOLVERS[solver], 0.0,
+                                   H.make_opts(fixed_iters=k, inner_form=form), x)
+        assert st["iterations"] == 1 and st["inner_iterations"] == k
+        if solver == "cg":
+            ref = O.cg(sysn, E, fixed_iters=k).x
+        else:
+            ref = O.chebyshev(sysn, E, cA, CA, fixed_iters=k).x
+        assert rel(x.cpu().numpy(), ref) < 2e-5, (k, rel(x.cpu().numpy(), ref))
+        P.close()
+
+
 @pytest.mark.parametrize("N", [(23, 23, 23), (41, 23, 23)])
 def test_potential_inner_cg_exact_integration(N):
     # Ga on the double grid 2N - 1 (45, 81: specialised plans on every axis): the preconditioner
