@@ -289,8 +289,19 @@ void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, con
     const long long C = g.scs / g.n[0];
     const dim3 gs((unsigned)((C + g.TCs0 - 1) / g.TCs0), (unsigned)g.NC, (unsigned)nreq);
     const size_t sms = smem_strided(P.n, g.TCs0p, P.nst);
-    launch_pass(k_strided<T>, gs, g.NTs0, sms, st, S, P, tw, C, C, g.scs, g.TCs0, g.TCs0p, 0,
-                sc, reqs);
+    // a column pass of the NC components along axis 0 (compile-time kernels for the FP32
+    // plans that have them)
+    auto axis0 = [&](int inv) {
+      if constexpr (std::is_same<T, float>::value) {
+        if (pair_plan<T>(P)) {
+          pair_strided_f32(P, inv, S, tw, C, C, g.scs, g.NC, sc, st, reqs, nreq);
+          return;
+        }
+      }
+      launch_pass(k_strided<T>, gs, g.NTs0, sms, st, S, P, tw, C, C, g.scs, g.TCs0, g.TCs0p,
+                  inv, sc, reqs);
+    };
+    axis0(0);
     const dim3 gp((unsigned)((pg.C + kThreads - 1) / kThreads), (unsigned)P.n, (unsigned)nreq);
 #define HOM_PJE(D_, NC_, M_) launch_pass(k_proj_point<T, D_, NC_, M_>, gp, kThreads, 0, st, S, pg, P.n, (T)g.nodes, sc, reqs)
     if (g.D == 2) {
@@ -299,8 +310,7 @@ void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, con
       if (mode == PROJ_EM) HOM_PJE(3, 6, PROJ_EM); else HOM_PJE(3, 6, PROJ_GAMMA);
     }
 #undef HOM_PJE
-    launch_pass(k_strided<T>, gs, g.NTs0, sms, st, S, P, tw, C, C, g.scs, g.TCs0, g.TCs0p, 1,
-                sc, reqs);
+    axis0(1);
     if (prof) prof_mark(KIND_PROJ, st, false);
     launch_counter() += 3;
     return;
