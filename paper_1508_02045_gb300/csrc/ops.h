@@ -111,12 +111,16 @@ void pair_strided2_f32(const AxisPlan& P, int inv, cpx<float>* S, const cpx<floa
                        const Scalars* sc, cudaStream_t st, const ReqDesc<float>* reqs, int nreq);
 // the line passes are specialised for D = 3 and the pre-/post-operators of the FP32 inner
 // solves (CG, Chebyshev) and of plain operator applications
+// D: components of the fields (3: vector fields of a 3-D grid; 6: strain fields of a 3-D
+// grid, for the inner steps of the refinement)
 inline bool pair_line_fwd_has(int D, int pre) {
-  return D == 3 && (pre == PRE_CG || pre == PRE_CG_DOT || pre == PRE_LINEAR);
+  return (D == 3 && (pre == PRE_CG || pre == PRE_CG_DOT || pre == PRE_LINEAR)) ||
+         (D == 6 && (pre == PRE_CG_DOT || pre == PRE_LINEAR));
 }
 inline bool pair_line_inv_has(int D, int post) {
-  return D == 3 && (post == POST_CG || post == POST_CG_FUSED || post == POST_CHEB ||
-                    post == POST_STORE);
+  return (D == 3 && (post == POST_CG || post == POST_CG_FUSED || post == POST_CHEB ||
+                     post == POST_STORE)) ||
+         (D == 6 && (post == POST_CG_FUSED || post == POST_CHEB));
 }
 // returns the number of CTAs (the partials a PRE_CG_DOT pass writes)
 int pair_line_fwd_f32(int D, int pre, const AxisPlan& P, const Fields<float>& f, cpx<float>* S,

@@ -208,10 +208,10 @@ void Ops<T>::line_fwd(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S,
                       Scalars* sc, const OpArgs& args, cudaStream_t st,
                       const ReqDesc<T>* reqs, int nreq, double* partials) {
   if constexpr (std::is_same<T, float>::value) {
-    if (ncomp == g.D && pair_line_fwd_has(g.D, pre) && pair_plan<T>(P)) {
+    if (g.D == 3 && ncomp == g.NC && pair_line_fwd_has(ncomp, pre) && pair_plan<T>(P)) {
       const bool prof = profiling();
       if (prof) prof_mark(KIND_LINE_FWD, st, true);
-      const int nb = pair_line_fwd_f32(g.D, pre, P, f, S, tw, g.nlines, g.scs, mat, sc, args,
+      const int nb = pair_line_fwd_f32(ncomp, pre, P, f, S, tw, g.nlines, g.scs, mat, sc, args,
                                        partials, st, reqs, nreq);
       ++launch_counter();
       if (pre == PRE_CG_DOT) {
@@ -408,11 +408,11 @@ void Ops<T>::line_inv(const PassGeom& g, int post, const cpx<T>* S, const Fields
                       Scalars* sc, const OpArgs& args, double* partials, unsigned* counter,
                       int negate, cudaStream_t st, const ReqDesc<T>* reqs, int nreq) {
   if constexpr (std::is_same<T, float>::value) {
-    if (ncomp == g.D && pair_line_inv_has(g.D, post) && pair_plan<T>(P)) {
+    if (g.D == 3 && ncomp == g.NC && pair_line_inv_has(ncomp, post) && pair_plan<T>(P)) {
       const bool prof = profiling();
       if (prof) prof_mark(KIND_LINE_INV, st, true);
-      pair_line_inv_f32(g.D, post, P, S, f, tw, g.nlines, g.scs, mat, sc, args, partials, counter,
-                        negate, st, reqs, nreq);
+      pair_line_inv_f32(ncomp, post, P, S, f, tw, g.nlines, g.scs, mat, sc, args, partials,
+                        counter, negate, st, reqs, nreq);
       if (prof) prof_mark(KIND_LINE_INV, st, false);
       ++launch_counter();
       return;

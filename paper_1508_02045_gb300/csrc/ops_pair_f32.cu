@@ -46,7 +46,11 @@ cudaError_t pair_prepare_f32(int cap) {
   HOM_SET_SMEM((k_pair_line_fwd<T, 3, PRE_LINEAR, R1_, R2_>));  \
   HOM_SET_SMEM((k_pair_line_inv<T, 3, POST_CG, R1_, R2_>));     \
   HOM_SET_SMEM((k_pair_line_inv<T, 3, POST_CHEB, R1_, R2_>));   \
-  HOM_SET_SMEM((k_pair_line_inv<T, 3, POST_STORE, R1_, R2_>));
+  HOM_SET_SMEM((k_pair_line_inv<T, 3, POST_STORE, R1_, R2_>));  \
+  HOM_SET_SMEM((k_pair_line_fwd<T, 6, PRE_CG_DOT, R1_, R2_>));  \
+  HOM_SET_SMEM((k_pair_line_fwd<T, 6, PRE_LINEAR, R1_, R2_>));  \
+  HOM_SET_SMEM((k_pair_line_inv<T, 6, POST_CG_FUSED, R1_, R2_>)); \
+  HOM_SET_SMEM((k_pair_line_inv<T, 6, POST_CHEB, R1_, R2_>));
   HOM_PAIR_PLANS(HOM_PAIR_SMEM)
 #undef HOM_PAIR_SMEM
 #define HOM_POT_SMEM(R1_, R2_)                                  \
@@ -213,20 +217,28 @@ int pair_line_fwd_f32(int D, int pre, const AxisPlan& P, const Fields<float>& f,
                       const MatView<float>& mat, Scalars* sc, const OpArgs& args,
                       double* partials, cudaStream_t st, const ReqDesc<float>* reqs, int nreq) {
   using T = float;
-  (void)D;  // D = 3 (pair_line_fwd_has)
   const FastDiv fdn = make_fastdiv(P.n);
-#define HOM_PAIR_LF_P(PRE_, R1_, R2_)                                                          \
-  launch_pass(k_pair_line_fwd<T, 3, PRE_, R1_, R2_>, grid, NT, sm, st, f, S, tw, nlines, scs, mat, sc,    \
-                                                             args, fdn, partials, reqs)
+#define HOM_PAIR_LF_P(D_, PRE_, R1_, R2_)                                                      \
+  launch_pass(k_pair_line_fwd<T, D_, PRE_, R1_, R2_>, grid, NT, sm, st, f, S, tw, nlines, scs, mat, sc, \
+              args, fdn, partials, reqs)
 #define HOM_PAIR_LF(R1_, R2_)                                                                  \
   if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
+    if (D == 6) {                                                                              \
+      constexpr int LB = 2 * pair_lbp<6, R2_>();                                               \
+      const dim3 grid((unsigned)((nlines + LB - 1) / LB), 1, (unsigned)nreq);                 \
+      const size_t sm = PairFwdSmem<6, R1_, R2_>::bytes;                                       \
+      constexpr int NT = pair_line_threads<6, R2_>();                                          \
+      if (pre == PRE_CG_DOT) HOM_PAIR_LF_P(6, PRE_CG_DOT, R1_, R2_);                           \
+      else HOM_PAIR_LF_P(6, PRE_LINEAR, R1_, R2_);                                             \
+      return (int)grid.x;                                                                      \
+    }                                                                                          \
     constexpr int LB = 2 * pair_lbp<3, R2_>();                                                 \
     const dim3 grid((unsigned)((nlines + LB - 1) / LB), 1, (unsigned)nreq);                   \
     const size_t sm = PairFwdSmem<3, R1_, R2_>::bytes;                                         \
     constexpr int NT = pair_line_threads<3, R2_>();                                            \
-    if (pre == PRE_CG) HOM_PAIR_LF_P(PRE_CG, R1_, R2_);                                        \
-    else if (pre == PRE_CG_DOT) HOM_PAIR_LF_P(PRE_CG_DOT, R1_, R2_);                           \
-    else HOM_PAIR_LF_P(PRE_LINEAR, R1_, R2_);                                                  \
+    if (pre == PRE_CG) HOM_PAIR_LF_P(3, PRE_CG, R1_, R2_);                                     \
+    else if (pre == PRE_CG_DOT) HOM_PAIR_LF_P(3, PRE_CG_DOT, R1_, R2_);                        \
+    else HOM_PAIR_LF_P(3, PRE_LINEAR, R1_, R2_);                                               \
     return (int)grid.x;                                                                        \
   }
   HOM_PAIR_PLANS(HOM_PAIR_LF)
@@ -241,22 +253,29 @@ void pair_line_inv_f32(int D, int post, const AxisPlan& P, const cpx<float>* S,
                        double* partials, unsigned* counter, int negate, cudaStream_t st,
                        const ReqDesc<float>* reqs, int nreq) {
   using T = float;
-  (void)D;  // D = 3 (pair_line_inv_has)
   const FastDiv fdn = make_fastdiv(P.n);
-#define HOM_PAIR_LI_P(POST_, R1_, R2_)                                                         \
-  launch_pass(k_pair_line_inv<T, 3, POST_, R1_, R2_>, grid, NT, sm, st, S, f, tw, nlines, scs, mat, sc,   \
-                                                               args, partials, counter, negate, \
-                                                               fdn, reqs)
+#define HOM_PAIR_LI_P(D_, POST_, R1_, R2_)                                                     \
+  launch_pass(k_pair_line_inv<T, D_, POST_, R1_, R2_>, grid, NT, sm, st, S, f, tw, nlines, scs, mat, \
+              sc, args, partials, counter, negate, fdn, reqs)
 #define HOM_PAIR_LI(R1_, R2_)                                                                  \
   if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
+    if (D == 6) {                                                                              \
+      constexpr int LB = 2 * pair_lbp<6, R2_>();                                               \
+      const dim3 grid((unsigned)((nlines + LB - 1) / LB), 1, (unsigned)nreq);                 \
+      const size_t sm = PairFwdSmem<6, R1_, R2_>::bytes;                                       \
+      constexpr int NT = pair_line_threads<6, R2_>();                                          \
+      if (post == POST_CG_FUSED) HOM_PAIR_LI_P(6, POST_CG_FUSED, R1_, R2_);                    \
+      else HOM_PAIR_LI_P(6, POST_CHEB, R1_, R2_);                                              \
+      return;                                                                                  \
+    }                                                                                          \
     constexpr int LB = 2 * pair_lbp<3, R2_>();                                                 \
     const dim3 grid((unsigned)((nlines + LB - 1) / LB), 1, (unsigned)nreq);                   \
     const size_t sm = PairFwdSmem<3, R1_, R2_>::bytes;                                         \
     constexpr int NT = pair_line_threads<3, R2_>();                                            \
-    if (post == POST_CG) HOM_PAIR_LI_P(POST_CG, R1_, R2_);                                     \
-    else if (post == POST_CG_FUSED) HOM_PAIR_LI_P(POST_CG_FUSED, R1_, R2_);                    \
-    else if (post == POST_CHEB) HOM_PAIR_LI_P(POST_CHEB, R1_, R2_);                            \
-    else HOM_PAIR_LI_P(POST_STORE, R1_, R2_);                                                  \
+    if (post == POST_CG) HOM_PAIR_LI_P(3, POST_CG, R1_, R2_);                                  \
+    else if (post == POST_CG_FUSED) HOM_PAIR_LI_P(3, POST_CG_FUSED, R1_, R2_);                 \
+    else if (post == POST_CHEB) HOM_PAIR_LI_P(3, POST_CHEB, R1_, R2_);                         \
+    else HOM_PAIR_LI_P(3, POST_STORE, R1_, R2_);                                               \
     return;                                                                                    \
   }
   HOM_PAIR_PLANS(HOM_PAIR_LI)

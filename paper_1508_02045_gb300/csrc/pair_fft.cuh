@@ -454,8 +454,8 @@ __host__ __device__ constexpr int pair_line_threads() {
 // n twiddles; the D x LBP complex lines, which the pre-operator first fills with the D real
 // tiles of LB x n nodes, component a at raw0 + a rstride + s_a where s_a (< 4) is the position
 // of the tile's first node within its 16-byte segment of the field, so that aligned 16-byte
-// vectors of the field are aligned in shared memory too (the tiles end at most 20 floats past
-// the complex lines); then a phase table of up to kPairTab entries. The whole stays within
+// vectors of the field are aligned in shared memory too (the tiles end at most 8 D - 4 floats
+// past the complex lines); then a phase table of up to kPairTab entries. The whole stays within
 // 48 KiB for the 243-point plans, so that four CTAs fit the SM's 196 KiB shared-memory
 // configuration: a larger one leaves the kernels that follow with less L1 (a 228 KiB line_fwd
 // was measured to slow the next line_inv pass by a third).
@@ -465,9 +465,10 @@ struct PairFwdSmem {
   static constexpr int n = R1 * R2, LBP = pair_lbp<D, R2>(), ntile = 2 * LBP * n;
   static constexpr int raw0 = (2 * n + 3) / 4 * 4;
   static constexpr int rstride = (ntile + 3) / 4 * 4 + 4;
-  static constexpr int tab = (2 * n + D * ntile + 20 + 3) / 4 * 4;
+  static constexpr int slack = 8 * D - 4;
+  static constexpr int tab = (2 * n + D * ntile + slack + 3) / 4 * 4;
   static constexpr int bytes = 4 * (tab + kPairTab);
-  static_assert(raw0 + (D - 1) * rstride + 3 + ntile <= 2 * n + D * ntile + 20,
+  static_assert(raw0 + (D - 1) * rstride + 3 + ntile <= 2 * n + D * ntile + slack,
                 "raw tiles overrun the line buffer's slack");
 };
 
@@ -735,7 +736,7 @@ k_pair_line_inv(const cpx<T>* S, Fields<T> f, const cpx<T>* __restrict__ twg, lo
   DotAcc<T> dacc;
   // Chebyshev and fused CG read three operands a node: smaller batches keep them within the
   // register budget
-  line_post_from_smem<T, D, POST, (POST == POST_CHEB || POST == POST_CG_FUSED) ? 2 : 4, n>(f, n, n, LBP, D, l0, LB, nlines, fdn,
+  line_post_from_smem<T, D, POST, (D > 3) ? 1 : ((POST == POST_CHEB || POST == POST_CG_FUSED) ? 2 : 4), n>(f, n, n, LBP, D, l0, LB, nlines, fdn,
                                                             mat, sc, args, negate, dacc);
   if (partials == nullptr) return;
   double acc[1] = {dacc.value()};
