@@ -134,6 +134,24 @@ def test_fp32_inner_iterates_follow_the_algorithms(solver, form):
         P.close()
 
 
+@pytest.mark.parametrize("N", [(161, 45, 63), (175, 63, 45), (189, 45, 81), (135, 81, 45),
+                               (405, 45, 45), (45, 45, 243), (45, 45, 405), (45, 63, 175),
+                               (63, 45, 189), (45, 45, 161), (45, 81, 135)])
+def test_potential_inner_iterates_on_every_specialised_plan(N):
+    # the nine two-stage FP32 plans (27x9, 27x15, 27x3, 15x9, 15x3, 23x7, 21x3, 21x9, 25x7) on
+    # axis 0 and on the contiguous axis, and the plans of 45, 63 and 81 on axis 1: four inner
+    # CG steps in potential coordinates against the oracle's Algorithm 2 after four steps
+    ph, table = spheres(N, 12, vf=0.2)
+    E = np.array([0.6, -0.3, 0.74])
+    sysn = O.GaNi(O.expand_phase(ph, table)[0, 0], 3)
+    P = H.Problem(3, N, H.phase_material(ph, table), precision=H.HOM_FP32_REFINED)
+    x = P.field()
+    H.hom_solve(P.h, E, H.HOM_CG, 0.0, H.make_opts(fixed_iters=4), x)
+    ref = O.cg(sysn, E, fixed_iters=4).x
+    assert rel(x.cpu().numpy(), ref) < 2e-5
+    P.close()
+
+
 @pytest.mark.parametrize("N", [(23, 23, 23), (41, 23, 23)])
 def test_potential_inner_cg_exact_integration(N):
     # Ga on the double grid 2N - 1 (45, 81: specialised plans on every axis): the preconditioner
