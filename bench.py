@@ -332,8 +332,11 @@ def measure_fp64_peak(H, local):
 # DRAM bytes (read + write) of one launch of the dominant kernels of the 243^3 CG steps, from
 # one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum on GB300; other kernels and
 # grids have no capture (null)
-NCU_TRAFFIC = {("fp64", "strided"): 650.4e6, ("fp32", "line_fwd"): 643.2e6,
-               ("fp32", "line_inv"): 987.0e6}
+# DRAM bytes read + written per launch at 243^3 (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of the kernels as they are now; profiles/ gives the commands)
+NCU_TRAFFIC = {("fp64", "strided"): 650.8e6, ("fp32", "line_fwd"): 644.0e6,
+               ("fp32", "line_inv"): 984.8e6, ("fp32", "pot_inv"): 342.6e6,
+               ("fp32", "pot_line"): 300.9e6, ("fp32", "pot_fwd"): 199.0e6}
 
 
 def ncu_traffic(precision, kind):
