@@ -31,7 +31,7 @@
 
 namespace hom {
 
-// 1 / |k|^2 (0 at k = 0) and the Hermitian weight of a half-spectrum column
+// 1 / |k|^2 of an integer |k|^2 (0 at k = 0)
 __device__ __forceinline__ float pot_inv_kk(int kk) { return kk > 0 ? 1.0f / (float)kk : 0.0f; }
 
 // Tiles of the two axis-0 kernels: TC columns of the half spectrum, all n rows, row-major in

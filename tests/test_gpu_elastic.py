@@ -253,3 +253,32 @@ def test_elastic_batch_equals_solo():
         H.hom_batch_destroy(B)
         for P in probs:
             P.close()
+
+
+@pytest.mark.parametrize("solver", ["cg", "chebyshev"])
+def test_elastic_refined_batch_equals_solo(solver):
+    # FP32-refined strain problems of one shape advanced together (hom_batch, graph replays)
+    # end exactly where their solo solves end
+    N = (45, 45, 45)
+    Es = [np.array([1.0, 0, 0, 0, 0, 0]), np.array([0.2, -0.1, 0.4, 0.3, 0.0, -0.5])]
+    solo = []
+    for k, E in enumerate(Es):
+        P, _, _ = refined_problem(N, seed=7 + k)
+        solo.append(H.hom_solve(P.h, E, H.SOLVERS[solver], 1e-9)[:3])
+        P.close()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        probs = [refined_problem(N, seed=7 + k)[0] for k in range(len(Es))]
+        for P, E in zip(probs, Es):
+            H.hom_solve_begin(P.h, E, H.SOLVERS[solver], 1e-9, None)
+        B = H.hom_batch_create([P.h for P in probs])
+        for _ in range(1000):
+            if H.hom_batch_iterate(B, 8, use_graph=True, poll=True):
+                break
+        for P, (AH, _, st) in zip(probs, solo):
+            AHb, _, stb, _ = H.hom_solve_end(P.h, 6)
+            assert stb["converged"] and AHb == AH
+            assert stb["inner_iterations"] == st["inner_iterations"]
+        H.hom_batch_destroy(B)
+        for P in probs:
+            P.close()
