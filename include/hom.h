@@ -325,7 +325,7 @@ typedef struct {
   hom_material material;   /* host data only; copied at submit                              */
   int integration;
   int precision;
-  double E[3];
+  double E[6];             /* nc entries: d, or d (d + 1) / 2 for a stiffness material      */
   int solver;
   double tol;
   hom_opts opts;
@@ -335,18 +335,19 @@ typedef struct {
   long long id;
   int status;              /* hom_solve status of the request                              */
   double AH_EE;            /* (A_H E, E)                                                    */
-  double flux[3];
+  double flux[6];          /* nc entries                                                    */
   hom_stats stats;
   double latency_ms;       /* submit -> finished, host wall clock                           */
   double queue_ms;         /* submit -> admitted                                            */
 } hom_result;
 
-/* A continuous-batching solve server on one stream (NULL: the server creates its own
- * non-blocking stream, since CUDA graphs cannot be captured on the legacy default stream). Requests are admitted in arrival order
- * while their estimated device memory fits hbm_budget_bytes (at least one is always admitted),
- * grouped into buckets of equal grid, integration, precision and solver with up to max_batch
- * slots each, and advanced together: one launch per pass and bucket (captured CUDA graphs of
- * the batched step), whatever the mix of arrival times. Finished requests free their slot and
+/* A continuous-batching solve server. Requests are admitted in arrival order while their
+ * estimated device memory fits hbm_budget_bytes (at least one is always admitted), grouped into
+ * buckets of equal grid, component count (conductivity or stiffness), integration, precision,
+ * solver and inner form with up to max_batch slots each, and advanced together: one launch per
+ * pass and bucket (captured CUDA graphs of the batched step), whatever the mix of arrival
+ * times. Every bucket runs on a non-blocking stream of its own, so that buckets of different
+ * grids overlap on the device; `stream` is not used. Finished requests free their slot and
  * memory at the step that detects them, and queued ones take their place. */
 int hom_server_create(size_t hbm_budget_bytes, int max_batch, void* stream, hom_server** out);
 /* Queue a request (the coefficient data is copied); *id identifies its result. */

@@ -70,13 +70,13 @@ class hom_stats(ctypes.Structure):
 class hom_request(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("N", ctypes.c_int * 3), ("material", hom_material),
                 ("integration", ctypes.c_int), ("precision", ctypes.c_int),
-                ("E", ctypes.c_double * 3), ("solver", ctypes.c_int), ("tol", ctypes.c_double),
+                ("E", ctypes.c_double * 6), ("solver", ctypes.c_int), ("tol", ctypes.c_double),
                 ("opts", hom_opts)]
 
 
 class hom_result(ctypes.Structure):
     _fields_ = [("id", ctypes.c_longlong), ("status", ctypes.c_int), ("AH_EE", ctypes.c_double),
-                ("flux", ctypes.c_double * 3), ("stats", hom_stats),
+                ("flux", ctypes.c_double * 6), ("stats", hom_stats),
                 ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
 
 

@@ -323,9 +323,15 @@ struct ServerReq {
   Clock::time_point t_submit, t_admit;
 };
 
-// a bucket: same grid, integration, precision and solver; fixed-capacity slots
+// components of a request's fields: d, or d (d + 1) / 2 for a stiffness material
+int req_nc(const hom_request& r) {
+  return r.material.kind == HOM_A_STIFFNESS ? r.d * (r.d + 1) / 2 : r.d;
+}
+
+// a bucket: same grid, component count, integration, precision and solver; fixed-capacity
+// slots
 struct Bucket {
-  int d = 0, M[3] = {1, 1, 1}, N[3] = {1, 1, 1};
+  int d = 0, nc = 0, M[3] = {1, 1, 1}, N[3] = {1, 1, 1};
   int integration = 0, precision = 0, solver = 0;
   int cap = 0;
   std::vector<ServerReq*> slots;
@@ -371,6 +377,7 @@ void bucket_release(Bucket& b) {
 // grid, as hom_create makes it), descriptor arrays and stream
 int bucket_init(Bucket& b, const hom_request& r, const int* M, int cap) {
   b.d = r.d;
+  b.nc = req_nc(r);
   for (int a = 0; a < 3; ++a) {
     b.M[a] = a < r.d ? M[a] : 1;
     b.N[a] = a < r.d ? r.N[a] : 1;
@@ -383,7 +390,7 @@ int bucket_init(Bucket& b, const hom_request& r, const int* M, int cap) {
   b.slots.assign(b.cap, nullptr);
   b.nodes = 1;
   for (int a = 0; a < r.d; ++a) b.nodes *= M[a];
-  b.red_grid = (int)std::min<long long>((b.nodes * b.d + kThreads - 1) / kThreads, 152 * 8);
+  b.red_grid = (int)std::min<long long>((b.nodes * b.nc + kThreads - 1) / kThreads, 152 * 8);
   int rc;
   if ((rc = alloc((void**)&b.d64, sizeof(ReqDesc<double>) * b.cap)) ||
       (rc = alloc((void**)&b.d32, sizeof(ReqDesc<float>) * b.cap)) ||
@@ -398,20 +405,21 @@ int bucket_init(Bucket& b, const hom_request& r, const int* M, int cap) {
     b.stream = nullptr;
     return HOM_ERR_CUDA;
   }
-  const PlanChoice p64 = plan_choice(8, b.d, b.M, b.N);
+  const PlanChoice p64 = plan_choice(8, b.d, b.M, b.N, b.nc);
   b.e64 = new Engine<double>();
-  if ((rc = b.e64->init(b.d, b.M, b.N, p64.budget, p64.rmax, p64.threads, p64.two_line)))
+  if ((rc = b.e64->init(b.d, b.M, b.N, p64.budget, p64.rmax, p64.threads, p64.two_line, b.nc)))
     return rc;
   if (b.precision == HOM_FP32_REFINED) {
-    const PlanChoice p32 = plan_choice(4, b.d, b.M, b.N);
+    const PlanChoice p32 = plan_choice(4, b.d, b.M, b.N, b.nc);
     b.e32 = new Engine<float>();
-    if ((rc = b.e32->init(b.d, b.M, b.N, p32.budget, p32.rmax, p32.threads, p32.two_line)))
+    if ((rc = b.e32->init(b.d, b.M, b.N, p32.budget, p32.rmax, p32.threads, p32.two_line, b.nc)))
       return rc;
   }
   return HOM_OK;
 }
 
 size_t estimate_bytes(const hom_request& r) {
+  const int nc = req_nc(r);
   long long nodes = 1;
   for (int a = 0; a < r.d; ++a)
     nodes *= (r.integration == HOM_EXACT) ? (r.material.M[a] > 0 ? r.material.M[a] : 2 * r.N[a] - 1)
@@ -420,10 +428,10 @@ size_t estimate_bytes(const hom_request& r) {
                                     ? (r.material.M[r.d - 1] > 0 ? r.material.M[r.d - 1] : 2 * r.N[r.d - 1] - 1)
                                     : r.N[r.d - 1]);
   const int nlast = (int)(nodes / nl);
-  size_t b = sizeof(double) * 5 * r.d * nodes;                     // solver vectors
-  b += sizeof(double) * 2 * r.d * nl * ((nlast + 1) / 2);          // half spectrum
+  size_t b = sizeof(double) * 5 * nc * nodes;                      // solver vectors
+  b += sizeof(double) * 2 * nc * nl * ((nlast + 1) / 2);           // half spectrum
   b += nodes * 2 + sizeof(double) * nodes;                         // phases / coefficient field
-  if (r.precision == HOM_FP32_REFINED) b += sizeof(float) * (4 * r.d + 1) * nodes;
+  if (r.precision == HOM_FP32_REFINED) b += sizeof(float) * (4 * nc + 1) * nodes;
   const long long maxit = r.opts.fixed_iters > 0 ? r.opts.fixed_iters
                                                  : (r.opts.maxit > 0 ? r.opts.maxit : 100000);
   b += sizeof(double) * (size_t)std::min<long long>(maxit + 2, kHistMax);  // iteration history
@@ -448,8 +456,9 @@ namespace {
 int find_bucket(hom_server* S, const hom_request& r, const int* M) {
   for (size_t i = 0; i < S->buckets.size(); ++i) {
     const Bucket& b = S->buckets[i];
-    bool same = b.d == r.d && b.integration == r.integration && b.precision == r.precision &&
-                b.solver == r.solver && b.inner_form == r.opts.inner_form;
+    bool same = b.d == r.d && b.nc == req_nc(r) && b.integration == r.integration &&
+                b.precision == r.precision && b.solver == r.solver &&
+                b.inner_form == r.opts.inner_form;
     for (int a = 0; a < r.d && same; ++a) same = b.M[a] == M[a] && b.N[a] == r.N[a];
     if (same) return (int)i;
   }
@@ -624,7 +633,6 @@ extern "C" int hom_server_create(size_t hbm_budget_bytes, int max_batch, void* s
 extern "C" int hom_server_submit(hom_server* S, const hom_request* req, long long* id) {
   if (!S || !req || !id) return HOM_ERR_INVALID;
   if (req->d != 2 && req->d != 3) return HOM_ERR_INVALID;
-  if (req->material.kind == HOM_A_STIFFNESS) return HOM_ERR_UNSUPPORTED;  // E, flux: d entries
   long long nodes = 1;
   for (int a = 0; a < req->d; ++a) {
     if (req->N[a] < 3 || req->N[a] % 2 == 0) return HOM_ERR_INVALID;
@@ -639,9 +647,14 @@ extern "C" int hom_server_submit(hom_server* S, const hom_request* req, long lon
     delete r;
     return HOM_ERR_INVALID;  // the server keeps host copies until admission
   }
-  if (m.kind == HOM_A_PHASE) {
+  if (m.kind == HOM_A_PHASE || m.kind == HOM_A_STIFFNESS) {
+    const int nc = req_nc(*req);
+    if (!m.table || m.nphase < 1) {
+      delete r;
+      return HOM_ERR_INVALID;
+    }
     r->data.assign((const unsigned char*)m.data, (const unsigned char*)m.data + nodes * m.index_bytes);
-    r->table.assign(m.table, m.table + (size_t)m.nphase * req->d * req->d);
+    r->table.assign(m.table, m.table + (size_t)m.nphase * nc * nc);
   } else if (m.kind == HOM_A_SCALAR) {
     r->data.assign((const unsigned char*)m.data, (const unsigned char*)m.data + nodes * sizeof(double));
   } else {

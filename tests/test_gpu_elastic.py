@@ -282,3 +282,43 @@ def test_elastic_refined_batch_equals_solo(solver):
         H.hom_batch_destroy(B)
         for P in probs:
             P.close()
+
+
+def test_server_serves_strain_problems_with_vector_ones():
+    # stiffness requests (FP64 CG and Chebyshev, FP32-refined CG) in flight with a conductivity
+    # request: each result equals its solo solve; E and the flux carry six entries
+    N = (21, 19, 17)
+    plan = []
+    for k, (solver, prec) in enumerate([("cg", H.HOM_FP64), ("chebyshev", H.HOM_FP64),
+                                         ("cg", H.HOM_FP32_REFINED), ("cg", H.HOM_FP64)]):
+        ph = ms.box_phase(N, 0.6)
+        table = random_stiffness_table(2, 3, seed=30 + k, scale=(1.0, 12.0))
+        E = ms.random_field((6,), 40 + k)
+        plan.append((H.stiffness_material(ph, table), E, solver, prec))
+    phc = ms.box_phase(N, 0.5)
+    conductivity = (H.phase_material(phc, ms.isotropic_table([1.0, 20.0], 3)),
+                    np.array([1.0, 0.0, 0.0]), "cg", H.HOM_FP64)
+    S = H.hom_server_create(1 << 30, max_batch=2)
+    ids = {}
+    for i, (mat, E, solver, prec) in enumerate(plan + [conductivity]):
+        req = H.make_request(3, N, mat, E, H.SOLVERS[solver], 1e-9, precision=prec)
+        ids[H.hom_server_submit(S, req)] = i
+    results = {}
+    for _ in range(20000):
+        H.hom_server_step(S, 4)
+        for r in H.hom_server_poll(S):
+            results[r["id"]] = r
+        if len(results) == len(ids):
+            break
+    H.hom_server_destroy(S)
+    assert len(results) == len(ids)
+    for rid, r in results.items():
+        mat, E, solver, prec = (plan + [conductivity])[ids[rid]]
+        assert r["status"] == H.HOM_OK
+        P = H.Problem(3, N, mat, precision=prec)
+        AH, flux, st, _ = H.hom_solve(P.h, E, H.SOLVERS[solver], 1e-9)
+        P.close()
+        assert r["stats"]["iterations"] == st["iterations"]
+        assert abs(r["AH_EE"] - AH) <= 1e-14 * abs(AH)
+        nc = len(E)
+        np.testing.assert_allclose(r["flux"][:nc], flux[:nc], rtol=1e-13, atol=1e-14)
