@@ -269,16 +269,15 @@ __device__ __forceinline__ void reg_stage(Loc<T> in, Loc<T> out, int n, int p, i
   }
 }
 
-// Dispatch of one stage on the runtime radix (not inlined: one copy per precision/direction).
+// Dispatch of one stage on the runtime radix. The radices of the common plans (3, 5, 7, 9) are
+// expanded in the calling kernel; the others go through one out-of-line copy per
+// precision/direction (a call, whose argument passing and register saves cost local-memory
+// traffic, but keeps every kernel's code and register budget small).
 template <typename T, bool INV>
-__device__ __noinline__ void reg_stage_any(int R, Loc<T> in, Loc<T> out, int n, int p, int nl,
+__device__ __noinline__ void reg_stage_big(int R, Loc<T> in, Loc<T> out, int n, int p, int nl,
                                            bool colmajor, int tw_base, FastDiv fm, FastDiv fp,
                                            int cj) {
   switch (R) {
-    case 3: reg_stage<T, 3, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
-    case 5: reg_stage<T, 5, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
-    case 7: reg_stage<T, 7, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
-    case 9: reg_stage<T, 9, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
     case 11: reg_stage<T, 11, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
     case 13: reg_stage<T, 13, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
     case 15: reg_stage<T, 15, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
@@ -291,6 +290,19 @@ __device__ __noinline__ void reg_stage_any(int R, Loc<T> in, Loc<T> out, int n, 
     case 29: reg_stage<T, 29, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
     case 31: reg_stage<T, 31, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
     default: break;
+  }
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void reg_stage_any(int R, Loc<T> in, Loc<T> out, int n, int p, int nl,
+                                              bool colmajor, int tw_base, FastDiv fm, FastDiv fp,
+                                              int cj) {
+  switch (R) {
+    case 3: reg_stage<T, 3, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    case 5: reg_stage<T, 5, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    case 7: reg_stage<T, 7, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    case 9: reg_stage<T, 9, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    default: reg_stage_big<T, INV>(R, in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
   }
 }
 
