@@ -293,7 +293,9 @@ __device__ __noinline__ void reg_stage_big(int R, Loc<T> in, Loc<T> out, int n, 
   }
 }
 
-template <typename T, bool INV>
+// SMALLR: the caller's plan has no radix above 9 (checked on the host before the launch), so
+// the kernel carries no out-of-line path at all (no call sites, lighter register allocation)
+template <typename T, bool INV, bool SMALLR = false>
 __device__ __forceinline__ void reg_stage_any(int R, Loc<T> in, Loc<T> out, int n, int p, int nl,
                                               bool colmajor, int tw_base, FastDiv fm, FastDiv fp,
                                               int cj) {
@@ -302,23 +304,26 @@ __device__ __forceinline__ void reg_stage_any(int R, Loc<T> in, Loc<T> out, int 
     case 5: reg_stage<T, 5, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
     case 7: reg_stage<T, 7, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
     case 9: reg_stage<T, 9, INV>(in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
-    default: reg_stage_big<T, INV>(R, in, out, n, p, nl, colmajor, tw_base, fm, fp, cj); break;
+    default:
+      if constexpr (!SMALLR)
+        reg_stage_big<T, INV>(R, in, out, n, p, nl, colmajor, tw_base, fm, fp, cj);
+      break;
   }
 }
 
 // stage st of plan P (an inverse transform is conj(F(conj .)) over the whole sequence of stages
 // 0 .. nst - 1: the first stage conjugates what it loads, the last what it stores, the ones
 // between neither)
-template <typename T>
+template <typename T, bool SMALLR = false>
 __device__ __forceinline__ void stage_any(bool inv, const AxisPlan* P, int st, Loc<T> in,
                                           Loc<T> out, int nl, bool colmajor, int tw_base) {
   const int cj = (st == 0 ? 1 : 0) | (st == P->nst - 1 ? 2 : 0);
   if (inv)
-    reg_stage_any<T, true>(P->radix[st], in, out, P->n, P->pprev[st], nl, colmajor, tw_base,
-                           P->fdm[st], P->fdp[st], cj);
+    reg_stage_any<T, true, SMALLR>(P->radix[st], in, out, P->n, P->pprev[st], nl, colmajor,
+                                   tw_base, P->fdm[st], P->fdp[st], cj);
   else
-    reg_stage_any<T, false>(P->radix[st], in, out, P->n, P->pprev[st], nl, colmajor, tw_base,
-                            P->fdm[st], P->fdp[st], cj);
+    reg_stage_any<T, false, SMALLR>(P->radix[st], in, out, P->n, P->pprev[st], nl, colmajor,
+                                    tw_base, P->fdm[st], P->fdp[st], cj);
 }
 
 // shared-memory location helpers
@@ -359,13 +364,14 @@ __device__ __forceinline__ int reg_lines2(int a, int b, const AxisPlan* P, int n
 // All stages of one axis on nl lines in shared memory (element j of line l at a + l*ls + j*es,
 // a and b element offsets of the two ping-pong buffers); returns the offset of the buffer that
 // holds the natural-order result. Ends with a __syncthreads().
-template <typename T>
+template <typename T, bool SMALLR = false>
 __device__ __forceinline__ int reg_lines(int a, int b, const AxisPlan* P, int nl, int ls, int es,
                                          bool colmajor, bool inv, int tw_base) {
   const int nst = P->nst;
 #pragma unroll 1
   for (int st = 0; st < nst; ++st) {
-    stage_any<T>(inv, P, st, sloc<T>(a, ls, es), sloc<T>(b, ls, es), nl, colmajor, tw_base);
+    stage_any<T, SMALLR>(inv, P, st, sloc<T>(a, ls, es), sloc<T>(b, ls, es), nl, colmajor,
+                         tw_base);
     __syncthreads();
     const int t = a;
     a = b;
@@ -379,27 +385,27 @@ __device__ __forceinline__ int reg_lines(int a, int b, const AxisPlan* P, int nl
 // ping-pong between the shared-memory buffers at a and b (element (l, j) at l_in + l_out*cstr +
 // j*TCp), and the last stage stores straight back; a single-stage plan reads and writes the
 // tile directly (each butterfly is then a whole column). No barrier after the final stores.
-template <typename T>
+template <typename T, bool SMALLR = false>
 __device__ __forceinline__ void reg_columns_global(Loc<T> gl, int a, int b, int TCp, int cstr,
                                                    int nli_log, int nl, const AxisPlan* P,
                                                    bool inv) {
   const int nst = P->nst;
   if (nst == 1) {
-    stage_any<T>(inv, P, 0, gl, gl, nl, true, 0);
+    stage_any<T, SMALLR>(inv, P, 0, gl, gl, nl, true, 0);
     return;
   }
-  stage_any<T>(inv, P, 0, gl, sloc2<T>(a, 1, TCp, cstr, nli_log), nl, true, 0);
+  stage_any<T, SMALLR>(inv, P, 0, gl, sloc2<T>(a, 1, TCp, cstr, nli_log), nl, true, 0);
   __syncthreads();
 #pragma unroll 1
   for (int st = 1; st < nst - 1; ++st) {
-    stage_any<T>(inv, P, st, sloc2<T>(a, 1, TCp, cstr, nli_log),
-                 sloc2<T>(b, 1, TCp, cstr, nli_log), nl, true, 0);
+    stage_any<T, SMALLR>(inv, P, st, sloc2<T>(a, 1, TCp, cstr, nli_log),
+                         sloc2<T>(b, 1, TCp, cstr, nli_log), nl, true, 0);
     __syncthreads();
     const int t = a;
     a = b;
     b = t;
   }
-  stage_any<T>(inv, P, nst - 1, sloc2<T>(a, 1, TCp, cstr, nli_log), gl, nl, true, 0);
+  stage_any<T, SMALLR>(inv, P, nst - 1, sloc2<T>(a, 1, TCp, cstr, nli_log), gl, nl, true, 0);
 }
 
 }  // namespace hom

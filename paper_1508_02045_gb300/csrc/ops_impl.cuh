@@ -17,6 +17,14 @@ static bool pair_plan(const AxisPlan& P) {
 }
 
 
+// every radix of plan P at most 9: the FP64 kernels of the CG step and of hom_apply then run
+// their variant without an out-of-line radix path
+static bool small_radices(const AxisPlan& P) {
+  for (int s = 0; s < P.nst; ++s)
+    if (P.radix[s] > 9) return false;
+  return true;
+}
+
 template <typename T>
 cudaError_t Ops<T>::upload_constants() {
   return upload_reg_tables();
@@ -158,6 +166,16 @@ cudaError_t Ops<T>::prepare(int) {
   HOM_SET_SMEM((k_line_fwd<T, 3, PRE_CG_DOT>));
   HOM_SET_SMEM((k_line_inv<T, 2, POST_CG_FUSED>));
   HOM_SET_SMEM((k_line_inv<T, 3, POST_CG_FUSED>));
+  if constexpr (std::is_same<T, double>::value) {
+    // the variants without an out-of-line radix path (plans with radices up to 9)
+    HOM_SET_SMEM((k_line_fwd<T, 3, PRE_CG_DOT, true>));
+    HOM_SET_SMEM((k_line_fwd<T, 3, PRE_LINEAR, true>));
+    HOM_SET_SMEM((k_line_fwd<T, 3, PRE_AFFINE, true>));
+    HOM_SET_SMEM((k_line_inv<T, 3, POST_CG_FUSED, true>));
+    HOM_SET_SMEM((k_line_inv<T, 3, POST_STORE, true>));
+    HOM_SET_SMEM((k_strided<T, true>));
+    HOM_SET_SMEM((k_proj_scalar<T, true>));
+  }
   {
     // elasticity: strain fields of 3 (2-D, the 3-component line kernels above) or 6
     // components (their projection pass is two strided passes around k_proj_point)
@@ -189,6 +207,19 @@ static void line_fwd_d(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S
   const bool prof = profiling();
   if (prof) prof_mark(KIND_LINE_FWD, st, true);
 #define HOM_LF(PRE_) launch_pass(k_line_fwd<T, D, PRE_>, grid, g.NTl, sm, st, f, S, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, reqs)
+#define HOM_LFS(PRE_) launch_pass(k_line_fwd<T, D, PRE_, true>, grid, g.NTl, sm, st, f, S, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, reqs)
+  if constexpr (std::is_same<T, double>::value && D == 3) {
+    if (small_radices(P) &&
+        (pre == PRE_CG_DOT || pre == PRE_LINEAR || pre == PRE_AFFINE)) {
+      if (pre == PRE_CG_DOT) HOM_LFS(PRE_CG_DOT);
+      else if (pre == PRE_LINEAR) HOM_LFS(PRE_LINEAR);
+      else HOM_LFS(PRE_AFFINE);
+      if (prof) prof_mark(KIND_LINE_FWD, st, false);
+      ++launch_counter();
+      return;
+    }
+  }
+#undef HOM_LFS
   switch (pre) {
     case PRE_AFFINE: HOM_LF(PRE_AFFINE); break;
     case PRE_LINEAR: HOM_LF(PRE_LINEAR); break;
@@ -269,7 +300,16 @@ void Ops<T>::strided(const PassGeom& g, int axis, int inv, cpx<T>* S, const Axis
   } else {
     const dim3 grid((unsigned)((C + TC - 1) / TC), (unsigned)batches, (unsigned)nreq);
     const size_t sm = smem_strided(P.n, TCp, P.nst);
-    launch_pass(k_strided<T>, grid, NT, sm, st, S, P, tw, C, es, bs, TC, TCp, inv, sc, reqs);
+    bool done = false;
+    if constexpr (std::is_same<T, double>::value) {
+      if (small_radices(P)) {
+        launch_pass(k_strided<T, true>, grid, NT, sm, st, S, P, tw, C, es, bs, TC, TCp, inv, sc,
+                    reqs);
+        done = true;
+      }
+    }
+    if (!done)
+      launch_pass(k_strided<T>, grid, NT, sm, st, S, P, tw, C, es, bs, TC, TCp, inv, sc, reqs);
   }
   if (prof) prof_mark(KIND_STRIDED, st, false);
   ++launch_counter();
@@ -325,7 +365,16 @@ void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, con
   if (g.D == 3 && mode == PROJ_GAMMA) {
     const dim3 grid((unsigned)((pg.C + g.TCq - 1) / g.TCq), 1, (unsigned)nreq);
     const size_t sm = smem_proj_scalar(P.n, g.TCqp);
-    launch_pass(k_proj_scalar<T>, grid, g.NTq, sm, st, S, P, tw, pg, g.TCq, g.TCqp, sc, reqs);
+    bool done = false;
+    if constexpr (std::is_same<T, double>::value) {
+      if (small_radices(P)) {
+        launch_pass(k_proj_scalar<T, true>, grid, g.NTq, sm, st, S, P, tw, pg, g.TCq, g.TCqp, sc,
+                    reqs);
+        done = true;
+      }
+    }
+    if (!done)
+      launch_pass(k_proj_scalar<T>, grid, g.NTq, sm, st, S, P, tw, pg, g.TCq, g.TCqp, sc, reqs);
     if (prof) prof_mark(KIND_PROJ, st, false);
     ++launch_counter();
     return;
@@ -388,6 +437,17 @@ static void line_inv_d(const PassGeom& g, int post, const cpx<T>* S, const Field
   const bool prof = profiling();
   if (prof) prof_mark(KIND_LINE_INV, st, true);
 #define HOM_LI(POST_) launch_pass(k_line_inv<T, D, POST_>, grid, g.NTl, sm, st, S, f, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, counter, negate, reqs)
+#define HOM_LIS(POST_) launch_pass(k_line_inv<T, D, POST_, true>, grid, g.NTl, sm, st, S, f, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, counter, negate, reqs)
+  if constexpr (std::is_same<T, double>::value && D == 3) {
+    if (small_radices(P) && (post == POST_CG_FUSED || post == POST_STORE)) {
+      if (post == POST_CG_FUSED) HOM_LIS(POST_CG_FUSED);
+      else HOM_LIS(POST_STORE);
+      if (prof) prof_mark(KIND_LINE_INV, st, false);
+      ++launch_counter();
+      return;
+    }
+  }
+#undef HOM_LIS
   switch (post) {
     case POST_RICH: HOM_LI(POST_RICH); break;
     case POST_CG: HOM_LI(POST_CG); break;

@@ -423,7 +423,7 @@ __device__ __forceinline__ void line_pre_to_smem(const Fields<T>& f, int b0, int
   }
 }
 
-template <typename T, int D, int PRE>
+template <typename T, int D, int PRE, bool SMALLR = false>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
 k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
            int ncomp, long long nlines, int LB, LineDiv ld, long long scs, MatView<T> mat,
@@ -450,7 +450,7 @@ k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
   DotAcc<T> dacc;
   line_pre_to_smem<T, D, PRE>(f, b0, n, half, ncomp, l0, LB, nlines, P.fdn, mat, sc, args, &dacc);
   __syncthreads();
-  const int res = reg_lines<T>(b0, b1, &Ps, nlc, n, 1, false, false, 0);
+  const int res = reg_lines<T, SMALLR>(b0, b1, &Ps, nlc, n, 1, false, false, 0);
   for (int idx = threadIdx.x; idx < nlc * nh; idx += blockDim.x) {
     const int lc = fdiv(idx, P.fdnh), k = idx - lc * nh;
     const int a = fdiv(lc, ld.half), pr = lc - a * half;
@@ -475,7 +475,7 @@ k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
 // kColThreads): the first stage reads the rows of the tile straight from the spectrum (a warp
 // takes consecutive columns, so each row segment is one coalesced access) and the last stage
 // writes them back, so the tile crosses shared memory only between stages.
-template <typename T>
+template <typename T, bool SMALLR = false>
 __global__ void __launch_bounds__(kColThreads<T>, 2)
 k_strided(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, long long C, long long es,
           long long bs, int TC, int TCp, int inv, const Scalars* sc,
@@ -495,7 +495,7 @@ k_strided(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, long long C, lo
   const long long c0 = (long long)blockIdx.x * TC;
   const int ncols = (int)min((long long)TC, C - c0);
   const Loc<T> gl = gcols<T>(S + (long long)blockIdx.y * bs + c0, (int)es, 0, -1, ncols);
-  reg_columns_global<T>(gl, n, n + n * TCp, TCp, 0, -1, ncols, &Ps, inv != 0);
+  reg_columns_global<T, SMALLR>(gl, n, n + n * TCp, TCp, 0, -1, ncols, &Ps, inv != 0);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -760,7 +760,7 @@ k_proj_point(cpx<T>* S, ProjGeom g, int n0, T nodes, const Scalars* sc,
   for (int a = 0; a < NC; ++a) p[(long long)a * g.cs] = o[a];
 }
 
-template <typename T>
+template <typename T, bool SMALLR = false>
 __global__ void __launch_bounds__(kColThreads<T>, 2)
 k_proj_scalar(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC,
               int TCp, const Scalars* sc, const ReqDesc<T>* __restrict__ reqs) {
@@ -802,8 +802,8 @@ k_proj_scalar(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g,
   int a = bufA, b = bufB;
 #pragma unroll 1
   for (int st = 0; st < Ps.nst; ++st) {
-    stage_any<T>(false, &Ps, st, sloc2<T>(a, 1, TCp, cstr, tcl), sloc2<T>(b, 1, TCp, cstr, tcl),
-                 nl, true, 0);
+    stage_any<T, SMALLR>(false, &Ps, st, sloc2<T>(a, 1, TCp, cstr, tcl),
+                         sloc2<T>(b, 1, TCp, cstr, tcl), nl, true, 0);
     __syncthreads();
     const int t = a;
     a = b;
@@ -827,8 +827,8 @@ k_proj_scalar(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g,
   __syncthreads();
 #pragma unroll 1
   for (int st = 0; st < Ps.nst; ++st) {
-    stage_any<T>(true, &Ps, st, sloc2<T>(a, 1, TCp, cstr, tcl), sloc2<T>(b, 1, TCp, cstr, tcl),
-                 nl, true, 0);
+    stage_any<T, SMALLR>(true, &Ps, st, sloc2<T>(a, 1, TCp, cstr, tcl),
+                         sloc2<T>(b, 1, TCp, cstr, tcl), nl, true, 0);
     __syncthreads();
     const int t = a;
     a = b;
@@ -1061,7 +1061,7 @@ __device__ __forceinline__ void line_inv_finish(Scalars* sc, double tot0, double
 // ---------------------------------------------------------------------------------------
 // line_inv: inverse real DFT of the contiguous axis + post-operator
 // ---------------------------------------------------------------------------------------
-template <typename T, int D, int POST>
+template <typename T, int D, int POST, bool SMALLR = false>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
 k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ twg,
            int ncomp, long long nlines, int LB, LineDiv ld, long long scs, MatView<T> mat,
@@ -1115,7 +1115,7 @@ k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ 
     }
   }
   __syncthreads();
-  const int res = reg_lines<T>(b0, b1, &Ps, nlc, n, 1, false, true, 0);
+  const int res = reg_lines<T, SMALLR>(b0, b1, &Ps, nlc, n, 1, false, true, 0);
 
   DotAcc<T> dacc;
   line_post_from_smem<T, D, POST>(f, res, n, half, ncomp, l0, LB, nlines, P.fdn, mat, sc, args,
