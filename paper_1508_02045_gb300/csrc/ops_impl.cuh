@@ -175,6 +175,11 @@ cudaError_t Ops<T>::prepare(int) {
     HOM_SET_SMEM((k_line_inv<T, 3, POST_STORE, true>));
     HOM_SET_SMEM((k_strided<T, true>));
     HOM_SET_SMEM((k_proj_scalar<T, true>));
+    HOM_SET_SMEM((k_line_fwd<T, 6, PRE_CG_DOT, true>));
+    HOM_SET_SMEM((k_line_fwd<T, 6, PRE_LINEAR, true>));
+    HOM_SET_SMEM((k_line_fwd<T, 6, PRE_AFFINE, true>));
+    HOM_SET_SMEM((k_line_inv<T, 6, POST_CG_FUSED, true>));
+    HOM_SET_SMEM((k_line_inv<T, 6, POST_STORE, true>));
   }
   {
     // elasticity: strain fields of 3 (2-D, the 3-component line kernels above) or 6
@@ -208,7 +213,7 @@ static void line_fwd_d(const PassGeom& g, int pre, const Fields<T>& f, cpx<T>* S
   if (prof) prof_mark(KIND_LINE_FWD, st, true);
 #define HOM_LF(PRE_) launch_pass(k_line_fwd<T, D, PRE_>, grid, g.NTl, sm, st, f, S, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, reqs)
 #define HOM_LFS(PRE_) launch_pass(k_line_fwd<T, D, PRE_, true>, grid, g.NTl, sm, st, f, S, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, reqs)
-  if constexpr (std::is_same<T, double>::value && D == 3) {
+  if constexpr (std::is_same<T, double>::value && (D == 3 || D == 6)) {
     if (small_radices(P) &&
         (pre == PRE_CG_DOT || pre == PRE_LINEAR || pre == PRE_AFFINE)) {
       if (pre == PRE_CG_DOT) HOM_LFS(PRE_CG_DOT);
@@ -337,6 +342,12 @@ void Ops<T>::proj(const PassGeom& g, int mode, cpx<T>* S, const AxisPlan& P, con
           pair_strided_f32(P, inv, S, tw, C, C, g.scs, g.NC, sc, st, reqs, nreq);
           return;
         }
+      } else {
+        if (small_radices(P)) {
+          launch_pass(k_strided<T, true>, gs, g.NTs0, sms, st, S, P, tw, C, C, g.scs, g.TCs0,
+                      g.TCs0p, inv, sc, reqs);
+          return;
+        }
       }
       launch_pass(k_strided<T>, gs, g.NTs0, sms, st, S, P, tw, C, C, g.scs, g.TCs0, g.TCs0p,
                   inv, sc, reqs);
@@ -438,7 +449,7 @@ static void line_inv_d(const PassGeom& g, int post, const cpx<T>* S, const Field
   if (prof) prof_mark(KIND_LINE_INV, st, true);
 #define HOM_LI(POST_) launch_pass(k_line_inv<T, D, POST_>, grid, g.NTl, sm, st, S, f, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, counter, negate, reqs)
 #define HOM_LIS(POST_) launch_pass(k_line_inv<T, D, POST_, true>, grid, g.NTl, sm, st, S, f, P, tw, ncomp, g.nlines, g.LB, LineDiv{make_fastdiv(g.LB), make_fastdiv(g.LB / 2)}, g.scs, mat, sc, args, partials, counter, negate, reqs)
-  if constexpr (std::is_same<T, double>::value && D == 3) {
+  if constexpr (std::is_same<T, double>::value && (D == 3 || D == 6)) {
     if (small_radices(P) && (post == POST_CG_FUSED || post == POST_STORE)) {
       if (post == POST_CG_FUSED) HOM_LIS(POST_CG_FUSED);
       else HOM_LIS(POST_STORE);
