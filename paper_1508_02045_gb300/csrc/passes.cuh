@@ -424,7 +424,7 @@ __device__ __forceinline__ void line_pre_to_smem(const Fields<T>& f, int b0, int
 }
 
 template <typename T, int D, int PRE, bool SMALLR = false>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
+__global__ void __launch_bounds__(kThreads, SMALLR ? 3 : kMinBlocks<T>)
 k_line_fwd(Fields<T> f, cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg,
            int ncomp, long long nlines, int LB, LineDiv ld, long long scs, MatView<T> mat,
            Scalars* sc, OpArgs args, double* partials, const ReqDesc<T>* __restrict__ reqs) {
@@ -761,7 +761,7 @@ k_proj_point(cpx<T>* S, ProjGeom g, int n0, T nodes, const Scalars* sc,
 }
 
 template <typename T, bool SMALLR = false>
-__global__ void __launch_bounds__(kColThreads<T>, 2)
+__global__ void __launch_bounds__(kColThreads<T>, SMALLR ? 3 : 2)
 k_proj_scalar(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g, int TC,
               int TCp, const Scalars* sc, const ReqDesc<T>* __restrict__ reqs) {
   wait_prior_grid();
@@ -1062,7 +1062,7 @@ __device__ __forceinline__ void line_inv_finish(Scalars* sc, double tot0, double
 // line_inv: inverse real DFT of the contiguous axis + post-operator
 // ---------------------------------------------------------------------------------------
 template <typename T, int D, int POST, bool SMALLR = false>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
+__global__ void __launch_bounds__(kThreads, SMALLR ? 3 : kMinBlocks<T>)
 k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ twg,
            int ncomp, long long nlines, int LB, LineDiv ld, long long scs, MatView<T> mat,
            Scalars* sc, OpArgs args, double* partials, unsigned* counter, int negate,
