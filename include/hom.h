@@ -56,9 +56,12 @@ typedef enum {
   HOM_ERR_UNSUPPORTED = 3,    /* e.g. Eyre-Milton with exact integration (Section 3.4)     */
   HOM_ERR_NOT_CONVERGED = 4,  /* iteration limit reached; results are still written        */
   HOM_ERR_CUDA = 5,           /* a CUDA call failed                                        */
-  HOM_ERR_TIMEOUT = 6,        /* reserved: no entry point waits on the device (the grid
-                                 reductions take a completion ticket and never spin), so
-                                 none returns it                                           */
+  HOM_ERR_TIMEOUT = 6,        /* a device wait ran out: the FP32 strided pass on TMA-staged
+                                 tiles waits for each tile's copy at most ~1 s of SM clock,
+                                 then counts the failure and stops its CTA; hom_solve_end
+                                 (and hom_solve) return this code when the count since the
+                                 last check is not zero. The grid reductions take a
+                                 completion ticket and never wait.                          */
   HOM_ERR_SCRATCH = 7         /* problem larger than the static scratch of hom_apply_static */
 } hom_status;
 
@@ -403,6 +406,13 @@ int hom_measure_fp64(int kind, int iters, void* stream, double* ms, double* ops)
  * the entry point that needed it frees what it had allocated and returns HOM_ERR_OOM. The
  * failure fires once; n < 0 disarms. Process-wide. */
 int hom_debug_fail_alloc(int n);
+
+/* Testing hook (the paper has no counterpart): on != 0 makes every TMA-staged strided pass
+ * launched from now on wait for 16 bytes more than its tile copies deliver, so that each of
+ * its waits runs out after ~1 s of SM clock; the CTAs stop, the copies that were issued land,
+ * and the next hom_solve_end returns HOM_ERR_TIMEOUT. The results of such a solve are
+ * meaningless; on = 0 restores normal operation. Process-wide. */
+int hom_debug_tma_stall(int on);
 
 /* Free everything the handle owns. NULL is accepted. */
 void hom_destroy(hom_problem* P);

@@ -38,7 +38,7 @@ EXPORTED = ["hom_create", "hom_grid", "hom_bounds", "hom_apply", "hom_solve", "h
             "hom_batch_destroy", "hom_server_create", "hom_server_submit", "hom_server_step",
             "hom_server_poll", "hom_server_status", "hom_server_destroy", "hom_autotune",
             "hom_solve_history", "hom_solve_current", "hom_solve_nonconformity", "hom_restrict",
-            "hom_measure_fp64", "hom_debug_fail_alloc", "hom_set_plan"]
+            "hom_measure_fp64", "hom_debug_fail_alloc", "hom_debug_tma_stall", "hom_set_plan"]
 PASS_KINDS = ["line_fwd", "strided", "proj", "line_inv", "vector", "pot_inv", "pot_line",
               "pot_fwd"]
 
@@ -125,6 +125,7 @@ def _load():
     lib.hom_restrict.argtypes = [vp, vp, vp]
     lib.hom_measure_fp64.argtypes = [ip, ip, vp, dp, dp]
     lib.hom_debug_fail_alloc.argtypes = [ip]
+    lib.hom_debug_tma_stall.argtypes = [ip]
     lib.hom_bound.argtypes = [vp, vp, dp, vp, dp]
     lib.hom_destroy.argtypes = [vp]
     lib.hom_destroy.restype = None
@@ -259,6 +260,10 @@ def hom_measure_fp64(kind=0, iters=2000, stream=None):
 
 def hom_debug_fail_alloc(n):
     return _check(_lib.hom_debug_fail_alloc(int(n)), "hom_debug_fail_alloc")
+
+
+def hom_debug_tma_stall(on):
+    return _check(_lib.hom_debug_tma_stall(int(bool(on))), "hom_debug_tma_stall")
 
 
 def hom_solve(P, E, solver, tol, opts: hom_opts | None = None, x=None, allow_not_converged=False):

@@ -354,6 +354,11 @@ int hom_debug_fail_alloc(int n) {
   return HOM_OK;
 }
 
+int hom_debug_tma_stall(int on) {
+  tma_debug_stall(on != 0);
+  return HOM_OK;
+}
+
 int hom_profile_enable(int on) {
   ProfState& ps = prof_state();
   if (on) {
@@ -1320,6 +1325,7 @@ extern "C" int hom_solve_end(hom_problem* P, double* x_dev, double* AH_EE, doubl
     }
     if (x_dev && (rc = write_corrector(P, P->vec[0], x_dev))) return rc;
     if ((rc = check_last())) return rc;
+    if (tma_wait_errors(true) != 0) return HOM_ERR_TIMEOUT;
     return (S_.converged || S_.fixed) ? HOM_OK : HOM_ERR_NOT_CONVERGED;
   }
   rc = poll(P, P->d_sc);
@@ -1369,6 +1375,7 @@ extern "C" int hom_solve_end(hom_problem* P, double* x_dev, double* AH_EE, doubl
   }
   if (x_dev && (rc = write_corrector(P, result, x_dev))) return rc;
   if ((rc = check_last())) return rc;
+  if (tma_wait_errors(true) != 0) return HOM_ERR_TIMEOUT;
   return (fin.converged || S_.fixed) ? HOM_OK : HOM_ERR_NOT_CONVERGED;
 }
 

@@ -99,6 +99,10 @@ struct Ops {
 // (ops_pair_f32.cu); the callers fall back to the runtime-radix kernels for everything else
 bool pair_plan_f32(const AxisPlan& P);
 cudaError_t pair_prepare_f32(int smem_cap);
+// TMA waits that ran out on the current device since the last reset (tma.cuh)
+unsigned tma_wait_errors(bool reset);
+// on: announce 16 bytes more than each TMA tile copy delivers, so that its waits run out
+void tma_debug_stall(bool on);
 void pair_strided_f32(const AxisPlan& P, int inv, cpx<float>* S, const cpx<float>* tw,
                       long long C, long long es, long long bs, int batches, const Scalars* sc,
                       cudaStream_t st, const ReqDesc<float>* reqs, int nreq);

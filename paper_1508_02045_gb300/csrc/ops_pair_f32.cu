@@ -1,5 +1,7 @@
 // Launchers of the FP32 kernels specialised at compile time for two-stage plans (pair_fft.cuh),
 // in a translation unit of their own so that they compile in parallel with the rest.
+#include <algorithm>
+#include <cstdlib>
 #include <type_traits>
 
 #include "ops.h"
@@ -24,6 +26,104 @@ bool pair_plan_f32(const AxisPlan& P) {
     if (e_ != cudaSuccess) return e_;                                                         \
   } while (0)
 
+// ---------------------------------------------------------------------------------------
+// TMA tensor maps and the device counter of TMA waits that ran out
+// ---------------------------------------------------------------------------------------
+constexpr int kTmaDevices = 64;
+static __device__ unsigned g_tma_wait_errors;
+
+static unsigned* tma_error_counter() {
+  static unsigned* addr[kTmaDevices] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= kTmaDevices) return nullptr;
+  if (addr[dev] == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_tma_wait_errors) == cudaSuccess) addr[dev] = (unsigned*)p;
+  }
+  return addr[dev];
+}
+
+unsigned tma_wait_errors(bool reset) {
+  unsigned* p = tma_error_counter();
+  if (p == nullptr) return 0;
+  unsigned v = 0;
+  if (cudaMemcpy(&v, p, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+  if (reset && v != 0) cudaMemset(p, 0, sizeof v);
+  return v;
+}
+
+using TmaEncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static TmaEncodeFn tma_encoder() {
+  static const TmaEncodeFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<TmaEncodeFn>(p);
+  }();
+  return fn;
+}
+
+bool tma_map_3d(CUtensorMap* map, const void* base, long long C, long long rows,
+                long long batches, long long es, long long bs, int box_c, int box_rows) {
+  constexpr long long el = 8;
+  const TmaEncodeFn enc = tma_encoder();
+  if (enc == nullptr) return false;
+  if (((uintptr_t)base & 15) != 0 || (es * el) % 16 != 0 || (bs * el) % 16 != 0) return false;
+  if ((box_c * el) % 16 != 0 || box_c > 256 || box_rows > 256 || box_c < 1 || box_rows < 1)
+    return false;
+  if (C < 1 || rows < 1 || batches < 1 || es < C || bs < es * rows) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)rows, (cuuint64_t)batches};
+  const cuuint64_t strides[2] = {(cuuint64_t)(es * el), (cuuint64_t)(bs * el)};
+  const cuuint32_t box[3] = {(cuuint32_t)box_c, (cuuint32_t)box_rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, const_cast<void*>(base), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// bytes announced on top of each TMA tile copy (hom_debug_tma_stall)
+static unsigned g_tma_extra_tx = 0;
+void tma_debug_stall(bool on) { g_tma_extra_tx = on ? 16u : 0u; }
+
+// the TMA-staged strided pass is used unless HOM_PAIR_TMA=0
+static bool pair_tma_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("HOM_PAIR_TMA");
+    return e == nullptr || e[0] != '0';
+  }();
+  return on;
+}
+
+// persistent grid of a TMA-staged kernel: its resident CTAs on every SM
+template <typename K>
+static int persistent_ctas(K kernel, int threads, size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess)
+    per = 0;
+  return std::max(1, per) * std::max(1, sms);
+}
+
+// resident CTAs of the TMA-staged strided kernel of a plan on the current device (set by
+// pair_prepare_f32, before any stream capture)
+template <int R1, int R2, bool INV>
+static int& strided_tma_ctas() {
+  static int v[kTmaDevices] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return v[(unsigned)dev % kTmaDevices];
+}
+
 cudaError_t pair_prepare_f32(int cap) {
   using T = float;
   // this unit's copies of the register-DFT constants
@@ -32,6 +132,8 @@ cudaError_t pair_prepare_f32(int cap) {
 #define HOM_PAIR_SMEM(R1_, R2_)                                 \
   HOM_SET_SMEM((k_pair_strided<T, R1_, R2_, false>));           \
   HOM_SET_SMEM((k_pair_strided<T, R1_, R2_, true>));            \
+  HOM_SET_SMEM((k_pair_strided_tma<T, R1_, R2_, false>));       \
+  HOM_SET_SMEM((k_pair_strided_tma<T, R1_, R2_, true>));        \
   HOM_SET_SMEM((k_pair_proj<T, 2, PROJ_GAMMA, R1_, R2_>));      \
   HOM_SET_SMEM((k_pair_proj<T, 2, PROJ_EM, R1_, R2_>));         \
   HOM_SET_SMEM((k_pair_proj<T, 3, PROJ_GAMMA, R1_, R2_>));      \
@@ -53,6 +155,17 @@ cudaError_t pair_prepare_f32(int cap) {
   HOM_SET_SMEM((k_pair_line_inv<T, 6, POST_CHEB, R1_, R2_>));
   HOM_PAIR_PLANS(HOM_PAIR_SMEM)
 #undef HOM_PAIR_SMEM
+#define HOM_PAIR_TMA_CTAS(R1_, R2_)                                                            \
+  strided_tma_ctas<R1_, R2_, false>() =                                                        \
+      persistent_ctas(k_pair_strided_tma<T, R1_, R2_, false>, pair_tc_strided<R2_>() * R2_,    \
+                      pair_strided_tma_smem<T, R1_, R2_>());                                   \
+  strided_tma_ctas<R1_, R2_, true>() =                                                         \
+      persistent_ctas(k_pair_strided_tma<T, R1_, R2_, true>, pair_tc_strided<R2_>() * R2_,     \
+                      pair_strided_tma_smem<T, R1_, R2_>());
+  HOM_PAIR_PLANS(HOM_PAIR_TMA_CTAS)
+#undef HOM_PAIR_TMA_CTAS
+  tma_error_counter();
+  tma_encoder();
 #define HOM_POT_SMEM(R1_, R2_)                                  \
   HOM_SET_SMEM((k_pot_inv<T, R1_, R2_, POT_STEP>));             \
   HOM_SET_SMEM((k_pot_inv<T, R1_, R2_, POT_FIELD>));            \
@@ -144,6 +257,20 @@ void pair_strided_f32(const AxisPlan& P, int inv, cpx<float>* S, const cpx<float
 #define HOM_PAIR_ST(R1_, R2_)                                                                  \
   if (P.radix[0] == R1_ && P.radix[1] == R2_) {                                                \
     constexpr int TC = pair_tc_strided<R2_>();                                                 \
+    CUtensorMap map;                                                                           \
+    const long long ntc = (C + TC - 1) / TC, ntiles = ntc * batches;                          \
+    if (reqs == nullptr && nreq == 1 && pair_tma_enabled() && ntiles < (1LL << 30) &&         \
+        tma_map_3d(&map, S, C, R1_ * R2_, batches, es, bs, TC, R1_ * R2_)) {                  \
+      constexpr size_t sm = pair_strided_tma_smem<T, R1_, R2_>();                              \
+      auto kern = inv ? k_pair_strided_tma<T, R1_, R2_, true>                                  \
+                      : k_pair_strided_tma<T, R1_, R2_, false>;                                \
+      int& nc = inv ? strided_tma_ctas<R1_, R2_, true>() : strided_tma_ctas<R1_, R2_, false>(); \
+      if (nc == 0) nc = persistent_ctas(kern, TC * R2_, sm);                                   \
+      const int grid = (int)std::min<long long>(nc, ntiles);                                   \
+      launch_pass(kern, dim3((unsigned)grid), TC * R2_, sm, st, map, S, tw, C, es, bs,         \
+                  (int)ntc, (int)ntiles, sc, tma_error_counter(), g_tma_extra_tx);             \
+      return;                                                                                  \
+    }                                                                                          \
     const dim3 grid((unsigned)((C + TC - 1) / TC), (unsigned)batches, (unsigned)nreq);        \
     size_t sm = sizeof(cpx<T>) * (size_t)(R1_ * R2_) * (TC + 2);                                \
     if (TC * R2_ >= 128 && sm < kPairStridedMinSmem) sm = kPairStridedMinSmem;                 \

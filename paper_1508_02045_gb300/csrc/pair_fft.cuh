@@ -13,6 +13,7 @@
 #include <type_traits>
 
 #include "passes.cuh"
+#include "tma.cuh"
 
 namespace hom {
 
@@ -118,6 +119,103 @@ k_pair_strided(cpx<T>* S, const cpx<T>* __restrict__ twg, long long C, long long
     if (INV) conj_all<T, R2>(u);
 #pragma unroll
     for (int r = 0; r < R2; ++r) base[(long long)(i + r * R1) * es + c] = u[r];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// the same pass on tiles staged by the TMA unit (tma.cuh): a persistent CTA walks the tiles
+// (column tile fastest, then batch) with two TC x n tile buffers and loads the next tile by one
+// box copy while it transforms the current one. Stage 1 runs in place: butterfly i keeps rows
+// i + r R2 and leaves its output r in row i + r R2, so stage 2 finds output position
+// i2 + r2 R1 of stage 1 (butterfly r2, output i2) in row r2 + i2 R2. Rows are TC = 16
+// values (128 bytes) wide, and each half-warp reads one whole row in both stages.
+// extra_tx (0 except under hom_debug_tma_stall) is announced on top of each tile's bytes, so
+// that no barrier phase completes and every wait runs out.
+// ---------------------------------------------------------------------------------------
+template <typename T, int R1, int R2>
+__host__ __device__ constexpr size_t pair_strided_tma_smem() {
+  // alignment slack, two tiles, twiddles, two barriers
+  return 128 + sizeof(cpx<T>) * (size_t)R1 * R2 * (2 * pair_tc_strided<R2>() + 1) + 16;
+}
+
+template <typename T, int R1, int R2, bool INV>
+__global__ void __launch_bounds__(pair_tc_strided<R2>() * R2)
+k_pair_strided_tma(const __grid_constant__ CUtensorMap map, cpx<T>* S,
+                   const cpx<T>* __restrict__ twg, long long C, long long es, long long bs,
+                   int ntc, int ntiles, const Scalars* sc, unsigned* wait_errors,
+                   unsigned extra_tx) {
+  wait_prior_grid();
+  constexpr int n = R1 * R2, TC = pair_tc_strided<R2>(), NT = TC * R2;
+  constexpr unsigned kTileBytes = (unsigned)(sizeof(cpx<T>) * TC * n);
+  if (sc != nullptr && sc->done) return;
+  unsigned char* raw = hom_dyn_smem;
+  const unsigned a0 = smem_addr(raw);
+  raw += ((a0 + 127u) & ~127u) - a0;
+  cpx<T>* buf = reinterpret_cast<cpx<T>*>(raw);  // tile b at buf + b * TC * n
+  cpx<T>* tw = buf + 2 * TC * n;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tw + n);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n; i += NT) tw[i] = twg[i];
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+  int t = blockIdx.x;
+  if (tid == 0 && t < ntiles) {
+    mbar_expect_tx(&bar[0], kTileBytes + extra_tx);
+    tma_load_3d(buf, &map, (t % ntc) * TC, 0, t / ntc, &bar[0]);
+  }
+  for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
+    const int b = it & 1;
+    cpx<T>* tile = buf + b * TC * n;
+    const int tn = t + gridDim.x;
+    if (tid == 0 && tn < ntiles) {
+      // the other buffer was last accessed before the fence and barrier that ended the
+      // previous tile
+      mbar_expect_tx(&bar[b ^ 1], kTileBytes + extra_tx);
+      tma_load_3d(buf + (b ^ 1) * TC * n, &map, (tn % ntc) * TC, 0, tn / ntc, &bar[b ^ 1]);
+    }
+    const bool ok = mbar_wait(&bar[b], (unsigned)(it >> 1) & 1u);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        if (wait_errors != nullptr) atomicAdd(wait_errors, 1u);
+        // let the copy in flight into the other buffer land before the CTA's memory goes
+        if (tn < ntiles) mbar_wait(&bar[b ^ 1], (unsigned)((it + 1) >> 1) & 1u);
+      }
+      return;
+    }
+    const long long c0 = (long long)(t % ntc) * TC;
+    const int ncols = (int)min((long long)TC, C - c0);
+    {
+      const int c = tid % TC, i = tid / TC;
+      cpx<T> u[R1];
+#pragma unroll
+      for (int r = 0; r < R1; ++r) u[r] = tile[(i + r * R2) * TC + c];
+      if (INV) conj_all<T, R1>(u);
+      RegDft<T, R1>::run(u);
+#pragma unroll
+      for (int r = 0; r < R1; ++r) tile[(i + r * R2) * TC + c] = u[r];
+    }
+    __syncthreads();
+    cpx<T>* base = S + (long long)(t / ntc) * bs + c0;
+    for (int w = tid; w < TC * R1; w += NT) {
+      const int c = w % TC, i2 = w / TC;
+      if (c >= ncols) continue;
+      cpx<T> u[R2];
+#pragma unroll
+      for (int r = 0; r < R2; ++r) u[r] = tile[(r + i2 * R2) * TC + c];
+#pragma unroll
+      for (int r = 1; r < R2; ++r) u[r] = cmul(u[r], tw[r * i2]);
+      RegDft<T, R2>::run(u);
+      if (INV) conj_all<T, R2>(u);
+#pragma unroll
+      for (int r = 0; r < R2; ++r) base[(long long)(i2 + r * R1) * es + c] = u[r];
+    }
+    // this tile's shared-memory accesses come before the TMA's next write to the buffer
+    fence_proxy_async_smem();
+    __syncthreads();
   }
 }
 
