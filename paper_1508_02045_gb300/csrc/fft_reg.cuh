@@ -32,13 +32,14 @@ constexpr int kRegTable = reg_offset(kRegMax) + kRegMax;  // 255
 
 static __constant__ double c_rcos_d[kRegTable];
 static __constant__ double c_rsin_d[kRegTable];
+static __constant__ double c_rtan_d[kRegTable];  // tan(2 pi j / R): never infinite for odd R
 static __constant__ float c_rcos_f[kRegTable];
 static __constant__ float c_rsin_f[kRegTable];
 
 // Fill this translation unit's copies of the tables (each unit that launches register DFTs
 // calls it once per device), from long double cos / sin.
 static inline cudaError_t upload_reg_tables() {
-  double cd[kRegTable], sd[kRegTable];
+  double cd[kRegTable], sd[kRegTable], td[kRegTable];
   float cf[kRegTable], sf[kRegTable];
   const long double twopi = 6.283185307179586476925286766559005768L;
   for (int R = 3; R <= kRegMax; R += 2) {
@@ -47,6 +48,7 @@ static inline cudaError_t upload_reg_tables() {
       const long double t = twopi * (long double)j / (long double)R;
       cd[off + j] = (double)cosl(t);
       sd[off + j] = (double)sinl(t);
+      td[off + j] = (double)(sinl(t) / cosl(t));
       cf[off + j] = (float)cosl(t);
       sf[off + j] = (float)sinl(t);
     }
@@ -54,6 +56,7 @@ static inline cudaError_t upload_reg_tables() {
   cudaError_t e;
   if ((e = cudaMemcpyToSymbol(c_rcos_d, cd, sizeof(cd))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(c_rsin_d, sd, sizeof(sd))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_rtan_d, td, sizeof(td))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(c_rcos_f, cf, sizeof(cf))) != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_rsin_f, sf, sizeof(sf));
 }
@@ -160,6 +163,157 @@ struct RegDft {
 };
 
 // ---------------------------------------------------------------------------------------
+// FP64 radix-3 and radix-9 stages with cosine-factored twiddles
+//
+// FP64 work is bound by the number of FP64 instructions, and a complex product with a twiddle
+// costs four of them (two multiplications, two fused multiply-adds). With a twiddle written as
+// w = c (1 + i t), c = Re w, t = Im w / Re w (c is never zero for odd lengths), u w = c v with
+// v = (u_x - t u_y, u_y + t u_x): two fused multiply-adds, and the real factor c rides along
+// into the butterfly's own multiply-adds (the factorisation of twiddles for multiply-add units
+// of Linzer and Feig, and of Goedecker for radices 2 to 5). A twiddled 3-point DFT then costs
+// 18 instructions instead of 20, a twiddled 9-point one 106 instead of 120, an untwiddled
+// 9-point one (its internal twiddles factored the same way) 84 instead of 88. The stage
+// twiddle tables of FP64 transforms hold (c, t) instead of (Re w, Im w).
+// ---------------------------------------------------------------------------------------
+
+// v = u (1 + i t)
+__device__ __forceinline__ cpx<double> tan_rot(cpx<double> u, double t) {
+  cpx<double> v;
+  v.x = fma(-t, u.y, u.x);
+  v.y = fma(t, u.x, u.y);
+  return v;
+}
+
+// the 3-point outputs y1 = t - i S d, y2 = t + i S d with S = sin(2 pi / 3)
+__device__ __forceinline__ void dft3_tail(cpx<double> t, cpx<double> d, cpx<double>& y1,
+                                          cpx<double>& y2) {
+  const double S = rsin<double>(reg_offset(3) + 1);
+  y1.x = fma(S, d.y, t.x);
+  y1.y = fma(-S, d.x, t.y);
+  y2.x = fma(-S, d.y, t.x);
+  y2.y = fma(S, d.x, t.y);
+}
+
+// DFT_3 of (a, c1 v1, c2 v2), in place
+__device__ __forceinline__ void dft3_s2(cpx<double>& a, cpx<double>& v1, cpx<double>& v2,
+                                        double c1, double c2) {
+  const double h = rcos<double>(reg_offset(3) + 1);  // cos(2 pi / 3) = -1/2
+  cpx<double> q, s, d, t;
+  q.x = c2 * v2.x;
+  q.y = c2 * v2.y;
+  s.x = fma(c1, v1.x, q.x);
+  s.y = fma(c1, v1.y, q.y);
+  d.x = fma(c1, v1.x, -q.x);
+  d.y = fma(c1, v1.y, -q.y);
+  t.x = fma(h, s.x, a.x);
+  t.y = fma(h, s.y, a.y);
+  a.x += s.x;
+  a.y += s.y;
+  dft3_tail(t, d, v1, v2);
+}
+
+// DFT_3 of (c0 v0, c1 v1, c2 v2), in place; the middle term c0 v0 - s/2 is formed as
+// y0 - (3/2) s from y0 = c0 v0 + s
+__device__ __forceinline__ void dft3_s3(cpx<double>& v0, cpx<double>& v1, cpx<double>& v2,
+                                        double c0, double c1, double c2) {
+  cpx<double> q, s, d, t;
+  q.x = c2 * v2.x;
+  q.y = c2 * v2.y;
+  s.x = fma(c1, v1.x, q.x);
+  s.y = fma(c1, v1.y, q.y);
+  d.x = fma(c1, v1.x, -q.x);
+  d.y = fma(c1, v1.y, -q.y);
+  v0.x = fma(c0, v0.x, s.x);
+  v0.y = fma(c0, v0.y, s.y);
+  t.x = fma(-1.5, s.x, v0.x);
+  t.y = fma(-1.5, s.y, v0.y);
+  dft3_tail(t, d, v1, v2);
+}
+
+// DFT_3 of (a, b, e), in place (the 12-instruction butterfly of RegDft<double, 3>)
+__device__ __forceinline__ void dft3_p(cpx<double>& a, cpx<double>& b, cpx<double>& e) {
+  const double h = rcos<double>(reg_offset(3) + 1);
+  cpx<double> s, d, t;
+  s.x = b.x + e.x;
+  s.y = b.y + e.y;
+  d.x = b.x - e.x;
+  d.y = b.y - e.y;
+  t.x = fma(h, s.x, a.x);
+  t.y = fma(h, s.y, a.y);
+  a.x += s.x;
+  a.y += s.y;
+  dft3_tail(t, d, b, e);
+}
+
+// Second half of the 9-point DFT (3 x 3 split as in RegDft, j = j2 + 3 j1 -> k = k1 + 3 k2):
+// u[j2 + 3 k1] holds the output k1 of the 3-point DFT of column j2; the internal twiddles
+// exp(-2 pi i j2 k1 / 9) = C_m (1 - i tan(2 pi m / 9)), m = j2 k1, are factored as above.
+// Writes X[k1 + 3 k2] to u in natural order.
+__device__ __forceinline__ void dft9_rows(cpx<double> (&u)[9]) {
+  constexpr int o9 = reg_offset(9);
+  const double C1 = rcos<double>(o9 + 1), C2 = rcos<double>(o9 + 2), C4 = rcos<double>(o9 + 4);
+  const double T1 = -c_rtan_d[o9 + 1], T2 = -c_rtan_d[o9 + 2], T4 = -c_rtan_d[o9 + 4];
+  // row k1 = 0: (V0[0], V1[0], V2[0]) at u[0], u[1], u[2]
+  cpx<double> a0 = u[0], a1 = u[1], a2 = u[2];
+  dft3_p(a0, a1, a2);
+  // row k1 = 1: (V0[1], V1[1] w^1, V2[1] w^2) at u[3], u[4], u[5]
+  cpx<double> b0 = u[3], b1 = tan_rot(u[4], T1), b2 = tan_rot(u[5], T2);
+  dft3_s2(b0, b1, b2, C1, C2);
+  // row k1 = 2: (V0[2], V1[2] w^2, V2[2] w^4) at u[6], u[7], u[8]
+  cpx<double> e0 = u[6], e1 = tan_rot(u[7], T2), e2 = tan_rot(u[8], T4);
+  dft3_s2(e0, e1, e2, C2, C4);
+  u[0] = a0; u[3] = a1; u[6] = a2;
+  u[1] = b0; u[4] = b1; u[7] = b2;
+  u[2] = e0; u[5] = e1; u[8] = e2;
+}
+
+// the column outputs of the 9-point split, regrouped so that u[j2 + 3 k1] = V_{j2}[k1]
+__device__ __forceinline__ void dft9_regroup(cpx<double> (&u)[9], const cpx<double> (&V)[3][3]) {
+#pragma unroll
+  for (int j2 = 0; j2 < 3; ++j2)
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) u[3 * k1 + j2] = V[j2][k1];
+}
+
+// DFT_9 of u without stage twiddles
+__device__ __forceinline__ void dft9_plain(cpx<double> (&u)[9]) {
+  cpx<double> V[3][3];
+#pragma unroll
+  for (int j2 = 0; j2 < 3; ++j2) {
+    V[j2][0] = u[j2];
+    V[j2][1] = u[j2 + 3];
+    V[j2][2] = u[j2 + 6];
+    dft3_p(V[j2][0], V[j2][1], V[j2][2]);
+  }
+  dft9_regroup(u, V);
+  dft9_rows(u);
+}
+
+// DFT_9 of (u0, w^{1 k} u1, ..., w^{8 k} u8) with the stage twiddles w^{r k} = c_r (1 + i t_r)
+// read as (c_r, t_r) from tw[r * step]; each column of the split loads its own three
+__device__ __forceinline__ void dft9_twiddled(cpx<double> (&u)[9], const cpx<double>* tw,
+                                              int step) {
+  cpx<double> V[3][3];
+  {
+    const cpx<double> w3 = tw[3 * step], w6 = tw[6 * step];
+    V[0][0] = u[0];
+    V[0][1] = tan_rot(u[3], w3.y);
+    V[0][2] = tan_rot(u[6], w6.y);
+    dft3_s2(V[0][0], V[0][1], V[0][2], w3.x, w6.x);
+  }
+#pragma unroll
+  for (int j2 = 1; j2 < 3; ++j2) {
+    const cpx<double> wa = tw[j2 * step], wb = tw[(j2 + 3) * step], wc = tw[(j2 + 6) * step];
+    V[j2][0] = tan_rot(u[j2], wa.y);
+    V[j2][1] = tan_rot(u[j2 + 3], wb.y);
+    V[j2][2] = tan_rot(u[j2 + 6], wc.y);
+    dft3_s3(V[j2][0], V[j2][1], V[j2][2], wa.x, wb.x, wc.x);
+  }
+  dft9_regroup(u, V);
+  dft9_rows(u);
+}
+
+// ---------------------------------------------------------------------------------------
 // dynamic shared memory of every pass kernel, addressed with 32-bit element offsets
 // ---------------------------------------------------------------------------------------
 extern __shared__ __align__(16) unsigned char hom_dyn_smem[];
@@ -248,12 +402,44 @@ __device__ __forceinline__ void reg_stage(Loc<T> in, Loc<T> out, int n, int p, i
 #pragma unroll
       for (int r = 0; r < R; ++r) u[r].y = flip_sign(u[r].y, m_in);
     }
-    if (p > 1) {
-      const int step = k * ts;
+    if constexpr (sizeof(T) == 8 && (R == 3 || R == 9)) {
+      // FP64 radices 3 and 9: stage twiddles (c, t), w = c (1 + i t), folded into the DFT
+      if (p > 1) {
+        const int step = k * ts;
+        const cpx<T>* tw = sm + tw_base;
+        if constexpr (R == 3) {
+          const cpx<T> w1 = tw[step], w2 = tw[2 * step];
+          u[1] = tan_rot(u[1], w1.y);
+          u[2] = tan_rot(u[2], w2.y);
+          dft3_s2(u[0], u[1], u[2], w1.x, w2.x);
+        } else {
+          dft9_twiddled(u, tw, step);
+        }
+      } else {
+        if constexpr (R == 9)
+          dft9_plain(u);
+        else
+          RegDft<T, R>::run(u);
+      }
+    } else {
+      if (p > 1) {
+        const int step = k * ts;
 #pragma unroll
-      for (int r = 1; r < R; ++r) u[r] = cmul(u[r], sm[tw_base + r * step]);
+        for (int r = 1; r < R; ++r) {
+          const cpx<T> w = sm[tw_base + r * step];
+          if constexpr (sizeof(T) == 8) {
+            // FP64 twiddle (c, t): u w = c (u_x - t u_y, u_y + t u_x), four instructions as a
+            // complex product
+            const T ux = u[r].x;
+            u[r].x = w.x * fma(-w.y, u[r].y, ux);
+            u[r].y = w.x * fma(w.y, ux, u[r].y);
+          } else {
+            u[r] = cmul(u[r], w);
+          }
+        }
+      }
+      RegDft<T, R>::run(u);
     }
-    RegDft<T, R>::run(u);
     if (INV) {
 #pragma unroll
       for (int r = 0; r < R; ++r) u[r].y = flip_sign(u[r].y, m_out);

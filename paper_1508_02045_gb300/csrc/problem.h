@@ -77,14 +77,18 @@ int alloc(void** p, size_t bytes);
 // largest register radix per precision (FP64 values take twice the registers)
 template <typename T> constexpr int reg_rmax() { return sizeof(T) == 8 ? 15 : 27; }
 
+// Stage twiddles w_j = exp(-2 pi i j / n) of an odd length n: (Re w, Im w) in FP32; in FP64
+// (c, t) with w = c (1 + i t), c = Re w, t = Im w / Re w (Re w is never zero for odd n), the
+// cosine-factored form that the FP64 register stages fold into their multiply-adds.
 template <typename T>
 std::vector<cpx<T>> twiddles(int n) {
   std::vector<cpx<T>> tw(n);
   const long double twopi = 6.283185307179586476925286766559005768L;
   for (int j = 0; j < n; ++j) {
     const long double t = -twopi * (long double)j / (long double)n;
-    tw[j].x = (T)cosl(t);
-    tw[j].y = (T)sinl(t);
+    const long double c = cosl(t), s = sinl(t);
+    tw[j].x = (T)c;
+    tw[j].y = sizeof(T) == 8 ? (T)(s / c) : (T)s;
   }
   return tw;
 }
