@@ -329,12 +329,10 @@ def measure_fp64_peak(H, local):
                    "full wave of resident CTAs on every SM, CUDA events, best of 3"}
 
 
-# DRAM bytes (read + write) of one launch of the dominant kernels of the 243^3 CG steps, from
-# one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum on GB300; other kernels and
-# grids have no capture (null)
-# DRAM bytes read + written per launch at 243^3 (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of the kernels as they are now; profiles/ gives the commands)
-NCU_TRAFFIC = {("fp64", "strided"): 631.9e6, ("fp32", "line_fwd"): 644.0e6,
+# DRAM bytes read + written per launch of the dominant kernels of the 243^3 CG steps (ncu
+# dram__bytes_read.sum + dram__bytes_write.sum on GB300 of the kernels as they are now;
+# profiles/ gives the commands); other kernels and grids have no capture (null)
+NCU_TRAFFIC = {("fp64", "strided"): 634.6e6, ("fp32", "line_fwd"): 644.0e6,
                ("fp32", "line_inv"): 984.8e6, ("fp32", "pot_inv"): 342.6e6,
                ("fp32", "pot_line"): 300.9e6, ("fp32", "pot_fwd"): 199.0e6}
 
