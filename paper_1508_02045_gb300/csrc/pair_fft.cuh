@@ -835,7 +835,8 @@ k_pair_line_inv(const cpx<T>* S, Fields<T> f, const cpx<T>* __restrict__ twg, lo
   // Chebyshev and fused CG read three operands a node: smaller batches keep them within the
   // register budget
   line_post_from_smem<T, D, POST, (D > 3) ? 1 : ((POST == POST_CHEB || POST == POST_CG_FUSED) ? 2 : 4), n>(f, n, n, LBP, D, l0, LB, nlines, fdn,
-                                                            mat, sc, args, negate, dacc);
+                                                            mat, sc, args, negate, dacc,
+                                                            partials != nullptr);
   if (partials == nullptr) return;
   double acc[1] = {dacc.value()};
   double tot[1];

@@ -848,14 +848,15 @@ k_proj_scalar(cpx<T>* S, AxisPlan P, const cpx<T>* __restrict__ twg, ProjGeom g,
 // Post-operator of the lines l0 .. l0 + LB - 1 after their inverse transform: node j of line
 // l0 + ll is the real (ll even) or imaginary (ll odd) part of shared-memory complex line
 // res + (a * half + ll / 2) * n; the solver's vector update, batches of K nodes whose operands
-// are loaded before any use, and the inner-product partial in dacc.
+// are loaded before any use, and the inner-product partial in dacc (for POST_STORE only when
+// `dot` is set: a plain operator application has no partial to form).
 template <typename T, int D, int POST, int K = (sizeof(T) == 4 ? 4 : (D > 3 ? 1 : 2)), int NC = 0>
 __device__ __forceinline__ void line_post_from_smem(const Fields<T>& f, int res, int n, int half,
                                                     int ncomp, long long l0, int LB,
                                                     long long nlines, FastDiv fdn,
                                                     const MatView<T>& mat, const Scalars* sc,
                                                     const OpArgs& args, int negate,
-                                                    DotAcc<T>& dacc) {
+                                                    DotAcc<T>& dacc, bool dot) {
   cpx<T>* sm = smem_c<T>();
   const double* Es = sc != nullptr ? sc->E : args.E;
   T E[D];
@@ -910,11 +911,12 @@ __device__ __forceinline__ void line_post_from_smem(const Fields<T>& f, int res,
       }
       if (POST == POST_STORE) {
         for (int a = 0; a < ncomp; ++a) {
-          const T o = negate ? -y[a] : y[a];
+          // the sign flip of `negate` as an integer xor of the sign bit, off the FP pipes
+          const T o = flip_sign(y[a], negate ? 0x80000000u : 0u);
           f.out[a * cs + g] = o;
           if (f.r) f.r[a * cs + g] = o;
           if (f.p) f.p[a * cs + g] = o;
-          dacc.add(y[a], y[a]);
+          if (dot) dacc.add(y[a], y[a]);
         }
       } else if (POST == POST_RICH) {
 #pragma unroll
@@ -1119,7 +1121,7 @@ k_line_inv(const cpx<T>* S, Fields<T> f, AxisPlan P, const cpx<T>* __restrict__ 
 
   DotAcc<T> dacc;
   line_post_from_smem<T, D, POST>(f, res, n, half, ncomp, l0, LB, nlines, P.fdn, mat, sc, args,
-                                  negate, dacc);
+                                  negate, dacc, partials != nullptr);
   if (partials == nullptr) return;
   double acc[1] = {dacc.value()};
   double tot[1];
