@@ -205,6 +205,32 @@ def cufft_matvec(ph, table, x_dev, dtype, steps):
     return e0.elapsed_time(e1) / steps, y
 
 
+def host_cpu() -> str:
+    """The host CPU as the kernel reports it: model name (x86) or implementer/part (Arm)."""
+    model, impl, part = "", "", ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                k, v = k.strip(), v.strip()
+                if k == "model name" and not model:
+                    model = v
+                elif k == "CPU implementer" and not impl:
+                    impl = v
+                elif k == "CPU part" and not part:
+                    part = v
+    except OSError:
+        pass
+    if model:
+        return model
+    if impl or part:
+        # 0x41 = Arm Ltd; part 0xd4f = Neoverse V2 (the Grace core)
+        names = {("0x41", "0xd4f"): "Arm Neoverse V2"}
+        return names.get((impl, part), f"Arm implementer {impl} part {part}")
+    import platform
+    return platform.machine()
+
+
 def cpu_oracle_cg_steps(nsteps=1):
     """Time CG iterations of the FP64 NumPy oracle on this host at the bench workload."""
     import oracle as O
@@ -218,7 +244,8 @@ def cpu_oracle_cg_steps(nsteps=1):
     matvecs = nsteps + 2
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     del res
-    return {"value": matvecs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": matvecs / dt, "unit": UNIT, "cores": cores, "cpu": host_cpu(),
+            "kind": "oracle",
             "sample": f"{nsteps} oracle CG iteration(s) + set-up at 243^3 ({matvecs} matvecs, "
                       f"{dt:.1f} s, NumPy FP64 dense-matrix DFT, BLAS threads = host cores)"}
 
@@ -1146,8 +1173,8 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000.0 / v, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded centred-cube phase image)", "config": config(),
-        "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": cores, "cpu": host_cpu(),
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": round(v, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
