@@ -79,12 +79,16 @@ __host__ __device__ constexpr int smallest_factor(int R) {
 template <typename T, int R, int A = smallest_factor(R)>
 struct RegDft;
 
+// The outputs of a prime R-point DFT from its pair sums u[r] = x_r + x_{R-r} and differences
+// u[R-r] = x_r - x_{R-r} (1 <= r <= (R-1)/2), u[0] = x_0 and y0 = the sum of all x_r
+template <typename T, int R>
+__device__ __forceinline__ void prime_dft_tail(cpx<T> (&u)[R], cpx<T> y0);
+
 // prime R
 template <typename T, int R>
 struct RegDft<T, R, R> {
   static __device__ __forceinline__ void run(cpx<T> (&u)[R]) {
     constexpr int H = (R - 1) / 2;
-    constexpr int off = reg_offset(R);
     cpx<T> y0 = u[0];
 #pragma unroll
     for (int r = 1; r <= H; ++r) {
@@ -96,33 +100,40 @@ struct RegDft<T, R, R> {
       y0.x += u[r].x;
       y0.y += u[r].y;
     }
-    cpx<T> o[R];
-    o[0] = y0;
-#pragma unroll
-    for (int s = 1; s <= H; ++s) {
-      cpx<T> C, S;
-      C.x = fma(rcos<T>(off + s), u[1].x, u[0].x);
-      C.y = fma(rcos<T>(off + s), u[1].y, u[0].y);
-      S.x = rsin<T>(off + s) * u[R - 1].x;
-      S.y = rsin<T>(off + s) * u[R - 1].y;
-#pragma unroll
-      for (int r = 2; r <= H; ++r) {
-        const int j = (r * s) % R;
-        C.x = fma(rcos<T>(off + j), u[r].x, C.x);
-        C.y = fma(rcos<T>(off + j), u[r].y, C.y);
-        S.x = fma(rsin<T>(off + j), u[R - r].x, S.x);
-        S.y = fma(rsin<T>(off + j), u[R - r].y, S.y);
-      }
-      // y_s = C - i S, y_{R-s} = C + i S
-      o[s].x = C.x + S.y;
-      o[s].y = C.y - S.x;
-      o[R - s].x = C.x - S.y;
-      o[R - s].y = C.y + S.x;
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) u[r] = o[r];
+    prime_dft_tail<T, R>(u, y0);
   }
 };
+
+template <typename T, int R>
+__device__ __forceinline__ void prime_dft_tail(cpx<T> (&u)[R], cpx<T> y0) {
+  constexpr int H = (R - 1) / 2;
+  constexpr int off = reg_offset(R);
+  cpx<T> o[R];
+  o[0] = y0;
+#pragma unroll
+  for (int s = 1; s <= H; ++s) {
+    cpx<T> C, S;
+    C.x = fma(rcos<T>(off + s), u[1].x, u[0].x);
+    C.y = fma(rcos<T>(off + s), u[1].y, u[0].y);
+    S.x = rsin<T>(off + s) * u[R - 1].x;
+    S.y = rsin<T>(off + s) * u[R - 1].y;
+#pragma unroll
+    for (int r = 2; r <= H; ++r) {
+      const int j = (r * s) % R;
+      C.x = fma(rcos<T>(off + j), u[r].x, C.x);
+      C.y = fma(rcos<T>(off + j), u[r].y, C.y);
+      S.x = fma(rsin<T>(off + j), u[R - r].x, S.x);
+      S.y = fma(rsin<T>(off + j), u[R - r].y, S.y);
+    }
+    // y_s = C - i S, y_{R-s} = C + i S
+    o[s].x = C.x + S.y;
+    o[s].y = C.y - S.x;
+    o[R - s].x = C.x - S.y;
+    o[R - s].y = C.y + S.x;
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) u[r] = o[r];
+}
 
 // composite R = A * B: A-point DFTs over the stride-B subsequences, twiddles
 // exp(-2 pi i j2 k1 / R), B-point DFTs over j2: X[k1 + A k2]
@@ -172,8 +183,9 @@ struct RegDft {
 // into the butterfly's own multiply-adds (the factorisation of twiddles for multiply-add units
 // of Linzer and Feig, and of Goedecker for radices 2 to 5). A twiddled 3-point DFT then costs
 // 18 instructions instead of 20, a twiddled 9-point one 106 instead of 120, an untwiddled
-// 9-point one (its internal twiddles factored the same way) 84 instead of 88. The stage
-// twiddle tables of FP64 transforms hold (c, t) instead of (Re w, Im w).
+// 9-point one (its internal twiddles factored the same way) 84 instead of 88, and a twiddled
+// prime one (5, 7) two fewer per pair of terms r, R - r. The stage twiddle tables of FP64
+// transforms hold (c, t) instead of (Re w, Im w).
 // ---------------------------------------------------------------------------------------
 
 // v = u (1 + i t)
@@ -313,6 +325,32 @@ __device__ __forceinline__ void dft9_twiddled(cpx<double> (&u)[9], const cpx<dou
   dft9_rows(u);
 }
 
+// DFT_R of a prime R in a twiddled stage, (u0, w^{k} u1, ..., w^{(R-1) k} u_{R-1}) with the
+// stage twiddles (c_r, t_r) read from tw[r * step]: the pair sum and difference of terms r and
+// R - r become c_r v_r + q and c_r v_r - q with q = c_{R-r} v_{R-r} (one multiplication and two
+// multiply-adds a part), 12 instructions a pair instead of 14 with complex twiddle products
+template <int R>
+__device__ __forceinline__ void dft_prime_twiddled(cpx<double> (&u)[R], const cpx<double>* tw,
+                                                   int step) {
+  constexpr int H = (R - 1) / 2;
+  cpx<double> y0 = u[0];
+#pragma unroll
+  for (int r = 1; r <= H; ++r) {
+    const cpx<double> wa = tw[r * step], wb = tw[(R - r) * step];
+    const cpx<double> va = tan_rot(u[r], wa.y), vb = tan_rot(u[R - r], wb.y);
+    cpx<double> q;
+    q.x = wb.x * vb.x;
+    q.y = wb.x * vb.y;
+    u[r].x = fma(wa.x, va.x, q.x);
+    u[r].y = fma(wa.x, va.y, q.y);
+    u[R - r].x = fma(wa.x, va.x, -q.x);
+    u[R - r].y = fma(wa.x, va.y, -q.y);
+    y0.x += u[r].x;
+    y0.y += u[r].y;
+  }
+  prime_dft_tail<double, R>(u, y0);
+}
+
 // ---------------------------------------------------------------------------------------
 // dynamic shared memory of every pass kernel, addressed with 32-bit element offsets
 // ---------------------------------------------------------------------------------------
@@ -402,8 +440,8 @@ __device__ __forceinline__ void reg_stage(Loc<T> in, Loc<T> out, int n, int p, i
 #pragma unroll
       for (int r = 0; r < R; ++r) u[r].y = flip_sign(u[r].y, m_in);
     }
-    if constexpr (sizeof(T) == 8 && (R == 3 || R == 9)) {
-      // FP64 radices 3 and 9: stage twiddles (c, t), w = c (1 + i t), folded into the DFT
+    if constexpr (sizeof(T) == 8 && (R == 3 || R == 5 || R == 7 || R == 9)) {
+      // FP64 radices 3, 5, 7 and 9: stage twiddles (c, t), w = c (1 + i t), folded into the DFT
       if (p > 1) {
         const int step = k * ts;
         const cpx<T>* tw = sm + tw_base;
@@ -412,8 +450,10 @@ __device__ __forceinline__ void reg_stage(Loc<T> in, Loc<T> out, int n, int p, i
           u[1] = tan_rot(u[1], w1.y);
           u[2] = tan_rot(u[2], w2.y);
           dft3_s2(u[0], u[1], u[2], w1.x, w2.x);
-        } else {
+        } else if constexpr (R == 9) {
           dft9_twiddled(u, tw, step);
+        } else {
+          dft_prime_twiddled<R>(u, tw, step);
         }
       } else {
         if constexpr (R == 9)
