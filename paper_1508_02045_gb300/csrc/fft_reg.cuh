@@ -67,6 +67,8 @@ template <> __device__ __forceinline__ double rcos<double>(int j) { return c_rco
 template <> __device__ __forceinline__ double rsin<double>(int j) { return c_rsin_d[j]; }
 template <> __device__ __forceinline__ float rcos<float>(int j) { return c_rcos_f[j]; }
 template <> __device__ __forceinline__ float rsin<float>(int j) { return c_rsin_f[j]; }
+template <typename T> __device__ __forceinline__ T rtan(int j);
+template <> __device__ __forceinline__ double rtan<double>(int j) { return c_rtan_d[j]; }
 
 __host__ __device__ constexpr int smallest_factor(int R) {
   return R % 3 == 0 ? 3 : R % 5 == 0 ? 5 : R % 7 == 0 ? 7 : R % 11 == 0 ? 11 : R % 13 == 0 ? 13
@@ -174,7 +176,7 @@ struct RegDft {
 };
 
 // ---------------------------------------------------------------------------------------
-// FP64 radix-3 and radix-9 stages with cosine-factored twiddles
+// FP64 stages with cosine-factored twiddles
 //
 // FP64 work is bound by the number of FP64 instructions, and a complex product with a twiddle
 // costs four of them (two multiplications, two fused multiply-adds). With a twiddle written as
@@ -183,23 +185,27 @@ struct RegDft {
 // into the butterfly's own multiply-adds (the factorisation of twiddles for multiply-add units
 // of Linzer and Feig, and of Goedecker for radices 2 to 5). A twiddled 3-point DFT then costs
 // 18 instructions instead of 20, a twiddled 9-point one 106 instead of 120, an untwiddled
-// 9-point one (its internal twiddles factored the same way) 84 instead of 88, and a twiddled
-// prime one (5, 7) two fewer per pair of terms r, R - r. The stage twiddle tables of FP64
-// transforms hold (c, t) instead of (Re w, Im w).
+// 9-point one (its internal twiddles factored the same way) 84 instead of 88, an untwiddled
+// 27-point one (3 x 9) 404 instead of 436, and a twiddled prime one (5, 7) two fewer per pair
+// of terms r, R - r. The stage twiddle tables of FP64 transforms hold (c, t) instead of
+// (Re w, Im w). The helpers are written for either precision; FP32 keeps complex products
+// (its passes are not bound by FP32 issue, and the folded forms cost the column passes
+// registers and occupancy).
 // ---------------------------------------------------------------------------------------
 
 // v = u (1 + i t)
-__device__ __forceinline__ cpx<double> tan_rot(cpx<double> u, double t) {
-  cpx<double> v;
+template <typename T>
+__device__ __forceinline__ cpx<T> tan_rot(cpx<T> u, T t) {
+  cpx<T> v;
   v.x = fma(-t, u.y, u.x);
   v.y = fma(t, u.x, u.y);
   return v;
 }
 
 // the 3-point outputs y1 = t - i S d, y2 = t + i S d with S = sin(2 pi / 3)
-__device__ __forceinline__ void dft3_tail(cpx<double> t, cpx<double> d, cpx<double>& y1,
-                                          cpx<double>& y2) {
-  const double S = rsin<double>(reg_offset(3) + 1);
+template <typename T>
+__device__ __forceinline__ void dft3_tail(cpx<T> t, cpx<T> d, cpx<T>& y1, cpx<T>& y2) {
+  const T S = rsin<T>(reg_offset(3) + 1);
   y1.x = fma(S, d.y, t.x);
   y1.y = fma(-S, d.x, t.y);
   y2.x = fma(-S, d.y, t.x);
@@ -207,10 +213,10 @@ __device__ __forceinline__ void dft3_tail(cpx<double> t, cpx<double> d, cpx<doub
 }
 
 // DFT_3 of (a, c1 v1, c2 v2), in place
-__device__ __forceinline__ void dft3_s2(cpx<double>& a, cpx<double>& v1, cpx<double>& v2,
-                                        double c1, double c2) {
-  const double h = rcos<double>(reg_offset(3) + 1);  // cos(2 pi / 3) = -1/2
-  cpx<double> q, s, d, t;
+template <typename T>
+__device__ __forceinline__ void dft3_s2(cpx<T>& a, cpx<T>& v1, cpx<T>& v2, T c1, T c2) {
+  const T h = rcos<T>(reg_offset(3) + 1);  // cos(2 pi / 3) = -1/2
+  cpx<T> q, s, d, t;
   q.x = c2 * v2.x;
   q.y = c2 * v2.y;
   s.x = fma(c1, v1.x, q.x);
@@ -226,9 +232,9 @@ __device__ __forceinline__ void dft3_s2(cpx<double>& a, cpx<double>& v1, cpx<dou
 
 // DFT_3 of (c0 v0, c1 v1, c2 v2), in place; the middle term c0 v0 - s/2 is formed as
 // y0 - (3/2) s from y0 = c0 v0 + s
-__device__ __forceinline__ void dft3_s3(cpx<double>& v0, cpx<double>& v1, cpx<double>& v2,
-                                        double c0, double c1, double c2) {
-  cpx<double> q, s, d, t;
+template <typename T>
+__device__ __forceinline__ void dft3_s3(cpx<T>& v0, cpx<T>& v1, cpx<T>& v2, T c0, T c1, T c2) {
+  cpx<T> q, s, d, t;
   q.x = c2 * v2.x;
   q.y = c2 * v2.y;
   s.x = fma(c1, v1.x, q.x);
@@ -237,15 +243,16 @@ __device__ __forceinline__ void dft3_s3(cpx<double>& v0, cpx<double>& v1, cpx<do
   d.y = fma(c1, v1.y, -q.y);
   v0.x = fma(c0, v0.x, s.x);
   v0.y = fma(c0, v0.y, s.y);
-  t.x = fma(-1.5, s.x, v0.x);
-  t.y = fma(-1.5, s.y, v0.y);
+  t.x = fma((T)-1.5, s.x, v0.x);
+  t.y = fma((T)-1.5, s.y, v0.y);
   dft3_tail(t, d, v1, v2);
 }
 
-// DFT_3 of (a, b, e), in place (the 12-instruction butterfly of RegDft<double, 3>)
-__device__ __forceinline__ void dft3_p(cpx<double>& a, cpx<double>& b, cpx<double>& e) {
-  const double h = rcos<double>(reg_offset(3) + 1);
-  cpx<double> s, d, t;
+// DFT_3 of (a, b, e), in place (the 12-instruction butterfly of RegDft<T, 3>)
+template <typename T>
+__device__ __forceinline__ void dft3_p(cpx<T>& a, cpx<T>& b, cpx<T>& e) {
+  const T h = rcos<T>(reg_offset(3) + 1);
+  cpx<T> s, d, t;
   s.x = b.x + e.x;
   s.y = b.y + e.y;
   d.x = b.x - e.x;
@@ -261,18 +268,19 @@ __device__ __forceinline__ void dft3_p(cpx<double>& a, cpx<double>& b, cpx<doubl
 // u[j2 + 3 k1] holds the output k1 of the 3-point DFT of column j2; the internal twiddles
 // exp(-2 pi i j2 k1 / 9) = C_m (1 - i tan(2 pi m / 9)), m = j2 k1, are factored as above.
 // Writes X[k1 + 3 k2] to u in natural order.
-__device__ __forceinline__ void dft9_rows(cpx<double> (&u)[9]) {
+template <typename T>
+__device__ __forceinline__ void dft9_rows(cpx<T> (&u)[9]) {
   constexpr int o9 = reg_offset(9);
-  const double C1 = rcos<double>(o9 + 1), C2 = rcos<double>(o9 + 2), C4 = rcos<double>(o9 + 4);
-  const double T1 = -c_rtan_d[o9 + 1], T2 = -c_rtan_d[o9 + 2], T4 = -c_rtan_d[o9 + 4];
+  const T C1 = rcos<T>(o9 + 1), C2 = rcos<T>(o9 + 2), C4 = rcos<T>(o9 + 4);
+  const T T1 = -rtan<T>(o9 + 1), T2 = -rtan<T>(o9 + 2), T4 = -rtan<T>(o9 + 4);
   // row k1 = 0: (V0[0], V1[0], V2[0]) at u[0], u[1], u[2]
-  cpx<double> a0 = u[0], a1 = u[1], a2 = u[2];
+  cpx<T> a0 = u[0], a1 = u[1], a2 = u[2];
   dft3_p(a0, a1, a2);
   // row k1 = 1: (V0[1], V1[1] w^1, V2[1] w^2) at u[3], u[4], u[5]
-  cpx<double> b0 = u[3], b1 = tan_rot(u[4], T1), b2 = tan_rot(u[5], T2);
+  cpx<T> b0 = u[3], b1 = tan_rot(u[4], T1), b2 = tan_rot(u[5], T2);
   dft3_s2(b0, b1, b2, C1, C2);
   // row k1 = 2: (V0[2], V1[2] w^2, V2[2] w^4) at u[6], u[7], u[8]
-  cpx<double> e0 = u[6], e1 = tan_rot(u[7], T2), e2 = tan_rot(u[8], T4);
+  cpx<T> e0 = u[6], e1 = tan_rot(u[7], T2), e2 = tan_rot(u[8], T4);
   dft3_s2(e0, e1, e2, C2, C4);
   u[0] = a0; u[3] = a1; u[6] = a2;
   u[1] = b0; u[4] = b1; u[7] = b2;
@@ -280,16 +288,18 @@ __device__ __forceinline__ void dft9_rows(cpx<double> (&u)[9]) {
 }
 
 // the column outputs of the 9-point split, regrouped so that u[j2 + 3 k1] = V_{j2}[k1]
-__device__ __forceinline__ void dft9_regroup(cpx<double> (&u)[9], const cpx<double> (&V)[3][3]) {
+template <typename T>
+__device__ __forceinline__ void dft9_regroup(cpx<T> (&u)[9], const cpx<T> (&V)[3][3]) {
 #pragma unroll
   for (int j2 = 0; j2 < 3; ++j2)
 #pragma unroll
     for (int k1 = 0; k1 < 3; ++k1) u[3 * k1 + j2] = V[j2][k1];
 }
 
-// DFT_9 of u without stage twiddles
-__device__ __forceinline__ void dft9_plain(cpx<double> (&u)[9]) {
-  cpx<double> V[3][3];
+// DFT_9 of u without twiddles on its inputs
+template <typename T>
+__device__ __forceinline__ void dft9_plain(cpx<T> (&u)[9]) {
+  cpx<T> V[3][3];
 #pragma unroll
   for (int j2 = 0; j2 < 3; ++j2) {
     V[j2][0] = u[j2];
@@ -301,13 +311,13 @@ __device__ __forceinline__ void dft9_plain(cpx<double> (&u)[9]) {
   dft9_rows(u);
 }
 
-// DFT_9 of (u0, w^{1 k} u1, ..., w^{8 k} u8) with the stage twiddles w^{r k} = c_r (1 + i t_r)
-// read as (c_r, t_r) from tw[r * step]; each column of the split loads its own three
-__device__ __forceinline__ void dft9_twiddled(cpx<double> (&u)[9], const cpx<double>* tw,
-                                              int step) {
-  cpx<double> V[3][3];
+// DFT_9 of (u0, w_1 u1, ..., w_8 u8) with w_r = c_r (1 + i t_r) given as (c_r, t_r) = tw(r);
+// each column of the split takes its own three
+template <typename T, typename TW>
+__device__ __forceinline__ void dft9_tw(cpx<T> (&u)[9], TW tw) {
+  cpx<T> V[3][3];
   {
-    const cpx<double> w3 = tw[3 * step], w6 = tw[6 * step];
+    const cpx<T> w3 = tw(3), w6 = tw(6);
     V[0][0] = u[0];
     V[0][1] = tan_rot(u[3], w3.y);
     V[0][2] = tan_rot(u[6], w6.y);
@@ -315,7 +325,7 @@ __device__ __forceinline__ void dft9_twiddled(cpx<double> (&u)[9], const cpx<dou
   }
 #pragma unroll
   for (int j2 = 1; j2 < 3; ++j2) {
-    const cpx<double> wa = tw[j2 * step], wb = tw[(j2 + 3) * step], wc = tw[(j2 + 6) * step];
+    const cpx<T> wa = tw(j2), wb = tw(j2 + 3), wc = tw(j2 + 6);
     V[j2][0] = tan_rot(u[j2], wa.y);
     V[j2][1] = tan_rot(u[j2 + 3], wb.y);
     V[j2][2] = tan_rot(u[j2 + 6], wc.y);
@@ -325,20 +335,46 @@ __device__ __forceinline__ void dft9_twiddled(cpx<double> (&u)[9], const cpx<dou
   dft9_rows(u);
 }
 
-// DFT_R of a prime R in a twiddled stage, (u0, w^{k} u1, ..., w^{(R-1) k} u_{R-1}) with the
-// stage twiddles (c_r, t_r) read from tw[r * step]: the pair sum and difference of terms r and
-// R - r become c_r v_r + q and c_r v_r - q with q = c_{R-r} v_{R-r} (one multiplication and two
-// multiply-adds a part), 12 instructions a pair instead of 14 with complex twiddle products
-template <int R>
-__device__ __forceinline__ void dft_prime_twiddled(cpx<double> (&u)[R], const cpx<double>* tw,
-                                                   int step) {
+// DFT_27 of u without twiddles on its inputs, split 3 x 9 as in RegDft (j = j2 + 9 j1 ->
+// k = k1 + 3 k2): 3-point DFTs over the columns j2, then for each k1 the 9-point DFT over j2 of
+// the column outputs times exp(-2 pi i j2 k1 / 27), factored as above
+template <typename T>
+__device__ __forceinline__ void dft27_plain(cpx<T> (&u)[27]) {
+  constexpr int o27 = reg_offset(27);
+#pragma unroll
+  for (int j2 = 0; j2 < 9; ++j2) dft3_p(u[j2], u[j2 + 9], u[j2 + 18]);
+  // the column outputs k1 sit at u[j2 + 9 k1]
+  cpx<T> w0[9], w1[9], w2[9];
+#pragma unroll
+  for (int j2 = 0; j2 < 9; ++j2) {
+    w0[j2] = u[j2];
+    w1[j2] = u[j2 + 9];
+    w2[j2] = u[j2 + 18];
+  }
+  dft9_plain(w0);
+  dft9_tw(w1, [&](int r) { return cpx<T>{rcos<T>(o27 + r), -rtan<T>(o27 + r)}; });
+  dft9_tw(w2, [&](int r) { return cpx<T>{rcos<T>(o27 + 2 * r), -rtan<T>(o27 + 2 * r)}; });
+#pragma unroll
+  for (int k2 = 0; k2 < 9; ++k2) {
+    u[3 * k2] = w0[k2];
+    u[1 + 3 * k2] = w1[k2];
+    u[2 + 3 * k2] = w2[k2];
+  }
+}
+
+// DFT_R of a prime R with twiddled inputs, (u0, w_1 u1, ..., w_{R-1} u_{R-1}), (c_r, t_r) =
+// tw[r * step]: the pair sum and difference of terms r and R - r become c_r v_r + q and
+// c_r v_r - q with q = c_{R-r} v_{R-r} (one multiplication and two multiply-adds a part), 12
+// instructions a pair instead of 14 with complex twiddle products
+template <typename T, int R>
+__device__ __forceinline__ void dft_prime_twiddled(cpx<T> (&u)[R], const cpx<T>* tw, int step) {
   constexpr int H = (R - 1) / 2;
-  cpx<double> y0 = u[0];
+  cpx<T> y0 = u[0];
 #pragma unroll
   for (int r = 1; r <= H; ++r) {
-    const cpx<double> wa = tw[r * step], wb = tw[(R - r) * step];
-    const cpx<double> va = tan_rot(u[r], wa.y), vb = tan_rot(u[R - r], wb.y);
-    cpx<double> q;
+    const cpx<T> wa = tw[r * step], wb = tw[(R - r) * step];
+    const cpx<T> va = tan_rot(u[r], wa.y), vb = tan_rot(u[R - r], wb.y);
+    cpx<T> q;
     q.x = wb.x * vb.x;
     q.y = wb.x * vb.y;
     u[r].x = fma(wa.x, va.x, q.x);
@@ -348,7 +384,56 @@ __device__ __forceinline__ void dft_prime_twiddled(cpx<double> (&u)[R], const cp
     y0.x += u[r].x;
     y0.y += u[r].y;
   }
-  prime_dft_tail<double, R>(u, y0);
+  prime_dft_tail<T, R>(u, y0);
+}
+
+// the untwiddled FP64 9- and 27-point DFTs with factored internal twiddles (in FP32 they cost
+// registers in the column passes and gained nothing: its passes are not bound by FP32 issue)
+template <>
+struct RegDft<double, 9, 3> {
+  static __device__ __forceinline__ void run(cpx<double> (&u)[9]) { dft9_plain(u); }
+};
+template <>
+struct RegDft<double, 27, 3> {
+  static __device__ __forceinline__ void run(cpx<double> (&u)[27]) { dft27_plain(u); }
+};
+
+// u_r *= w_r for r >= 1, w_r = (c_r, t_r) from tw[r * step]: u w = c (u_x - t u_y, u_y + t u_x),
+// four instructions, as a complex product
+template <typename T, int R>
+__device__ __forceinline__ void apply_twiddles(cpx<T> (&u)[R], const cpx<T>* tw, int step) {
+#pragma unroll
+  for (int r = 1; r < R; ++r) {
+    const cpx<T> w = tw[r * step];
+    const T ux = u[r].x;
+    u[r].x = w.x * fma(-w.y, u[r].y, ux);
+    u[r].y = w.x * fma(w.y, ux, u[r].y);
+  }
+}
+
+// the radices whose twiddled DFT folds the twiddle cosines into its own multiply-adds
+template <int R>
+__host__ __device__ constexpr bool folds_twiddles() {
+  return R == 3 || R == 5 || R == 7 || R == 9;
+}
+
+// DFT_R of (u0, w_1 u1, ..., w_{R-1} u_{R-1}) in a twiddled stage, w_r = (c_r, t_r) from
+// tw[r * step]
+template <typename T, int R>
+__device__ __forceinline__ void dft_twiddled(cpx<T> (&u)[R], const cpx<T>* tw, int step) {
+  if constexpr (R == 3) {
+    const cpx<T> w1 = tw[step], w2 = tw[2 * step];
+    u[1] = tan_rot(u[1], w1.y);
+    u[2] = tan_rot(u[2], w2.y);
+    dft3_s2(u[0], u[1], u[2], w1.x, w2.x);
+  } else if constexpr (R == 9) {
+    dft9_tw(u, [&](int r) { return tw[r * step]; });
+  } else if constexpr (R == 5 || R == 7) {
+    dft_prime_twiddled<T, R>(u, tw, step);
+  } else {
+    apply_twiddles<T, R>(u, tw, step);
+    RegDft<T, R>::run(u);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -440,42 +525,21 @@ __device__ __forceinline__ void reg_stage(Loc<T> in, Loc<T> out, int n, int p, i
 #pragma unroll
       for (int r = 0; r < R; ++r) u[r].y = flip_sign(u[r].y, m_in);
     }
-    if constexpr (sizeof(T) == 8 && (R == 3 || R == 5 || R == 7 || R == 9)) {
-      // FP64 radices 3, 5, 7 and 9: stage twiddles (c, t), w = c (1 + i t), folded into the DFT
-      if (p > 1) {
-        const int step = k * ts;
-        const cpx<T>* tw = sm + tw_base;
-        if constexpr (R == 3) {
-          const cpx<T> w1 = tw[step], w2 = tw[2 * step];
-          u[1] = tan_rot(u[1], w1.y);
-          u[2] = tan_rot(u[2], w2.y);
-          dft3_s2(u[0], u[1], u[2], w1.x, w2.x);
-        } else if constexpr (R == 9) {
-          dft9_twiddled(u, tw, step);
-        } else {
-          dft_prime_twiddled<R>(u, tw, step);
-        }
-      } else {
-        if constexpr (R == 9)
-          dft9_plain(u);
-        else
-          RegDft<T, R>::run(u);
-      }
+    if constexpr (sizeof(T) == 8 && folds_twiddles<R>()) {
+      if (p > 1)
+        dft_twiddled<T, R>(u, sm + tw_base, k * ts);
+      else
+        RegDft<T, R>::run(u);
     } else {
+      // one copy of the larger DFTs: the twiddles first, then the plain DFT; FP64 twiddles are
+      // (c, t), FP32 ones (Re w, Im w)
       if (p > 1) {
-        const int step = k * ts;
+        if constexpr (sizeof(T) == 8) {
+          apply_twiddles<T, R>(u, sm + tw_base, k * ts);
+        } else {
+          const int step = k * ts;
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          const cpx<T> w = sm[tw_base + r * step];
-          if constexpr (sizeof(T) == 8) {
-            // FP64 twiddle (c, t): u w = c (u_x - t u_y, u_y + t u_x), four instructions as a
-            // complex product
-            const T ux = u[r].x;
-            u[r].x = w.x * fma(-w.y, u[r].y, ux);
-            u[r].y = w.x * fma(w.y, ux, u[r].y);
-          } else {
-            u[r] = cmul(u[r], w);
-          }
+          for (int r = 1; r < R; ++r) u[r] = cmul(u[r], sm[tw_base + r * step]);
         }
       }
       RegDft<T, R>::run(u);

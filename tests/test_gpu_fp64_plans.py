@@ -7,7 +7,8 @@ length is placed on every axis (contiguous axis: line passes; middle axis: strid
 axis 0: projection pass), in 2-D and 3-D, and compared with the oracle at the operator
 tolerance of eq. (linsys) parity (1e-12 relative per application). The 243^3 cube of volume
 fraction 0.2 and contrast 1e3 is the benchmarked workload: one full application and three
-fixed CG iterations (Algorithm 2) are compared at full size.
+fixed CG iterations (Algorithm 2) are compared at full size. Plans with radices up to 27
+(set with hom_set_plan) are compared on axes 27, 81, 243 and 729.
 """
 import numpy as np
 import pytest
@@ -146,4 +147,32 @@ def test_cg_three_fixed_iterations_243_cubed():
     hist = H.hom_solve_history(P.h)
     assert np.allclose(hist, ref.history, rtol=1e-9, atol=0)
     assert abs(AH - sysn.energy(E, ref.x)) < AH_TOL * abs(AH)
+    P.close()
+
+
+PLAN27 = {"rmax64": 27, "smem_kb64": 110, "threads64": 256, "rmax32": 27, "smem_kb32": 110,
+          "threads32": 256, "two_line32": 1}
+
+
+@pytest.mark.parametrize("N", [(81, 5, 3), (3, 243, 5), (5, 3, 27), (27, 81), (3, 729)])
+@pytest.mark.parametrize("op", ["linear", "em"])
+def test_radix27_fp64_plans(N, op):
+    # FP64 plans with register radices up to 27 (81 = [27, 3], 243 = [27, 9], 27 = [27],
+    # 729 = [27, 27]): the untwiddled 27-point DFT split 3 x 9 with its internal twiddles
+    # factored into the 9-point rows, and behind it twiddled radices 3, 9 and 27
+    d = len(N)
+    ph = ms.box_phase(N, 0.6)
+    table = ms.isotropic_table([1.0, 10.0], d)
+    A = O.expand_phase(ph, table)[0, 0]
+    P = H.Problem(d, N, H.phase_material(ph, table))
+    H.hom_set_plan(P.h, PLAN27)
+    x = ms.random_field((d,) + N, 13)
+    y = P.field()
+    H.hom_apply(P.h, OPS[op], None, to_dev(x), y)
+    sysn = O.GaNi(A, d)
+    if op == "linear":
+        ref = sysn.matvec(x)
+    else:
+        ref = sysn.em_project(O.apply_A(A, x) - np.sqrt(10.0) * x)
+    assert rel(y.cpu().numpy(), ref) < OP_TOL
     P.close()
