@@ -663,14 +663,17 @@ def _run_ours(args, rank, world, local):
                        "device_ms": round(stats["time_ms"], 2), "A_H": AH,
                        "converged": bool(stats["converged"])},
     }
-    if not args.no_elastic:
+    # the studies after the timed step run at one GPU only: a replica run (N > 1) would hold
+    # every GPU while rank 0 repeats them, and the oracle's host timing belongs to N = 1
+    single = world == 1
+    if single and not args.no_elastic:
         line["elastic"] = elastic_step(min(args.steps, 10), 3, solves=True)
-    if not args.no_kappa:
+    if single and not args.no_kappa:
         # Section 4.6 in 3-D, reduced: 63^3 and its double grid 125^3, kappa 10, 100, 1000, all
         # four solvers (Richardson where its O(kappa) count stays within 8000 iterations)
         line["kappa_63"] = kappa_sweep(63, (10.0, 100.0, 1000.0),
                                        ("richardson", "cg", "chebyshev", "eyre_milton"), 8000)
-    if not args.no_served:
+    if single and not args.no_served:
         # a short served run (driver-visible): 12 requests over 0.5 s, Richardson capped at
         # 2000 iterations (--serve runs longer mixes with the cap at 1e5)
         sv = served_mix(12, 0.5, 64.0, 2000)
@@ -678,10 +681,12 @@ def _run_ours(args, rank, world, local):
                                              "fp64", "speedup_vs_fp64",
                                              "AH_max_rel_diff_fp32_refined_vs_fp64",
                                              "AH_compared_requests", "config")}
-    if not args.no_c4:
+    if single and not args.no_c4:
         line["c4_405_refined"] = c4_check()
-    if not args.no_cpu_baseline:
+    if single and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_cg_steps(1)
+    if not single:
+        line["studies"] = "elastic, kappa_63, served, c4_405_refined and cpu_baseline run at N = 1 only"
     return line
 
 
