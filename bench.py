@@ -370,6 +370,33 @@ def ncu_traffic(precision, kind):
     return NCU_TRAFFIC.get((precision, kind))
 
 
+# FP64 thread instructions (DADD + DFMA + DMUL) per launch of the FP64 CG step's pass kernels at
+# 243^3 (ncu smsp__sass_thread_inst_executed_op_{dadd,dfma,dmul}_pred_on.sum on GB300 of the
+# kernels as they are now; profiles/ gives the command). The strided pass runs 27.11 a complex
+# point: 84/9 + 106/9 + 18/3 for the [9, 9, 3] plan with cosine-factored twiddles.
+NCU_FP64_INST = {"line_fwd": 808.7e6, "strided": 585.9e6, "proj": 882.1e6, "line_inv": 765.1e6}
+
+
+def fp64_issue(pk, ms_step, steps, probe):
+    """The FP64 step against its instruction bound: the FP64 instructions ncu counts in each
+    pass kernel, over its measured time, as a fraction of the FP64 instruction rate the probe
+    measured on this GPU (the larger of DFMA and DADD instructions per second)."""
+    if tuple(N_GRID) != (243, 243, 243) or not probe:
+        return None
+    rate = max(probe["dfma_tflops"] / 2.0, probe["dadd_tinstr_per_s"]) * 1e12
+    out = {"rate_tinst_per_s": round(rate / 1e12, 4), "source": "ncu FP64 instruction counts "
+           "(NCU_FP64_INST) over the measured pass times and the probe's instruction rate"}
+    step_inst = 0.0
+    for k, v in pk.items():
+        if k in NCU_FP64_INST:
+            inst = NCU_FP64_INST[k]
+            step_inst += inst * v["launches"] / steps
+            out[k] = round(inst / (v["ms_avg"] * 1e-3) / rate, 4)
+    out["step_inst"] = step_inst
+    out["step_frac"] = round(step_inst / (ms_step * 1e-3) / rate, 4)
+    return out
+
+
 def pass_bytes(word=8, two_line=False, fused_cg=False):
     """Compulsory DRAM bytes of one launch of each pass kind in a CG step (word = 8 for FP64,
     4 for FP32). two_line: the 3-D scalar projection keeps two spectrum lines between its column
@@ -643,6 +670,7 @@ def _run_ours(args, rank, world, local):
                      "flops_per_launch": round(flops[dom]),
                      "achieved_radix_model": round(flops_radix[dom] / (dom_ms * 1e-3) / 1e12, 4),
                      "fp64_probe": fp64_peak,
+                     "fp64_issue_frac": fp64_issue(pk, ms_step, args.steps, fp64_peak),
                      "hbm_gbs_of_dominant": round(byts[dom] / (dom_ms * 1e-3) / 1e9, 1)},
         "passes": pk,
         "fp32_step": {"metric": "G·A matvecs/s at 243^3 (FP32 CG step, inner solver of the refinement, "

@@ -97,3 +97,29 @@ def test_flop_model_sums_to_the_fft_count_of_a_matvec(bench):
     nodes = 243 ** 3
     assert abs(per_step - 2 * 3 * 2.5 * nodes * math.log2(nodes)) < 1e-6 * per_step
     assert abs(flops["strided"] / 1e9 - 0.8526) < 1e-3  # one axis of three transforms
+
+
+def test_fp64_instruction_counts_match_the_factored_plan(bench):
+    # the stored ncu count of the FP64 strided pass at 243^3 is the count of its [9, 9, 3] plan
+    # with cosine-factored twiddles: an untwiddled 9-point DFT (84 instructions), a twiddled one
+    # (106) and a twiddled 3-point one (18), per complex point of the half spectrum's three
+    # components; the projection runs four such transforms on one line each
+    assert bench.plan_radices(243, 15) == [9, 9, 3]
+    per_point = 84 / 9 + 106 / 9 + 18 / 3
+    points = 243 * 243 * 122 * 3
+    assert abs(bench.NCU_FP64_INST["strided"] / points - per_point) < 0.02
+    assert bench.NCU_FP64_INST["proj"] > 4 / 3 * bench.NCU_FP64_INST["strided"]
+
+
+def test_fp64_issue_fraction(bench):
+    # pass times at exactly the instruction bound give a fraction of 1 per pass and per step
+    probe = {"dfma_tflops": 1.0, "dadd_tinstr_per_s": 0.5}
+    rate = 0.5e12
+    pk = {k: {"ms_avg": v / rate * 1e3, "launches": 2 if k == "strided" else 1}
+          for k, v in bench.NCU_FP64_INST.items()}
+    step_ms = sum(v["ms_avg"] * v["launches"] for v in pk.values())
+    out = bench.fp64_issue(pk, step_ms, 1, probe)
+    for k in bench.NCU_FP64_INST:
+        assert abs(out[k] - 1.0) < 1e-3
+    assert abs(out["step_frac"] - 1.0) < 1e-3
+    assert bench.fp64_issue(pk, step_ms, 1, None) is None
