@@ -242,6 +242,26 @@ int hom_solve_current(hom_problem* P, double* x_dev);
  * synchronises the stream; HOM_ERR_INVALID without an active session. */
 int hom_solve_nonconformity(hom_problem* P, double* value);
 
+/* Snapshot and restore of an FP64 solve session (a build extension; the paper's solves run to
+ * the end). A snapshot is everything the next hom_solve_iterate reads: the five solver vectors
+ * (5 x d x |M| doubles), the device scalars (step coefficients, norms, iteration count, stop
+ * flags, Richardson's buffer index), the recorded history and the host-side step counters.
+ * Restoring it into an active session of a problem created the same way (same d, grid,
+ * integration, coefficients and launch plan — results then agree bit for bit) whose session
+ * was begun with the same E, solver, stopping rule and iteration limit continues the solve
+ * exactly where the snapshot was taken; use: preempting a long solve (snapshot, end or
+ * destroy, later create, begin and restore). Every call synchronises the stream.
+ *
+ * hom_solve_snapshot_size writes the bytes a snapshot of P's active session takes (a header,
+ * the vectors and room for the whole history). hom_solve_snapshot writes the snapshot to the
+ * host buffer host_buf of `bytes` bytes (at least that size, else HOM_ERR_INVALID).
+ * hom_solve_restore reads one back; HOM_ERR_INVALID if it is not a snapshot, or was taken from
+ * a session of another shape, solver, stopping rule, limit or E. HOM_FP32_REFINED sessions:
+ * HOM_ERR_UNSUPPORTED; no active session: HOM_ERR_INVALID. */
+int hom_solve_snapshot_size(hom_problem* P, size_t* bytes);
+int hom_solve_snapshot(hom_problem* P, void* host_buf, size_t bytes);
+int hom_solve_restore(hom_problem* P, const void* host_buf, size_t bytes);
+
 /* Energy (A(E + x), E + x) and flux <A(E + x)> of a device field x_dev on the solve grid
  * (x_dev may be NULL for x = 0, the Voigt value of Section 4.3). Synchronises the stream. */
 int hom_energy(hom_problem* P, const double* E, const double* x_dev, double* energy, double* flux);

@@ -38,7 +38,8 @@ EXPORTED = ["hom_create", "hom_grid", "hom_bounds", "hom_apply", "hom_solve", "h
             "hom_batch_destroy", "hom_server_create", "hom_server_submit", "hom_server_step",
             "hom_server_poll", "hom_server_status", "hom_server_destroy", "hom_autotune",
             "hom_solve_history", "hom_solve_current", "hom_solve_nonconformity", "hom_restrict",
-            "hom_measure_fp64", "hom_debug_fail_alloc", "hom_debug_tma_stall", "hom_set_plan"]
+            "hom_measure_fp64", "hom_debug_fail_alloc", "hom_debug_tma_stall", "hom_set_plan",
+            "hom_solve_snapshot_size", "hom_solve_snapshot", "hom_solve_restore"]
 PASS_KINDS = ["line_fwd", "strided", "proj", "line_inv", "vector", "pot_inv", "pot_line",
               "pot_fwd"]
 
@@ -121,6 +122,9 @@ def _load():
     lib.hom_solve_history.argtypes = [vp, dp, ip, ctypes.POINTER(ctypes.c_int)]
     lib.hom_solve_current.argtypes = [vp, vp]
     lib.hom_solve_nonconformity.argtypes = [vp, dp]
+    lib.hom_solve_snapshot_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.hom_solve_snapshot.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.hom_solve_restore.argtypes = [vp, vp, ctypes.c_size_t]
     lib.hom_prolongate.argtypes = [vp, vp, vp, vp]
     lib.hom_restrict.argtypes = [vp, vp, vp]
     lib.hom_measure_fp64.argtypes = [ip, ip, vp, dp, dp]
@@ -332,6 +336,21 @@ def hom_solve_nonconformity(P):
     v = ctypes.c_double()
     _check(_lib.hom_solve_nonconformity(P, ctypes.byref(v)), "hom_solve_nonconformity")
     return v.value
+
+
+def hom_solve_snapshot(P):
+    """The active FP64 session of P as host bytes (a numpy uint8 array)."""
+    n = ctypes.c_size_t()
+    _check(_lib.hom_solve_snapshot_size(P, ctypes.byref(n)), "hom_solve_snapshot_size")
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(_lib.hom_solve_snapshot(P, buf.ctypes.data, n.value), "hom_solve_snapshot")
+    return buf
+
+
+def hom_solve_restore(P, snapshot):
+    """Restore a snapshot (from hom_solve_snapshot) into P's active session."""
+    buf = np.ascontiguousarray(snapshot, dtype=np.uint8)
+    return _check(_lib.hom_solve_restore(P, buf.ctypes.data, buf.nbytes), "hom_solve_restore")
 
 
 def hom_solve_end(P, d, x=None, allow_not_converged=False):

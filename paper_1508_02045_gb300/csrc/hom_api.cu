@@ -1460,6 +1460,123 @@ extern "C" int hom_solve_nonconformity(hom_problem* P, double* value) {
   return HOM_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// snapshot / restore of an FP64 session: the five solver vectors, the device scalars, the
+// stored history and the host-side counters behind a header that identifies the session
+// ---------------------------------------------------------------------------------------
+namespace {
+
+struct SnapHeader {
+  unsigned magic;
+  int nc, M[3];
+  long long nodes;
+  int integration, solver, stop, fixed, maxit, check, out_flags;
+  int issued, matvecs;
+  double E[kMaxComp], nE;
+  Scalars sc;            // the device scalars at the snapshot (hist is the source's pointer)
+  long long nhist_kept;  // history entries that follow the vectors
+};
+constexpr unsigned kSnapMagic = 0x686f6d53u;  // "homS"
+
+size_t snap_vec_bytes(const hom_problem* P) {
+  return sizeof(double) * 5 * (size_t)P->nc * (size_t)P->nodes;
+}
+
+// the size a snapshot of P's session takes: header, vectors, room for the whole history
+size_t snap_bytes(const hom_problem* P) {
+  return sizeof(SnapHeader) + snap_vec_bytes(P) + sizeof(double) * (size_t)P->hist_alloc;
+}
+
+bool snap_ok(const hom_problem* P) {
+  return P && P->sv.active && !P->sv.refined && P->sv.solver_begun;
+}
+
+}  // namespace
+
+extern "C" int hom_solve_snapshot_size(hom_problem* P, size_t* bytes) {
+  if (!P || !bytes || !P->sv.active) return HOM_ERR_INVALID;
+  if (P->sv.refined) return HOM_ERR_UNSUPPORTED;
+  if (!snap_ok(P)) return HOM_ERR_INVALID;
+  *bytes = snap_bytes(P);
+  return HOM_OK;
+}
+
+extern "C" int hom_solve_snapshot(hom_problem* P, void* host_buf, size_t bytes) {
+  if (!P || !host_buf || !P->sv.active) return HOM_ERR_INVALID;
+  if (P->sv.refined) return HOM_ERR_UNSUPPORTED;
+  if (!snap_ok(P) || bytes < snap_bytes(P)) return HOM_ERR_INVALID;
+  const SolveState& S_ = P->sv;
+  HOM_CUDA(cudaStreamSynchronize(P->stream));
+  SnapHeader h{};
+  h.magic = kSnapMagic;
+  h.nc = P->nc;
+  for (int a = 0; a < 3; ++a) h.M[a] = P->M[a];
+  h.nodes = P->nodes;
+  h.integration = P->integration;
+  h.solver = S_.solver;
+  h.stop = S_.stop;
+  h.fixed = S_.fixed ? 1 : 0;
+  h.maxit = S_.maxit;
+  h.check = S_.check;
+  h.out_flags = S_.out_flags;
+  h.issued = S_.issued;
+  h.matvecs = S_.matvecs;
+  for (int a = 0; a < kMaxComp; ++a) h.E[a] = S_.E[a];
+  h.nE = S_.nE;
+  int rc = poll(P, P->d_sc);
+  if (rc) return rc;
+  h.sc = *P->h_sc;
+  h.nhist_kept = (h.sc.hist != nullptr) ? std::min<long long>(h.sc.nhist, h.sc.hist_cap) : 0;
+  unsigned char* out = static_cast<unsigned char*>(host_buf);
+  std::memcpy(out, &h, sizeof(h));
+  cudaStream_t st = P->stream;
+  HOM_CUDA(cudaMemcpyAsync(out + sizeof(h), P->vbase, snap_vec_bytes(P), cudaMemcpyDeviceToHost,
+                           st));
+  if (h.nhist_kept > 0)
+    HOM_CUDA(cudaMemcpyAsync(out + sizeof(h) + snap_vec_bytes(P), h.sc.hist,
+                             sizeof(double) * (size_t)h.nhist_kept, cudaMemcpyDeviceToHost, st));
+  HOM_CUDA(cudaStreamSynchronize(st));
+  return check_last();
+}
+
+extern "C" int hom_solve_restore(hom_problem* P, const void* host_buf, size_t bytes) {
+  if (!P || !host_buf || !P->sv.active) return HOM_ERR_INVALID;
+  if (P->sv.refined) return HOM_ERR_UNSUPPORTED;
+  if (!snap_ok(P) || bytes < sizeof(SnapHeader)) return HOM_ERR_INVALID;
+  SnapHeader h;
+  std::memcpy(&h, host_buf, sizeof(h));
+  SolveState& S_ = P->sv;
+  // the same shape, solver, stopping rule, limits and macroscopic field as the session begun
+  // here; the coefficients and the launch plan are the caller's to keep equal
+  bool same = h.magic == kSnapMagic && h.nc == P->nc && h.nodes == P->nodes &&
+              h.integration == P->integration && h.solver == S_.solver && h.stop == S_.stop &&
+              h.fixed == (S_.fixed ? 1 : 0) && h.maxit == S_.maxit && h.nE == S_.nE &&
+              h.nhist_kept >= 0 &&
+              bytes >= sizeof(h) + snap_vec_bytes(P) + sizeof(double) * (size_t)h.nhist_kept;
+  for (int a = 0; a < 3; ++a) same = same && h.M[a] == P->M[a];
+  for (int a = 0; a < kMaxComp; ++a) same = same && h.E[a] == S_.E[a];
+  if (!same) return HOM_ERR_INVALID;
+  cudaStream_t st = P->stream;
+  int rc = poll(P, P->d_sc);  // also waits for the steps already enqueued
+  if (rc) return rc;
+  Scalars sc = h.sc;
+  sc.hist = P->h_sc->hist;  // this session's history buffer and capacity
+  sc.hist_cap = P->h_sc->hist_cap;
+  const unsigned char* in = static_cast<const unsigned char*>(host_buf);
+  HOM_CUDA(cudaMemcpyAsync(P->vbase, in + sizeof(h), snap_vec_bytes(P), cudaMemcpyHostToDevice,
+                           st));
+  const long long keep = sc.hist ? std::min<long long>(h.nhist_kept, sc.hist_cap) : 0;
+  if (keep > 0)
+    HOM_CUDA(cudaMemcpyAsync(sc.hist, in + sizeof(h) + snap_vec_bytes(P),
+                             sizeof(double) * (size_t)keep, cudaMemcpyHostToDevice, st));
+  if ((rc = upload_scalars(P, P->d_sc, sc))) return rc;  // synchronises the stream
+  S_.issued = h.issued;
+  S_.matvecs = h.matvecs;
+  S_.check = h.check;
+  S_.out_flags = h.out_flags;
+  return check_last();
+}
+
 extern "C" int hom_solve(hom_problem* P, const double* E, int solver, double tol,
                          const hom_opts* opts, double* x_dev, double* AH_EE, double* flux,
                          hom_stats* stats) {
