@@ -1470,7 +1470,7 @@ struct SnapHeader {
   unsigned magic;
   int nc, M[3];
   long long nodes;
-  int integration, solver, stop, fixed, maxit, check, out_flags;
+  int integration, solver, stop, fixed, maxit;
   int issued, matvecs;
   double E[kMaxComp], nE;
   Scalars sc;            // the device scalars at the snapshot (hist is the source's pointer)
@@ -1517,8 +1517,6 @@ extern "C" int hom_solve_snapshot(hom_problem* P, void* host_buf, size_t bytes) 
   h.stop = S_.stop;
   h.fixed = S_.fixed ? 1 : 0;
   h.maxit = S_.maxit;
-  h.check = S_.check;
-  h.out_flags = S_.out_flags;
   h.issued = S_.issued;
   h.matvecs = S_.matvecs;
   for (int a = 0; a < kMaxComp; ++a) h.E[a] = S_.E[a];
@@ -1570,10 +1568,9 @@ extern "C" int hom_solve_restore(hom_problem* P, const void* host_buf, size_t by
     HOM_CUDA(cudaMemcpyAsync(sc.hist, in + sizeof(h) + snap_vec_bytes(P),
                              sizeof(double) * (size_t)keep, cudaMemcpyHostToDevice, st));
   if ((rc = upload_scalars(P, P->d_sc, sc))) return rc;  // synchronises the stream
+  // the polling interval and output flags stay those this session was begun with
   S_.issued = h.issued;
   S_.matvecs = h.matvecs;
-  S_.check = h.check;
-  S_.out_flags = h.out_flags;
   return check_last();
 }
 
