@@ -256,8 +256,10 @@ int hom_solve_nonconformity(hom_problem* P, double* value);
  * the vectors and room for the whole history). hom_solve_snapshot writes the snapshot to the
  * host buffer host_buf of `bytes` bytes (at least that size, else HOM_ERR_INVALID).
  * hom_solve_restore reads one back; HOM_ERR_INVALID if it is not a snapshot, or was taken from
- * a session of another shape, solver, stopping rule, limit or E. HOM_FP32_REFINED sessions:
- * HOM_ERR_UNSUPPORTED; no active session: HOM_ERR_INVALID. */
+ * a session of another shape, solver, stopping rule, limit or E. A snapshot holds the
+ * library's internal scalar layout: restore it with the same build of the library that wrote
+ * it. The restoring session keeps its own polling interval and output flags.
+ * HOM_FP32_REFINED sessions: HOM_ERR_UNSUPPORTED; no active session: HOM_ERR_INVALID. */
 int hom_solve_snapshot_size(hom_problem* P, size_t* bytes);
 int hom_solve_snapshot(hom_problem* P, void* host_buf, size_t bytes);
 int hom_solve_restore(hom_problem* P, const void* host_buf, size_t bytes);
